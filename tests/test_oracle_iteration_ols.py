@@ -1,0 +1,140 @@
+"""Pins of the FP64 oracle for the general iteration and for OLS (CPU only)."""
+import numpy as np
+import pytest
+
+import linview_inputs as li
+from oracle import iteration as oi
+from oracle import ols as oo
+from oracle import powers as op
+from oracle.metrics import rel_frob
+
+
+# ---------------------------------------------------------------- iteration
+@pytest.mark.parametrize("n,p,k,r", [(8, 3, 16, 1), (16, 5, 8, 2), (5, 1, 4, 3)])
+def test_iteration_incremental_and_hybrid_match_reeval(n, p, k, r):
+    a, b, t0 = li.iteration_inputs(n, p, seed=n)
+    inc = oi.IncrementalIteration(a, b, t0, k)
+    hyb = oi.HybridIteration(a, b, t0, k)
+    acur = a.copy()
+    for (u, v) in li.lowrank_update_stream(n, r, 3, seed=n + 7, sigma=0.2):
+        U, V = inc.apply(u, v)
+        hyb.apply(u, v)
+        acur += u @ v.T
+        ref = oi.reeval(acur, b, t0, k)
+        for i in range(1, k + 1):
+            assert rel_frob(inc.t[i], ref[i]) < 1e-12
+            assert rel_frob(hyb.t[i], ref[i]) < 1e-12
+            # Appendix B: U_i is n x i and V_i is p x i for a rank-1 update
+            assert U[i].shape == (n, i * r) and V[i].shape == (p, i * r)
+
+
+def test_iteration_closed_form_scalar_plus_rank1():
+    # A' = lam I + u v^T: A'^j = lam^j I + c_j u v^T, c_j = ((lam+alpha)^j - lam^j)/alpha,
+    # T_i = A'^i T_0 + sum_{j<i} A'^j B  (unrolled form, Section 4.3)
+    n, p, k, lam = 6, 2, 16, 0.8
+    _, b, t0 = li.iteration_inputs(n, p, seed=3)
+    g = np.random.default_rng(5)
+    u = g.standard_normal((n, 1)) * 0.3
+    v = g.standard_normal((n, 1)) * 0.3
+    alpha = float((v.T @ u)[0, 0])
+    inc = oi.IncrementalIteration(lam * np.eye(n), b, t0, k)
+    inc.apply(u, v)
+
+    def apow(j):
+        return lam ** j * np.eye(n) + ((lam + alpha) ** j - lam ** j) / alpha * (u @ v.T)
+
+    for i in range(1, k + 1):
+        ti = apow(i) @ t0 + sum(apow(j) for j in range(i)) @ b
+        assert rel_frob(inc.t[i], ti) < 1e-13
+
+
+def test_iteration_unrolled_identity():
+    # T_{i+s} = A^s T_i + (A^{s-1} + ... + I) B  (Section 4.3)
+    n, p, k = 9, 4, 16
+    a, b, t0 = li.iteration_inputs(n, p, seed=4)
+    t = oi.reeval(a, b, t0, k)
+    pw = op.reeval_powers(a, 8)
+    for s in (1, 2, 4, 8):
+        ssum = op.paper_sums(a, s) if s > 1 else np.eye(n)
+        for i in (0, 3, 8):
+            assert rel_frob(t[i + s], pw[s] @ t[i] + ssum @ b) < 1e-12
+
+
+def _unit(x):
+    return x / np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("n,p,k", [(12, 3, 16), (512, 64, 16)])
+def test_iteration_adjoint_central_fd(n, p, k):
+    # central differences, h = 1e-3, FP64; 8 random unit directions + single entries
+    a, b, t0 = li.iteration_inputs(n, p, seed=21)
+    da, db, dt0 = oi.adjoint(a, b, t0, k)
+    h = 1e-3
+    g = np.random.default_rng(22)
+    dirs = [_unit(li.normal((n, n), seed=30 + t)) for t in range(8)]
+    for _ in range(8 if n > 100 else 16):
+        e = np.zeros((n, n)); e[g.integers(n), g.integers(n)] = 1.0
+        dirs.append(e)
+    # unit directions: |<dA, E>| <= ||dA||_F, and the O(h^2) truncation term is
+    # far below 1e-6 ||dA||_F; a dropped or mis-signed term would be O(||dA||_F)
+    gscale = float(np.linalg.norm(da))
+    for e in dirs:
+        fd = (oi.loss(a + h * e, b, t0, k) - oi.loss(a - h * e, b, t0, k)) / (2 * h)
+        an = float(np.sum(da * e))
+        assert abs(fd - an) <= 1e-6 * gscale, (fd, an)
+    for t in range(3):
+        e = _unit(li.normal((n, p), seed=40 + t))
+        fd = (oi.loss(a, b + h * e, t0, k) - oi.loss(a, b - h * e, t0, k)) / (2 * h)
+        assert abs(fd - float(np.sum(db * e))) <= 1e-6 * float(np.linalg.norm(db))
+        fd = (oi.loss(a, b, t0 + h * e, k) - oi.loss(a, b, t0 - h * e, k)) / (2 * h)
+        assert abs(fd - float(np.sum(dt0 * e))) <= 1e-6 * float(np.linalg.norm(dt0))
+
+
+# ---------------------------------------------------------------------- OLS
+def test_sherman_morrison_vs_library_inverse():
+    n = 20
+    g = np.random.default_rng(1)
+    e = g.standard_normal((n, n)) + n * np.eye(n)
+    u = g.standard_normal(n)
+    v = g.standard_normal(n)
+    einv = np.linalg.inv(e)
+    got = einv + oo.sherman_morrison(einv, u, v)
+    assert rel_frob(got, np.linalg.inv(e + np.outer(u, v))) < 1e-13
+
+
+def test_sm_two_step_row_change():
+    m, n, p = 60, 12, 2
+    x, y, _ = li.ols_inputs(m, n, p, seed=2, frac=0.25)
+    r = oo.reeval(x, y)
+    d = np.random.default_rng(3).standard_normal(n)
+    w2 = oo.sm_two_step(r["W"], x, 17, d)
+    x2 = x.copy(); x2[17] += d
+    assert rel_frob(w2, np.linalg.inv(x2.T @ x2)) < 1e-9
+
+
+@pytest.mark.parametrize("k", [1, 4, 16])
+def test_woodbury_row_blocks_vs_sm_and_lstsq(k):
+    m, n, p = 400, 24, 3
+    x, y, _ = li.ols_inputs(m, n, p, seed=5)
+    a = oo.IncrementalOLS(x, y)
+    b = oo.IncrementalOLS(x, y)
+    for rows, new in li.ols_row_replacements(m, n, k, 3, seed=6):
+        a.replace_rows(rows, new, "woodbury")
+        b.replace_rows(rows, new, "sm")
+    ref = oo.reeval(a.x, y)
+    assert np.array_equal(a.x, b.x)
+    assert rel_frob(a.w, ref["W"]) < 1e-9
+    assert rel_frob(b.w, ref["W"]) < 1e-9
+    assert rel_frob(a.z, ref["Z"]) < 1e-13
+    assert rel_frob(a.xty, ref["XtY"]) < 1e-13
+    beta_ls = np.linalg.lstsq(a.x, y, rcond=None)[0]   # independent library solver
+    assert rel_frob(a.beta, beta_ls) < 1e-8
+
+
+def test_ols_inputs_are_ill_conditioned():
+    # 10% of columns scaled by 1e-2: kappa(X^T X) ~ 1e4 x ((sqrt m + sqrt n)/(sqrt m - sqrt n))^2
+    m, n = 4096, 128
+    x, _, cols = li.ols_inputs(m, n, 1, seed=0)
+    assert len(cols) == round(0.1 * n)
+    kappa = np.linalg.cond(x.T @ x)
+    assert 5e3 < kappa < 1e5
