@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark: incremental view refresh of A^16 and S' = A + ... + A^16 on one GB300.
+
+Workload (the paper's powers / sums-of-powers experiments, Section 6, at the
+GPU-sized configuration): A is 8192 x 8192 FP32 with i.i.d. N(0,1)/(2 sqrt n)
+entries; a stream of rank-1 row updates dA = e_i v^T (i uniform, v ~
+N(0, 0.01^2)) arrives; after every update all nine views (A, A^2, A^4, A^8,
+A^16, S'_2, S'_4, S'_8, S'_16) are refreshed in place by the exponential-model
+trigger.  A step is one update = one refresh of every view.
+
+Printed JSON line: refreshes/s (device-timed, inputs resident), e2e through the
+public API with host buffers, p50/p99 step latency, the view-pass kernels'
+achieved HBM bandwidth against the measured copy bandwidth, GPU re-evaluation of
+the same views in three GEMM arithmetics, and the FP64 CPU oracle on a bounded
+sample (``cpu_baseline``).  ``--impl reference`` times the FP64 oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("view refreshes/s incremental vs GPU re-eval, 1 GB300, rel err≤1e-4; "
+          "p99 latency")
+UNIT = "refreshes/s"
+WORKLOAD = ("A^16 and S'=sum_{i=1..16} A^i (9 views) maintained under rank-1 row updates "
+            "dA=e_i v^T, n=8192, FP32, A~N(0,1)/(2 sqrt n), v~N(0,0.01^2)")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--k", type=int, default=16)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--reeval-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=3, help="oracle updates timed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _dist_init(ws, local, use_cuda):
+    import torch
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        if use_cuda:
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    return dist if ws > 1 else None
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(dist, x, use_cuda):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if use_cuda else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling during the timed region (200 ms period)."""
+
+    def __init__(self, uuid, enabled=True):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+        self.enabled = enabled
+
+    def start(self):
+        if not self.enabled:
+            return
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        q = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            if self.uuid and self.uuid not in f[0]:
+                continue
+            rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _uuid():
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
+    None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_1403_6968_gb300", "csrc", "lv_pass.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    e = d.get(kernel)
+    if not e or e.get("lv_pass_sha256_16") != h:
+        return None
+    return e.get("dram_bytes_per_launch_full_size")
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(n, k, updates, seed=0):
+    """The FP64 oracle's incremental refresh (as it stands) on ``updates`` row
+    updates of the same workload; returns (refreshes/s, seconds, setup s)."""
+    import numpy as np
+    import linview_inputs as li
+    from oracle import powers as op
+    a = li.power_matrix(n, seed=seed, dtype=np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    inc = op.IncrementalPowers(a, k, sums=True)
+    setup = time.perf_counter() - t0
+    ups = li.row_update_stream(n, updates, seed=seed + 1000, dtype=np.float32)
+    t0 = time.perf_counter()
+    for i, v in ups:
+        inc.apply_row(i, v.astype(np.float64))
+    dt = time.perf_counter() - t0
+    return updates / dt, dt, setup
+
+
+def _cores():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import linview_inputs as li
+    from oracle import powers as op
+    n, k = args.n, args.k
+    a = li.power_matrix(n, seed=0, dtype=np.float32).astype(np.float64)
+    inc = op.IncrementalPowers(a, k, sums=True)
+    ups = li.row_update_stream(n, args.warmup + args.steps, seed=0, dtype=np.float32)
+    for i, v in ups[:args.warmup]:
+        inc.apply_row(i, v.astype(np.float64))
+    lat = []
+    t0 = time.perf_counter()
+    for i, v in ups[args.warmup:]:
+        s = time.perf_counter()
+        inc.apply_row(i, v.astype(np.float64))
+        lat.append(time.perf_counter() - s)
+    dt = time.perf_counter() - t0
+    val = args.steps / dt
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "strategy": "FP64 CPU oracle, incremental "
+                      "exponential model (numpy BLAS)"},
+           "latency_ms": {"p50": 1e3 * statistics.median(lat),
+                          "p99": 1e3 * float(np.percentile(lat, 99))},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                            "sample": f"{args.steps} row updates at n={n} after {args.warmup} "
+                                      "warm-up updates (views initialised by the oracle's own "
+                                      "re-evaluation, untimed)"},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    dist = _dist_init(ws, local, True)
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    import linview_inputs as li
+    from paper_1403_6968_gb300 import Program
+
+    n, k = args.n, args.k
+    L = k.bit_length() - 1
+    K, W, E = args.steps, args.warmup, args.e2e_steps
+    a = li.power_matrix(n, seed=rank, dtype=np.float32)
+    ups = li.row_update_stream(n, W + K + E + args.reeval_steps + 1, seed=rank,
+                               dtype=np.float32)
+    dev_v = [torch.from_numpy(v).cuda() for _, v in ups]
+    rows = [i for i, _ in ups]
+    prog = Program("power_sum", [torch.from_numpy(a).cuda()], k=k, r_max=1)
+    stream = torch.cuda.current_stream()
+    for t in range(W):
+        prog.apply_row_delta(rows[t], dev_v[t])
+    torch.cuda.synchronize()
+    _barrier(dist)
+    clocks = Clocks(_uuid(), enabled=not args.no_clocks)
+    clocks.start()
+    prog.reset_stats()
+    prog.set_profiling(True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for t in range(K):
+        prog.apply_row_delta(rows[W + t], dev_v[W + t])
+        evs[t + 1].record(stream)
+    torch.cuda.synchronize()
+    _barrier(dist)
+    clk = clocks.stop()
+    prog.set_profiling(False)
+    lat = [evs[t].elapsed_time(evs[t + 1]) for t in range(K)]
+    tot_ms = evs[0].elapsed_time(evs[K])
+    st_all = prog.pass_stats(0)
+    st_f = prog.pass_stats(1)
+    st_u = prog.pass_stats(2)
+    prog.sync()
+    max_ms = _max_over_ranks(dist, tot_ms, True)
+    value = ws * K / (max_ms / 1e3)
+
+    # roofline of the dominant view-pass kernel (per-launch algorithmic bytes:
+    # one read + one write of an n x n FP32 view)
+    peaks = _peaks()
+    peak = peaks.get("hbm_gbs") if peaks else 6800.0
+    peak_src = "measured" if peaks else "fallback"
+    dom, st = ("lv::update_pass_kernel", st_u) if st_u["ms"] >= st_f["ms"] else \
+        ("lv::fused_pass_kernel", st_f)
+    per_launch = st["bytes"] / max(st["launches"], 1)
+    avg_s = st["ms"] / 1e3 / max(st["launches"], 1)
+    achieved = per_launch / avg_s / 1e9
+    other = st_f if st is st_u else st_u
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": _traffic(dom), "kernel": dom,
+            "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_launch": per_launch,
+            "launches": st["launches"], "avg_launch_us": avg_s * 1e6,
+            "all_view_passes": {"launches": st_all["launches"],
+                                "achieved_gbs": st_all["bytes"] / (st_all["ms"] / 1e3) / 1e9},
+            "other_pass_kernel": {"launches": other["launches"],
+                                  "achieved_gbs": (other["bytes"] / (other["ms"] / 1e3) / 1e9)
+                                  if other["ms"] > 0 else None}}
+    bytes_per_refresh = (2 * L + 1) * 2.0 * n * n * 4
+    step_s = max_ms / 1e3 / K
+
+    # e2e through the public API: host v (pinned) in, one refreshed row of
+    # A^16 out, every step
+    pin_v = [torch.from_numpy(v).pin_memory() for _, v in ups[W + K:W + K + E]]
+    row_out = torch.empty((1, n), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    _barrier(dist)
+    t0 = time.perf_counter()
+    for t in range(E):
+        i = rows[W + K + t]
+        prog.apply_row_delta(i, pin_v[t])
+        prog.read_view_rows(L, i, 1, out=row_out)   # synchronises the stream
+    e2e_s = _max_over_ranks(dist, time.perf_counter() - t0, True)
+    e2e = {"value": ws * E / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
+           "d2h_bytes_per_step": 4 * n, "steps": E}
+
+    # GPU re-evaluation of the same views: apply dA to A, recompute all views
+    reeval = {}
+    samp = [0, n // 3, n - 1]
+    inc_rows = {j: prog.read_view_rows(j, 0, n)[samp] for j in (L, 2 * L)}
+    aptr, ald = prog.view_device_ptr(0)
+    base = None
+    for mode in ("fp32", "bf16x9", "tf32"):
+        prog.set_reeval_mode(mode)
+        prog.reeval()
+        torch.cuda.synchronize()
+        got = {j: prog.read_view_rows(j, 0, n)[samp] for j in (L, 2 * L)}
+        if base is None:
+            base = got
+        errs = {("P16" if j == L else "S16"): float(np.linalg.norm(got[j] - inc_rows[j]) /
+                                                    np.linalg.norm(inc_rows[j])) for j in got}
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(args.reeval_steps):
+            # the re-evaluation strategy: apply the update to A, then recompute
+            ti = W + K + E + t
+            u = torch.zeros((1, n), dtype=torch.float32, device="cuda")
+            u[0, rows[ti]] = 1.0
+            vv = dev_v[ti].reshape(1, n)
+            _apply_to_a(aptr, ald, n, u, vv)
+            prog.reeval()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.reeval_steps
+        reeval[mode] = {"refreshes_per_s": 1e3 / ms, "ms_per_refresh": ms,
+                        "rel_err_vs_incremental_sampled_rows": errs}
+    acc = [m for m in ("fp32", "bf16x9") if max(reeval[m]["rel_err_vs_incremental_sampled_rows"]
+                                                .values()) <= 1e-4]
+    fastest_acc = max(acc, key=lambda m: reeval[m]["refreshes_per_s"]) if acc else None
+    fastest_any = max(reeval, key=lambda m: reeval[m]["refreshes_per_s"])
+    speed = {"vs_fastest_accurate_reeval": (value / ws) / reeval[fastest_acc]["refreshes_per_s"]
+             if fastest_acc else None, "fastest_accurate_reeval": fastest_acc,
+             "vs_fastest_any_reeval": (value / ws) / reeval[fastest_any]["refreshes_per_s"],
+             "fastest_any_reeval": fastest_any}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+           "warmup": W, "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": n, "k": k, "views": 2 * L + 1,
+                      "update": "rank-1 row", "parallelism": "replicas" if ws > 1 else "single",
+                      "l2": "inputs larger than L2: 9 views x 268 MB = 2.4 GB per refresh",
+                      "bytes_per_refresh_algorithmic": bytes_per_refresh},
+           "latency_ms": {"p50": statistics.median(lat), "p99": float(np.percentile(lat, 99)),
+                          "max": max(lat)},
+           "achieved_refresh_gbs": bytes_per_refresh / step_s / 1e9,
+           "roofline": roof, "e2e": e2e, "gpu_launches": st_all["all_launches"],
+           "reeval": reeval, "speedup": speed, "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, dt, setup = cpu_oracle_rate(n, k, args.cpu_sample)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                               "sample": f"{args.cpu_sample} rank-1 row updates of the same "
+                                         f"workload at n={n} (FP64 numpy oracle; its own "
+                                         f"re-evaluation setup of {setup:.1f} s untimed)"}
+    prog.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _apply_to_a(aptr, ald, n, u, v):
+    """A += u v^T through the library's stand-alone level pass (update only)."""
+    import ctypes as C
+    from paper_1403_6968_gb300 import _lib as L
+    from paper_1403_6968_gb300.linview import _stream_ptr
+    L.call("linview_level_pass", L.F32, n, C.c_void_p(aptr), ald, C.c_void_p(u.data_ptr()),
+           C.c_void_p(v.data_ptr()), n, 1, None, None, 1, _stream_ptr())
+
+
+def main():
+    args = _args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -108,6 +108,16 @@ def power_rows(a: np.ndarray, rows, k: int):
     return pw, sm
 
 
+def level_products(p, u, v):
+    """One level of Appendix A on a view P_h with factors U_h, V_h:
+    (P_h U_h, P_h^T V_h, P_h + U_h V_h^T), products on the view before the
+    update (the plain definitions)."""
+    p = np.asarray(p, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    return p @ u, p.T @ v, p + u @ v.T
+
+
 # --------------------------------------------------------------------------
 # Incremental maintenance
 # --------------------------------------------------------------------------

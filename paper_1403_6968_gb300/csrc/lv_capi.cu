@@ -1,0 +1,1095 @@
+// C ABI and program engine of the GB300 LINVIEW library (arXiv 1403.6968).
+//
+// A program owns its views (materialised in HBM, row-major, leading
+// dimension padded to a multiple of 256 elements and rows to a multiple of
+// kBatch so that every TMA box of a view pass lies inside the allocation),
+// the factor arenas of the exponential model (column-major n x R_cap: U
+// grows left to right, V grows right to left so that V_{2h} = [Y_h, V_h]
+// stays contiguous and pairs column by column with U_{2h} = [U_h, X'_h]),
+// the partial-sum buffers of the view passes and a device status word.
+#include <cublas_v2.h>
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/linview.h"
+#include "lv_device.cuh"
+#include "lv_internal.h"
+
+using namespace lv;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static linview_status fail(linview_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define LV_CUDA(expr)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(LINVIEW_EDEVICE, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                    \
+  } while (0)
+
+#define LV_BLAS(expr)                                                                     \
+  do {                                                                                    \
+    cublasStatus_t e_ = (expr);                                                           \
+    if (e_ != CUBLAS_STATUS_SUCCESS)                                                      \
+      return fail(LINVIEW_EDEVICE, "%s failed: cublas status %d (%s:%d)", #expr, (int)e_, \
+                  __FILE__, __LINE__);                                                    \
+  } while (0)
+
+#define LV_TRY(expr)                        \
+  do {                                      \
+    linview_status s_ = (expr);             \
+    if (s_ != LINVIEW_OK) return s_;        \
+  } while (0)
+
+static int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// ---------------------------------------------------------------------------
+// program
+// ---------------------------------------------------------------------------
+struct View {
+  void* ptr = nullptr;
+  int64_t rows = 0, cols = 0, ld = 0;
+  bool square = false;  // has a tensor map for view passes
+  CUtensorMap tmap;
+};
+
+struct linview_program {
+  linview_program_desc d;
+  int elem = 4;
+  int device = 0;
+  int sms = 148;
+  cublasHandle_t blas = nullptr;
+  cusolverDnHandle_t solver = nullptr;
+  std::vector<void*> allocs;
+  std::vector<View> views;
+  int L = 0;  // log2 k for powers
+  // factor arenas
+  void* Uar = nullptr;
+  void* Var = nullptr;
+  void* War = nullptr;
+  int64_t fs = 0;
+  int Rcap = 0;
+  // partial sums of the view passes
+  void* Xpart = nullptr;
+  void* Ypart = nullptr;
+  int64_t part_cs = 0, xp_s = 0, yp_q = 0;
+  double* Cpart = nullptr;
+  unsigned* ticket = nullptr;
+  double* C = nullptr;
+  unsigned* status = nullptr;
+  // host -> device staging for host-side update factors
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  int64_t updates = 0;
+  // iteration
+  void* Tpanel = nullptr;
+  int64_t ldT = 0;
+  void* Bm = nullptr;
+  int64_t ldB = 0;
+  void* Kar = nullptr;  // Krylov blocks K_0..K_{k-1}, column-major n x k r_max
+  void* V1 = nullptr;   // input right factor, column-major n x r_max
+  void* Mr = nullptr;   // T_i^T V blocks in reverse order, p x k r_max
+  void* Gpanel = nullptr;
+  int64_t ldG = 0;
+  // power adjoint work
+  void* Gw0 = nullptr;
+  void* Gw1 = nullptr;
+  // profiling
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec {
+    int e0, e1, kind;
+    double bytes;
+  };
+  std::vector<Rec> ev_recs;
+  int64_t all_launches = 0;
+};
+
+static linview_status dalloc(linview_program* p, size_t bytes, void** out) {
+  void* ptr = nullptr;
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMalloc(&ptr, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(LINVIEW_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  p->allocs.push_back(ptr);
+  LV_CUDA(cudaMemset(ptr, 0, bytes));
+  *out = ptr;
+  return LINVIEW_OK;
+}
+
+static linview_status add_square_view(linview_program* p, int64_t n) {
+  View v;
+  v.rows = n;
+  v.cols = n;
+  v.ld = rup(n, 256);
+  const int64_t rows_pad = rup(n, kBatch);
+  LV_TRY(dalloc(p, (size_t)(rows_pad * v.ld * p->elem), &v.ptr));
+  v.square = true;
+  if (!make_tmap(&v.tmap, v.ptr, p->elem, v.ld, rows_pad, v.ld))
+    return fail(LINVIEW_EDEVICE, "cuTensorMapEncodeTiled failed for an %lld x %lld view",
+                (long long)n, (long long)n);
+  p->views.push_back(v);
+  return LINVIEW_OK;
+}
+
+static linview_status add_rect_view(linview_program* p, void* ptr, int64_t rows, int64_t cols,
+                                    int64_t ld) {
+  View v;
+  v.ptr = ptr;
+  v.rows = rows;
+  v.cols = cols;
+  v.ld = ld;
+  p->views.push_back(v);
+  return LINVIEW_OK;
+}
+
+static linview_status copy_in(void* dst, int64_t ldd, const void* src, int64_t lds, int64_t rows,
+                              int64_t cols, int elem, int on_device, cudaStream_t s) {
+  if (rows == 0 || cols == 0) return LINVIEW_OK;
+  LV_CUDA(cudaMemcpy2DAsync(dst, ldd * elem, src, lds * elem, cols * elem, rows,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  return LINVIEW_OK;
+}
+
+static linview_status ensure_stage(linview_program* p, size_t bytes) {
+  if (p->stage_bytes >= bytes) return LINVIEW_OK;
+  void* np = nullptr;
+  LV_TRY(dalloc(p, bytes, &np));
+  p->stage = np;
+  p->stage_bytes = bytes;
+  return LINVIEW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// profiling of view passes
+// ---------------------------------------------------------------------------
+static int prof_event(linview_program* p) {
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return -1;
+  p->ev_pool.push_back(e);
+  return (int)p->ev_pool.size() - 1;
+}
+
+struct ProfScope {
+  linview_program* p;
+  cudaStream_t s;
+  int e0 = -1;
+  int kind = 0;
+  double bytes = 0.0;
+  // kind 1 = fused pass, 2 = update pass (timed when profiling); kind 0 =
+  // other kernels (only counted)
+  ProfScope(linview_program* p_, cudaStream_t s_, double bytes_, int kind_ = 0)
+      : p(p_), s(s_), kind(kind_), bytes(bytes_) {
+    p->all_launches++;
+    if (!p->prof || kind == 0) return;
+    e0 = prof_event(p);
+    if (e0 >= 0) cudaEventRecord(p->ev_pool[e0], s);
+  }
+  ~ProfScope() {
+    if (!p->prof || e0 < 0) return;
+    int e1 = prof_event(p);
+    if (e1 < 0) return;
+    cudaEventRecord(p->ev_pool[e1], s);
+    p->ev_recs.push_back({e0, e1, kind, bytes});
+  }
+};
+
+// ---------------------------------------------------------------------------
+// view passes
+// ---------------------------------------------------------------------------
+template <typename T>
+static constexpr int max_update_r() {
+  return sizeof(T) == 4 ? 64 : 32;
+}
+
+// X = P Xf, Y = P^T Yf (either may be skipped by mode), optional P += Uu Wu^T,
+// for a factor block of width r <= kMaxFusedR; partials land at column offset 0
+// of the given partial arrays.
+template <typename T>
+static linview_status run_fused(linview_program* p, const View& v, int mode, int r, const T* Xf,
+                                const T* Yf, const T* Uu, const T* Wu, void* Xpart, void* Ypart,
+                                cudaStream_t s) {
+  const PassGeom g = fused_geom(sizeof(T), (int)v.rows, p->sms);
+  PassParams pp{};
+  pp.P = v.ptr;
+  pp.ldp = v.ld;
+  pp.n = (int)v.rows;
+  pp.Xf = Xf;
+  pp.Yf = Yf;
+  pp.Uu = Uu;
+  pp.Wu = Wu;
+  pp.fs = p->fs;
+  pp.r = r;
+  pp.Xpart = Xpart;
+  pp.Ypart = Ypart;
+  pp.part_cs = p->part_cs;
+  pp.xp_s = p->xp_s;
+  pp.yp_q = p->yp_q;
+  pp.gC = g.gC;
+  pp.gR = g.gR;
+  pp.rows_per_cta = g.rows_per_cta;
+  pp.status = p->status;
+  const double nn = (double)v.rows * (double)v.rows * sizeof(T);
+  ProfScope ps(p, s, (mode & 4) ? 2.0 * nn : nn, 1);
+  LV_CUDA((launch_fused<T>(pp, v.tmap, r, mode, s)));
+  return LINVIEW_OK;
+}
+
+template <typename T>
+static linview_status run_update(linview_program* p, const View& v, const T* Uu, const T* Wu,
+                                 int r, cudaStream_t s) {
+  constexpr int MU = max_update_r<T>();
+  for (int c0 = 0; c0 < r; c0 += MU) {
+    const int w = (r - c0 < MU) ? (r - c0) : MU;
+    const PassGeom g = update_geom(sizeof(T), w, (int)v.rows, p->sms);
+    PassParams pp{};
+    pp.P = v.ptr;
+    pp.ldp = v.ld;
+    pp.n = (int)v.rows;
+    pp.Uu = Uu + (int64_t)c0 * p->fs;
+    pp.Wu = Wu + (int64_t)c0 * p->fs;
+    pp.fs = p->fs;
+    pp.r = w;
+    pp.gC = g.gC;
+    pp.gR = g.gR;
+    pp.rows_per_cta = g.rows_per_cta;
+    pp.status = p->status;
+    ProfScope ps(p, s, 2.0 * (double)v.rows * (double)v.rows * sizeof(T), 2);
+    LV_CUDA((launch_update<T>(pp, v.tmap, w, s)));
+  }
+  return LINVIEW_OK;
+}
+
+// Products X = P Xf, Y = P^T Yf for any width r (chunks of kMaxFusedR) into
+// the program's partial buffers (column block c0 at column offset c0), then
+// (if Uu) the in-place update.  Fused in one pass when r <= kMaxFusedR.
+template <typename T>
+static linview_status run_products_update(linview_program* p, const View& v, int r, const T* Xf,
+                                          const T* Yf, const T* Uu, const T* Wu, cudaStream_t s) {
+  const bool want_y = (Yf != nullptr);
+  if (r <= kMaxFusedR) {
+    const int mode = kModeX | (want_y ? 2 : 0) | (Uu ? 4 : 0);  // XYU, XY, XU or X
+    return run_fused<T>(p, v, mode, r, Xf, Yf, Uu, Wu, p->Xpart, p->Ypart, s);
+  }
+  for (int c0 = 0; c0 < r; c0 += kMaxFusedR) {
+    const int w = (r - c0 < kMaxFusedR) ? (r - c0) : kMaxFusedR;
+    T* xp = static_cast<T*>(p->Xpart) + (int64_t)c0 * p->part_cs;
+    T* yp = static_cast<T*>(p->Ypart) + (int64_t)c0 * p->part_cs;
+    LV_TRY(run_fused<T>(p, v, want_y ? kModeXY : kModeX, w, Xf + (int64_t)c0 * p->fs,
+                        want_y ? Yf + (int64_t)c0 * p->fs : nullptr, nullptr, nullptr, xp, yp, s));
+  }
+  if (Uu) LV_TRY(run_update<T>(p, v, Uu, Wu, r, s));
+  return LINVIEW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// GEMM helper: row-major C = alpha op(A) op(B) + beta C  (M x N, inner K)
+// ---------------------------------------------------------------------------
+static linview_status gemm_cm(linview_program* p, bool ta, bool tb, int64_t M, int64_t N,
+                              int64_t K, double alpha, const void* A, int64_t lda, const void* B,
+                              int64_t ldb, double beta, void* C, int64_t ldc, cudaStream_t s,
+                              int mode) {
+  LV_BLAS(cublasSetStream(p->blas, s));
+  p->all_launches++;
+  const cublasOperation_t oa = ta ? CUBLAS_OP_T : CUBLAS_OP_N;
+  const cublasOperation_t ob = tb ? CUBLAS_OP_T : CUBLAS_OP_N;
+  if (p->elem == 8) {
+    LV_BLAS(cublasDgemm(p->blas, oa, ob, (int)M, (int)N, (int)K, &alpha,
+                        static_cast<const double*>(A), (int)lda, static_cast<const double*>(B),
+                        (int)ldb, &beta, static_cast<double*>(C), (int)ldc));
+    return LINVIEW_OK;
+  }
+  const float af = (float)alpha, bf = (float)beta;
+  cublasComputeType_t ct = CUBLAS_COMPUTE_32F_PEDANTIC;
+  if (mode == LINVIEW_REEVAL_TF32) ct = CUBLAS_COMPUTE_32F_FAST_TF32;
+  if (mode == LINVIEW_REEVAL_BF16X9) ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+  LV_BLAS(cublasGemmEx(p->blas, oa, ob, (int)M, (int)N, (int)K, &af, A, CUDA_R_32F, (int)lda, B,
+                       CUDA_R_32F, (int)ldb, &bf, C, CUDA_R_32F, (int)ldc, ct,
+                       CUBLAS_GEMM_DEFAULT));
+  return LINVIEW_OK;
+}
+
+// Row-major C = alpha op(A) op(B) + beta C (M x N, inner K): the column-major
+// view of a row-major buffer is its transpose, so swap the operands.
+static linview_status gemm_rm(linview_program* p, bool ta, bool tb, int64_t M, int64_t N,
+                              int64_t K, double alpha, const void* A, int64_t lda, const void* B,
+                              int64_t ldb, double beta, void* C, int64_t ldc, cudaStream_t s,
+                              int mode) {
+  return gemm_cm(p, tb, ta, N, M, K, alpha, B, ldb, A, lda, beta, C, ldc, s, mode);
+}
+
+// accurate arithmetic for the internal small GEMMs of the incremental path
+static int exact_mode(const linview_program* p) {
+  return p->elem == 8 ? LINVIEW_REEVAL_FP64 : LINVIEW_REEVAL_FP32;
+}
+
+static int reeval_mode(const linview_program* p) {
+  int m = p->d.reeval_mode;
+  if (m == LINVIEW_REEVAL_DEFAULT) m = (p->elem == 8) ? LINVIEW_REEVAL_FP64 : LINVIEW_REEVAL_FP32;
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// powers and sums of powers
+// ---------------------------------------------------------------------------
+static bool is_pow2(int k) { return k >= 1 && (k & (k - 1)) == 0; }
+static int ilog2(int k) {
+  int l = 0;
+  while ((1 << l) < k) ++l;
+  return l;
+}
+static bool has_sums(const linview_program* p) {
+  return p->d.kind == LINVIEW_POWER_SUM && p->L >= 1;
+}
+static View& pview(linview_program* p, int l) { return p->views[l]; }
+static View& sview(linview_program* p, int l) { return p->views[p->L + l]; }  // S'_{2^l}, l>=1
+
+static linview_status powers_reeval(linview_program* p, cudaStream_t s) {
+  const int64_t n = p->d.n;
+  const int mode = reeval_mode(p);
+  for (int l = 0; l < p->L; ++l) {
+    View& a = pview(p, l);
+    View& c = pview(p, l + 1);
+    LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, a.ptr, a.ld, a.ptr, a.ld, 0.0, c.ptr, c.ld, s,
+                   mode));
+  }
+  if (has_sums(p)) {
+    for (int l = 0; l < p->L; ++l) {
+      View& ph = pview(p, l);
+      View& sh = (l == 0) ? pview(p, 0) : sview(p, l);
+      View& s2 = sview(p, l + 1);
+      LV_CUDA(cudaMemcpy2DAsync(s2.ptr, s2.ld * p->elem, sh.ptr, sh.ld * p->elem, n * p->elem, n,
+                                cudaMemcpyDeviceToDevice, s));
+      LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, ph.ptr, ph.ld, sh.ptr, sh.ld, 1.0, s2.ptr,
+                     s2.ld, s, mode));
+    }
+  }
+  return LINVIEW_OK;
+}
+
+static linview_status powers_create(linview_program* p, const void* const* inputs,
+                                    const int64_t* lds, int on_dev, cudaStream_t s) {
+  const int64_t n = p->d.n;
+  const int k = p->d.k;
+  if (!is_pow2(k)) return fail(LINVIEW_EINVAL, "k=%d must be a power of two", k);
+  p->L = ilog2(k);
+  if ((int64_t)p->d.r_max * k > 128)
+    return fail(LINVIEW_EUNSUPPORTED, "r_max*k=%lld exceeds 128 (factor cores are at most 64x64)",
+                (long long)p->d.r_max * k);
+  if (lds[0] < n) return fail(LINVIEW_ESHAPE, "ld of A (%lld) < n", (long long)lds[0]);
+  for (int l = 0; l <= p->L; ++l) LV_TRY(add_square_view(p, n));
+  if (p->d.kind == LINVIEW_POWER_SUM)
+    for (int l = 1; l <= p->L; ++l) LV_TRY(add_square_view(p, n));
+  LV_TRY(copy_in(pview(p, 0).ptr, pview(p, 0).ld, inputs[0], lds[0], n, n, p->elem, on_dev, s));
+  p->Rcap = p->d.r_max * k;
+  p->fs = rup(n, 64);
+  const size_t fbytes = (size_t)p->fs * p->Rcap * p->elem;
+  LV_TRY(dalloc(p, fbytes, &p->Uar));
+  LV_TRY(dalloc(p, fbytes, &p->Var));
+  if (p->d.kind == LINVIEW_POWER_SUM) LV_TRY(dalloc(p, fbytes, &p->War));
+  const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
+  const int half = (p->Rcap / 2 > 0) ? p->Rcap / 2 : 1;
+  p->part_cs = p->fs;
+  p->xp_s = (int64_t)half * p->part_cs;
+  p->yp_q = (int64_t)half * p->part_cs;
+  LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart));
+  LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart));
+  return powers_reeval(p, s);
+}
+
+template <typename T>
+static linview_status powers_propagate(linview_program* p, int r, cudaStream_t s) {
+  const int n = (int)p->d.n;
+  const int64_t fs = p->fs;
+  T* U = static_cast<T*>(p->Uar);
+  T* V = static_cast<T*>(p->Var);
+  T* W = static_cast<T*>(p->War);
+  const bool sums = has_sums(p);
+  const PassGeom g = fused_geom(sizeof(T), n, p->sms);
+  for (int l = 0; l < p->L; ++l) {
+    const int rh = r << l;
+    T* Vh = V + (int64_t)(p->Rcap - rh) * fs;
+    {
+      ProfScope ps(p, s, 0.0);
+      (void)ps;
+      LV_CUDA((launch_gram<T>(Vh, U, fs, n, rh, p->Cpart, p->ticket, p->C, p->status, s)));
+    }
+    // Appendix A level pass: P_h U_h, P_h^T V_h from the old view; P_h += U_h V_h^T
+    LV_TRY(run_products_update<T>(p, pview(p, l), rh, U, Vh, U, Vh, s));
+    if (sums && l >= 1) LV_TRY(run_update<T>(p, sview(p, l), U, W, rh, s));
+    AssembleParams a{};
+    a.n = n;
+    a.r_h = rh;
+    a.r_in = r;
+    a.fs = fs;
+    a.Xpart = p->Xpart;
+    a.gC = g.gC;
+    a.xp_s = p->xp_s;
+    a.Ypart = p->Ypart;
+    a.gR = g.gR;
+    a.yp_q = p->yp_q;
+    a.part_cs = p->part_cs;
+    a.C = p->C;
+    a.Uh = U;
+    a.Unew = U + (int64_t)rh * fs;
+    a.Ynew = V + (int64_t)(p->Rcap - 2 * rh) * fs;
+    a.V2h = a.Ynew;
+    a.W2h = sums ? (void*)W : nullptr;
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_assemble<T>(a, s));
+  }
+  const int rk = r << p->L;
+  LV_TRY(run_update<T>(p, pview(p, p->L), U, V + (int64_t)(p->Rcap - rk) * fs, rk, s));
+  if (sums) LV_TRY(run_update<T>(p, sview(p, p->L), U, W, rk, s));
+  return LINVIEW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// general form T_{i+1} = A T_i + B (Appendix B, linear model)
+// ---------------------------------------------------------------------------
+
+static linview_status iter_reeval(linview_program* p, cudaStream_t s) {
+  const int64_t n = p->d.n, pp = p->d.p;
+  const int k = p->d.k;
+  const int mode = reeval_mode(p);
+  View& a = p->views[0];
+  char* T = static_cast<char*>(p->Tpanel);
+  for (int i = 1; i <= k; ++i) {
+    void* ti = T + (size_t)i * pp * p->elem;
+    void* tp = T + (size_t)(i - 1) * pp * p->elem;
+    LV_CUDA(cudaMemcpy2DAsync(ti, p->ldT * p->elem, p->Bm, p->ldB * p->elem, pp * p->elem, n,
+                              cudaMemcpyDeviceToDevice, s));
+    LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, a.ptr, a.ld, tp, p->ldT, 1.0, ti, p->ldT, s,
+                   mode));
+  }
+  return LINVIEW_OK;
+}
+
+static linview_status iter_create(linview_program* p, const void* const* inputs,
+                                  const int64_t* lds, int on_dev, cudaStream_t s) {
+  const int64_t n = p->d.n, pp = p->d.p;
+  const int k = p->d.k;
+  if (pp < 1) return fail(LINVIEW_EINVAL, "p must be >= 1");
+  if (k < 1) return fail(LINVIEW_EINVAL, "k must be >= 1");
+  if (p->d.r_max > kMaxFusedR)
+    return fail(LINVIEW_EUNSUPPORTED, "iteration programs accept rank <= %d", kMaxFusedR);
+  if (lds[0] < n || lds[1] < pp || lds[2] < pp) return fail(LINVIEW_ESHAPE, "bad leading dims");
+  LV_TRY(add_square_view(p, n));
+  p->ldT = rup((int64_t)(k + 1) * pp, 64);
+  LV_TRY(dalloc(p, (size_t)n * p->ldT * p->elem, &p->Tpanel));
+  p->ldB = rup(pp, 64);
+  LV_TRY(dalloc(p, (size_t)n * p->ldB * p->elem, &p->Bm));
+  for (int i = 1; i <= k; ++i)
+    LV_TRY(add_rect_view(p, static_cast<char*>(p->Tpanel) + (size_t)i * pp * p->elem, n, pp,
+                         p->ldT));
+  LV_TRY(add_rect_view(p, p->Bm, n, pp, p->ldB));
+  LV_TRY(add_rect_view(p, p->Tpanel, n, pp, p->ldT));
+  LV_TRY(copy_in(p->views[0].ptr, p->views[0].ld, inputs[0], lds[0], n, n, p->elem, on_dev, s));
+  LV_TRY(copy_in(p->Bm, p->ldB, inputs[1], lds[1], n, pp, p->elem, on_dev, s));
+  LV_TRY(copy_in(p->Tpanel, p->ldT, inputs[2], lds[2], n, pp, p->elem, on_dev, s));
+  p->fs = rup(n, 64);
+  p->Rcap = p->d.r_max * k;
+  LV_TRY(dalloc(p, (size_t)p->fs * p->Rcap * p->elem, &p->Kar));
+  LV_TRY(dalloc(p, (size_t)p->fs * p->d.r_max * p->elem, &p->V1));
+  LV_TRY(dalloc(p, (size_t)pp * p->Rcap * p->elem, &p->Mr));
+  const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
+  p->part_cs = p->fs;
+  p->xp_s = (int64_t)kMaxFusedR * p->part_cs;
+  p->yp_q = p->xp_s;
+  LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart));
+  LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart));
+  return iter_reeval(p, s);
+}
+
+// Appendix B: U_1 = U, V_1 = T_0^T V, U_i = [U, A U_{i-1} + U (V^T U_{i-1})],
+// V_i = [T_{i-1}^T V, V_{i-1}], dT_i = U_i V_i^T.  U_i's blocks are the
+// Krylov blocks K_a = A'^a U (A' = A + U V^T); each step adds only the
+// newest block, K_1 = A K_0 + K_0 (V^T K_0) from the old A in the pass that
+// also writes A', and K_a = A' K_{a-1} afterwards.
+template <typename T>
+static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) {
+  const int n = (int)p->d.n;
+  const int64_t pp = p->d.p;
+  const int k = p->d.k;
+  const int64_t fs = p->fs;
+  T* K = static_cast<T*>(p->Kar);
+  T* V1 = static_cast<T*>(p->V1);
+  T* M = static_cast<T*>(p->Mr);
+  char* Tp = static_cast<char*>(p->Tpanel);
+  View& a = p->views[0];
+  const PassGeom g = fused_geom(sizeof(T), n, p->sms);
+  // M_i = T_i^T V (old T_i), stored at block k-1-i so that [M_{i-1} .. M_0]
+  // is one contiguous p x (i r) slab.
+  // column-major view: T_i is p x n (ld ldT), V is n x r (ld fs)
+  for (int i = 0; i < k; ++i) {
+    const void* ti = Tp + (size_t)i * pp * sizeof(T);
+    LV_TRY(gemm_cm(p, false, false, pp, r, n, 1.0, ti, p->ldT, V1, fs, 0.0,
+                   M + (int64_t)(k - 1 - i) * r * pp, pp, s, exact_mode(p)));
+  }
+  if (k >= 2) {
+    {
+      ProfScope ps(p, s, 0.0);
+      LV_CUDA((launch_gram<T>(V1, K, fs, n, r, p->Cpart, p->ticket, p->C, p->status, s)));
+    }
+    // X = A K_0 on the old A, A += K_0 V^T in the same pass
+    LV_TRY(run_fused<T>(p, a, kModeXU, r, K, nullptr, K, V1, p->Xpart, p->Ypart, s));
+    AssembleParams as{};
+    as.n = n;
+    as.r_h = r;
+    as.r_in = r;
+    as.fs = fs;
+    as.Xpart = p->Xpart;
+    as.gC = g.gC;
+    as.xp_s = p->xp_s;
+    as.part_cs = p->part_cs;
+    as.C = p->C;
+    as.Uh = K;
+    as.Unew = K + (int64_t)r * fs;
+    {
+      ProfScope ps(p, s, 0.0);
+      LV_CUDA(launch_assemble<T>(as, s));
+    }
+    for (int j = 2; j < k; ++j) {
+      LV_TRY(run_fused<T>(p, a, kModeX, r, K + (int64_t)(j - 1) * r * fs, nullptr, nullptr,
+                          nullptr, p->Xpart, p->Ypart, s));
+      ProfScope ps(p, s, 0.0);
+      LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, r,
+                                     K + (int64_t)j * r * fs, fs, s));
+    }
+  } else {
+    LV_TRY(run_update<T>(p, a, K, V1, r, s));
+  }
+  // T_i += [K_0 .. K_{i-1}] [M_{i-1} .. M_0]^T; column-major: T_i^T (p x n)
+  // += Mc (p x ir) Kc^T, Kc column-major n x ir (ld fs)
+  for (int i = 1; i <= k; ++i) {
+    void* ti = Tp + (size_t)i * pp * sizeof(T);
+    const T* mc = M + (int64_t)(k - i) * r * pp;
+    LV_TRY(gemm_cm(p, false, true, pp, n, (int64_t)i * r, 1.0, mc, pp, K, fs, 1.0, ti, p->ldT, s,
+                   exact_mode(p)));
+  }
+  return LINVIEW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* linview_last_error(void) { return g_err.c_str(); }
+
+linview_status linview_create_program(const linview_program_desc* desc, const void* const* inputs,
+                                      const int64_t* lds, int inputs_on_device, void* stream,
+                                      linview_program** out) {
+  if (!desc || !inputs || !lds || !out) return fail(LINVIEW_EINVAL, "null argument");
+  *out = nullptr;
+  if (desc->precision != LINVIEW_F32 && desc->precision != LINVIEW_F64)
+    return fail(LINVIEW_EINVAL, "bad precision %d", desc->precision);
+  if (desc->n < 1 || desc->n > (1 << 20)) return fail(LINVIEW_EINVAL, "bad n=%lld", (long long)desc->n);
+  if (desc->r_max < 1) return fail(LINVIEW_EINVAL, "r_max must be >= 1");
+  if (desc->correction_period < 0) return fail(LINVIEW_EINVAL, "correction_period < 0");
+  int ninputs = 0;
+  switch (desc->kind) {
+    case LINVIEW_POWER:
+    case LINVIEW_POWER_SUM: ninputs = 1; break;
+    case LINVIEW_ITERATION: ninputs = 3; break;
+    case LINVIEW_OLS: ninputs = 2; break;
+    default: return fail(LINVIEW_EINVAL, "bad kind %d", desc->kind);
+  }
+  for (int i = 0; i < ninputs; ++i)
+    if (!inputs[i]) return fail(LINVIEW_EINVAL, "input %d is null", i);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    (void)cudaGetLastError();
+    return fail(LINVIEW_EDEVICE, "no CUDA device");
+  }
+  linview_program* p = new linview_program();
+  p->d = *desc;
+  p->elem = desc->precision == LINVIEW_F64 ? 8 : 4;
+  cudaGetDevice(&p->device);
+  cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  linview_status st = LINVIEW_OK;
+  if (cublasCreate(&p->blas) != CUBLAS_STATUS_SUCCESS) {
+    st = fail(LINVIEW_EDEVICE, "cublasCreate failed");
+  }
+  if (st == LINVIEW_OK) {
+    void* tmp = nullptr;
+    st = dalloc(p, sizeof(unsigned) * 4, &tmp);
+    p->status = static_cast<unsigned*>(tmp);
+    p->ticket = p->status + 1;
+  }
+  if (st == LINVIEW_OK) {
+    void* tmp = nullptr;
+    st = dalloc(p, sizeof(double) * 64 * 64, &tmp);
+    p->C = static_cast<double*>(tmp);
+  }
+  if (st == LINVIEW_OK) {
+    void* tmp = nullptr;
+    st = dalloc(p, sizeof(double) * 64 * 64 * gram_grid((int)desc->n), &tmp);
+    p->Cpart = static_cast<double*>(tmp);
+  }
+  if (st == LINVIEW_OK) {
+    switch (desc->kind) {
+      case LINVIEW_POWER:
+      case LINVIEW_POWER_SUM: st = powers_create(p, inputs, lds, inputs_on_device, s); break;
+      case LINVIEW_ITERATION: st = iter_create(p, inputs, lds, inputs_on_device, s); break;
+      default: st = fail(LINVIEW_EUNSUPPORTED, "program kind %d not built", desc->kind);
+    }
+  }
+  if (st != LINVIEW_OK) {
+    std::string keep = g_err;
+    cudaStreamSynchronize(s);
+    linview_destroy(p);
+    g_err = keep;
+    return st;
+  }
+  *out = p;
+  return LINVIEW_OK;
+}
+
+void linview_destroy(linview_program* p) {
+  if (!p) return;
+  cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  for (void* a : p->allocs) cudaFree(a);
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  if (p->blas) cublasDestroy(p->blas);
+  if (p->solver) cusolverDnDestroy(p->solver);
+  delete p;
+}
+
+int linview_num_views(const linview_program* p) { return p ? (int)p->views.size() : 0; }
+
+linview_status linview_view_shape(const linview_program* p, int id, int64_t* rows, int64_t* cols) {
+  if (!p || !rows || !cols) return fail(LINVIEW_EINVAL, "null argument");
+  if (id < 0 || id >= (int)p->views.size()) return fail(LINVIEW_EINVAL, "bad view id %d", id);
+  *rows = p->views[id].rows;
+  *cols = p->views[id].cols;
+  return LINVIEW_OK;
+}
+
+linview_status linview_view_device_ptr(const linview_program* p, int id, void** ptr, int64_t* ld) {
+  if (!p || !ptr || !ld) return fail(LINVIEW_EINVAL, "null argument");
+  if (id < 0 || id >= (int)p->views.size()) return fail(LINVIEW_EINVAL, "bad view id %d", id);
+  *ptr = p->views[id].ptr;
+  *ld = p->views[id].ld;
+  return LINVIEW_OK;
+}
+
+linview_status linview_read_view(const linview_program* p, int id, void* dst, int64_t ld,
+                                 int dst_on_device, void* stream) {
+  if (!p || !dst) return fail(LINVIEW_EINVAL, "null argument");
+  if (id < 0 || id >= (int)p->views.size()) return fail(LINVIEW_EINVAL, "bad view id %d", id);
+  const View& v = p->views[id];
+  if (ld < v.cols) return fail(LINVIEW_ESHAPE, "ld %lld < cols %lld", (long long)ld, (long long)v.cols);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LV_CUDA(cudaSetDevice(p->device));
+  LV_CUDA(cudaMemcpy2DAsync(dst, ld * p->elem, v.ptr, v.ld * p->elem, v.cols * p->elem, v.rows,
+                            dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!dst_on_device) LV_CUDA(cudaStreamSynchronize(s));
+  return LINVIEW_OK;
+}
+
+linview_status linview_read_view_rows(const linview_program* p, int id, int64_t row0,
+                                      int64_t nrows, void* dst, int64_t ld, int dst_on_device,
+                                      void* stream) {
+  if (!p || !dst) return fail(LINVIEW_EINVAL, "null argument");
+  if (id < 0 || id >= (int)p->views.size()) return fail(LINVIEW_EINVAL, "bad view id %d", id);
+  const View& v = p->views[id];
+  if (row0 < 0 || nrows < 0 || row0 + nrows > v.rows)
+    return fail(LINVIEW_EINVAL, "rows [%lld, %lld) outside the view", (long long)row0,
+                (long long)(row0 + nrows));
+  if (ld < v.cols) return fail(LINVIEW_ESHAPE, "ld < cols");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LV_CUDA(cudaSetDevice(p->device));
+  if (nrows > 0)
+    LV_CUDA(cudaMemcpy2DAsync(dst, ld * p->elem,
+                              static_cast<const char*>(v.ptr) + (size_t)row0 * v.ld * p->elem,
+                              v.ld * p->elem, v.cols * p->elem, nrows,
+                              dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!dst_on_device) LV_CUDA(cudaStreamSynchronize(s));
+  return LINVIEW_OK;
+}
+
+linview_status linview_reeval(linview_program* p, void* stream) {
+  if (!p) return fail(LINVIEW_EINVAL, "null program");
+  LV_CUDA(cudaSetDevice(p->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (p->d.kind) {
+    case LINVIEW_POWER:
+    case LINVIEW_POWER_SUM: return powers_reeval(p, s);
+    case LINVIEW_ITERATION: return iter_reeval(p, s);
+    default: return fail(LINVIEW_EUNSUPPORTED, "reeval for kind %d", p->d.kind);
+  }
+}
+
+linview_status linview_set_reeval_mode(linview_program* p, int mode) {
+  if (!p) return fail(LINVIEW_EINVAL, "null program");
+  if (mode < LINVIEW_REEVAL_DEFAULT || mode > LINVIEW_REEVAL_FP64)
+    return fail(LINVIEW_EINVAL, "bad reeval mode %d", mode);
+  if (p->elem == 8 && mode != LINVIEW_REEVAL_DEFAULT && mode != LINVIEW_REEVAL_FP64)
+    return fail(LINVIEW_EINVAL, "FP64 programs re-evaluate in FP64");
+  if (p->elem == 4 && mode == LINVIEW_REEVAL_FP64)
+    return fail(LINVIEW_EINVAL, "FP32 programs cannot re-evaluate in FP64 storage");
+  p->d.reeval_mode = mode;
+  return LINVIEW_OK;
+}
+
+static linview_status after_update(linview_program* p, cudaStream_t s) {
+  p->updates++;
+  if (p->d.correction_period > 0 && p->updates % p->d.correction_period == 0)
+    return linview_reeval(p, s);
+  return LINVIEW_OK;
+}
+
+static linview_status propagate(linview_program* p, int r, cudaStream_t s) {
+  switch (p->d.kind) {
+    case LINVIEW_POWER:
+    case LINVIEW_POWER_SUM:
+      return p->elem == 4 ? powers_propagate<float>(p, r, s) : powers_propagate<double>(p, r, s);
+    case LINVIEW_ITERATION:
+      return p->elem == 4 ? iter_propagate<float>(p, r, s) : iter_propagate<double>(p, r, s);
+    default: return fail(LINVIEW_EUNSUPPORTED, "updates for kind %d", p->d.kind);
+  }
+}
+
+// column-major destinations of the input factors
+static void* u_dst(linview_program* p) {
+  return p->d.kind == LINVIEW_ITERATION ? p->Kar : p->Uar;
+}
+static void* v_dst(linview_program* p, int r) {
+  if (p->d.kind == LINVIEW_ITERATION) return p->V1;
+  return static_cast<char*>(p->Var) + (size_t)(p->Rcap - r) * p->fs * p->elem;
+}
+
+linview_status linview_apply_delta(linview_program* p, int input_id, int64_t rank, const void* U,
+                                   int64_t ldu, const void* V, int64_t ldv, int on_device,
+                                   void* stream) {
+  if (!p || !U || !V) return fail(LINVIEW_EINVAL, "null argument");
+  if (p->d.kind == LINVIEW_OLS) return fail(LINVIEW_EINVAL, "OLS takes linview_apply_row_block");
+  if (input_id != 0) return fail(LINVIEW_EUNSUPPORTED, "only input 0 (A) has a trigger");
+  if (rank < 1) return fail(LINVIEW_EINVAL, "rank must be >= 1");
+  if (rank > p->d.r_max) return fail(LINVIEW_ERANK, "rank %lld > r_max %d", (long long)rank, p->d.r_max);
+  if (ldu < rank || ldv < rank) return fail(LINVIEW_ESHAPE, "ldu/ldv < rank");
+  LV_CUDA(cudaSetDevice(p->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t n = p->d.n;
+  const int r = (int)rank;
+  const void* u = U;
+  const void* v = V;
+  if (!on_device) {
+    LV_TRY(ensure_stage(p, (size_t)2 * n * r * p->elem));
+    char* st = static_cast<char*>(p->stage);
+    LV_TRY(copy_in(st, r, U, ldu, n, r, p->elem, 0, s));
+    LV_TRY(copy_in(st + (size_t)n * r * p->elem, r, V, ldv, n, r, p->elem, 0, s));
+    u = st;
+    v = st + (size_t)n * r * p->elem;
+    ldu = r;
+    ldv = r;
+  }
+  if (p->elem == 4) {
+    LV_CUDA(launch_rm_to_cm<float>(static_cast<const float*>(u), ldu, static_cast<float*>(u_dst(p)),
+                                   p->fs, (int)n, r, s));
+    LV_CUDA(launch_rm_to_cm<float>(static_cast<const float*>(v), ldv,
+                                   static_cast<float*>(v_dst(p, r)), p->fs, (int)n, r, s));
+    if (has_sums(p))
+      LV_CUDA(launch_suffix_sums<float>(static_cast<float*>(v_dst(p, r)),
+                                        static_cast<float*>(p->War), p->fs, (int)n, r, r, s));
+  } else {
+    LV_CUDA(launch_rm_to_cm<double>(static_cast<const double*>(u), ldu,
+                                    static_cast<double*>(u_dst(p)), p->fs, (int)n, r, s));
+    LV_CUDA(launch_rm_to_cm<double>(static_cast<const double*>(v), ldv,
+                                    static_cast<double*>(v_dst(p, r)), p->fs, (int)n, r, s));
+    if (has_sums(p))
+      LV_CUDA(launch_suffix_sums<double>(static_cast<double*>(v_dst(p, r)),
+                                         static_cast<double*>(p->War), p->fs, (int)n, r, r, s));
+  }
+  p->all_launches += has_sums(p) ? 3 : 2;
+  LV_TRY(propagate(p, r, s));
+  return after_update(p, s);
+}
+
+linview_status linview_apply_row_delta(linview_program* p, int input_id, int64_t row,
+                                       const void* v, int on_device, void* stream) {
+  if (!p || !v) return fail(LINVIEW_EINVAL, "null argument");
+  if (p->d.kind == LINVIEW_OLS) return fail(LINVIEW_EINVAL, "OLS takes linview_apply_row_block");
+  if (input_id != 0) return fail(LINVIEW_EUNSUPPORTED, "only input 0 (A) has a trigger");
+  const int64_t n = p->d.n;
+  if (row < 0 || row >= n) return fail(LINVIEW_EINVAL, "row %lld out of range", (long long)row);
+  LV_CUDA(cudaSetDevice(p->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LV_CUDA(cudaMemcpyAsync(v_dst(p, 1), v, n * p->elem,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if (p->elem == 4) {
+    LV_CUDA(launch_unit_column<float>(static_cast<float*>(u_dst(p)), (int)n, (int)row, s));
+    if (has_sums(p))
+      LV_CUDA(launch_suffix_sums<float>(static_cast<float*>(v_dst(p, 1)),
+                                        static_cast<float*>(p->War), p->fs, (int)n, 1, 1, s));
+  } else {
+    LV_CUDA(launch_unit_column<double>(static_cast<double*>(u_dst(p)), (int)n, (int)row, s));
+    if (has_sums(p))
+      LV_CUDA(launch_suffix_sums<double>(static_cast<double*>(v_dst(p, 1)),
+                                         static_cast<double*>(p->War), p->fs, (int)n, 1, 1, s));
+  }
+  p->all_launches += has_sums(p) ? 2 : 1;
+  LV_TRY(propagate(p, 1, s));
+  return after_update(p, s);
+}
+
+linview_status linview_apply_row_block(linview_program* p, int64_t kr, const int64_t* rows,
+                                       const void* new_rows, int64_t ld, int on_device,
+                                       void* stream) {
+  (void)kr; (void)rows; (void)new_rows; (void)ld; (void)on_device; (void)stream;
+  if (!p) return fail(LINVIEW_EINVAL, "null program");
+  return fail(LINVIEW_EUNSUPPORTED, "OLS is not built in this library version");
+}
+
+linview_status linview_sync(linview_program* p, void* stream) {
+  if (!p) return fail(LINVIEW_EINVAL, "null program");
+  LV_CUDA(cudaSetDevice(p->device));
+  LV_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  unsigned st = 0;
+  LV_CUDA(cudaMemcpy(&st, p->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (st) LV_CUDA(cudaMemset(p->status, 0, sizeof(unsigned)));
+  if (st & kStatusTimeout) return fail(LINVIEW_ETIMEOUT, "a bounded device wait expired");
+  if (st & kStatusSingular) return fail(LINVIEW_ESINGULAR, "Woodbury core is singular");
+  if (st & kStatusNonFinite) return fail(LINVIEW_ENONFINITE, "non-finite factor core");
+  return LINVIEW_OK;
+}
+
+// ---------------------------------------------------------------- adjoints
+linview_status linview_adjoint_iteration(linview_program* p, void* dA, int64_t ld_dA, void* dB,
+                                         int64_t ld_dB, void* stream) {
+  if (!p) return fail(LINVIEW_EINVAL, "null program");
+  if (p->d.kind != LINVIEW_ITERATION) return fail(LINVIEW_EINVAL, "not an iteration program");
+  const int64_t n = p->d.n, pp = p->d.p;
+  const int k = p->d.k;
+  if ((dA && ld_dA < n) || (dB && ld_dB < pp)) return fail(LINVIEW_ESHAPE, "bad leading dims");
+  LV_CUDA(cudaSetDevice(p->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->Gpanel) {
+    p->ldG = rup((int64_t)k * pp, 64);
+    LV_TRY(dalloc(p, (size_t)n * p->ldG * p->elem, &p->Gpanel));
+  }
+  const int mode = exact_mode(p);
+  const int e = p->elem;
+  char* G = static_cast<char*>(p->Gpanel);
+  char* T = static_cast<char*>(p->Tpanel);
+  View& a = p->views[0];
+  // G_k = 2 T_k; G_i = A^T G_{i+1}
+  void* gk = G + (size_t)(k - 1) * pp * e;
+  void* tk = T + (size_t)k * pp * e;
+  if (e == 4)
+    LV_CUDA(launch_scale_copy<float>(static_cast<float*>(gk), p->ldG, static_cast<float*>(tk),
+                                     p->ldT, 2.0f, (int)n, (int)pp, s));
+  else
+    LV_CUDA(launch_scale_copy<double>(static_cast<double*>(gk), p->ldG, static_cast<double*>(tk),
+                                      p->ldT, 2.0, (int)n, (int)pp, s));
+  p->all_launches++;
+  for (int i = k - 1; i >= 1; --i) {
+    void* gi = G + (size_t)(i - 1) * pp * e;
+    void* gn = G + (size_t)i * pp * e;
+    LV_TRY(gemm_rm(p, true, false, n, pp, n, 1.0, a.ptr, a.ld, gn, p->ldG, 0.0, gi, p->ldG, s,
+                   mode));
+  }
+  if (dB) {
+    LV_CUDA(cudaMemcpy2DAsync(dB, ld_dB * e, G, p->ldG * e, pp * e, n, cudaMemcpyDeviceToDevice, s));
+    for (int i = 2; i <= k; ++i) {
+      void* gi = G + (size_t)(i - 1) * pp * e;
+      if (e == 4)
+        LV_CUDA(launch_axpy_rows<float>(static_cast<float*>(dB), ld_dB, static_cast<float*>(gi),
+                                        p->ldG, 1.0f, (int)n, (int)pp, s));
+      else
+        LV_CUDA(launch_axpy_rows<double>(static_cast<double*>(dB), ld_dB,
+                                         static_cast<double*>(gi), p->ldG, 1.0, (int)n, (int)pp, s));
+      p->all_launches++;
+    }
+  }
+  if (dA) {
+    // dA = [G_1 .. G_k] [T_0 .. T_{k-1}]^T, one GEMM with inner dimension k p
+    LV_TRY(gemm_rm(p, false, true, n, n, (int64_t)k * pp, 1.0, G, p->ldG, T, p->ldT, 0.0, dA,
+                   ld_dA, s, mode));
+  }
+  return LINVIEW_OK;
+}
+
+linview_status linview_adjoint_power(linview_program* p, const void* G, int64_t ldg, void* dA,
+                                     int64_t ld_dA, void* stream) {
+  if (!p || !G || !dA) return fail(LINVIEW_EINVAL, "null argument");
+  if (p->d.kind != LINVIEW_POWER && p->d.kind != LINVIEW_POWER_SUM)
+    return fail(LINVIEW_EINVAL, "not a power program");
+  const int64_t n = p->d.n;
+  if (ldg < n || ld_dA < n) return fail(LINVIEW_ESHAPE, "bad leading dims");
+  LV_CUDA(cudaSetDevice(p->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int e = p->elem;
+  const int64_t ldw = rup(n, 64);
+  if (!p->Gw0) {
+    LV_TRY(dalloc(p, (size_t)n * ldw * e, &p->Gw0));
+    LV_TRY(dalloc(p, (size_t)n * ldw * e, &p->Gw1));
+  }
+  const int mode = exact_mode(p);
+  LV_CUDA(cudaMemcpy2DAsync(p->Gw0, ldw * e, G, ldg * e, n * e, n, cudaMemcpyDeviceToDevice, s));
+  void* cur = p->Gw0;
+  void* nxt = p->Gw1;
+  // Gbar_h = Gbar_{2h} P_h^T + P_h^T Gbar_{2h}, h = k/2, ..., 1
+  for (int l = p->L - 1; l >= 0; --l) {
+    View& ph = pview(p, l);
+    LV_TRY(gemm_rm(p, false, true, n, n, n, 1.0, cur, ldw, ph.ptr, ph.ld, 0.0, nxt, ldw, s, mode));
+    LV_TRY(gemm_rm(p, true, false, n, n, n, 1.0, ph.ptr, ph.ld, cur, ldw, 1.0, nxt, ldw, s, mode));
+    void* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  LV_CUDA(cudaMemcpy2DAsync(dA, ld_dA * e, cur, ldw * e, n * e, n, cudaMemcpyDeviceToDevice, s));
+  return LINVIEW_OK;
+}
+
+// ------------------------------------------------------ stand-alone level pass
+linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp, const void* U,
+                                  const void* V, int64_t ldf, int64_t r, void* X, void* Y,
+                                  int do_update, void* stream) {
+  if (precision != LINVIEW_F32 && precision != LINVIEW_F64)
+    return fail(LINVIEW_EINVAL, "bad precision");
+  if (!P || !U || !V) return fail(LINVIEW_EINVAL, "null argument");
+  if (n < 1 || r < 1 || r > 64) return fail(LINVIEW_EINVAL, "need n >= 1 and 1 <= r <= 64");
+  const int e = precision == LINVIEW_F64 ? 8 : 4;
+  if (precision == LINVIEW_F64 && r > 32)
+    return fail(LINVIEW_EUNSUPPORTED, "FP64 level pass takes r <= 32");
+  if (ldp < n || ldf < n) return fail(LINVIEW_ESHAPE, "ldp/ldf < n");
+  if ((ldp * e) % 16 != 0 || (reinterpret_cast<uintptr_t>(P) % 16) != 0)
+    return fail(LINVIEW_ESHAPE, "P must be 16-byte aligned with ldp*elem a multiple of 16");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  linview_program tmp;  // borrowed machinery, no views owned
+  tmp.elem = e;
+  cudaGetDevice(&tmp.device);
+  cudaDeviceGetAttribute(&tmp.sms, cudaDevAttrMultiProcessorCount, tmp.device);
+  View v;
+  v.ptr = P;
+  v.rows = n;
+  v.cols = n;
+  v.ld = ldp;
+  v.square = true;
+  if (!make_tmap(&v.tmap, P, e, n, n, ldp)) return fail(LINVIEW_EDEVICE, "tensor map encode failed");
+  const PassGeom g = fused_geom(e, (int)n, tmp.sms);
+  tmp.fs = ldf;
+  tmp.part_cs = rup(n, 64);
+  tmp.xp_s = r * tmp.part_cs;
+  tmp.yp_q = r * tmp.part_cs;
+  const bool products = (X != nullptr) || (Y != nullptr);
+  void* xp = nullptr;
+  void* yp = nullptr;
+  void* stw = nullptr;
+  if (products) {
+    LV_CUDA(cudaMallocAsync(&xp, (size_t)g.gC * tmp.xp_s * e, s));
+    LV_CUDA(cudaMallocAsync(&yp, (size_t)g.gR * tmp.yp_q * e, s));
+  }
+  LV_CUDA(cudaMallocAsync(&stw, sizeof(unsigned) * 4, s));
+  LV_CUDA(cudaMemsetAsync(stw, 0, sizeof(unsigned) * 4, s));
+  tmp.status = static_cast<unsigned*>(stw);
+  tmp.Xpart = xp;
+  tmp.Ypart = yp;
+  linview_status st = LINVIEW_OK;
+  if (e == 4) {
+    const float* u = static_cast<const float*>(U);
+    const float* vv = static_cast<const float*>(V);
+    if (products)
+      st = run_products_update<float>(&tmp, v, (int)r, u, vv, do_update ? u : nullptr,
+                                      do_update ? vv : nullptr, s);
+    else if (do_update)
+      st = run_update<float>(&tmp, v, u, vv, (int)r, s);
+    if (st == LINVIEW_OK && X)
+      st = launch_sum_partials<float>(static_cast<float*>(xp), g.gC, tmp.xp_s, tmp.part_cs,
+                                      (int)n, (int)r, static_cast<float*>(X), ldf, s) == cudaSuccess
+               ? LINVIEW_OK : fail(LINVIEW_EDEVICE, "sum_partials launch failed");
+    if (st == LINVIEW_OK && Y)
+      st = launch_sum_partials<float>(static_cast<float*>(yp), g.gR, tmp.yp_q, tmp.part_cs,
+                                      (int)n, (int)r, static_cast<float*>(Y), ldf, s) == cudaSuccess
+               ? LINVIEW_OK : fail(LINVIEW_EDEVICE, "sum_partials launch failed");
+  } else {
+    const double* u = static_cast<const double*>(U);
+    const double* vv = static_cast<const double*>(V);
+    if (products)
+      st = run_products_update<double>(&tmp, v, (int)r, u, vv, do_update ? u : nullptr,
+                                       do_update ? vv : nullptr, s);
+    else if (do_update)
+      st = run_update<double>(&tmp, v, u, vv, (int)r, s);
+    if (st == LINVIEW_OK && X)
+      st = launch_sum_partials<double>(static_cast<double*>(xp), g.gC, tmp.xp_s, tmp.part_cs,
+                                       (int)n, (int)r, static_cast<double*>(X), ldf, s) == cudaSuccess
+               ? LINVIEW_OK : fail(LINVIEW_EDEVICE, "sum_partials launch failed");
+    if (st == LINVIEW_OK && Y)
+      st = launch_sum_partials<double>(static_cast<double*>(yp), g.gR, tmp.yp_q, tmp.part_cs,
+                                       (int)n, (int)r, static_cast<double*>(Y), ldf, s) == cudaSuccess
+               ? LINVIEW_OK : fail(LINVIEW_EDEVICE, "sum_partials launch failed");
+  }
+  unsigned hs = 0;
+  cudaMemcpyAsync(&hs, stw, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (xp) cudaFreeAsync(xp, s);
+  if (yp) cudaFreeAsync(yp, s);
+  cudaFreeAsync(stw, s);
+  LV_CUDA(cudaStreamSynchronize(s));
+  if (st == LINVIEW_OK && (hs & kStatusTimeout)) st = fail(LINVIEW_ETIMEOUT, "bounded wait expired");
+  return st;
+}
+
+// ------------------------------------------------------------- profiling
+linview_status linview_set_profiling(linview_program* p, int enable) {
+  if (!p) return fail(LINVIEW_EINVAL, "null program");
+  p->prof = enable != 0;
+  return LINVIEW_OK;
+}
+
+linview_status linview_reset_stats(linview_program* p) {
+  if (!p) return fail(LINVIEW_EINVAL, "null program");
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  p->ev_pool.clear();
+  p->ev_recs.clear();
+  p->all_launches = 0;
+  return LINVIEW_OK;
+}
+
+linview_status linview_pass_stats(linview_program* p, int kernel, int64_t* launches, double* ms,
+                                  double* bytes, int64_t* all_launches) {
+  if (!p) return fail(LINVIEW_EINVAL, "null program");
+  if (kernel < 0 || kernel > 2) return fail(LINVIEW_EINVAL, "bad kernel selector %d", kernel);
+  double tot = 0.0, by = 0.0;
+  int64_t cnt = 0;
+  for (auto& rc : p->ev_recs) {
+    if (kernel != 0 && rc.kind != kernel) continue;
+    float t = 0.f;
+    LV_CUDA(cudaEventSynchronize(p->ev_pool[rc.e1]));
+    LV_CUDA(cudaEventElapsedTime(&t, p->ev_pool[rc.e0], p->ev_pool[rc.e1]));
+    tot += t;
+    by += rc.bytes;
+    ++cnt;
+  }
+  if (launches) *launches = cnt;
+  if (ms) *ms = tot;
+  if (bytes) *bytes = by;
+  if (all_launches) *all_launches = p->all_launches;
+  return LINVIEW_OK;
+}
+
+}  // extern "C"

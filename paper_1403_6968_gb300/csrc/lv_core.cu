@@ -1,0 +1,304 @@
+// Factor cores and factor assembly of the exponential model (Appendix A of
+// arXiv 1403.6968) and small helpers (ingest, layout changes).
+//
+//   C_h     = V_h^T U_h                       (r_h x r_h, FP64)
+//   U_{2h}  = [U_h, P_h U_h + U_h C_h]         (right block written here)
+//   V_{2h}  = [P_h^T V_h, V_h]                 (left block written here)
+//
+// P_h U_h and P_h^T V_h arrive as per-block partial sums from the view pass;
+// they are summed here in a fixed order so every run gives identical bits.
+#include <cuda_runtime.h>
+
+#include "lv_device.cuh"
+#include "lv_internal.h"
+
+namespace lv {
+
+constexpr int kGramRows = 32;   // rows staged per tile
+constexpr int kGramMaxR = 64;
+constexpr int kGramPerThread = kGramMaxR * kGramMaxR / kThreads;  // 16
+
+int gram_grid(int n) {
+  int g = (n + 127) / 128;
+  if (g > 64) g = 64;
+  if (g < 1) g = 1;
+  return g;
+}
+
+// C = V^T U (r x r, row-major, FP64).  Block b sums rows of its chunk; the
+// last block to finish (ticket) adds the block partials in index order.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ V,
+                                                        const T* __restrict__ U, int64_t fs, int n,
+                                                        int r, double* Cpart, unsigned* ticket,
+                                                        double* C, unsigned* status) {
+  __shared__ T Vs[kGramRows][kGramMaxR + 1];
+  __shared__ T Us[kGramRows][kGramMaxR + 1];
+  __shared__ bool last;
+  const int tid = threadIdx.x;
+  const int G = gridDim.x;
+  const int chunk = (n + G - 1) / G;
+  const int r0 = blockIdx.x * chunk;
+  const int r1 = min(n, r0 + chunk);
+  const int ne = r * r;
+  double acc[kGramPerThread];
+#pragma unroll
+  for (int i = 0; i < kGramPerThread; ++i) acc[i] = 0.0;
+  for (int t0 = r0; t0 < r1; t0 += kGramRows) {
+    const int nr = min(kGramRows, r1 - t0);
+    for (int idx = tid; idx < kGramRows * r; idx += kThreads) {
+      const int c = idx / kGramRows;
+      const int j = idx % kGramRows;
+      const bool ok = j < nr;
+      Vs[j][c] = ok ? V[(int64_t)c * fs + t0 + j] : T(0);
+      Us[j][c] = ok ? U[(int64_t)c * fs + t0 + j] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kGramPerThread; ++i) {
+      const int e = tid + i * kThreads;
+      if (e < ne) {
+        const int c1 = e / r, c2 = e % r;
+        double a = acc[i];
+        for (int j = 0; j < nr; ++j) a = fma((double)Vs[j][c1], (double)Us[j][c2], a);
+        acc[i] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < kGramPerThread; ++i) {
+    const int e = tid + i * kThreads;
+    if (e < ne) Cpart[(int64_t)blockIdx.x * ne + e] = acc[i];
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(ticket, 1u) == (unsigned)(G - 1));
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    for (int e = tid; e < ne; e += kThreads) {
+      double sum = 0.0;
+      for (int b = 0; b < G; ++b) sum += Cpart[(int64_t)b * ne + e];
+      if (!isfinite(sum)) atomicOr(status, kStatusNonFinite);
+      C[e] = sum;
+    }
+    if (tid == 0) *ticket = 0u;
+  }
+}
+
+template <typename T>
+cudaError_t launch_gram(const T* V, const T* U, int64_t fs, int n, int r, double* Cpart,
+                        unsigned* ticket, double* C, unsigned* status, cudaStream_t s) {
+  if (r < 1 || r > kGramMaxR) return cudaErrorInvalidValue;
+  gram_kernel<T><<<gram_grid(n), kThreads, 0, s>>>(V, U, fs, n, r, Cpart, ticket, C, status);
+  return cudaGetLastError();
+}
+
+// One thread per row j:  X'(j,:) = sum_s Xpart[s](j,:) + U_h(j,:) C_h,
+// Y(j,:) = sum_q Ypart[q](j,:), then (optionally) the suffix block sums of
+// V_{2h}(j,:) for the sums views.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) assemble_kernel(const AssembleParams a) {
+  extern __shared__ double Cs[];  // r_h x r_h
+  const int rh = a.r_h;
+  for (int e = threadIdx.x; e < rh * rh; e += blockDim.x) Cs[e] = a.C[e];
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.n) return;
+  const T* Xp = static_cast<const T*>(a.Xpart);
+  const T* Yp = static_cast<const T*>(a.Ypart);
+  const T* Uh = static_cast<const T*>(a.Uh);
+  T* Un = static_cast<T*>(a.Unew);
+  T* Yn = static_cast<T*>(a.Ynew);
+  for (int c = 0; c < rh; ++c) {
+    double x = 0.0;
+    for (int sidx = 0; sidx < a.gC; ++sidx)
+      x += (double)Xp[(int64_t)sidx * a.xp_s + (int64_t)c * a.part_cs + j];
+    for (int c2 = 0; c2 < rh; ++c2) x = fma((double)Uh[(int64_t)c2 * a.fs + j], Cs[c2 * rh + c], x);
+    Un[(int64_t)c * a.fs + j] = (T)x;
+    if (Yp) {
+      double y = 0.0;
+      for (int q = 0; q < a.gR; ++q)
+        y += (double)Yp[(int64_t)q * a.yp_q + (int64_t)c * a.part_cs + j];
+      Yn[(int64_t)c * a.fs + j] = (T)y;
+    }
+  }
+  if (a.W2h) {
+    // W_{2h} block b = sum of V_{2h} blocks b..end (blocks of r_in columns)
+    const T* V2 = static_cast<const T*>(a.V2h);
+    T* W2 = static_cast<T*>(a.W2h);
+    const int width = 2 * rh;
+    const int nblk = width / a.r_in;
+    for (int c = 0; c < a.r_in; ++c) {
+      double acc = 0.0;
+      for (int b = nblk - 1; b >= 0; --b) {
+        const int col = b * a.r_in + c;
+        acc += (double)V2[(int64_t)col * a.fs + j];
+        W2[(int64_t)col * a.fs + j] = (T)acc;
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_assemble(const AssembleParams& a, cudaStream_t s) {
+  const int grid = (a.n + kThreads - 1) / kThreads;
+  const size_t smem = sizeof(double) * (size_t)a.r_h * a.r_h;
+  assemble_kernel<T><<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void suffix_sums_kernel(const T* V, T* W, int64_t fs, int n, int width, int r_in) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int nblk = width / r_in;
+  for (int c = 0; c < r_in; ++c) {
+    double acc = 0.0;
+    for (int b = nblk - 1; b >= 0; --b) {
+      const int col = b * r_in + c;
+      acc += (double)V[(int64_t)col * fs + j];
+      W[(int64_t)col * fs + j] = (T)acc;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_suffix_sums(const T* V, T* W, int64_t fs, int n, int width, int r_in,
+                               cudaStream_t s) {
+  suffix_sums_kernel<T><<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(V, W, fs, n, width,
+                                                                          r_in);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void rm_to_cm_kernel(const T* src, int64_t ld, T* dst, int64_t fs, int rows, int cols) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)rows * cols) return;
+  const int c = (int)(idx / rows);
+  const int j = (int)(idx % rows);
+  dst[(int64_t)c * fs + j] = src[(int64_t)j * ld + c];
+}
+
+template <typename T>
+cudaError_t launch_rm_to_cm(const T* src, int64_t ld, T* dst, int64_t fs, int rows, int cols,
+                            cudaStream_t s) {
+  const int64_t tot = (int64_t)rows * cols;
+  if (tot == 0) return cudaSuccess;
+  rm_to_cm_kernel<T><<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      src, ld, dst, fs, rows, cols);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void cm_to_rm_kernel(const T* src, int64_t fs, T* dst, int64_t ld, int rows, int cols) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)rows * cols) return;
+  const int j = (int)(idx / cols);
+  const int c = (int)(idx % cols);
+  dst[(int64_t)j * ld + c] = src[(int64_t)c * fs + j];
+}
+
+template <typename T>
+cudaError_t launch_cm_to_rm(const T* src, int64_t fs, T* dst, int64_t ld, int rows, int cols,
+                            cudaStream_t s) {
+  const int64_t tot = (int64_t)rows * cols;
+  if (tot == 0) return cudaSuccess;
+  cm_to_rm_kernel<T><<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      src, fs, dst, ld, rows, cols);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void unit_column_kernel(T* dst, int n, int row) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) dst[j] = (j == row) ? T(1) : T(0);
+}
+
+template <typename T>
+cudaError_t launch_unit_column(T* dst, int n, int row, cudaStream_t s) {
+  unit_column_kernel<T><<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(dst, n, row);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void sum_partials_kernel(const T* part, int blocks, int64_t bs, int64_t cs, int n,
+                                    int r, T* out, int64_t ocs) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * r) return;
+  const int c = (int)(idx / n);
+  const int j = (int)(idx % n);
+  double acc = 0.0;
+  for (int b = 0; b < blocks; ++b) acc += (double)part[(int64_t)b * bs + (int64_t)c * cs + j];
+  out[(int64_t)c * ocs + j] = (T)acc;
+}
+
+template <typename T>
+cudaError_t launch_sum_partials(const T* part, int blocks, int64_t block_stride, int64_t cs, int n,
+                                int r, T* out, int64_t out_cs, cudaStream_t s) {
+  const int64_t tot = (int64_t)n * r;
+  if (tot == 0) return cudaSuccess;
+  sum_partials_kernel<T><<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      part, blocks, block_stride, cs, n, r, out, out_cs);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void axpy_rows_kernel(T* y, int64_t ldy, const T* x, int64_t ldx, T alpha, int rows,
+                                 int cols) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)rows * cols) return;
+  const int i = (int)(idx / cols), c = (int)(idx % cols);
+  y[(int64_t)i * ldy + c] += alpha * x[(int64_t)i * ldx + c];
+}
+
+template <typename T>
+cudaError_t launch_axpy_rows(T* y, int64_t ldy, const T* x, int64_t ldx, T alpha, int rows,
+                             int cols, cudaStream_t s) {
+  const int64_t tot = (int64_t)rows * cols;
+  if (tot == 0) return cudaSuccess;
+  axpy_rows_kernel<T><<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      y, ldy, x, ldx, alpha, rows, cols);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void scale_copy_kernel(T* y, int64_t ldy, const T* x, int64_t ldx, T alpha, int rows,
+                                  int cols) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)rows * cols) return;
+  const int i = (int)(idx / cols), c = (int)(idx % cols);
+  y[(int64_t)i * ldy + c] = alpha * x[(int64_t)i * ldx + c];
+}
+
+template <typename T>
+cudaError_t launch_scale_copy(T* y, int64_t ldy, const T* x, int64_t ldx, T alpha, int rows,
+                              int cols, cudaStream_t s) {
+  const int64_t tot = (int64_t)rows * cols;
+  if (tot == 0) return cudaSuccess;
+  scale_copy_kernel<T><<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      y, ldy, x, ldx, alpha, rows, cols);
+  return cudaGetLastError();
+}
+
+#define LV_INST(T)                                                                              \
+  template cudaError_t launch_gram<T>(const T*, const T*, int64_t, int, int, double*, unsigned*, \
+                                      double*, unsigned*, cudaStream_t);                        \
+  template cudaError_t launch_assemble<T>(const AssembleParams&, cudaStream_t);                  \
+  template cudaError_t launch_suffix_sums<T>(const T*, T*, int64_t, int, int, int, cudaStream_t); \
+  template cudaError_t launch_rm_to_cm<T>(const T*, int64_t, T*, int64_t, int, int,               \
+                                          cudaStream_t);                                        \
+  template cudaError_t launch_cm_to_rm<T>(const T*, int64_t, T*, int64_t, int, int,               \
+                                          cudaStream_t);                                        \
+  template cudaError_t launch_unit_column<T>(T*, int, int, cudaStream_t);                        \
+  template cudaError_t launch_sum_partials<T>(const T*, int, int64_t, int64_t, int, int, T*,      \
+                                              int64_t, cudaStream_t);                           \
+  template cudaError_t launch_axpy_rows<T>(T*, int64_t, const T*, int64_t, T, int, int,           \
+                                           cudaStream_t);                                       \
+  template cudaError_t launch_scale_copy<T>(T*, int64_t, const T*, int64_t, T, int, int,          \
+                                            cudaStream_t);
+LV_INST(float)
+LV_INST(double)
+
+}  // namespace lv

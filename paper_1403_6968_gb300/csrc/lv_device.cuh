@@ -1,0 +1,114 @@
+// Device-side building blocks shared by the LINVIEW kernels: mbarrier and
+// TMA (cp.async.bulk.tensor) wrappers in inline PTX for sm_103a, with every
+// wait bounded so that a lost transaction turns into a latched error status
+// instead of a hung GPU.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lv {
+
+// Device status word bits (latched by kernels, read by linview_sync).
+enum : unsigned {
+  kStatusTimeout = 1u,
+  kStatusNonFinite = 2u,
+  kStatusSingular = 4u,
+};
+
+// ~ several seconds of polling on a 2 GHz part before a wait gives up.
+constexpr long long kMaxPolls = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wall-clock limit of one bounded wait (2 s).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// Bounded wait on phase ``parity``; returns false (and latches a timeout in
+// *status) if the barrier did not complete within kWaitLimitNs (or
+// kMaxPolls polls, whichever comes first).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (long long i = 0; i < kMaxPolls; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && global_ns() - t0 > kWaitLimitNs) break;
+  }
+  if (status) atomicOr(status, kStatusTimeout);
+  return false;
+}
+
+// 2-D tiled TMA load of a box at element coordinates (x = column, y = row)
+// into shared memory, completing ``bytes`` transaction bytes on ``bar``.
+// x * sizeof(element) must be a multiple of 16 bytes (callers pass multiples
+// of the box width, which is 1 KB).
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const void* tmap) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmap)) : "memory");
+}
+
+// 16-byte vector helpers for float (4 lanes) and double (2 lanes).
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  static constexpr int N = 4;
+  using type = float4;
+};
+template <>
+struct Vec<double> {
+  static constexpr int N = 2;
+  using type = double2;
+};
+
+}  // namespace lv

@@ -1,0 +1,118 @@
+// Internal declarations shared by the LINVIEW translation units (kernels and
+// the C-ABI/engine).  Not part of the public ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lv {
+
+constexpr int kThreads = 256;   // threads per pass CTA
+constexpr int kBatch = 8;       // rows per pipeline stage = TMA box height = warps per CTA
+constexpr int kStages = 4;      // TMA ring depth
+constexpr int kBoxBytes = 1024; // bytes per TMA box row (256 floats / 128 doubles)
+constexpr int kMaxFusedR = 8;   // widest factor block of the fused products pass
+constexpr int kMaxUpdateR = 64; // widest rank of the update-only pass (float)
+
+// Pass modes: which of X = P Xf, Y = P^T Yf and P += Uu Wu^T a launch does.
+enum PassMode : int { kModeXYU = 7, kModeXY = 3, kModeXU = 5, kModeX = 1 };
+
+// Everything a view pass needs.  Factors are column-major with column
+// stride ``fs`` (elements); the partial-sum arrays are [block][column][row]
+// with column stride ``part_cs`` and block strides ``xp_s`` / ``yp_q``.
+struct PassParams {
+  void* P;            // view, row-major
+  int64_t ldp;        // leading dimension of P (elements)
+  int n;              // P is n x n
+  const void* Xf;     // X factor (n x r) or null
+  const void* Yf;     // Y factor (n x r) or null
+  const void* Uu;     // update left factor (n x r) or null
+  const void* Wu;     // update right factor (n x r) or null
+  int64_t fs;         // factor column stride
+  int r;              // valid factor columns (<= template width)
+  void* Xpart;        // [gC][r][part_cs] row-sum partials (pre-offset to the column block)
+  void* Ypart;        // [gR][r][part_cs] column-sum partials
+  int64_t part_cs;
+  int64_t xp_s;
+  int64_t yp_q;
+  int gC, gR;         // column strips x row ranges; grid = gC * gR
+  int rows_per_cta;   // multiple of kBatch
+  unsigned* status;   // device status word
+};
+
+// Host: grid geometry for a pass over an n x n view.
+struct PassGeom {
+  int strip, gC, gR, rows_per_cta;
+};
+PassGeom fused_geom(int elem_bytes, int n, int num_sms);
+PassGeom update_geom(int elem_bytes, int R, int n, int num_sms);
+
+// Host: 2-D tensor map over a row-major matrix (rows x cols, ld elements),
+// box = (kBoxBytes / elem_bytes) columns x kBatch rows.
+bool make_tmap(CUtensorMap* out, const void* base, int elem_bytes, int64_t cols, int64_t rows,
+               int64_t ld);
+
+// Launchers (return cudaGetLastError()).  R is the runtime factor width,
+// bucketed internally to a compiled width.
+template <typename T>
+cudaError_t launch_fused(const PassParams& p, const CUtensorMap& tm, int R, int mode,
+                         cudaStream_t s);
+template <typename T>
+cudaError_t launch_update(const PassParams& p, const CUtensorMap& tm, int R, cudaStream_t s);
+
+// Factor cores and assembly (lv_core.cu).
+// C (r x r, FP64, row-major) = V^T U over n rows; deterministic two-level
+// reduction using Cpart (grid x r*r doubles) and a ticket counter.
+template <typename T>
+cudaError_t launch_gram(const T* V, const T* U, int64_t fs, int n, int r, double* Cpart,
+                        unsigned* ticket, double* C, unsigned* status, cudaStream_t s);
+int gram_grid(int n);
+
+struct AssembleParams {
+  int n, r_h, r_in;       // rows, current factor width, input rank (block width)
+  int64_t fs;             // arena column stride
+  const void* Xpart; int gC; int64_t xp_s;   // row-sum partials of P_h U_h
+  const void* Ypart; int gR; int64_t yp_q;   // column-sum partials of P_h^T V_h
+  int64_t part_cs;
+  const double* C;        // r_h x r_h = V_h^T U_h
+  const void* Uh;         // U_h (n x r_h)
+  void* Unew;             // destination of X_h + U_h C_h (n x r_h), = U arena + r_h columns
+  void* Ynew;             // destination of Y_h (n x r_h), = V arena left of V_h
+  const void* V2h;        // V_{2h} (n x 2 r_h), for the suffix sums
+  void* W2h;              // Ŵ_{2h} (n x 2 r_h) or null
+};
+template <typename T>
+cudaError_t launch_assemble(const AssembleParams& a, cudaStream_t s);
+
+// Suffix block sums: W[:, a-block] = sum_{b >= a} V[:, b-block] (blocks of r_in).
+template <typename T>
+cudaError_t launch_suffix_sums(const T* V, T* W, int64_t fs, int n, int width, int r_in,
+                               cudaStream_t s);
+
+// Copy a row-major user matrix (rows x cols, ld) into column-major storage
+// (column stride fs) -- factor ingest.
+template <typename T>
+cudaError_t launch_rm_to_cm(const T* src, int64_t ld, T* dst, int64_t fs, int rows, int cols,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_cm_to_rm(const T* src, int64_t fs, T* dst, int64_t ld, int rows, int cols,
+                            cudaStream_t s);
+// e_row as one column (column-major, n rows).
+template <typename T>
+cudaError_t launch_unit_column(T* dst, int n, int row, cudaStream_t s);
+
+// Sum of column-major partial blocks: out[c][j] = sum_b part[b][c][j].
+template <typename T>
+cudaError_t launch_sum_partials(const T* part, int blocks, int64_t block_stride, int64_t cs,
+                                int n, int r, T* out, int64_t out_cs, cudaStream_t s);
+
+// Elementwise helpers.
+template <typename T>
+cudaError_t launch_axpy_rows(T* y, int64_t ldy, const T* x, int64_t ldx, T alpha, int rows,
+                             int cols, cudaStream_t s);  // y += alpha x (row-major blocks)
+template <typename T>
+cudaError_t launch_scale_copy(T* y, int64_t ldy, const T* x, int64_t ldx, T alpha, int rows,
+                              int cols, cudaStream_t s);  // y = alpha x
+
+}  // namespace lv

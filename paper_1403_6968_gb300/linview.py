@@ -1,0 +1,233 @@
+"""Thin Python binding of the LINVIEW C ABI (argument marshalling only).
+
+Every computation runs in the CUDA library (``liblinview.so``); this module
+turns torch tensors / numpy arrays into pointers, leading dimensions and the
+current CUDA stream, and raises ``LinviewError`` on a non-OK status.
+PyTorch provides device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import LinviewError  # noqa: F401
+
+KINDS = {"power": L.POWER, "power_sum": L.POWER_SUM, "iteration": L.ITERATION, "ols": L.OLS}
+REEVAL = {"default": L.REEVAL_DEFAULT, "fp32": L.REEVAL_FP32, "tf32": L.REEVAL_TF32,
+          "bf16x9": L.REEVAL_BF16X9, "fp64": L.REEVAL_FP64}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dtype_of(precision):
+    return np.float64 if precision == L.F64 else np.float32
+
+
+class _Operand:
+    """A 2-D row-major operand: (pointer, ld, on_device, keepalive)."""
+
+    def __init__(self, x, np_dtype):
+        torch = _torch()
+        if isinstance(x, torch.Tensor):
+            want = torch.float64 if np_dtype == np.float64 else torch.float32
+            if x.dtype != want:
+                raise TypeError(f"expected {want}, got {x.dtype}")
+            if x.dim() == 1:
+                x = x.reshape(-1, 1)
+            if x.stride(1) != 1:
+                x = x.contiguous()
+            self.keep = x
+            self.ptr = C.c_void_p(x.data_ptr())
+            self.ld = x.stride(0) if x.shape[0] > 1 else x.shape[1]
+            self.on_device = 1 if x.is_cuda else 0
+            self.shape = tuple(x.shape)
+        else:
+            a = np.asarray(x)
+            if a.dtype != np_dtype:
+                raise TypeError(f"expected {np_dtype}, got {a.dtype}")
+            if a.ndim == 1:
+                a = a.reshape(-1, 1)
+            a = np.ascontiguousarray(a)
+            self.keep = a
+            self.ptr = C.c_void_p(a.ctypes.data)
+            self.ld = a.shape[1]
+            self.on_device = 0
+            self.shape = a.shape
+
+
+class Program:
+    """A maintained program (powers, sums of powers, iteration, OLS).
+
+    ``inputs`` are torch tensors (CUDA or CPU) or numpy arrays, all of the
+    program's element type (float32 or float64).
+    """
+
+    def __init__(self, kind, inputs, k, r_max=1, precision="f32", p=0, m=0,
+                 correction_period=0, reeval_mode="default", stream=None):
+        self.lib = L.load()
+        self.precision = L.F64 if precision in ("f64", "fp64", L.F64) else L.F32
+        self.np_dtype = _dtype_of(self.precision)
+        ops = [_Operand(x, self.np_dtype) for x in inputs]
+        d = L.ProgramDesc()
+        d.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+        d.precision = self.precision
+        d.n = ops[0].shape[1] if d.kind != L.OLS else ops[0].shape[1]
+        d.m = m if m else (ops[0].shape[0] if d.kind == L.OLS else 0)
+        d.p = p if p else (ops[1].shape[1] if d.kind in (L.ITERATION, L.OLS) else 0)
+        d.k = int(k)
+        d.r_max = int(r_max)
+        d.correction_period = int(correction_period)
+        d.reeval_mode = REEVAL[reeval_mode] if isinstance(reeval_mode, str) else int(reeval_mode)
+        on_dev = {o.on_device for o in ops}
+        if len(on_dev) != 1:
+            raise ValueError("inputs must all be on the device or all on the host")
+        ptrs = (C.c_void_p * len(ops))(*[o.ptr for o in ops])
+        lds = (C.c_int64 * len(ops))(*[o.ld for o in ops])
+        h = C.c_void_p()
+        L.call("linview_create_program", C.byref(d), ptrs, lds, on_dev.pop(), _stream_ptr(stream),
+               C.byref(h))
+        self.h = h
+        self.desc = d
+        self.n = d.n
+        self.k = d.k
+
+    # -- updates -----------------------------------------------------------
+    def apply_delta(self, U, V, input_id=0, stream=None):
+        u = _Operand(U, self.np_dtype)
+        v = _Operand(V, self.np_dtype)
+        if u.on_device != v.on_device:
+            raise ValueError("U and V must be on the same side")
+        L.call("linview_apply_delta", self.h, input_id, u.shape[1], u.ptr, u.ld, v.ptr, v.ld,
+               u.on_device, _stream_ptr(stream))
+
+    def apply_row_delta(self, row, v, input_id=0, stream=None):
+        o = _Operand(v, self.np_dtype)
+        L.call("linview_apply_row_delta", self.h, input_id, int(row), o.ptr, o.on_device,
+               _stream_ptr(stream))
+
+    def apply_row_block(self, rows, new_rows, stream=None):
+        rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+        o = _Operand(new_rows, self.np_dtype)
+        L.call("linview_apply_row_block", self.h, len(rows),
+               rows.ctypes.data_as(C.POINTER(C.c_int64)), o.ptr, o.ld, o.on_device,
+               _stream_ptr(stream))
+
+    # -- views -------------------------------------------------------------
+    def num_views(self):
+        return self.lib.linview_num_views(self.h)
+
+    def view_shape(self, vid):
+        r, c = C.c_int64(), C.c_int64()
+        L.call("linview_view_shape", self.h, int(vid), C.byref(r), C.byref(c))
+        return r.value, c.value
+
+    def read_view(self, vid, out=None, stream=None):
+        """Copy view ``vid`` into a new (or given) CUDA tensor."""
+        torch = _torch()
+        rows, cols = self.view_shape(vid)
+        if out is None:
+            dt = torch.float64 if self.precision == L.F64 else torch.float32
+            out = torch.empty((rows, cols), dtype=dt, device="cuda")
+        L.call("linview_read_view", self.h, int(vid), C.c_void_p(out.data_ptr()), out.stride(0),
+               1 if out.is_cuda else 0, _stream_ptr(stream))
+        return out
+
+    def read_view_rows(self, vid, row0, nrows, out=None, stream=None):
+        """Rows [row0, row0+nrows) of a view into ``out`` (numpy or torch; host
+        or device); returns ``out``."""
+        rows, cols = self.view_shape(vid)
+        if out is None:
+            out = np.empty((nrows, cols), dtype=self.np_dtype)
+        o = _Operand(out, self.np_dtype)
+        L.call("linview_read_view_rows", self.h, int(vid), int(row0), int(nrows), o.ptr, o.ld,
+               o.on_device, _stream_ptr(stream))
+        return out
+
+    def read_view_host(self, vid, stream=None):
+        rows, cols = self.view_shape(vid)
+        out = np.empty((rows, cols), dtype=self.np_dtype)
+        L.call("linview_read_view", self.h, int(vid), C.c_void_p(out.ctypes.data), cols, 0,
+               _stream_ptr(stream))
+        return out
+
+    # -- strategies and status --------------------------------------------
+    def reeval(self, stream=None):
+        L.call("linview_reeval", self.h, _stream_ptr(stream))
+
+    def set_reeval_mode(self, mode):
+        L.call("linview_set_reeval_mode", self.h, REEVAL[mode] if isinstance(mode, str) else mode)
+
+    def sync(self, stream=None):
+        L.call("linview_sync", self.h, _stream_ptr(stream))
+
+    # -- adjoints ----------------------------------------------------------
+    def adjoint_iteration(self, dA=None, dB=None, stream=None):
+        pa = C.c_void_p(dA.data_ptr()) if dA is not None else None
+        pb = C.c_void_p(dB.data_ptr()) if dB is not None else None
+        L.call("linview_adjoint_iteration", self.h, pa, dA.stride(0) if dA is not None else 0,
+               pb, dB.stride(0) if dB is not None else 0, _stream_ptr(stream))
+
+    def adjoint_power(self, G, dA, stream=None):
+        L.call("linview_adjoint_power", self.h, C.c_void_p(G.data_ptr()), G.stride(0),
+               C.c_void_p(dA.data_ptr()), dA.stride(0), _stream_ptr(stream))
+
+    # -- measurement -------------------------------------------------------
+    def set_profiling(self, on=True):
+        L.call("linview_set_profiling", self.h, 1 if on else 0)
+
+    def reset_stats(self):
+        L.call("linview_reset_stats", self.h)
+
+    def pass_stats(self, kernel=0):
+        """kernel: 0 all view passes, 1 fused products+update pass, 2 update-only pass."""
+        n, ms, b, al = C.c_int64(), C.c_double(), C.c_double(), C.c_int64()
+        L.call("linview_pass_stats", self.h, int(kernel), C.byref(n), C.byref(ms), C.byref(b),
+               C.byref(al))
+        return {"launches": n.value, "ms": ms.value, "bytes": b.value, "all_launches": al.value}
+
+    def view_device_ptr(self, vid):
+        ptr, ld = C.c_void_p(), C.c_int64()
+        L.call("linview_view_device_ptr", self.h, int(vid), C.byref(ptr), C.byref(ld))
+        return ptr.value, ld.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.linview_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def level_pass(P, U, V, X=None, Y=None, do_update=True, stream=None):
+    """One exponential-model level pass on caller tensors (all CUDA).
+
+    P: n x n (row-major); U, V, X, Y: column-major n x r given as r x n
+    row-major tensors (each row one factor column, i.e. U_cm = U.T)."""
+    torch = _torch()
+    n = P.shape[0]
+    prec = L.F64 if P.dtype == torch.float64 else L.F32
+    r = U.shape[0]
+    ldf = U.stride(0)
+    for t in (V, X, Y):
+        if t is not None and (t.shape[0] != r or t.stride(0) != ldf):
+            raise ValueError("U, V, X, Y must share shape (r, n) and stride")
+    L.call("linview_level_pass", prec, n, C.c_void_p(P.data_ptr()), P.stride(0),
+           C.c_void_p(U.data_ptr()), C.c_void_p(V.data_ptr()), ldf, r,
+           C.c_void_p(X.data_ptr()) if X is not None else None,
+           C.c_void_p(Y.data_ptr()) if Y is not None else None,
+           1 if do_update else 0, _stream_ptr(stream))

@@ -1,0 +1,137 @@
+"""GPU parity: general form T_{i+1} = A T_i + B (Appendix B, linear model) and
+the adjoints of L = ||T_k||_F^2 and of a loss of P_k, vs the FP64 oracle.
+
+Tolerances: FP64 1e-10 for views, FP32 1e-4 (spec bounds); the FP64 GPU
+adjoint meets central finite differences (h = 1e-3, FP64, n = 512) within
+1e-6 ||dA||_F (truncation O(h^2) is far smaller; a wrong term is O(||dA||))."""
+import numpy as np
+import pytest
+
+import linview_inputs as li
+from oracle import iteration as oi
+from oracle import powers as op
+from oracle.metrics import rel_frob
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _prog(*a, **kw):
+    from paper_1403_6968_gb300 import Program
+    return Program(*a, **kw)
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,p,k,r", [(300, 5, 16, 2), (1, 1, 1, 1), (777, 64, 16, 2),
+                                     (1030, 3, 4, 4), (64, 7, 2, 1)])
+def test_iteration_incremental(prec, n, p, k, r):
+    dt = np.float64 if prec == "f64" else np.float32
+    a, b, t0 = li.iteration_inputs(n, p, seed=n, dtype=dt)
+    prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=k, r_max=r, precision=prec)
+    acur = a.astype(np.float64)
+    b64, t064 = b.astype(np.float64), t0.astype(np.float64)
+    tol = 1e-10 if prec == "f64" else 1e-4
+    ref = oi.reeval(acur, b64, t064, k)
+    prog.sync()
+    for i in range(1, k + 1):
+        assert rel_frob(prog.read_view_host(i), ref[i]) <= tol
+    for u, v in li.lowrank_update_stream(n, r, 3, seed=n + 1, dtype=dt):
+        prog.apply_delta(_dev(u), _dev(v))
+        acur += u.astype(np.float64) @ v.astype(np.float64).T
+        prog.sync()
+        ref = oi.reeval(acur, b64, t064, k)
+        for i in range(1, k + 1):
+            assert rel_frob(prog.read_view_host(i), ref[i]) <= tol, i
+        assert rel_frob(prog.read_view_host(0), acur) <= tol
+
+
+def test_iteration_matches_oracle_incremental_factors_path():
+    n, p, k, r = 500, 8, 16, 2
+    a, b, t0 = li.iteration_inputs(n, p, seed=1)
+    prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=k, r_max=r, precision="f64")
+    inc = oi.IncrementalIteration(a, b, t0, k)
+    for u, v in li.lowrank_update_stream(n, r, 3, seed=2):
+        prog.apply_delta(_dev(u), _dev(v))
+        inc.apply(u, v)
+    prog.sync()
+    for i in range(1, k + 1):
+        assert rel_frob(prog.read_view_host(i), inc.t[i]) <= 1e-10
+
+
+def _unit(x):
+    return x / np.linalg.norm(x)
+
+
+def test_iteration_adjoint_fp64_central_fd_n512():
+    """Differentiation form at the FD size: n=512, p=64, k=16, FP64."""
+    n, p, k = 512, 64, 16
+    a, b, t0 = li.iteration_inputs(n, p, seed=21)
+    prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=k, r_max=2, precision="f64")
+    (u, v), = li.lowrank_update_stream(n, 2, 1, seed=22)
+    prog.apply_delta(_dev(u), _dev(v))
+    acur = a + u @ v.T
+    dA = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    dB = torch.empty((n, p), dtype=torch.float64, device="cuda")
+    prog.adjoint_iteration(dA, dB)
+    torch.cuda.synchronize()
+    da, db = dA.cpu().numpy(), dB.cpu().numpy()
+    ra, rb, _ = oi.adjoint(acur, b, t0, k)
+    assert rel_frob(da, ra) <= 1e-10
+    assert rel_frob(db, rb) <= 1e-10
+    h = 1e-3
+    g = np.random.default_rng(23)
+    dirs = [_unit(li.normal((n, n), seed=30 + t)) for t in range(8)]
+    for _ in range(8):
+        e = np.zeros((n, n)); e[g.integers(n), g.integers(n)] = 1.0
+        dirs.append(e)
+    scale = float(np.linalg.norm(da))
+    for e in dirs:
+        fd = (oi.loss(acur + h * e, b, t0, k) - oi.loss(acur - h * e, b, t0, k)) / (2 * h)
+        assert abs(fd - float(np.sum(da * e))) <= 1e-6 * scale
+    for t in range(3):
+        e = _unit(li.normal((n, p), seed=40 + t))
+        fd = (oi.loss(acur, b + h * e, t0, k) - oi.loss(acur, b - h * e, t0, k)) / (2 * h)
+        assert abs(fd - float(np.sum(db * e))) <= 1e-6 * float(np.linalg.norm(db))
+
+
+def test_iteration_adjoint_fp32_vs_oracle():
+    n, p, k = 2048, 64, 16
+    a, b, t0 = li.iteration_inputs(n, p, seed=31, dtype=np.float32)
+    prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=k, r_max=2)
+    (u, v), = li.lowrank_update_stream(n, 2, 1, seed=32, dtype=np.float32)
+    prog.apply_delta(_dev(u), _dev(v))
+    acur = a.astype(np.float64) + u.astype(np.float64) @ v.astype(np.float64).T
+    dA = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    dB = torch.empty((n, p), dtype=torch.float32, device="cuda")
+    prog.adjoint_iteration(dA, dB)
+    torch.cuda.synchronize()
+    ra, rb, _ = oi.adjoint(acur, b.astype(np.float64), t0.astype(np.float64), k)
+    assert rel_frob(dA.cpu().numpy(), ra) <= 1e-4
+    assert rel_frob(dB.cpu().numpy(), rb) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_power_adjoint_vs_oracle(prec):
+    n, k = 384, 16
+    dt = np.float64 if prec == "f64" else np.float32
+    a = li.power_matrix(n, seed=41, dtype=dt)
+    g = li.normal((n, n), seed=42, dtype=dt)
+    prog = _prog("power", [_dev(a)], k=k, r_max=1, precision=prec)
+    dA = torch.empty((n, n), dtype=torch.float64 if prec == "f64" else torch.float32,
+                     device="cuda")
+    prog.adjoint_power(_dev(g), dA)
+    torch.cuda.synchronize()
+    ref = op.adjoint_power_chain(a.astype(np.float64), k, g.astype(np.float64))
+    assert rel_frob(dA.cpu().numpy(), ref) <= (1e-10 if prec == "f64" else 1e-4)

@@ -1,0 +1,237 @@
+"""GPU parity: matrix powers and sums of powers through the C ABI vs the FP64 oracle.
+
+Tolerances: FP64 programs 1e-10 relative Frobenius (the benchmark spec's bound);
+FP32 programs 1e-4 (spec bound for reduced-precision forms; a missing or
+mis-signed delta term gives errors of the size of the delta, >= 1e-3 here).
+"""
+import numpy as np
+import pytest
+
+import linview_inputs as li
+from oracle import powers as op
+from oracle.metrics import rel_frob
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _prog(*a, **kw):
+    from paper_1403_6968_gb300 import Program
+    return Program(*a, **kw)
+
+
+def _np(prec):
+    return np.float64 if prec == "f64" else np.float32
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _check_all(prog, acur, k, sums, tol):
+    pw = op.reeval_powers(acur, k)
+    sm = op.reeval_sums(acur, k, pw) if sums else None
+    L = len(op.levels(k)) - 1
+    errs = []
+    for j in range(L + 1):
+        errs.append(rel_frob(prog.read_view_host(j), pw[1 << j]))
+    if sums:
+        for j in range(1, L + 1):
+            errs.append(rel_frob(prog.read_view_host(L + j), sm[1 << j]))
+    assert max(errs) <= tol, errs
+    return max(errs)
+
+
+def test_config0_fp64_a8_row_updates():
+    """A^8 by 3 squarings, n=256, FP64, 10 row updates e_i v^T (i uniform,
+    v ~ N(0, 0.01^2)); every view vs FP64 re-evaluation after every update."""
+    n, k = 256, 8
+    a = li.power_matrix(n, seed=0)
+    prog = _prog("power", [_dev(a)], k=k, r_max=1, precision="f64")
+    acur = a.copy()
+    _check_all(prog, acur, k, False, 1e-12)
+    for i, v in li.row_update_stream(n, 10, seed=0):
+        prog.apply_row_delta(i, _dev(v))
+        acur[i] += v
+        prog.sync()
+        _check_all(prog, acur, k, False, TOL["f64"])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,k,r,sums", [
+    (1, 1, 1, False), (7, 2, 1, True), (100, 16, 1, True), (513, 4, 3, True),
+    (1000, 8, 2, False), (1500, 16, 8, True), (777, 16, 4, True), (2049, 2, 5, True)])
+def test_ragged_sizes_and_ranks(prec, n, k, r, sums):
+    dt = _np(prec)
+    a = li.power_matrix(n, seed=n, dtype=dt)
+    prog = _prog("power_sum" if sums else "power", [_dev(a)], k=k, r_max=r, precision=prec)
+    acur = a.astype(np.float64)
+    for t, (u, v) in enumerate(li.lowrank_update_stream(n, r, 3, seed=n + 1, dtype=dt)):
+        prog.apply_delta(_dev(u), _dev(v))
+        acur += u.astype(np.float64) @ v.astype(np.float64).T
+    # plus a row update at the last row
+    (_, v), = li.row_update_stream(n, 1, seed=n + 2, dtype=dt)
+    prog.apply_row_delta(n - 1, _dev(v))
+    acur[n - 1] += v.astype(np.float64)
+    prog.sync()
+    _check_all(prog, acur, k, sums, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_matches_oracle_incremental(prec):
+    n, k, r = 600, 16, 2
+    dt = _np(prec)
+    a = li.power_matrix(n, seed=3, dtype=dt)
+    prog = _prog("power_sum", [_dev(a)], k=k, r_max=r, precision=prec)
+    inc = op.IncrementalPowers(a.astype(np.float64), k, sums=True)
+    for u, v in li.lowrank_update_stream(n, r, 4, seed=4, dtype=dt):
+        prog.apply_delta(_dev(u), _dev(v))
+        inc.apply(u.astype(np.float64), v.astype(np.float64))
+    prog.sync()
+    L = 4
+    for j in range(L + 1):
+        assert rel_frob(prog.read_view_host(j), inc.p[1 << j]) <= TOL[prec]
+    for j in range(1, L + 1):
+        assert rel_frob(prog.read_view_host(L + j), inc.s[1 << j]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,r,upd", [(1, 1, True), (5, 3, True), (300, 8, True), (1000, 8, False),
+                                     (1031, 16, True), (2048, 64, True), (640, 24, False)])
+def test_level_pass_kernel(prec, n, r, upd):
+    """One Appendix-A level pass (P U, P^T V, P += U V^T) on caller memory."""
+    from paper_1403_6968_gb300 import level_pass
+    if prec == "f64" and r > 32:
+        pytest.skip("FP64 level pass takes r <= 32")
+    dt = _np(prec)
+    g = np.random.default_rng(n * 100 + r)
+    p = g.standard_normal((n, n)).astype(dt)
+    u = g.standard_normal((n, r)).astype(dt)
+    v = g.standard_normal((n, r)).astype(dt)
+    ld = ((n + 3) // 4) * 4
+    P = torch.zeros((n, ld), dtype=torch.float64 if prec == "f64" else torch.float32,
+                    device="cuda")
+    P[:, :n] = _dev(p)
+    Pv = P[:, :n]
+    Ut, Vt = _dev(u.T.copy()), _dev(v.T.copy())
+    Xt, Yt = torch.empty_like(Ut), torch.empty_like(Ut)
+    level_pass(Pv, Ut, Vt, Xt, Yt, do_update=upd)
+    torch.cuda.synchronize()
+    x_ref, y_ref, p_ref = op.level_products(p, u, v)
+    tol = 1e-13 if prec == "f64" else 1e-5
+    assert rel_frob(Xt.cpu().numpy().T, x_ref) <= tol
+    assert rel_frob(Yt.cpu().numpy().T, y_ref) <= tol
+    got_p = Pv.cpu().numpy()
+    assert rel_frob(got_p, p_ref if upd else p) <= tol
+    assert not P[:, n:].any()  # padding untouched
+
+
+def test_reeval_modes_against_oracle():
+    n, k = 1024, 16
+    a = li.power_matrix(n, seed=5, dtype=np.float32)
+    prog = _prog("power_sum", [_dev(a)], k=k, r_max=1)
+    ref_p = op.reeval_powers(a.astype(np.float64), k)
+    errs = {}
+    for mode, tol in (("fp32", 1e-5), ("bf16x9", 1e-5), ("tf32", 5e-2)):
+        prog.set_reeval_mode(mode)
+        prog.reeval()
+        prog.sync()
+        errs[mode] = rel_frob(prog.read_view_host(4), ref_p[16])
+        assert errs[mode] <= tol, errs
+
+
+def test_bitwise_deterministic():
+    n, k = 1200, 16
+    a = li.power_matrix(n, seed=6, dtype=np.float32)
+    ups = li.lowrank_update_stream(n, 2, 3, seed=7, dtype=np.float32)
+    outs = []
+    for _ in range(2):
+        prog = _prog("power_sum", [_dev(a)], k=k, r_max=2)
+        for u, v in ups:
+            prog.apply_delta(_dev(u), _dev(v))
+        prog.sync()
+        outs.append([prog.read_view_host(j) for j in range(prog.num_views())])
+        prog.close()
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
+
+
+def test_correction_period_resets_to_reeval():
+    n, k = 512, 8
+    a = li.power_matrix(n, seed=8, dtype=np.float32)
+    prog = _prog("power", [_dev(a)], k=k, r_max=1, correction_period=3)
+    acur = a.astype(np.float64)
+    for i, v in li.row_update_stream(n, 3, seed=9, dtype=np.float32):
+        prog.apply_row_delta(i, _dev(v))
+        acur[i] += v
+    prog.sync()
+    got = [prog.read_view_host(j) for j in range(4)]
+    prog.reeval()
+    prog.sync()
+    for j in range(4):
+        assert np.array_equal(got[j], prog.read_view_host(j))  # last update ran re-evaluation
+    _check_all(prog, acur, k, False, 1e-5)
+
+
+def test_host_side_factors_and_errors():
+    from paper_1403_6968_gb300 import LinviewError
+    n, k = 64, 4
+    a = li.power_matrix(n, seed=10, dtype=np.float32)
+    prog = _prog("power", [a], k=k, r_max=2)          # host input
+    (u, v), = li.lowrank_update_stream(n, 2, 1, seed=11, dtype=np.float32)
+    prog.apply_delta(u, v)                             # host factors
+    prog.sync()
+    acur = a.astype(np.float64) + u.astype(np.float64) @ v.astype(np.float64).T
+    _check_all(prog, acur, k, False, 1e-5)
+    (u3, v3), = li.lowrank_update_stream(n, 3, 1, seed=12, dtype=np.float32)
+    with pytest.raises(LinviewError) as e:
+        prog.apply_delta(u3, v3)
+    assert e.value.name == "ERANK"
+    with pytest.raises(LinviewError) as e:
+        prog.apply_row_delta(n, np.zeros(n, np.float32))
+    assert e.value.name == "EINVAL"
+    with pytest.raises(LinviewError) as e:
+        _prog("power", [a], k=3, r_max=1)
+    assert e.value.name == "EINVAL"
+    _check_all(prog, acur, k, False, 1e-5)             # failed calls changed nothing
+
+
+def test_full_size_sampled_rows():
+    """configs: A^16 and S' = sum_{i<=16} A^i, n=8192, FP32, row and rank-4
+    updates; sampled rows of every view vs the oracle computed row by row."""
+    n, k = 8192, 16
+    a = li.power_matrix(n, seed=0, dtype=np.float32)
+    prog = _prog("power_sum", [_dev(a)], k=k, r_max=4)
+    acur = a.astype(np.float64)
+    rows = [0, 1234, 4097, n - 1]
+
+    def check():
+        pr, sr = op.power_rows(acur, rows, k)
+        L = 4
+        for j in range(L + 1):
+            got = prog.read_view_host(j)[rows]
+            assert rel_frob(got, pr[1 << j]) <= TOL["f32"], (j, rel_frob(got, pr[1 << j]))
+        for j in range(1, L + 1):
+            got = prog.read_view_host(L + j)[rows]
+            assert rel_frob(got, sr[1 << j]) <= TOL["f32"]
+
+    prog.sync()
+    check()
+    for i, v in li.row_update_stream(n, 3, seed=0, dtype=np.float32):
+        prog.apply_row_delta(i, _dev(v))
+        acur[i] += v
+    for u, v in li.lowrank_update_stream(n, 4, 2, seed=0, dtype=np.float32):
+        prog.apply_delta(_dev(u), _dev(v))
+        acur += u.astype(np.float64) @ v.astype(np.float64).T
+    prog.sync()
+    check()
