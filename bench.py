@@ -310,58 +310,74 @@ def run_ours(args):
 
     # e2e through the public API: host v (pinned) in, one refreshed row of
     # A^16 out, every step
-    pin_v = [torch.from_numpy(v).pin_memory() for _, v in ups[W + K:W + K + E]]
-    row_out = torch.empty((1, n), dtype=torch.float32).pin_memory()
-    torch.cuda.synchronize()
-    _barrier(dist)
-    t0 = time.perf_counter()
-    for t in range(E):
-        i = rows[W + K + t]
-        prog.apply_row_delta(i, pin_v[t])
-        prog.read_view_rows(L, i, 1, out=row_out)   # synchronises the stream
-    e2e_s = _max_over_ranks(dist, time.perf_counter() - t0, True)
-    e2e = {"value": ws * E / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
-           "d2h_bytes_per_step": 4 * n, "steps": E}
+    e2e = None
+    if E > 0:
+        pin_v = [torch.from_numpy(v).pin_memory() for _, v in ups[W + K:W + K + E]]
+        row_out = torch.empty((1, n), dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        _barrier(dist)
+        t0 = time.perf_counter()
+        for t in range(E):
+            i = rows[W + K + t]
+            prog.apply_row_delta(i, pin_v[t])
+            prog.read_view_rows(L, i, 1, out=row_out)   # synchronises the stream
+        e2e_s = _max_over_ranks(dist, time.perf_counter() - t0, True)
+        e2e = {"value": ws * E / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
+               "d2h_bytes_per_step": 4 * n, "steps": E}
 
-    # GPU re-evaluation of the same views: apply dA to A, recompute all views
-    reeval = {}
-    samp = [0, n // 3, n - 1]
-    inc_rows = {j: prog.read_view_rows(j, 0, n)[samp] for j in (L, 2 * L)}
-    aptr, ald = prog.view_device_ptr(0)
-    base = None
-    for mode in ("fp32", "bf16x9", "tf32"):
-        prog.set_reeval_mode(mode)
+    # GPU re-evaluation of the same views (the paper's re-evaluation strategy:
+    # apply dA to A, recompute every view) in three GEMM arithmetics.  Errors
+    # are taken at one fixed A: each mode's views vs the IEEE-FP32 re-evaluation
+    # (sampled rows of A^16 and S'_16), and the incremental views vs it.
+    reeval, speed = {}, {}
+    if args.reeval_steps > 0:
+        samp = [0, n // 3, n - 1]
+
+        def rows_of():
+            torch.cuda.synchronize()
+            return {j: prog.read_view_rows(j, 0, n)[samp].astype(np.float64) for j in (L, 2 * L)}
+
+        def rel(x, y):
+            return {("P16" if j == L else "S16"): float(np.linalg.norm(x[j] - y[j]) /
+                                                        np.linalg.norm(y[j])) for j in x}
+
+        inc_rows = rows_of()
+        prog.set_reeval_mode("fp32")
         prog.reeval()
-        torch.cuda.synchronize()
-        got = {j: prog.read_view_rows(j, 0, n)[samp] for j in (L, 2 * L)}
-        if base is None:
-            base = got
-        errs = {("P16" if j == L else "S16"): float(np.linalg.norm(got[j] - inc_rows[j]) /
-                                                    np.linalg.norm(inc_rows[j])) for j in got}
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for t in range(args.reeval_steps):
-            # the re-evaluation strategy: apply the update to A, then recompute
-            ti = W + K + E + t
-            u = torch.zeros((1, n), dtype=torch.float32, device="cuda")
-            u[0, rows[ti]] = 1.0
-            vv = dev_v[ti].reshape(1, n)
-            _apply_to_a(aptr, ald, n, u, vv)
+        base = rows_of()
+        inc_err = rel(inc_rows, base)
+        errs = {"fp32": rel(base, base)}
+        for mode in ("bf16x9", "tf32"):
+            prog.set_reeval_mode(mode)
             prog.reeval()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.reeval_steps
-        reeval[mode] = {"refreshes_per_s": 1e3 / ms, "ms_per_refresh": ms,
-                        "rel_err_vs_incremental_sampled_rows": errs}
-    acc = [m for m in ("fp32", "bf16x9") if max(reeval[m]["rel_err_vs_incremental_sampled_rows"]
-                                                .values()) <= 1e-4]
-    fastest_acc = max(acc, key=lambda m: reeval[m]["refreshes_per_s"]) if acc else None
-    fastest_any = max(reeval, key=lambda m: reeval[m]["refreshes_per_s"])
-    speed = {"vs_fastest_accurate_reeval": (value / ws) / reeval[fastest_acc]["refreshes_per_s"]
-             if fastest_acc else None, "fastest_accurate_reeval": fastest_acc,
-             "vs_fastest_any_reeval": (value / ws) / reeval[fastest_any]["refreshes_per_s"],
-             "fastest_any_reeval": fastest_any}
+            errs[mode] = rel(rows_of(), base)
+        aptr, ald = prog.view_device_ptr(0)
+        for mode in ("fp32", "bf16x9", "tf32"):
+            prog.set_reeval_mode(mode)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for t in range(args.reeval_steps):
+                ti = W + K + E + t
+                u = torch.zeros((1, n), dtype=torch.float32, device="cuda")
+                u[0, rows[ti]] = 1.0
+                _apply_to_a(aptr, ald, n, u, dev_v[ti].reshape(1, n))
+                prog.reeval()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.reeval_steps
+            reeval[mode] = {"refreshes_per_s": 1e3 / ms, "ms_per_refresh": ms,
+                            "rel_err_vs_fp32_reeval_sampled_rows": errs[mode]}
+        reeval["incremental_rel_err_vs_fp32_reeval_sampled_rows"] = inc_err
+        modes = ("fp32", "bf16x9", "tf32")
+        acc = [m for m in modes if max(errs[m].values()) <= 1e-4]
+        fastest_acc = max(acc, key=lambda m: reeval[m]["refreshes_per_s"]) if acc else None
+        fastest_any = max(modes, key=lambda m: reeval[m]["refreshes_per_s"])
+        speed = {"vs_fastest_accurate_reeval":
+                 (value / ws) / reeval[fastest_acc]["refreshes_per_s"] if fastest_acc else None,
+                 "fastest_accurate_reeval": fastest_acc,
+                 "vs_fastest_any_reeval": (value / ws) / reeval[fastest_any]["refreshes_per_s"],
+                 "fastest_any_reeval": fastest_any}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
            "warmup": W, "ms_per_step": max_ms / K, "higher_is_better": True, "scaling": "weak",

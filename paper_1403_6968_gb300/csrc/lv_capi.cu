@@ -113,6 +113,29 @@ struct linview_program {
   // power adjoint work
   void* Gw0 = nullptr;
   void* Gw1 = nullptr;
+  // OLS: X (m x n), Y (m x p) on the device; views W, beta, X^T Y, X
+  void* Xd = nullptr;
+  int64_t ldX = 0;
+  void* Yd = nullptr;
+  int64_t ldY = 0;
+  void* XtYc = nullptr;   // column-major mirror of X^T Y (n x p, fs)
+  void* Gf = nullptr;     // G = W U, column-major n x 2k
+  void* Wuf = nullptr;    // -G M^{-1}, column-major n x 2k
+  void* betac = nullptr;  // beta, column-major n x p
+  void* Yr = nullptr;     // Y rows of the block, k x p
+  int64_t* rows_d = nullptr;
+  double* Minv = nullptr;
+  // OLS re-evaluation scratch (FP64)
+  double* Z64 = nullptr;
+  double* X64 = nullptr;
+  double* Y64 = nullptr;
+  double* XtY64 = nullptr;
+  double* W64 = nullptr;
+  double* B64 = nullptr;
+  double* solver_work = nullptr;
+  int solver_lwork = 0;
+  int* solver_info = nullptr;
+  int64_t ols_chunk = 0;
   // profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -592,6 +615,195 @@ static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) 
 }
 
 // ---------------------------------------------------------------------------
+// OLS (Section 4.1): views W = (X^T X)^{-1}, beta = W X^T Y, X^T Y, X
+// ---------------------------------------------------------------------------
+#define LV_SOLVER(expr)                                                                      \
+  do {                                                                                       \
+    cusolverStatus_t e_ = (expr);                                                            \
+    if (e_ != CUSOLVER_STATUS_SUCCESS)                                                       \
+      return fail(LINVIEW_EDEVICE, "%s failed: cusolver status %d", #expr, (int)e_);         \
+  } while (0)
+
+enum { kOlsW = 0, kOlsBeta = 1, kOlsXtY = 2, kOlsX = 3 };
+
+// Re-evaluation: Z = X^T X and X^T Y accumulated in FP64 over row chunks
+// (DSYRK / DGEMM), W = Z^{-1} by Cholesky (potrf + potri), beta = W X^T Y in
+// FP64, rounded once to the view type.
+template <typename T>
+static linview_status ols_reeval_t(linview_program* p, cudaStream_t s) {
+  const int64_t m = p->d.m, n = p->d.n, pp = p->d.p;
+  const int64_t ch = p->ols_chunk;
+  if (!p->Z64) {
+    void* t;
+    LV_TRY(dalloc(p, sizeof(double) * n * n, &t)); p->Z64 = static_cast<double*>(t);
+    LV_TRY(dalloc(p, sizeof(double) * n * n, &t)); p->W64 = static_cast<double*>(t);
+    LV_TRY(dalloc(p, sizeof(double) * ch * n, &t)); p->X64 = static_cast<double*>(t);
+    LV_TRY(dalloc(p, sizeof(double) * ch * pp, &t)); p->Y64 = static_cast<double*>(t);
+    LV_TRY(dalloc(p, sizeof(double) * n * pp, &t)); p->XtY64 = static_cast<double*>(t);
+    LV_TRY(dalloc(p, sizeof(double) * n * pp, &t)); p->B64 = static_cast<double*>(t);
+    LV_TRY(dalloc(p, sizeof(int) * 4, &t)); p->solver_info = static_cast<int*>(t);
+  }
+  if (!p->solver && cusolverDnCreate(&p->solver) != CUSOLVER_STATUS_SUCCESS)
+    return fail(LINVIEW_EDEVICE, "cusolverDnCreate failed");
+  LV_BLAS(cublasSetStream(p->blas, s));
+  LV_SOLVER(cusolverDnSetStream(p->solver, s));
+  const double one = 1.0, zero = 0.0;
+  const T* X = static_cast<const T*>(p->Xd);
+  const T* Y = static_cast<const T*>(p->Yd);
+  for (int64_t r0 = 0; r0 < m; r0 += ch) {
+    const int64_t mc = (m - r0 < ch) ? (m - r0) : ch;
+    LV_CUDA(launch_to_double<T>(X + r0 * p->ldX, p->ldX, p->X64, n, (int)mc, (int)n, s));
+    LV_CUDA(launch_to_double<T>(Y + r0 * p->ldY, p->ldY, p->Y64, pp, (int)mc, (int)pp, s));
+    // column-major view: X_c is n x mc (ld n); Z += X_c X_c^T (lower)
+    LV_BLAS(cublasDsyrk(p->blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, (int)n, (int)mc, &one,
+                        p->X64, (int)n, r0 ? &one : &zero, p->Z64, (int)n));
+    // (X^T Y)^T (p x n) += Y_c^T-view (p x mc) * X_c-view^T (mc x n)
+    LV_BLAS(cublasDgemm(p->blas, CUBLAS_OP_N, CUBLAS_OP_T, (int)pp, (int)n, (int)mc, &one,
+                        p->Y64, (int)pp, p->X64, (int)n, r0 ? &one : &zero, p->XtY64, (int)pp));
+    p->all_launches += 4;
+  }
+  if (!p->solver_work) {
+    int l1 = 0, l2 = 0;
+    LV_SOLVER(cusolverDnDpotrf_bufferSize(p->solver, CUBLAS_FILL_MODE_LOWER, (int)n, p->Z64,
+                                          (int)n, &l1));
+    LV_SOLVER(cusolverDnDpotri_bufferSize(p->solver, CUBLAS_FILL_MODE_LOWER, (int)n, p->Z64,
+                                          (int)n, &l2));
+    p->solver_lwork = l1 > l2 ? l1 : l2;
+    void* t;
+    LV_TRY(dalloc(p, sizeof(double) * (size_t)p->solver_lwork, &t));
+    p->solver_work = static_cast<double*>(t);
+  }
+  LV_SOLVER(cusolverDnDpotrf(p->solver, CUBLAS_FILL_MODE_LOWER, (int)n, p->Z64, (int)n,
+                             p->solver_work, p->solver_lwork, p->solver_info));
+  LV_SOLVER(cusolverDnDpotri(p->solver, CUBLAS_FILL_MODE_LOWER, (int)n, p->Z64, (int)n,
+                             p->solver_work, p->solver_lwork, p->solver_info + 1));
+  View& w = p->views[kOlsW];
+  LV_CUDA(launch_sym_lower_to_full<T>(p->Z64, n, (int)n, static_cast<T*>(w.ptr), w.ld, p->W64, n,
+                                      s));
+  // beta^T (p x n) = (X^T Y)^T (p x n) * W (symmetric)
+  LV_BLAS(cublasDgemm(p->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)pp, (int)n, (int)n, &one, p->XtY64,
+                      (int)pp, p->W64, (int)n, &zero, p->B64, (int)pp));
+  View& xty = p->views[kOlsXtY];
+  View& beta = p->views[kOlsBeta];
+  LV_CUDA(launch_from_double<T>(p->XtY64, pp, static_cast<T*>(xty.ptr), xty.ld, (int)n, (int)pp,
+                                static_cast<T*>(p->XtYc), p->fs, s));
+  LV_CUDA(launch_from_double<T>(p->B64, pp, static_cast<T*>(beta.ptr), beta.ld, (int)n, (int)pp,
+                                static_cast<T*>(nullptr), 0, s));
+  p->all_launches += 6;
+  int info[2] = {0, 0};
+  LV_CUDA(cudaMemcpyAsync(info, p->solver_info, sizeof(info), cudaMemcpyDeviceToHost, s));
+  LV_CUDA(cudaStreamSynchronize(s));
+  if (info[0] != 0 || info[1] != 0)
+    return fail(LINVIEW_ESINGULAR, "X^T X is not positive definite (potrf/potri info %d/%d)",
+                info[0], info[1]);
+  return LINVIEW_OK;
+}
+
+static linview_status ols_create(linview_program* p, const void* const* inputs,
+                                 const int64_t* lds, int on_dev, cudaStream_t s) {
+  const int64_t m = p->d.m, n = p->d.n, pp = p->d.p;
+  const int kmax = p->d.k;
+  if (m < n || pp < 1 || kmax < 1) return fail(LINVIEW_EINVAL, "OLS needs m >= n, p >= 1, k >= 1");
+  if (2 * kmax > 64) return fail(LINVIEW_EUNSUPPORTED, "row blocks are limited to k <= 32");
+  if (lds[0] < n || lds[1] < pp) return fail(LINVIEW_ESHAPE, "bad leading dims");
+  p->fs = rup(n, 64);
+  LV_TRY(add_square_view(p, n));                     // W
+  const int64_t ldp = rup(pp, 4);
+  void* t;
+  LV_TRY(dalloc(p, (size_t)n * ldp * p->elem, &t));   // beta
+  LV_TRY(add_rect_view(p, t, n, pp, ldp));
+  LV_TRY(dalloc(p, (size_t)n * ldp * p->elem, &t));   // X^T Y
+  LV_TRY(add_rect_view(p, t, n, pp, ldp));
+  p->ldX = rup(n, 64);
+  LV_TRY(dalloc(p, (size_t)m * p->ldX * p->elem, &p->Xd));
+  LV_TRY(add_rect_view(p, p->Xd, m, n, p->ldX));
+  p->ldY = ldp;
+  LV_TRY(dalloc(p, (size_t)m * p->ldY * p->elem, &p->Yd));
+  LV_TRY(copy_in(p->Xd, p->ldX, inputs[0], lds[0], m, n, p->elem, on_dev, s));
+  LV_TRY(copy_in(p->Yd, p->ldY, inputs[1], lds[1], m, pp, p->elem, on_dev, s));
+  const int kk = 2 * kmax;
+  LV_TRY(dalloc(p, (size_t)p->fs * pp * p->elem, &p->XtYc));
+  LV_TRY(dalloc(p, (size_t)p->fs * kk * p->elem, &p->Uar));
+  LV_TRY(dalloc(p, (size_t)p->fs * kk * p->elem, &p->Gf));
+  LV_TRY(dalloc(p, (size_t)p->fs * kk * p->elem, &p->Wuf));
+  LV_TRY(dalloc(p, (size_t)p->fs * pp * p->elem, &p->betac));
+  LV_TRY(dalloc(p, (size_t)kmax * pp * p->elem, &p->Yr));
+  LV_TRY(dalloc(p, sizeof(int64_t) * kmax, &t));
+  p->rows_d = static_cast<int64_t*>(t);
+  LV_TRY(dalloc(p, sizeof(double) * kk * kk, &t));
+  p->Minv = static_cast<double*>(t);
+  const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
+  p->part_cs = p->fs;
+  const int64_t width = (kk > pp) ? kk : pp;
+  p->xp_s = rup(width, kMaxFusedR) * p->part_cs;
+  p->yp_q = p->xp_s;
+  LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart));
+  LV_TRY(dalloc(p, (size_t)g.gR * kMaxFusedR * p->part_cs * p->elem, &p->Ypart));
+  p->ols_chunk = m < 8192 ? m : 8192;
+  return p->elem == 4 ? ols_reeval_t<float>(p, s) : ols_reeval_t<double>(p, s);
+}
+
+// Row-block replacement by block Woodbury (see lv_ols.cu for the algebra).
+template <typename T>
+static linview_status ols_replace_t(linview_program* p, int kr, const void* nrows, int64_t ld,
+                                    int on_dev, cudaStream_t s) {
+  const int n = (int)p->d.n;
+  const int pp = (int)p->d.p;
+  const int64_t fs = p->fs;
+  const int kk = 2 * kr;
+  T* U = static_cast<T*>(p->Uar);
+  T* G = static_cast<T*>(p->Gf);
+  T* Wu = static_cast<T*>(p->Wuf);
+  View& w = p->views[kOlsW];
+  const PassGeom g = fused_geom(sizeof(T), n, p->sms);
+  // U = [X'_R^T, X_R^T]: new rows become the first kr columns, old rows the next kr
+  LV_CUDA(cudaMemcpy2DAsync(U, fs * sizeof(T), nrows, ld * sizeof(T), (size_t)n * sizeof(T), kr,
+                            on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  LV_CUDA(launch_gather_rows<T>(static_cast<const T*>(p->Xd), p->ldX, p->rows_d, kr, n,
+                                U + (int64_t)kr * fs, fs, 1, s));
+  LV_CUDA(launch_gather_rows<T>(static_cast<const T*>(p->Yd), p->ldY, p->rows_d, kr, pp,
+                                static_cast<T*>(p->Yr), pp, 1, s));
+  p->all_launches += 2;
+  // G = W U (one read of W per 8 columns)
+  LV_TRY(run_products_update<T>(p, w, kk, U, nullptr, nullptr, nullptr, s));
+  {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, kk, G,
+                                   fs, s));
+  }
+  // M = C^{-1} + U^T G (FP64), its inverse, Wu = -G M^{-1}
+  {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA((launch_gram<T>(U, G, fs, n, kk, p->Cpart, p->ticket, p->C, p->status, s)));
+  }
+  {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_core_inverse(p->C, kk, kr, p->Minv, p->status, s));
+  }
+  {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_wu<T>(G, fs, n, kk, p->Minv, Wu, s));
+  }
+  // W' = W + G Wu^T = W - G M^{-1} G^T
+  LV_TRY(run_update<T>(p, w, G, Wu, kk, s));
+  // X rows, X^T Y, beta = W' X^T Y
+  LV_CUDA(launch_scatter_rows<T>(static_cast<T*>(p->Xd), p->ldX, p->rows_d, kr, n, U, fs, s));
+  View& xty = p->views[kOlsXtY];
+  LV_CUDA(launch_xty_update<T>(static_cast<T*>(xty.ptr), xty.ld, static_cast<T*>(p->XtYc), fs, U,
+                               n, pp, kr, static_cast<const T*>(p->Yr), s));
+  p->all_launches += 2;
+  LV_TRY(run_products_update<T>(p, w, pp, static_cast<const T*>(p->XtYc), nullptr, nullptr,
+                                nullptr, s));
+  View& beta = p->views[kOlsBeta];
+  LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, pp,
+                                 static_cast<T*>(p->betac), fs, s));
+  LV_CUDA(launch_cm_to_rm<T>(static_cast<const T*>(p->betac), fs, static_cast<T*>(beta.ptr),
+                             beta.ld, n, pp, s));
+  p->all_launches += 2;
+  return LINVIEW_OK;
+}
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -654,6 +866,7 @@ linview_status linview_create_program(const linview_program_desc* desc, const vo
       case LINVIEW_POWER:
       case LINVIEW_POWER_SUM: st = powers_create(p, inputs, lds, inputs_on_device, s); break;
       case LINVIEW_ITERATION: st = iter_create(p, inputs, lds, inputs_on_device, s); break;
+      case LINVIEW_OLS: st = ols_create(p, inputs, lds, inputs_on_device, s); break;
       default: st = fail(LINVIEW_EUNSUPPORTED, "program kind %d not built", desc->kind);
     }
   }
@@ -740,6 +953,7 @@ linview_status linview_reeval(linview_program* p, void* stream) {
     case LINVIEW_POWER:
     case LINVIEW_POWER_SUM: return powers_reeval(p, s);
     case LINVIEW_ITERATION: return iter_reeval(p, s);
+    case LINVIEW_OLS: return p->elem == 4 ? ols_reeval_t<float>(p, s) : ols_reeval_t<double>(p, s);
     default: return fail(LINVIEW_EUNSUPPORTED, "reeval for kind %d", p->d.kind);
   }
 }
@@ -860,9 +1074,26 @@ linview_status linview_apply_row_delta(linview_program* p, int input_id, int64_t
 linview_status linview_apply_row_block(linview_program* p, int64_t kr, const int64_t* rows,
                                        const void* new_rows, int64_t ld, int on_device,
                                        void* stream) {
-  (void)kr; (void)rows; (void)new_rows; (void)ld; (void)on_device; (void)stream;
-  if (!p) return fail(LINVIEW_EINVAL, "null program");
-  return fail(LINVIEW_EUNSUPPORTED, "OLS is not built in this library version");
+  if (!p || !rows || !new_rows) return fail(LINVIEW_EINVAL, "null argument");
+  if (p->d.kind != LINVIEW_OLS) return fail(LINVIEW_EINVAL, "not an OLS program");
+  if (kr < 1 || kr > p->d.k)
+    return fail(LINVIEW_ESHAPE, "row block of %lld rows (program takes 1..%d)", (long long)kr,
+                p->d.k);
+  const int64_t n = p->d.n, m = p->d.m;
+  if (ld < n) return fail(LINVIEW_ESHAPE, "ld < n");
+  for (int64_t i = 0; i < kr; ++i) {
+    if (rows[i] < 0 || rows[i] >= m) return fail(LINVIEW_EINVAL, "row index out of range");
+    for (int64_t j = 0; j < i; ++j)
+      if (rows[j] == rows[i]) return fail(LINVIEW_EINVAL, "row indices must be distinct");
+  }
+  LV_CUDA(cudaSetDevice(p->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LV_CUDA(cudaMemcpyAsync(p->rows_d, rows, sizeof(int64_t) * kr, cudaMemcpyHostToDevice, s));
+  if (p->elem == 4)
+    LV_TRY(ols_replace_t<float>(p, (int)kr, new_rows, ld, on_device, s));
+  else
+    LV_TRY(ols_replace_t<double>(p, (int)kr, new_rows, ld, on_device, s));
+  return after_update(p, s);
 }
 
 linview_status linview_sync(linview_program* p, void* stream) {

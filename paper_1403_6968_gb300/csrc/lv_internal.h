@@ -115,4 +115,29 @@ template <typename T>
 cudaError_t launch_scale_copy(T* y, int64_t ldy, const T* x, int64_t ldx, T alpha, int rows,
                               int cols, cudaStream_t s);  // y = alpha x
 
+// OLS pieces (lv_ols.cu).
+template <typename T>
+cudaError_t launch_gather_rows(const T* X, int64_t ldx, const int64_t* rows, int k, int n, T* dst,
+                               int64_t ts, int64_t js, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scatter_rows(T* X, int64_t ldx, const int64_t* rows, int k, int n,
+                                const T* src, int64_t ts, cudaStream_t s);
+cudaError_t launch_core_inverse(const double* S, int kk, int kpos, double* Minv, unsigned* status,
+                                cudaStream_t s);
+template <typename T>
+cudaError_t launch_wu(const T* G, int64_t fs, int n, int kk, const double* Minv, T* Wu,
+                      cudaStream_t s);
+template <typename T>
+cudaError_t launch_xty_update(T* xty, int64_t ld, T* xtyc, int64_t fs, const T* U, int n, int p,
+                              int k, const T* Yr, cudaStream_t s);
+template <typename T>
+cudaError_t launch_to_double(const T* src, int64_t lds, double* dst, int64_t ldd, int rows,
+                             int cols, cudaStream_t s);
+template <typename T>
+cudaError_t launch_sym_lower_to_full(const double* Lcm, int64_t ldl, int n, T* dst, int64_t ldd,
+                                     double* full, int64_t ldf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_from_double(const double* src, int64_t lds, T* dst, int64_t ldd, int rows,
+                               int cols, T* cm, int64_t cfs, cudaStream_t s);
+
 }  // namespace lv

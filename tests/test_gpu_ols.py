@@ -1,0 +1,108 @@
+"""GPU parity: OLS with W = (X^T X)^{-1} maintained by block Woodbury under
+row-block replacements, vs the FP64 oracle (Section 4.1, Example 3.3).
+
+Tolerances: FP64 programs 1e-9 (kappa(X^T X) ~ 1e4 times FP64 rounding);
+FP32 programs 1e-4 relative Frobenius per update (the reduced-precision bound)."""
+import numpy as np
+import pytest
+
+import linview_inputs as li
+from oracle import ols as oo
+from oracle.metrics import rel_frob
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _prog(*a, **kw):
+    from paper_1403_6968_gb300 import Program
+    return Program(*a, **kw)
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("m,n,p,k", [(2000, 200, 4, 1), (3000, 257, 3, 4), (4096, 512, 16, 16),
+                                     (100, 30, 1, 5)])
+def test_row_block_updates(prec, m, n, p, k):
+    dt = np.float64 if prec == "f64" else np.float32
+    x, y, _ = li.ols_inputs(m, n, p, seed=m + n, dtype=dt)
+    prog = _prog("ols", [_dev(x), _dev(y)], k=k, precision=prec)
+    ref = oo.IncrementalOLS(x.astype(np.float64), y.astype(np.float64))
+    tol = 1e-9 if prec == "f64" else 1e-4
+    prog.sync()
+    assert rel_frob(prog.read_view_host(0), ref.w) <= tol
+    assert rel_frob(prog.read_view_host(1), ref.beta) <= tol
+    for rows, new in li.ols_row_replacements(m, n, k, 5, seed=m, dtype=dt):
+        prog.apply_row_block(rows, _dev(new))
+        ref.replace_rows(rows, new.astype(np.float64))
+        prog.sync()
+        fresh = oo.reeval(ref.x, ref.y)
+        assert rel_frob(prog.read_view_host(0), fresh["W"]) <= tol
+        assert rel_frob(prog.read_view_host(1), fresh["beta"]) <= tol
+        assert rel_frob(prog.read_view_host(2), fresh["XtY"]) <= (1e-12 if prec == "f64" else 1e-6)
+    assert np.array_equal(prog.read_view_host(3), ref.x.astype(dt))
+
+
+def test_host_rows_and_errors():
+    from paper_1403_6968_gb300 import LinviewError
+    m, n, p, k = 500, 40, 2, 3
+    x, y, _ = li.ols_inputs(m, n, p, seed=1)
+    prog = _prog("ols", [x, y], k=k, precision="f64")
+    ref = oo.IncrementalOLS(x, y)
+    (rows, new), = li.ols_row_replacements(m, n, k, 1, seed=2)
+    prog.apply_row_block(rows, new)          # host new rows
+    ref.replace_rows(rows, new)
+    prog.sync()
+    assert rel_frob(prog.read_view_host(0), ref.w) <= 1e-10
+    for bad_rows in ([0, 0, 1], [m, 1, 2], [-1, 1, 2]):
+        with pytest.raises(LinviewError) as e:
+            prog.apply_row_block(bad_rows, new)
+        assert e.value.name == "EINVAL"
+    with pytest.raises(LinviewError) as e:
+        prog.apply_row_block(list(range(k + 1)), np.zeros((k + 1, n)))
+    assert e.value.name == "ESHAPE"
+    assert rel_frob(prog.read_view_host(0), ref.w) <= 1e-10
+
+
+def test_reeval_resets_to_fresh_inverse():
+    m, n, p, k = 3000, 256, 4, 4
+    x, y, _ = li.ols_inputs(m, n, p, seed=3, dtype=np.float32)
+    prog = _prog("ols", [_dev(x), _dev(y)], k=k)
+    xs = x.astype(np.float64)
+    for rows, new in li.ols_row_replacements(m, n, k, 4, seed=4, dtype=np.float32):
+        prog.apply_row_block(rows, _dev(new))
+        xs[rows] = new
+    prog.reeval()
+    prog.sync()
+    fresh = oo.reeval(xs, y.astype(np.float64))
+    assert rel_frob(prog.read_view_host(0), fresh["W"]) <= 1e-5
+    assert rel_frob(prog.read_view_host(1), fresh["beta"]) <= 1e-5
+
+
+@pytest.mark.parametrize("k", [1, 16])
+def test_full_size_precision_form(k):
+    """X 65536 x 4096 (10% columns x1e-2), Y 65536 x 16, FP32 views, FP64 core;
+    three row-block updates, W (sampled rows) and beta vs the FP64 oracle."""
+    m, n, p = 65536, 4096, 16
+    x, y, _ = li.ols_inputs(m, n, p, seed=0, dtype=np.float32)
+    prog = _prog("ols", [_dev(x), _dev(y)], k=k)
+    ref = oo.IncrementalOLS(x.astype(np.float64), y.astype(np.float64))
+    rows_s = [0, 1000, 2047, n - 1]
+    for rows, new in li.ols_row_replacements(m, n, k, 3, seed=k, dtype=np.float32):
+        prog.apply_row_block(rows, _dev(new))
+        ref.replace_rows(rows, new.astype(np.float64))
+        prog.sync()
+        w = prog.read_view_rows(0, 0, n)[rows_s]
+        assert rel_frob(w, ref.w[rows_s]) <= 1e-4
+        assert rel_frob(prog.read_view_host(1), ref.beta) <= 1e-4
