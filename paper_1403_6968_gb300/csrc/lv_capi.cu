@@ -85,7 +85,7 @@ struct linview_program {
   // factor arenas
   void* Uar = nullptr;
   void* Var = nullptr;
-  void* War = nullptr;
+  void* Wsum = nullptr;  // explicit V_h K_h^T for sums programs with wide factors
   int64_t fs = 0;
   int Rcap = 0;
   // partial sums of the view passes
@@ -252,7 +252,7 @@ static constexpr int max_update_r() {
 template <typename T>
 static linview_status run_fused(linview_program* p, const View& v, int mode, int r, const T* Xf,
                                 const T* Yf, const T* Uu, const T* Wu, void* Xpart, void* Ypart,
-                                cudaStream_t s) {
+                                cudaStream_t s, double* Cpart = nullptr) {
   const PassGeom g = fused_geom(sizeof(T), (int)v.rows, p->sms);
   PassParams pp{};
   pp.P = v.ptr;
@@ -273,6 +273,7 @@ static linview_status run_fused(linview_program* p, const View& v, int mode, int
   pp.gR = g.gR;
   pp.rows_per_cta = g.rows_per_cta;
   pp.status = p->status;
+  pp.Cpart = Cpart;
   const double nn = (double)v.rows * (double)v.rows * sizeof(T);
   ProfScope ps(p, s, (mode & 4) ? 2.0 * nn : nn, 1);
   LV_CUDA((launch_fused<T>(pp, v.tmap, r, mode, s)));
@@ -281,7 +282,7 @@ static linview_status run_fused(linview_program* p, const View& v, int mode, int
 
 template <typename T>
 static linview_status run_update(linview_program* p, const View& v, const T* Uu, const T* Wu,
-                                 int r, cudaStream_t s) {
+                                 int r, cudaStream_t s, int suffix_rin = 0) {
   constexpr int MU = max_update_r<T>();
   for (int c0 = 0; c0 < r; c0 += MU) {
     const int w = (r - c0 < MU) ? (r - c0) : MU;
@@ -298,6 +299,7 @@ static linview_status run_update(linview_program* p, const View& v, const T* Uu,
     pp.gR = g.gR;
     pp.rows_per_cta = g.rows_per_cta;
     pp.status = p->status;
+    pp.suffix_rin = suffix_rin;  // host guarantees a single chunk when set
     ProfScope ps(p, s, 2.0 * (double)v.rows * (double)v.rows * sizeof(T), 2);
     LV_CUDA((launch_update<T>(pp, v.tmap, w, s)));
   }
@@ -309,11 +311,13 @@ static linview_status run_update(linview_program* p, const View& v, const T* Uu,
 // (if Uu) the in-place update.  Fused in one pass when r <= kMaxFusedR.
 template <typename T>
 static linview_status run_products_update(linview_program* p, const View& v, int r, const T* Xf,
-                                          const T* Yf, const T* Uu, const T* Wu, cudaStream_t s) {
+                                          const T* Yf, const T* Uu, const T* Wu, cudaStream_t s,
+                                          double* Cpart = nullptr) {
   const bool want_y = (Yf != nullptr);
   if (r <= kMaxFusedR) {
     const int mode = kModeX | (want_y ? 2 : 0) | (Uu ? 4 : 0);  // XYU, XY, XU or X
-    return run_fused<T>(p, v, mode, r, Xf, Yf, Uu, Wu, p->Xpart, p->Ypart, s);
+    return run_fused<T>(p, v, mode, r, Xf, Yf, Uu, Wu, p->Xpart, p->Ypart, s,
+                        mode == kModeXYU ? Cpart : nullptr);
   }
   for (int c0 = 0; c0 < r; c0 += kMaxFusedR) {
     const int w = (r - c0 < kMaxFusedR) ? (r - c0) : kMaxFusedR;
@@ -420,6 +424,12 @@ static linview_status powers_create(linview_program* p, const void* const* input
   if ((int64_t)p->d.r_max * k > 128)
     return fail(LINVIEW_EUNSUPPORTED, "r_max*k=%lld exceeds 128 (factor cores are at most 64x64)",
                 (long long)p->d.r_max * k);
+  // the sums views apply their block-triangular core inside one update pass
+  // when the whole factor fits one pass; wider factors get an explicit
+  // suffix-sum factor (see sums_update)
+  const int64_t mu = p->elem == 4 ? 64 : 32;
+  const bool wide_sums =
+      p->d.kind == LINVIEW_POWER_SUM && ((int64_t)p->d.r_max * k > mu || p->d.r_max > 8);
   if (lds[0] < n) return fail(LINVIEW_ESHAPE, "ld of A (%lld) < n", (long long)lds[0]);
   for (int l = 0; l <= p->L; ++l) LV_TRY(add_square_view(p, n));
   if (p->d.kind == LINVIEW_POWER_SUM)
@@ -430,7 +440,7 @@ static linview_status powers_create(linview_program* p, const void* const* input
   const size_t fbytes = (size_t)p->fs * p->Rcap * p->elem;
   LV_TRY(dalloc(p, fbytes, &p->Uar));
   LV_TRY(dalloc(p, fbytes, &p->Var));
-  if (p->d.kind == LINVIEW_POWER_SUM) LV_TRY(dalloc(p, fbytes, &p->War));
+  if (wide_sums) LV_TRY(dalloc(p, fbytes, &p->Wsum));
   const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
   const int half = (p->Rcap / 2 > 0) ? p->Rcap / 2 : 1;
   p->part_cs = p->fs;
@@ -441,30 +451,45 @@ static linview_status powers_create(linview_program* p, const void* const* input
   return powers_reeval(p, s);
 }
 
+// S'_h += U_h (V_h K_h^T)^T, K_h block upper triangular of identities: the
+// update pass takes the suffix block sums of V_h itself when the factor fits
+// one pass, else they are formed first (one thread per row).
+template <typename T>
+static linview_status sums_update(linview_program* p, View& sv, const T* U, const T* Vh, int rh,
+                                  int r, cudaStream_t s) {
+  if (!p->Wsum) return run_update<T>(p, sv, U, Vh, rh, s, r);
+  {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_suffix_sums<T>(Vh, static_cast<T*>(p->Wsum), p->fs, (int)p->d.n, rh, r, s));
+  }
+  return run_update<T>(p, sv, U, static_cast<const T*>(p->Wsum), rh, s, 0);
+}
+
 template <typename T>
 static linview_status powers_propagate(linview_program* p, int r, cudaStream_t s) {
   const int n = (int)p->d.n;
   const int64_t fs = p->fs;
   T* U = static_cast<T*>(p->Uar);
   T* V = static_cast<T*>(p->Var);
-  T* W = static_cast<T*>(p->War);
   const bool sums = has_sums(p);
   const PassGeom g = fused_geom(sizeof(T), n, p->sms);
   for (int l = 0; l < p->L; ++l) {
     const int rh = r << l;
     T* Vh = V + (int64_t)(p->Rcap - rh) * fs;
-    {
+    // Appendix A level pass: P_h U_h, P_h^T V_h from the old view, P_h += U_h V_h^T;
+    // for r_h <= kMaxFusedR the same pass also yields the partials of C_h = V_h^T U_h
+    const bool fused = rh <= kMaxFusedR;
+    if (!fused) {
       ProfScope ps(p, s, 0.0);
-      (void)ps;
       LV_CUDA((launch_gram<T>(Vh, U, fs, n, rh, p->Cpart, p->ticket, p->C, p->status, s)));
     }
-    // Appendix A level pass: P_h U_h, P_h^T V_h from the old view; P_h += U_h V_h^T
-    LV_TRY(run_products_update<T>(p, pview(p, l), rh, U, Vh, U, Vh, s));
-    if (sums && l >= 1) LV_TRY(run_update<T>(p, sview(p, l), U, W, rh, s));
+    LV_TRY(run_products_update<T>(p, pview(p, l), rh, U, Vh, U, Vh, s,
+                                  fused ? p->Cpart : nullptr));
+    // sums: S'_h += U_h (V_h K_h^T)^T, the suffix block sums taken in the pass
+    if (sums && l >= 1) LV_TRY(sums_update<T>(p, sview(p, l), U, Vh, rh, r, s));
     AssembleParams a{};
     a.n = n;
     a.r_h = rh;
-    a.r_in = r;
     a.fs = fs;
     a.Xpart = p->Xpart;
     a.gC = g.gC;
@@ -473,18 +498,18 @@ static linview_status powers_propagate(linview_program* p, int r, cudaStream_t s
     a.gR = g.gR;
     a.yp_q = p->yp_q;
     a.part_cs = p->part_cs;
-    a.C = p->C;
+    a.C = fused ? p->Cpart : p->C;
+    a.nC = fused ? g.gR : 1;
     a.Uh = U;
     a.Unew = U + (int64_t)rh * fs;
     a.Ynew = V + (int64_t)(p->Rcap - 2 * rh) * fs;
-    a.V2h = a.Ynew;
-    a.W2h = sums ? (void*)W : nullptr;
     ProfScope ps(p, s, 0.0);
     LV_CUDA(launch_assemble<T>(a, s));
   }
   const int rk = r << p->L;
-  LV_TRY(run_update<T>(p, pview(p, p->L), U, V + (int64_t)(p->Rcap - rk) * fs, rk, s));
-  if (sums) LV_TRY(run_update<T>(p, sview(p, p->L), U, W, rk, s));
+  T* Vk = V + (int64_t)(p->Rcap - rk) * fs;
+  LV_TRY(run_update<T>(p, pview(p, p->L), U, Vk, rk, s));
+  if (sums) LV_TRY(sums_update<T>(p, sview(p, p->L), U, Vk, rk, r, s));
   return LINVIEW_OK;
 }
 
@@ -580,13 +605,13 @@ static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) 
     AssembleParams as{};
     as.n = n;
     as.r_h = r;
-    as.r_in = r;
     as.fs = fs;
     as.Xpart = p->Xpart;
     as.gC = g.gC;
     as.xp_s = p->xp_s;
     as.part_cs = p->part_cs;
     as.C = p->C;
+    as.nC = 1;
     as.Uh = K;
     as.Unew = K + (int64_t)r * fs;
     {
@@ -858,7 +883,10 @@ linview_status linview_create_program(const linview_program_desc* desc, const vo
   }
   if (st == LINVIEW_OK) {
     void* tmp = nullptr;
-    st = dalloc(p, sizeof(double) * 64 * 64 * gram_grid((int)desc->n), &tmp);
+    const int sms_guess = 2 * 256;  // >= 2 CTAs per SM for any current part
+    const size_t cp = (size_t)64 * 64 * gram_grid((int)desc->n);
+    const size_t cf = (size_t)64 * sms_guess;
+    st = dalloc(p, sizeof(double) * (cp > cf ? cp : cf), &tmp);
     p->Cpart = static_cast<double*>(tmp);
   }
   if (st == LINVIEW_OK) {
@@ -1027,19 +1055,13 @@ linview_status linview_apply_delta(linview_program* p, int input_id, int64_t ran
                                    p->fs, (int)n, r, s));
     LV_CUDA(launch_rm_to_cm<float>(static_cast<const float*>(v), ldv,
                                    static_cast<float*>(v_dst(p, r)), p->fs, (int)n, r, s));
-    if (has_sums(p))
-      LV_CUDA(launch_suffix_sums<float>(static_cast<float*>(v_dst(p, r)),
-                                        static_cast<float*>(p->War), p->fs, (int)n, r, r, s));
   } else {
     LV_CUDA(launch_rm_to_cm<double>(static_cast<const double*>(u), ldu,
                                     static_cast<double*>(u_dst(p)), p->fs, (int)n, r, s));
     LV_CUDA(launch_rm_to_cm<double>(static_cast<const double*>(v), ldv,
                                     static_cast<double*>(v_dst(p, r)), p->fs, (int)n, r, s));
-    if (has_sums(p))
-      LV_CUDA(launch_suffix_sums<double>(static_cast<double*>(v_dst(p, r)),
-                                         static_cast<double*>(p->War), p->fs, (int)n, r, r, s));
   }
-  p->all_launches += has_sums(p) ? 3 : 2;
+  p->all_launches += 2;
   LV_TRY(propagate(p, r, s));
   return after_update(p, s);
 }
@@ -1057,16 +1079,10 @@ linview_status linview_apply_row_delta(linview_program* p, int input_id, int64_t
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
   if (p->elem == 4) {
     LV_CUDA(launch_unit_column<float>(static_cast<float*>(u_dst(p)), (int)n, (int)row, s));
-    if (has_sums(p))
-      LV_CUDA(launch_suffix_sums<float>(static_cast<float*>(v_dst(p, 1)),
-                                        static_cast<float*>(p->War), p->fs, (int)n, 1, 1, s));
   } else {
     LV_CUDA(launch_unit_column<double>(static_cast<double*>(u_dst(p)), (int)n, (int)row, s));
-    if (has_sums(p))
-      LV_CUDA(launch_suffix_sums<double>(static_cast<double*>(v_dst(p, 1)),
-                                         static_cast<double*>(p->War), p->fs, (int)n, 1, 1, s));
   }
-  p->all_launches += has_sums(p) ? 2 : 1;
+  p->all_launches += 1;
   LV_TRY(propagate(p, 1, s));
   return after_update(p, s);
 }

@@ -95,55 +95,44 @@ cudaError_t launch_gram(const T* V, const T* U, int64_t fs, int n, int r, double
   return cudaGetLastError();
 }
 
-// One thread per row j:  X'(j,:) = sum_s Xpart[s](j,:) + U_h(j,:) C_h,
-// Y(j,:) = sum_q Ypart[q](j,:), then (optionally) the suffix block sums of
-// V_{2h}(j,:) for the sums views.
+// One thread per (row j, factor column c):
+//   X'(j,c) = sum_s Xpart[s](j,c) + sum_c2 U_h(j,c2) C_h(c2,c),
+//   Y(j,c)  = sum_q Ypart[q](j,c),
+// with C_h = sum of the nC partial blocks (fixed order, FP64) staged per CTA.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) assemble_kernel(const AssembleParams a) {
   extern __shared__ double Cs[];  // r_h x r_h
   const int rh = a.r_h;
-  for (int e = threadIdx.x; e < rh * rh; e += blockDim.x) Cs[e] = a.C[e];
+  const int ne = rh * rh;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    double sum = 0.0;
+    for (int b = 0; b < a.nC; ++b) sum += a.C[(int64_t)b * ne + e];
+    Cs[e] = sum;
+  }
   __syncthreads();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.n) return;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)a.n * rh) return;
+  const int c = (int)(idx / a.n);
+  const int j = (int)(idx % a.n);
   const T* Xp = static_cast<const T*>(a.Xpart);
   const T* Yp = static_cast<const T*>(a.Ypart);
   const T* Uh = static_cast<const T*>(a.Uh);
-  T* Un = static_cast<T*>(a.Unew);
-  T* Yn = static_cast<T*>(a.Ynew);
-  for (int c = 0; c < rh; ++c) {
-    double x = 0.0;
-    for (int sidx = 0; sidx < a.gC; ++sidx)
-      x += (double)Xp[(int64_t)sidx * a.xp_s + (int64_t)c * a.part_cs + j];
-    for (int c2 = 0; c2 < rh; ++c2) x = fma((double)Uh[(int64_t)c2 * a.fs + j], Cs[c2 * rh + c], x);
-    Un[(int64_t)c * a.fs + j] = (T)x;
-    if (Yp) {
-      double y = 0.0;
-      for (int q = 0; q < a.gR; ++q)
-        y += (double)Yp[(int64_t)q * a.yp_q + (int64_t)c * a.part_cs + j];
-      Yn[(int64_t)c * a.fs + j] = (T)y;
-    }
-  }
-  if (a.W2h) {
-    // W_{2h} block b = sum of V_{2h} blocks b..end (blocks of r_in columns)
-    const T* V2 = static_cast<const T*>(a.V2h);
-    T* W2 = static_cast<T*>(a.W2h);
-    const int width = 2 * rh;
-    const int nblk = width / a.r_in;
-    for (int c = 0; c < a.r_in; ++c) {
-      double acc = 0.0;
-      for (int b = nblk - 1; b >= 0; --b) {
-        const int col = b * a.r_in + c;
-        acc += (double)V2[(int64_t)col * a.fs + j];
-        W2[(int64_t)col * a.fs + j] = (T)acc;
-      }
-    }
+  double x = 0.0;
+  for (int sidx = 0; sidx < a.gC; ++sidx)
+    x += (double)Xp[(int64_t)sidx * a.xp_s + (int64_t)c * a.part_cs + j];
+  for (int c2 = 0; c2 < rh; ++c2) x = fma((double)Uh[(int64_t)c2 * a.fs + j], Cs[c2 * rh + c], x);
+  static_cast<T*>(a.Unew)[(int64_t)c * a.fs + j] = (T)x;
+  if (Yp) {
+    double y = 0.0;
+    for (int q = 0; q < a.gR; ++q) y += (double)Yp[(int64_t)q * a.yp_q + (int64_t)c * a.part_cs + j];
+    static_cast<T*>(a.Ynew)[(int64_t)c * a.fs + j] = (T)y;
   }
 }
 
 template <typename T>
 cudaError_t launch_assemble(const AssembleParams& a, cudaStream_t s) {
-  const int grid = (a.n + kThreads - 1) / kThreads;
+  const int64_t tot = (int64_t)a.n * a.r_h;
+  const unsigned grid = (unsigned)((tot + kThreads - 1) / kThreads);
   const size_t smem = sizeof(double) * (size_t)a.r_h * a.r_h;
   assemble_kernel<T><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();

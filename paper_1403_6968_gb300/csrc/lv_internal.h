@@ -39,6 +39,8 @@ struct PassParams {
   int gC, gR;         // column strips x row ranges; grid = gC * gR
   int rows_per_cta;   // multiple of kBatch
   unsigned* status;   // device status word
+  double* Cpart;      // fused XYU pass: per-row-range V^T U partials [gR][r*r] (or null)
+  int suffix_rin;     // update pass: >0 applies block suffix sums (block width) to Wu
 };
 
 // Host: grid geometry for a pass over an n x n view.
@@ -70,17 +72,16 @@ cudaError_t launch_gram(const T* V, const T* U, int64_t fs, int n, int r, double
 int gram_grid(int n);
 
 struct AssembleParams {
-  int n, r_h, r_in;       // rows, current factor width, input rank (block width)
+  int n, r_h;             // rows, current factor width
   int64_t fs;             // arena column stride
   const void* Xpart; int gC; int64_t xp_s;   // row-sum partials of P_h U_h
-  const void* Ypart; int gR; int64_t yp_q;   // column-sum partials of P_h^T V_h
+  const void* Ypart; int gR; int64_t yp_q;   // column-sum partials of P_h^T V_h (or null)
   int64_t part_cs;
-  const double* C;        // r_h x r_h = V_h^T U_h
+  const double* C;        // r_h x r_h = V_h^T U_h, summed over nC partial blocks
+  int nC;                 // number of [r_h*r_h] partial blocks in C (1 = already reduced)
   const void* Uh;         // U_h (n x r_h)
   void* Unew;             // destination of X_h + U_h C_h (n x r_h), = U arena + r_h columns
   void* Ynew;             // destination of Y_h (n x r_h), = V arena left of V_h
-  const void* V2h;        // V_{2h} (n x 2 r_h), for the suffix sums
-  void* W2h;              // Ŵ_{2h} (n x 2 r_h) or null
 };
 template <typename T>
 cudaError_t launch_assemble(const AssembleParams& a, cudaStream_t s);
