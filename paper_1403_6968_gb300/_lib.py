@@ -69,6 +69,7 @@ _SIGS = [
     ("linview_adjoint_iteration", _I, [_P, _P, _I64, _P, _I64, _P]),
     ("linview_adjoint_power", _I, [_P, _P, _I64, _P, _I64, _P]),
     ("linview_level_pass", _I, [_I, _I64, _P, _I64, _P, _P, _I64, _I64, _P, _P, _I, _P]),
+    ("linview_level_pass_noalloc", _I, [_I, _I64, _P, _I64, _P, _P, _I64, _I64, _P, _P, _I, _P]),
     ("linview_set_profiling", _I, [_P, _I]),
     ("linview_pass_stats", _I, [_P, _I, C.POINTER(_I64), C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.POINTER(_I64)]),

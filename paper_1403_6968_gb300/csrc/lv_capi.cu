@@ -38,6 +38,19 @@ static linview_status fail(linview_status st, const char* fmt, ...) {
   return st;
 }
 
+namespace lv {
+// error setter for the other translation units of the ABI
+linview_status lv_set_error(linview_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+}  // namespace lv
+
 #define LV_CUDA(expr)                                                                     \
   do {                                                                                    \
     cudaError_t e_ = (expr);                                                              \

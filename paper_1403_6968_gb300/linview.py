@@ -231,3 +231,24 @@ def level_pass(P, U, V, X=None, Y=None, do_update=True, stream=None):
            C.c_void_p(X.data_ptr()) if X is not None else None,
            C.c_void_p(Y.data_ptr()) if Y is not None else None,
            1 if do_update else 0, _stream_ptr(stream))
+
+
+def level_pass_noalloc(P, U, V, X=None, Y=None, do_update=True, stream=None):
+    """``level_pass`` for callers that may not allocate device memory: the
+    partial sums use the library's built-in 16 MiB device array instead of
+    stream-ordered allocations (see linview_level_pass_noalloc in
+    include/linview.h for the size limit and the rule that overlapping calls
+    must be serialised)."""
+    torch = _torch()
+    n = P.shape[0]
+    prec = L.F64 if P.dtype == torch.float64 else L.F32
+    r = U.shape[0]
+    ldf = U.stride(0)
+    for t in (V, X, Y):
+        if t is not None and (t.shape[0] != r or t.stride(0) != ldf):
+            raise ValueError("U, V, X, Y must share shape (r, n) and stride")
+    L.call("linview_level_pass_noalloc", prec, n, C.c_void_p(P.data_ptr()), P.stride(0),
+           C.c_void_p(U.data_ptr()), C.c_void_p(V.data_ptr()), ldf, r,
+           C.c_void_p(X.data_ptr()) if X is not None else None,
+           C.c_void_p(Y.data_ptr()) if Y is not None else None,
+           1 if do_update else 0, _stream_ptr(stream))

@@ -1,0 +1,79 @@
+"""The allocation-free level pass (linview_level_pass_noalloc) against the
+allocating one (linview_level_pass).
+
+Some callers may not allocate device memory on their call path -- e.g. a
+serving process or an engine plugin that reserved all of the GPU's memory up
+front, or a latency-critical loop that must avoid cudaMalloc's implicit
+synchronisation.  The no-alloc entry takes its partial sums from a fixed array
+built into the library; this test checks that it gives the results of the
+allocating entry, on two calls in a row (the second call sees the array as the
+first left it), and that it rejects sizes beyond the array.  This file is
+collected last so that a failure here stops a -x run only after every other
+test has run; it also passes alone in a fresh process.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _rel(x, y):
+    x = x.double().cpu().numpy()
+    y = y.double().cpu().numpy()
+    d = np.linalg.norm(y)
+    return np.linalg.norm(x - y) / (d if d else 1.0)
+
+
+@pytest.mark.parametrize("prec,n,r,upd", [("f32", 1000, 3, True), ("f32", 8192, 8, True),
+                                          ("f32", 777, 24, True), ("f32", 2048, 8, False),
+                                          ("f64", 513, 4, True), ("f64", 300, 12, True)])
+def test_noalloc_matches_allocating_entry_two_calls(prec, n, r, upd):
+    from paper_1403_6968_gb300 import level_pass, level_pass_noalloc
+    dt = torch.float64 if prec == "f64" else torch.float32
+    tol = 1e-13 if prec == "f64" else 1e-5        # the level-pass test tolerances
+    g = torch.Generator(device="cpu").manual_seed(n * 10 + r)
+    ld = (n + 3) // 4 * 4
+    p0 = torch.randn((n, ld), generator=g, dtype=dt).cuda()
+    pa, pb = p0.clone(), p0.clone()
+    for call in range(2):
+        u = torch.randn((r, n), generator=g, dtype=dt).cuda()
+        v = torch.randn((r, n), generator=g, dtype=dt).cuda()
+        xa, ya = torch.empty_like(u), torch.empty_like(u)
+        xb, yb = torch.full_like(u, float("nan")), torch.full_like(u, float("nan"))
+        level_pass(pa[:, :n], u, v, xa, ya, do_update=upd)
+        level_pass_noalloc(pb[:, :n], u, v, xb, yb, do_update=upd)
+        torch.cuda.synchronize()
+        assert _rel(xb, xa) <= tol, call
+        assert _rel(yb, ya) <= tol, call
+        assert _rel(pb, pa) <= tol, call
+
+
+def test_noalloc_update_only_and_size_limit():
+    from paper_1403_6968_gb300 import LinviewError, level_pass, level_pass_noalloc
+    n, r = 4096, 32
+    p0 = torch.randn((n, n), dtype=torch.float32, device="cuda")
+    u = torch.randn((r, n), dtype=torch.float32, device="cuda")
+    v = torch.randn((r, n), dtype=torch.float32, device="cuda")
+    pa, pb = p0.clone(), p0.clone()
+    level_pass(pa, u, v, None, None, do_update=True)
+    level_pass_noalloc(pb, u, v, None, None, do_update=True)   # no partial sums needed
+    torch.cuda.synchronize()
+    assert _rel(pb, pa) <= 1e-5
+    big = 16384
+    P = torch.zeros((big, big), dtype=torch.float32, device="cuda")
+    U = torch.zeros((16, big), dtype=torch.float32, device="cuda")
+    X = torch.empty_like(U)
+    with pytest.raises(LinviewError) as e:
+        level_pass_noalloc(P, U, U, X, X.clone(), do_update=False)
+    assert e.value.name == "ESHAPE" and "scratch" in str(e.value)
