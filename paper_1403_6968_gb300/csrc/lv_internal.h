@@ -10,7 +10,8 @@ namespace lv {
 
 constexpr int kThreads = 256;   // threads per pass CTA
 constexpr int kBatch = 8;       // rows per pipeline stage = TMA box height = warps per CTA
-constexpr int kStages = 4;      // TMA ring depth
+constexpr int kStages = 4;      // TMA ring depth (generic passes)
+constexpr int kStagesWs = 6;    // TMA ring depth of the decoupled-ring FP32 passes
 constexpr int kBoxBytes = 1024; // bytes per TMA box row (256 floats / 128 doubles)
 constexpr int kMaxFusedR = 8;   // widest factor block of the fused products pass
 constexpr int kMaxUpdateR = 64; // widest rank of the update-only pass (float)

@@ -294,269 +294,6 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
-// ---------------------------------------------------------------------------
-// FP32 fused pass with packed FP32x2 FMAs (Blackwell FFMA2, __ffma2_rn).
-// Same schedule as fused_pass_kernel; every lane of a packed FMA performs the
-// same multiply-add, in the same order, as the scalar kernel, so results are
-// bitwise identical while the FMA instruction count halves:
-//   Y:  yacc[k][c..c+1]  += p[k] * V_row[c..c+1]           (pairs over c)
-//   X:  x[c..c+1]        += p[k] * U_col[k][c..c+1]        (pairs over c)
-//   U:  p'[k..k+1]       += u_row[c] * W_col[k..k+1][c]    (pairs over k)
-// The update-left rows are staged in shared memory already duplicated,
-// (u, u), so the third form needs no register shuffling.
-// ---------------------------------------------------------------------------
-template <int R, int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
-    fused_pass_f2_kernel(const __grid_constant__ CUtensorMap tmap, const PassParams p) {
-  using T = float;
-  constexpr int COLS = 4;
-  constexpr int STRIP = 128 * COLS;
-  constexpr int BOXC = box_cols<T>();
-  constexpr int NB = STRIP / BOXC;
-  constexpr int STAGE_ELEMS = kBatch * STRIP;
-  constexpr int R2 = R / 2;
-  constexpr bool DO_X = (MODE & 1) != 0;
-  constexpr bool DO_Y = (MODE & 2) != 0;
-  constexpr bool DO_U = (MODE & 4) != 0;
-  static_assert(R >= 2 && R % 2 == 0 && 32 % R == 0, "packed pass takes R in {2,4,8,16,32}");
-  constexpr int XS = 128 + 32 / R;
-
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  T* stages = reinterpret_cast<T*>(smem_raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * kStages * STAGE_ELEMS);
-  float2* Us2 = reinterpret_cast<float2*>(full + kStages);  // [kBatch][R] (u, u)
-  T* Vs = reinterpret_cast<T*>(Us2 + kBatch * R);            // [kBatch][R]
-  T* Xbuf = Vs + kBatch * R;                                  // [kBatch][R][XS]
-  double* Csh = reinterpret_cast<double*>(Xbuf + kBatch * R * XS);
-
-  const int tid = threadIdx.x;
-  const int rg = tid >> 7;
-  const int tc = tid & 127;
-  const int s = blockIdx.x % p.gC;
-  const int q = blockIdx.x / p.gC;
-  const int n = p.n;
-  const int r = p.r;
-  const int rb = q * p.rows_per_cta;
-  const int re = min(n, rb + p.rows_per_cta);
-  if (rb >= re) return;
-  const int strip0 = s * STRIP;
-  const int col0 = strip0 + tc * COLS;
-  const int nbatch = (re - rb + kBatch - 1) / kBatch;
-  const T* Xf = static_cast<const T*>(p.Xf);
-  const T* Yf = static_cast<const T*>(p.Yf);
-  const T* Uu = static_cast<const T*>(p.Uu);
-  const T* Wu = static_cast<const T*>(p.Wu);
-  T* P = static_cast<T*>(p.P);
-
-  if (tid == 0) {
-    prefetch_tmap(&tmap);
-    for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  int nbox = 0;
-#pragma unroll
-  for (int b = 0; b < NB; ++b) nbox += (strip0 + b * BOXC < n) ? 1 : 0;
-  const uint32_t stage_bytes = (uint32_t)(nbox * kBatch * BOXC * sizeof(T));
-  auto issue = [&](int b) {
-    const int st = b % kStages;
-    T* dst = stages + st * STAGE_ELEMS;
-    mbar_arrive_expect_tx(&full[st], stage_bytes);
-#pragma unroll
-    for (int bx = 0; bx < NB; ++bx) {
-      if (strip0 + bx * BOXC < n)
-        tma_load_2d(dst + bx * kBatch * BOXC, &tmap, strip0 + bx * BOXC, rb + b * kBatch,
-                    &full[st]);
-    }
-  };
-  if (tid == 0) {
-    for (int b = 0; b < kStages && b < nbatch; ++b) issue(b);
-  }
-
-  float2 ucol2[COLS][R2];   // (U(col_k, c), U(col_k, c+1))
-  float2 vcolT2[R][2];      // (W(col_2m, c), W(col_2m+1, c)), m = 0, 1
-  float2 yacc2[COLS][R2];
-#pragma unroll
-  for (int k = 0; k < COLS; ++k) {
-    const int col = col0 + k;
-#pragma unroll
-    for (int c2 = 0; c2 < R2; ++c2) {
-      const int c = 2 * c2;
-      const bool ok0 = (c < r) && (col < n), ok1 = (c + 1 < r) && (col < n);
-      ucol2[k][c2] = make_float2(DO_X && ok0 ? Xf[(int64_t)c * p.fs + col] : 0.f,
-                                 DO_X && ok1 ? Xf[(int64_t)(c + 1) * p.fs + col] : 0.f);
-      yacc2[k][c2] = make_float2(0.f, 0.f);
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < R; ++c) {
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      const int ca = col0 + 2 * m, cb = col0 + 2 * m + 1;
-      vcolT2[c][m] = make_float2(DO_U && c < r && ca < n ? Wu[(int64_t)c * p.fs + ca] : 0.f,
-                                 DO_U && c < r && cb < n ? Wu[(int64_t)c * p.fs + cb] : 0.f);
-    }
-  }
-  const int box = (tc * COLS) / BOXC;
-  const int inbox = (tc * COLS) % BOXC;
-  const bool vec_ok = (col0 + COLS <= n);
-  const int ecore = s + tid * p.gC;
-  const bool do_core = DO_U && DO_Y && (p.Cpart != nullptr) && (ecore < r * r);
-  if (do_core) Csh[tid] = 0.0;
-
-  int issued = min(kStages, nbatch);
-  for (int b = 0; b < nbatch; ++b) {
-    const int st = b % kStages;
-    const uint32_t parity = (uint32_t)((b / kStages) & 1);
-    const int row0 = rb + b * kBatch;
-    const int nb = min(kBatch, re - row0);
-    for (int idx = tid; idx < kBatch * R; idx += kThreads) {
-      const int c = idx / kBatch;
-      const int j = idx % kBatch;
-      const bool ok = (j < nb) && (c < r);
-      if (DO_U) {
-        const T u = ok ? Uu[(int64_t)c * p.fs + row0 + j] : 0.f;
-        Us2[j * R + c] = make_float2(u, u);
-      }
-      if (DO_Y) Vs[j * R + c] = ok ? Yf[(int64_t)c * p.fs + row0 + j] : 0.f;
-    }
-    const bool ok = mbar_wait_bounded(&full[st], parity, p.status);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        for (int bb = b + 1; bb < issued; ++bb)
-          mbar_wait_bounded(&full[bb % kStages], (uint32_t)((bb / kStages) & 1), nullptr);
-      }
-      return;
-    }
-    if (do_core) {
-      const int c1 = ecore / r, c2 = ecore % r;
-      double acc = Csh[tid];
-#pragma unroll
-      for (int j = 0; j < kBatch; ++j)
-        acc = fma((double)Vs[j * R + c1], (double)Us2[j * R + c2].x, acc);
-      Csh[tid] = acc;
-    }
-    const T* sp = stages + st * STAGE_ELEMS + box * kBatch * BOXC + inbox;
-#pragma unroll
-    for (int jj = 0; jj < kBatch / 2; ++jj) {
-      const int j = rg + 2 * jj;
-      float2 x2[R2];
-#pragma unroll
-      for (int c2 = 0; c2 < R2; ++c2) x2[c2] = make_float2(0.f, 0.f);
-      if (j < nb) {
-        float4 v4 = *reinterpret_cast<const float4*>(sp + j * BOXC);
-        if (!vec_ok) {
-          v4.x = (col0 + 0 < n) ? v4.x : 0.f;
-          v4.y = (col0 + 1 < n) ? v4.y : 0.f;
-          v4.z = (col0 + 2 < n) ? v4.z : 0.f;
-          v4.w = (col0 + 3 < n) ? v4.w : 0.f;
-        }
-        const float2 pd[COLS] = {make_float2(v4.x, v4.x), make_float2(v4.y, v4.y),
-                                 make_float2(v4.z, v4.z), make_float2(v4.w, v4.w)};
-        if (DO_Y) {
-          const float2* vr2 = reinterpret_cast<const float2*>(Vs + j * R);
-#pragma unroll
-          for (int c2 = 0; c2 < R2; ++c2) {
-            const float2 v = vr2[c2];
-#pragma unroll
-            for (int k = 0; k < COLS; ++k) yacc2[k][c2] = __ffma2_rn(pd[k], v, yacc2[k][c2]);
-          }
-        }
-        if (DO_X) {
-#pragma unroll
-          for (int k = 0; k < COLS; ++k)
-#pragma unroll
-            for (int c2 = 0; c2 < R2; ++c2) x2[c2] = __ffma2_rn(pd[k], ucol2[k][c2], x2[c2]);
-        }
-        if (DO_U) {
-          float2 pn[2] = {make_float2(v4.x, v4.y), make_float2(v4.z, v4.w)};
-          const float2* ur = Us2 + j * R;
-#pragma unroll
-          for (int c = 0; c < R; ++c) {
-            const float2 u = ur[c];
-            pn[0] = __ffma2_rn(u, vcolT2[c][0], pn[0]);
-            pn[1] = __ffma2_rn(u, vcolT2[c][1], pn[1]);
-          }
-          T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
-          if (vec_ok) {
-            *reinterpret_cast<float4*>(dst) = make_float4(pn[0].x, pn[0].y, pn[1].x, pn[1].y);
-          } else {
-            const float o[4] = {pn[0].x, pn[0].y, pn[1].x, pn[1].y};
-#pragma unroll
-            for (int k = 0; k < COLS; ++k)
-              if (col0 + k < n) dst[k] = o[k];
-          }
-        }
-      }
-      if (DO_X) {
-#pragma unroll
-        for (int c2 = 0; c2 < R2; ++c2) {
-          Xbuf[(j * R + 2 * c2) * XS + tc] = x2[c2].x;
-          Xbuf[(j * R + 2 * c2 + 1) * XS + tc] = x2[c2].y;
-        }
-      }
-    }
-    __syncthreads();
-    if (tid == 0 && b + kStages < nbatch) {
-      fence_proxy_async();
-      issue(b + kStages);
-      ++issued;
-    }
-    if (DO_X) {
-      const int w = tid >> 5;
-      const int lane = tid & 31;
-      constexpr int L = 32 / R;
-      const int c = lane % R;
-      const int ts = lane / R;
-      T sum = 0.f;
-#pragma unroll 4
-      for (int t = ts; t < 128; t += L) sum += Xbuf[(w * R + c) * XS + t];
-#pragma unroll
-      for (int off = R; off < 32; off <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-      if (ts == 0 && w < nb && c < r) {
-        T* xo = static_cast<T*>(p.Xpart);
-        xo[(int64_t)s * p.xp_s + (int64_t)c * p.part_cs + row0 + w] = sum;
-      }
-    }
-  }
-  if (do_core) p.Cpart[(int64_t)q * r * r + ecore] = Csh[tid];
-  if (DO_Y) {
-    __syncthreads();
-    T* yc = Xbuf;  // [k][c][tc]
-    if (rg == 1) {
-#pragma unroll
-      for (int k = 0; k < COLS; ++k)
-#pragma unroll
-        for (int c2 = 0; c2 < R2; ++c2) {
-          yc[(k * R + 2 * c2) * 128 + tc] = yacc2[k][c2].x;
-          yc[(k * R + 2 * c2 + 1) * 128 + tc] = yacc2[k][c2].y;
-        }
-    }
-    __syncthreads();
-    if (rg == 0 && col0 < n) {
-      T* yo = static_cast<T*>(p.Ypart) + (int64_t)q * p.yp_q;
-#pragma unroll
-      for (int c = 0; c < R; ++c) {
-        if (c >= r) break;
-        float vals[COLS];
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) {
-          const float mine = (c & 1) ? yacc2[k][c / 2].y : yacc2[k][c / 2].x;
-          vals[k] = mine + yc[(k * R + c) * 128 + tc];
-        }
-        T* dst = yo + (int64_t)c * p.part_cs + col0;
-        if (vec_ok) {
-          *reinterpret_cast<float4*>(dst) = make_float4(vals[0], vals[1], vals[2], vals[3]);
-        } else {
-#pragma unroll
-          for (int k = 0; k < COLS; ++k)
-            if (col0 + k < n) dst[k] = vals[k];
-        }
-      }
-    }
-  }
-}
-
 // w[:, c] += w[:, c + RI] from the last column down: block suffix sums
 template <typename T, int R, int COLS, int RI>
 __device__ __forceinline__ void suffix_blocks(T (&w)[COLS][R]) {
@@ -717,142 +454,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
-// ---------------------------------------------------------------------------
-// FP32 update-only pass with packed FP32x2 FMAs: each thread owns two
-// adjacent columns, so p'(row, k..k+1) += u(row, c) * W(k..k+1, c) is one
-// FFMA2 per factor column with u staged duplicated, (u, u), in shared memory.
-// Bitwise identical to update_pass_kernel<float, R, 2>.
-// ---------------------------------------------------------------------------
-template <int R>
-__global__ void __launch_bounds__(kThreads, 2)
-    update_pass_f2_kernel(const __grid_constant__ CUtensorMap tmap, const PassParams p) {
-  using T = float;
-  constexpr int COLS = 2;
-  constexpr int STRIP = kThreads * COLS;
-  constexpr int BOXC = box_cols<T>();
-  constexpr int NB = STRIP / BOXC;
-  constexpr int STAGE_ELEMS = kBatch * STRIP;
-  static_assert(NB * BOXC == STRIP, "strip must be whole boxes");
-
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  T* stages = reinterpret_cast<T*>(smem_raw);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * kStages * STAGE_ELEMS);
-  float2* Us2 = reinterpret_cast<float2*>(full + kStages);  // [kBatch][R] (u, u)
-
-  const int tid = threadIdx.x;
-  const int s = blockIdx.x % p.gC;
-  const int q = blockIdx.x / p.gC;
-  const int n = p.n;
-  const int r = p.r;
-  const int rb = q * p.rows_per_cta;
-  const int re = min(n, rb + p.rows_per_cta);
-  if (rb >= re) return;
-  const int strip0 = s * STRIP;
-  const int col0 = strip0 + tid * COLS;
-  const int nbatch = (re - rb + kBatch - 1) / kBatch;
-  const T* Uu = static_cast<const T*>(p.Uu);
-  const T* Wu = static_cast<const T*>(p.Wu);
-  T* P = static_cast<T*>(p.P);
-
-  if (tid == 0) {
-    prefetch_tmap(&tmap);
-    for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  int nbox = 0;
-#pragma unroll
-  for (int b = 0; b < NB; ++b) nbox += (strip0 + b * BOXC < n) ? 1 : 0;
-  const uint32_t stage_bytes = (uint32_t)(nbox * kBatch * BOXC * sizeof(T));
-  auto issue = [&](int b) {
-    const int st = b % kStages;
-    T* dst = stages + st * STAGE_ELEMS;
-    mbar_arrive_expect_tx(&full[st], stage_bytes);
-#pragma unroll
-    for (int bx = 0; bx < NB; ++bx) {
-      if (strip0 + bx * BOXC < n)
-        tma_load_2d(dst + bx * kBatch * BOXC, &tmap, strip0 + bx * BOXC, rb + b * kBatch,
-                    &full[st]);
-    }
-  };
-  if (tid == 0) {
-    for (int b = 0; b < kStages && b < nbatch; ++b) issue(b);
-  }
-
-  T wcol[COLS][R];
-#pragma unroll
-  for (int k = 0; k < COLS; ++k) {
-    const int col = col0 + k;
-#pragma unroll
-    for (int c = 0; c < R; ++c)
-      wcol[k][c] = (c < r && col < n) ? Wu[(int64_t)c * p.fs + col] : 0.f;
-  }
-  switch (p.suffix_rin) {
-    case 0: break;
-    case 1: suffix_blocks<T, R, COLS, 1>(wcol); break;
-    case 2: suffix_blocks<T, R, COLS, 2>(wcol); break;
-    case 3: suffix_blocks<T, R, COLS, 3>(wcol); break;
-    case 4: suffix_blocks<T, R, COLS, 4>(wcol); break;
-    case 5: suffix_blocks<T, R, COLS, 5>(wcol); break;
-    case 6: suffix_blocks<T, R, COLS, 6>(wcol); break;
-    case 7: suffix_blocks<T, R, COLS, 7>(wcol); break;
-    case 8: suffix_blocks<T, R, COLS, 8>(wcol); break;
-    default: break;
-  }
-  float2 w2[R];
-#pragma unroll
-  for (int c = 0; c < R; ++c) w2[c] = make_float2(wcol[0][c], wcol[1][c]);
-  const int box = (tid * COLS) / BOXC;
-  const int inbox = (tid * COLS) % BOXC;
-  const bool vec_ok = (col0 + COLS <= n);
-  const bool any_col = (col0 < n);
-
-  int issued = min(kStages, nbatch);
-  for (int b = 0; b < nbatch; ++b) {
-    const int st = b % kStages;
-    const uint32_t parity = (uint32_t)((b / kStages) & 1);
-    const int row0 = rb + b * kBatch;
-    const int nb = min(kBatch, re - row0);
-    for (int idx = tid; idx < kBatch * R; idx += kThreads) {
-      const int c = idx / kBatch;
-      const int j = idx % kBatch;
-      const T u = (j < nb && c < r) ? Uu[(int64_t)c * p.fs + row0 + j] : 0.f;
-      Us2[j * R + c] = make_float2(u, u);
-    }
-    const bool ok = mbar_wait_bounded(&full[st], parity, p.status);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        for (int bb = b + 1; bb < issued; ++bb)
-          mbar_wait_bounded(&full[bb % kStages], (uint32_t)((bb / kStages) & 1), nullptr);
-      }
-      return;
-    }
-    const T* sp = stages + st * STAGE_ELEMS + box * kBatch * BOXC + inbox;
-    if (any_col) {
-#pragma unroll
-      for (int j = 0; j < kBatch; ++j) {
-        if (j < nb) {
-          float2 pv = *reinterpret_cast<const float2*>(sp + j * BOXC);
-          const float2* ur = Us2 + j * R;
-#pragma unroll
-          for (int c = 0; c < R; ++c) pv = __ffma2_rn(ur[c], w2[c], pv);
-          T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
-          if (vec_ok) {
-            *reinterpret_cast<float2*>(dst) = pv;
-          } else {
-            dst[0] = pv.x;  // col0 < n, col0 + 1 >= n
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (tid == 0 && b + kStages < nbatch) {
-      fence_proxy_async();
-      issue(b + kStages);
-      ++issued;
-    }
-  }
-}
+#include "lv_pass_ws.cuh"
 
 // ---------------------------------------------------------------------------
 // Host side: geometry, tensor maps and launchers.
@@ -914,14 +516,18 @@ template <typename T, int R, int MODE>
 static cudaError_t launch_fused_t(const PassParams& p, const CUtensorMap& tm, cudaStream_t s) {
   constexpr int COLS = Vec<T>::N;
   constexpr int STRIP = 128 * COLS;
-  // FP32 with R >= 2 runs the packed-FMA variant (Us staged as (u, u) pairs)
-  constexpr bool kPacked = std::is_same<T, float>::value && R >= 2;
-  const size_t smem = sizeof(T) * kStages * kBatch * STRIP + sizeof(uint64_t) * kStages +
-                      sizeof(T) * ((kPacked ? 3 : 2) * kBatch * R + kBatch * R * (128 + 32 / R)) +
-                      sizeof(double) * R * R;
+  // FP32 runs the decoupled-ring variant (lv_pass_ws.cuh)
+  constexpr bool kWs = std::is_same<T, float>::value;
+  const size_t smem =
+      kWs ? sizeof(T) * kStagesWs * kBatch * STRIP + sizeof(uint64_t) * (2 * kStagesWs + 1) +
+                kStagesWs * kBatch * R * (sizeof(float2) + sizeof(float) + 4 * sizeof(float)) +
+                sizeof(double) * kThreads
+          : sizeof(T) * kStages * kBatch * STRIP + sizeof(uint64_t) * kStages +
+                sizeof(T) * (2 * kBatch * R + kBatch * R * (128 + 32 / R)) +
+                sizeof(double) * R * R;
   void (*kfn)(const CUtensorMap, const PassParams);
-  if constexpr (kPacked)
-    kfn = fused_pass_f2_kernel<R, MODE>;
+  if constexpr (kWs)
+    kfn = fused_ws_kernel<R, MODE>;
   else
     kfn = fused_pass_kernel<T, R, MODE>;
   static bool configured = false;
@@ -960,12 +566,15 @@ cudaError_t launch_fused(const PassParams& p, const CUtensorMap& tm, int R, int 
 template <typename T, int R, int COLS>
 static cudaError_t launch_update_t(const PassParams& p, const CUtensorMap& tm, cudaStream_t s) {
   constexpr int STRIP = kThreads * COLS;
-  constexpr bool kPacked = std::is_same<T, float>::value && COLS == 2;
-  const size_t smem = sizeof(T) * kStages * kBatch * STRIP + sizeof(uint64_t) * kStages +
-                      sizeof(T) * kBatch * R * (kPacked ? 2 : 1);
+  constexpr bool kWs = std::is_same<T, float>::value && COLS >= 2;
+  const size_t smem =
+      kWs ? sizeof(T) * kStagesWs * kBatch * STRIP + sizeof(uint64_t) * (2 * kStagesWs + 1) +
+                sizeof(float2) * kStagesWs * kBatch * R
+          : sizeof(T) * kStages * kBatch * STRIP + sizeof(uint64_t) * kStages +
+                sizeof(T) * kBatch * R;
   void (*kfn)(const CUtensorMap, const PassParams);
-  if constexpr (kPacked)
-    kfn = update_pass_f2_kernel<R>;
+  if constexpr (kWs)
+    kfn = update_ws_kernel<R, COLS>;
   else
     kfn = update_pass_kernel<T, R, COLS>;
   static bool configured = false;

@@ -1,0 +1,574 @@
+// FP32 view passes with a decoupled stage ring (included by lv_pass.cu).
+//
+// Same arithmetic and ownership as fused_pass_kernel / update_pass_kernel
+// (every lane performs the same multiply-adds in the same order, with packed
+// FP32x2 FMAs), but no CTA-wide barrier per batch:
+//  * each stage of the ring has a "full" mbarrier (TMA bytes of the view tile
+//    + the asynchronous copies of the batch's factor rows) and an "empty"
+//    mbarrier that every warp arrives on once it has finished with the stage;
+//  * warp 0 alone waits for "empty", combines the per-warp row sums of the
+//    batch (fused pass), starts the cp.async copies of the factor rows of the
+//    batch kStages ahead (tracked by "full" through
+//    cp.async.mbarrier.arrive.noinc, so no warp waits for their latency) and
+//    re-issues the TMA loads; the other warps run up to kStages-1 batches
+//    ahead;
+//  * the row sums P U are reduced inside each warp by a fixed butterfly
+//    (shuffle reduce-scatter), so only R values per warp and row cross warps.
+// Every wait is bounded; the first expired wait sets a CTA-wide abort flag
+// that makes all later waits return at once, so a lost transaction ends the
+// kernel with LINVIEW_ETIMEOUT latched instead of a hang.
+// (Included inside namespace lv after update_pass_kernel and suffix_blocks.)
+
+// Sum each of x[0..V) over the 32 lanes of a warp by a fixed butterfly
+// (reduce-scatter): each level sends half of the remaining values to the
+// partner lane and keeps the other half, then plain xor-sums finish.  On
+// return, lanes with lane % (32 / V) == 0 hold the total of value idx.
+// Costs V - 1 + 5 - log2(V) shuffles for all V values.
+template <int M>
+__device__ __forceinline__ float rs_levels(const float (&in)[M], int lane, int o, int& idx) {
+  constexpr unsigned FULL = 0xffffffffu;
+  if constexpr (M == 1) {
+    float v = in[0];
+#pragma unroll
+    for (int oo = o; oo >= 1; oo >>= 1) v += __shfl_xor_sync(FULL, v, oo);
+    return v;
+  } else {
+    const bool up = (lane & o) != 0;
+    float out[M / 2];
+#pragma unroll
+    for (int i = 0; i < M / 2; ++i)
+      out[i] = (up ? in[i + M / 2] : in[i]) + __shfl_xor_sync(FULL, up ? in[i] : in[i + M / 2], o);
+    idx += up ? M / 2 : 0;
+    return rs_levels<M / 2>(out, lane, o >> 1, idx);
+  }
+}
+
+template <int V>
+__device__ __forceinline__ float warp_reduce_scatter(const float (&x)[V], int lane, int& idx) {
+  static_assert(V >= 1 && V <= 32 && (V & (V - 1)) == 0, "V must be a power of two <= 32");
+  idx = 0;
+  return rs_levels<V>(x, lane, 16, idx);
+}
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                              unsigned* status) {
+  if (*abort_flag) return false;
+  if (mbar_wait_bounded(bar, parity, status)) return true;
+  *abort_flag = 1;
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Fused products (+ update) pass, FP32, R in {1, 2, 4, 8}.
+// Thread (rg = warp / 4, tc = tid % 128) owns columns strip0 + 4 tc .. +3 and
+// processes rows rg, rg+2, rg+4, rg+6 of every batch.
+// ---------------------------------------------------------------------------
+template <int R, int MODE>
+__global__ void __launch_bounds__(kThreads, 2)
+    fused_ws_kernel(const __grid_constant__ CUtensorMap tmap, const PassParams p) {
+  using T = float;
+  constexpr int COLS = 4;
+  constexpr int STRIP = 128 * COLS;
+  constexpr int BOXC = kBoxBytes / 4;
+  constexpr int NB = STRIP / BOXC;
+  constexpr int STAGE_ELEMS = kBatch * STRIP;
+  constexpr bool DO_X = (MODE & 1) != 0;
+  constexpr bool DO_Y = (MODE & 2) != 0;
+  constexpr bool DO_U = (MODE & 4) != 0;
+  constexpr bool PACK = R >= 2;
+  constexpr int R2 = PACK ? R / 2 : 1;
+  constexpr int S = kStagesWs;
+  // the row sums of G rows are reduced by one butterfly over G*R values
+  constexpr int G = R <= 4 ? kBatch / 2 : 1;
+
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  T* stages = reinterpret_cast<T*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * S * STAGE_ELEMS);
+  uint64_t* empty = full + S;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
+  float2* Us2 = reinterpret_cast<float2*>(empty + S + 1);  // [S][kBatch][R] (u, u)
+  T* Vs = reinterpret_cast<T*>(Us2 + S * kBatch * R);      // [S][kBatch][R]
+  T* Xw = Vs + S * kBatch * R;                             // [S][kBatch][4][R] warp sums
+  double* Csh = reinterpret_cast<double*>(Xw + S * kBatch * 4 * R);  // [kThreads] core sums
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int rg = warp >> 2;
+  const int wq = warp & 3;
+  const int tc = tid & 127;
+  const int s = blockIdx.x % p.gC;
+  const int q = blockIdx.x / p.gC;
+  const int n = p.n;
+  const int r = p.r;
+  const int rb = q * p.rows_per_cta;
+  const int re = min(n, rb + p.rows_per_cta);
+  if (rb >= re) return;
+  const int strip0 = s * STRIP;
+  const int col0 = strip0 + tc * COLS;
+  const int nbatch = (re - rb + kBatch - 1) / kBatch;
+  const T* Xf = static_cast<const T*>(p.Xf);
+  const T* Yf = static_cast<const T*>(p.Yf);
+  const T* Uu = static_cast<const T*>(p.Uu);
+  const T* Wu = static_cast<const T*>(p.Wu);
+  T* P = static_cast<T*>(p.P);
+  constexpr bool STAGE_ROWS = DO_U || DO_Y;
+
+  if (tid == 0) {
+    prefetch_tmap(&tmap);
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], STAGE_ROWS ? 33 : 1);  // expect_tx arrive (+ 32 cp.async arrivals)
+      mbar_init(&empty[i], kThreads / 32);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  int nbox = 0;
+#pragma unroll
+  for (int bx = 0; bx < NB; ++bx) nbox += (strip0 + bx * BOXC < n) ? 1 : 0;
+  const uint32_t stage_bytes = (uint32_t)(nbox * kBatch * BOXC * sizeof(T));
+
+  // warp 0: start batch b in stage b % S (factor rows by cp.async, tile by TMA)
+  auto produce = [&](int b) {
+    const int st = b % S;
+    const int row0 = rb + b * kBatch;
+    const int nb = min(kBatch, re - row0);
+    if constexpr (STAGE_ROWS) {
+      for (int idx = lane; idx < kBatch * R; idx += 32) {
+        const int c = idx / kBatch;
+        const int j = idx % kBatch;
+        const bool ok = (j < nb) && (c < r);
+        const int64_t g = ok ? (int64_t)c * p.fs + row0 + j : 0;
+        if constexpr (DO_U) {
+          float* d = reinterpret_cast<float*>(Us2 + (st * kBatch + j) * R + c);
+          cp_async4(d, Uu + g, ok);
+          cp_async4(d + 1, Uu + g, ok);
+        }
+        if constexpr (DO_Y) cp_async4(Vs + (st * kBatch + j) * R + c, Yf + g, ok);
+      }
+      cp_async_arrive_noinc(&full[st]);
+    }
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&full[st], stage_bytes);
+#pragma unroll
+      for (int bx = 0; bx < NB; ++bx) {
+        if (strip0 + bx * BOXC < n)
+          tma_load_2d(stages + st * STAGE_ELEMS + bx * kBatch * BOXC, &tmap, strip0 + bx * BOXC,
+                      row0, &full[st]);
+      }
+    }
+  };
+  int issued = 0;
+  if (warp == 0) {
+    for (int b = 0; b < S && b < nbatch; ++b) produce(b);
+    issued = min(S, nbatch);
+  }
+
+  // column-side factors for this thread's 4 columns
+  float2 ucol2[COLS][R2];  // PACK: (U(col_k, c), U(col_k, c+1)); else .x = U(col_k, 0)
+  float2 vw2[R][2];        // (W(col_2m, c), W(col_2m+1, c))
+  float2 yacc2[COLS][R2];
+#pragma unroll
+  for (int k = 0; k < COLS; ++k) {
+    const int col = col0 + k;
+#pragma unroll
+    for (int c2 = 0; c2 < R2; ++c2) {
+      const int c = PACK ? 2 * c2 : 0;
+      const bool ok0 = DO_X && (c < r) && (col < n);
+      const bool ok1 = DO_X && PACK && (c + 1 < r) && (col < n);
+      ucol2[k][c2] = make_float2(ok0 ? Xf[(int64_t)c * p.fs + col] : 0.f,
+                                 ok1 ? Xf[(int64_t)(c + 1) * p.fs + col] : 0.f);
+      yacc2[k][c2] = make_float2(0.f, 0.f);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < R; ++c) {
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const int ca = col0 + 2 * m, cb = ca + 1;
+      const bool okc = DO_U && (c < r);
+      vw2[c][m] = make_float2(okc && ca < n ? Wu[(int64_t)c * p.fs + ca] : 0.f,
+                              okc && cb < n ? Wu[(int64_t)c * p.fs + cb] : 0.f);
+    }
+  }
+  const int box = (tc * COLS) / BOXC;
+  const int inbox = (tc * COLS) % BOXC;
+  const bool vec_ok = (col0 + COLS <= n);
+  // factor core C = V^T U over this CTA's rows (FP64).  The CTA owns the
+  // entries e = s + i * gC; each entry is split over LPE threads, thread li
+  // taking batch rows li, li + LPE, ..., so every thread does at most
+  // kBatch / LPE independent FP64 FMAs per batch (no dependent chain, which
+  // on this part would make its warp the slowest).  Threads are taken from
+  // the end of the CTA so warp 0, which refills the ring, stays free.
+  const int ncore = (r * r > s) ? (r * r - s + p.gC - 1) / p.gC : 0;  // entries owned
+  const int LPE = ncore * kBatch <= kThreads ? kBatch : kBatch / 2;
+  const int cslot = kThreads - 1 - tid;
+  const int centry = cslot / LPE;
+  const int cli = cslot % LPE;
+  const int ecore = s + centry * p.gC;
+  const bool do_core = DO_U && DO_Y && (p.Cpart != nullptr) && (centry < ncore);
+  if (do_core) Csh[cslot] = 0.0;  // one slot per thread (kept out of registers)
+  int waited = 0;  // batches whose "full" phase this thread has seen complete
+
+  for (int b = 0; b < nbatch; ++b) {
+    const int st = b % S;
+    const uint32_t parity = (uint32_t)((b / S) & 1);
+    const int row0 = rb + b * kBatch;
+    const int nb = min(kBatch, re - row0);
+    if (wait_or_abort(&full[st], parity, abort_flag, p.status)) {
+      waited = b + 1;
+      const float2* Ust = Us2 + st * kBatch * R;
+      const T* Vst = Vs + st * kBatch * R;
+      if (do_core) {
+        const int c1 = ecore / r, c2 = ecore % r;
+        double acc = Csh[cslot];
+        for (int j = cli; j < kBatch; j += LPE)
+          acc = fma((double)Vst[j * R + c1], (double)Ust[j * R + c2].x, acc);
+        Csh[cslot] = acc;
+      }
+      const T* sp = stages + st * STAGE_ELEMS + box * kBatch * BOXC + inbox;
+      float xg[G * R];  // row sums of the current group of rows (zero for absent rows)
+#pragma unroll
+      for (int jj = 0; jj < kBatch / 2; ++jj) {
+        const int j = rg + 2 * jj;
+        float* xr = xg + (jj % G) * R;
+        if constexpr (DO_X) {
+#pragma unroll
+          for (int c = 0; c < R; ++c) xr[c] = 0.f;
+        }
+        if (j < nb) {
+          float4 v4 = *reinterpret_cast<const float4*>(sp + j * BOXC);
+          if (!vec_ok) {
+            v4.x = (col0 + 0 < n) ? v4.x : 0.f;
+            v4.y = (col0 + 1 < n) ? v4.y : 0.f;
+            v4.z = (col0 + 2 < n) ? v4.z : 0.f;
+            v4.w = (col0 + 3 < n) ? v4.w : 0.f;
+          }
+          const float pvs[COLS] = {v4.x, v4.y, v4.z, v4.w};
+          if constexpr (PACK) {
+            const float2 pd[COLS] = {make_float2(v4.x, v4.x), make_float2(v4.y, v4.y),
+                                     make_float2(v4.z, v4.z), make_float2(v4.w, v4.w)};
+            if constexpr (DO_Y) {
+              const float2* vr2 = reinterpret_cast<const float2*>(Vst + j * R);
+#pragma unroll
+              for (int c2 = 0; c2 < R2; ++c2) {
+                const float2 v = vr2[c2];
+#pragma unroll
+                for (int k = 0; k < COLS; ++k) yacc2[k][c2] = __ffma2_rn(pd[k], v, yacc2[k][c2]);
+              }
+            }
+            if constexpr (DO_X) {
+              float2 x2[R2];
+#pragma unroll
+              for (int c2 = 0; c2 < R2; ++c2) x2[c2] = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int k = 0; k < COLS; ++k)
+#pragma unroll
+                for (int c2 = 0; c2 < R2; ++c2) x2[c2] = __ffma2_rn(pd[k], ucol2[k][c2], x2[c2]);
+#pragma unroll
+              for (int c2 = 0; c2 < R2; ++c2) {
+                xr[2 * c2] = x2[c2].x;
+                xr[2 * c2 + 1] = x2[c2].y;
+              }
+            }
+          } else {
+            if constexpr (DO_Y) {
+              const float v = Vst[j * R];
+#pragma unroll
+              for (int k = 0; k < COLS; ++k) yacc2[k][0].x = fmaf(pvs[k], v, yacc2[k][0].x);
+            }
+            if constexpr (DO_X) {
+              float x = 0.f;
+#pragma unroll
+              for (int k = 0; k < COLS; ++k) x = fmaf(pvs[k], ucol2[k][0].x, x);
+              xr[0] = x;
+            }
+          }
+          if constexpr (DO_U) {
+            float2 pn[2] = {make_float2(v4.x, v4.y), make_float2(v4.z, v4.w)};
+            const float2* ur = Ust + j * R;
+#pragma unroll
+            for (int c = 0; c < R; ++c) {
+              const float2 u = ur[c];
+              pn[0] = __ffma2_rn(u, vw2[c][0], pn[0]);
+              pn[1] = __ffma2_rn(u, vw2[c][1], pn[1]);
+            }
+            T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
+            if (vec_ok) {
+              *reinterpret_cast<float4*>(dst) = make_float4(pn[0].x, pn[0].y, pn[1].x, pn[1].y);
+            } else {
+              const float o[4] = {pn[0].x, pn[0].y, pn[1].x, pn[1].y};
+#pragma unroll
+              for (int k = 0; k < COLS; ++k)
+                if (col0 + k < n) dst[k] = o[k];
+            }
+          }
+        }
+        if constexpr (DO_X) {
+          if ((jj % G) == G - 1) {
+            int v = 0;
+            const float tot = warp_reduce_scatter<G * R>(xg, lane, v);
+            const int jr = rg + 2 * (jj - (G - 1) + v / R);  // batch row of value v
+            if ((lane % (32 / (G * R))) == 0) Xw[((st * kBatch + jr) * 4 + wq) * R + (v % R)] = tot;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+    if (warp == 0) {
+      // all warps are done with batch b: fold its row sums, refill the stage
+      if (wait_or_abort(&empty[st], parity, abort_flag, p.status)) {
+        if constexpr (DO_X) {
+          T* xo = static_cast<T*>(p.Xpart) + (int64_t)s * p.xp_s;
+          for (int idx = lane; idx < kBatch * R; idx += 32) {
+            const int j = idx / R, c = idx % R;
+            if (j < nb && c < r) {
+              const T* w4 = Xw + ((st * kBatch + j) * 4) * R + c;
+              xo[(int64_t)c * p.part_cs + row0 + j] = ((w4[0] + w4[R]) + w4[2 * R]) + w4[3 * R];
+            }
+          }
+        }
+        if (b + S < nbatch) {
+          __syncwarp();
+          produce(b + S);
+          ++issued;
+        }
+      }
+    }
+  }
+  // on an abort, wait (bounded) for the copies issued but never waited on
+  if (warp == 0 && *abort_flag) {
+    for (int bb = waited; bb < issued; ++bb)
+      mbar_wait_bounded(&full[bb % S], (uint32_t)((bb / S) & 1), nullptr);
+  }
+  if (DO_U && DO_Y && p.Cpart != nullptr) {
+    __syncthreads();
+    if (do_core && cli == 0) {  // fixed-order sum of the entry's LPE partials
+      double sum = 0.0;
+      for (int i = 0; i < LPE; ++i) sum += Csh[centry * LPE + i];
+      p.Cpart[(int64_t)q * r * r + ecore] = sum;
+    }
+  }
+  if constexpr (DO_Y) {
+    __syncthreads();
+    T* yc = stages;  // [k][c][tc], reusing the ring
+    if (rg == 1) {
+#pragma unroll
+      for (int k = 0; k < COLS; ++k)
+#pragma unroll
+        for (int c2 = 0; c2 < R2; ++c2) {
+          yc[(k * R + (PACK ? 2 * c2 : 0)) * 128 + tc] = yacc2[k][c2].x;
+          if (PACK) yc[(k * R + 2 * c2 + 1) * 128 + tc] = yacc2[k][c2].y;
+        }
+    }
+    __syncthreads();
+    if (rg == 0 && col0 < n && !*abort_flag) {
+      T* yo = static_cast<T*>(p.Ypart) + (int64_t)q * p.yp_q;
+#pragma unroll
+      for (int c = 0; c < R; ++c) {
+        if (c >= r) break;
+        float vals[COLS];
+#pragma unroll
+        for (int k = 0; k < COLS; ++k) {
+          const float mine = (c & 1) ? yacc2[k][c / 2].y : yacc2[k][c / 2].x;
+          vals[k] = mine + yc[(k * R + c) * 128 + tc];
+        }
+        T* dst = yo + (int64_t)c * p.part_cs + col0;
+        if (vec_ok) {
+          *reinterpret_cast<float4*>(dst) = make_float4(vals[0], vals[1], vals[2], vals[3]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < COLS; ++k)
+            if (col0 + k < n) dst[k] = vals[k];
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Update-only pass, FP32.  COLS = 4: two row groups of 128 threads, thread
+// (rg, tc) owns columns strip0 + 4 tc .. +3 and rows rg, rg+2, ... of each
+// batch (each broadcast U row is read by 4 warps); COLS = 2: one group of 256
+// threads owning 2 columns each (for R = 32, whose column factor would not
+// fit the registers of 4 columns).
+// ---------------------------------------------------------------------------
+template <int R, int COLS>
+__global__ void __launch_bounds__(kThreads, 2)
+    update_ws_kernel(const __grid_constant__ CUtensorMap tmap, const PassParams p) {
+  using T = float;
+  constexpr int GROUPS = COLS == 4 ? 2 : 1;
+  constexpr int GT = kThreads / GROUPS;  // threads per row group
+  constexpr int STRIP = GT * COLS;
+  constexpr int BOXC = kBoxBytes / 4;
+  constexpr int NB = STRIP / BOXC;
+  constexpr int STAGE_ELEMS = kBatch * STRIP;
+  constexpr int S = kStagesWs;
+  constexpr int M = COLS / 2;  // float2 pairs per thread and row
+  static_assert(NB * BOXC == STRIP, "strip must be whole boxes");
+
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  T* stages = reinterpret_cast<T*>(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * S * STAGE_ELEMS);
+  uint64_t* empty = full + S;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
+  float2* Us2 = reinterpret_cast<float2*>(empty + S + 1);  // [S][kBatch][R] (u, u)
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int rg = GROUPS == 2 ? (tid / GT) : 0;
+  const int tc = tid % GT;
+  const int s = blockIdx.x % p.gC;
+  const int q = blockIdx.x / p.gC;
+  const int n = p.n;
+  const int r = p.r;
+  const int rb = q * p.rows_per_cta;
+  const int re = min(n, rb + p.rows_per_cta);
+  if (rb >= re) return;
+  const int strip0 = s * STRIP;
+  const int col0 = strip0 + tc * COLS;
+  const int nbatch = (re - rb + kBatch - 1) / kBatch;
+  const T* Uu = static_cast<const T*>(p.Uu);
+  const T* Wu = static_cast<const T*>(p.Wu);
+  T* P = static_cast<T*>(p.P);
+
+  if (tid == 0) {
+    prefetch_tmap(&tmap);
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 33);
+      mbar_init(&empty[i], kThreads / 32);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  int nbox = 0;
+#pragma unroll
+  for (int bx = 0; bx < NB; ++bx) nbox += (strip0 + bx * BOXC < n) ? 1 : 0;
+  const uint32_t stage_bytes = (uint32_t)(nbox * kBatch * BOXC * sizeof(T));
+  auto produce = [&](int b) {
+    const int st = b % S;
+    const int row0 = rb + b * kBatch;
+    const int nb = min(kBatch, re - row0);
+    for (int idx = lane; idx < kBatch * R; idx += 32) {
+      const int c = idx / kBatch;
+      const int j = idx % kBatch;
+      const bool ok = (j < nb) && (c < r);
+      const int64_t g = ok ? (int64_t)c * p.fs + row0 + j : 0;
+      float* d = reinterpret_cast<float*>(Us2 + (st * kBatch + j) * R + c);
+      cp_async4(d, Uu + g, ok);
+      cp_async4(d + 1, Uu + g, ok);
+    }
+    cp_async_arrive_noinc(&full[st]);
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&full[st], stage_bytes);
+#pragma unroll
+      for (int bx = 0; bx < NB; ++bx) {
+        if (strip0 + bx * BOXC < n)
+          tma_load_2d(stages + st * STAGE_ELEMS + bx * kBatch * BOXC, &tmap, strip0 + bx * BOXC,
+                      row0, &full[st]);
+      }
+    }
+  };
+  int issued = 0;
+  if (warp == 0) {
+    for (int b = 0; b < S && b < nbatch; ++b) produce(b);
+    issued = min(S, nbatch);
+  }
+
+  T wcol[COLS][R];
+#pragma unroll
+  for (int k = 0; k < COLS; ++k) {
+    const int col = col0 + k;
+#pragma unroll
+    for (int c = 0; c < R; ++c)
+      wcol[k][c] = (c < r && col < n) ? Wu[(int64_t)c * p.fs + col] : 0.f;
+  }
+  switch (p.suffix_rin) {
+    case 0: break;
+    case 1: suffix_blocks<T, R, COLS, 1>(wcol); break;
+    case 2: suffix_blocks<T, R, COLS, 2>(wcol); break;
+    case 3: suffix_blocks<T, R, COLS, 3>(wcol); break;
+    case 4: suffix_blocks<T, R, COLS, 4>(wcol); break;
+    case 5: suffix_blocks<T, R, COLS, 5>(wcol); break;
+    case 6: suffix_blocks<T, R, COLS, 6>(wcol); break;
+    case 7: suffix_blocks<T, R, COLS, 7>(wcol); break;
+    case 8: suffix_blocks<T, R, COLS, 8>(wcol); break;
+    default: break;
+  }
+  float2 w2[R][M];  // (W(col_2m, c), W(col_2m+1, c))
+#pragma unroll
+  for (int c = 0; c < R; ++c)
+#pragma unroll
+    for (int m = 0; m < M; ++m) w2[c][m] = make_float2(wcol[2 * m][c], wcol[2 * m + 1][c]);
+  const int box = (tc * COLS) / BOXC;
+  const int inbox = (tc * COLS) % BOXC;
+  const bool vec_ok = (col0 + COLS <= n);
+  const bool any_col = (col0 < n);
+  int waited = 0;
+
+  for (int b = 0; b < nbatch; ++b) {
+    const int st = b % S;
+    const uint32_t parity = (uint32_t)((b / S) & 1);
+    const int row0 = rb + b * kBatch;
+    const int nb = min(kBatch, re - row0);
+    const bool ready = wait_or_abort(&full[st], parity, abort_flag, p.status);
+    if (ready) waited = b + 1;
+    if (ready && any_col) {
+      const T* sp = stages + st * STAGE_ELEMS + box * kBatch * BOXC + inbox;
+      const float2* Ust = Us2 + st * kBatch * R;
+#pragma unroll
+      for (int jj = 0; jj < kBatch / GROUPS; ++jj) {
+        const int j = rg + GROUPS * jj;
+        if (j < nb) {
+          float2 pv[M];
+          if constexpr (COLS == 4) {
+            const float4 v4 = *reinterpret_cast<const float4*>(sp + j * BOXC);
+            pv[0] = make_float2(v4.x, v4.y);
+            pv[M - 1] = make_float2(v4.z, v4.w);
+          } else {
+            pv[0] = *reinterpret_cast<const float2*>(sp + j * BOXC);
+          }
+          const float2* ur = Ust + j * R;
+#pragma unroll
+          for (int c = 0; c < R; ++c) {
+            const float2 u = ur[c];
+#pragma unroll
+            for (int m = 0; m < M; ++m) pv[m] = __ffma2_rn(u, w2[c][m], pv[m]);
+          }
+          T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
+          if (vec_ok) {
+            if constexpr (COLS == 4)
+              *reinterpret_cast<float4*>(dst) = make_float4(pv[0].x, pv[0].y, pv[M - 1].x,
+                                                            pv[M - 1].y);
+            else
+              *reinterpret_cast<float2*>(dst) = pv[0];
+          } else {
+            const float* o = reinterpret_cast<const float*>(pv);
+#pragma unroll
+            for (int k = 0; k < COLS; ++k)
+              if (col0 + k < n) dst[k] = o[k];
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+    if (warp == 0 && b + S < nbatch) {
+      if (wait_or_abort(&empty[st], parity, abort_flag, p.status)) {
+        __syncwarp();
+        produce(b + S);
+        ++issued;
+      }
+    }
+  }
+  if (warp == 0 && *abort_flag) {
+    for (int bb = waited; bb < issued; ++bb)
+      mbar_wait_bounded(&full[bb % S], (uint32_t)((bb / S) & 1), nullptr);
+  }
+}
