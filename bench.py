@@ -155,6 +155,14 @@ def _peaks():
         return None
 
 
+def _pass_source_hash():
+    """Hash of the view-pass kernel sources (a capture is stale once they change)."""
+    h = hashlib.sha256()
+    for f in ("lv_pass.cu", "lv_pass_ws.cuh", "lv_device.cuh", "lv_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1403_6968_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _traffic(kernel):
     """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
     None when the kernel source changed since the capture."""
@@ -163,10 +171,9 @@ def _traffic(kernel):
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_1403_6968_gb300", "csrc", "lv_pass.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = _pass_source_hash()
     e = d.get(kernel)
-    if not e or e.get("lv_pass_sha256_16") != h:
+    if not e or e.get("pass_source_sha256_16") != h:
         return None
     return e.get("dram_bytes_per_launch_full_size")
 
@@ -264,7 +271,6 @@ def run_ours(args):
     clocks = Clocks(_uuid(), enabled=not args.no_clocks)
     clocks.start()
     prog.reset_stats()
-    prog.set_profiling(True)
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     torch.cuda.synchronize()
     evs[0].record(stream)
@@ -274,12 +280,24 @@ def run_ours(args):
     torch.cuda.synchronize()
     _barrier(dist)
     clk = clocks.stop()
-    prog.set_profiling(False)
     lat = [evs[t].elapsed_time(evs[t + 1]) for t in range(K)]
     tot_ms = evs[0].elapsed_time(evs[K])
+    launches_timed = prog.pass_stats(0)["all_launches"]
+    prog.sync()
+    # roofline window: the same updates right after the timed region, each view
+    # pass launched individually with a CUDA event pair around it (the timed
+    # region replays CUDA graphs, which carry no per-pass events)
+    KP = min(K, 20)
+    prog.reset_stats()
+    prog.set_profiling(True)
+    for t in range(KP):
+        prog.apply_row_delta(rows[W + t], dev_v[W + t])
+    torch.cuda.synchronize()
     st_all = prog.pass_stats(0)
     st_f = prog.pass_stats(1)
     st_u = prog.pass_stats(2)
+    prog.set_profiling(False)
+    prog.reset_stats()
     prog.sync()
     max_ms = _max_over_ranks(dist, tot_ms, True)
     value = ws * K / (max_ms / 1e3)
@@ -289,8 +307,8 @@ def run_ours(args):
     peaks = _peaks()
     peak = peaks.get("hbm_gbs") if peaks else 6800.0
     peak_src = "measured" if peaks else "fallback"
-    dom, st = ("lv::update_pass_kernel", st_u) if st_u["ms"] >= st_f["ms"] else \
-        ("lv::fused_pass_kernel", st_f)
+    dom, st = ("lv::update_ws_kernel", st_u) if st_u["ms"] >= st_f["ms"] else \
+        ("lv::fused_ws_kernel", st_f)
     per_launch = st["bytes"] / max(st["launches"], 1)
     avg_s = st["ms"] / 1e3 / max(st["launches"], 1)
     achieved = per_launch / avg_s / 1e9
@@ -300,6 +318,8 @@ def run_ours(args):
             "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
             "algorithmic_bytes_per_launch": per_launch,
             "launches": st["launches"], "avg_launch_us": avg_s * 1e6,
+            "window": f"{KP} updates right after the timed region, passes launched individually "
+                      "with CUDA events on the launching stream",
             "all_view_passes": {"launches": st_all["launches"],
                                 "achieved_gbs": st_all["bytes"] / (st_all["ms"] / 1e3) / 1e9},
             "other_pass_kernel": {"launches": other["launches"],
@@ -389,7 +409,7 @@ def run_ours(args):
            "latency_ms": {"p50": statistics.median(lat), "p99": float(np.percentile(lat, 99)),
                           "max": max(lat)},
            "achieved_refresh_gbs": bytes_per_refresh / step_s / 1e9,
-           "roofline": roof, "e2e": e2e, "gpu_launches": st_all["all_launches"],
+           "roofline": roof, "e2e": e2e, "gpu_launches": launches_timed,
            "reeval": reeval, "speedup": speed, "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, dt, setup = cpu_oracle_rate(n, k, args.cpu_sample)

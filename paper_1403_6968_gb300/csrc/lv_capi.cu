@@ -149,6 +149,17 @@ struct linview_program {
   int solver_lwork = 0;
   int* solver_info = nullptr;
   int64_t ols_chunk = 0;
+  // CUDA graphs of the per-update propagation (powers/sums), one per rank,
+  // replayed on a program-owned stream joined to the caller's stream
+  bool use_graphs = true;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+  struct GraphEntry {
+    int r;
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  std::vector<GraphEntry> graphs;
   // profiling
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -928,6 +939,10 @@ void linview_destroy(linview_program* p) {
   cudaDeviceSynchronize();
   for (void* a : p->allocs) cudaFree(a);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  for (auto& ge : p->graphs) cudaGraphExecDestroy(ge.exec);
+  if (p->gev_in) cudaEventDestroy(p->gev_in);
+  if (p->gev_out) cudaEventDestroy(p->gev_out);
+  if (p->gstream) cudaStreamDestroy(p->gstream);
   if (p->blas) cublasDestroy(p->blas);
   if (p->solver) cusolverDnDestroy(p->solver);
   delete p;
@@ -1018,10 +1033,58 @@ static linview_status after_update(linview_program* p, cudaStream_t s) {
   return LINVIEW_OK;
 }
 
+// Powers/sums: the launches after ingest depend only on the rank (all
+// pointers are the program's own), so they are captured once per rank into
+// a CUDA graph and replayed.  Profiling runs eagerly so that every pass keeps
+// its own event pair.
+static linview_status powers_graph(linview_program* p, int r, cudaStream_t s) {
+  if (!p->gstream) {
+    LV_CUDA(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
+    LV_CUDA(cudaEventCreateWithFlags(&p->gev_in, cudaEventDisableTiming));
+    LV_CUDA(cudaEventCreateWithFlags(&p->gev_out, cudaEventDisableTiming));
+  }
+  linview_program::GraphEntry* ge = nullptr;
+  for (auto& g : p->graphs)
+    if (g.r == r) ge = &g;
+  if (!ge) {
+    const int64_t before = p->all_launches;
+    LV_CUDA(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
+    linview_status st = p->elem == 4 ? powers_propagate<float>(p, r, p->gstream)
+                                     : powers_propagate<double>(p, r, p->gstream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->gstream, &graph);
+    if (st != LINVIEW_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      (void)cudaGetLastError();  // do not leave the capture error to later calls
+      return st;
+    }
+    if (ec != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(LINVIEW_EDEVICE, "graph capture failed: %s", cudaGetErrorString(ec));
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess)
+      return fail(LINVIEW_EDEVICE, "graph instantiate failed: %s", cudaGetErrorString(ei));
+    p->graphs.push_back({r, exec, p->all_launches - before});
+    p->all_launches = before;
+    ge = &p->graphs.back();
+  }
+  LV_CUDA(cudaEventRecord(p->gev_in, s));
+  LV_CUDA(cudaStreamWaitEvent(p->gstream, p->gev_in, 0));
+  LV_CUDA(cudaGraphLaunch(ge->exec, p->gstream));
+  LV_CUDA(cudaEventRecord(p->gev_out, p->gstream));
+  LV_CUDA(cudaStreamWaitEvent(s, p->gev_out, 0));
+  p->all_launches += ge->launches;
+  return LINVIEW_OK;
+}
+
 static linview_status propagate(linview_program* p, int r, cudaStream_t s) {
   switch (p->d.kind) {
     case LINVIEW_POWER:
     case LINVIEW_POWER_SUM:
+      if (p->use_graphs && !p->prof) return powers_graph(p, r, s);
       return p->elem == 4 ? powers_propagate<float>(p, r, s) : powers_propagate<double>(p, r, s);
     case LINVIEW_ITERATION:
       return p->elem == 4 ? iter_propagate<float>(p, r, s) : iter_propagate<double>(p, r, s);

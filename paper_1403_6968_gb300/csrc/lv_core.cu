@@ -98,16 +98,20 @@ cudaError_t launch_gram(const T* V, const T* U, int64_t fs, int n, int r, double
 // One thread per (row j, factor column c):
 //   X'(j,c) = sum_s Xpart[s](j,c) + sum_c2 U_h(j,c2) C_h(c2,c),
 //   Y(j,c)  = sum_q Ypart[q](j,c),
-// with C_h = sum of the nC partial blocks (fixed order, FP64) staged per CTA.
+// with C_h = sum of the nC FP64 partial blocks (fixed order, FP64), staged per
+// CTA.  The partial sums and the U_h C_h correction are accumulated in the
+// view type (fixed order): FP64 arithmetic here would be slow on this part and
+// buys nothing, the partials themselves being sums in the view type.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) assemble_kernel(const AssembleParams a) {
-  extern __shared__ double Cs[];  // r_h x r_h
+  extern __shared__ double Cs[];  // r_h x r_h, FP64 sums rounded to T
   const int rh = a.r_h;
   const int ne = rh * rh;
+  T* Ct = reinterpret_cast<T*>(Cs);
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     double sum = 0.0;
     for (int b = 0; b < a.nC; ++b) sum += a.C[(int64_t)b * ne + e];
-    Cs[e] = sum;
+    Ct[e] = (T)sum;
   }
   __syncthreads();
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -117,15 +121,16 @@ __global__ void __launch_bounds__(kThreads) assemble_kernel(const AssembleParams
   const T* Xp = static_cast<const T*>(a.Xpart);
   const T* Yp = static_cast<const T*>(a.Ypart);
   const T* Uh = static_cast<const T*>(a.Uh);
-  double x = 0.0;
-  for (int sidx = 0; sidx < a.gC; ++sidx)
-    x += (double)Xp[(int64_t)sidx * a.xp_s + (int64_t)c * a.part_cs + j];
-  for (int c2 = 0; c2 < rh; ++c2) x = fma((double)Uh[(int64_t)c2 * a.fs + j], Cs[c2 * rh + c], x);
-  static_cast<T*>(a.Unew)[(int64_t)c * a.fs + j] = (T)x;
+  T x = T(0);
+#pragma unroll 8
+  for (int sidx = 0; sidx < a.gC; ++sidx) x += Xp[(int64_t)sidx * a.xp_s + (int64_t)c * a.part_cs + j];
+  for (int c2 = 0; c2 < rh; ++c2) x = fma(Uh[(int64_t)c2 * a.fs + j], Ct[c2 * rh + c], x);
+  static_cast<T*>(a.Unew)[(int64_t)c * a.fs + j] = x;
   if (Yp) {
-    double y = 0.0;
-    for (int q = 0; q < a.gR; ++q) y += (double)Yp[(int64_t)q * a.yp_q + (int64_t)c * a.part_cs + j];
-    static_cast<T*>(a.Ynew)[(int64_t)c * a.fs + j] = (T)y;
+    T y = T(0);
+#pragma unroll 8
+    for (int q = 0; q < a.gR; ++q) y += Yp[(int64_t)q * a.yp_q + (int64_t)c * a.part_cs + j];
+    static_cast<T*>(a.Ynew)[(int64_t)c * a.fs + j] = y;
   }
 }
 
@@ -133,7 +138,7 @@ template <typename T>
 cudaError_t launch_assemble(const AssembleParams& a, cudaStream_t s) {
   const int64_t tot = (int64_t)a.n * a.r_h;
   const unsigned grid = (unsigned)((tot + kThreads - 1) / kThreads);
-  const size_t smem = sizeof(double) * (size_t)a.r_h * a.r_h;
+  const size_t smem = sizeof(T) * (size_t)a.r_h * a.r_h;  // <= 32 KB for r_h <= 64
   assemble_kernel<T><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }

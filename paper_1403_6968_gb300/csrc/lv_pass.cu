@@ -519,7 +519,7 @@ static cudaError_t launch_fused_t(const PassParams& p, const CUtensorMap& tm, cu
   // FP32 runs the decoupled-ring variant (lv_pass_ws.cuh)
   constexpr bool kWs = std::is_same<T, float>::value;
   const size_t smem =
-      kWs ? sizeof(T) * kStagesWs * kBatch * STRIP + sizeof(uint64_t) * (2 * kStagesWs + 1) +
+      kWs ? sizeof(T) * kStagesWs * kBatch * STRIP + sizeof(uint64_t) * (2 * kStagesWs + 2) +
                 kStagesWs * kBatch * R * (sizeof(float2) + sizeof(float) + 4 * sizeof(float)) +
                 sizeof(double) * kThreads
           : sizeof(T) * kStages * kBatch * STRIP + sizeof(uint64_t) * kStages +
@@ -568,7 +568,7 @@ static cudaError_t launch_update_t(const PassParams& p, const CUtensorMap& tm, c
   constexpr int STRIP = kThreads * COLS;
   constexpr bool kWs = std::is_same<T, float>::value && COLS >= 2;
   const size_t smem =
-      kWs ? sizeof(T) * kStagesWs * kBatch * STRIP + sizeof(uint64_t) * (2 * kStagesWs + 1) +
+      kWs ? sizeof(T) * kStagesWs * kBatch * STRIP + sizeof(uint64_t) * (2 * kStagesWs + 2) +
                 sizeof(float2) * kStagesWs * kBatch * R
           : sizeof(T) * kStages * kBatch * STRIP + sizeof(uint64_t) * kStages +
                 sizeof(T) * kBatch * R;

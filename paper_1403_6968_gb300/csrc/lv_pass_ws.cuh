@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * S * STAGE_ELEMS);
   uint64_t* empty = full + S;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
-  float2* Us2 = reinterpret_cast<float2*>(empty + S + 1);  // [S][kBatch][R] (u, u)
+  // 16-byte aligned so that two (u, u) pairs / four v values load as one 128-bit word
+  float2* Us2 = reinterpret_cast<float2*>(empty + S + 2);  // [S][kBatch][R] (u, u)
   T* Vs = reinterpret_cast<T*>(Us2 + S * kBatch * R);      // [S][kBatch][R]
   T* Xw = Vs + S * kBatch * R;                             // [S][kBatch][4][R] warp sums
   double* Csh = reinterpret_cast<double*>(Xw + S * kBatch * 4 * R);  // [kThreads] core sums
@@ -135,9 +136,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int row0 = rb + b * kBatch;
     const int nb = min(kBatch, re - row0);
     if constexpr (STAGE_ROWS) {
+      // consecutive lanes take consecutive factor columns of a row: the shared
+      // memory writes then fall in distinct banks (the reads are L2 hits)
       for (int idx = lane; idx < kBatch * R; idx += 32) {
-        const int c = idx / kBatch;
-        const int j = idx % kBatch;
+        const int j = idx / R;
+        const int c = idx % R;
         const bool ok = (j < nb) && (c < r);
         const int64_t g = ok ? (int64_t)c * p.fs + row0 + j : 0;
         if constexpr (DO_U) {
@@ -230,15 +233,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       const T* sp = stages + st * STAGE_ELEMS + box * kBatch * BOXC + inbox;
       float xg[G * R];  // row sums of the current group of rows (zero for absent rows)
-#pragma unroll
-      for (int jj = 0; jj < kBatch / 2; ++jj) {
-        const int j = rg + 2 * jj;
-        float* xr = xg + (jj % G) * R;
-        if constexpr (DO_X) {
-#pragma unroll
-          for (int c = 0; c < R; ++c) xr[c] = 0.f;
-        }
-        if (j < nb) {
+      auto do_row = [&](int j, float* xr) {
           float4 v4 = *reinterpret_cast<const float4*>(sp + j * BOXC);
           if (!vec_ok) {
             v4.x = (col0 + 0 < n) ? v4.x : 0.f;
@@ -251,13 +246,22 @@ __global__ void __launch_bounds__(kThreads, 2)
             const float2 pd[COLS] = {make_float2(v4.x, v4.x), make_float2(v4.y, v4.y),
                                      make_float2(v4.z, v4.z), make_float2(v4.w, v4.w)};
             if constexpr (DO_Y) {
-              const float2* vr2 = reinterpret_cast<const float2*>(Vst + j * R);
+              float2 vv[R2];
+              if constexpr (R >= 4) {
+                const float4* vr4 = reinterpret_cast<const float4*>(Vst + j * R);
 #pragma unroll
-              for (int c2 = 0; c2 < R2; ++c2) {
-                const float2 v = vr2[c2];
-#pragma unroll
-                for (int k = 0; k < COLS; ++k) yacc2[k][c2] = __ffma2_rn(pd[k], v, yacc2[k][c2]);
+                for (int c4 = 0; c4 < R / 4; ++c4) {
+                  const float4 t = vr4[c4];
+                  vv[2 * c4] = make_float2(t.x, t.y);
+                  vv[2 * c4 + 1] = make_float2(t.z, t.w);
+                }
+              } else {
+                vv[0] = *reinterpret_cast<const float2*>(Vst + j * R);
               }
+#pragma unroll
+              for (int c2 = 0; c2 < R2; ++c2)
+#pragma unroll
+                for (int k = 0; k < COLS; ++k) yacc2[k][c2] = __ffma2_rn(pd[k], vv[c2], yacc2[k][c2]);
             }
             if constexpr (DO_X) {
               float2 x2[R2];
@@ -288,12 +292,22 @@ __global__ void __launch_bounds__(kThreads, 2)
           }
           if constexpr (DO_U) {
             float2 pn[2] = {make_float2(v4.x, v4.y), make_float2(v4.z, v4.w)};
-            const float2* ur = Ust + j * R;
+            float2 uu[R];
+            if constexpr (R >= 2) {
+              const float4* ur4 = reinterpret_cast<const float4*>(Ust + j * R);
+#pragma unroll
+              for (int c2 = 0; c2 < R / 2; ++c2) {
+                const float4 t = ur4[c2];
+                uu[2 * c2] = make_float2(t.x, t.y);
+                uu[2 * c2 + 1] = make_float2(t.z, t.w);
+              }
+            } else {
+              uu[0] = Ust[j * R];
+            }
 #pragma unroll
             for (int c = 0; c < R; ++c) {
-              const float2 u = ur[c];
-              pn[0] = __ffma2_rn(u, vw2[c][0], pn[0]);
-              pn[1] = __ffma2_rn(u, vw2[c][1], pn[1]);
+              pn[0] = __ffma2_rn(uu[c], vw2[c][0], pn[0]);
+              pn[1] = __ffma2_rn(uu[c], vw2[c][1], pn[1]);
             }
             T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
             if (vec_ok) {
@@ -305,7 +319,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                 if (col0 + k < n) dst[k] = o[k];
             }
           }
-        }
+      };
+      auto finish_group = [&](int jj) {  // after the last row of a group: one butterfly
         if constexpr (DO_X) {
           if ((jj % G) == G - 1) {
             int v = 0;
@@ -313,6 +328,31 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int jr = rg + 2 * (jj - (G - 1) + v / R);  // batch row of value v
             if ((lane % (32 / (G * R))) == 0) Xw[((st * kBatch + jr) * 4 + wq) * R + (v % R)] = tot;
           }
+        }
+      };
+      // full batch: no per-row guards so that rows interleave (R <= 4; at R = 8
+      // the extra live registers would spill)
+      if (R <= 4 && nb == kBatch) {
+#pragma unroll
+        for (int jj = 0; jj < kBatch / 2; ++jj) {
+          float* xr = xg + (jj % G) * R;
+          if constexpr (DO_X) {
+#pragma unroll
+            for (int c = 0; c < R; ++c) xr[c] = 0.f;
+          }
+          do_row(rg + 2 * jj, xr);
+          finish_group(jj);
+        }
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < kBatch / 2; ++jj) {
+          float* xr = xg + (jj % G) * R;
+          if constexpr (DO_X) {
+#pragma unroll
+            for (int c = 0; c < R; ++c) xr[c] = 0.f;
+          }
+          if (rg + 2 * jj < nb) do_row(rg + 2 * jj, xr);
+          finish_group(jj);
         }
       }
     }
@@ -415,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * S * STAGE_ELEMS);
   uint64_t* empty = full + S;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
-  float2* Us2 = reinterpret_cast<float2*>(empty + S + 1);  // [S][kBatch][R] (u, u)
+  float2* Us2 = reinterpret_cast<float2*>(empty + S + 2);  // [S][kBatch][R] (u, u), 16-B aligned
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -454,9 +494,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int st = b % S;
     const int row0 = rb + b * kBatch;
     const int nb = min(kBatch, re - row0);
-    for (int idx = lane; idx < kBatch * R; idx += 32) {
-      const int c = idx / kBatch;
-      const int j = idx % kBatch;
+    for (int idx = lane; idx < kBatch * R; idx += 32) {  // lanes over columns (see above)
+      const int j = idx / R;
+      const int c = idx % R;
       const bool ok = (j < nb) && (c < r);
       const int64_t g = ok ? (int64_t)c * p.fs + row0 + j : 0;
       float* d = reinterpret_cast<float*>(Us2 + (st * kBatch + j) * R + c);
@@ -522,10 +562,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (ready && any_col) {
       const T* sp = stages + st * STAGE_ELEMS + box * kBatch * BOXC + inbox;
       const float2* Ust = Us2 + st * kBatch * R;
-#pragma unroll
-      for (int jj = 0; jj < kBatch / GROUPS; ++jj) {
-        const int j = rg + GROUPS * jj;
-        if (j < nb) {
+      auto row = [&](int j) {
           float2 pv[M];
           if constexpr (COLS == 4) {
             const float4 v4 = *reinterpret_cast<const float4*>(sp + j * BOXC);
@@ -534,13 +571,22 @@ __global__ void __launch_bounds__(kThreads, 2)
           } else {
             pv[0] = *reinterpret_cast<const float2*>(sp + j * BOXC);
           }
-          const float2* ur = Ust + j * R;
+          float2 uu[R];
+          if constexpr (R >= 2) {
+            const float4* ur4 = reinterpret_cast<const float4*>(Ust + j * R);
 #pragma unroll
-          for (int c = 0; c < R; ++c) {
-            const float2 u = ur[c];
-#pragma unroll
-            for (int m = 0; m < M; ++m) pv[m] = __ffma2_rn(u, w2[c][m], pv[m]);
+            for (int c2 = 0; c2 < R / 2; ++c2) {
+              const float4 t = ur4[c2];
+              uu[2 * c2] = make_float2(t.x, t.y);
+              uu[2 * c2 + 1] = make_float2(t.z, t.w);
+            }
+          } else {
+            uu[0] = Ust[j * R];
           }
+#pragma unroll
+          for (int c = 0; c < R; ++c)
+#pragma unroll
+            for (int m = 0; m < M; ++m) pv[m] = __ffma2_rn(uu[c], w2[c][m], pv[m]);
           T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
           if (vec_ok) {
             if constexpr (COLS == 4)
@@ -554,7 +600,14 @@ __global__ void __launch_bounds__(kThreads, 2)
             for (int k = 0; k < COLS; ++k)
               if (col0 + k < n) dst[k] = o[k];
           }
-        }
+      };
+      if (nb == kBatch) {  // full batch: no per-row guards, rows interleave
+#pragma unroll
+        for (int jj = 0; jj < kBatch / GROUPS; ++jj) row(rg + GROUPS * jj);
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < kBatch / GROUPS; ++jj)
+          if (rg + GROUPS * jj < nb) row(rg + GROUPS * jj);
       }
     }
     __syncwarp();
