@@ -196,6 +196,16 @@ const char* linview_last_error(void);
  */
 linview_status linview_adjoint_iteration(linview_program* prog, void* dA, int64_t ld_dA, void* dB,
                                          int64_t ld_dB, void* stream);
+/*
+ * linview_adjoint_iteration_seed: the same reverse pass from an arbitrary
+ * upstream gradient Gk = dL/dT_k (device, n x p, row-major, ldg >= p) instead
+ * of 2 T_k: G_k = Gk, G_i = A^T G_{i+1}; dA = sum_i G_i T_{i-1}^T,
+ * dB = sum_i G_i, dT0 (n x p, may be NULL) = A^T G_1.  This is the vector-
+ * Jacobian product of the map (A, B, T_0) -> T_k, for reverse-mode autodiff.
+ */
+linview_status linview_adjoint_iteration_seed(linview_program* prog, const void* Gk, int64_t ldg,
+                                              void* dA, int64_t ld_dA, void* dB, int64_t ld_dB,
+                                              void* dT0, int64_t ld_dT0, void* stream);
 linview_status linview_adjoint_power(linview_program* prog, const void* G, int64_t ldg, void* dA,
                                      int64_t ld_dA, void* stream);
 
@@ -252,6 +262,124 @@ linview_status linview_set_profiling(linview_program* prog, int enable);
 linview_status linview_pass_stats(linview_program* prog, int kernel, int64_t* launches, double* ms,
                                   double* bytes, int64_t* all_launches);
 linview_status linview_reset_stats(linview_program* prog);
+
+/*
+ * Device memory of a program.  linview_program_device_bytes: the bytes the
+ * program holds (the sum of its device allocations: views, factor arenas,
+ * partial sums, staging).  linview_estimate_device_bytes: the same figure for
+ * a LINVIEW_POWER or LINVIEW_POWER_SUM program that linview_create_program
+ * would build from ``desc`` on the current device, without allocating
+ * (other kinds return LINVIEW_EUNSUPPORTED).
+ */
+linview_status linview_program_device_bytes(const linview_program* prog, int64_t* bytes);
+linview_status linview_estimate_device_bytes(const linview_program_desc* desc, int64_t* bytes);
+
+/*
+ * Serving: many maintained matrix-power programs (Section 4.2, A^k by
+ * repeated squaring, FP32) kept resident in device memory under a stream of
+ * factored updates dA = U V^T (Section 3.2: updates and deltas in factored
+ * form) that arrive over time, with continuous batching:
+ *  - a scheduler thread owned by the server takes queued requests as soon as
+ *    a slot is free (at most ``max_inflight`` views refreshing at once, each
+ *    on its own CUDA stream, so their work overlaps on the GPU);
+ *  - the requests queued for one view while it is busy are coalesced into a
+ *    single delta of higher rank, [U_1 .. U_m][V_1 .. V_m]^T = sum_j U_j V_j^T
+ *    (the concatenation rule of factored deltas, Section 3.2; the paper's
+ *    batch updates, Section 6, Table 4), as long as the total rank stays
+ *    within ``r_cap``; the rest waits for the next refresh of that view;
+ *  - a view is admitted (its program created) only when its device bytes
+ *    (linview_estimate_device_bytes) fit both the server budget and the free
+ *    device memory; otherwise it waits, with its requests queued, and is
+ *    admitted when a removed view frees memory.
+ * Times are seconds on the server clock (a monotonic clock started by
+ * linview_server_create; linview_server_clock reads it).  Latency of a
+ * request = done_s - arrival_s, where done_s is when the scheduler saw the
+ * refresh's completion event.
+ *
+ * linview_server_create: hbm_budget_bytes <= 0 means the free device memory
+ *   at creation minus 1 GiB; max_inflight >= 1; 1 <= r_cap and r_cap * k <= 128
+ *   for every view.  Uses the current device.
+ * linview_server_add_view: A is n x n FP32 row-major (lda), host or device;
+ *   the server copies it before returning.  *view receives the view id; the
+ *   view is admitted at once if memory allows (state 1), else it waits
+ *   (state 0).  k is a power of two.  The view's program ids are those of a
+ *   LINVIEW_POWER program: 0 = A, j = A^(2^j).
+ * linview_server_submit: one request dA = U V^T for ``view``; U, V are n x
+ *   rank FP32 row-major host arrays (ldu, ldv >= rank), copied before the
+ *   call returns; 1 <= rank <= r_cap, else LINVIEW_ERANK.  arrival_s < 0
+ *   stamps the current server time.  *ticket receives the request id
+ *   (tickets count from 1 in submission order).
+ * linview_server_replay: open-loop load for measurement.  The calling thread
+ *   submits request i at server time t0 + t_s[i] (t0 = the time of the call,
+ *   t_s non-decreasing) with arrival_s = t0 + t_s[i], and returns after the
+ *   last one.  Its factors are NOT copied: U_i is the n_view x rank[i]
+ *   row-major array at factors + offset[i] (floats), V_i follows it
+ *   directly; the caller keeps ``factors`` alive until linview_server_drain
+ *   returns.
+ * linview_server_poll: moves up to ``max`` completion records (oldest first)
+ *   to ``out``; *count receives how many.  Never blocks.
+ * linview_server_drain: waits until every request submitted so far has
+ *   completed (LINVIEW_ETIMEOUT after timeout_s seconds; timeout_s <= 0
+ *   waits without limit).
+ * linview_server_view_state: 0 waiting for admission, 1 resident, 2 removed.
+ * linview_server_view_program: the program of a resident view, for
+ *   linview_read_view & co.  Only valid while the view is resident; read it
+ *   only after linview_server_drain (the scheduler thread issues its work).
+ * linview_server_remove_view: the scheduler lets the view's refresh in flight
+ *   finish, completes its still-queued requests with status LINVIEW_EINVAL,
+ *   destroys the program and admits waiting views that now fit.  Returns
+ *   at once; the view's state turns 2 when it is gone.
+ * linview_server_stats: counters since creation (see the struct).
+ * linview_server_destroy: stops the scheduler after the refreshes in flight
+ *   have finished (queued requests are dropped) and frees every view.
+ * A refresh that fails on the device reports its status in the completion
+ * records of its requests; the view stays resident.
+ */
+typedef struct linview_server linview_server; /* opaque, library-owned */
+
+typedef struct {
+  uint64_t ticket;     /* request id from submit / replay order */
+  int32_t view;        /* view id */
+  int32_t rank;        /* rank of this request */
+  int32_t batch_rank;  /* rank of the coalesced delta the request was applied in */
+  int32_t batch_size;  /* requests coalesced into that delta */
+  int32_t status;      /* linview_status of the refresh */
+  int32_t reserved;
+  double arrival_s;    /* server time the request arrived */
+  double start_s;      /* server time its refresh was issued */
+  double done_s;       /* server time its refresh was seen complete */
+} linview_completion;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  int64_t refreshes;          /* coalesced deltas applied */
+  int64_t coalesced_rank_sum; /* sum of their ranks */
+  int32_t views_resident, views_waiting;
+  int32_t max_inflight_seen;  /* most views refreshing at the same time */
+  int32_t reserved;
+  int64_t bytes_used, bytes_budget;
+} linview_server_stats;
+
+linview_status linview_server_create(int64_t hbm_budget_bytes, int32_t max_inflight, int32_t r_cap,
+                                     linview_server** out);
+linview_status linview_server_add_view(linview_server* srv, int64_t n, int32_t k, const void* A,
+                                       int64_t lda, int on_device, int32_t* view);
+linview_status linview_server_submit(linview_server* srv, int32_t view, int32_t rank, const void* U,
+                                     int64_t ldu, const void* V, int64_t ldv, double arrival_s,
+                                     uint64_t* ticket);
+linview_status linview_server_replay(linview_server* srv, int64_t count, const double* t_s,
+                                     const int32_t* view, const int32_t* rank, const void* factors,
+                                     const int64_t* offset);
+linview_status linview_server_poll(linview_server* srv, linview_completion* out, int32_t max,
+                                   int32_t* count);
+linview_status linview_server_drain(linview_server* srv, double timeout_s);
+linview_status linview_server_view_state(linview_server* srv, int32_t view, int32_t* state);
+linview_status linview_server_view_program(linview_server* srv, int32_t view,
+                                           linview_program** prog);
+linview_status linview_server_remove_view(linview_server* srv, int32_t view);
+linview_status linview_server_stats_get(linview_server* srv, linview_server_stats* out);
+double linview_server_clock(const linview_server* srv);
+void linview_server_destroy(linview_server* srv);
 
 #ifdef __cplusplus
 }

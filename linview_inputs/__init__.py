@@ -24,6 +24,15 @@ Recipes (all FP64 draws from numpy's PCG64 ``default_rng``; a workload-level
   update replaces k distinct rows of X by fresh rows drawn the same way (same
   scaled columns), Y unchanged (OLS, Section 4.1).
 
+* ``serving_views`` / ``serving_trace``: many maintained A^k views with n drawn
+  uniformly from a size set, and an open-loop request trace: Poisson arrivals
+  (exponential gaps at ``rate`` per second), target view uniform, rank
+  uniform in 1..r_hi, U and V i.i.d. N(0, sigma^2); the factors of all
+  requests packed in one float32 array (U_i then V_i, each n x rank
+  row-major).  The paper streams rank-1 updates and batches of updates
+  (Section 6); the rate sweep and the mix of sizes are this build's serving
+  workload.
+
 ``dtype`` rounds the FP64 draw to nearest in the requested type; consumers that
 compare against the FP64 oracle promote the rounded values back to FP64, so the
 comparison measures the method's error and not input quantisation.
@@ -43,6 +52,8 @@ _STREAM_OLS_Y = 6
 _STREAM_OLS_COLS = 7
 _STREAM_OLS_UPD = 8
 _STREAM_MISC = 9
+_STREAM_SERVE_SIZES = 10
+_STREAM_SERVE_TRACE = 11
 
 
 def rng(seed: int, stream: int) -> np.random.Generator:
@@ -141,3 +152,33 @@ def normal(shape, seed: int = 0, stream: int = _STREAM_MISC, scale: float = 1.0,
            dtype=np.float64) -> np.ndarray:
     """Generic i.i.d. N(0, scale^2) array (test helpers, FD directions)."""
     return _cast(scale * rng(seed, stream).standard_normal(shape), dtype)
+
+
+def serving_views(count: int, sizes=(1024, 2048, 4096, 8192), seed: int = 0):
+    """Sizes n of ``count`` views, each drawn uniformly from ``sizes``."""
+    g = rng(seed, _STREAM_SERVE_SIZES)
+    return [int(sizes[i]) for i in g.integers(0, len(sizes), size=count)]
+
+
+def serving_trace(view_sizes, count: int, rate: float, seed: int = 0, r_hi: int = 8,
+                  sigma: float = 0.01):
+    """Open-loop trace of ``count`` requests over views with sizes
+    ``view_sizes``: (t_s, views, ranks, factors, offsets), t_s in seconds
+    from the start; request i's U is factors[offsets[i]:][:n*rank] (n x rank
+    row-major) and its V the n*rank floats after it."""
+    g = rng(seed, _STREAM_SERVE_TRACE)
+    gaps = g.exponential(1.0 / rate, size=count)
+    t_s = np.cumsum(gaps) - gaps[0]
+    views = g.integers(0, len(view_sizes), size=count).astype(np.int32)
+    ranks = g.integers(1, r_hi + 1, size=count).astype(np.int32)
+    sizes = np.array([2 * view_sizes[v] * r for v, r in zip(views, ranks)], dtype=np.int64)
+    offsets = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+    factors = (sigma * g.standard_normal(int(sizes.sum()))).astype(np.float32)
+    return t_s.astype(np.float64), views, ranks, factors, offsets
+
+
+def trace_factors(view_sizes, views, ranks, factors, offsets, i: int):
+    """(U_i, V_i) of request i of a ``serving_trace`` (views into ``factors``)."""
+    n, r, o = view_sizes[views[i]], int(ranks[i]), int(offsets[i])
+    return factors[o:o + n * r].reshape(n, r), factors[o + n * r:o + 2 * n * r].reshape(n, r)
+

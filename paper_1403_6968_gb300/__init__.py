@@ -6,5 +6,6 @@ the C ABI in ``include/linview.h``); ``linview`` is a thin ctypes binding that
 marshals torch tensors and streams.  Build with ``python -m
 paper_1403_6968_gb300.build``.
 """
-from .linview import Program, LinviewError, level_pass, level_pass_noalloc  # noqa: F401
+from .linview import (Program, LinviewError, Server, level_pass, level_pass_noalloc,  # noqa: F401
+                      estimate_device_bytes, program_device_bytes)
 from . import _lib  # noqa: F401

@@ -37,6 +37,37 @@ class ProgramDesc(C.Structure):
     ]
 
 
+class Completion(C.Structure):
+    _fields_ = [
+        ("ticket", C.c_uint64),
+        ("view", C.c_int32),
+        ("rank", C.c_int32),
+        ("batch_rank", C.c_int32),
+        ("batch_size", C.c_int32),
+        ("status", C.c_int32),
+        ("reserved", C.c_int32),
+        ("arrival_s", C.c_double),
+        ("start_s", C.c_double),
+        ("done_s", C.c_double),
+    ]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [
+        ("submitted", C.c_int64),
+        ("completed", C.c_int64),
+        ("failed", C.c_int64),
+        ("refreshes", C.c_int64),
+        ("coalesced_rank_sum", C.c_int64),
+        ("views_resident", C.c_int32),
+        ("views_waiting", C.c_int32),
+        ("max_inflight_seen", C.c_int32),
+        ("reserved", C.c_int32),
+        ("bytes_used", C.c_int64),
+        ("bytes_budget", C.c_int64),
+    ]
+
+
 class LinviewError(RuntimeError):
     def __init__(self, status: int, fn: str, msg: str):
         name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
@@ -67,6 +98,7 @@ _SIGS = [
     ("linview_destroy", None, [_P]),
     ("linview_last_error", C.c_char_p, []),
     ("linview_adjoint_iteration", _I, [_P, _P, _I64, _P, _I64, _P]),
+    ("linview_adjoint_iteration_seed", _I, [_P, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P]),
     ("linview_adjoint_power", _I, [_P, _P, _I64, _P, _I64, _P]),
     ("linview_level_pass", _I, [_I, _I64, _P, _I64, _P, _P, _I64, _I64, _P, _P, _I, _P]),
     ("linview_level_pass_noalloc", _I, [_I, _I64, _P, _I64, _P, _P, _I64, _I64, _P, _P, _I, _P]),
@@ -74,6 +106,21 @@ _SIGS = [
     ("linview_pass_stats", _I, [_P, _I, C.POINTER(_I64), C.POINTER(C.c_double),
                                 C.POINTER(C.c_double), C.POINTER(_I64)]),
     ("linview_reset_stats", _I, [_P]),
+    ("linview_program_device_bytes", _I, [_P, C.POINTER(_I64)]),
+    ("linview_estimate_device_bytes", _I, [C.POINTER(ProgramDesc), C.POINTER(_I64)]),
+    ("linview_server_create", _I, [_I64, C.c_int32, C.c_int32, C.POINTER(_P)]),
+    ("linview_server_add_view", _I, [_P, _I64, C.c_int32, _P, _I64, _I, C.POINTER(C.c_int32)]),
+    ("linview_server_submit", _I, [_P, C.c_int32, C.c_int32, _P, _I64, _P, _I64, C.c_double,
+                                   C.POINTER(C.c_uint64)]),
+    ("linview_server_replay", _I, [_P, _I64, _P, _P, _P, _P, _P]),
+    ("linview_server_poll", _I, [_P, _P, C.c_int32, C.POINTER(C.c_int32)]),
+    ("linview_server_drain", _I, [_P, C.c_double]),
+    ("linview_server_view_state", _I, [_P, C.c_int32, C.POINTER(C.c_int32)]),
+    ("linview_server_view_program", _I, [_P, C.c_int32, C.POINTER(_P)]),
+    ("linview_server_remove_view", _I, [_P, C.c_int32]),
+    ("linview_server_stats_get", _I, [_P, _P]),
+    ("linview_server_clock", C.c_double, [_P]),
+    ("linview_server_destroy", None, [_P]),
 ]
 
 EXPORTED = [s[0] for s in _SIGS]

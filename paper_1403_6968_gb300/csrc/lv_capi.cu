@@ -93,6 +93,7 @@ struct linview_program {
   cublasHandle_t blas = nullptr;
   cusolverDnHandle_t solver = nullptr;
   std::vector<void*> allocs;
+  int64_t bytes = 0;  // sum of the device allocations in allocs
   std::vector<View> views;
   int L = 0;  // log2 k for powers
   // factor arenas
@@ -180,9 +181,23 @@ static linview_status dalloc(linview_program* p, size_t bytes, void** out) {
     return fail(LINVIEW_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
   }
   p->allocs.push_back(ptr);
+  p->bytes += (int64_t)bytes;
   LV_CUDA(cudaMemset(ptr, 0, bytes));
   *out = ptr;
   return LINVIEW_OK;
+}
+
+// partial factor cores: one 64 x 64 block per gram CTA, or one r_h^2 <= 64
+// block per row range of a fused pass (>= 2 CTAs per SM on any current part)
+static size_t cpart_bytes(int64_t n) {
+  const int sms_guess = 2 * 256;
+  const size_t cp = (size_t)64 * 64 * gram_grid((int)n);
+  const size_t cf = (size_t)64 * sms_guess;
+  return sizeof(double) * (cp > cf ? cp : cf);
+}
+
+static int64_t square_view_bytes(int64_t n, int elem) {
+  return rup(n, kBatch) * rup(n, 256) * elem;
 }
 
 static linview_status add_square_view(linview_program* p, int64_t n) {
@@ -191,7 +206,7 @@ static linview_status add_square_view(linview_program* p, int64_t n) {
   v.cols = n;
   v.ld = rup(n, 256);
   const int64_t rows_pad = rup(n, kBatch);
-  LV_TRY(dalloc(p, (size_t)(rows_pad * v.ld * p->elem), &v.ptr));
+  LV_TRY(dalloc(p, (size_t)square_view_bytes(n, p->elem), &v.ptr));
   v.square = true;
   if (!make_tmap(&v.tmap, v.ptr, p->elem, v.ld, rows_pad, v.ld))
     return fail(LINVIEW_EDEVICE, "cuTensorMapEncodeTiled failed for an %lld x %lld view",
@@ -439,6 +454,34 @@ static linview_status powers_reeval(linview_program* p, cudaStream_t s) {
   return LINVIEW_OK;
 }
 
+// sums programs apply their block-triangular core inside one update pass
+// when the whole factor fits one pass; wider factors get an explicit
+// suffix-sum factor (see sums_update)
+static bool powers_wide_sums(const linview_program_desc& d) {
+  const int64_t mu = d.precision == LINVIEW_F64 ? 32 : 64;
+  return d.kind == LINVIEW_POWER_SUM && ((int64_t)d.r_max * d.k > mu || d.r_max > 8);
+}
+
+// Device bytes powers_create allocates (with the buffers every program has),
+// in the same order; linview_estimate_device_bytes reports it.
+static int64_t powers_device_bytes(const linview_program_desc& d, int sms) {
+  const int elem = d.precision == LINVIEW_F64 ? 8 : 4;
+  const int64_t n = d.n;
+  const int L = ilog2(d.k);
+  int64_t b = (int64_t)sizeof(unsigned) * 4 + (int64_t)sizeof(double) * 64 * 64 +
+              (int64_t)cpart_bytes(n);
+  const int nviews = L + 1 + (d.kind == LINVIEW_POWER_SUM ? L : 0);
+  b += nviews * square_view_bytes(n, elem);
+  const int64_t Rcap = (int64_t)d.r_max * d.k;
+  const int64_t fs = rup(n, 64);
+  b += (powers_wide_sums(d) ? 3 : 2) * fs * Rcap * elem;
+  const PassGeom g = fused_geom(elem, (int)n, sms);
+  const int64_t half = Rcap / 2 > 0 ? Rcap / 2 : 1;
+  b += (int64_t)g.gC * half * fs * elem + (int64_t)g.gR * half * fs * elem;
+  b += 2 * n * d.r_max * elem;
+  return b;
+}
+
 static linview_status powers_create(linview_program* p, const void* const* inputs,
                                     const int64_t* lds, int on_dev, cudaStream_t s) {
   const int64_t n = p->d.n;
@@ -448,12 +491,7 @@ static linview_status powers_create(linview_program* p, const void* const* input
   if ((int64_t)p->d.r_max * k > 128)
     return fail(LINVIEW_EUNSUPPORTED, "r_max*k=%lld exceeds 128 (factor cores are at most 64x64)",
                 (long long)p->d.r_max * k);
-  // the sums views apply their block-triangular core inside one update pass
-  // when the whole factor fits one pass; wider factors get an explicit
-  // suffix-sum factor (see sums_update)
-  const int64_t mu = p->elem == 4 ? 64 : 32;
-  const bool wide_sums =
-      p->d.kind == LINVIEW_POWER_SUM && ((int64_t)p->d.r_max * k > mu || p->d.r_max > 8);
+  const bool wide_sums = powers_wide_sums(p->d);
   if (lds[0] < n) return fail(LINVIEW_ESHAPE, "ld of A (%lld) < n", (long long)lds[0]);
   for (int l = 0; l <= p->L; ++l) LV_TRY(add_square_view(p, n));
   if (p->d.kind == LINVIEW_POWER_SUM)
@@ -472,6 +510,9 @@ static linview_status powers_create(linview_program* p, const void* const* input
   p->yp_q = (int64_t)half * p->part_cs;
   LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart));
   LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart));
+  // host-side update factors are staged here (allocated now so that an
+  // update never allocates)
+  LV_TRY(ensure_stage(p, (size_t)2 * n * p->d.r_max * p->elem));
   return powers_reeval(p, s);
 }
 
@@ -907,10 +948,7 @@ linview_status linview_create_program(const linview_program_desc* desc, const vo
   }
   if (st == LINVIEW_OK) {
     void* tmp = nullptr;
-    const int sms_guess = 2 * 256;  // >= 2 CTAs per SM for any current part
-    const size_t cp = (size_t)64 * 64 * gram_grid((int)desc->n);
-    const size_t cf = (size_t)64 * sms_guess;
-    st = dalloc(p, sizeof(double) * (cp > cf ? cp : cf), &tmp);
+    st = dalloc(p, cpart_bytes(desc->n), &tmp);
     p->Cpart = static_cast<double*>(tmp);
   }
   if (st == LINVIEW_OK) {
@@ -946,6 +984,32 @@ void linview_destroy(linview_program* p) {
   if (p->blas) cublasDestroy(p->blas);
   if (p->solver) cusolverDnDestroy(p->solver);
   delete p;
+}
+
+linview_status linview_program_device_bytes(const linview_program* p, int64_t* bytes) {
+  if (!p || !bytes) return fail(LINVIEW_EINVAL, "null argument");
+  *bytes = p->bytes;
+  return LINVIEW_OK;
+}
+
+linview_status linview_estimate_device_bytes(const linview_program_desc* d, int64_t* bytes) {
+  if (!d || !bytes) return fail(LINVIEW_EINVAL, "null argument");
+  if (d->kind != LINVIEW_POWER && d->kind != LINVIEW_POWER_SUM)
+    return fail(LINVIEW_EUNSUPPORTED, "estimate only for power programs");
+  if (d->precision != LINVIEW_F32 && d->precision != LINVIEW_F64)
+    return fail(LINVIEW_EINVAL, "bad precision %d", d->precision);
+  if (d->n < 1 || d->n > (1 << 20)) return fail(LINVIEW_EINVAL, "bad n=%lld", (long long)d->n);
+  if (!is_pow2(d->k)) return fail(LINVIEW_EINVAL, "k=%d must be a power of two", d->k);
+  if (d->r_max < 1 || (int64_t)d->r_max * d->k > 128)
+    return fail(LINVIEW_EUNSUPPORTED, "r_max*k must be in 1..128");
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(LINVIEW_EDEVICE, "no CUDA device");
+  }
+  *bytes = powers_device_bytes(*d, sms);
+  return LINVIEW_OK;
 }
 
 int linview_num_views(const linview_program* p) { return p ? (int)p->views.size() : 0; }
@@ -1202,13 +1266,17 @@ linview_status linview_sync(linview_program* p, void* stream) {
 }
 
 // ---------------------------------------------------------------- adjoints
-linview_status linview_adjoint_iteration(linview_program* p, void* dA, int64_t ld_dA, void* dB,
-                                         int64_t ld_dB, void* stream) {
+// Reverse pass of T_i = A T_{i-1} + B, i = 1..k, from the seed G_k = dL/dT_k
+// (Gk, or 2 T_k when Gk is NULL: L = ||T_k||_F^2).
+static linview_status adjoint_iteration(linview_program* p, const void* Gk, int64_t ldg, void* dA,
+                                        int64_t ld_dA, void* dB, int64_t ld_dB, void* dT0,
+                                        int64_t ld_dT0, void* stream) {
   if (!p) return fail(LINVIEW_EINVAL, "null program");
   if (p->d.kind != LINVIEW_ITERATION) return fail(LINVIEW_EINVAL, "not an iteration program");
   const int64_t n = p->d.n, pp = p->d.p;
   const int k = p->d.k;
-  if ((dA && ld_dA < n) || (dB && ld_dB < pp)) return fail(LINVIEW_ESHAPE, "bad leading dims");
+  if ((dA && ld_dA < n) || (dB && ld_dB < pp) || (Gk && ldg < pp) || (dT0 && ld_dT0 < pp))
+    return fail(LINVIEW_ESHAPE, "bad leading dims");
   LV_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!p->Gpanel) {
@@ -1220,15 +1288,18 @@ linview_status linview_adjoint_iteration(linview_program* p, void* dA, int64_t l
   char* G = static_cast<char*>(p->Gpanel);
   char* T = static_cast<char*>(p->Tpanel);
   View& a = p->views[0];
-  // G_k = 2 T_k; G_i = A^T G_{i+1}
+  // G_k = seed; G_i = A^T G_{i+1}
   void* gk = G + (size_t)(k - 1) * pp * e;
-  void* tk = T + (size_t)k * pp * e;
+  const void* src = Gk ? Gk : T + (size_t)k * pp * e;
+  const int64_t lds = Gk ? ldg : p->ldT;
   if (e == 4)
-    LV_CUDA(launch_scale_copy<float>(static_cast<float*>(gk), p->ldG, static_cast<float*>(tk),
-                                     p->ldT, 2.0f, (int)n, (int)pp, s));
+    LV_CUDA(launch_scale_copy<float>(static_cast<float*>(gk), p->ldG,
+                                     static_cast<const float*>(src), lds, Gk ? 1.0f : 2.0f,
+                                     (int)n, (int)pp, s));
   else
-    LV_CUDA(launch_scale_copy<double>(static_cast<double*>(gk), p->ldG, static_cast<double*>(tk),
-                                      p->ldT, 2.0, (int)n, (int)pp, s));
+    LV_CUDA(launch_scale_copy<double>(static_cast<double*>(gk), p->ldG,
+                                      static_cast<const double*>(src), lds, Gk ? 1.0 : 2.0,
+                                      (int)n, (int)pp, s));
   p->all_launches++;
   for (int i = k - 1; i >= 1; --i) {
     void* gi = G + (size_t)(i - 1) * pp * e;
@@ -1254,7 +1325,24 @@ linview_status linview_adjoint_iteration(linview_program* p, void* dA, int64_t l
     LV_TRY(gemm_rm(p, false, true, n, n, (int64_t)k * pp, 1.0, G, p->ldG, T, p->ldT, 0.0, dA,
                    ld_dA, s, mode));
   }
+  if (dT0) {
+    // dL/dT_0 = A^T G_1
+    LV_TRY(gemm_rm(p, true, false, n, pp, n, 1.0, a.ptr, a.ld, G, p->ldG, 0.0, dT0, ld_dT0, s,
+                   mode));
+  }
   return LINVIEW_OK;
+}
+
+linview_status linview_adjoint_iteration(linview_program* p, void* dA, int64_t ld_dA, void* dB,
+                                         int64_t ld_dB, void* stream) {
+  return adjoint_iteration(p, nullptr, 0, dA, ld_dA, dB, ld_dB, nullptr, 0, stream);
+}
+
+linview_status linview_adjoint_iteration_seed(linview_program* p, const void* Gk, int64_t ldg,
+                                              void* dA, int64_t ld_dA, void* dB, int64_t ld_dB,
+                                              void* dT0, int64_t ld_dT0, void* stream) {
+  if (!Gk) return fail(LINVIEW_EINVAL, "null seed");
+  return adjoint_iteration(p, Gk, ldg, dA, ld_dA, dB, ld_dB, dT0, ld_dT0, stream);
 }
 
 linview_status linview_adjoint_power(linview_program* p, const void* G, int64_t ldg, void* dA,

@@ -490,16 +490,17 @@ PassGeom update_geom(int elem_bytes, int R, int n, int num_sms) {
 
 bool make_tmap(CUtensorMap* out, const void* base, int elem_bytes, int64_t cols, int64_t rows,
                int64_t ld) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // looked up once (thread-safe static initialisation)
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
                                          &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return false;
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * elem_bytes)};
   cuuint32_t box[2] = {(cuuint32_t)(kBoxBytes / elem_bytes), (cuuint32_t)kBatch};
@@ -520,7 +521,7 @@ static cudaError_t launch_fused_t(const PassParams& p, const CUtensorMap& tm, cu
   constexpr bool kWs = std::is_same<T, float>::value;
   const size_t smem =
       kWs ? sizeof(T) * kStagesWs * kBatch * STRIP + sizeof(uint64_t) * (2 * kStagesWs + 2) +
-                kStagesWs * kBatch * R * (sizeof(float2) + sizeof(float) + 4 * sizeof(float)) +
+                kStagesWs * kBatch * R * (sizeof(float) + sizeof(float) + 4 * sizeof(float)) +
                 sizeof(double) * kThreads
           : sizeof(T) * kStages * kBatch * STRIP + sizeof(uint64_t) * kStages +
                 sizeof(T) * (2 * kBatch * R + kBatch * R * (128 + 32 / R)) +
@@ -530,13 +531,10 @@ static cudaError_t launch_fused_t(const PassParams& p, const CUtensorMap& tm, cu
     kfn = fused_ws_kernel<R, MODE>;
   else
     kfn = fused_pass_kernel<T, R, MODE>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // set once per kernel instance (thread-safe static initialisation)
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (configured != cudaSuccess) return configured;
   kfn<<<p.gC * p.gR, kThreads, smem, s>>>(tm, p);
   return cudaGetLastError();
 }
@@ -569,7 +567,7 @@ static cudaError_t launch_update_t(const PassParams& p, const CUtensorMap& tm, c
   constexpr bool kWs = std::is_same<T, float>::value && COLS >= 2;
   const size_t smem =
       kWs ? sizeof(T) * kStagesWs * kBatch * STRIP + sizeof(uint64_t) * (2 * kStagesWs + 2) +
-                sizeof(float2) * kStagesWs * kBatch * R
+                sizeof(float) * kStagesWs * kBatch * R
           : sizeof(T) * kStages * kBatch * STRIP + sizeof(uint64_t) * kStages +
                 sizeof(T) * kBatch * R;
   void (*kfn)(const CUtensorMap, const PassParams);
@@ -577,13 +575,10 @@ static cudaError_t launch_update_t(const PassParams& p, const CUtensorMap& tm, c
     kfn = update_ws_kernel<R, COLS>;
   else
     kfn = update_pass_kernel<T, R, COLS>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // set once per kernel instance (thread-safe static initialisation)
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (configured != cudaSuccess) return configured;
   kfn<<<p.gC * p.gR, kThreads, smem, s>>>(tm, p);
   return cudaGetLastError();
 }

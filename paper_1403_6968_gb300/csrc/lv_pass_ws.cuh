@@ -58,10 +58,56 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
   return false;
 }
 
+// One row of the in-place rank-R update p_k + sum_c u_c W(col_k, c) for the
+// COLS columns of a thread.  R >= 2: the staged row u (16-byte aligned) is
+// read once and the FMAs are paired over factor columns, (u_c, u_c+1) *
+// (W(col_k, c), W(col_k, c+1)), accumulated from (p_k, 0) in increasing c
+// and finished as even + odd: a fixed order, so results are reproducible.
+// R = 1: one FMA per entry, two columns per packed FMA.
+template <int R, int COLS>
+__device__ __forceinline__ void rank_update_row(const float* u, const float (&pv)[COLS],
+                                                const float2 (&wp)[COLS][R >= 2 ? R / 2 : 1],
+                                                float (&out)[COLS]) {
+  if constexpr (R == 1) {
+    const float2 uu = make_float2(u[0], u[0]);
+#pragma unroll
+    for (int m = 0; m < COLS / 2; ++m) {
+      const float2 t = __ffma2_rn(uu, wp[m][0], make_float2(pv[2 * m], pv[2 * m + 1]));
+      out[2 * m] = t.x;
+      out[2 * m + 1] = t.y;
+    }
+  } else {
+    float2 uu[R / 2];
+    if constexpr (R >= 4) {
+      const float4* u4 = reinterpret_cast<const float4*>(u);
+#pragma unroll
+      for (int c4 = 0; c4 < R / 4; ++c4) {
+        const float4 t = u4[c4];
+        uu[2 * c4] = make_float2(t.x, t.y);
+        uu[2 * c4 + 1] = make_float2(t.z, t.w);
+      }
+    } else {
+      uu[0] = *reinterpret_cast<const float2*>(u);
+    }
+#pragma unroll
+    for (int k = 0; k < COLS; ++k) {
+      float2 acc = make_float2(pv[k], 0.f);
+#pragma unroll
+      for (int c2 = 0; c2 < R / 2; ++c2) acc = __ffma2_rn(uu[c2], wp[k][c2], acc);
+      out[k] = acc.x + acc.y;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Fused products (+ update) pass, FP32, R in {1, 2, 4, 8}.
-// Thread (rg = warp / 4, tc = tid % 128) owns columns strip0 + 4 tc .. +3 and
-// processes rows rg, rg+2, rg+4, rg+6 of every batch.
+// Thread (rg = warp / 4, tc = tid % 128) owns columns strip0 + 4 tc .. +3.
+//  R <= 2: row group rg takes rows rg, rg+2, rg+4, rg+6 of every batch (all
+//          R factor columns);
+//  R >= 4 (SPLIT): row group rg takes the products P U and P^T V of factor
+//          columns rg R/2 .. rg R/2 + R/2 - 1 on all 8 rows of the batch, and
+//          the in-place update of rows 4 rg .. 4 rg + 3; this halves the
+//          column factors each thread keeps in registers.
 // ---------------------------------------------------------------------------
 template <int R, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -77,19 +123,24 @@ __global__ void __launch_bounds__(kThreads, 2)
   constexpr bool DO_U = (MODE & 4) != 0;
   constexpr bool PACK = R >= 2;
   constexpr int R2 = PACK ? R / 2 : 1;
+  constexpr bool SPLIT = R >= 4;
+  constexpr int RH = SPLIT ? R / 2 : R;          // factor columns of the products per group
+  constexpr int RH2 = PACK ? RH / 2 : 1;         // ... as packed pairs
+  constexpr int ROWS = SPLIT ? kBatch : kBatch / 2;  // batch rows a thread visits
+  // rows whose products are reduced by one butterfly (G * RH values)
+  constexpr int G = SPLIT ? 16 / RH : (R <= 4 ? ROWS : 1);
   constexpr int S = kStagesWs;
-  // the row sums of G rows are reduced by one butterfly over G*R values
-  constexpr int G = R <= 4 ? kBatch / 2 : 1;
+  static_assert(ROWS % G == 0 && G * RH <= 32, "butterfly grouping");
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   T* stages = reinterpret_cast<T*>(smem_raw);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * S * STAGE_ELEMS);
   uint64_t* empty = full + S;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
-  // 16-byte aligned so that two (u, u) pairs / four v values load as one 128-bit word
-  float2* Us2 = reinterpret_cast<float2*>(empty + S + 2);  // [S][kBatch][R] (u, u)
-  T* Vs = reinterpret_cast<T*>(Us2 + S * kBatch * R);      // [S][kBatch][R]
-  T* Xw = Vs + S * kBatch * R;                             // [S][kBatch][4][R] warp sums
+  // 16-byte aligned so that four u or v values load as one 128-bit word
+  T* Us = reinterpret_cast<T*>(empty + S + 2);  // [S][kBatch][R]
+  T* Vs = Us + S * kBatch * R;                  // [S][kBatch][R]
+  T* Xw = Vs + S * kBatch * R;                  // [S][kBatch][4][R] warp sums
   double* Csh = reinterpret_cast<double*>(Xw + S * kBatch * 4 * R);  // [kThreads] core sums
 
   const int tid = threadIdx.x;
@@ -98,6 +149,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int rg = warp >> 2;
   const int wq = warp & 3;
   const int tc = tid & 127;
+  const int cb = SPLIT ? rg * RH : 0;  // first factor column of this group's products
   const int s = blockIdx.x % p.gC;
   const int q = blockIdx.x / p.gC;
   const int n = p.n;
@@ -143,11 +195,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int c = idx % R;
         const bool ok = (j < nb) && (c < r);
         const int64_t g = ok ? (int64_t)c * p.fs + row0 + j : 0;
-        if constexpr (DO_U) {
-          float* d = reinterpret_cast<float*>(Us2 + (st * kBatch + j) * R + c);
-          cp_async4(d, Uu + g, ok);
-          cp_async4(d + 1, Uu + g, ok);
-        }
+        if constexpr (DO_U) cp_async4(Us + (st * kBatch + j) * R + c, Uu + g, ok);
         if constexpr (DO_Y) cp_async4(Vs + (st * kBatch + j) * R + c, Yf + g, ok);
       }
       cp_async_arrive_noinc(&full[st]);
@@ -170,15 +218,14 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 
   // column-side factors for this thread's 4 columns
-  float2 ucol2[COLS][R2];  // PACK: (U(col_k, c), U(col_k, c+1)); else .x = U(col_k, 0)
-  float2 vw2[R][2];        // (W(col_2m, c), W(col_2m+1, c))
-  float2 yacc2[COLS][R2];
+  float2 ucol2[COLS][RH2];  // PACK: (U(col_k, cb+2c2), U(col_k, cb+2c2+1)); else .x = U(col_k, 0)
+  float2 yacc2[COLS][RH2];
 #pragma unroll
   for (int k = 0; k < COLS; ++k) {
     const int col = col0 + k;
 #pragma unroll
-    for (int c2 = 0; c2 < R2; ++c2) {
-      const int c = PACK ? 2 * c2 : 0;
+    for (int c2 = 0; c2 < RH2; ++c2) {
+      const int c = cb + (PACK ? 2 * c2 : 0);
       const bool ok0 = DO_X && (c < r) && (col < n);
       const bool ok1 = DO_X && PACK && (c + 1 < r) && (col < n);
       ucol2[k][c2] = make_float2(ok0 ? Xf[(int64_t)c * p.fs + col] : 0.f,
@@ -186,14 +233,19 @@ __global__ void __launch_bounds__(kThreads, 2)
       yacc2[k][c2] = make_float2(0.f, 0.f);
     }
   }
+  // R >= 2: wp[k][c2] = (W(col_k, 2 c2), W(col_k, 2 c2 + 1)), paired over
+  // factor columns; R = 1: wp[m][0] = (W(col_2m, 0), W(col_2m+1, 0))
+  float2 wp[COLS][R2];
 #pragma unroll
-  for (int c = 0; c < R; ++c) {
+  for (int k = 0; k < COLS; ++k) {
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      const int ca = col0 + 2 * m, cb = ca + 1;
-      const bool okc = DO_U && (c < r);
-      vw2[c][m] = make_float2(okc && ca < n ? Wu[(int64_t)c * p.fs + ca] : 0.f,
-                              okc && cb < n ? Wu[(int64_t)c * p.fs + cb] : 0.f);
+    for (int c2 = 0; c2 < R2; ++c2) {
+      // (column, factor column) of the two entries of wp[k][c2]
+      const int ca = PACK ? col0 + k : col0 + 2 * k, fa = PACK ? 2 * c2 : 0;
+      const int cb2 = PACK ? ca : ca + 1, fb = PACK ? fa + 1 : 0;
+      const bool use = DO_U && (PACK || k < 2);
+      wp[k][c2] = make_float2(use && fa < r && ca < n ? Wu[(int64_t)fa * p.fs + ca] : 0.f,
+                              use && fb < r && cb2 < n ? Wu[(int64_t)fb * p.fs + cb2] : 0.f);
     }
   }
   const int box = (tc * COLS) / BOXC;
@@ -214,6 +266,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   const bool do_core = DO_U && DO_Y && (p.Cpart != nullptr) && (centry < ncore);
   if (do_core) Csh[cslot] = 0.0;  // one slot per thread (kept out of registers)
   int waited = 0;  // batches whose "full" phase this thread has seen complete
+  // batch row of the jj-th row this thread visits
+  auto row_of = [&](int jj) { return SPLIT ? ((jj + 4 * rg) & (kBatch - 1)) : rg + 2 * jj; };
 
   for (int b = 0; b < nbatch; ++b) {
     const int st = b % S;
@@ -222,18 +276,18 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int nb = min(kBatch, re - row0);
     if (wait_or_abort(&full[st], parity, abort_flag, p.status)) {
       waited = b + 1;
-      const float2* Ust = Us2 + st * kBatch * R;
+      const T* Ust = Us + st * kBatch * R;
       const T* Vst = Vs + st * kBatch * R;
       if (do_core) {
         const int c1 = ecore / r, c2 = ecore % r;
         double acc = Csh[cslot];
         for (int j = cli; j < kBatch; j += LPE)
-          acc = fma((double)Vst[j * R + c1], (double)Ust[j * R + c2].x, acc);
+          acc = fma((double)Vst[j * R + c1], (double)Ust[j * R + c2], acc);
         Csh[cslot] = acc;
       }
       const T* sp = stages + st * STAGE_ELEMS + box * kBatch * BOXC + inbox;
-      float xg[G * R];  // row sums of the current group of rows (zero for absent rows)
-      auto do_row = [&](int j, float* xr) {
+      float xg[G * RH];  // products of the current group of rows (zero for absent rows)
+      auto do_row = [&](int j, float* xr, bool upd) {
           float4 v4 = *reinterpret_cast<const float4*>(sp + j * BOXC);
           if (!vec_ok) {
             v4.x = (col0 + 0 < n) ? v4.x : 0.f;
@@ -246,33 +300,33 @@ __global__ void __launch_bounds__(kThreads, 2)
             const float2 pd[COLS] = {make_float2(v4.x, v4.x), make_float2(v4.y, v4.y),
                                      make_float2(v4.z, v4.z), make_float2(v4.w, v4.w)};
             if constexpr (DO_Y) {
-              float2 vv[R2];
-              if constexpr (R >= 4) {
-                const float4* vr4 = reinterpret_cast<const float4*>(Vst + j * R);
+              float2 vv[RH2];
+              if constexpr (RH >= 4) {
+                const float4* vr4 = reinterpret_cast<const float4*>(Vst + j * R + cb);
 #pragma unroll
-                for (int c4 = 0; c4 < R / 4; ++c4) {
+                for (int c4 = 0; c4 < RH / 4; ++c4) {
                   const float4 t = vr4[c4];
                   vv[2 * c4] = make_float2(t.x, t.y);
                   vv[2 * c4 + 1] = make_float2(t.z, t.w);
                 }
               } else {
-                vv[0] = *reinterpret_cast<const float2*>(Vst + j * R);
+                vv[0] = *reinterpret_cast<const float2*>(Vst + j * R + cb);
               }
 #pragma unroll
-              for (int c2 = 0; c2 < R2; ++c2)
+              for (int c2 = 0; c2 < RH2; ++c2)
 #pragma unroll
                 for (int k = 0; k < COLS; ++k) yacc2[k][c2] = __ffma2_rn(pd[k], vv[c2], yacc2[k][c2]);
             }
             if constexpr (DO_X) {
-              float2 x2[R2];
+              float2 x2[RH2];
 #pragma unroll
-              for (int c2 = 0; c2 < R2; ++c2) x2[c2] = make_float2(0.f, 0.f);
+              for (int c2 = 0; c2 < RH2; ++c2) x2[c2] = make_float2(0.f, 0.f);
 #pragma unroll
               for (int k = 0; k < COLS; ++k)
 #pragma unroll
-                for (int c2 = 0; c2 < R2; ++c2) x2[c2] = __ffma2_rn(pd[k], ucol2[k][c2], x2[c2]);
+                for (int c2 = 0; c2 < RH2; ++c2) x2[c2] = __ffma2_rn(pd[k], ucol2[k][c2], x2[c2]);
 #pragma unroll
-              for (int c2 = 0; c2 < R2; ++c2) {
+              for (int c2 = 0; c2 < RH2; ++c2) {
                 xr[2 * c2] = x2[c2].x;
                 xr[2 * c2 + 1] = x2[c2].y;
               }
@@ -291,32 +345,17 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
           }
           if constexpr (DO_U) {
-            float2 pn[2] = {make_float2(v4.x, v4.y), make_float2(v4.z, v4.w)};
-            float2 uu[R];
-            if constexpr (R >= 2) {
-              const float4* ur4 = reinterpret_cast<const float4*>(Ust + j * R);
+            if (upd) {
+              float o[COLS];
+              rank_update_row<R, COLS>(Ust + j * R, pvs, wp, o);
+              T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
+              if (vec_ok) {
+                *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+              } else {
 #pragma unroll
-              for (int c2 = 0; c2 < R / 2; ++c2) {
-                const float4 t = ur4[c2];
-                uu[2 * c2] = make_float2(t.x, t.y);
-                uu[2 * c2 + 1] = make_float2(t.z, t.w);
+                for (int k = 0; k < COLS; ++k)
+                  if (col0 + k < n) dst[k] = o[k];
               }
-            } else {
-              uu[0] = Ust[j * R];
-            }
-#pragma unroll
-            for (int c = 0; c < R; ++c) {
-              pn[0] = __ffma2_rn(uu[c], vw2[c][0], pn[0]);
-              pn[1] = __ffma2_rn(uu[c], vw2[c][1], pn[1]);
-            }
-            T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
-            if (vec_ok) {
-              *reinterpret_cast<float4*>(dst) = make_float4(pn[0].x, pn[0].y, pn[1].x, pn[1].y);
-            } else {
-              const float o[4] = {pn[0].x, pn[0].y, pn[1].x, pn[1].y};
-#pragma unroll
-              for (int k = 0; k < COLS; ++k)
-                if (col0 + k < n) dst[k] = o[k];
             }
           }
       };
@@ -324,34 +363,38 @@ __global__ void __launch_bounds__(kThreads, 2)
         if constexpr (DO_X) {
           if ((jj % G) == G - 1) {
             int v = 0;
-            const float tot = warp_reduce_scatter<G * R>(xg, lane, v);
-            const int jr = rg + 2 * (jj - (G - 1) + v / R);  // batch row of value v
-            if ((lane % (32 / (G * R))) == 0) Xw[((st * kBatch + jr) * 4 + wq) * R + (v % R)] = tot;
+            const float tot = warp_reduce_scatter<G * RH>(xg, lane, v);
+            const int jr = row_of(jj - (G - 1) + v / RH);  // batch row of value v
+            if ((lane % (32 / (G * RH))) == 0)
+              Xw[((st * kBatch + jr) * 4 + wq) * R + cb + (v % RH)] = tot;
           }
         }
       };
+      // rows this thread updates: its own half of the batch (SPLIT: the
+      // first four rows it visits)
+      auto updates_row = [&](int jj) { return SPLIT ? jj < kBatch / 2 : true; };
       // full batch: no per-row guards so that rows interleave (R <= 4; at R = 8
       // the extra live registers would spill)
       if (R <= 4 && nb == kBatch) {
 #pragma unroll
-        for (int jj = 0; jj < kBatch / 2; ++jj) {
-          float* xr = xg + (jj % G) * R;
+        for (int jj = 0; jj < ROWS; ++jj) {
+          float* xr = xg + (jj % G) * RH;
           if constexpr (DO_X) {
 #pragma unroll
-            for (int c = 0; c < R; ++c) xr[c] = 0.f;
+            for (int c = 0; c < RH; ++c) xr[c] = 0.f;
           }
-          do_row(rg + 2 * jj, xr);
+          do_row(row_of(jj), xr, updates_row(jj));
           finish_group(jj);
         }
       } else {
 #pragma unroll
-        for (int jj = 0; jj < kBatch / 2; ++jj) {
-          float* xr = xg + (jj % G) * R;
+        for (int jj = 0; jj < ROWS; ++jj) {
+          float* xr = xg + (jj % G) * RH;
           if constexpr (DO_X) {
 #pragma unroll
-            for (int c = 0; c < R; ++c) xr[c] = 0.f;
+            for (int c = 0; c < RH; ++c) xr[c] = 0.f;
           }
-          if (rg + 2 * jj < nb) do_row(rg + 2 * jj, xr);
+          if (row_of(jj) < nb) do_row(row_of(jj), xr, updates_row(jj));
           finish_group(jj);
         }
       }
@@ -393,36 +436,63 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
   }
   if constexpr (DO_Y) {
-    __syncthreads();
-    T* yc = stages;  // [k][c][tc], reusing the ring
-    if (rg == 1) {
+    T* yo = static_cast<T*>(p.Ypart) + (int64_t)q * p.yp_q;
+    if constexpr (SPLIT) {
+      // each group holds whole column sums of its own factor columns
+      __syncthreads();
+      if (col0 < n && !*abort_flag) {
 #pragma unroll
-      for (int k = 0; k < COLS; ++k)
+        for (int c2 = 0; c2 < RH2; ++c2) {
 #pragma unroll
-        for (int c2 = 0; c2 < R2; ++c2) {
-          yc[(k * R + (PACK ? 2 * c2 : 0)) * 128 + tc] = yacc2[k][c2].x;
-          if (PACK) yc[(k * R + 2 * c2 + 1) * 128 + tc] = yacc2[k][c2].y;
+          for (int h = 0; h < 2; ++h) {
+            const int c = cb + 2 * c2 + h;
+            if (c >= r) break;
+            const float vals[COLS] = {h ? yacc2[0][c2].y : yacc2[0][c2].x,
+                                      h ? yacc2[1][c2].y : yacc2[1][c2].x,
+                                      h ? yacc2[2][c2].y : yacc2[2][c2].x,
+                                      h ? yacc2[3][c2].y : yacc2[3][c2].x};
+            T* dst = yo + (int64_t)c * p.part_cs + col0;
+            if (vec_ok) {
+              *reinterpret_cast<float4*>(dst) = make_float4(vals[0], vals[1], vals[2], vals[3]);
+            } else {
+#pragma unroll
+              for (int k = 0; k < COLS; ++k)
+                if (col0 + k < n) dst[k] = vals[k];
+            }
+          }
         }
-    }
-    __syncthreads();
-    if (rg == 0 && col0 < n && !*abort_flag) {
-      T* yo = static_cast<T*>(p.Ypart) + (int64_t)q * p.yp_q;
+      }
+    } else {
+      __syncthreads();
+      T* yc = stages;  // [k][c][tc], reusing the ring
+      if (rg == 1) {
 #pragma unroll
-      for (int c = 0; c < R; ++c) {
-        if (c >= r) break;
-        float vals[COLS];
+        for (int k = 0; k < COLS; ++k)
 #pragma unroll
-        for (int k = 0; k < COLS; ++k) {
-          const float mine = (c & 1) ? yacc2[k][c / 2].y : yacc2[k][c / 2].x;
-          vals[k] = mine + yc[(k * R + c) * 128 + tc];
-        }
-        T* dst = yo + (int64_t)c * p.part_cs + col0;
-        if (vec_ok) {
-          *reinterpret_cast<float4*>(dst) = make_float4(vals[0], vals[1], vals[2], vals[3]);
-        } else {
+          for (int c2 = 0; c2 < R2; ++c2) {
+            yc[(k * R + (PACK ? 2 * c2 : 0)) * 128 + tc] = yacc2[k][c2].x;
+            if (PACK) yc[(k * R + 2 * c2 + 1) * 128 + tc] = yacc2[k][c2].y;
+          }
+      }
+      __syncthreads();
+      if (rg == 0 && col0 < n && !*abort_flag) {
 #pragma unroll
-          for (int k = 0; k < COLS; ++k)
-            if (col0 + k < n) dst[k] = vals[k];
+        for (int c = 0; c < R; ++c) {
+          if (c >= r) break;
+          float vals[COLS];
+#pragma unroll
+          for (int k = 0; k < COLS; ++k) {
+            const float mine = (c & 1) ? yacc2[k][c / 2].y : yacc2[k][c / 2].x;
+            vals[k] = mine + yc[(k * R + c) * 128 + tc];
+          }
+          T* dst = yo + (int64_t)c * p.part_cs + col0;
+          if (vec_ok) {
+            *reinterpret_cast<float4*>(dst) = make_float4(vals[0], vals[1], vals[2], vals[3]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < COLS; ++k)
+              if (col0 + k < n) dst[k] = vals[k];
+          }
         }
       }
     }
@@ -447,7 +517,6 @@ __global__ void __launch_bounds__(kThreads, 2)
   constexpr int NB = STRIP / BOXC;
   constexpr int STAGE_ELEMS = kBatch * STRIP;
   constexpr int S = kStagesWs;
-  constexpr int M = COLS / 2;  // float2 pairs per thread and row
   static_assert(NB * BOXC == STRIP, "strip must be whole boxes");
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -455,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * S * STAGE_ELEMS);
   uint64_t* empty = full + S;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
-  float2* Us2 = reinterpret_cast<float2*>(empty + S + 2);  // [S][kBatch][R] (u, u), 16-B aligned
+  T* Us = reinterpret_cast<T*>(empty + S + 2);  // [S][kBatch][R], 16-byte aligned
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -499,9 +568,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int c = idx % R;
       const bool ok = (j < nb) && (c < r);
       const int64_t g = ok ? (int64_t)c * p.fs + row0 + j : 0;
-      float* d = reinterpret_cast<float*>(Us2 + (st * kBatch + j) * R + c);
-      cp_async4(d, Uu + g, ok);
-      cp_async4(d + 1, Uu + g, ok);
+      cp_async4(Us + (st * kBatch + j) * R + c, Uu + g, ok);
     }
     cp_async_arrive_noinc(&full[st]);
     if (lane == 0) {
@@ -541,11 +608,16 @@ __global__ void __launch_bounds__(kThreads, 2)
     case 8: suffix_blocks<T, R, COLS, 8>(wcol); break;
     default: break;
   }
-  float2 w2[R][M];  // (W(col_2m, c), W(col_2m+1, c))
+  // column factor in the layout of rank_update_row
+  constexpr int R2 = R >= 2 ? R / 2 : 1;
+  float2 wp[COLS][R2];
 #pragma unroll
-  for (int c = 0; c < R; ++c)
+  for (int k = 0; k < COLS; ++k)
 #pragma unroll
-    for (int m = 0; m < M; ++m) w2[c][m] = make_float2(wcol[2 * m][c], wcol[2 * m + 1][c]);
+    for (int c2 = 0; c2 < R2; ++c2)
+      wp[k][c2] = R >= 2 ? make_float2(wcol[k][2 * c2], wcol[k][2 * c2 + 1])
+                         : make_float2(k < COLS / 2 ? wcol[2 * k][0] : 0.f,
+                                       k < COLS / 2 ? wcol[2 * k + 1][0] : 0.f);
   const int box = (tc * COLS) / BOXC;
   const int inbox = (tc * COLS) % BOXC;
   const bool vec_ok = (col0 + COLS <= n);
@@ -561,41 +633,25 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (ready) waited = b + 1;
     if (ready && any_col) {
       const T* sp = stages + st * STAGE_ELEMS + box * kBatch * BOXC + inbox;
-      const float2* Ust = Us2 + st * kBatch * R;
+      const T* Ust = Us + st * kBatch * R;
       auto row = [&](int j) {
-          float2 pv[M];
+          float pv[COLS];
           if constexpr (COLS == 4) {
             const float4 v4 = *reinterpret_cast<const float4*>(sp + j * BOXC);
-            pv[0] = make_float2(v4.x, v4.y);
-            pv[M - 1] = make_float2(v4.z, v4.w);
+            pv[0] = v4.x; pv[1] = v4.y; pv[2] = v4.z; pv[3] = v4.w;
           } else {
-            pv[0] = *reinterpret_cast<const float2*>(sp + j * BOXC);
+            const float2 v2 = *reinterpret_cast<const float2*>(sp + j * BOXC);
+            pv[0] = v2.x; pv[1] = v2.y;
           }
-          float2 uu[R];
-          if constexpr (R >= 2) {
-            const float4* ur4 = reinterpret_cast<const float4*>(Ust + j * R);
-#pragma unroll
-            for (int c2 = 0; c2 < R / 2; ++c2) {
-              const float4 t = ur4[c2];
-              uu[2 * c2] = make_float2(t.x, t.y);
-              uu[2 * c2 + 1] = make_float2(t.z, t.w);
-            }
-          } else {
-            uu[0] = Ust[j * R];
-          }
-#pragma unroll
-          for (int c = 0; c < R; ++c)
-#pragma unroll
-            for (int m = 0; m < M; ++m) pv[m] = __ffma2_rn(uu[c], w2[c][m], pv[m]);
+          float o[COLS];
+          rank_update_row<R, COLS>(Ust + j * R, pv, wp, o);
           T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
           if (vec_ok) {
             if constexpr (COLS == 4)
-              *reinterpret_cast<float4*>(dst) = make_float4(pv[0].x, pv[0].y, pv[M - 1].x,
-                                                            pv[M - 1].y);
+              *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
             else
-              *reinterpret_cast<float2*>(dst) = pv[0];
+              *reinterpret_cast<float2*>(dst) = make_float2(o[0], o[1]);
           } else {
-            const float* o = reinterpret_cast<const float*>(pv);
 #pragma unroll
             for (int k = 0; k < COLS; ++k)
               if (col0 + k < n) dst[k] = o[k];

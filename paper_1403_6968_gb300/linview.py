@@ -178,6 +178,14 @@ class Program:
         L.call("linview_adjoint_iteration", self.h, pa, dA.stride(0) if dA is not None else 0,
                pb, dB.stride(0) if dB is not None else 0, _stream_ptr(stream))
 
+    def adjoint_iteration_seed(self, Gk, dA=None, dB=None, dT0=None, stream=None):
+        """Vector-Jacobian product of (A, B, T_0) -> T_k at dL/dT_k = Gk (CUDA tensors)."""
+        def ptr(t):
+            return (C.c_void_p(t.data_ptr()), t.stride(0)) if t is not None else (None, 0)
+        (pa, la), (pb, lb), (pt, lt) = ptr(dA), ptr(dB), ptr(dT0)
+        L.call("linview_adjoint_iteration_seed", self.h, C.c_void_p(Gk.data_ptr()), Gk.stride(0),
+               pa, la, pb, lb, pt, lt, _stream_ptr(stream))
+
     def adjoint_power(self, G, dA, stream=None):
         L.call("linview_adjoint_power", self.h, C.c_void_p(G.data_ptr()), G.stride(0),
                C.c_void_p(dA.data_ptr()), dA.stride(0), _stream_ptr(stream))
@@ -252,3 +260,138 @@ def level_pass_noalloc(P, U, V, X=None, Y=None, do_update=True, stream=None):
            C.c_void_p(X.data_ptr()) if X is not None else None,
            C.c_void_p(Y.data_ptr()) if Y is not None else None,
            1 if do_update else 0, _stream_ptr(stream))
+
+
+def estimate_device_bytes(n, k, r_max=1, kind="power", precision="f32"):
+    """Device bytes a power (or power-sum) program of this shape would hold."""
+    d = L.ProgramDesc()
+    d.kind = KINDS[kind]
+    d.precision = L.F64 if precision in ("f64", "fp64") else L.F32
+    d.n, d.k, d.r_max = int(n), int(k), int(r_max)
+    b = C.c_int64()
+    L.call("linview_estimate_device_bytes", C.byref(d), C.byref(b))
+    return b.value
+
+
+def program_device_bytes(prog):
+    b = C.c_int64()
+    L.call("linview_program_device_bytes", prog.h, C.byref(b))
+    return b.value
+
+
+class _ServedProgram(Program):
+    """A server-owned program: views can be read, the server frees it."""
+
+    def __init__(self, handle, n, k):
+        self.lib = L.load()
+        self.h = C.c_void_p(handle)
+        self.precision = L.F32
+        self.np_dtype = np.float32
+        self.n, self.k = n, k
+
+    def close(self):
+        self.h = None
+
+
+class Server:
+    """Continuous-batching server of maintained A^k views (linview_server_*).
+
+    Views and their factors stay resident on the GPU; requests dA = U V^T
+    are queued per view, coalesced while the view is busy, and refreshed on
+    per-view streams by the library's scheduler thread."""
+
+    def __init__(self, max_inflight=4, r_cap=8, hbm_budget_bytes=0):
+        L.load()
+        h = C.c_void_p()
+        L.call("linview_server_create", int(hbm_budget_bytes), int(max_inflight), int(r_cap),
+               C.byref(h))
+        self.h = h
+        self.r_cap = r_cap
+        self._n = {}
+        self._keep = []
+
+    def add_view(self, A, k):
+        a = _Operand(A, np.float32)
+        if a.on_device:  # the server reads A on its own stream
+            _torch().cuda.current_stream().synchronize()
+        v = C.c_int32()
+        L.call("linview_server_add_view", self.h, a.shape[0], int(k), a.ptr, a.ld, a.on_device,
+               C.byref(v))
+        self._n[v.value] = (a.shape[0], int(k))
+        return v.value
+
+    def submit(self, view, U, V, arrival_s=-1.0):
+        u = np.ascontiguousarray(np.asarray(U, dtype=np.float32))
+        w = np.ascontiguousarray(np.asarray(V, dtype=np.float32))
+        if u.ndim == 1:
+            u, w = u.reshape(-1, 1), w.reshape(-1, 1)
+        t = C.c_uint64()
+        L.call("linview_server_submit", self.h, int(view), u.shape[1], C.c_void_p(u.ctypes.data),
+               u.shape[1], C.c_void_p(w.ctypes.data), w.shape[1], float(arrival_s), C.byref(t))
+        return t.value
+
+    def replay(self, t_s, views, ranks, factors, offsets):
+        """Open-loop load: request i at t_s[i] seconds after the call; its U
+        (n x rank, row-major) at factors[offsets[i]:], V right after it.
+        ``factors`` must stay alive until ``drain`` returns."""
+        t_s = np.ascontiguousarray(t_s, dtype=np.float64)
+        views = np.ascontiguousarray(views, dtype=np.int32)
+        ranks = np.ascontiguousarray(ranks, dtype=np.int32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        if factors.dtype != np.float32 or not factors.flags.c_contiguous:
+            raise TypeError("factors must be a contiguous float32 array")
+        self._keep.append(factors)
+        L.call("linview_server_replay", self.h, len(t_s), C.c_void_p(t_s.ctypes.data),
+               C.c_void_p(views.ctypes.data), C.c_void_p(ranks.ctypes.data),
+               C.c_void_p(factors.ctypes.data), C.c_void_p(offsets.ctypes.data))
+
+    def drain(self, timeout_s=0.0):
+        L.call("linview_server_drain", self.h, float(timeout_s))
+        self._keep.clear()
+
+    def poll(self, max_records=4096):
+        """Completion records as a list of dicts (oldest first)."""
+        buf = (L.Completion * max_records)()
+        cnt = C.c_int32()
+        out = []
+        while True:
+            L.call("linview_server_poll", self.h, C.cast(buf, C.c_void_p), max_records, C.byref(cnt))
+            for i in range(cnt.value):
+                c = buf[i]
+                out.append({f: getattr(c, f) for f, _ in L.Completion._fields_ if f != "reserved"})
+            if cnt.value < max_records:
+                return out
+
+    def view_state(self, view):
+        st = C.c_int32()
+        L.call("linview_server_view_state", self.h, int(view), C.byref(st))
+        return ("waiting", "resident", "removed")[st.value]
+
+    def program(self, view):
+        """The resident view's program (read its views after ``drain``)."""
+        h = C.c_void_p()
+        L.call("linview_server_view_program", self.h, int(view), C.byref(h))
+        n, k = self._n[view]
+        return _ServedProgram(h.value, n, k)
+
+    def remove_view(self, view):
+        L.call("linview_server_remove_view", self.h, int(view))
+
+    def stats(self):
+        s = L.ServerStats()
+        L.call("linview_server_stats_get", self.h, C.byref(s))
+        return {f: getattr(s, f) for f, _ in L.ServerStats._fields_ if f != "reserved"}
+
+    def clock(self):
+        return L.load().linview_server_clock(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.load().linview_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
