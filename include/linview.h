@@ -257,6 +257,11 @@ linview_status linview_level_pass_noalloc(int precision, int64_t n, void* P, int
  * waits for the recorded events), and the algorithmic bytes those launches
  * move (each view element read once and, when refreshed, written once).
  * *all_launches counts every kernel and library call the program issued.
+ * Power programs replay their per-update propagation as CUDA graphs; with
+ * profiling enabled each rank's propagation is captured as 16 instrumented
+ * copies (event-record nodes around every view pass) replayed round-robin,
+ * and the statistics cover the last replay of every copy replayed since the
+ * last reset (so at most the last 16 updates).
  */
 linview_status linview_set_profiling(linview_program* prog, int enable);
 linview_status linview_pass_stats(linview_program* prog, int kernel, int64_t* launches, double* ms,
@@ -309,13 +314,21 @@ linview_status linview_estimate_device_bytes(const linview_program_desc* desc, i
  *   call returns; 1 <= rank <= r_cap, else LINVIEW_ERANK.  arrival_s < 0
  *   stamps the current server time.  *ticket receives the request id
  *   (tickets count from 1 in submission order).
+ * linview_server_submit_row: a row update dA = e_row v^T (v: n floats, host,
+ *   copied).  Row updates queued for one view coalesce by row: requests to a
+ *   row already in the delta add their v to that row's column and no rank,
+ *   so a delta's rank is its number of distinct rows (plus the ranks of the
+ *   factored requests in it); the paper's batch updates with skewed row
+ *   frequencies (Section 6, Table 4).
  * linview_server_replay: open-loop load for measurement.  The calling thread
  *   submits request i at server time t0 + t_s[i] (t0 = the time of the call,
  *   t_s non-decreasing) with arrival_s = t0 + t_s[i], and returns after the
  *   last one.  Its factors are NOT copied: U_i is the n_view x rank[i]
  *   row-major array at factors + offset[i] (floats), V_i follows it
- *   directly; the caller keeps ``factors`` alive until linview_server_drain
- *   returns.
+ *   directly; when ``rows`` is not NULL and rows[i] >= 0, request i is the
+ *   row update e_rows[i] v^T with v the n_view floats at factors + offset[i]
+ *   (rank[i] ignored).  The caller keeps ``factors`` alive until
+ *   linview_server_drain returns.
  * linview_server_poll: moves up to ``max`` completion records (oldest first)
  *   to ``out``; *count receives how many.  Never blocks.
  * linview_server_drain: waits until every request submitted so far has
@@ -367,9 +380,11 @@ linview_status linview_server_add_view(linview_server* srv, int64_t n, int32_t k
 linview_status linview_server_submit(linview_server* srv, int32_t view, int32_t rank, const void* U,
                                      int64_t ldu, const void* V, int64_t ldv, double arrival_s,
                                      uint64_t* ticket);
+linview_status linview_server_submit_row(linview_server* srv, int32_t view, int64_t row,
+                                         const void* v, double arrival_s, uint64_t* ticket);
 linview_status linview_server_replay(linview_server* srv, int64_t count, const double* t_s,
                                      const int32_t* view, const int32_t* rank, const void* factors,
-                                     const int64_t* offset);
+                                     const int64_t* offset, const int64_t* rows);
 linview_status linview_server_poll(linview_server* srv, linview_completion* out, int32_t max,
                                    int32_t* count);
 linview_status linview_server_drain(linview_server* srv, double timeout_s);

@@ -33,6 +33,12 @@ Recipes (all FP64 draws from numpy's PCG64 ``default_rng``; a workload-level
   (Section 6); the rate sweep and the mix of sizes are this build's serving
   workload.
 
+* ``zipf_row_batch``: a batch of row updates whose rows follow a Zipf law
+  (frequency of the i-th most popular row proportional to i^-z over a random
+  ordering of the n rows; z = 0 is uniform), v i.i.d. N(0, sigma^2): the
+  batch-update workload of Section 6 (Table 4, batches of 1,000 updates,
+  Zipf factors 5 to 0).
+
 ``dtype`` rounds the FP64 draw to nearest in the requested type; consumers that
 compare against the FP64 oracle promote the rounded values back to FP64, so the
 comparison measures the method's error and not input quantisation.
@@ -54,6 +60,7 @@ _STREAM_OLS_UPD = 8
 _STREAM_MISC = 9
 _STREAM_SERVE_SIZES = 10
 _STREAM_SERVE_TRACE = 11
+_STREAM_ZIPF = 12
 
 
 def rng(seed: int, stream: int) -> np.random.Generator:
@@ -181,4 +188,16 @@ def trace_factors(view_sizes, views, ranks, factors, offsets, i: int):
     """(U_i, V_i) of request i of a ``serving_trace`` (views into ``factors``)."""
     n, r, o = view_sizes[views[i]], int(ranks[i]), int(offsets[i])
     return factors[o:o + n * r].reshape(n, r), factors[o + n * r:o + 2 * n * r].reshape(n, r)
+
+
+def zipf_row_batch(n: int, count: int, z: float, seed: int = 0, sigma: float = 0.01,
+                   dtype=np.float32):
+    """(rows, vs): ``count`` row updates e_rows[j] vs[j]^T, rows Zipf(z)-distributed."""
+    g = rng(seed, _STREAM_ZIPF)
+    perm = g.permutation(n)
+    w = np.arange(1, n + 1, dtype=np.float64) ** (-float(z))
+    ranks = g.choice(n, size=count, p=w / w.sum())
+    rows = perm[ranks].astype(np.int64)
+    vs = _cast(sigma * g.standard_normal((count, n)), dtype)
+    return rows, vs
 

@@ -112,7 +112,9 @@ _SIGS = [
     ("linview_server_add_view", _I, [_P, _I64, C.c_int32, _P, _I64, _I, C.POINTER(C.c_int32)]),
     ("linview_server_submit", _I, [_P, C.c_int32, C.c_int32, _P, _I64, _P, _I64, C.c_double,
                                    C.POINTER(C.c_uint64)]),
-    ("linview_server_replay", _I, [_P, _I64, _P, _P, _P, _P, _P]),
+    ("linview_server_submit_row", _I, [_P, C.c_int32, _I64, _P, C.c_double,
+                                       C.POINTER(C.c_uint64)]),
+    ("linview_server_replay", _I, [_P, _I64, _P, _P, _P, _P, _P, _P]),
     ("linview_server_poll", _I, [_P, _P, C.c_int32, C.POINTER(C.c_int32)]),
     ("linview_server_drain", _I, [_P, C.c_double]),
     ("linview_server_view_state", _I, [_P, C.c_int32, C.POINTER(C.c_int32)]),

@@ -155,19 +155,29 @@ struct linview_program {
   bool use_graphs = true;
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+  struct Rec {
+    cudaEvent_t e0, e1;
+    int kind;
+    double bytes;
+  };
   struct GraphEntry {
     int r;
     cudaGraphExec_t exec;
     int64_t launches;
+    // instrumented copies (profiling): event-record nodes around each view
+    // pass; recs hold the events of the copy's last replay
+    bool instrumented = false;
+    std::vector<Rec> recs;
+    bool replayed = false;  // replayed since the last linview_reset_stats
   };
   std::vector<GraphEntry> graphs;
+  std::vector<int> prof_rr;  // round-robin position over the instrumented copies, per rank
   // profiling
   bool prof = false;
-  std::vector<cudaEvent_t> ev_pool;
-  struct Rec {
-    int e0, e1, kind;
-    double bytes;
-  };
+  bool capturing_prof = false;       // capturing an instrumented graph copy
+  std::vector<Rec>* capture_recs = nullptr;
+  std::vector<cudaEvent_t> ev_pool;  // events of eager records (freed by reset)
+  std::vector<cudaEvent_t> gev_pool; // events owned by instrumented graphs
   std::vector<Rec> ev_recs;
   int64_t all_launches = 0;
 };
@@ -246,17 +256,27 @@ static linview_status ensure_stage(linview_program* p, size_t bytes) {
 // ---------------------------------------------------------------------------
 // profiling of view passes
 // ---------------------------------------------------------------------------
-static int prof_event(linview_program* p) {
+// An event for a profiling record.  While an instrumented graph copy is
+// captured the event belongs to the graph (an external event-record node
+// that records on every replay); otherwise it is an eager record.
+static cudaEvent_t prof_event(linview_program* p) {
   cudaEvent_t e;
-  if (cudaEventCreate(&e) != cudaSuccess) return -1;
-  p->ev_pool.push_back(e);
-  return (int)p->ev_pool.size() - 1;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  (p->capturing_prof ? p->gev_pool : p->ev_pool).push_back(e);
+  return e;
+}
+
+static void prof_record(linview_program* p, cudaEvent_t e, cudaStream_t s) {
+  if (p->capturing_prof)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
 }
 
 struct ProfScope {
   linview_program* p;
   cudaStream_t s;
-  int e0 = -1;
+  cudaEvent_t e0 = nullptr;
   int kind = 0;
   double bytes = 0.0;
   // kind 1 = fused pass, 2 = update pass (timed when profiling); kind 0 =
@@ -266,24 +286,20 @@ struct ProfScope {
     p->all_launches++;
     if (!p->prof || kind == 0) return;
     e0 = prof_event(p);
-    if (e0 >= 0) cudaEventRecord(p->ev_pool[e0], s);
+    if (e0) prof_record(p, e0, s);
   }
   ~ProfScope() {
-    if (!p->prof || e0 < 0) return;
-    int e1 = prof_event(p);
-    if (e1 < 0) return;
-    cudaEventRecord(p->ev_pool[e1], s);
-    p->ev_recs.push_back({e0, e1, kind, bytes});
+    if (!p->prof || !e0) return;
+    cudaEvent_t e1 = prof_event(p);
+    if (!e1) return;
+    prof_record(p, e1, s);
+    (p->capturing_prof ? *p->capture_recs : p->ev_recs).push_back({e0, e1, kind, bytes});
   }
 };
 
 // ---------------------------------------------------------------------------
 // view passes
 // ---------------------------------------------------------------------------
-template <typename T>
-static constexpr int max_update_r() {
-  return sizeof(T) == 4 ? 64 : 32;
-}
 
 // X = P Xf, Y = P^T Yf (either may be skipped by mode), optional P += Uu Wu^T,
 // for a factor block of width r <= kMaxFusedR; partials land at column offset 0
@@ -322,7 +338,7 @@ static linview_status run_fused(linview_program* p, const View& v, int mode, int
 template <typename T>
 static linview_status run_update(linview_program* p, const View& v, const T* Uu, const T* Wu,
                                  int r, cudaStream_t s, int suffix_rin = 0) {
-  constexpr int MU = max_update_r<T>();
+  constexpr int MU = kMaxUpdateR;
   for (int c0 = 0; c0 < r; c0 += MU) {
     const int w = (r - c0 < MU) ? (r - c0) : MU;
     const PassGeom g = update_geom(sizeof(T), w, (int)v.rows, p->sms);
@@ -345,7 +361,8 @@ static linview_status run_update(linview_program* p, const View& v, const T* Uu,
   return LINVIEW_OK;
 }
 
-// Products X = P Xf, Y = P^T Yf for any width r (chunks of kMaxFusedR) into
+// Products X = P Xf, Y = P^T Yf for any width r (chunks of kMaxProductR in
+// FP32, kMaxFusedR in FP64) into
 // the program's partial buffers (column block c0 at column offset c0), then
 // (if Uu) the in-place update.  Fused in one pass when r <= kMaxFusedR.
 template <typename T>
@@ -358,8 +375,9 @@ static linview_status run_products_update(linview_program* p, const View& v, int
     return run_fused<T>(p, v, mode, r, Xf, Yf, Uu, Wu, p->Xpart, p->Ypart, s,
                         mode == kModeXYU ? Cpart : nullptr);
   }
-  for (int c0 = 0; c0 < r; c0 += kMaxFusedR) {
-    const int w = (r - c0 < kMaxFusedR) ? (r - c0) : kMaxFusedR;
+  constexpr int MW = sizeof(T) == 4 ? kMaxProductR : kMaxFusedR;  // products-only width
+  for (int c0 = 0; c0 < r; c0 += MW) {
+    const int w = (r - c0 < MW) ? (r - c0) : MW;
     T* xp = static_cast<T*>(p->Xpart) + (int64_t)c0 * p->part_cs;
     T* yp = static_cast<T*>(p->Ypart) + (int64_t)c0 * p->part_cs;
     LV_TRY(run_fused<T>(p, v, want_y ? kModeXY : kModeX, w, Xf + (int64_t)c0 * p->fs,
@@ -458,7 +476,7 @@ static linview_status powers_reeval(linview_program* p, cudaStream_t s) {
 // when the whole factor fits one pass; wider factors get an explicit
 // suffix-sum factor (see sums_update)
 static bool powers_wide_sums(const linview_program_desc& d) {
-  const int64_t mu = d.precision == LINVIEW_F64 ? 32 : 64;
+  const int64_t mu = kMaxUpdateR;
   return d.kind == LINVIEW_POWER_SUM && ((int64_t)d.r_max * d.k > mu || d.r_max > 8);
 }
 
@@ -976,8 +994,9 @@ void linview_destroy(linview_program* p) {
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
   for (void* a : p->allocs) cudaFree(a);
-  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   for (auto& ge : p->graphs) cudaGraphExecDestroy(ge.exec);
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->gev_pool) cudaEventDestroy(e);
   if (p->gev_in) cudaEventDestroy(p->gev_in);
   if (p->gev_out) cudaEventDestroy(p->gev_out);
   if (p->gstream) cudaStreamDestroy(p->gstream);
@@ -1099,48 +1118,80 @@ static linview_status after_update(linview_program* p, cudaStream_t s) {
 
 // Powers/sums: the launches after ingest depend only on the rank (all
 // pointers are the program's own), so they are captured once per rank into
-// a CUDA graph and replayed.  Profiling runs eagerly so that every pass keeps
-// its own event pair.
+// a CUDA graph and replayed.  With profiling on, kProfCopies instrumented
+// copies per rank (an event pair around every view pass) are captured at the
+// first call and replayed round-robin, so that the passes are timed inside
+// the same graph replays the caller times.
+constexpr int kProfCopies = 16;
+
+static linview_status capture_graph(linview_program* p, int r, bool inst,
+                                    linview_program::GraphEntry* out) {
+  const int64_t before = p->all_launches;
+  out->r = r;
+  out->instrumented = inst;
+  p->capturing_prof = inst;
+  p->capture_recs = inst ? &out->recs : nullptr;
+  const bool prof_was = p->prof;
+  p->prof = inst;
+  LV_CUDA(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
+  linview_status st = p->elem == 4 ? powers_propagate<float>(p, r, p->gstream)
+                                   : powers_propagate<double>(p, r, p->gstream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(p->gstream, &graph);
+  p->capturing_prof = false;
+  p->capture_recs = nullptr;
+  p->prof = prof_was;
+  const int64_t launches = p->all_launches - before;
+  p->all_launches = before;
+  if (st != LINVIEW_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    (void)cudaGetLastError();  // do not leave the capture error to later calls
+    return st;
+  }
+  if (ec != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(LINVIEW_EDEVICE, "graph capture failed: %s", cudaGetErrorString(ec));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&out->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess)
+    return fail(LINVIEW_EDEVICE, "graph instantiate failed: %s", cudaGetErrorString(ei));
+  out->launches = launches;
+  return LINVIEW_OK;
+}
+
 static linview_status powers_graph(linview_program* p, int r, cudaStream_t s) {
   if (!p->gstream) {
     LV_CUDA(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
     LV_CUDA(cudaEventCreateWithFlags(&p->gev_in, cudaEventDisableTiming));
     LV_CUDA(cudaEventCreateWithFlags(&p->gev_out, cudaEventDisableTiming));
   }
-  linview_program::GraphEntry* ge = nullptr;
-  for (auto& g : p->graphs)
-    if (g.r == r) ge = &g;
-  if (!ge) {
-    const int64_t before = p->all_launches;
-    LV_CUDA(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
-    linview_status st = p->elem == 4 ? powers_propagate<float>(p, r, p->gstream)
-                                     : powers_propagate<double>(p, r, p->gstream);
-    cudaGraph_t graph = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(p->gstream, &graph);
-    if (st != LINVIEW_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      (void)cudaGetLastError();  // do not leave the capture error to later calls
-      return st;
+  const bool inst = p->prof;
+  std::vector<size_t> idx;
+  for (size_t i = 0; i < p->graphs.size(); ++i)
+    if (p->graphs[i].r == r && p->graphs[i].instrumented == inst) idx.push_back(i);
+  if (idx.empty()) {
+    const int copies = inst ? kProfCopies : 1;
+    for (int c = 0; c < copies; ++c) {
+      linview_program::GraphEntry ge;
+      LV_TRY(capture_graph(p, r, inst, &ge));
+      p->graphs.push_back(std::move(ge));
+      idx.push_back(p->graphs.size() - 1);
     }
-    if (ec != cudaSuccess) {
-      (void)cudaGetLastError();
-      return fail(LINVIEW_EDEVICE, "graph capture failed: %s", cudaGetErrorString(ec));
-    }
-    cudaGraphExec_t exec = nullptr;
-    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ei != cudaSuccess)
-      return fail(LINVIEW_EDEVICE, "graph instantiate failed: %s", cudaGetErrorString(ei));
-    p->graphs.push_back({r, exec, p->all_launches - before});
-    p->all_launches = before;
-    ge = &p->graphs.back();
   }
+  size_t pick = idx[0];
+  if (inst) {
+    if ((int)p->prof_rr.size() <= r) p->prof_rr.resize(r + 1, 0);
+    pick = idx[p->prof_rr[r]++ % idx.size()];
+  }
+  linview_program::GraphEntry& ge = p->graphs[pick];
   LV_CUDA(cudaEventRecord(p->gev_in, s));
   LV_CUDA(cudaStreamWaitEvent(p->gstream, p->gev_in, 0));
-  LV_CUDA(cudaGraphLaunch(ge->exec, p->gstream));
+  LV_CUDA(cudaGraphLaunch(ge.exec, p->gstream));
   LV_CUDA(cudaEventRecord(p->gev_out, p->gstream));
   LV_CUDA(cudaStreamWaitEvent(s, p->gev_out, 0));
-  p->all_launches += ge->launches;
+  ge.replayed = true;
+  p->all_launches += ge.launches;
   return LINVIEW_OK;
 }
 
@@ -1148,7 +1199,7 @@ static linview_status propagate(linview_program* p, int r, cudaStream_t s) {
   switch (p->d.kind) {
     case LINVIEW_POWER:
     case LINVIEW_POWER_SUM:
-      if (p->use_graphs && !p->prof) return powers_graph(p, r, s);
+      if (p->use_graphs) return powers_graph(p, r, s);
       return p->elem == 4 ? powers_propagate<float>(p, r, s) : powers_propagate<double>(p, r, s);
     case LINVIEW_ITERATION:
       return p->elem == 4 ? iter_propagate<float>(p, r, s) : iter_propagate<double>(p, r, s);
@@ -1477,6 +1528,7 @@ linview_status linview_reset_stats(linview_program* p) {
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   p->ev_pool.clear();
   p->ev_recs.clear();
+  for (auto& ge : p->graphs) ge.replayed = false;
   p->all_launches = 0;
   return LINVIEW_OK;
 }
@@ -1487,15 +1539,22 @@ linview_status linview_pass_stats(linview_program* p, int kernel, int64_t* launc
   if (kernel < 0 || kernel > 2) return fail(LINVIEW_EINVAL, "bad kernel selector %d", kernel);
   double tot = 0.0, by = 0.0;
   int64_t cnt = 0;
-  for (auto& rc : p->ev_recs) {
-    if (kernel != 0 && rc.kind != kernel) continue;
-    float t = 0.f;
-    LV_CUDA(cudaEventSynchronize(p->ev_pool[rc.e1]));
-    LV_CUDA(cudaEventElapsedTime(&t, p->ev_pool[rc.e0], p->ev_pool[rc.e1]));
-    tot += t;
-    by += rc.bytes;
-    ++cnt;
-  }
+  auto add = [&](const std::vector<linview_program::Rec>& recs) -> linview_status {
+    for (auto& rc : recs) {
+      if (kernel != 0 && rc.kind != kernel) continue;
+      float t = 0.f;
+      LV_CUDA(cudaEventSynchronize(rc.e1));
+      LV_CUDA(cudaEventElapsedTime(&t, rc.e0, rc.e1));
+      tot += t;
+      by += rc.bytes;
+      ++cnt;
+    }
+    return LINVIEW_OK;
+  };
+  LV_TRY(add(p->ev_recs));
+  // instrumented graph copies replayed since the reset: their last replay
+  for (auto& ge : p->graphs)
+    if (ge.instrumented && ge.replayed) LV_TRY(add(ge.recs));
   if (launches) *launches = cnt;
   if (ms) *ms = tot;
   if (bytes) *bytes = by;

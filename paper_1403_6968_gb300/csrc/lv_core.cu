@@ -9,6 +9,8 @@
 // they are summed here in a fixed order so every run gives identical bits.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lv_device.cuh"
 #include "lv_internal.h"
 
@@ -18,22 +20,25 @@ constexpr int kGramRows = 32;   // rows staged per tile
 constexpr int kGramMaxR = 64;
 constexpr int kGramPerThread = kGramMaxR * kGramMaxR / kThreads;  // 16
 
+// Blocks of the factor-core kernels: one 32-row tile per block up to 320
+// blocks (>= 2 per SM), more tiles per block beyond.
 int gram_grid(int n) {
-  int g = (n + 127) / 128;
-  if (g > 64) g = 64;
+  int g = (n + kGramRows - 1) / kGramRows;
+  if (g > 320) g = 320;
   if (g < 1) g = 1;
   return g;
 }
 
-// C = V^T U (r x r, row-major, FP64).  Block b sums rows of its chunk; the
-// last block to finish (ticket) adds the block partials in index order.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ V,
-                                                        const T* __restrict__ U, int64_t fs, int n,
-                                                        int r, double* Cpart, unsigned* ticket,
-                                                        double* C, unsigned* status) {
-  __shared__ T Vs[kGramRows][kGramMaxR + 1];
-  __shared__ T Us[kGramRows][kGramMaxR + 1];
+// FP64 programs: C = V^T U (r x r, row-major, FP64).  Block b sums rows of its
+// chunk; the last block to finish (ticket) adds the block partials in index
+// order.
+__global__ void __launch_bounds__(kThreads) gram_f64_kernel(const double* __restrict__ V,
+                                                            const double* __restrict__ U,
+                                                            int64_t fs, int n, int r,
+                                                            double* Cpart, unsigned* ticket,
+                                                            double* C, unsigned* status) {
+  __shared__ double Vs[kGramRows][kGramMaxR + 1];
+  __shared__ double Us[kGramRows][kGramMaxR + 1];
   __shared__ bool last;
   const int tid = threadIdx.x;
   const int G = gridDim.x;
@@ -50,8 +55,8 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ V,
       const int c = idx / kGramRows;
       const int j = idx % kGramRows;
       const bool ok = j < nr;
-      Vs[j][c] = ok ? V[(int64_t)c * fs + t0 + j] : T(0);
-      Us[j][c] = ok ? U[(int64_t)c * fs + t0 + j] : T(0);
+      Vs[j][c] = ok ? V[(int64_t)c * fs + t0 + j] : 0.0;
+      Us[j][c] = ok ? U[(int64_t)c * fs + t0 + j] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -60,7 +65,7 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ V,
       if (e < ne) {
         const int c1 = e / r, c2 = e % r;
         double a = acc[i];
-        for (int j = 0; j < nr; ++j) a = fma((double)Vs[j][c1], (double)Us[j][c2], a);
+        for (int j = 0; j < nr; ++j) a = fma(Vs[j][c1], Us[j][c2], a);
         acc[i] = a;
       }
     }
@@ -87,11 +92,107 @@ __global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ V,
   }
 }
 
+// Double-float accumulation (hi + lo, each FP32): the exact product of two
+// floats is p + pe with pe = fma(v, u, -p); hi absorbs it by Knuth's TwoSum
+// and lo collects the rounding errors, so the sum carries about 44 bits.
+// Rounded intrinsics keep the compiler from contracting the error terms.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x, float xe) {
+  const float t = __fadd_rn(hi, x);
+  const float z = __fsub_rn(t, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(x, z));
+  hi = t;
+  lo = __fadd_rn(lo, __fadd_rn(err, xe));
+}
+
+// FP32 programs: per-block partials of C = V^T U in double-float.  GB300's
+// FP64 pipe is narrow, so the FP64-grade sums use FP32 arithmetic; every
+// block of 256 threads takes one 32-row tile per step.
+__global__ void __launch_bounds__(kThreads) gram_df_kernel(const float* __restrict__ V,
+                                                           const float* __restrict__ U,
+                                                           int64_t fs, int n, int r,
+                                                           float2* Cpart) {
+  __shared__ float Vs[kGramRows][kGramMaxR + 1];
+  __shared__ float Us[kGramRows][kGramMaxR + 1];
+  const int tid = threadIdx.x;
+  const int G = gridDim.x;
+  const int ne = r * r;
+  float hi[kGramPerThread], lo[kGramPerThread];
+#pragma unroll
+  for (int i = 0; i < kGramPerThread; ++i) hi[i] = lo[i] = 0.f;
+  for (int t0 = blockIdx.x * kGramRows; t0 < n; t0 += G * kGramRows) {
+    const int nr = min(kGramRows, n - t0);
+    for (int idx = tid; idx < kGramRows * r; idx += kThreads) {
+      const int c = idx / kGramRows;
+      const int j = idx % kGramRows;
+      const bool ok = j < nr;
+      Vs[j][c] = ok ? V[(int64_t)c * fs + t0 + j] : 0.f;
+      Us[j][c] = ok ? U[(int64_t)c * fs + t0 + j] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kGramPerThread; ++i) {
+      const int e = tid + i * kThreads;
+      if (e < ne) {
+        const int c1 = e / r, c2 = e % r;
+        float h = hi[i], l = lo[i];
+        for (int j = 0; j < nr; ++j) {
+          const float v = Vs[j][c1], u = Us[j][c2];
+          const float p = __fmul_rn(v, u);
+          df_add(h, l, p, __fmaf_rn(v, u, -p));
+        }
+        hi[i] = h;
+        lo[i] = l;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < kGramPerThread; ++i) {
+    const int e = tid + i * kThreads;
+    if (e < ne) Cpart[(int64_t)blockIdx.x * ne + e] = make_float2(hi[i], lo[i]);
+  }
+}
+
+// One warp per core entry: lane l adds the partials of blocks l, l + 32, ...
+// in order, then a fixed butterfly combines the lanes (lane 0's sum is kept).
+__global__ void gram_reduce_kernel(const float2* __restrict__ Cpart, int G, int ne, double* C,
+                                   unsigned* status) {
+  const int e = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= ne) return;  // warp-uniform
+  float h = 0.f, l = 0.f;
+  for (int b = lane; b < G; b += 32) {
+    const float2 x = Cpart[(int64_t)b * ne + e];
+    df_add(h, l, x.x, x.y);
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, l, o);
+    df_add(h, l, oh, ol);
+  }
+  if (lane == 0) {
+    const double sum = (double)h + (double)l;
+    if (!isfinite(sum)) atomicOr(status, kStatusNonFinite);
+    C[e] = sum;
+  }
+}
+
 template <typename T>
 cudaError_t launch_gram(const T* V, const T* U, int64_t fs, int n, int r, double* Cpart,
                         unsigned* ticket, double* C, unsigned* status, cudaStream_t s) {
   if (r < 1 || r > kGramMaxR) return cudaErrorInvalidValue;
-  gram_kernel<T><<<gram_grid(n), kThreads, 0, s>>>(V, U, fs, n, r, Cpart, ticket, C, status);
+  const int G = gram_grid(n);
+  if constexpr (std::is_same<T, float>::value) {
+    float2* part = reinterpret_cast<float2*>(Cpart);
+    gram_df_kernel<<<G, kThreads, 0, s>>>(V, U, fs, n, r, part);
+    const int ne = r * r;
+    const int warps_per_block = kThreads / 32;
+    gram_reduce_kernel<<<(ne + warps_per_block - 1) / warps_per_block, kThreads, 0, s>>>(
+        part, G, ne, C, status);
+  } else {
+    gram_f64_kernel<<<G, kThreads, 0, s>>>(V, U, fs, n, r, Cpart, ticket, C, status);
+  }
   return cudaGetLastError();
 }
 

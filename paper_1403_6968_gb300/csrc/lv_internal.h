@@ -14,7 +14,9 @@ constexpr int kStages = 4;      // TMA ring depth (generic passes)
 constexpr int kStagesWs = 6;    // TMA ring depth of the decoupled-ring FP32 passes
 constexpr int kBoxBytes = 1024; // bytes per TMA box row (256 floats / 128 doubles)
 constexpr int kMaxFusedR = 8;   // widest factor block of the fused products pass
-constexpr int kMaxUpdateR = 64; // widest rank of the update-only pass (float)
+constexpr int kMaxProductR = 16;  // widest factor block of an FP32 products-only pass
+constexpr int kMaxUpdateR = 32;   // widest factor block of one update pass (shared-memory
+                                  // broadcasts of the factor rows bound wider blocks)
 
 // Pass modes: which of X = P Xf, Y = P^T Yf and P += Uu Wu^T a launch does.
 enum PassMode : int { kModeXYU = 7, kModeXY = 3, kModeXU = 5, kModeX = 1 };

@@ -101,7 +101,7 @@ cudaError_t run(lv::PassParams base, const CUtensorMap& tm, int n, int r, int sm
     }
   }
   if (do_update) {
-    const int MU = sizeof(T) == 4 ? 64 : 32;
+    const int MU = kMaxUpdateR;
     for (int c0 = 0; c0 < r; c0 += MU) {
       const int w = (r - c0 < MU) ? (r - c0) : MU;
       const PassGeom gu = update_geom(sizeof(T), w, n, sms);

@@ -521,8 +521,10 @@ static cudaError_t launch_fused_t(const PassParams& p, const CUtensorMap& tm, cu
   constexpr bool kWs = std::is_same<T, float>::value;
   const size_t smem =
       kWs ? sizeof(T) * kStagesWs * kBatch * STRIP + sizeof(uint64_t) * (2 * kStagesWs + 2) +
-                kStagesWs * kBatch * R * (sizeof(float) + sizeof(float) + 4 * sizeof(float)) +
-                sizeof(double) * kThreads
+                kStagesWs * kBatch * R *
+                    (((MODE & 4) ? sizeof(float) : 0) + ((MODE & 2) ? sizeof(float) : 0) +
+                     4 * sizeof(float)) +
+                (((MODE & 6) == 6) ? sizeof(double) * kThreads : 0)
           : sizeof(T) * kStages * kBatch * STRIP + sizeof(uint64_t) * kStages +
                 sizeof(T) * (2 * kBatch * R + kBatch * R * (128 + 32 / R)) +
                 sizeof(double) * R * R;
@@ -546,6 +548,8 @@ static cudaError_t fused_by_r(const PassParams& p, const CUtensorMap& tm, int R,
   if (R <= 2) return launch_fused_t<T, 2, MODE>(p, tm, s);
   if (R <= 4) return launch_fused_t<T, 4, MODE>(p, tm, s);
   if (R <= 8) return launch_fused_t<T, 8, MODE>(p, tm, s);
+  if constexpr (std::is_same<T, float>::value && (MODE & 4) == 0)
+    if (R <= kMaxProductR) return launch_fused_t<T, kMaxProductR, MODE>(p, tm, s);
   return cudaErrorInvalidValue;
 }
 
@@ -564,7 +568,7 @@ cudaError_t launch_fused(const PassParams& p, const CUtensorMap& tm, int R, int 
 template <typename T, int R, int COLS>
 static cudaError_t launch_update_t(const PassParams& p, const CUtensorMap& tm, cudaStream_t s) {
   constexpr int STRIP = kThreads * COLS;
-  constexpr bool kWs = std::is_same<T, float>::value && COLS >= 2;
+  constexpr bool kWs = std::is_same<T, float>::value;
   const size_t smem =
       kWs ? sizeof(T) * kStagesWs * kBatch * STRIP + sizeof(uint64_t) * (2 * kStagesWs + 2) +
                 sizeof(float) * kStagesWs * kBatch * R
@@ -592,7 +596,6 @@ cudaError_t launch_update<float>(const PassParams& p, const CUtensorMap& tm, int
   if (R <= 8) return launch_update_t<float, 8, 2>(p, tm, s);
   if (R <= 16) return launch_update_t<float, 16, 2>(p, tm, s);
   if (R <= 32) return launch_update_t<float, 32, 2>(p, tm, s);
-  if (R <= 64) return launch_update_t<float, 64, 1>(p, tm, s);
   return cudaErrorInvalidValue;
 }
 

@@ -100,7 +100,8 @@ __device__ __forceinline__ void rank_update_row(const float* u, const float (&pv
 }
 
 // ---------------------------------------------------------------------------
-// Fused products (+ update) pass, FP32, R in {1, 2, 4, 8}.
+// Fused products (+ update) pass, FP32, R in {1, 2, 4, 8}; products only
+// (no update) also R = 16.
 // Thread (rg = warp / 4, tc = tid % 128) owns columns strip0 + 4 tc .. +3.
 //  R <= 2: row group rg takes rows rg, rg+2, rg+4, rg+6 of every batch (all
 //          R factor columns);
@@ -137,11 +138,12 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * S * STAGE_ELEMS);
   uint64_t* empty = full + S;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
-  // 16-byte aligned so that four u or v values load as one 128-bit word
-  T* Us = reinterpret_cast<T*>(empty + S + 2);  // [S][kBatch][R]
-  T* Vs = Us + S * kBatch * R;                  // [S][kBatch][R]
-  T* Xw = Vs + S * kBatch * R;                  // [S][kBatch][4][R] warp sums
-  double* Csh = reinterpret_cast<double*>(Xw + S * kBatch * 4 * R);  // [kThreads] core sums
+  // 16-byte aligned so that four u or v values load as one 128-bit word;
+  // regions a mode does not use take no space
+  T* Us = reinterpret_cast<T*>(empty + S + 2);   // [S][kBatch][R] (DO_U)
+  T* Vs = Us + (DO_U ? S * kBatch * R : 0);      // [S][kBatch][R] (DO_Y)
+  T* Xw = Vs + (DO_Y ? S * kBatch * R : 0);      // [S][kBatch][4][R] warp sums
+  double* Csh = reinterpret_cast<double*>(Xw + S * kBatch * 4 * R);  // [kThreads] core sums (DO_U && DO_Y)
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -503,8 +505,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 // Update-only pass, FP32.  COLS = 4: two row groups of 128 threads, thread
 // (rg, tc) owns columns strip0 + 4 tc .. +3 and rows rg, rg+2, ... of each
 // batch (each broadcast U row is read by 4 warps); COLS = 2: one group of 256
-// threads owning 2 columns each (for R = 32, whose column factor would not
-// fit the registers of 4 columns).
+// threads owning 2 columns each (R <= 32); COLS = 1: one column each (R = 64,
+// whose column factor fills 64 registers per column).
 // ---------------------------------------------------------------------------
 template <int R, int COLS>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -639,9 +641,11 @@ __global__ void __launch_bounds__(kThreads, 2)
           if constexpr (COLS == 4) {
             const float4 v4 = *reinterpret_cast<const float4*>(sp + j * BOXC);
             pv[0] = v4.x; pv[1] = v4.y; pv[2] = v4.z; pv[3] = v4.w;
-          } else {
+          } else if constexpr (COLS == 2) {
             const float2 v2 = *reinterpret_cast<const float2*>(sp + j * BOXC);
             pv[0] = v2.x; pv[1] = v2.y;
+          } else {
+            pv[0] = sp[j * BOXC];
           }
           float o[COLS];
           rank_update_row<R, COLS>(Ust + j * R, pv, wp, o);
@@ -649,8 +653,10 @@ __global__ void __launch_bounds__(kThreads, 2)
           if (vec_ok) {
             if constexpr (COLS == 4)
               *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
-            else
+            else if constexpr (COLS == 2)
               *reinterpret_cast<float2*>(dst) = make_float2(o[0], o[1]);
+            else
+              dst[0] = o[0];
           } else {
 #pragma unroll
             for (int k = 0; k < COLS; ++k)

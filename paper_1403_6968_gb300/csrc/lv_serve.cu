@@ -42,6 +42,7 @@ using Clock = std::chrono::steady_clock;
 struct Request {
   uint64_t ticket = 0;
   int32_t rank = 0;
+  int64_t row = -1;          // >= 0: row update dA = e_row v^T (V = v, U unused)
   const float* U = nullptr;  // n x rank row-major, ld = rank
   const float* V = nullptr;
   std::vector<float> own;    // storage when the server copied the factors
@@ -66,6 +67,7 @@ struct ServedView {
   // the refresh in flight
   bool busy = false;
   std::vector<Request> batch;
+  std::vector<int64_t> batch_rows;  // distinct rows of the batch's row updates
   int32_t batch_rank = 0;
   double start = 0.0;
 };
@@ -190,12 +192,26 @@ linview_status issue_batch(linview_server* s, ServedView* v) {
   float* V = v->pin + (size_t)n * R;
   int c0 = 0;
   for (const Request& r : v->batch) {
+    if (r.row >= 0) continue;
     const int rk = r.rank;
     for (int64_t i = 0; i < n; ++i) {
       std::memcpy(U + i * R + c0, r.U + i * rk, sizeof(float) * rk);
       std::memcpy(V + i * R + c0, r.V + i * rk, sizeof(float) * rk);
     }
     c0 += rk;
+  }
+  // one column per distinct row: U = e_row, V = the sum of its v's in arrival order
+  for (const int64_t row : v->batch_rows) {
+    for (int64_t i = 0; i < n; ++i) {
+      U[i * R + c0] = 0.f;
+      V[i * R + c0] = 0.f;
+    }
+    U[row * R + c0] = 1.f;
+    for (const Request& r : v->batch) {
+      if (r.row != row) continue;
+      for (int64_t i = 0; i < n; ++i) V[i * R + c0] += r.V[i];
+    }
+    ++c0;
   }
   linview_status st = linview_apply_delta(v->prog, 0, R, U, R, V, R, 0, v->stream);
   if (st != LINVIEW_OK) return st;
@@ -293,9 +309,18 @@ void scheduler(linview_server* s) {
         if (!pick || v->queue.front().arrival < pick->queue.front().arrival) pick = v;
       }
       if (!pick) break;
+      // row updates to a row already in the batch add no rank: their v's
+      // are summed into that row's column (e_i v1^T + e_i v2^T = e_i (v1 + v2)^T)
       int32_t R = 0;
-      while (!pick->queue.empty() && R + pick->queue.front().rank <= s->r_cap) {
-        R += pick->queue.front().rank;
+      std::vector<int64_t>& rows = pick->batch_rows;
+      rows.clear();
+      while (!pick->queue.empty()) {
+        const Request& f = pick->queue.front();
+        int32_t add = f.rank;
+        if (f.row >= 0) add = std::find(rows.begin(), rows.end(), f.row) == rows.end() ? 1 : 0;
+        if (R + add > s->r_cap) break;
+        if (f.row >= 0 && add) rows.push_back(f.row);
+        R += add;
         pick->batch.push_back(std::move(pick->queue.front()));
         pick->queue.pop_front();
       }
@@ -464,9 +489,34 @@ linview_status linview_server_submit(linview_server* s, int32_t view, int32_t ra
   return LINVIEW_OK;
 }
 
+linview_status linview_server_submit_row(linview_server* s, int32_t view, int64_t row,
+                                         const void* v, double arrival_s, uint64_t* ticket) {
+  if (!s || !v) return set_err(LINVIEW_EINVAL, "null argument");
+  int64_t n = 0;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    if (view < 0 || view >= (int32_t)s->views.size())
+      return set_err(LINVIEW_EINVAL, "bad view id");
+    n = s->views[view]->n;
+  }
+  if (row < 0 || row >= n) return set_err(LINVIEW_EINVAL, "row out of range");
+  Request r;
+  r.rank = 1;
+  r.row = row;
+  r.own.assign(static_cast<const float*>(v), static_cast<const float*>(v) + n);
+  r.V = r.own.data();
+  std::lock_guard<std::mutex> g(s->mu);
+  r.arrival = arrival_s >= 0 ? arrival_s : s->now();
+  const uint64_t tk = s->next_ticket;
+  LV_TRY(enqueue(s, view, std::move(r)));
+  if (ticket) *ticket = tk;
+  s->work_cv.notify_all();
+  return LINVIEW_OK;
+}
+
 linview_status linview_server_replay(linview_server* s, int64_t count, const double* t_s,
                                      const int32_t* view, const int32_t* rank, const void* factors,
-                                     const int64_t* offset) {
+                                     const int64_t* offset, const int64_t* rows) {
   if (!s || (count > 0 && (!t_s || !view || !rank || !factors || !offset)))
     return set_err(LINVIEW_EINVAL, "null argument");
   {
@@ -474,7 +524,10 @@ linview_status linview_server_replay(linview_server* s, int64_t count, const dou
     for (int64_t i = 0; i < count; ++i) {
       if (view[i] < 0 || view[i] >= (int32_t)s->views.size())
         return set_err(LINVIEW_EINVAL, "bad view id in the trace");
-      if (rank[i] < 1 || rank[i] > s->r_cap) return set_err(LINVIEW_ERANK, "rank outside 1..r_cap");
+      if (rows && rows[i] >= s->views[view[i]]->n)
+        return set_err(LINVIEW_EINVAL, "row out of range in the trace");
+      if (!(rows && rows[i] >= 0) && (rank[i] < 1 || rank[i] > s->r_cap))
+        return set_err(LINVIEW_ERANK, "rank outside 1..r_cap");
       if (i > 0 && t_s[i] < t_s[i - 1]) return set_err(LINVIEW_EINVAL, "t_s must be non-decreasing");
     }
   }
@@ -491,11 +544,17 @@ linview_status linview_server_replay(linview_server* s, int64_t count, const dou
         std::this_thread::yield();
     }
     Request r;
-    r.rank = rank[i];
     std::lock_guard<std::mutex> g(s->mu);
     const int64_t n = s->views[view[i]]->n;
-    r.U = f + offset[i];
-    r.V = r.U + n * r.rank;
+    if (rows && rows[i] >= 0) {
+      r.rank = 1;
+      r.row = rows[i];
+      r.V = f + offset[i];
+    } else {
+      r.rank = rank[i];
+      r.U = f + offset[i];
+      r.V = r.U + n * r.rank;
+    }
     r.arrival = due;
     LV_TRY(enqueue(s, view[i], std::move(r)));
     s->work_cv.notify_all();

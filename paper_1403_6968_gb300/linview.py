@@ -330,20 +330,32 @@ class Server:
                u.shape[1], C.c_void_p(w.ctypes.data), w.shape[1], float(arrival_s), C.byref(t))
         return t.value
 
-    def replay(self, t_s, views, ranks, factors, offsets):
+    def submit_row(self, view, row, v, arrival_s=-1.0):
+        """Row update dA = e_row v^T (coalesced by row with other queued ones)."""
+        w = np.ascontiguousarray(np.asarray(v, dtype=np.float32).reshape(-1))
+        t = C.c_uint64()
+        L.call("linview_server_submit_row", self.h, int(view), int(row),
+               C.c_void_p(w.ctypes.data), float(arrival_s), C.byref(t))
+        return t.value
+
+    def replay(self, t_s, views, ranks, factors, offsets, rows=None):
         """Open-loop load: request i at t_s[i] seconds after the call; its U
-        (n x rank, row-major) at factors[offsets[i]:], V right after it.
-        ``factors`` must stay alive until ``drain`` returns."""
+        (n x rank, row-major) at factors[offsets[i]:], V right after it; with
+        ``rows`` given and rows[i] >= 0, the row update e_rows[i] v^T with v
+        at factors[offsets[i]:].  ``factors`` must stay alive until ``drain``
+        returns."""
         t_s = np.ascontiguousarray(t_s, dtype=np.float64)
         views = np.ascontiguousarray(views, dtype=np.int32)
         ranks = np.ascontiguousarray(ranks, dtype=np.int32)
         offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        rows_a = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
         if factors.dtype != np.float32 or not factors.flags.c_contiguous:
             raise TypeError("factors must be a contiguous float32 array")
         self._keep.append(factors)
         L.call("linview_server_replay", self.h, len(t_s), C.c_void_p(t_s.ctypes.data),
                C.c_void_p(views.ctypes.data), C.c_void_p(ranks.ctypes.data),
-               C.c_void_p(factors.ctypes.data), C.c_void_p(offsets.ctypes.data))
+               C.c_void_p(factors.ctypes.data), C.c_void_p(offsets.ctypes.data),
+               None if rows_a is None else C.c_void_p(rows_a.ctypes.data))
 
     def drain(self, timeout_s=0.0):
         L.call("linview_server_drain", self.h, float(timeout_s))

@@ -235,3 +235,34 @@ def test_full_size_sampled_rows():
         acur += u.astype(np.float64) @ v.astype(np.float64).T
     prog.sync()
     check()
+
+
+def test_profiling_inside_graph_replays():
+    """Per-pass timing runs inside the replayed graphs (instrumented copies)
+    and changes no result bit."""
+    n, k = 1024, 16
+    a = li.power_matrix(n, seed=41, dtype=np.float32)
+    ups = li.row_update_stream(n, 28, seed=42, dtype=np.float32)
+    plain = _prog("power_sum", [a], k=k, r_max=1)
+    prof = _prog("power_sum", [a], k=k, r_max=1)
+    prof.set_profiling(True)
+    for i, v in ups[:3]:
+        plain.apply_row_delta(i, _dev(v))
+        prof.apply_row_delta(i, _dev(v))
+    prof.reset_stats()
+    for i, v in ups[3:8]:
+        plain.apply_row_delta(i, _dev(v))
+        prof.apply_row_delta(i, _dev(v))
+    st = prof.pass_stats(0)
+    passes = 9  # 4 fused level passes, 3 sums updates, final P_16 and S'_16 updates
+    assert st["launches"] == 5 * passes
+    assert st["ms"] > 0 and st["bytes"] == st["launches"] * 2.0 * n * n * 4
+    assert prof.pass_stats(1)["launches"] + prof.pass_stats(2)["launches"] == st["launches"]
+    for i, v in ups[8:]:
+        plain.apply_row_delta(i, _dev(v))
+        prof.apply_row_delta(i, _dev(v))
+    assert prof.pass_stats(0)["launches"] == 16 * passes  # one sample per instrumented copy
+    for vid in range(plain.num_views()):
+        assert torch.equal(plain.read_view(vid), prof.read_view(vid))
+    plain.close()
+    prof.close()

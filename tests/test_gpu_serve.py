@@ -167,6 +167,43 @@ def _body_serve_remove_cancels_queue_and_errors():
         srv.close()
 
 
+def _body_serve_row_coalescing():
+    """Queued row updates to one view merge by row: each delta's rank is the
+    number of distinct rows of the requests it carries (Section 6, batch
+    updates), and the view equals the oracle on A + sum_j e_{i_j} v_j^T."""
+    P = _pkg()
+    n, count = 512, 60
+    a0 = li.power_matrix(n, seed=50, dtype=np.float32)
+    rows, vs = li.zipf_row_batch(n, count, 2.0, seed=51)
+    assert len(np.unique(rows)) < count  # the batch repeats rows
+    srv = P.Server(max_inflight=1, r_cap=8)
+    try:
+        v = srv.add_view(a0, K)
+        srv.replay(np.zeros(count), np.zeros(count, np.int32), np.ones(count, np.int32),
+                   np.ascontiguousarray(vs.reshape(-1)), np.arange(count) * n, rows=rows)
+        srv.drain(timeout_s=120)
+        recs = srv.poll()
+        assert len(recs) == count and all(r["status"] == 0 for r in recs)
+        batches = {}
+        for r in recs:
+            batches.setdefault(r["start_s"], []).append(r)
+        merged = False
+        for group in batches.values():
+            distinct = {int(rows[r["ticket"] - 1]) for r in group}
+            assert all(r["batch_rank"] == len(distinct) for r in group)
+            assert all(r["batch_size"] == len(group) for r in group)
+            merged |= len(group) > len(distinct)
+        assert merged
+        assert srv.stats()["refreshes"] == len(batches)
+        got = srv.program(v).read_view(L).cpu().numpy().astype(np.float64)
+    finally:
+        srv.close()
+    af = a0.astype(np.float64).copy()
+    for i, w in zip(rows, vs):
+        af[i] += w.astype(np.float64)
+    assert rel_frob(got, op.reeval_powers(af, K)[K]) <= TOL
+
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -187,6 +224,10 @@ def test_serve_admission_by_memory():
 
 def test_serve_remove_cancels_queue_and_errors():
     _run_child("serve_remove_cancels_queue_and_errors")
+
+
+def test_serve_row_coalescing():
+    _run_child("serve_row_coalescing")
 
 
 @pytest.mark.parametrize("kind,n,k,r_max", [("power", 1000, 16, 8), ("power", 256, 8, 1),
