@@ -290,8 +290,10 @@ linview_status linview_estimate_device_bytes(const linview_program_desc* desc, i
  *  - the requests queued for one view while it is busy are coalesced into a
  *    single delta of higher rank, [U_1 .. U_m][V_1 .. V_m]^T = sum_j U_j V_j^T
  *    (the concatenation rule of factored deltas, Section 3.2; the paper's
- *    batch updates, Section 6, Table 4), as long as the total rank stays
- *    within ``r_cap``; the rest waits for the next refresh of that view;
+ *    batch updates, Section 6, Table 4): in arrival order, every queued
+ *    request that keeps the total rank within ``r_cap`` joins (deltas add,
+ *    so the order of application does not change the result); the oldest
+ *    request always joins, the others wait for the next refresh;
  *  - a view is admitted (its program created) only when its device bytes
  *    (linview_estimate_device_bytes) fit both the server budget and the free
  *    device memory; otherwise it waits, with its requests queued, and is

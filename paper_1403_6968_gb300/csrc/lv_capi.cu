@@ -83,6 +83,7 @@ struct View {
   int64_t rows = 0, cols = 0, ld = 0;
   bool square = false;  // has a tensor map for view passes
   CUtensorMap tmap;
+  CUtensorMap tmap_tc;  // FP32: 32 x 128 boxes, 128B swizzle (tensor-core update pass)
 };
 
 struct linview_program {
@@ -100,6 +101,10 @@ struct linview_program {
   void* Uar = nullptr;
   void* Var = nullptr;
   void* Wsum = nullptr;  // explicit V_h K_h^T for sums programs with wide factors
+  // tensor-core update pass: split factors A_cat, B_cat (n x 64 each) and their maps
+  float* tcA = nullptr;
+  float* tcB = nullptr;
+  CUtensorMap tmA, tmB;
   int64_t fs = 0;
   int Rcap = 0;
   // partial sums of the view passes
@@ -221,6 +226,9 @@ static linview_status add_square_view(linview_program* p, int64_t n) {
   if (!make_tmap(&v.tmap, v.ptr, p->elem, v.ld, rows_pad, v.ld))
     return fail(LINVIEW_EDEVICE, "cuTensorMapEncodeTiled failed for an %lld x %lld view",
                 (long long)n, (long long)n);
+  if (p->elem == 4 && !make_tmap_sw128(&v.tmap_tc, v.ptr, n, n, v.ld, 128))
+    return fail(LINVIEW_EDEVICE, "cuTensorMapEncodeTiled (swizzled) failed for an %lld x %lld view",
+                (long long)n, (long long)n);
   p->views.push_back(v);
   return LINVIEW_OK;
 }
@@ -341,6 +349,19 @@ static linview_status run_update(linview_program* p, const View& v, const T* Uu,
   constexpr int MU = kMaxUpdateR;
   for (int c0 = 0; c0 < r; c0 += MU) {
     const int w = (r - c0 < MU) ? (r - c0) : MU;
+    if constexpr (sizeof(T) == 4) {
+      // blocks wider than the CUDA-core pass sustains go to the tensor cores
+      if (p->tcA && w > kMaxProductR && suffix_rin == 0) {
+        ProfScope ps(p, s, 2.0 * (double)v.rows * (double)v.rows * sizeof(T), 2);
+        LV_CUDA(launch_tc_update(v.tmap_tc, p->tmA, p->tmB, static_cast<float*>(v.ptr), v.ld,
+                                 p->tcA, p->tcB,
+                                 reinterpret_cast<const float*>(Uu) + (int64_t)c0 * p->fs,
+                                 reinterpret_cast<const float*>(Wu) + (int64_t)c0 * p->fs, p->fs,
+                                 (int)v.rows, w, p->sms, p->status, s));
+        p->all_launches++;  // the split kernel
+        continue;
+      }
+    }
     const PassGeom g = update_geom(sizeof(T), w, (int)v.rows, p->sms);
     PassParams pp{};
     pp.P = v.ptr;
@@ -480,6 +501,12 @@ static bool powers_wide_sums(const linview_program_desc& d) {
   return d.kind == LINVIEW_POWER_SUM && ((int64_t)d.r_max * d.k > mu || d.r_max > 8);
 }
 
+// FP32 power programs whose update blocks can be wider than kMaxProductR
+// refresh those blocks on the tensor cores.
+static bool powers_uses_tc(const linview_program_desc& d) {
+  return d.precision == LINVIEW_F32 && (int64_t)d.r_max * d.k > kMaxProductR;
+}
+
 // Device bytes powers_create allocates (with the buffers every program has),
 // in the same order; linview_estimate_device_bytes reports it.
 static int64_t powers_device_bytes(const linview_program_desc& d, int sms) {
@@ -497,6 +524,7 @@ static int64_t powers_device_bytes(const linview_program_desc& d, int sms) {
   const int64_t half = Rcap / 2 > 0 ? Rcap / 2 : 1;
   b += (int64_t)g.gC * half * fs * elem + (int64_t)g.gR * half * fs * elem;
   b += 2 * n * d.r_max * elem;
+  if (powers_uses_tc(d)) b += tc_split_floats(n) * 4;
   return b;
 }
 
@@ -531,6 +559,15 @@ static linview_status powers_create(linview_program* p, const void* const* input
   // host-side update factors are staged here (allocated now so that an
   // update never allocates)
   LV_TRY(ensure_stage(p, (size_t)2 * n * p->d.r_max * p->elem));
+  if (powers_uses_tc(p->d)) {
+    void* tc = nullptr;
+    LV_TRY(dalloc(p, (size_t)tc_split_floats(n) * sizeof(float), &tc));
+    p->tcA = static_cast<float*>(tc);
+    p->tcB = p->tcA + tc_split_floats(n) / 2;
+    if (!make_tmap_sw128(&p->tmA, p->tcA, 64, n, 64, 128) ||
+        !make_tmap_sw128(&p->tmB, p->tcB, 64, n, 64, 64))
+      return fail(LINVIEW_EDEVICE, "cuTensorMapEncodeTiled failed for the split factors");
+  }
   return powers_reeval(p, s);
 }
 
@@ -1470,6 +1507,18 @@ linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp
   LV_CUDA(cudaMallocAsync(&stw, sizeof(unsigned) * 4, s));
   LV_CUDA(cudaMemsetAsync(stw, 0, sizeof(unsigned) * 4, s));
   tmp.status = static_cast<unsigned*>(stw);
+  void* tcs = nullptr;  // split factors of the tensor-core update pass (FP32, r > 16)
+  if (e == 4 && do_update && r > kMaxProductR) {
+    LV_CUDA(cudaMallocAsync(&tcs, (size_t)tc_split_floats(n) * sizeof(float), s));
+    tmp.tcA = static_cast<float*>(tcs);
+    tmp.tcB = tmp.tcA + tc_split_floats(n) / 2;
+    if (!make_tmap_sw128(&tmp.tmA, tmp.tcA, 64, n, 64, 128) ||
+        !make_tmap_sw128(&tmp.tmB, tmp.tcB, 64, n, 64, 64) ||
+        !make_tmap_sw128(&v.tmap_tc, P, n, n, ldp, 128)) {
+      cudaFreeAsync(tcs, s);
+      return fail(LINVIEW_EDEVICE, "tensor map encode failed");
+    }
+  }
   tmp.Xpart = xp;
   tmp.Ypart = yp;
   linview_status st = LINVIEW_OK;
@@ -1510,6 +1559,7 @@ linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp
   cudaMemcpyAsync(&hs, stw, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
   if (xp) cudaFreeAsync(xp, s);
   if (yp) cudaFreeAsync(yp, s);
+  if (tcs) cudaFreeAsync(tcs, s);
   cudaFreeAsync(stw, s);
   LV_CUDA(cudaStreamSynchronize(s));
   if (st == LINVIEW_OK && (hs & kStatusTimeout)) st = fail(LINVIEW_ETIMEOUT, "bounded wait expired");

@@ -58,6 +58,23 @@ PassGeom update_geom(int elem_bytes, int R, int n, int num_sms);
 bool make_tmap(CUtensorMap* out, const void* base, int elem_bytes, int64_t cols, int64_t rows,
                int64_t ld);
 
+// Host: FP32 tensor map with 32-column x box_rows boxes and 128-byte swizzle
+// (operand and tile layout of the tensor-core update pass).
+bool make_tmap_sw128(CUtensorMap* out, const void* base, int64_t cols, int64_t rows, int64_t ld,
+                     int box_rows);
+// Floats of the split-factor scratch of the tensor-core update pass (A_cat
+// then B_cat, n x 64 each).
+int64_t tc_split_floats(int64_t n);
+// Tensor-core update pass P += U W^T (FP32 view, 17 <= r <= 32 factor
+// columns, split TF32): splits U, W into the scratch, then one persistent
+// launch over 128 x 64 tiles.  tmP: make_tmap_sw128 over the view P (box
+// rows 128, row stride ldp); tmA / tmB: over A_cat (box rows 128) / B_cat
+// (box rows 64).
+cudaError_t launch_tc_update(const CUtensorMap& tmP, const CUtensorMap& tmA,
+                             const CUtensorMap& tmB, float* P, int64_t ldp, float* Acat,
+                             float* Bcat, const float* U, const float* W, int64_t fs, int n, int r,
+                             int num_sms, unsigned* status, cudaStream_t s);
+
 // Launchers (return cudaGetLastError()).  R is the runtime factor width,
 // bucketed internally to a compiled width.
 template <typename T>

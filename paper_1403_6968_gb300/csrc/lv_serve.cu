@@ -309,21 +309,30 @@ void scheduler(linview_server* s) {
         if (!pick || v->queue.front().arrival < pick->queue.front().arrival) pick = v;
       }
       if (!pick) break;
-      // row updates to a row already in the batch add no rank: their v's
-      // are summed into that row's column (e_i v1^T + e_i v2^T = e_i (v1 + v2)^T)
+      // Take, in arrival order, every queued request that fits the rank cap
+      // (the oldest always does).  Row updates to a row already in the batch
+      // add no rank: their v's are summed into that row's column
+      // (e_i v1^T + e_i v2^T = e_i (v1 + v2)^T).  Deltas add, so a request
+      // may join a batch ahead of an older one that did not fit; that one
+      // leads the next batch.
       int32_t R = 0;
       std::vector<int64_t>& rows = pick->batch_rows;
       rows.clear();
+      std::deque<Request> rest;
       while (!pick->queue.empty()) {
-        const Request& f = pick->queue.front();
+        Request f = std::move(pick->queue.front());
+        pick->queue.pop_front();
         int32_t add = f.rank;
         if (f.row >= 0) add = std::find(rows.begin(), rows.end(), f.row) == rows.end() ? 1 : 0;
-        if (R + add > s->r_cap) break;
+        if (R + add > s->r_cap) {
+          rest.push_back(std::move(f));
+          continue;
+        }
         if (f.row >= 0 && add) rows.push_back(f.row);
         R += add;
-        pick->batch.push_back(std::move(pick->queue.front()));
-        pick->queue.pop_front();
+        pick->batch.push_back(std::move(f));
       }
+      pick->queue.swap(rest);
       pick->batch_rank = R;
       pick->busy = true;
       pick->start = s->now();

@@ -1,0 +1,466 @@
+// Tensor-core update pass (tcgen05, sm_103a): P += U W^T for a factor block
+// of 17..32 columns, the in-place rank-r refresh of a view (App. A, the
+// "P_h += U_h V_h^T" step; the final P_k update) once r is past what the
+// shared-memory broadcasts of the CUDA-core pass sustain at HBM speed.
+//
+// Arithmetic: split TF32 ("3xTF32").  Each FP32 factor value x is split as
+// x = hi + lo with hi = x with the low 13 mantissa bits cleared (exact in
+// TF32) and lo = x - hi (exact in FP32), and
+//   U W^T ~= hi(U) hi(W)^T + lo(U) hi(W)^T + hi(U) lo(W)^T
+// accumulated in FP32 in tensor memory: about 2^-22 relative error per
+// product, i.e. FP32 accuracy for the delta.  A = [hi(U) | lo(U)] and
+// B = [hi(W) | lo(W)] (row-major, 32 columns per half, zero padded); the
+// three products are one MMA chain over the K-chunk pairs (hi, hi), (lo, hi),
+// (hi, lo).
+//
+// Tiles: 128 rows x 64 columns of P.  A persistent grid (one CTA per SM)
+// walks the tiles row-block by row-block; per CTA:
+//   warp 0     TMA producer: A block (48 KB, reloaded when the row block
+//              changes), B tile (double buffered) and P tile (4 stages);
+//   warp 1     allocates 128 TMEM columns (two 64-column FP32 accumulators)
+//              and issues the MMAs from one thread;
+//   warps 2-5  epilogue: TMEM -> registers, + P (shared, 128B-swizzled),
+//              back to shared memory, TMA store (by one thread once the four
+//              warps have arrived on an mbarrier; a stage is released when
+//              its store has been read out, up to 2 stores in flight).
+// Every mbarrier wait is bounded; an expired wait latches LINVIEW_ETIMEOUT,
+// aborts the CTA's loops, drains the copies in flight and frees the TMEM.
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include "lv_device.cuh"
+#include "lv_internal.h"
+
+namespace lv {
+
+namespace {
+
+constexpr int kBM = 128;                 // tile rows (MMA M)
+constexpr int kBN = 64;                  // tile columns (MMA N)
+constexpr int kRp = 32;                  // factor columns per block (padded)
+constexpr int kK = 2 * kRp;              // columns of A_cat / B_cat: hi and lo halves
+constexpr int kKC = kK / 32;             // 128-byte K chunks (32 floats): hi, lo
+constexpr int kTcThreads = 192;
+constexpr uint32_t kABytes = kKC * kBM * 128;   // 32 KB
+constexpr uint32_t kBBytes = kKC * kBN * 128;   // 16 KB
+constexpr uint32_t kPBytes = 2 * kBM * 128;     // 32 KB (two 32-column boxes)
+constexpr int kPS = 5;                          // P tile stages
+constexpr int kStoresInFlight = 1;              // TMA stores not yet read out
+constexpr uint32_t kTmemCols = 2 * kBN;         // two accumulators
+
+// shared-memory layout (offsets from a 1024-byte aligned base)
+constexpr uint32_t kOffA = 0;
+constexpr uint32_t kOffB = kOffA + kABytes;          // 2 buffers
+constexpr uint32_t kOffP = kOffB + 2 * kBBytes;      // kPS buffers
+constexpr uint32_t kOffBar = kOffP + kPS * kPBytes;
+constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;  // + alignment slack
+
+// instruction descriptor: D F32, A/B TF32, both K-major, N = 64, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+// shared-memory matrix descriptor: K-major operand in 128-byte swizzled rows,
+// 8-row groups 1024 bytes apart (the layout TMA writes with SWIZZLE_128B)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);         // start address
+  d |= (uint64_t)1u << 16;                          // leading byte offset (unused)
+  d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)1u << 46;                          // descriptor version
+  d |= (uint64_t)2u << 61;                          // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const void* tmap, const void* src, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+          reinterpret_cast<uint64_t>(tmap)),
+      "r"(x), "r"(y), "r"(smem_u32(src))
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait0() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+struct TcBars {
+  uint64_t a_full;
+  uint64_t b_full[2], b_empty[2];
+  uint64_t p_full[kPS], p_empty[kPS];
+  uint64_t acc_full[2], acc_empty[2];
+  uint64_t ep_done[kPS];  // the 4 epilogue warps have written their rows of a P tile
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                        unsigned* status) {
+  if (*abort_flag) return false;
+  if (mbar_wait_bounded(bar, parity, status)) return true;
+  *abort_flag = 1;
+  return false;
+}
+
+// P (n x n, row-major, tensor map tmP: box 32 x 128, 128B swizzle) +=
+// A_cat B_cat^T with A_cat, B_cat n x 64 row-major (tmA: box 32 x 128,
+// tmB: box 32 x 64, both 128B swizzle).
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_update_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmA,
+                     const __grid_constant__ CUtensorMap tmB, float* P, int64_t ldp, int n,
+                     unsigned* status) {
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  const uint32_t raw = smem_u32(tc_smem_raw);
+  unsigned char* base = tc_smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  TcBars* bars = reinterpret_cast<TcBars*>(base + kOffBar);
+  volatile int* abort_flag = &bars->abort;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+
+  const int nrb = (n + kBM - 1) / kBM;
+  const int ncb = (n + kBN - 1) / kBN;
+  const long long T = (long long)nrb * ncb;
+  const long long t0 = T * blockIdx.x / gridDim.x;
+  const long long t1 = T * (blockIdx.x + 1) / gridDim.x;
+  const int ntile = (int)(t1 - t0);
+
+  if (tid == 0) {
+    prefetch_tmap(&tmP);
+    prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
+    mbar_init(&bars->a_full, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bars->b_full[i], 1);
+      mbar_init(&bars->b_empty[i], 1);
+      mbar_init(&bars->acc_full[i], 1);
+      mbar_init(&bars->acc_empty[i], 4);  // one arrival per epilogue warp
+    }
+    for (int i = 0; i < kPS; ++i) {
+      mbar_init(&bars->p_full[i], 1);
+      mbar_init(&bars->p_empty[i], 1);
+      mbar_init(&bars->ep_done[i], 4);
+    }
+    bars->abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {  // TMEM: two 64-column FP32 accumulators
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&bars->tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int cur_rb = -1;
+      int b_issued = 0, p_issued = 0, a_issued = 0;  // loads issued (for the abort drain)
+      for (int i = 0; i < ntile && !*abort_flag; ++i) {
+        const long long t = t0 + i;
+        const int rb = (int)(t / ncb), cb = (int)(t % ncb);
+        const int buf = i & 1, use = i >> 1;
+        if (rb != cur_rb) {
+          // the MMAs of the previous tile read the old A block
+          if (i > 0 && !tc_wait(&bars->acc_full[(i - 1) & 1], ((i - 1) >> 1) & 1, abort_flag,
+                                status))
+            break;
+          fence_proxy_async();
+          mbar_arrive_expect_tx(&bars->a_full, kABytes);
+          for (int kc = 0; kc < kKC; ++kc)
+            tma_load_2d(base + kOffA + kc * kBM * 128, &tmA, kc * 32, rb * kBM, &bars->a_full);
+          ++a_issued;
+          cur_rb = rb;
+        }
+        if (use >= 1 && !tc_wait(&bars->b_empty[buf], (use - 1) & 1, abort_flag, status)) break;
+        mbar_arrive_expect_tx(&bars->b_full[buf], kBBytes);
+        for (int kc = 0; kc < kKC; ++kc)
+          tma_load_2d(base + kOffB + buf * kBBytes + kc * kBN * 128, &tmB, kc * 32, cb * kBN,
+                      &bars->b_full[buf]);
+        ++b_issued;
+        const int ps = i % kPS, puse = i / kPS;
+        if (puse >= 1 && !tc_wait(&bars->p_empty[ps], (puse - 1) & 1, abort_flag, status)) break;
+        mbar_arrive_expect_tx(&bars->p_full[ps], kPBytes);
+        for (int h = 0; h < 2; ++h)
+          tma_load_2d(base + kOffP + ps * kPBytes + h * kBM * 128, &tmP, cb * kBN + 32 * h,
+                      rb * kBM, &bars->p_full[ps]);
+        ++p_issued;
+      }
+      if (*abort_flag) {
+        // wait (bounded) until every load issued has landed before the CTA exits
+        for (int j = 0; j < a_issued; ++j) mbar_wait_bounded(&bars->a_full, j & 1, nullptr);
+        for (int j = 0; j < b_issued; ++j)
+          mbar_wait_bounded(&bars->b_full[j & 1], (j >> 1) & 1, nullptr);
+        for (int j = 0; j < p_issued; ++j)
+          mbar_wait_bounded(&bars->p_full[j % kPS], (j / kPS) & 1, nullptr);
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int cur_rb = -1, a_loads = 0, issued = 0;
+      for (int i = 0; i < ntile && !*abort_flag; ++i) {
+        const long long t = t0 + i;
+        const int rb = (int)(t / ncb);
+        const int buf = i & 1, use = i >> 1;
+        if (rb != cur_rb) {
+          if (!tc_wait(&bars->a_full, a_loads & 1, abort_flag, status)) break;
+          ++a_loads;
+          cur_rb = rb;
+        }
+        if (!tc_wait(&bars->b_full[buf], use & 1, abort_flag, status)) break;
+        if (use >= 1 && !tc_wait(&bars->acc_empty[buf], (use - 1) & 1, abort_flag, status)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + buf * kBN;
+        const uint32_t a0 = smem_u32(base + kOffA);
+        const uint32_t b0 = smem_u32(base + kOffB + buf * kBBytes);
+        // (A chunk, B chunk): hi*hi, lo*hi, hi*lo
+        constexpr int kPairA[3] = {0, 1, 0};
+        constexpr int kPairB[3] = {0, 0, 1};
+#pragma unroll
+        for (int pr = 0; pr < 3; ++pr) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {  // K = 8 per MMA: 32 bytes of a 128-byte row
+            const uint64_t ad = sw128_desc(a0 + kPairA[pr] * kBM * 128 + kk * 32);
+            const uint64_t bd = sw128_desc(b0 + kPairB[pr] * kBN * 128 + kk * 32);
+            tc_mma(d, ad, bd, kIdesc, (pr | kk) != 0 ? 1u : 0u);
+          }
+        }
+        tc_commit(&bars->b_empty[buf]);
+        tc_commit(&bars->acc_full[buf]);
+        issued = i + 1;
+      }
+      if (*abort_flag && issued > 0) {
+        // the MMAs issued must finish before the TMEM is freed
+        const int j = issued - 1;
+        mbar_wait_bounded(&bars->acc_full[j & 1], (j >> 1) & 1, nullptr);
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31
+    const int row = quarter * 32 + lane;        // tile row of this thread
+    const bool leader = (warp == 2 && lane == 0);
+    // A TMA store writes whole 16-byte chunks at the right edge of the
+    // tensor; when n % 4 != 0 the last tile column is stored element by
+    // element instead, so that no column >= n (caller padding) is written.
+    const bool ragged = (n & 3) != 0;
+    for (int i = 0; i < ntile; ++i) {
+      const long long t = t0 + i;
+      const int rb = (int)(t / ncb), cb = (int)(t % ncb);
+      const int buf = i & 1, use = i >> 1;
+      const int ps = i % kPS, puse = i / kPS;
+      bool ok = tc_wait(&bars->acc_full[buf], use & 1, abort_flag, status) &&
+                tc_wait(&bars->p_full[ps], puse & 1, abort_flag, status);
+      // the TMEM loads below are warp-collective: the warp leaves together
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      float acc[kBN];
+      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + buf * kBN;
+#pragma unroll
+      for (int q = 0; q < kBN / 16; ++q) {
+        float v[16];
+        tmem_ld16(ta + q * 16, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[q * 16 + e] = v[e];
+      }
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
+      // P tile: two 32-column boxes, rows of 128 bytes, 16-byte chunk j of
+      // row r stored at chunk j ^ (r % 8)
+      unsigned char* pt = base + kOffP + ps * kPBytes;
+      const bool direct = ragged && cb == ncb - 1;
+      const int grow = rb * kBM + row;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float4* q = reinterpret_cast<float4*>(pt + h * kBM * 128 + row * 128 +
+                                                ((j ^ (row & 7)) << 4));
+          float4 pv = *q;
+          const int c = h * 32 + j * 4;
+          pv.x += acc[c];
+          pv.y += acc[c + 1];
+          pv.z += acc[c + 2];
+          pv.w += acc[c + 3];
+          if (!direct) {
+            *q = pv;
+          } else if (grow < n) {
+            const int gc = cb * kBN + c;
+            float* dst = P + (int64_t)grow * ldp + gc;
+            if (gc + 0 < n) dst[0] = pv.x;
+            if (gc + 1 < n) dst[1] = pv.y;
+            if (gc + 2 < n) dst[2] = pv.z;
+            if (gc + 3 < n) dst[3] = pv.w;
+          }
+        }
+      }
+      // make the rows visible to the TMA store (async proxy); the leader
+      // stores once all four warps have arrived (a bounded wait, no
+      // unbounded named barrier)
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bars->ep_done[ps]);
+      bool stop = false;
+      if (leader) {
+        if (tc_wait(&bars->ep_done[ps], puse & 1, abort_flag, status)) {
+          if (!direct) {
+            tma_store_2d(&tmP, pt, cb * kBN, rb * kBM);
+            tma_store_2d(&tmP, pt + kBM * 128, cb * kBN + 32, rb * kBM);
+          }
+          bulk_commit();  // one group per tile (empty for a ragged edge tile)
+          // the store group of tile i - kStoresInFlight has read its stage
+          bulk_wait_read<kStoresInFlight>();
+          if (i >= kStoresInFlight) mbar_arrive(&bars->p_empty[(i - kStoresInFlight) % kPS]);
+        } else {
+          stop = true;
+        }
+      }
+      if (__any_sync(0xffffffffu, stop)) break;  // warp-uniform exit
+    }
+    if (leader) bulk_wait0();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+// A_cat = [hi(U) | lo(U)], B_cat = [hi(W) | lo(W)] (n x 64, row-major) from
+// column-major U, W (column stride fs, r <= 32 columns).
+// A block of 256 threads transposes 32 rows through shared memory: reads run
+// down the factor columns, writes along the rows.
+__global__ void __launch_bounds__(256) tc_split_kernel(const float* __restrict__ U,
+                                                       const float* __restrict__ W, int64_t fs,
+                                                       int n, int r, float* __restrict__ Acat,
+                                                       float* __restrict__ Bcat) {
+  __shared__ float su[kRp][33], sw[kRp][33];
+  const int row0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 warps
+  for (int c = ty; c < kRp; c += 8) {
+    const int i = row0 + tx;
+    const bool ok = c < r && i < n;
+    su[c][tx] = ok ? U[(int64_t)c * fs + i] : 0.f;
+    sw[c][tx] = ok ? W[(int64_t)c * fs + i] : 0.f;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int i = row0 + j;
+    if (i >= n) break;
+    const float u = su[tx][j], w = sw[tx][j];
+    const float uh = __uint_as_float(__float_as_uint(u) & 0xFFFFE000u);
+    const float wh = __uint_as_float(__float_as_uint(w) & 0xFFFFE000u);
+    float* a = Acat + (int64_t)i * kK;
+    float* b = Bcat + (int64_t)i * kK;
+    a[tx] = uh;
+    a[kRp + tx] = u - uh;
+    b[tx] = wh;
+    b[kRp + tx] = w - wh;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+}  // namespace
+
+bool make_tmap_sw128(CUtensorMap* out, const void* base, int64_t cols, int64_t rows, int64_t ld,
+                     int box_rows) {
+  const PFN_cuTensorMapEncodeTiled_v12000 encode = encode_fn();
+  if (!encode) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {32u, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int64_t tc_split_floats(int64_t n) { return 2 * n * kK; }
+
+cudaError_t launch_tc_update(const CUtensorMap& tmP, const CUtensorMap& tmA,
+                             const CUtensorMap& tmB, float* P, int64_t ldp, float* Acat,
+                             float* Bcat, const float* U, const float* W, int64_t fs, int n, int r,
+                             int num_sms, unsigned* status, cudaStream_t s) {
+  if (r < 1 || r > kRp) return cudaErrorInvalidValue;
+  tc_split_kernel<<<(n + 31) / 32, 256, 0, s>>>(U, W, fs, n, r, Acat, Bcat);
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  if (configured != cudaSuccess) return configured;
+  const long long T = (long long)((n + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
+  const int grid = (int)(T < num_sms ? T : num_sms);
+  tc_update_kernel<<<grid, kTcThreads, kSmemBytes, s>>>(tmP, tmA, tmB, P, ldp, n, status);
+  return cudaGetLastError();
+}
+
+}  // namespace lv
