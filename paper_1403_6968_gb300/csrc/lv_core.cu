@@ -244,26 +244,30 @@ cudaError_t launch_assemble(const AssembleParams& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// W = V K^T for the block-upper-triangular K of identity blocks (width r_in):
+// block b of W is the sum of blocks b .. nblk-1 of V, added from the last
+// block down in the element type.  One thread per (row, column in block).
 template <typename T>
 __global__ void suffix_sums_kernel(const T* V, T* W, int64_t fs, int n, int width, int r_in) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * r_in) return;
+  const int c = (int)(idx / n);
+  const int j = (int)(idx % n);
   const int nblk = width / r_in;
-  for (int c = 0; c < r_in; ++c) {
-    double acc = 0.0;
-    for (int b = nblk - 1; b >= 0; --b) {
-      const int col = b * r_in + c;
-      acc += (double)V[(int64_t)col * fs + j];
-      W[(int64_t)col * fs + j] = (T)acc;
-    }
+  T acc = T(0);
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int col = b * r_in + c;
+    acc += V[(int64_t)col * fs + j];
+    W[(int64_t)col * fs + j] = acc;
   }
 }
 
 template <typename T>
 cudaError_t launch_suffix_sums(const T* V, T* W, int64_t fs, int n, int width, int r_in,
                                cudaStream_t s) {
-  suffix_sums_kernel<T><<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(V, W, fs, n, width,
-                                                                          r_in);
+  const int64_t tot = (int64_t)n * r_in;
+  suffix_sums_kernel<T><<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+      V, W, fs, n, width, r_in);
   return cudaGetLastError();
 }
 
