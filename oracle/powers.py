@@ -21,7 +21,10 @@ Incremental maintenance for a factored update dA = U V^T (Section 3.2):
   i.e. dS'_h = Z_h W_h^T with Z_1 = U_1, W_1 = V_1 and
       Z_{2h} = [U_h, P_h Z_h + U_h (V_h^T Z_h) + Z_h],  W_{2h} = [S'_h^T V_h, W_h];
 * linear model, Appendix A: U_1 = U, V_1 = V and
-      U_i = [U_1, A U_{i-1} + U_1 (V_1^T U_{i-1})],  V_i = [P_{i-1}^T V_1, V_{i-1}].
+      U_i = [U_1, A U_{i-1} + U_1 (V_1^T U_{i-1})],  V_i = [P_{i-1}^T V_1, V_{i-1}];
+* skip-s model, Appendix A: P_1 .. P_s by the exponential model, then
+  P_i = P_s P_{i-s} for i = 2s, 3s, ..., k, with
+      U_i = [U_s, P_s U_{i-s} + U_s (V_s^T U_{i-s})],  V_i = [P_{i-s}^T V_s, V_{i-s}].
 
 The instrumented ``ops`` counter tallies multiplications with the convention of
 Appendix A (a product of an a x b by a b x c matrix costs a*b*c, the addition
@@ -53,6 +56,22 @@ def reeval_powers(a: np.ndarray, k: int) -> dict:
     p = {1: a.copy()}
     for h in levels(k)[:-1]:
         p[2 * h] = p[h] @ p[h]
+    return p
+
+
+def skip_levels(k: int, s: int):
+    """Views of the skip-s model: 1, 2, 4, ..., s, then 2s, 3s, ..., k."""
+    if s < 1 or (s & (s - 1)) != 0 or k % s != 0 or k < 2 * s:
+        raise ValueError("s must be a power of two and k a multiple of s with k >= 2s")
+    return levels(s) + list(range(2 * s, k + 1, s))
+
+
+def skip_powers(a: np.ndarray, k: int, s: int) -> dict:
+    """Skip-s model: {h: A^h} for the views of ``skip_levels``: squarings up
+    to P_s, then P_i = P_s P_{i-s}."""
+    p = reeval_powers(a, s)
+    for i in range(2 * s, k + 1, s):
+        p[i] = p[s] @ p[i - s]
     return p
 
 
@@ -210,6 +229,39 @@ class LinearIncrementalPowers:
             V.append(np.hstack([o.mul(self.p[i - 2].T, v), V[-1]]))  # P_{i-1}^T V_1
         for i in range(1, self.k + 1):
             self.p[i - 1] += o.mul(U[i - 1], V[i - 1].T)
+        return U, V
+
+
+class SkipIncrementalPowers:
+    """Views of the skip-s model (``skip_levels``), Appendix A: the
+    exponential rules up to P_s, then the skip rule for i = 2s, ..., k; all
+    factors from the views before the update, the += statements last."""
+
+    def __init__(self, a: np.ndarray, k: int, s: int):
+        self.k, self.step = k, s
+        self.hs = skip_levels(k, s)
+        self.p = skip_powers(a, k, s)
+        self.ops = _Ops()
+
+    def apply(self, u: np.ndarray, v: np.ndarray):
+        n = self.p[1].shape[0]
+        u = np.asarray(u, dtype=np.float64).reshape(n, -1)
+        v = np.asarray(v, dtype=np.float64).reshape(n, -1)
+        o, s = self.ops, self.step
+        U, V = {1: u}, {1: v}
+        for h in levels(s)[:-1]:
+            ph = self.p[h]
+            c = o.mul(V[h].T, U[h])
+            U[2 * h] = np.hstack([U[h], o.add(o.mul(ph, U[h]), o.mul(U[h], c))])
+            V[2 * h] = np.hstack([o.mul(ph.T, V[h]), V[h]])
+        ps = self.p[s]
+        for i in range(2 * s, self.k + 1, s):
+            c = o.mul(V[s].T, U[i - s])                              # V_s^T U_{i-s}
+            right = o.add(o.mul(ps, U[i - s]), o.mul(U[s], c))       # P_s U_{i-s} + U_s (.)
+            U[i] = np.hstack([U[s], right])
+            V[i] = np.hstack([o.mul(self.p[i - s].T, V[s]), V[i - s]])  # P_{i-s}^T V_s
+        for h in self.hs:
+            self.p[h] += o.mul(U[h], V[h].T)
         return U, V
 
 

@@ -237,3 +237,54 @@ def test_power_adjoint_chain_vs_sum_and_fd(n, k):
         fd = _fd_power_grad(a, k, g, e)
         an = float(np.sum(chain * e))
         assert abs(fd - an) <= 1e-6 * gscale
+
+
+# ---------------------------------------------------------------- skip-s model
+@pytest.mark.parametrize("k,s,r", [(8, 2, 1), (12, 4, 2), (16, 4, 1), (16, 2, 3)])
+def test_skip_model_incremental_matches_brute_force(k, s, r):
+    """Appendix A skip-s rules against re-evaluation of the updated A after
+    every update (products of the definition P_i = P_s P_{i-s})."""
+    n = 9
+    a = li.power_matrix(n, seed=k + s)
+    inc = op.SkipIncrementalPowers(a, k, s)
+    acur = a.copy()
+    for (u, v) in li.lowrank_update_stream(n, r, 3, seed=k * s, sigma=0.3):
+        inc.apply(u, v)
+        acur += u @ v.T
+        for h in op.skip_levels(k, s):
+            assert rel_frob(inc.p[h], np.linalg.matrix_power(acur, h)) < 1e-12, h
+
+
+def test_skip_model_special_cases():
+    """s = 1 is the linear model and s = k/2 is the exponential model: the
+    factors of the three rule sets coincide."""
+    n, k = 6, 8
+    a = li.power_matrix(n, seed=3)
+    u, v = li.lowrank_update_stream(n, 2, 1, seed=4, sigma=0.2)[0]
+    sk = op.SkipIncrementalPowers(a, k, 1)
+    lin = op.LinearIncrementalPowers(a, k)
+    U1, V1 = sk.apply(u, v)
+    U2, V2 = lin.apply(u, v)
+    for i in range(1, k + 1):
+        assert np.allclose(U1[i], U2[i - 1], rtol=0, atol=1e-14)
+        assert np.allclose(V1[i], V2[i - 1], rtol=0, atol=1e-14)
+    sk = op.SkipIncrementalPowers(a, k, k // 2)
+    ex = op.IncrementalPowers(a, k)
+    U1, V1 = sk.apply(u, v)
+    f = ex.apply(u, v)
+    for h in op.levels(k):
+        assert np.allclose(U1[h], f["U"][h], rtol=0, atol=1e-14)
+        assert np.allclose(V1[h], f["V"][h], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("n,k,s", [(10, 8, 2), (16, 16, 4), (12, 12, 4)])
+def test_skip_model_multiplication_count(n, k, s):
+    """Appendix A, skip model: the levels above s cost
+    sum_{i = 2s, 3s, .., k} (2 n^2 i + n (2s + 1)(i - s)) multiplications for
+    a rank-1 update, on top of the exponential model's n^2 (4s - 3) +
+    n (s - 1)(2s + 5) / 3 for P_1 .. P_s."""
+    inc = op.SkipIncrementalPowers(li.power_matrix(n, seed=1), k, s)
+    inc.apply(*li.lowrank_update_stream(n, 1, 1, seed=2)[0])
+    exp_part = n * n * (4 * s - 3) + n * (s - 1) * (2 * s + 5) // 3
+    skip_part = sum(2 * n * n * i + n * (2 * s + 1) * (i - s) for i in range(2 * s, k + 1, s))
+    assert inc.ops.mults == exp_part + skip_part
