@@ -54,6 +54,7 @@ def _args():
     ap.add_argument("--serve-views", type=int, default=32)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-rank4", action="store_true")
+    ap.add_argument("--no-ksweep", action="store_true")
     return ap.parse_args()
 
 
@@ -438,6 +439,8 @@ def run_ours(args):
     prog.close()
     if not args.no_rank4:
         out["rank4_stream"] = rank_stream(args, 4, seed=rank)
+    if not args.no_ksweep:
+        out["k_sweep"] = k_sweep(args, seed=rank)
     if rank == 0 and not args.no_serving:
         out["serving"] = serving_sweep(args, seed=rank)
         out["zipf_batches"] = zipf_batches(args, seed=rank)
@@ -485,6 +488,55 @@ def rank_stream(args, r, seed=0, steps=20, warmup=3):
             "achieved_refresh_gbs": alg / (tot_ms / steps / 1e3) / 1e9,
             "note": "achieved GB/s counts each of the 9 views read and written once per "
                     "refresh (the method's minimum traffic)"}
+
+
+def k_sweep(args, seed=0, steps=8, warmup=2, ks=(2, 4, 8, 16, 32)):
+    """Iterative models of A^k (Section 3.3, Appendix A) against k: per-update
+    refresh time of the exponential model (views A^(2^j)), the linear model
+    (views A^1..A^k) and the skip-4 model (A, A^2, A^4, A^8, A^12, ..) under
+    rank-1 row updates, beside the re-evaluation of each (BF16x9 GEMMs)."""
+    import numpy as np
+    import torch
+    import linview_inputs as li
+    from paper_1403_6968_gb300 import Program
+
+    n = args.n
+    a = torch.from_numpy(li.power_matrix(n, seed=seed, dtype=np.float32)).cuda()
+    ups = li.row_update_stream(n, warmup + steps, seed=seed + 7, dtype=np.float32)
+    dv = [(i, torch.from_numpy(v).cuda()) for i, v in ups]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for j in range(reps):
+            fn(j)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    rows = []
+    for k in ks:
+        row = {"k": k}
+        for model in ("exp", "linear", "skip4"):
+            if model == "skip4" and k < 8:
+                continue
+            kw = {"model": "skip", "skip": 4} if model == "skip4" else {"model": model}
+            prog = Program("power", [a], k=k, r_max=1, **kw)
+            for i, v in dv[:warmup]:
+                prog.apply_row_delta(i, v)
+            row[f"{model}_ms"] = timed(lambda j: prog.apply_row_delta(*dv[warmup + j]), steps)
+            row[f"{model}_views"] = prog.num_views()
+            prog.set_reeval_mode("bf16x9")
+            prog.reeval()
+            row[f"{model}_reeval_ms"] = timed(lambda j: prog.reeval(), 2)
+            prog.sync()
+            prog.close()
+        rows.append(row)
+    return {"n": n, "update": "rank-1 row", "steps": steps, "rows": rows,
+            "note": "per-update refresh of all views of the model; re-evaluation recomputes "
+                    "the same views from A"}
 
 
 def serving_sweep(args, seed=0):

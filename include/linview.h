@@ -84,13 +84,25 @@ typedef struct {
   int64_t n;                 /* A is n x n (POWER, POWER_SUM, ITERATION); X has n columns (OLS) */
   int64_t m;                 /* OLS: rows of X and Y; otherwise 0 */
   int64_t p;                 /* ITERATION: columns of B and T_i; OLS: columns of Y; otherwise 0 */
-  int32_t k;                 /* POWER/POWER_SUM: highest power, a power of two >= 1;
+  int32_t k;                 /* POWER/POWER_SUM: highest power (a power of two >= 1 in
+                                the exponential model, >= 2 in the linear model);
                                 ITERATION: number of steps >= 1; OLS: largest row block */
   int32_t r_max;             /* largest rank accepted by linview_apply_delta (>= 1) */
   int32_t correction_period; /* >0: re-evaluate every this many updates (residual
                                 correction of accumulated rounding); 0 = never */
   int32_t reeval_mode;       /* linview_reeval_mode used by linview_reeval and by correction */
+  int32_t model;             /* POWER/POWER_SUM: linview_model; other kinds: 0 */
+  int32_t skip;              /* LINVIEW_MODEL_SKIP: the step s; otherwise 0 */
 } linview_program_desc;
+
+/* Iterative model of a power program (Section 3.3; Appendix A). */
+typedef enum {
+  LINVIEW_MODEL_EXP = 0,     /* P_{2h} = P_h P_h: views A, A^2, A^4, ..., A^k */
+  LINVIEW_MODEL_LINEAR = 1,  /* P_i = A P_{i-1}: views A, A^2, A^3, ..., A^k; r_max * k <= 64 */
+  LINVIEW_MODEL_SKIP = 2     /* exponential up to A^s, then P_i = A^s P_{i-s}: views A, A^2,
+                                A^4, ..., A^s, A^2s, ..., A^k; s a power of two, k a multiple
+                                of s, k >= 2s, r_max * k <= 64; POWER only */
+} linview_model;
 
 /*
  * Create a program and materialise its views by re-evaluation on the device
@@ -143,6 +155,10 @@ linview_status linview_apply_row_block(linview_program* prog, int64_t kr, const 
  * View ids:
  *   POWER:     0 = A = P_1, j = P_{2^j} (j = 1..log2 k)
  *   POWER_SUM: as POWER, then log2(k) + j = S'_{2^j} (j = 1..log2 k); S'_1 = A
+ *   linear model (LINVIEW_MODEL_LINEAR): i - 1 = P_i (i = 1..k); POWER_SUM adds
+ *              k = S'_k
+ *   skip-s model (LINVIEW_MODEL_SKIP): j = P_{2^j} (j = 0..log2 s), then
+ *              log2(s) + i - 1 = P_{is} (i = 2..k/s)
  *   ITERATION: 0 = A, i = T_i (i = 1..k), k + 1 = B, k + 2 = T_0
  *   OLS:       0 = W (n x n), 1 = beta (n x p), 2 = X^T Y (n x p), 3 = X (m x n)
  */

@@ -21,6 +21,8 @@ POWER, POWER_SUM, ITERATION, OLS = range(4)
 F64, F32 = 0, 1
 # linview_reeval_mode
 REEVAL_DEFAULT, REEVAL_FP32, REEVAL_TF32, REEVAL_BF16X9, REEVAL_FP64 = range(5)
+# linview_model
+MODEL_EXP, MODEL_LINEAR, MODEL_SKIP = 0, 1, 2
 
 
 class ProgramDesc(C.Structure):
@@ -34,6 +36,8 @@ class ProgramDesc(C.Structure):
         ("r_max", C.c_int32),
         ("correction_period", C.c_int32),
         ("reeval_mode", C.c_int32),
+        ("model", C.c_int32),
+        ("skip", C.c_int32),
     ]
 
 

@@ -464,13 +464,91 @@ static int ilog2(int k) {
   while ((1 << l) < k) ++l;
   return l;
 }
+static bool is_linear(const linview_program* p) { return p->d.model == LINVIEW_MODEL_LINEAR; }
+
+// Shape rules of the linear and skip-s models (the exponential model's are
+// checked where it is built).
+static linview_status check_power_model(const linview_program_desc& d) {
+  if (d.model == LINVIEW_MODEL_LINEAR || d.model == LINVIEW_MODEL_SKIP) {
+    if (d.k < 2) return fail(LINVIEW_EINVAL, "k=%d must be >= 2", d.k);
+    if (d.r_max < 1 || (int64_t)d.r_max * d.k > 64)
+      return fail(LINVIEW_EUNSUPPORTED, "linear and skip models: r_max*k=%lld must be <= 64",
+                  (long long)d.r_max * d.k);
+  }
+  if (d.model == LINVIEW_MODEL_SKIP) {
+    if (!is_pow2(d.skip) || d.k % d.skip != 0 || d.k < 2 * d.skip)
+      return fail(LINVIEW_EINVAL, "skip s=%d: s must be a power of two and k=%d a multiple >= 2s",
+                  d.skip, d.k);
+  } else if (d.skip != 0) {
+    return fail(LINVIEW_EINVAL, "skip must be 0 unless model is LINVIEW_MODEL_SKIP");
+  }
+  return LINVIEW_OK;
+}
 static bool has_sums(const linview_program* p) {
+  if (is_linear(p)) return p->d.kind == LINVIEW_POWER_SUM;
   return p->d.kind == LINVIEW_POWER_SUM && p->L >= 1;
 }
 static View& pview(linview_program* p, int l) { return p->views[l]; }
 static View& sview(linview_program* p, int l) { return p->views[p->L + l]; }  // S'_{2^l}, l>=1
 
+// Linear model (Section 3.3): P_i = P_{i-1} A, i = 2..k (views i-1), and
+// S'_k = P_1 + ... + P_k (view k) for sums programs.
+static linview_status linear_reeval(linview_program* p, cudaStream_t s) {
+  const int64_t n = p->d.n;
+  const int k = p->d.k;
+  const int mode = reeval_mode(p);
+  View& a = p->views[0];
+  for (int i = 2; i <= k; ++i) {
+    View& prev = p->views[i - 2];
+    View& c = p->views[i - 1];
+    LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, prev.ptr, prev.ld, a.ptr, a.ld, 0.0, c.ptr, c.ld,
+                   s, mode));
+  }
+  if (has_sums(p)) {
+    View& sv = p->views[k];
+    LV_CUDA(cudaMemcpy2DAsync(sv.ptr, sv.ld * p->elem, a.ptr, a.ld * p->elem, n * p->elem, n,
+                              cudaMemcpyDeviceToDevice, s));
+    for (int i = 2; i <= k; ++i) {
+      View& pi = p->views[i - 1];
+      if (p->elem == 4)
+        LV_CUDA(launch_axpy_rows<float>(static_cast<float*>(sv.ptr), sv.ld,
+                                        static_cast<const float*>(pi.ptr), pi.ld, 1.0f, (int)n,
+                                        (int)n, s));
+      else
+        LV_CUDA(launch_axpy_rows<double>(static_cast<double*>(sv.ptr), sv.ld,
+                                         static_cast<const double*>(pi.ptr), pi.ld, 1.0, (int)n,
+                                         (int)n, s));
+      p->all_launches++;
+    }
+  }
+  return LINVIEW_OK;
+}
+
+// Skip-s model: squarings up to P_s (views 0..log2 s), then P_{is} =
+// P_s P_{(i-1)s} (views log2(s) + i - 1, i = 2..k/s).
+static linview_status skip_reeval(linview_program* p, cudaStream_t s) {
+  const int64_t n = p->d.n;
+  const int mode = reeval_mode(p);
+  const int Ls = ilog2(p->d.skip);
+  for (int l = 0; l < Ls; ++l) {
+    View& a = pview(p, l);
+    View& c = pview(p, l + 1);
+    LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, a.ptr, a.ld, a.ptr, a.ld, 0.0, c.ptr, c.ld, s,
+                   mode));
+  }
+  View& ps = pview(p, Ls);
+  for (int i = 2; i <= p->d.k / p->d.skip; ++i) {
+    View& prev = pview(p, Ls + i - 2);
+    View& c = pview(p, Ls + i - 1);
+    LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, ps.ptr, ps.ld, prev.ptr, prev.ld, 0.0, c.ptr,
+                   c.ld, s, mode));
+  }
+  return LINVIEW_OK;
+}
+
 static linview_status powers_reeval(linview_program* p, cudaStream_t s) {
+  if (is_linear(p)) return linear_reeval(p, s);
+  if (p->d.model == LINVIEW_MODEL_SKIP) return skip_reeval(p, s);
   const int64_t n = p->d.n;
   const int mode = reeval_mode(p);
   for (int l = 0; l < p->L; ++l) {
@@ -501,6 +579,17 @@ static bool powers_wide_sums(const linview_program_desc& d) {
   return d.kind == LINVIEW_POWER_SUM && ((int64_t)d.r_max * d.k > mu || d.r_max > 8);
 }
 
+// Views of a power program: exponential model P_{2^j} (j = 0..log2 k) and,
+// with sums, S'_{2^j} (j >= 1); linear model P_1..P_k and, with sums, S'_k;
+// skip-s model P_{2^j} (j = 0..log2 s) then P_{2s}, ..., P_k.
+static int powers_num_views(const linview_program_desc& d) {
+  const bool sums = d.kind == LINVIEW_POWER_SUM;
+  if (d.model == LINVIEW_MODEL_LINEAR) return d.k + (sums ? 1 : 0);
+  if (d.model == LINVIEW_MODEL_SKIP) return ilog2(d.skip) + d.k / d.skip;
+  const int L = ilog2(d.k);
+  return L + 1 + (sums ? L : 0);
+}
+
 // FP32 power programs whose update blocks can be wider than kMaxProductR
 // refresh those blocks on the tensor cores.
 static bool powers_uses_tc(const linview_program_desc& d) {
@@ -512,11 +601,9 @@ static bool powers_uses_tc(const linview_program_desc& d) {
 static int64_t powers_device_bytes(const linview_program_desc& d, int sms) {
   const int elem = d.precision == LINVIEW_F64 ? 8 : 4;
   const int64_t n = d.n;
-  const int L = ilog2(d.k);
   int64_t b = (int64_t)sizeof(unsigned) * 4 + (int64_t)sizeof(double) * 64 * 64 +
               (int64_t)cpart_bytes(n);
-  const int nviews = L + 1 + (d.kind == LINVIEW_POWER_SUM ? L : 0);
-  b += nviews * square_view_bytes(n, elem);
+  b += powers_num_views(d) * square_view_bytes(n, elem);
   const int64_t Rcap = (int64_t)d.r_max * d.k;
   const int64_t fs = rup(n, 64);
   b += (powers_wide_sums(d) ? 3 : 2) * fs * Rcap * elem;
@@ -532,16 +619,21 @@ static linview_status powers_create(linview_program* p, const void* const* input
                                     const int64_t* lds, int on_dev, cudaStream_t s) {
   const int64_t n = p->d.n;
   const int k = p->d.k;
-  if (!is_pow2(k)) return fail(LINVIEW_EINVAL, "k=%d must be a power of two", k);
+  LV_TRY(check_power_model(p->d));
+  if (p->d.model != LINVIEW_MODEL_EXP) {
+    // the Krylov-type levels use square factor cores of width < r_max * k
+  } else {
+    if (!is_pow2(k)) return fail(LINVIEW_EINVAL, "k=%d must be a power of two", k);
+    if ((int64_t)p->d.r_max * k > 128)
+      return fail(LINVIEW_EUNSUPPORTED,
+                  "r_max*k=%lld exceeds 128 (factor cores are at most 64x64)",
+                  (long long)p->d.r_max * k);
+  }
   p->L = ilog2(k);
-  if ((int64_t)p->d.r_max * k > 128)
-    return fail(LINVIEW_EUNSUPPORTED, "r_max*k=%lld exceeds 128 (factor cores are at most 64x64)",
-                (long long)p->d.r_max * k);
   const bool wide_sums = powers_wide_sums(p->d);
   if (lds[0] < n) return fail(LINVIEW_ESHAPE, "ld of A (%lld) < n", (long long)lds[0]);
-  for (int l = 0; l <= p->L; ++l) LV_TRY(add_square_view(p, n));
-  if (p->d.kind == LINVIEW_POWER_SUM)
-    for (int l = 1; l <= p->L; ++l) LV_TRY(add_square_view(p, n));
+  const int nviews = powers_num_views(p->d);
+  for (int l = 0; l < nviews; ++l) LV_TRY(add_square_view(p, n));
   LV_TRY(copy_in(pview(p, 0).ptr, pview(p, 0).ld, inputs[0], lds[0], n, n, p->elem, on_dev, s));
   p->Rcap = p->d.r_max * k;
   p->fs = rup(n, 64);
@@ -585,19 +677,21 @@ static linview_status sums_update(linview_program* p, View& sv, const T* U, cons
   return run_update<T>(p, sv, U, static_cast<const T*>(p->Wsum), rh, s, 0);
 }
 
+// Exponential-model levels l = 0 .. nlev-1 (h = 2^l, Appendix A): the level
+// pass on P_h (P_h U_h, P_h^T V_h from the old view, P_h += U_h V_h^T; for
+// r_h <= kMaxFusedR the same pass yields the partials of C_h = V_h^T U_h),
+// the sums view S'_h (h >= 2) when ``sums``, and the assembly of
+// U_{2h} = [U_h, P_h U_h + U_h C_h], V_{2h} = [P_h^T V_h, V_h].
 template <typename T>
-static linview_status powers_propagate(linview_program* p, int r, cudaStream_t s) {
+static linview_status exp_levels(linview_program* p, int r, int nlev, bool sums, cudaStream_t s) {
   const int n = (int)p->d.n;
   const int64_t fs = p->fs;
   T* U = static_cast<T*>(p->Uar);
   T* V = static_cast<T*>(p->Var);
-  const bool sums = has_sums(p);
   const PassGeom g = fused_geom(sizeof(T), n, p->sms);
-  for (int l = 0; l < p->L; ++l) {
+  for (int l = 0; l < nlev; ++l) {
     const int rh = r << l;
     T* Vh = V + (int64_t)(p->Rcap - rh) * fs;
-    // Appendix A level pass: P_h U_h, P_h^T V_h from the old view, P_h += U_h V_h^T;
-    // for r_h <= kMaxFusedR the same pass also yields the partials of C_h = V_h^T U_h
     const bool fused = rh <= kMaxFusedR;
     if (!fused) {
       ProfScope ps(p, s, 0.0);
@@ -626,8 +720,88 @@ static linview_status powers_propagate(linview_program* p, int r, cudaStream_t s
     ProfScope ps(p, s, 0.0);
     LV_CUDA(launch_assemble<T>(a, s));
   }
+  return LINVIEW_OK;
+}
+
+// Linear-type levels on a base block of width bw (Appendix A).  Linear model:
+// base (U_1, V_1), Q_j = P_j;  skip-s model: base (U_s, V_s) from the
+// exponential levels, Q_j = P_{js}.  With Q' the refreshed views,
+//   U_{j+1} = [U_base, Q_1' U_j]   = [U_base, Q_1' U_base, ..., Q_j' U_base],
+//   V_{j+1} = [Q_j^T V_base, V_j]  (old Q),  Q_j += U_j V_j^T,
+// since Q_1'^j = Q_j'.  Only the newest blocks are new at each step (Krylov
+// reuse): the pass over the old Q_j yields Y = Q_j^T V_base and X = Q_j U_base,
+// and Q_j' U_base = X + U_j (V_j^T U_base); the view is refreshed after its
+// products.  U grows from the left of the arena, V from the right, block i of
+// U_j pairing with block i of V_j.  Views: Q_j = views[view0 + j - 1]; the
+// last one, views[view0 + nsteps], gets only its refresh.
+template <typename T>
+static linview_status krylov_levels(linview_program* p, int bw, int nsteps, int view0,
+                                    cudaStream_t s) {
+  const int n = (int)p->d.n;
+  const int64_t fs = p->fs;
+  T* U = static_cast<T*>(p->Uar);
+  T* V = static_cast<T*>(p->Var);
+  const PassGeom g = fused_geom(sizeof(T), n, p->sms);
+  const T* Vb = V + (int64_t)(p->Rcap - bw) * fs;
+  for (int j = 1; j <= nsteps; ++j) {
+    const int rh = j * bw;
+    T* Vj = V + (int64_t)(p->Rcap - rh) * fs;
+    View& Q = p->views[view0 + j - 1];
+    {  // C = V_j^T U_j (its first bw columns are V_j^T U_base)
+      ProfScope ps(p, s, 0.0);
+      LV_CUDA((launch_gram<T>(Vj, U, fs, n, rh, p->Cpart, p->ticket, p->C, p->status, s)));
+    }
+    LV_TRY(run_products_update<T>(p, Q, bw, U, Vb, nullptr, nullptr, s));
+    LV_TRY(run_update<T>(p, Q, U, Vj, rh, s));
+    AssembleParams a{};
+    a.n = n;
+    a.r_h = rh;
+    a.r_out = bw;
+    a.fs = fs;
+    a.Xpart = p->Xpart;
+    a.gC = g.gC;
+    a.xp_s = p->xp_s;
+    a.Ypart = p->Ypart;
+    a.gR = g.gR;
+    a.yp_q = p->yp_q;
+    a.part_cs = p->part_cs;
+    a.C = p->C;
+    a.nC = 1;
+    a.Uh = U;
+    a.Unew = U + (int64_t)rh * fs;
+    a.Ynew = V + (int64_t)(p->Rcap - rh - bw) * fs;
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_assemble<T>(a, s));
+  }
+  const int rk = (nsteps + 1) * bw;
+  LV_TRY(run_update<T>(p, p->views[view0 + nsteps], U, V + (int64_t)(p->Rcap - rk) * fs, rk, s));
+  return LINVIEW_OK;
+}
+
+template <typename T>
+static linview_status powers_propagate(linview_program* p, int r, cudaStream_t s) {
+  T* U = static_cast<T*>(p->Uar);
+  T* V = static_cast<T*>(p->Var);
+  const int k = p->d.k;
+  if (p->d.model == LINVIEW_MODEL_LINEAR) {
+    LV_TRY(krylov_levels<T>(p, r, k - 1, 0, s));
+    // S'_k = sum_i P_i: dS'_k = U_k K V_k^T (suffix block sums, as for the
+    // exponential model's sums)
+    if (has_sums(p)) {
+      const int rk = k * r;
+      LV_TRY(sums_update<T>(p, p->views[k], U, V + (int64_t)(p->Rcap - rk) * p->fs, rk, r, s));
+    }
+    return LINVIEW_OK;
+  }
+  if (p->d.model == LINVIEW_MODEL_SKIP) {
+    const int sk = p->d.skip, Ls = ilog2(sk);
+    LV_TRY(exp_levels<T>(p, r, Ls, false, s));
+    return krylov_levels<T>(p, sk * r, k / sk - 1, Ls, s);
+  }
+  const bool sums = has_sums(p);
+  LV_TRY(exp_levels<T>(p, r, p->L, sums, s));
   const int rk = r << p->L;
-  T* Vk = V + (int64_t)(p->Rcap - rk) * fs;
+  T* Vk = V + (int64_t)(p->Rcap - rk) * p->fs;
   LV_TRY(run_update<T>(p, pview(p, p->L), U, Vk, rk, s));
   if (sums) LV_TRY(sums_update<T>(p, sview(p, p->L), U, Vk, rk, r, s));
   return LINVIEW_OK;
@@ -965,6 +1139,11 @@ linview_status linview_create_program(const linview_program_desc* desc, const vo
   if (desc->n < 1 || desc->n > (1 << 20)) return fail(LINVIEW_EINVAL, "bad n=%lld", (long long)desc->n);
   if (desc->r_max < 1) return fail(LINVIEW_EINVAL, "r_max must be >= 1");
   if (desc->correction_period < 0) return fail(LINVIEW_EINVAL, "correction_period < 0");
+  if (desc->model != LINVIEW_MODEL_EXP &&
+      !(desc->model == LINVIEW_MODEL_LINEAR &&
+        (desc->kind == LINVIEW_POWER || desc->kind == LINVIEW_POWER_SUM)) &&
+      !(desc->model == LINVIEW_MODEL_SKIP && desc->kind == LINVIEW_POWER))
+    return fail(LINVIEW_EINVAL, "model %d is not available for kind %d", desc->model, desc->kind);
   int ninputs = 0;
   switch (desc->kind) {
     case LINVIEW_POWER:
@@ -1055,9 +1234,17 @@ linview_status linview_estimate_device_bytes(const linview_program_desc* d, int6
   if (d->precision != LINVIEW_F32 && d->precision != LINVIEW_F64)
     return fail(LINVIEW_EINVAL, "bad precision %d", d->precision);
   if (d->n < 1 || d->n > (1 << 20)) return fail(LINVIEW_EINVAL, "bad n=%lld", (long long)d->n);
-  if (!is_pow2(d->k)) return fail(LINVIEW_EINVAL, "k=%d must be a power of two", d->k);
-  if (d->r_max < 1 || (int64_t)d->r_max * d->k > 128)
-    return fail(LINVIEW_EUNSUPPORTED, "r_max*k must be in 1..128");
+  if (d->model == LINVIEW_MODEL_LINEAR || d->model == LINVIEW_MODEL_SKIP) {
+    if (d->model == LINVIEW_MODEL_SKIP && d->kind != LINVIEW_POWER)
+      return fail(LINVIEW_EINVAL, "the skip model maintains powers only");
+    LV_TRY(check_power_model(*d));
+  } else if (d->model == LINVIEW_MODEL_EXP) {
+    if (!is_pow2(d->k)) return fail(LINVIEW_EINVAL, "k=%d must be a power of two", d->k);
+    if (d->r_max < 1 || (int64_t)d->r_max * d->k > 128)
+      return fail(LINVIEW_EUNSUPPORTED, "r_max*k must be in 1..128");
+  } else {
+    return fail(LINVIEW_EINVAL, "bad model %d", d->model);
+  }
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -1438,6 +1625,8 @@ linview_status linview_adjoint_power(linview_program* p, const void* G, int64_t 
   if (!p || !G || !dA) return fail(LINVIEW_EINVAL, "null argument");
   if (p->d.kind != LINVIEW_POWER && p->d.kind != LINVIEW_POWER_SUM)
     return fail(LINVIEW_EINVAL, "not a power program");
+  if (p->d.model != LINVIEW_MODEL_EXP)
+    return fail(LINVIEW_EUNSUPPORTED, "the power adjoint runs on the squaring chain (exponential model)");
   const int64_t n = p->d.n;
   if (ldg < n || ld_dA < n) return fail(LINVIEW_ESHAPE, "bad leading dims");
   LV_CUDA(cudaSetDevice(p->device));

@@ -215,8 +215,9 @@ __global__ void __launch_bounds__(kThreads) assemble_kernel(const AssembleParams
     Ct[e] = (T)sum;
   }
   __syncthreads();
+  const int ro = a.r_out > 0 ? a.r_out : rh;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)a.n * rh) return;
+  if (idx >= (int64_t)a.n * ro) return;
   const int c = (int)(idx / a.n);
   const int j = (int)(idx % a.n);
   const T* Xp = static_cast<const T*>(a.Xpart);
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(kThreads) assemble_kernel(const AssembleParams
 
 template <typename T>
 cudaError_t launch_assemble(const AssembleParams& a, cudaStream_t s) {
-  const int64_t tot = (int64_t)a.n * a.r_h;
+  const int64_t tot = (int64_t)a.n * (a.r_out > 0 ? a.r_out : a.r_h);
   const unsigned grid = (unsigned)((tot + kThreads - 1) / kThreads);
   const size_t smem = sizeof(T) * (size_t)a.r_h * a.r_h;  // <= 32 KB for r_h <= 64
   assemble_kernel<T><<<grid, kThreads, smem, s>>>(a);

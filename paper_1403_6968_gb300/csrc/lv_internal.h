@@ -93,11 +93,13 @@ int gram_grid(int n);
 
 struct AssembleParams {
   int n, r_h;             // rows, current factor width
+  int r_out;              // columns of X_h / Y_h to assemble (0 = r_h)
   int64_t fs;             // arena column stride
   const void* Xpart; int gC; int64_t xp_s;   // row-sum partials of P_h U_h
   const void* Ypart; int gR; int64_t yp_q;   // column-sum partials of P_h^T V_h (or null)
   int64_t part_cs;
-  const double* C;        // r_h x r_h = V_h^T U_h, summed over nC partial blocks
+  const double* C;        // r_h x r_h = V_h^T U_h, summed over nC partial blocks (the first
+                          // r_out columns are used)
   int nC;                 // number of [r_h*r_h] partial blocks in C (1 = already reduced)
   const void* Uh;         // U_h (n x r_h)
   void* Unew;             // destination of X_h + U_h C_h (n x r_h), = U arena + r_h columns

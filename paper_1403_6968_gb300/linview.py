@@ -15,6 +15,7 @@ from . import _lib as L
 from ._lib import LinviewError  # noqa: F401
 
 KINDS = {"power": L.POWER, "power_sum": L.POWER_SUM, "iteration": L.ITERATION, "ols": L.OLS}
+MODELS = {"exp": L.MODEL_EXP, "linear": L.MODEL_LINEAR, "skip": L.MODEL_SKIP}
 REEVAL = {"default": L.REEVAL_DEFAULT, "fp32": L.REEVAL_FP32, "tf32": L.REEVAL_TF32,
           "bf16x9": L.REEVAL_BF16X9, "fp64": L.REEVAL_FP64}
 
@@ -74,7 +75,7 @@ class Program:
     """
 
     def __init__(self, kind, inputs, k, r_max=1, precision="f32", p=0, m=0,
-                 correction_period=0, reeval_mode="default", stream=None):
+                 correction_period=0, reeval_mode="default", model="exp", skip=0, stream=None):
         self.lib = L.load()
         self.precision = L.F64 if precision in ("f64", "fp64", L.F64) else L.F32
         self.np_dtype = _dtype_of(self.precision)
@@ -89,6 +90,8 @@ class Program:
         d.r_max = int(r_max)
         d.correction_period = int(correction_period)
         d.reeval_mode = REEVAL[reeval_mode] if isinstance(reeval_mode, str) else int(reeval_mode)
+        d.model = MODELS[model] if isinstance(model, str) else int(model)
+        d.skip = int(skip)
         on_dev = {o.on_device for o in ops}
         if len(on_dev) != 1:
             raise ValueError("inputs must all be on the device or all on the host")
@@ -262,10 +265,12 @@ def level_pass_noalloc(P, U, V, X=None, Y=None, do_update=True, stream=None):
            1 if do_update else 0, _stream_ptr(stream))
 
 
-def estimate_device_bytes(n, k, r_max=1, kind="power", precision="f32"):
+def estimate_device_bytes(n, k, r_max=1, kind="power", precision="f32", model="exp", skip=0):
     """Device bytes a power (or power-sum) program of this shape would hold."""
     d = L.ProgramDesc()
     d.kind = KINDS[kind]
+    d.model = MODELS[model]
+    d.skip = int(skip)
     d.precision = L.F64 if precision in ("f64", "fp64") else L.F32
     d.n, d.k, d.r_max = int(n), int(k), int(r_max)
     b = C.c_int64()

@@ -230,14 +230,18 @@ def test_serve_row_coalescing():
     _run_child("serve_row_coalescing")
 
 
-@pytest.mark.parametrize("kind,n,k,r_max", [("power", 1000, 16, 8), ("power", 256, 8, 1),
-                                            ("power_sum", 777, 16, 4), ("power_sum", 512, 4, 2)])
-def test_estimate_equals_program_bytes(kind, n, k, r_max):
+@pytest.mark.parametrize("kind,n,k,r_max,model", [
+    ("power", 1000, 16, 8, "exp"), ("power", 256, 8, 1, "exp"), ("power_sum", 777, 16, 4, "exp"),
+    ("power_sum", 512, 4, 2, "exp"), ("power", 300, 16, 4, "linear"),
+    ("power_sum", 300, 5, 1, "linear"), ("power", 300, 16, 2, "skip")])
+def test_estimate_equals_program_bytes(kind, n, k, r_max, model):
     P = _pkg()
     a = li.power_matrix(n, seed=1, dtype=np.float32)
-    prog = P.Program(kind, [a], k=k, r_max=r_max)
+    skip = 4 if model == "skip" else 0
+    prog = P.Program(kind, [a], k=k, r_max=r_max, model=model, skip=skip)
     try:
-        assert P.program_device_bytes(prog) == P.estimate_device_bytes(n, k, r_max=r_max, kind=kind)
+        assert P.program_device_bytes(prog) == P.estimate_device_bytes(n, k, r_max=r_max, kind=kind,
+                                                                       model=model, skip=skip)
     finally:
         prog.close()
 
