@@ -206,6 +206,8 @@ cudaError_t launch_gram(const T* V, const T* U, int64_t fs, int n, int r, double
 template <typename T>
 __global__ void __launch_bounds__(kThreads) assemble_kernel(const AssembleParams a) {
   extern __shared__ double Cs[];  // r_h x r_h, FP64 sums rounded to T
+  griddep_wait();  // everything read here comes from the kernels before
+  griddep_launch_dependents();
   const int rh = a.r_h;
   const int ne = rh * rh;
   T* Ct = reinterpret_cast<T*>(Cs);
@@ -241,7 +243,8 @@ cudaError_t launch_assemble(const AssembleParams& a, cudaStream_t s) {
   const int64_t tot = (int64_t)a.n * (a.r_out > 0 ? a.r_out : a.r_h);
   const unsigned grid = (unsigned)((tot + kThreads - 1) / kThreads);
   const size_t smem = sizeof(T) * (size_t)a.r_h * a.r_h;  // <= 32 KB for r_h <= 64
-  assemble_kernel<T><<<grid, kThreads, smem, s>>>(a);
+  const cudaError_t e = launch_pdl(assemble_kernel<T>, grid, kThreads, smem, s, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

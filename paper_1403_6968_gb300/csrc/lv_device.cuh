@@ -118,6 +118,18 @@ __device__ __forceinline__ void prefetch_tmap(const void* tmap) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmap)) : "memory");
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the kernel before it drains; griddep_wait()
+// blocks until that kernel has completed and its writes are visible, and
+// griddep_launch_dependents() lets the next kernel start early.  Work before
+// griddep_wait() may only touch data that the previous kernel does not write.
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // 16-byte vector helpers for float (4 lanes) and double (2 lanes).
 template <typename T>
 struct Vec;

@@ -8,6 +8,24 @@
 
 namespace lv {
 
+// Launch ``k`` with programmatic stream serialisation (the kernel calls
+// griddep_wait() before it reads what earlier kernels of the stream wrote).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 constexpr int kThreads = 256;   // threads per pass CTA
 constexpr int kBatch = 8;       // rows per pipeline stage = TMA box height = warps per CTA
 constexpr int kStages = 4;      // TMA ring depth (generic passes)

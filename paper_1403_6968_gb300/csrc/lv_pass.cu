@@ -537,7 +537,12 @@ static cudaError_t launch_fused_t(const PassParams& p, const CUtensorMap& tm, cu
   static const cudaError_t configured =
       cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (configured != cudaSuccess) return configured;
-  kfn<<<p.gC * p.gR, kThreads, smem, s>>>(tm, p);
+  if constexpr (kWs) {
+    const cudaError_t e = launch_pdl(kfn, p.gC * p.gR, kThreads, smem, s, tm, p);
+    if (e != cudaSuccess) return e;
+  } else {
+    kfn<<<p.gC * p.gR, kThreads, smem, s>>>(tm, p);
+  }
   return cudaGetLastError();
 }
 
@@ -583,7 +588,12 @@ static cudaError_t launch_update_t(const PassParams& p, const CUtensorMap& tm, c
   static const cudaError_t configured =
       cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (configured != cudaSuccess) return configured;
-  kfn<<<p.gC * p.gR, kThreads, smem, s>>>(tm, p);
+  if constexpr (kWs) {
+    const cudaError_t e = launch_pdl(kfn, p.gC * p.gR, kThreads, smem, s, tm, p);
+    if (e != cudaSuccess) return e;
+  } else {
+    kfn<<<p.gC * p.gR, kThreads, smem, s>>>(tm, p);
+  }
   return cudaGetLastError();
 }
 

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const uint32_t stage_bytes = (uint32_t)(nbox * kBatch * BOXC * sizeof(T));
 
   // warp 0: start batch b in stage b % S (factor rows by cp.async, tile by TMA)
-  auto produce = [&](int b) {
+  auto produce_rows = [&](int b) {
     const int st = b % S;
     const int row0 = rb + b * kBatch;
     const int nb = min(kBatch, re - row0);
@@ -202,6 +202,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       cp_async_arrive_noinc(&full[st]);
     }
+  };
+  auto produce_tile = [&](int b) {
+    const int st = b % S;
+    const int row0 = rb + b * kBatch;
     if (lane == 0) {
       fence_proxy_async();
       mbar_arrive_expect_tx(&full[st], stage_bytes);
@@ -213,9 +217,20 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
   };
+  auto produce = [&](int b) {
+    produce_rows(b);
+    produce_tile(b);
+  };
   int issued = 0;
+  // The view is not written by the kernels launched just before this one, so
+  // its first tiles are requested before waiting on them; the factors and the
+  // partial-sum buffers are (programmatic dependent launch).
+  if (warp == 0)
+    for (int b = 0; b < S && b < nbatch; ++b) produce_tile(b);
+  griddep_wait();
+  griddep_launch_dependents();
   if (warp == 0) {
-    for (int b = 0; b < S && b < nbatch; ++b) produce(b);
+    for (int b = 0; b < S && b < nbatch; ++b) produce_rows(b);
     issued = min(S, nbatch);
   }
 
@@ -561,7 +576,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
   for (int bx = 0; bx < NB; ++bx) nbox += (strip0 + bx * BOXC < n) ? 1 : 0;
   const uint32_t stage_bytes = (uint32_t)(nbox * kBatch * BOXC * sizeof(T));
-  auto produce = [&](int b) {
+  auto produce_rows = [&](int b) {
     const int st = b % S;
     const int row0 = rb + b * kBatch;
     const int nb = min(kBatch, re - row0);
@@ -573,6 +588,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       cp_async4(Us + (st * kBatch + j) * R + c, Uu + g, ok);
     }
     cp_async_arrive_noinc(&full[st]);
+  };
+  auto produce_tile = [&](int b) {
+    const int st = b % S;
+    const int row0 = rb + b * kBatch;
     if (lane == 0) {
       fence_proxy_async();
       mbar_arrive_expect_tx(&full[st], stage_bytes);
@@ -584,9 +603,19 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
   };
+  auto produce = [&](int b) {
+    produce_rows(b);
+    produce_tile(b);
+  };
   int issued = 0;
+  // first tiles of the view before waiting on the previous kernel (see the
+  // fused pass); the factor rows after
+  if (warp == 0)
+    for (int b = 0; b < S && b < nbatch; ++b) produce_tile(b);
+  griddep_wait();
+  griddep_launch_dependents();
   if (warp == 0) {
-    for (int b = 0; b < S && b < nbatch; ++b) produce(b);
+    for (int b = 0; b < S && b < nbatch; ++b) produce_rows(b);
     issued = min(S, nbatch);
   }
 
