@@ -60,6 +60,24 @@ class IncrementalIteration:
         return U, V
 
 
+    def apply_b(self, ub, vb):
+        """dB = U_b V_b^T (U_b n x r_b, V_b p x r_b) with A unchanged: dT_i =
+        A dT_{i-1} + dB, dT_0 = 0, i.e. dT_i = U_i V_i^T with
+        U_i = [U_b, A U_{i-1}], V_i = [V_b, V_{i-1}] (derived from the
+        recurrence; the paper omits changes in B, Section 4.3.2)."""
+        n, p = self.b.shape
+        ub = np.asarray(ub, dtype=np.float64).reshape(n, -1)
+        vb = np.asarray(vb, dtype=np.float64).reshape(p, -1)
+        U, V = {1: ub}, {1: vb}
+        for i in range(2, self.k + 1):
+            U[i] = np.hstack([ub, self.a @ U[i - 1]])
+            V[i] = np.hstack([vb, V[i - 1]])
+        self.b += ub @ vb.T
+        for i in range(1, self.k + 1):
+            self.t[i] += U[i] @ V[i].T
+        return U, V
+
+
 class HybridIteration:
     """Views T_1..T_k maintained with dense deltas (Appendix B, hybrid linear)."""
 

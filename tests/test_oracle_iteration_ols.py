@@ -28,6 +28,43 @@ def test_iteration_incremental_and_hybrid_match_reeval(n, p, k, r):
             assert U[i].shape == (n, i * r) and V[i].shape == (p, i * r)
 
 
+@pytest.mark.parametrize("n,p,k,rb", [(8, 3, 16, 1), (12, 7, 6, 2)])
+def test_iteration_b_update_matches_reeval(n, p, k, rb):
+    """Updates to B (dT_i = A dT_{i-1} + dB), interleaved with updates to A,
+    against re-evaluation on the current inputs after every update."""
+    a, b, t0 = li.iteration_inputs(n, p, seed=n + p)
+    inc = oi.IncrementalIteration(a, b, t0, k)
+    acur, bcur = a.copy(), b.copy()
+    g = np.random.default_rng(n)
+    for step in range(4):
+        if step % 2:
+            u, v = g.standard_normal((n, 1)) * 0.2, g.standard_normal((n, 1)) * 0.2
+            inc.apply(u, v)
+            acur += u @ v.T
+        else:
+            ub, vb = g.standard_normal((n, rb)), g.standard_normal((p, rb))
+            U, V = inc.apply_b(ub, vb)
+            bcur += ub @ vb.T
+            assert U[k].shape == (n, k * rb) and V[k].shape == (p, k * rb)
+        ref = oi.reeval(acur, bcur, t0, k)
+        for i in range(1, k + 1):
+            assert rel_frob(inc.t[i], ref[i]) < 1e-12
+
+
+def test_iteration_b_update_closed_form():
+    """A = lam I: dT_i = (1 + lam + ... + lam^(i-1)) dB exactly."""
+    n, p, k, lam = 5, 3, 10, 0.7
+    _, b, t0 = li.iteration_inputs(n, p, seed=4)
+    inc = oi.IncrementalIteration(lam * np.eye(n), b, t0, k)
+    before = [t.copy() for t in inc.t]
+    g = np.random.default_rng(9)
+    ub, vb = g.standard_normal((n, 1)), g.standard_normal((p, 1))
+    inc.apply_b(ub, vb)
+    for i in range(1, k + 1):
+        geo = (1 - lam ** i) / (1 - lam)
+        assert rel_frob(inc.t[i] - before[i], geo * (ub @ vb.T)) < 1e-13
+
+
 def test_iteration_closed_form_scalar_plus_rank1():
     # A' = lam I + u v^T: A'^j = lam^j I + c_j u v^T, c_j = ((lam+alpha)^j - lam^j)/alpha,
     # T_i = A'^i T_0 + sum_{j<i} A'^j B  (unrolled form, Section 4.3)
