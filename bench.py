@@ -55,6 +55,7 @@ def _args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-rank4", action="store_true")
     ap.add_argument("--no-ksweep", action="store_true")
+    ap.add_argument("--no-general", action="store_true")
     return ap.parse_args()
 
 
@@ -437,13 +438,24 @@ def run_ours(args):
                                          f"workload at n={n} (FP64 numpy oracle; its own "
                                          f"re-evaluation setup of {setup:.1f} s untimed)"}
     prog.close()
+    # secondary workloads: a failure in one is recorded in its field and does
+    # not take the headline line down with it
+    def section(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as e:  # noqa: BLE001
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+
     if not args.no_rank4:
-        out["rank4_stream"] = rank_stream(args, 4, seed=rank)
+        section("rank4_stream", lambda: rank_stream(args, 4, seed=rank))
     if not args.no_ksweep:
-        out["k_sweep"] = k_sweep(args, seed=rank)
+        section("k_sweep", lambda: k_sweep(args, seed=rank))
+    if not args.no_general:
+        section("iteration_p_sweep", lambda: iteration_p_sweep(args, seed=rank))
+        section("gd_regression", lambda: gd_regression(seed=rank))
     if rank == 0 and not args.no_serving:
-        out["serving"] = serving_sweep(args, seed=rank)
-        out["zipf_batches"] = zipf_batches(args, seed=rank)
+        section("serving", lambda: serving_sweep(args, seed=rank))
+        section("zipf_batches", lambda: zipf_batches(args, seed=rank))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -537,6 +549,113 @@ def k_sweep(args, seed=0, steps=8, warmup=2, ks=(2, 4, 8, 16, 32)):
     return {"n": n, "update": "rank-1 row", "steps": steps, "rows": rows,
             "note": "per-update refresh of all views of the model; re-evaluation recomputes "
                     "the same views from A"}
+
+
+def _event_ms(fn, reps):
+    import torch
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for j in range(reps):
+        fn(j)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def iteration_p_sweep(args, seed=0, k=16, steps=6, ps=(1, 16, 128, 1024)):
+    """General form with B = 0 (Section 6, "B=0"): T_{i+1} = A T_i, n = 8192,
+    k = 16, against the width p of T: per-update refresh of T_1..T_k
+    (rank-1 row updates of A) vs re-evaluation (k products A T_i)."""
+    import numpy as np
+    import torch
+    import linview_inputs as li
+    from paper_1403_6968_gb300 import Program
+
+    n = args.n
+    a = torch.from_numpy(li.power_matrix(n, seed=seed, dtype=np.float32)).cuda()
+    ups = [(i, torch.from_numpy(v).cuda())
+           for i, v in li.row_update_stream(n, steps + 2, seed=seed + 3, dtype=np.float32)]
+    rows = []
+    for p in ps:
+        t0 = torch.from_numpy(li.normal((n, p), seed=seed + p, dtype=np.float32)).cuda()
+        b = torch.zeros((n, p), dtype=torch.float32, device="cuda")
+        prog = Program("iteration", [a, b, t0], k=k, r_max=1)
+        for i, v in ups[:2]:
+            prog.apply_row_delta(i, v)
+        inc = _event_ms(lambda j: prog.apply_row_delta(*ups[2 + j]), steps)
+        row = {"p": p, "incremental_ms": inc}
+        for mode in ("bf16x9", "tf32"):
+            prog.set_reeval_mode(mode)
+            prog.reeval()
+            row[f"reeval_{mode}_ms"] = _event_ms(lambda j: prog.reeval(), 2)
+        prog.sync()
+        prog.close()
+        rows.append(row)
+    return {"n": n, "k": k, "B": "0", "update": "rank-1 row of A", "rows": rows}
+
+
+def gd_regression(seed=0, n=4096, m=4096, p=1024, k=16, steps=6):
+    """Batch gradient descent for least squares as the general form (Section
+    6, "B != 0"): Theta_{i+1} = Theta_i - eta X^T (X Theta_i - Y), i.e.
+    A = I - eta X^T X, B = eta X^T Y, Theta_0 = 0.  An update replaces one row
+    of X: dA = -eta (x' x'^T - x x^T) (rank 2) and dB = eta (x' - x) y^T
+    (rank 1), applied as two factored deltas; compared with re-evaluating the
+    k iterations.  X, Y ~ N(0, 1); eta = 1 / (1.05 lambda_max(X^T X))."""
+    import numpy as np
+    import torch
+    import linview_inputs as li
+    from paper_1403_6968_gb300 import Program
+
+    x = li.normal((m, n), seed=seed + 11)
+    y = li.normal((m, p), seed=seed + 12)
+    t_host = time.perf_counter()
+    g = x.T @ x                                   # workload construction on the host
+    z = li.normal((n, 1), seed=seed + 13)
+    for _ in range(30):                           # lambda_max by power iteration
+        z = g @ z
+        z /= np.linalg.norm(z)
+    eta = 1.0 / (1.05 * (z.T @ g @ z).item())
+    a = (np.eye(n) - eta * g).astype(np.float32)
+    b = (eta * (x.T @ y)).astype(np.float32)
+    host_s = time.perf_counter() - t_host
+    prog = Program("iteration", [torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(),
+                                 torch.zeros((n, p), dtype=torch.float32, device="cuda")],
+                   k=k, r_max=2)
+    newx = li.normal((steps + 2, n), seed=seed + 14)
+    rowsel = np.random.default_rng(seed + 15).integers(0, m, size=steps + 2)
+    deltas = []
+    for j in range(steps + 2):
+        i = int(rowsel[j])
+        xo, xn = x[i].copy(), newx[j]
+        x[i] = xn
+        u = np.stack([xn, xo], axis=1).astype(np.float32)
+        v = np.stack([-eta * xn, eta * xo], axis=1).astype(np.float32)
+        ub = (xn - xo).reshape(n, 1).astype(np.float32)
+        vb = (eta * y[i]).reshape(p, 1).astype(np.float32)
+        deltas.append(tuple(torch.from_numpy(t).cuda() for t in (u, v, ub, vb)))
+
+    def replace_row(j):
+        u, v, ub, vb = deltas[j]
+        prog.apply_delta(u, v)
+        prog.apply_delta(ub, vb, input_id=1)
+
+    replace_row(0)
+    replace_row(1)
+    inc = _event_ms(lambda j: replace_row(2 + j), steps)
+    out = {"n": n, "m": m, "p": p, "k": k, "eta": eta, "incremental_ms_per_row_replacement": inc,
+           "host_setup_s": host_s}
+    for mode in ("bf16x9", "tf32", "fp32"):
+        prog.set_reeval_mode(mode)
+        prog.reeval()
+        out[f"reeval_{mode}_ms"] = _event_ms(lambda j: prog.reeval(), 2)
+    prog.sync()
+    prog.close()
+    out["speedup_vs_bf16x9_reeval"] = out["reeval_bf16x9_ms"] / inc
+    out["note"] = ("incremental: the rank-2 dA and rank-1 dB of a row replacement; "
+                   "re-evaluation: T_i = A T_{i-1} + B for i = 1..k")
+    return out
 
 
 def serving_sweep(args, seed=0):

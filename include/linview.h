@@ -122,9 +122,12 @@ linview_status linview_create_program(const linview_program_desc* desc, const vo
 /*
  * Fire the trigger of input ``input_id`` for the factored update
  * dX = U V^T (Section 3.2; Example 3.8 for powers, Appendix A; Appendix B for
- * the iteration).  Only input 0 (A) is supported for POWER, POWER_SUM and
- * ITERATION.  U is n x rank (row-major, ldu >= rank); V is n x rank (ldv >=
- * rank).  Every view is refreshed in place: view += (its factored delta).
+ * the iteration).  Input 0 (A): U is n x rank (row-major, ldu >= rank), V is
+ * n x rank (ldv >= rank); POWER, POWER_SUM and ITERATION.  Input 1 (B) of an
+ * ITERATION program: U is n x rank, V is p x rank; with A unchanged,
+ * dT_i = A dT_{i-1} + dB, so dT_i = [U, A U, .., A^(i-1) U][V, .., V]^T (the
+ * paper omits changes in B, Section 4.3.2; this is the rule the recurrence
+ * gives).  Every view is refreshed in place: view += (its factored delta).
  * Errors: EINVAL, ESHAPE, ERANK (rank > r_max), EDEVICE.  On error the views
  * are unchanged.
  */

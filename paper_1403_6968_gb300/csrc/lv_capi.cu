@@ -933,6 +933,44 @@ static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) 
   return LINVIEW_OK;
 }
 
+// Updates to B, dB = U_b V_b^T with A unchanged (U_b in Krylov block K_0,
+// V_b in the first block of M): dT_i = A dT_{i-1} + dB gives
+// dT_i = [K_0 .. K_{i-1}] [V_b .. V_b]^T with K_a = A^a U_b, so the k-1
+// products with A are the only passes over the view, and every M block is
+// V_b.  B itself is refreshed as well.
+template <typename T>
+static linview_status iter_propagate_b(linview_program* p, int rb, cudaStream_t s) {
+  const int n = (int)p->d.n;
+  const int64_t pp = p->d.p;
+  const int k = p->d.k;
+  const int64_t fs = p->fs;
+  T* K = static_cast<T*>(p->Kar);
+  T* M = static_cast<T*>(p->Mr);
+  char* Tp = static_cast<char*>(p->Tpanel);
+  View& a = p->views[0];
+  const PassGeom g = fused_geom(sizeof(T), n, p->sms);
+  for (int i = 1; i < k; ++i)
+    LV_CUDA(cudaMemcpyAsync(M + (int64_t)i * rb * pp, M, sizeof(T) * rb * pp,
+                            cudaMemcpyDeviceToDevice, s));
+  for (int j = 1; j < k; ++j) {
+    LV_TRY(run_fused<T>(p, a, kModeX, rb, K + (int64_t)(j - 1) * rb * fs, nullptr, nullptr,
+                        nullptr, p->Xpart, p->Ypart, s));
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, rb,
+                                   K + (int64_t)j * rb * fs, fs, s));
+  }
+  // T_i += [K_0 .. K_{i-1}] [V_b .. V_b]^T; column-major T_i^T (p x n)
+  for (int i = 1; i <= k; ++i) {
+    void* ti = Tp + (size_t)i * pp * sizeof(T);
+    LV_TRY(gemm_cm(p, false, true, pp, n, (int64_t)i * rb, 1.0, M, pp, K, fs, 1.0, ti, p->ldT, s,
+                   exact_mode(p)));
+  }
+  // B += U_b V_b^T (column-major B^T, p x n)
+  LV_TRY(gemm_cm(p, false, true, pp, n, rb, 1.0, M, pp, K, fs, 1.0, p->Bm, p->ldB, s,
+                 exact_mode(p)));
+  return LINVIEW_OK;
+}
+
 // ---------------------------------------------------------------------------
 // OLS (Section 4.1): views W = (X^T X)^{-1}, beta = W X^T Y, X^T Y, X
 // ---------------------------------------------------------------------------
@@ -1440,17 +1478,53 @@ static void* v_dst(linview_program* p, int r) {
   return static_cast<char*>(p->Var) + (size_t)(p->Rcap - r) * p->fs * p->elem;
 }
 
+// dB = U V^T for an iteration program: U (n x rank) into Krylov block K_0, V
+// (p x rank) into the first M block, then the propagation above.
+static linview_status apply_b_delta(linview_program* p, int r, const void* U, int64_t ldu,
+                                    const void* V, int64_t ldv, int on_device, cudaStream_t s) {
+  const int64_t n = p->d.n, pp = p->d.p;
+  const void* u = U;
+  const void* v = V;
+  if (!on_device) {
+    LV_TRY(ensure_stage(p, (size_t)(n + pp) * r * p->elem));
+    char* st = static_cast<char*>(p->stage);
+    LV_TRY(copy_in(st, r, U, ldu, n, r, p->elem, 0, s));
+    LV_TRY(copy_in(st + (size_t)n * r * p->elem, r, V, ldv, pp, r, p->elem, 0, s));
+    u = st;
+    v = st + (size_t)n * r * p->elem;
+    ldu = r;
+    ldv = r;
+  }
+  if (p->elem == 4) {
+    LV_CUDA(launch_rm_to_cm<float>(static_cast<const float*>(u), ldu, static_cast<float*>(p->Kar),
+                                   p->fs, (int)n, r, s));
+    LV_CUDA(launch_rm_to_cm<float>(static_cast<const float*>(v), ldv, static_cast<float*>(p->Mr),
+                                   pp, (int)pp, r, s));
+  } else {
+    LV_CUDA(launch_rm_to_cm<double>(static_cast<const double*>(u), ldu,
+                                    static_cast<double*>(p->Kar), p->fs, (int)n, r, s));
+    LV_CUDA(launch_rm_to_cm<double>(static_cast<const double*>(v), ldv,
+                                    static_cast<double*>(p->Mr), pp, (int)pp, r, s));
+  }
+  p->all_launches += 2;
+  LV_TRY(p->elem == 4 ? iter_propagate_b<float>(p, r, s) : iter_propagate_b<double>(p, r, s));
+  return after_update(p, s);
+}
+
 linview_status linview_apply_delta(linview_program* p, int input_id, int64_t rank, const void* U,
                                    int64_t ldu, const void* V, int64_t ldv, int on_device,
                                    void* stream) {
   if (!p || !U || !V) return fail(LINVIEW_EINVAL, "null argument");
   if (p->d.kind == LINVIEW_OLS) return fail(LINVIEW_EINVAL, "OLS takes linview_apply_row_block");
-  if (input_id != 0) return fail(LINVIEW_EUNSUPPORTED, "only input 0 (A) has a trigger");
+  const bool b_update = p->d.kind == LINVIEW_ITERATION && input_id == 1;
+  if (input_id != 0 && !b_update)
+    return fail(LINVIEW_EUNSUPPORTED, "input %d has no trigger for this program", input_id);
   if (rank < 1) return fail(LINVIEW_EINVAL, "rank must be >= 1");
   if (rank > p->d.r_max) return fail(LINVIEW_ERANK, "rank %lld > r_max %d", (long long)rank, p->d.r_max);
   if (ldu < rank || ldv < rank) return fail(LINVIEW_ESHAPE, "ldu/ldv < rank");
   LV_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (b_update) return apply_b_delta(p, (int)rank, U, ldu, V, ldv, on_device, s);
   const int64_t n = p->d.n;
   const int r = (int)rank;
   const void* u = U;

@@ -135,3 +135,36 @@ def test_power_adjoint_vs_oracle(prec):
     torch.cuda.synchronize()
     ref = op.adjoint_power_chain(a.astype(np.float64), k, g.astype(np.float64))
     assert rel_frob(dA.cpu().numpy(), ref) <= (1e-10 if prec == "f64" else 1e-4)
+
+
+@pytest.mark.parametrize("prec,n,p,k,rb", [("f64", 300, 7, 8, 1), ("f64", 256, 16, 16, 2),
+                                            ("f32", 1000, 64, 16, 2)])
+def test_iteration_b_updates(prec, n, p, k, rb):
+    """Updates to B (input 1) interleaved with updates to A, against the
+    oracle's re-evaluation on the current A and B."""
+    from paper_1403_6968_gb300 import Program
+    from oracle import iteration as oi
+    dt = np.float64 if prec == "f64" else np.float32
+    a, b, t0 = li.iteration_inputs(n, p, seed=n + p, dtype=dt)
+    prog = Program("iteration", [a, b, t0], k=k, r_max=max(rb, 2), precision=prec)
+    acur, bcur = a.astype(np.float64), b.astype(np.float64)
+    g = np.random.default_rng(n)
+    for step in range(4):
+        if step % 2:
+            u = (g.standard_normal((n, 2)) * 0.01).astype(dt)
+            v = (g.standard_normal((n, 2)) * 0.01).astype(dt)
+            prog.apply_delta(u, v)
+            acur += u.astype(np.float64) @ v.astype(np.float64).T
+        else:
+            ub = g.standard_normal((n, rb)).astype(dt)
+            vb = g.standard_normal((p, rb)).astype(dt)
+            prog.apply_delta(ub, vb, input_id=1)
+            bcur += ub.astype(np.float64) @ vb.astype(np.float64).T
+    ref = oi.reeval(acur, bcur, t0.astype(np.float64), k)
+    tol = 1e-10 if prec == "f64" else 1e-4
+    for i in range(1, k + 1):
+        got = prog.read_view(i).cpu().numpy().astype(np.float64)
+        assert rel_frob(got, ref[i]) <= tol, i
+    got_b = prog.read_view(k + 1).cpu().numpy().astype(np.float64)
+    assert rel_frob(got_b, bcur) <= tol
+    prog.close()
