@@ -1386,6 +1386,21 @@ static linview_status after_update(linview_program* p, cudaStream_t s) {
 // the same graph replays the caller times.
 constexpr int kProfCopies = 16;
 
+// Graph keys: the update rank r; updates to B of an iteration program use
+// kKeyB + r.
+constexpr int kKeyB = 1024;
+
+// The launches of one update after its factors are in place, on stream s.
+static linview_status propagate_eager(linview_program* p, int key, cudaStream_t s) {
+  if (p->d.kind == LINVIEW_ITERATION) {
+    if (key >= kKeyB)
+      return p->elem == 4 ? iter_propagate_b<float>(p, key - kKeyB, s)
+                          : iter_propagate_b<double>(p, key - kKeyB, s);
+    return p->elem == 4 ? iter_propagate<float>(p, key, s) : iter_propagate<double>(p, key, s);
+  }
+  return p->elem == 4 ? powers_propagate<float>(p, key, s) : powers_propagate<double>(p, key, s);
+}
+
 static linview_status capture_graph(linview_program* p, int r, bool inst,
                                     linview_program::GraphEntry* out) {
   const int64_t before = p->all_launches;
@@ -1396,8 +1411,7 @@ static linview_status capture_graph(linview_program* p, int r, bool inst,
   const bool prof_was = p->prof;
   p->prof = inst;
   LV_CUDA(cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal));
-  linview_status st = p->elem == 4 ? powers_propagate<float>(p, r, p->gstream)
-                                   : powers_propagate<double>(p, r, p->gstream);
+  linview_status st = propagate_eager(p, r, p->gstream);
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(p->gstream, &graph);
   p->capturing_prof = false;
@@ -1422,7 +1436,7 @@ static linview_status capture_graph(linview_program* p, int r, bool inst,
   return LINVIEW_OK;
 }
 
-static linview_status powers_graph(linview_program* p, int r, cudaStream_t s) {
+static linview_status graph_propagate(linview_program* p, int r, cudaStream_t s) {
   if (!p->gstream) {
     LV_CUDA(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
     LV_CUDA(cudaEventCreateWithFlags(&p->gev_in, cudaEventDisableTiming));
@@ -1457,14 +1471,15 @@ static linview_status powers_graph(linview_program* p, int r, cudaStream_t s) {
   return LINVIEW_OK;
 }
 
-static linview_status propagate(linview_program* p, int r, cudaStream_t s) {
+// Powers, sums and iterations: the launches after ingest depend only on the
+// key (all pointers are the program's own), so they replay as CUDA graphs.
+static linview_status propagate(linview_program* p, int key, cudaStream_t s) {
   switch (p->d.kind) {
     case LINVIEW_POWER:
     case LINVIEW_POWER_SUM:
-      if (p->use_graphs) return powers_graph(p, r, s);
-      return p->elem == 4 ? powers_propagate<float>(p, r, s) : powers_propagate<double>(p, r, s);
     case LINVIEW_ITERATION:
-      return p->elem == 4 ? iter_propagate<float>(p, r, s) : iter_propagate<double>(p, r, s);
+      if (p->use_graphs) return graph_propagate(p, key, s);
+      return propagate_eager(p, key, s);
     default: return fail(LINVIEW_EUNSUPPORTED, "updates for kind %d", p->d.kind);
   }
 }
@@ -1507,7 +1522,7 @@ static linview_status apply_b_delta(linview_program* p, int r, const void* U, in
                                     static_cast<double*>(p->Mr), pp, (int)pp, r, s));
   }
   p->all_launches += 2;
-  LV_TRY(p->elem == 4 ? iter_propagate_b<float>(p, r, s) : iter_propagate_b<double>(p, r, s));
+  LV_TRY(propagate(p, kKeyB + r, s));
   return after_update(p, s);
 }
 
