@@ -75,6 +75,20 @@ def skip_powers(a: np.ndarray, k: int, s: int) -> dict:
     return p
 
 
+def skip_sums(a: np.ndarray, k: int, s: int) -> dict:
+    """Sums S'_h = A + ... + A^h for the skip-s views h > 1, by the model's
+    recurrences (Section 4.2.3): S'_{2h} = P_h S'_h + S'_h up to s, then
+    S'_i = P_s S'_{i-s} + S'_s for i = 2s, 3s, ..., k (S'_1 = A)."""
+    p = skip_powers(a, k, s)
+    sm = {1: p[1].copy()}
+    for h in levels(s)[:-1]:
+        sm[2 * h] = p[h] @ sm[h] + sm[h]
+    for i in range(2 * s, k + 1, s):
+        sm[i] = p[s] @ sm[i - s] + sm[s]
+    del sm[1]
+    return sm
+
+
 def linear_powers(a: np.ndarray, k: int) -> list:
     """Linear model: [A^1, A^2, ..., A^k] by k-1 products with A."""
     a = np.asarray(a, dtype=np.float64)

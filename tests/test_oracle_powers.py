@@ -288,3 +288,16 @@ def test_skip_model_multiplication_count(n, k, s):
     exp_part = n * n * (4 * s - 3) + n * (s - 1) * (2 * s + 5) // 3
     skip_part = sum(2 * n * n * i + n * (2 * s + 1) * (i - s) for i in range(2 * s, k + 1, s))
     assert inc.ops.mults == exp_part + skip_part
+
+
+@pytest.mark.parametrize("k,s", [(8, 2), (12, 4), (16, 4)])
+def test_skip_sums_recurrence_is_the_definition(k, s):
+    """The skip model's sum recurrence S'_i = P_s S'_{i-s} + S'_s gives
+    A + A^2 + ... + A^i (brute force)."""
+    n = 7
+    a = li.power_matrix(n, seed=k * s)
+    sm = op.skip_sums(a, k, s)
+    assert sorted(sm) == op.skip_levels(k, s)[1:]
+    for h, v in sm.items():
+        ref = sum(np.linalg.matrix_power(a, i) for i in range(1, h + 1))
+        assert rel_frob(v, ref) < 1e-13
