@@ -100,8 +100,9 @@ typedef enum {
   LINVIEW_MODEL_EXP = 0,     /* P_{2h} = P_h P_h: views A, A^2, A^4, ..., A^k */
   LINVIEW_MODEL_LINEAR = 1,  /* P_i = A P_{i-1}: views A, A^2, A^3, ..., A^k; r_max * k <= 64 */
   LINVIEW_MODEL_SKIP = 2     /* exponential up to A^s, then P_i = A^s P_{i-s}: views A, A^2,
-                                A^4, ..., A^s, A^2s, ..., A^k; s a power of two, k a multiple
-                                of s, k >= 2s, r_max * k <= 64; POWER only */
+                                A^4, ..., A^s, A^2s, ..., A^k (POWER_SUM adds S'_h for the same
+                                h > 1); s a power of two, k a multiple of s, k >= 2s,
+                                r_max * k <= 64 */
 } linview_model;
 
 /*
@@ -161,7 +162,8 @@ linview_status linview_apply_row_block(linview_program* prog, int64_t kr, const 
  *   linear model (LINVIEW_MODEL_LINEAR): i - 1 = P_i (i = 1..k); POWER_SUM adds
  *              k = S'_k
  *   skip-s model (LINVIEW_MODEL_SKIP): j = P_{2^j} (j = 0..log2 s), then
- *              log2(s) + i - 1 = P_{is} (i = 2..k/s)
+ *              log2(s) + i - 1 = P_{is} (i = 2..k/s); with N such power views,
+ *              POWER_SUM adds N + j - 1 = S'_h for the power view j >= 1
  *   ITERATION: 0 = A, i = T_i (i = 1..k), k + 1 = B, k + 2 = T_0
  *   OLS:       0 = W (n x n), 1 = beta (n x p), 2 = X^T Y (n x p), 3 = X (m x n)
  */

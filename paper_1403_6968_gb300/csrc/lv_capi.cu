@@ -96,7 +96,8 @@ struct linview_program {
   std::vector<void*> allocs;
   int64_t bytes = 0;  // sum of the device allocations in allocs
   std::vector<View> views;
-  int L = 0;  // log2 k for powers
+  int L = 0;    // log2 k for powers
+  int npv = 0;  // power programs: number of power views (the sums views follow)
   // factor arenas
   void* Uar = nullptr;
   void* Var = nullptr;
@@ -485,11 +486,12 @@ static linview_status check_power_model(const linview_program_desc& d) {
   return LINVIEW_OK;
 }
 static bool has_sums(const linview_program* p) {
-  if (is_linear(p)) return p->d.kind == LINVIEW_POWER_SUM;
+  if (p->d.model != LINVIEW_MODEL_EXP) return p->d.kind == LINVIEW_POWER_SUM;
   return p->d.kind == LINVIEW_POWER_SUM && p->L >= 1;
 }
 static View& pview(linview_program* p, int l) { return p->views[l]; }
-static View& sview(linview_program* p, int l) { return p->views[p->L + l]; }  // S'_{2^l}, l>=1
+// S'_h for the power view of index l >= 1 (h = 2^l, or the skip view l)
+static View& sview(linview_program* p, int l) { return p->views[p->npv + l - 1]; }
 
 // Linear model (Section 3.3): P_i = P_{i-1} A, i = 2..k (views i-1), and
 // S'_k = P_1 + ... + P_k (view k) for sums programs.
@@ -543,6 +545,24 @@ static linview_status skip_reeval(linview_program* p, cudaStream_t s) {
     LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, ps.ptr, ps.ld, prev.ptr, prev.ld, 0.0, c.ptr,
                    c.ld, s, mode));
   }
+  if (has_sums(p)) {
+    // S'_{2h} = P_h S'_h + S'_h up to s (S'_1 = A), then S'_i = P_s S'_{i-s} + S'_s
+    auto sum_step = [&](View& pm, View& prev, View& add, View& out) -> linview_status {
+      LV_CUDA(cudaMemcpy2DAsync(out.ptr, out.ld * p->elem, add.ptr, add.ld * p->elem,
+                                n * p->elem, n, cudaMemcpyDeviceToDevice, s));
+      return gemm_rm(p, false, false, n, n, n, 1.0, pm.ptr, pm.ld, prev.ptr, prev.ld, 1.0,
+                     out.ptr, out.ld, s, mode);
+    };
+    for (int l = 0; l < Ls; ++l) {
+      View& sh = (l == 0) ? pview(p, 0) : sview(p, l);
+      LV_TRY(sum_step(pview(p, l), sh, sh, sview(p, l + 1)));
+    }
+    View& ss = (Ls == 0) ? pview(p, 0) : sview(p, Ls);
+    for (int i = 2; i <= p->d.k / p->d.skip; ++i) {
+      View& prev = (Ls + i - 2 == 0) ? pview(p, 0) : sview(p, Ls + i - 2);
+      LV_TRY(sum_step(ps, prev, ss, sview(p, Ls + i - 1)));
+    }
+  }
   return LINVIEW_OK;
 }
 
@@ -581,11 +601,15 @@ static bool powers_wide_sums(const linview_program_desc& d) {
 
 // Views of a power program: exponential model P_{2^j} (j = 0..log2 k) and,
 // with sums, S'_{2^j} (j >= 1); linear model P_1..P_k and, with sums, S'_k;
-// skip-s model P_{2^j} (j = 0..log2 s) then P_{2s}, ..., P_k.
+// skip-s model P_{2^j} (j = 0..log2 s) then P_{2s}, ..., P_k and, with sums,
+// S'_h for the same h > 1.
 static int powers_num_views(const linview_program_desc& d) {
   const bool sums = d.kind == LINVIEW_POWER_SUM;
   if (d.model == LINVIEW_MODEL_LINEAR) return d.k + (sums ? 1 : 0);
-  if (d.model == LINVIEW_MODEL_SKIP) return ilog2(d.skip) + d.k / d.skip;
+  if (d.model == LINVIEW_MODEL_SKIP) {
+    const int np = ilog2(d.skip) + d.k / d.skip;
+    return np + (sums ? np - 1 : 0);
+  }
   const int L = ilog2(d.k);
   return L + 1 + (sums ? L : 0);
 }
@@ -634,6 +658,9 @@ static linview_status powers_create(linview_program* p, const void* const* input
   if (lds[0] < n) return fail(LINVIEW_ESHAPE, "ld of A (%lld) < n", (long long)lds[0]);
   const int nviews = powers_num_views(p->d);
   for (int l = 0; l < nviews; ++l) LV_TRY(add_square_view(p, n));
+  p->npv = p->d.model == LINVIEW_MODEL_EXP      ? p->L + 1
+           : p->d.model == LINVIEW_MODEL_SKIP ? ilog2(p->d.skip) + k / p->d.skip
+                                              : k;
   LV_TRY(copy_in(pview(p, 0).ptr, pview(p, 0).ld, inputs[0], lds[0], n, n, p->elem, on_dev, s));
   p->Rcap = p->d.r_max * k;
   p->fs = rup(n, 64);
@@ -736,7 +763,7 @@ static linview_status exp_levels(linview_program* p, int r, int nlev, bool sums,
 // last one, views[view0 + nsteps], gets only its refresh.
 template <typename T>
 static linview_status krylov_levels(linview_program* p, int bw, int nsteps, int view0,
-                                    cudaStream_t s) {
+                                    int sums_r, cudaStream_t s) {
   const int n = (int)p->d.n;
   const int64_t fs = p->fs;
   T* U = static_cast<T*>(p->Uar);
@@ -753,6 +780,11 @@ static linview_status krylov_levels(linview_program* p, int bw, int nsteps, int 
     }
     LV_TRY(run_products_update<T>(p, Q, bw, U, Vb, nullptr, nullptr, s));
     LV_TRY(run_update<T>(p, Q, U, Vj, rh, s));
+    // skip model with sums: U_j, V_j are Krylov bases of width j bw, so
+    // dS'_h = U_j (V_j K^T)^T as in the exponential model
+    // (S'_1 is A itself: no sums view for power index 0)
+    if (sums_r > 0 && view0 + j - 1 >= 1)
+      LV_TRY(sums_update<T>(p, sview(p, view0 + j - 1), U, Vj, rh, sums_r, s));
     AssembleParams a{};
     a.n = n;
     a.r_h = rh;
@@ -774,7 +806,9 @@ static linview_status krylov_levels(linview_program* p, int bw, int nsteps, int 
     LV_CUDA(launch_assemble<T>(a, s));
   }
   const int rk = (nsteps + 1) * bw;
-  LV_TRY(run_update<T>(p, p->views[view0 + nsteps], U, V + (int64_t)(p->Rcap - rk) * fs, rk, s));
+  T* Vk = V + (int64_t)(p->Rcap - rk) * fs;
+  LV_TRY(run_update<T>(p, p->views[view0 + nsteps], U, Vk, rk, s));
+  if (sums_r > 0) LV_TRY(sums_update<T>(p, sview(p, view0 + nsteps), U, Vk, rk, sums_r, s));
   return LINVIEW_OK;
 }
 
@@ -784,7 +818,7 @@ static linview_status powers_propagate(linview_program* p, int r, cudaStream_t s
   T* V = static_cast<T*>(p->Var);
   const int k = p->d.k;
   if (p->d.model == LINVIEW_MODEL_LINEAR) {
-    LV_TRY(krylov_levels<T>(p, r, k - 1, 0, s));
+    LV_TRY(krylov_levels<T>(p, r, k - 1, 0, 0, s));
     // S'_k = sum_i P_i: dS'_k = U_k K V_k^T (suffix block sums, as for the
     // exponential model's sums)
     if (has_sums(p)) {
@@ -795,8 +829,9 @@ static linview_status powers_propagate(linview_program* p, int r, cudaStream_t s
   }
   if (p->d.model == LINVIEW_MODEL_SKIP) {
     const int sk = p->d.skip, Ls = ilog2(sk);
-    LV_TRY(exp_levels<T>(p, r, Ls, false, s));
-    return krylov_levels<T>(p, sk * r, k / sk - 1, Ls, s);
+    const bool sums = has_sums(p);
+    LV_TRY(exp_levels<T>(p, r, Ls, sums, s));
+    return krylov_levels<T>(p, sk * r, k / sk - 1, Ls, sums ? r : 0, s);
   }
   const bool sums = has_sums(p);
   LV_TRY(exp_levels<T>(p, r, p->L, sums, s));
@@ -1180,7 +1215,8 @@ linview_status linview_create_program(const linview_program_desc* desc, const vo
   if (desc->model != LINVIEW_MODEL_EXP &&
       !(desc->model == LINVIEW_MODEL_LINEAR &&
         (desc->kind == LINVIEW_POWER || desc->kind == LINVIEW_POWER_SUM)) &&
-      !(desc->model == LINVIEW_MODEL_SKIP && desc->kind == LINVIEW_POWER))
+      !(desc->model == LINVIEW_MODEL_SKIP &&
+        (desc->kind == LINVIEW_POWER || desc->kind == LINVIEW_POWER_SUM)))
     return fail(LINVIEW_EINVAL, "model %d is not available for kind %d", desc->model, desc->kind);
   int ninputs = 0;
   switch (desc->kind) {
@@ -1273,8 +1309,6 @@ linview_status linview_estimate_device_bytes(const linview_program_desc* d, int6
     return fail(LINVIEW_EINVAL, "bad precision %d", d->precision);
   if (d->n < 1 || d->n > (1 << 20)) return fail(LINVIEW_EINVAL, "bad n=%lld", (long long)d->n);
   if (d->model == LINVIEW_MODEL_LINEAR || d->model == LINVIEW_MODEL_SKIP) {
-    if (d->model == LINVIEW_MODEL_SKIP && d->kind != LINVIEW_POWER)
-      return fail(LINVIEW_EINVAL, "the skip model maintains powers only");
     LV_TRY(check_power_model(*d));
   } else if (d->model == LINVIEW_MODEL_EXP) {
     if (!is_pow2(d->k)) return fail(LINVIEW_EINVAL, "k=%d must be a power of two", d->k);

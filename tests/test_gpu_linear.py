@@ -100,17 +100,20 @@ def test_linear_model_errors():
     prog.close()
 
 
-@pytest.mark.parametrize("prec,n,k,s,r", [
-    ("f64", 256, 8, 2, 1), ("f64", 200, 12, 4, 2), ("f64", 256, 16, 4, 1),
-    ("f32", 1000, 16, 4, 1), ("f32", 777, 16, 2, 4), ("f32", 512, 32, 8, 2)])
-def test_skip_model_matches_reevaluation(prec, n, k, s, r):
-    """Skip-s model (Appendix A): views A^(2^j) up to A^s, then A^2s .. A^k."""
+@pytest.mark.parametrize("prec,n,k,s,r,sums", [
+    ("f64", 256, 8, 2, 1, True), ("f64", 200, 12, 4, 2, False), ("f64", 256, 16, 4, 1, True),
+    ("f64", 128, 8, 1, 2, True), ("f32", 1000, 16, 4, 1, True), ("f32", 777, 16, 2, 4, True),
+    ("f32", 512, 32, 8, 2, False)])
+def test_skip_model_matches_reevaluation(prec, n, k, s, r, sums):
+    """Skip-s model (Appendix A): views A^(2^j) up to A^s, then A^2s .. A^k,
+    and the sums S'_h of the same h (Section 4.2.3)."""
     from paper_1403_6968_gb300 import Program
     dt = _np(prec)
     a = li.power_matrix(n, seed=n + k + s, dtype=dt)
-    prog = Program("power", [a], k=k, r_max=r, precision=prec, model="skip", skip=s)
+    prog = Program("power_sum" if sums else "power", [a], k=k, r_max=r, precision=prec,
+                   model="skip", skip=s)
     hs = op.skip_levels(k, s)
-    assert prog.num_views() == len(hs)
+    assert prog.num_views() == (2 * len(hs) - 1 if sums else len(hs))
     acur = a.astype(np.float64)
     if r == 1:
         for i, v in li.row_update_stream(n, 6, seed=k + s, dtype=dt):
@@ -124,6 +127,11 @@ def test_skip_model_matches_reevaluation(prec, n, k, s, r):
     for vid, h in enumerate(hs):
         got = prog.read_view(vid).cpu().numpy().astype(np.float64)
         assert rel_frob(got, ref[h]) <= TOL[prec], (h, rel_frob(got, ref[h]))
+    if sums:
+        sref = op.skip_sums(acur, k, s)
+        for j, h in enumerate(hs[1:], start=1):
+            got = prog.read_view(len(hs) + j - 1).cpu().numpy().astype(np.float64)
+            assert rel_frob(got, sref[h]) <= TOL[prec], ("S", h, rel_frob(got, sref[h]))
     prog.close()
 
 
@@ -133,7 +141,5 @@ def test_skip_model_errors():
     for k, s in ((16, 3), (12, 8), (8, 8)):
         with pytest.raises(LinviewError):
             Program("power", [a], k=k, r_max=1, model="skip", skip=s)
-    with pytest.raises(LinviewError):
-        Program("power_sum", [a], k=8, r_max=1, model="skip", skip=2)
     with pytest.raises(LinviewError):
         Program("power", [a], k=8, r_max=1, model="exp", skip=2)

@@ -233,7 +233,8 @@ def test_serve_row_coalescing():
 @pytest.mark.parametrize("kind,n,k,r_max,model", [
     ("power", 1000, 16, 8, "exp"), ("power", 256, 8, 1, "exp"), ("power_sum", 777, 16, 4, "exp"),
     ("power_sum", 512, 4, 2, "exp"), ("power", 300, 16, 4, "linear"),
-    ("power_sum", 300, 5, 1, "linear"), ("power", 300, 16, 2, "skip")])
+    ("power_sum", 300, 5, 1, "linear"), ("power", 300, 16, 2, "skip"),
+    ("power_sum", 300, 16, 4, "skip")])
 def test_estimate_equals_program_bytes(kind, n, k, r_max, model):
     P = _pkg()
     a = li.power_matrix(n, seed=1, dtype=np.float32)
