@@ -82,6 +82,7 @@ struct View {
   void* ptr = nullptr;
   int64_t rows = 0, cols = 0, ld = 0;
   bool square = false;  // has a tensor map for view passes
+  bool tma_store = false;  // tmap's row extent is a multiple of 16 bytes
   CUtensorMap tmap;
   CUtensorMap tmap_tc;  // FP32: 32 x 128 boxes, 128B swizzle (tensor-core update pass)
 };
@@ -224,6 +225,7 @@ static linview_status add_square_view(linview_program* p, int64_t n) {
   const int64_t rows_pad = rup(n, kBatch);
   LV_TRY(dalloc(p, (size_t)square_view_bytes(n, p->elem), &v.ptr));
   v.square = true;
+  v.tma_store = (v.ld * p->elem) % 16 == 0;
   if (!make_tmap(&v.tmap, v.ptr, p->elem, v.ld, rows_pad, v.ld))
     return fail(LINVIEW_EDEVICE, "cuTensorMapEncodeTiled failed for an %lld x %lld view",
                 (long long)n, (long long)n);
@@ -338,6 +340,7 @@ static linview_status run_fused(linview_program* p, const View& v, int mode, int
   pp.rows_per_cta = g.rows_per_cta;
   pp.status = p->status;
   pp.Cpart = Cpart;
+  pp.tma_store = v.tma_store ? 1 : 0;
   const double nn = (double)v.rows * (double)v.rows * sizeof(T);
   ProfScope ps(p, s, (mode & 4) ? 2.0 * nn : nn, 1);
   LV_CUDA((launch_fused<T>(pp, v.tmap, r, mode, s)));
@@ -377,6 +380,7 @@ static linview_status run_update(linview_program* p, const View& v, const T* Uu,
     pp.rows_per_cta = g.rows_per_cta;
     pp.status = p->status;
     pp.suffix_rin = suffix_rin;  // host guarantees a single chunk when set
+    pp.tma_store = v.tma_store ? 1 : 0;
     ProfScope ps(p, s, 2.0 * (double)v.rows * (double)v.rows * sizeof(T), 2);
     LV_CUDA((launch_update<T>(pp, v.tmap, w, s)));
   }
@@ -1803,6 +1807,7 @@ linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp
   v.ld = ldp;
   v.square = true;
   if (!make_tmap(&v.tmap, P, e, n, n, ldp)) return fail(LINVIEW_EDEVICE, "tensor map encode failed");
+  v.tma_store = (n * e) % 16 == 0;
   const PassGeom g = fused_geom(e, (int)n, tmp.sms);
   tmp.fs = ldf;
   tmp.part_cs = rup(n, 64);

@@ -62,6 +62,10 @@ struct PassParams {
   unsigned* status;   // device status word
   double* Cpart;      // fused XYU pass: per-row-range V^T U partials [gR][r*r] (or null)
   int suffix_rin;     // update pass: >0 applies block suffix sums (block width) to Wu
+  int tma_store;      // FP32 passes may store updated tiles with TMA: the tensor map's
+                      // row extent is a multiple of 16 bytes (a TMA store writes whole
+                      // 16-byte units, so a row ending inside one would overwrite the
+                      // elements past the view, e.g. a caller's padding)
 };
 
 // Host: grid geometry for a pass over an n x n view.

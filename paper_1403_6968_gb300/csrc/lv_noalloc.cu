@@ -184,6 +184,7 @@ extern "C" linview_status linview_level_pass_noalloc(int precision, int64_t n, v
   base.Xpart = static_cast<char*>(scratch) + kStatusBytes;
   base.Ypart = static_cast<char*>(base.Xpart) + rup64((int64_t)xbytes, 256);
   base.status = status;
+  base.tma_store = (n * e) % 16 == 0 ? 1 : 0;
   if (e == 4)
     ce = run<float>(base, tm, (int)n, (int)r, sms, static_cast<const float*>(U),
                     static_cast<const float*>(V), static_cast<float*>(X), static_cast<float*>(Y),

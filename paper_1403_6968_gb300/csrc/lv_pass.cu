@@ -528,15 +528,27 @@ static cudaError_t launch_fused_t(const PassParams& p, const CUtensorMap& tm, cu
           : sizeof(T) * kStages * kBatch * STRIP + sizeof(uint64_t) * kStages +
                 sizeof(T) * (2 * kBatch * R + kBatch * R * (128 + 32 / R)) +
                 sizeof(double) * R * R;
-  void (*kfn)(const CUtensorMap, const PassParams);
-  if constexpr (kWs)
-    kfn = fused_ws_kernel<R, MODE>;
-  else
+  using Kfn = void (*)(const CUtensorMap, const PassParams);
+  Kfn kfn;
+  if constexpr (kWs) {
+    // the TMA write-back variant exists for the non-split update modes only
+    constexpr bool kTs = (MODE & 4) != 0 && R <= 2;
+    static const cudaError_t configured_ts =
+        cudaFuncSetAttribute(fused_ws_kernel<R, MODE, kTs>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(fused_ws_kernel<R, MODE, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (configured_ts != cudaSuccess) return configured_ts;
+    if (configured != cudaSuccess) return configured;
+    kfn = p.tma_store ? fused_ws_kernel<R, MODE, kTs> : fused_ws_kernel<R, MODE, false>;
+  } else {
     kfn = fused_pass_kernel<T, R, MODE>;
-  // set once per kernel instance (thread-safe static initialisation)
-  static const cudaError_t configured =
-      cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (configured != cudaSuccess) return configured;
+    // set once per kernel instance (thread-safe static initialisation)
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (configured != cudaSuccess) return configured;
+  }
   if constexpr (kWs) {
     const cudaError_t e = launch_pdl(kfn, p.gC * p.gR, kThreads, smem, s, tm, p);
     if (e != cudaSuccess) return e;
@@ -579,15 +591,23 @@ static cudaError_t launch_update_t(const PassParams& p, const CUtensorMap& tm, c
                 sizeof(float) * kStagesWs * kBatch * R
           : sizeof(T) * kStages * kBatch * STRIP + sizeof(uint64_t) * kStages +
                 sizeof(T) * kBatch * R;
-  void (*kfn)(const CUtensorMap, const PassParams);
-  if constexpr (kWs)
-    kfn = update_ws_kernel<R, COLS>;
-  else
+  using Kfn = void (*)(const CUtensorMap, const PassParams);
+  Kfn kfn;
+  if constexpr (kWs) {
+    // set once per kernel instance (thread-safe static initialisation)
+    static const cudaError_t configured_ts = cudaFuncSetAttribute(
+        update_ws_kernel<R, COLS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static const cudaError_t configured = cudaFuncSetAttribute(
+        update_ws_kernel<R, COLS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (configured_ts != cudaSuccess) return configured_ts;
+    if (configured != cudaSuccess) return configured;
+    kfn = p.tma_store ? update_ws_kernel<R, COLS, true> : update_ws_kernel<R, COLS, false>;
+  } else {
     kfn = update_pass_kernel<T, R, COLS>;
-  // set once per kernel instance (thread-safe static initialisation)
-  static const cudaError_t configured =
-      cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (configured != cudaSuccess) return configured;
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (configured != cudaSuccess) return configured;
+  }
   if constexpr (kWs) {
     const cudaError_t e = launch_pdl(kfn, p.gC * p.gR, kThreads, smem, s, tm, p);
     if (e != cudaSuccess) return e;

@@ -19,35 +19,47 @@
 // kernel with LINVIEW_ETIMEOUT latched instead of a hang.
 // (Included inside namespace lv after update_pass_kernel and suffix_blocks.)
 
-// Sum each of x[0..V) over the 32 lanes of a warp by a fixed butterfly
-// (reduce-scatter): each level sends half of the remaining values to the
-// partner lane and keeps the other half, then plain xor-sums finish.  On
-// return, lanes with lane % (32 / V) == 0 hold the total of value idx.
-// Costs V - 1 + 5 - log2(V) shuffles for all V values.
-template <int M>
-__device__ __forceinline__ float rs_levels(const float (&in)[M], int lane, int o, int& idx) {
+// Row sums P U: each of V = MC x MG values (MC factor columns x MG rows) is
+// summed over the 32 lanes of a warp by a fixed butterfly (reduce-scatter):
+// each level sends half of the remaining values to the partner lane and keeps
+// the other half, then plain xor-sums finish (V - 1 + 5 - log2(V) shuffles
+// for all V values).
+// Reduce-scatter of MC x MG values (slot c * MG + g) in which the first
+// log2(MC) levels need no lane selects: there each lane keeps the first half
+// of its slots and adds its partner's second half, which works because lane
+// L stores value (c, g) at slot ((c ^ cmask) * MG + g), cmask =
+// scatter_mask<MC * MG>(L) / MG (so partners hold each other's halves).  The
+// log2(MG) levels after them keep the half the lane's own bit selects.  On
+// return, lanes with lane % (32 / (MC * MG)) == 0 hold the total of value
+// (cmask, scatter_mask<MC * MG>(L) % MG).
+template <int V>
+__device__ __forceinline__ int scatter_mask(int lane) {
+  constexpr int m = V >= 32 ? 5 : V >= 16 ? 4 : V >= 8 ? 3 : V >= 4 ? 2 : V >= 2 ? 1 : 0;
+  return (lane >> (5 - m)) & (V - 1);
+}
+
+template <int MC, int MG>
+__device__ __forceinline__ float mixed_levels(const float (&in)[MC * MG], int lane, int o) {
   constexpr unsigned FULL = 0xffffffffu;
+  constexpr int M = MC * MG;
   if constexpr (M == 1) {
     float v = in[0];
 #pragma unroll
     for (int oo = o; oo >= 1; oo >>= 1) v += __shfl_xor_sync(FULL, v, oo);
     return v;
+  } else if constexpr (MC > 1) {
+    float out[M / 2];
+#pragma unroll
+    for (int i = 0; i < M / 2; ++i) out[i] = in[i] + __shfl_xor_sync(FULL, in[i + M / 2], o);
+    return mixed_levels<MC / 2, MG>(out, lane, o >> 1);
   } else {
     const bool up = (lane & o) != 0;
     float out[M / 2];
 #pragma unroll
     for (int i = 0; i < M / 2; ++i)
       out[i] = (up ? in[i + M / 2] : in[i]) + __shfl_xor_sync(FULL, up ? in[i] : in[i + M / 2], o);
-    idx += up ? M / 2 : 0;
-    return rs_levels<M / 2>(out, lane, o >> 1, idx);
+    return mixed_levels<1, MG / 2>(out, lane, o >> 1);
   }
-}
-
-template <int V>
-__device__ __forceinline__ float warp_reduce_scatter(const float (&x)[V], int lane, int& idx) {
-  static_assert(V >= 1 && V <= 32 && (V & (V - 1)) == 0, "V must be a power of two <= 32");
-  idx = 0;
-  return rs_levels<V>(x, lane, 16, idx);
 }
 
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
@@ -110,7 +122,7 @@ __device__ __forceinline__ void rank_update_row(const float* u, const float (&pv
 //          the in-place update of rows 4 rg .. 4 rg + 3; this halves the
 //          column factors each thread keeps in registers.
 // ---------------------------------------------------------------------------
-template <int R, int MODE>
+template <int R, int MODE, bool TS>
 __global__ void __launch_bounds__(kThreads, 2)
     fused_ws_kernel(const __grid_constant__ CUtensorMap tmap, const PassParams p) {
   using T = float;
@@ -129,9 +141,14 @@ __global__ void __launch_bounds__(kThreads, 2)
   constexpr int RH2 = PACK ? RH / 2 : 1;         // ... as packed pairs
   constexpr int ROWS = SPLIT ? kBatch : kBatch / 2;  // batch rows a thread visits
   // rows whose products are reduced by one butterfly (G * RH values)
-  constexpr int G = SPLIT ? 16 / RH : (R <= 4 ? ROWS : 1);
+  constexpr int G = SPLIT ? (16 / RH < 4 ? 16 / RH : 4) : (R <= 4 ? ROWS : 1);
   constexpr int S = kStagesWs;
   static_assert(ROWS % G == 0 && G * RH <= 32, "butterfly grouping");
+  // Without SPLIT every view element is read and updated by one thread, so
+  // the updated rows go back into the stage and leave by TMA store (TS: the
+  // tensor map's rows end on 16-byte units); with SPLIT both row groups read
+  // every row, and each thread stores its own.
+  constexpr bool TSTORE = TS && DO_U && !SPLIT;
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   T* stages = reinterpret_cast<T*>(smem_raw);
@@ -178,6 +195,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     *abort_flag = 0;
     fence_mbar_init();
   }
+  // boxes of the strip that lie wholly past column n are never loaded: zero
+  // them once, so that every row of a stage can be read without masks (the
+  // loaded boxes read zeros past the view: TMA fills rows and columns outside
+  // the tensor map with zeros, and a program's own views keep zero padding)
+#pragma unroll
+  for (int bx = 0; bx < NB; ++bx)
+    if (strip0 + bx * BOXC >= n)
+      for (int i = tid; i < S * kBatch * BOXC; i += kThreads)
+        stages[(i / (kBatch * BOXC)) * STAGE_ELEMS + bx * kBatch * BOXC + i % (kBatch * BOXC)] = 0.f;
   __syncthreads();
   int nbox = 0;
 #pragma unroll
@@ -234,19 +260,25 @@ __global__ void __launch_bounds__(kThreads, 2)
     issued = min(S, nbatch);
   }
 
-  // column-side factors for this thread's 4 columns
-  float2 ucol2[COLS][RH2];  // PACK: (U(col_k, cb+2c2), U(col_k, cb+2c2+1)); else .x = U(col_k, 0)
+  // Lane layout of the row products P U: this lane keeps the product of
+  // (factor column c, row-in-group g) at slot (c ^ cmask) * G + g, so that
+  // the butterfly's column levels need no lane selects (mixed_levels).
+  const int vmask = scatter_mask<G * RH>(lane);
+  const int cmask = vmask / G, rmask = vmask % G;
+  // column-side factors for this thread's 4 columns (X slots permuted by cmask)
+  float2 ucol2[COLS][RH2];  // PACK: (U(col_k, cb+(2c2^cmask)), U(col_k, cb+((2c2+1)^cmask)))
   float2 yacc2[COLS][RH2];
 #pragma unroll
   for (int k = 0; k < COLS; ++k) {
     const int col = col0 + k;
 #pragma unroll
     for (int c2 = 0; c2 < RH2; ++c2) {
-      const int c = cb + (PACK ? 2 * c2 : 0);
+      const int c = cb + ((PACK ? 2 * c2 : 0) ^ cmask);
+      const int cn = cb + ((PACK ? 2 * c2 + 1 : 0) ^ cmask);
       const bool ok0 = DO_X && (c < r) && (col < n);
-      const bool ok1 = DO_X && PACK && (c + 1 < r) && (col < n);
+      const bool ok1 = DO_X && PACK && (cn < r) && (col < n);
       ucol2[k][c2] = make_float2(ok0 ? Xf[(int64_t)c * p.fs + col] : 0.f,
-                                 ok1 ? Xf[(int64_t)(c + 1) * p.fs + col] : 0.f);
+                                 ok1 ? Xf[(int64_t)cn * p.fs + col] : 0.f);
       yacc2[k][c2] = make_float2(0.f, 0.f);
     }
   }
@@ -302,16 +334,10 @@ __global__ void __launch_bounds__(kThreads, 2)
           acc = fma((double)Vst[j * R + c1], (double)Ust[j * R + c2], acc);
         Csh[cslot] = acc;
       }
-      const T* sp = stages + st * STAGE_ELEMS + box * kBatch * BOXC + inbox;
-      float xg[G * RH];  // products of the current group of rows (zero for absent rows)
-      auto do_row = [&](int j, float* xr, bool upd) {
-          float4 v4 = *reinterpret_cast<const float4*>(sp + j * BOXC);
-          if (!vec_ok) {
-            v4.x = (col0 + 0 < n) ? v4.x : 0.f;
-            v4.y = (col0 + 1 < n) ? v4.y : 0.f;
-            v4.z = (col0 + 2 < n) ? v4.z : 0.f;
-            v4.w = (col0 + 3 < n) ? v4.w : 0.f;
-          }
+      T* sp = stages + st * STAGE_ELEMS + box * kBatch * BOXC + inbox;
+      float xg[RH * G];  // products of the current group of rows
+      auto do_row = [&](int j, int g, bool upd) {
+          const float4 v4 = *reinterpret_cast<const float4*>(sp + j * BOXC);
           const float pvs[COLS] = {v4.x, v4.y, v4.z, v4.w};
           if constexpr (PACK) {
             const float2 pd[COLS] = {make_float2(v4.x, v4.x), make_float2(v4.y, v4.y),
@@ -344,8 +370,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                 for (int c2 = 0; c2 < RH2; ++c2) x2[c2] = __ffma2_rn(pd[k], ucol2[k][c2], x2[c2]);
 #pragma unroll
               for (int c2 = 0; c2 < RH2; ++c2) {
-                xr[2 * c2] = x2[c2].x;
-                xr[2 * c2 + 1] = x2[c2].y;
+                xg[(2 * c2) * G + g] = x2[c2].x;
+                xg[(2 * c2 + 1) * G + g] = x2[c2].y;
               }
             }
           } else {
@@ -358,20 +384,24 @@ __global__ void __launch_bounds__(kThreads, 2)
               float x = 0.f;
 #pragma unroll
               for (int k = 0; k < COLS; ++k) x = fmaf(pvs[k], ucol2[k][0].x, x);
-              xr[0] = x;
+              xg[g] = x;
             }
           }
           if constexpr (DO_U) {
-            if (upd) {
+            if (upd && (TSTORE || j < nb)) {
               float o[COLS];
               rank_update_row<R, COLS>(Ust + j * R, pvs, wp, o);
-              T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
-              if (vec_ok) {
-                *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+              if constexpr (TSTORE) {
+                *reinterpret_cast<float4*>(sp + j * BOXC) = make_float4(o[0], o[1], o[2], o[3]);
               } else {
+                T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
+                if (vec_ok) {
+                  *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+                } else {
 #pragma unroll
-                for (int k = 0; k < COLS; ++k)
-                  if (col0 + k < n) dst[k] = o[k];
+                  for (int k = 0; k < COLS; ++k)
+                    if (col0 + k < n) dst[k] = o[k];
+                }
               }
             }
           }
@@ -379,48 +409,48 @@ __global__ void __launch_bounds__(kThreads, 2)
       auto finish_group = [&](int jj) {  // after the last row of a group: one butterfly
         if constexpr (DO_X) {
           if ((jj % G) == G - 1) {
-            int v = 0;
-            const float tot = warp_reduce_scatter<G * RH>(xg, lane, v);
-            const int jr = row_of(jj - (G - 1) + v / RH);  // batch row of value v
+            const float tot = mixed_levels<RH, G>(xg, lane, 16);  // value (cmask, rmask)
+            const int jr = row_of(jj - (G - 1) + rmask);
             if ((lane % (32 / (G * RH))) == 0)
-              Xw[((st * kBatch + jr) * 4 + wq) * R + cb + (v % RH)] = tot;
+              Xw[((st * kBatch + jr) * 4 + wq) * R + cb + cmask] = tot;
           }
         }
       };
-      // rows this thread updates: its own half of the batch (SPLIT: the
-      // first four rows it visits)
+      // whether the row visited at step jj is one this thread updates: its
+      // own half of the batch (SPLIT: the first four rows it visits)
       auto updates_row = [&](int jj) { return SPLIT ? jj < kBatch / 2 : true; };
-      // full batch: no per-row guards so that rows interleave (R <= 4; at R = 8
-      // the extra live registers would spill)
-      if (R <= 4 && nb == kBatch) {
+      // rows past the view (a partial last batch) read zeros from the stage
+      // and the factor rows, so they add nothing to the products and need no
+      // guard (only their stores are skipped); R = 16 keeps one per row, which
+      // stops the compiler from interleaving rows past the register budget
 #pragma unroll
-        for (int jj = 0; jj < ROWS; ++jj) {
-          float* xr = xg + (jj % G) * RH;
-          if constexpr (DO_X) {
+      for (int jj = 0; jj < ROWS; ++jj) {
+        if (R < 16 || row_of(jj) < nb) {
+          do_row(row_of(jj), jj % G, updates_row(jj));
+        } else if constexpr (DO_X) {
 #pragma unroll
-            for (int c = 0; c < RH; ++c) xr[c] = 0.f;
-          }
-          do_row(row_of(jj), xr, updates_row(jj));
-          finish_group(jj);
+          for (int c = 0; c < RH; ++c) xg[c * G + jj % G] = 0.f;
         }
-      } else {
-#pragma unroll
-        for (int jj = 0; jj < ROWS; ++jj) {
-          float* xr = xg + (jj % G) * RH;
-          if constexpr (DO_X) {
-#pragma unroll
-            for (int c = 0; c < RH; ++c) xr[c] = 0.f;
-          }
-          if (row_of(jj) < nb) do_row(row_of(jj), xr, updates_row(jj));
-          finish_group(jj);
-        }
+        finish_group(jj);
       }
+      if constexpr (TSTORE) fence_proxy_async();  // rows written back, before the TMA store
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
     if (warp == 0) {
-      // all warps are done with batch b: fold its row sums, refill the stage
+      // all warps are done with batch b: store it (TSTORE), fold its row
+      // sums, refill a stage
       if (wait_or_abort(&empty[st], parity, abort_flag, p.status)) {
+        if constexpr (TSTORE) {
+          if (lane == 0) {
+#pragma unroll
+            for (int bx = 0; bx < NB; ++bx)
+              if (strip0 + bx * BOXC < n)
+                tma_store_2d(&tmap, stages + st * STAGE_ELEMS + bx * kBatch * BOXC,
+                             strip0 + bx * BOXC, row0);
+            bulk_commit();
+          }
+        }
         if constexpr (DO_X) {
           T* xo = static_cast<T*>(p.Xpart) + (int64_t)s * p.xp_s;
           for (int idx = lane; idx < kBatch * R; idx += 32) {
@@ -431,7 +461,16 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
           }
         }
-        if (b + S < nbatch) {
+        if constexpr (TSTORE) {
+          // the stage of batch b - 1, whose store has been read out, takes
+          // batch b - 1 + S
+          if (b >= 1 && b - 1 + S < nbatch) {
+            if (lane == 0) bulk_wait_read<1>();
+            __syncwarp();
+            produce(b - 1 + S);
+            ++issued;
+          }
+        } else if (b + S < nbatch) {
           __syncwarp();
           produce(b + S);
           ++issued;
@@ -439,10 +478,13 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
   }
-  // on an abort, wait (bounded) for the copies issued but never waited on
-  if (warp == 0 && *abort_flag) {
-    for (int bb = waited; bb < issued; ++bb)
-      mbar_wait_bounded(&full[bb % S], (uint32_t)((bb / S) & 1), nullptr);
+  if (warp == 0) {
+    // stores complete before the ring is reused below or the CTA exits
+    if (TSTORE && lane == 0) bulk_wait0();
+    // on an abort, wait (bounded) for the copies issued but never waited on
+    if (*abort_flag)
+      for (int bb = waited; bb < issued; ++bb)
+        mbar_wait_bounded(&full[bb % S], (uint32_t)((bb / S) & 1), nullptr);
   }
   if (DO_U && DO_Y && p.Cpart != nullptr) {
     __syncthreads();
@@ -523,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // threads owning 2 columns each (R <= 32); COLS = 1: one column each (R = 64,
 // whose column factor fills 64 registers per column).
 // ---------------------------------------------------------------------------
-template <int R, int COLS>
+template <int R, int COLS, bool TS>
 __global__ void __launch_bounds__(kThreads, 2)
     update_ws_kernel(const __grid_constant__ CUtensorMap tmap, const PassParams p) {
   using T = float;
@@ -663,8 +705,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     const bool ready = wait_or_abort(&full[st], parity, abort_flag, p.status);
     if (ready) waited = b + 1;
     if (ready && any_col) {
-      const T* sp = stages + st * STAGE_ELEMS + box * kBatch * BOXC + inbox;
+      T* sp = stages + st * STAGE_ELEMS + box * kBatch * BOXC + inbox;
       const T* Ust = Us + st * kBatch * R;
+      // TS: the updated row goes back to its place in the stage, which warp 0
+      // then stores with TMA (rows and columns past the view are clipped)
       auto row = [&](int j) {
           float pv[COLS];
           if constexpr (COLS == 4) {
@@ -678,8 +722,8 @@ __global__ void __launch_bounds__(kThreads, 2)
           }
           float o[COLS];
           rank_update_row<R, COLS>(Ust + j * R, pv, wp, o);
-          T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
-          if (vec_ok) {
+          T* dst = TS ? sp + j * BOXC : P + (int64_t)(row0 + j) * p.ldp + col0;
+          if (TS || vec_ok) {
             if constexpr (COLS == 4)
               *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
             else if constexpr (COLS == 2)
@@ -700,19 +744,41 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int jj = 0; jj < kBatch / GROUPS; ++jj)
           if (rg + GROUPS * jj < nb) row(rg + GROUPS * jj);
       }
+      if constexpr (TS) fence_proxy_async();  // rows written back, before the TMA store
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
-    if (warp == 0 && b + S < nbatch) {
+    if (warp == 0) {
       if (wait_or_abort(&empty[st], parity, abort_flag, p.status)) {
-        __syncwarp();
-        produce(b + S);
-        ++issued;
+        if constexpr (TS) {
+          // all warps have written batch b back: store it; the stage of
+          // batch b - 1, whose store has been read out, takes batch b - 1 + S
+          if (lane == 0) {
+#pragma unroll
+            for (int bx = 0; bx < NB; ++bx)
+              if (strip0 + bx * BOXC < n)
+                tma_store_2d(&tmap, stages + st * STAGE_ELEMS + bx * kBatch * BOXC,
+                             strip0 + bx * BOXC, row0);
+            bulk_commit();
+          }
+          if (b >= 1 && b - 1 + S < nbatch) {
+            if (lane == 0) bulk_wait_read<1>();
+            __syncwarp();
+            produce(b - 1 + S);
+            ++issued;
+          }
+        } else if (b + S < nbatch) {
+          __syncwarp();
+          produce(b + S);
+          ++issued;
+        }
       }
     }
   }
-  if (warp == 0 && *abort_flag) {
-    for (int bb = waited; bb < issued; ++bb)
-      mbar_wait_bounded(&full[bb % S], (uint32_t)((bb / S) & 1), nullptr);
+  if (warp == 0) {
+    if (TS && lane == 0) bulk_wait0();  // stores complete before the shared memory goes away
+    if (*abort_flag)  // on an abort, wait (bounded) for the copies never waited on
+      for (int bb = waited; bb < issued; ++bb)
+        mbar_wait_bounded(&full[bb % S], (uint32_t)((bb / S) & 1), nullptr);
   }
 }

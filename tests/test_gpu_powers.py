@@ -107,7 +107,9 @@ def test_matches_oracle_incremental(prec):
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("n,r,upd", [(1, 1, True), (5, 3, True), (300, 8, True), (1000, 8, False),
-                                     (1031, 16, True), (2048, 64, True), (640, 24, False)])
+                                     (1031, 16, True), (2048, 64, True), (640, 24, False),
+                                     (777, 1, True), (1029, 2, True), (1030, 4, True),
+                                     (1032, 16, True), (1036, 2, True)])
 def test_level_pass_kernel(prec, n, r, upd):
     """One Appendix-A level pass (P U, P^T V, P += U V^T) on caller memory."""
     from paper_1403_6968_gb300 import level_pass
@@ -119,8 +121,10 @@ def test_level_pass_kernel(prec, n, r, upd):
     u = g.standard_normal((n, r)).astype(dt)
     v = g.standard_normal((n, r)).astype(dt)
     ld = ((n + 3) // 4) * 4
-    P = torch.zeros((n, ld), dtype=torch.float64 if prec == "f64" else torch.float32,
-                    device="cuda")
+    # a sentinel in the caller's padding: row ends that fall inside a 16-byte
+    # unit (n % 4 != 0 in FP32) must not be written past
+    P = torch.full((n, ld), 3.0, dtype=torch.float64 if prec == "f64" else torch.float32,
+                   device="cuda")
     P[:, :n] = _dev(p)
     Pv = P[:, :n]
     Ut, Vt = _dev(u.T.copy()), _dev(v.T.copy())
@@ -133,7 +137,7 @@ def test_level_pass_kernel(prec, n, r, upd):
     assert rel_frob(Yt.cpu().numpy().T, y_ref) <= tol
     got_p = Pv.cpu().numpy()
     assert rel_frob(got_p, p_ref if upd else p) <= tol
-    assert not P[:, n:].any()  # padding untouched
+    assert bool((P[:, n:] == 3.0).all())  # padding untouched
 
 
 def test_reeval_modes_against_oracle():

@@ -36,7 +36,8 @@ def _rel(x, y):
 
 
 @pytest.mark.parametrize("prec,n,r,upd", [("f32", 1000, 3, True), ("f32", 8192, 8, True),
-                                          ("f32", 777, 24, True), ("f32", 2048, 8, False),
+                                          ("f32", 777, 24, True), ("f32", 780, 24, True),
+                                          ("f32", 2048, 8, False),
                                           ("f64", 513, 4, True), ("f64", 300, 12, True)])
 def test_noalloc_matches_allocating_entry_two_calls(prec, n, r, upd):
     from paper_1403_6968_gb300 import level_pass, level_pass_noalloc
