@@ -196,73 +196,141 @@ cudaError_t launch_gram(const T* V, const T* U, int64_t fs, int n, int r, double
   return cudaGetLastError();
 }
 
-// One thread per (row j, factor column c):
+// Assembly of the next level's factor columns, for factor column c and row j:
 //   X'(j,c) = sum_s Xpart[s](j,c) + sum_c2 U_h(j,c2) C_h(c2,c),
 //   Y(j,c)  = sum_q Ypart[q](j,c),
-// with C_h = sum of the nC FP64 partial blocks (fixed order, FP64), staged per
-// CTA.  The partial sums and the U_h C_h correction are accumulated in the
-// view type (fixed order): FP64 arithmetic here would be slow on this part and
-// buys nothing, the partials themselves being sums in the view type.
+// with C_h = V_h^T U_h the sum of the nC FP64 partial blocks.  Everything
+// read here was written by the kernels just before, so the time is load
+// latency, not bandwidth: a CTA takes 32 rows of one column c and its 8 warps
+// split the strips s, the row ranges q and the columns c2 (warp w takes those
+// congruent to w mod 8), so every thread issues a handful of independent
+// loads at once.  The C_h column is summed by groups of 8 lanes over the
+// blocks (same split) and a fixed butterfly; the warp partials are added in
+// warp order.  All orders are fixed, so the results are reproducible.  The
+// sums are in the view type except C_h (FP64, rounded once): FP64 arithmetic
+// is slow on this part and buys nothing, the partials themselves being sums
+// in the view type.
+constexpr int kAsmWarps = kThreads / 32;
+
+// sum over i = w, w + kAsmWarps, ... < count of src[i * stride], in increasing i
+template <typename T, typename A>
+__device__ __forceinline__ A strided_sum(const T* src, int64_t stride, int count, int w) {
+  A acc = A(0);
+  constexpr int kU = 4;
+  for (int i0 = w; i0 < count; i0 += kU * kAsmWarps) {
+    T v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = i0 + u * kAsmWarps;
+      v[u] = (i < count) ? src[(int64_t)i * stride] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) acc += (A)v[u];
+  }
+  return acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) assemble_kernel(const AssembleParams a) {
-  extern __shared__ double Cs[];  // r_h x r_h, FP64 sums rounded to T
+  __shared__ T Cc[kMaxAsmR];                 // column c of C_h (rounded to T)
+  __shared__ T red[3][kAsmWarps][32];        // per-warp partials: X, U_h C_h, Y
   griddep_wait();  // everything read here comes from the kernels before
   griddep_launch_dependents();
   const int rh = a.r_h;
-  const int ne = rh * rh;
-  T* Ct = reinterpret_cast<T*>(Cs);
-  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-    double sum = 0.0;
-    for (int b = 0; b < a.nC; ++b) sum += a.C[(int64_t)b * ne + e];
-    Ct[e] = (T)sum;
-  }
-  __syncthreads();
-  const int ro = a.r_out > 0 ? a.r_out : rh;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)a.n * ro) return;
-  const int c = (int)(idx / a.n);
-  const int j = (int)(idx % a.n);
+  const int c = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 32 + lane;
+  const bool valid = j < a.n;
+  const int jj = valid ? j : 0;
   const T* Xp = static_cast<const T*>(a.Xpart);
   const T* Yp = static_cast<const T*>(a.Ypart);
   const T* Uh = static_cast<const T*>(a.Uh);
-  T x = T(0);
-#pragma unroll 8
-  for (int sidx = 0; sidx < a.gC; ++sidx) x += Xp[(int64_t)sidx * a.xp_s + (int64_t)c * a.part_cs + j];
-  for (int c2 = 0; c2 < rh; ++c2) x = fma(Uh[(int64_t)c2 * a.fs + j], Ct[c2 * rh + c], x);
-  static_cast<T*>(a.Unew)[(int64_t)c * a.fs + j] = x;
-  if (Yp) {
-    T y = T(0);
-#pragma unroll 8
-    for (int q = 0; q < a.gR; ++q) y += Yp[(int64_t)q * a.yp_q + (int64_t)c * a.part_cs + j];
-    static_cast<T*>(a.Ynew)[(int64_t)c * a.fs + j] = y;
+  // C_h(c2, c): lane group g = threadIdx.x / 8 takes c2 = g, g + 32, ...;
+  // its 8 lanes split the blocks (the loop bound is the same for a whole
+  // warp, so every lane reaches the shuffles)
+  const int ne = rh * rh;
+  for (int c2b = warp * 4; c2b < rh; c2b += kThreads / 8) {
+    const int c2 = c2b + (lane >> 3);
+    double sum = (c2 < rh) ? strided_sum<double, double>(a.C + (int64_t)c2 * rh + c, ne, a.nC,
+                                                         lane & 7)
+                           : 0.0;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((lane & 7) == 0 && c2 < rh) Cc[c2] = (T)sum;
   }
+  // this warp's share of the strips, row ranges and columns of U_h
+  T x = strided_sum<T, T>(Xp + (int64_t)c * a.part_cs + jj, a.xp_s, a.gC, warp);
+  T y = Yp ? strided_sum<T, T>(Yp + (int64_t)c * a.part_cs + jj, a.yp_q, a.gR, warp) : T(0);
+  T u[kMaxAsmR / kAsmWarps];
+#pragma unroll
+  for (int i = 0; i < kMaxAsmR / kAsmWarps; ++i) {
+    const int c2 = warp + i * kAsmWarps;
+    u[i] = (c2 < rh) ? Uh[(int64_t)c2 * a.fs + jj] : T(0);
+  }
+  __syncthreads();  // Cc complete
+  T uc = T(0);
+#pragma unroll
+  for (int i = 0; i < kMaxAsmR / kAsmWarps; ++i) {
+    const int c2 = warp + i * kAsmWarps;
+    if (c2 < rh) uc = fma(u[i], Cc[c2], uc);
+  }
+  red[0][warp][lane] = x;
+  red[1][warp][lane] = uc;
+  red[2][warp][lane] = y;
+  __syncthreads();
+  if (warp != 0 || !valid) return;
+  T xs = T(0), us = T(0), ys = T(0);
+#pragma unroll
+  for (int w = 0; w < kAsmWarps; ++w) {
+    xs += red[0][w][lane];
+    us += red[1][w][lane];
+    ys += red[2][w][lane];
+  }
+  static_cast<T*>(a.Unew)[(int64_t)c * a.fs + j] = xs + us;
+  if (Yp) static_cast<T*>(a.Ynew)[(int64_t)c * a.fs + j] = ys;
 }
 
 template <typename T>
 cudaError_t launch_assemble(const AssembleParams& a, cudaStream_t s) {
-  const int64_t tot = (int64_t)a.n * (a.r_out > 0 ? a.r_out : a.r_h);
-  const unsigned grid = (unsigned)((tot + kThreads - 1) / kThreads);
-  const size_t smem = sizeof(T) * (size_t)a.r_h * a.r_h;  // <= 32 KB for r_h <= 64
-  const cudaError_t e = launch_pdl(assemble_kernel<T>, grid, kThreads, smem, s, a);
+  if (a.r_h > kMaxAsmR) return cudaErrorInvalidValue;
+  const int ro = a.r_out > 0 ? a.r_out : a.r_h;
+  const dim3 grid((unsigned)((a.n + 31) / 32), (unsigned)ro);
+  const cudaError_t e = launch_pdl(assemble_kernel<T>, grid, kThreads, 0, s, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
+
+constexpr int kChunk = 16;  // independent loads issued together
 
 // W = V K^T for the block-upper-triangular K of identity blocks (width r_in):
 // block b of W is the sum of blocks b .. nblk-1 of V, added from the last
 // block down in the element type.  One thread per (row, column in block).
 template <typename T>
-__global__ void suffix_sums_kernel(const T* V, T* W, int64_t fs, int n, int width, int r_in) {
+__global__ void suffix_sums_kernel(const T* __restrict__ V, T* __restrict__ W, int64_t fs, int n,
+                                   int width, int r_in) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n * r_in) return;
-  const int c = (int)(idx / n);
-  const int j = (int)(idx % n);
+  int c, j;
+  split_index(idx, n, c, j);
   const int nblk = width / r_in;
+  // the blocks are read in chunks of independent loads (V and W do not
+  // overlap), then summed from the last block down
   T acc = T(0);
-  for (int b = nblk - 1; b >= 0; --b) {
-    const int col = b * r_in + c;
-    acc += V[(int64_t)col * fs + j];
-    W[(int64_t)col * fs + j] = acc;
+  for (int b1 = nblk; b1 > 0; b1 -= kChunk) {
+    T v[kChunk];
+#pragma unroll
+    for (int i = 0; i < kChunk; ++i) {
+      const int b = b1 - 1 - i;
+      v[i] = (b >= 0) ? V[(int64_t)(b * r_in + c) * fs + j] : T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < kChunk; ++i) {
+      const int b = b1 - 1 - i;
+      if (b >= 0) {
+        acc += v[i];
+        W[(int64_t)(b * r_in + c) * fs + j] = acc;
+      }
+    }
   }
 }
 
@@ -279,8 +347,8 @@ template <typename T>
 __global__ void rm_to_cm_kernel(const T* src, int64_t ld, T* dst, int64_t fs, int rows, int cols) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)rows * cols) return;
-  const int c = (int)(idx / rows);
-  const int j = (int)(idx % rows);
+  int c, j;
+  split_index(idx, rows, c, j);
   dst[(int64_t)c * fs + j] = src[(int64_t)j * ld + c];
 }
 
@@ -298,8 +366,8 @@ template <typename T>
 __global__ void cm_to_rm_kernel(const T* src, int64_t fs, T* dst, int64_t ld, int rows, int cols) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)rows * cols) return;
-  const int j = (int)(idx / cols);
-  const int c = (int)(idx % cols);
+  int j, c;
+  split_index(idx, cols, j, c);
   dst[(int64_t)j * ld + c] = src[(int64_t)c * fs + j];
 }
 
@@ -330,8 +398,8 @@ __global__ void sum_partials_kernel(const T* part, int blocks, int64_t bs, int64
                                     int r, T* out, int64_t ocs) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n * r) return;
-  const int c = (int)(idx / n);
-  const int j = (int)(idx % n);
+  int c, j;
+  split_index(idx, n, c, j);
   double acc = 0.0;
   for (int b = 0; b < blocks; ++b) acc += (double)part[(int64_t)b * bs + (int64_t)c * cs + j];
   out[(int64_t)c * ocs + j] = (T)acc;
@@ -352,7 +420,8 @@ __global__ void axpy_rows_kernel(T* y, int64_t ldy, const T* x, int64_t ldx, T a
                                  int cols) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)rows * cols) return;
-  const int i = (int)(idx / cols), c = (int)(idx % cols);
+  int i, c;
+  split_index(idx, cols, i, c);
   y[(int64_t)i * ldy + c] += alpha * x[(int64_t)i * ldx + c];
 }
 
@@ -371,7 +440,8 @@ __global__ void scale_copy_kernel(T* y, int64_t ldy, const T* x, int64_t ldx, T 
                                   int cols) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)rows * cols) return;
-  const int i = (int)(idx / cols), c = (int)(idx % cols);
+  int i, c;
+  split_index(idx, cols, i, c);
   y[(int64_t)i * ldy + c] = alpha * x[(int64_t)i * ldx + c];
 }
 

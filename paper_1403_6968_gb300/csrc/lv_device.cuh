@@ -163,6 +163,20 @@ __device__ __forceinline__ void prefetch_tmap(const void* tmap) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmap)) : "memory");
 }
 
+// q = idx / d, r = idx % d for a flat element index: 32-bit arithmetic
+// whenever the index fits (a 64-bit division by a runtime divisor is a long
+// instruction sequence, which dominates the small element-wise kernels).
+__device__ __forceinline__ void split_index(int64_t idx, int d, int& q, int& r) {
+  if (idx <= 0x7fffffffll) {
+    const unsigned u = (unsigned)idx, ud = (unsigned)d;
+    q = (int)(u / ud);
+    r = (int)(u - (unsigned)q * ud);
+  } else {
+    q = (int)(idx / d);
+    r = (int)(idx - (int64_t)q * d);
+  }
+}
+
 // Programmatic dependent launch: a kernel launched with programmatic stream
 // serialisation may start while the kernel before it drains; griddep_wait()
 // blocks until that kernel has completed and its writes are visible, and

@@ -11,10 +11,10 @@ namespace lv {
 // Launch ``k`` with programmatic stream serialisation (the kernel calls
 // griddep_wait() before it reads what earlier kernels of the stream wrote).
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem,
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, unsigned block, size_t smem,
                        cudaStream_t s, Args... args) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
+  cfg.gridDim = grid;
   cfg.blockDim = dim3(block);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -31,6 +31,7 @@ constexpr int kBatch = 8;       // rows per pipeline stage = TMA box height = wa
 constexpr int kStages = 4;      // TMA ring depth (generic passes)
 constexpr int kStagesWs = 6;    // TMA ring depth of the decoupled-ring FP32 passes
 constexpr int kBoxBytes = 1024; // bytes per TMA box row (256 floats / 128 doubles)
+constexpr int kMaxAsmR = 64;    // widest factor block U_h of one assembly (= the widest Gram block)
 constexpr int kMaxFusedR = 8;   // widest factor block of the fused products pass
 constexpr int kMaxProductR = 16;  // widest factor block of an FP32 products-only pass
 constexpr int kMaxUpdateR = 32;   // widest factor block of one update pass (shared-memory

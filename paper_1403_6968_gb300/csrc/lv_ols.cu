@@ -22,7 +22,8 @@ __global__ void gather_rows_kernel(const T* X, int64_t ldx, const int64_t* rows,
                                    T* dst, int64_t ts, int64_t js) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)k * n) return;
-  const int t = (int)(idx / n), j = (int)(idx % n);
+  int t, j;
+  split_index(idx, n, t, j);
   dst[t * ts + j * js] = X[rows[t] * ldx + j];
 }
 
@@ -32,7 +33,8 @@ __global__ void scatter_rows_kernel(T* X, int64_t ldx, const int64_t* rows, int 
                                     const T* src, int64_t ts) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)k * n) return;
-  const int t = (int)(idx / n), j = (int)(idx % n);
+  int t, j;
+  split_index(idx, n, t, j);
   X[rows[t] * ldx + j] = src[t * ts + j];
 }
 
@@ -128,7 +130,8 @@ __global__ void xty_update_kernel(T* xty, int64_t ld, T* xtyc, int64_t fs, const
                                   int p, int k, const T* Yr) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n * p) return;
-  const int j = (int)(idx / p), c = (int)(idx % p);
+  int j, c;
+  split_index(idx, p, j, c);
   double acc = (double)xty[(int64_t)j * ld + c];
   for (int t = 0; t < k; ++t) {
     const double d = (double)U[(int64_t)t * fs + j] - (double)U[(int64_t)(k + t) * fs + j];
@@ -144,7 +147,8 @@ __global__ void to_double_kernel(const T* src, int64_t lds, double* dst, int64_t
                                  int cols) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)rows * cols) return;
-  const int i = (int)(idx / cols), j = (int)(idx % cols);
+  int i, j;
+  split_index(idx, cols, i, j);
   dst[(int64_t)i * ldd + j] = (double)src[(int64_t)i * lds + j];
 }
 
@@ -155,7 +159,8 @@ __global__ void sym_lower_to_full_kernel(const double* Lcm, int64_t ldl, int n, 
                                          int64_t ldd, double* full, int64_t ldf) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)n * n) return;
-  const int i = (int)(idx / n), j = (int)(idx % n);
+  int i, j;
+  split_index(idx, n, i, j);
   const int r = i > j ? i : j, c = i > j ? j : i;  // lower: row >= col
   const double v = Lcm[(int64_t)c * ldl + r];       // column-major (r, c)
   dst[(int64_t)i * ldd + j] = (T)v;
@@ -168,7 +173,8 @@ __global__ void from_double_kernel(const double* src, int64_t lds, T* dst, int64
                                    int cols, T* cm, int64_t cfs) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)rows * cols) return;
-  const int i = (int)(idx / cols), j = (int)(idx % cols);
+  int i, j;
+  split_index(idx, cols, i, j);
   const T v = (T)src[(int64_t)i * lds + j];
   dst[(int64_t)i * ldd + j] = v;
   if (cm) cm[(int64_t)j * cfs + i] = v;
