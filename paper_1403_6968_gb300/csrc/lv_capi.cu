@@ -107,6 +107,10 @@ struct linview_program {
   float* tcA = nullptr;
   float* tcB = nullptr;
   CUtensorMap tmA, tmB;
+  // a second set for the sums updates on the side stream (wide sums only)
+  float* tcA2 = nullptr;
+  float* tcB2 = nullptr;
+  CUtensorMap tmA2, tmB2;
   int64_t fs = 0;
   int Rcap = 0;
   // partial sums of the view passes
@@ -161,6 +165,11 @@ struct linview_program {
   // replayed on a program-owned stream joined to the caller's stream
   bool use_graphs = true;
   cudaStream_t gstream = nullptr;
+  // side stream of a propagation: the sums-view updates run there, forked
+  // from the main stream after the factors they read and joined at the end
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_fork_ev = nullptr, side_join_ev = nullptr;
+  bool side_pending = false;
   cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   struct Rec {
     cudaEvent_t e0, e1;
@@ -349,16 +358,20 @@ static linview_status run_fused(linview_program* p, const View& v, int mode, int
 
 template <typename T>
 static linview_status run_update(linview_program* p, const View& v, const T* Uu, const T* Wu,
-                                 int r, cudaStream_t s, int suffix_rin = 0) {
+                                 int r, cudaStream_t s, int suffix_rin = 0, int tcset = 0) {
   constexpr int MU = kMaxUpdateR;
+  // split-factor scratch of the tensor-core pass (set 1: the side stream's)
+  float* tA = tcset ? p->tcA2 : p->tcA;
+  float* tB = tcset ? p->tcB2 : p->tcB;
+  const CUtensorMap& mA = tcset ? p->tmA2 : p->tmA;
+  const CUtensorMap& mB = tcset ? p->tmB2 : p->tmB;
   for (int c0 = 0; c0 < r; c0 += MU) {
     const int w = (r - c0 < MU) ? (r - c0) : MU;
     if constexpr (sizeof(T) == 4) {
       // blocks wider than the CUDA-core pass sustains go to the tensor cores
-      if (p->tcA && w > kMaxProductR && suffix_rin == 0) {
+      if (tA && w > kMaxProductR && suffix_rin == 0) {
         ProfScope ps(p, s, 2.0 * (double)v.rows * (double)v.rows * sizeof(T), 2);
-        LV_CUDA(launch_tc_update(v.tmap_tc, p->tmA, p->tmB, static_cast<float*>(v.ptr), v.ld,
-                                 p->tcA, p->tcB,
+        LV_CUDA(launch_tc_update(v.tmap_tc, mA, mB, static_cast<float*>(v.ptr), v.ld, tA, tB,
                                  reinterpret_cast<const float*>(Uu) + (int64_t)c0 * p->fs,
                                  reinterpret_cast<const float*>(Wu) + (int64_t)c0 * p->fs, p->fs,
                                  (int)v.rows, w, p->sms, p->status, s));
@@ -639,7 +652,7 @@ static int64_t powers_device_bytes(const linview_program_desc& d, int sms) {
   const int64_t half = Rcap / 2 > 0 ? Rcap / 2 : 1;
   b += (int64_t)g.gC * half * fs * elem + (int64_t)g.gR * half * fs * elem;
   b += 2 * n * d.r_max * elem;
-  if (powers_uses_tc(d)) b += tc_split_floats(n) * 4;
+  if (powers_uses_tc(d)) b += tc_split_floats(n) * 4 * (powers_wide_sums(d) ? 2 : 1);
   return b;
 }
 
@@ -690,6 +703,15 @@ static linview_status powers_create(linview_program* p, const void* const* input
     if (!make_tmap_sw128(&p->tmA, p->tcA, 64, n, 64, 128) ||
         !make_tmap_sw128(&p->tmB, p->tcB, 64, n, 64, 64))
       return fail(LINVIEW_EDEVICE, "cuTensorMapEncodeTiled failed for the split factors");
+    if (wide_sums) {  // the sums updates on the side stream have their own
+      void* tc2 = nullptr;
+      LV_TRY(dalloc(p, (size_t)tc_split_floats(n) * sizeof(float), &tc2));
+      p->tcA2 = static_cast<float*>(tc2);
+      p->tcB2 = p->tcA2 + tc_split_floats(n) / 2;
+      if (!make_tmap_sw128(&p->tmA2, p->tcA2, 64, n, 64, 128) ||
+          !make_tmap_sw128(&p->tmB2, p->tcB2, 64, n, 64, 64))
+        return fail(LINVIEW_EDEVICE, "cuTensorMapEncodeTiled failed for the split factors");
+    }
   }
   return powers_reeval(p, s);
 }
@@ -698,14 +720,50 @@ static linview_status powers_create(linview_program* p, const void* const* input
 // update pass takes the suffix block sums of V_h itself when the factor fits
 // one pass, else they are formed first (one thread per row).
 template <typename T>
-static linview_status sums_update(linview_program* p, View& sv, const T* U, const T* Vh, int rh,
-                                  int r, cudaStream_t s) {
+static linview_status sums_update_on(linview_program* p, View& sv, const T* U, const T* Vh, int rh,
+                                     int r, cudaStream_t s, int tcset) {
   if (!p->Wsum) return run_update<T>(p, sv, U, Vh, rh, s, r);
   {
     ProfScope ps(p, s, 0.0);
     LV_CUDA(launch_suffix_sums<T>(Vh, static_cast<T*>(p->Wsum), p->fs, (int)p->d.n, rh, r, s));
   }
-  return run_update<T>(p, sv, U, static_cast<const T*>(p->Wsum), rh, s, 0);
+  return run_update<T>(p, sv, U, static_cast<const T*>(p->Wsum), rh, s, 0, tcset);
+}
+
+// A sums view is written by nothing else during a propagation and its update
+// reads only factor columns that are final once enqueued, so it runs on the
+// program's side stream, forked from s here (everything enqueued on s so far
+// happens before it) and joined by side_join at the end of the propagation.
+// The view passes of the two streams then fill each other's ramps and tails,
+// and an HBM-bound sums pass can use the bandwidth a compute-bound level pass
+// leaves idle.  (Inside a graph capture the fork and join become edges.)
+static linview_status side_fork(linview_program* p, cudaStream_t s, cudaStream_t* out) {
+  if (!p->side) {
+    LV_CUDA(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+    LV_CUDA(cudaEventCreateWithFlags(&p->side_fork_ev, cudaEventDisableTiming));
+    LV_CUDA(cudaEventCreateWithFlags(&p->side_join_ev, cudaEventDisableTiming));
+  }
+  LV_CUDA(cudaEventRecord(p->side_fork_ev, s));
+  LV_CUDA(cudaStreamWaitEvent(p->side, p->side_fork_ev, 0));
+  p->side_pending = true;
+  *out = p->side;
+  return LINVIEW_OK;
+}
+
+static linview_status side_join(linview_program* p, cudaStream_t s) {
+  if (!p->side_pending) return LINVIEW_OK;
+  p->side_pending = false;
+  LV_CUDA(cudaEventRecord(p->side_join_ev, p->side));
+  LV_CUDA(cudaStreamWaitEvent(s, p->side_join_ev, 0));
+  return LINVIEW_OK;
+}
+
+template <typename T>
+static linview_status sums_update(linview_program* p, View& sv, const T* U, const T* Vh, int rh,
+                                  int r, cudaStream_t s) {
+  cudaStream_t side = nullptr;
+  LV_TRY(side_fork(p, s, &side));
+  return sums_update_on<T>(p, sv, U, Vh, rh, r, side, 1);
 }
 
 // Exponential-model levels l = 0 .. nlev-1 (h = 2^l, Appendix A): the level
@@ -728,10 +786,11 @@ static linview_status exp_levels(linview_program* p, int r, int nlev, bool sums,
       ProfScope ps(p, s, 0.0);
       LV_CUDA((launch_gram<T>(Vh, U, fs, n, rh, p->Cpart, p->ticket, p->C, p->status, s)));
     }
+    // sums: S'_h += U_h (V_h K_h^T)^T, the suffix block sums taken in the pass
+    // (side stream, concurrent with the level pass)
+    if (sums && l >= 1) LV_TRY(sums_update<T>(p, sview(p, l), U, Vh, rh, r, s));
     LV_TRY(run_products_update<T>(p, pview(p, l), rh, U, Vh, U, Vh, s,
                                   fused ? p->Cpart : nullptr));
-    // sums: S'_h += U_h (V_h K_h^T)^T, the suffix block sums taken in the pass
-    if (sums && l >= 1) LV_TRY(sums_update<T>(p, sview(p, l), U, Vh, rh, r, s));
     AssembleParams a{};
     a.n = n;
     a.r_h = rh;
@@ -817,7 +876,7 @@ static linview_status krylov_levels(linview_program* p, int bw, int nsteps, int 
 }
 
 template <typename T>
-static linview_status powers_propagate(linview_program* p, int r, cudaStream_t s) {
+static linview_status powers_propagate_levels(linview_program* p, int r, cudaStream_t s) {
   T* U = static_cast<T*>(p->Uar);
   T* V = static_cast<T*>(p->Var);
   const int k = p->d.k;
@@ -841,9 +900,16 @@ static linview_status powers_propagate(linview_program* p, int r, cudaStream_t s
   LV_TRY(exp_levels<T>(p, r, p->L, sums, s));
   const int rk = r << p->L;
   T* Vk = V + (int64_t)(p->Rcap - rk) * p->fs;
-  LV_TRY(run_update<T>(p, pview(p, p->L), U, Vk, rk, s));
   if (sums) LV_TRY(sums_update<T>(p, sview(p, p->L), U, Vk, rk, r, s));
+  LV_TRY(run_update<T>(p, pview(p, p->L), U, Vk, rk, s));
   return LINVIEW_OK;
+}
+
+template <typename T>
+static linview_status powers_propagate(linview_program* p, int r, cudaStream_t s) {
+  const linview_status st = powers_propagate_levels<T>(p, r, s);
+  const linview_status sj = side_join(p, s);  // also after an error, to close the fork
+  return st != LINVIEW_OK ? st : sj;
 }
 
 // ---------------------------------------------------------------------------
@@ -1294,6 +1360,9 @@ void linview_destroy(linview_program* p) {
   if (p->gev_in) cudaEventDestroy(p->gev_in);
   if (p->gev_out) cudaEventDestroy(p->gev_out);
   if (p->gstream) cudaStreamDestroy(p->gstream);
+  if (p->side_fork_ev) cudaEventDestroy(p->side_fork_ev);
+  if (p->side_join_ev) cudaEventDestroy(p->side_join_ev);
+  if (p->side) cudaStreamDestroy(p->side);
   if (p->blas) cublasDestroy(p->blas);
   if (p->solver) cusolverDnDestroy(p->solver);
   delete p;
