@@ -761,6 +761,8 @@ static linview_status side_join(linview_program* p, cudaStream_t s) {
 template <typename T>
 static linview_status sums_update(linview_program* p, View& sv, const T* U, const T* Vh, int rh,
                                   int r, cudaStream_t s) {
+  // profiling times each view pass alone: no overlap
+  if (p->prof) return sums_update_on<T>(p, sv, U, Vh, rh, r, s, 0);
   cudaStream_t side = nullptr;
   LV_TRY(side_fork(p, s, &side));
   return sums_update_on<T>(p, sv, U, Vh, rh, r, side, 1);
