@@ -230,6 +230,21 @@ __device__ __forceinline__ A strided_sum(const T* src, int64_t stride, int count
   return acc;
 }
 
+// sum over all i < count of src[i * stride], in increasing i (chunks of 8
+// independent loads)
+template <typename T>
+__device__ __forceinline__ T strided_sum_all(const T* src, int64_t stride, int count) {
+  T acc = T(0);
+  for (int i0 = 0; i0 < count; i0 += 8) {
+    T v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = (i0 + i < count) ? src[(int64_t)(i0 + i) * stride] : T(0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc += v[i];
+  }
+  return acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) assemble_kernel(const AssembleParams a) {
   __shared__ T Cc[kMaxAsmR];                 // column c of C_h (rounded to T)
@@ -290,12 +305,63 @@ __global__ void __launch_bounds__(kThreads) assemble_kernel(const AssembleParams
   if (Yp) static_cast<T*>(a.Ynew)[(int64_t)c * a.fs + j] = ys;
 }
 
+// The same assembly for wide blocks (r_out >= 8): there are enough outputs
+// to fill the GPU with one thread per (j, c), which then sums all partials
+// itself (CTA = 256 rows of one column; the C_h column is summed once per
+// CTA).  Same fixed orders as above within a thread's sums.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) assemble_wide_kernel(const AssembleParams a) {
+  __shared__ T Cc[kMaxAsmR];
+  griddep_wait();
+  griddep_launch_dependents();
+  const int rh = a.r_h;
+  const int c = blockIdx.y;
+  const int j = blockIdx.x * kThreads + threadIdx.x;
+  const bool valid = j < a.n;
+  const int jj = valid ? j : 0;
+  const T* Xp = static_cast<const T*>(a.Xpart);
+  const T* Yp = static_cast<const T*>(a.Ypart);
+  const T* Uh = static_cast<const T*>(a.Uh);
+  const int ne = rh * rh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c2b = warp * 4; c2b < rh; c2b += kThreads / 8) {
+    const int c2 = c2b + (lane >> 3);
+    double sum = (c2 < rh) ? strided_sum<double, double>(a.C + (int64_t)c2 * rh + c, ne, a.nC,
+                                                         lane & 7)
+                           : 0.0;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((lane & 7) == 0 && c2 < rh) Cc[c2] = (T)sum;
+  }
+  T x = strided_sum_all<T>(Xp + (int64_t)c * a.part_cs + jj, a.xp_s, a.gC);
+  T y = Yp ? strided_sum_all<T>(Yp + (int64_t)c * a.part_cs + jj, a.yp_q, a.gR) : T(0);
+  __syncthreads();
+  if (!valid) return;
+  T uc = T(0);
+  for (int c0 = 0; c0 < rh; c0 += 8) {
+    T u[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) u[i] = (c0 + i < rh) ? Uh[(int64_t)(c0 + i) * a.fs + j] : T(0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (c0 + i < rh) uc = fma(u[i], Cc[c0 + i], uc);
+  }
+  static_cast<T*>(a.Unew)[(int64_t)c * a.fs + j] = x + uc;
+  if (Yp) static_cast<T*>(a.Ynew)[(int64_t)c * a.fs + j] = y;
+}
+
 template <typename T>
 cudaError_t launch_assemble(const AssembleParams& a, cudaStream_t s) {
   if (a.r_h > kMaxAsmR) return cudaErrorInvalidValue;
   const int ro = a.r_out > 0 ? a.r_out : a.r_h;
-  const dim3 grid((unsigned)((a.n + 31) / 32), (unsigned)ro);
-  const cudaError_t e = launch_pdl(assemble_kernel<T>, grid, kThreads, 0, s, a);
+  cudaError_t e;
+  if (ro >= 8) {
+    const dim3 grid((unsigned)((a.n + kThreads - 1) / kThreads), (unsigned)ro);
+    e = launch_pdl(assemble_wide_kernel<T>, grid, kThreads, 0, s, a);
+  } else {
+    const dim3 grid((unsigned)((a.n + 31) / 32), (unsigned)ro);
+    e = launch_pdl(assemble_kernel<T>, grid, kThreads, 0, s, a);
+  }
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
