@@ -597,8 +597,17 @@ def iteration_p_sweep(args, seed=0, k=16, steps=6, ps=(1, 16, 128, 1024)):
             row[f"reeval_{mode}_ms"] = _event_ms(lambda j: prog.reeval(), 2)
         prog.sync()
         prog.close()
+        # hybrid strategy (dense dT_i, one n x n x p product with A per step)
+        hyb = Program("iteration", [a, b, t0], k=k, r_max=1, strategy="hybrid")
+        for i, v in ups[:2]:
+            hyb.apply_row_delta(i, v)
+        row["hybrid_ms"] = _event_ms(lambda j: hyb.apply_row_delta(*ups[2 + j]), steps)
+        hyb.sync()
+        hyb.close()
         rows.append(row)
-    return {"n": n, "k": k, "B": "0", "update": "rank-1 row of A", "rows": rows}
+    return {"n": n, "k": k, "B": "0", "update": "rank-1 row of A", "rows": rows,
+            "note": "incremental = factored deltas (Krylov reuse); hybrid = dense deltas "
+                    "D_i = A D_{i-1} + rank-1 term; re-evaluation = k products A T_i"}
 
 
 def gd_regression(seed=0, n=4096, m=4096, p=1024, k=16, steps=6):

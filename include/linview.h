@@ -93,7 +93,17 @@ typedef struct {
   int32_t reeval_mode;       /* linview_reeval_mode used by linview_reeval and by correction */
   int32_t model;             /* POWER/POWER_SUM: linview_model; other kinds: 0 */
   int32_t skip;              /* LINVIEW_MODEL_SKIP: the step s; otherwise 0 */
+  int32_t strategy;          /* ITERATION: linview_strategy; other kinds: 0 */
 } linview_program_desc;
+
+/* Evaluation strategy of an iteration program's updates (Section 4.3). */
+typedef enum {
+  LINVIEW_STRATEGY_FACTORED = 0, /* incremental: dT_i = U_i V_i^T in factored form (App. B,
+                                    linear model with Krylov reuse) */
+  LINVIEW_STRATEGY_HYBRID = 1    /* hybrid: dT_i kept as one dense n x p matrix D_i,
+                                    D_i = A D_{i-1} + (rank-r term), one n x n x p product
+                                    with A per step (Sec. 4.3; App. B, hybrid linear) */
+} linview_strategy;
 
 /* Iterative model of a power program (Section 3.3; Appendix A). */
 typedef enum {

@@ -23,6 +23,7 @@ F64, F32 = 0, 1
 REEVAL_DEFAULT, REEVAL_FP32, REEVAL_TF32, REEVAL_BF16X9, REEVAL_FP64 = range(5)
 # linview_model
 MODEL_EXP, MODEL_LINEAR, MODEL_SKIP = 0, 1, 2
+STRATEGY_FACTORED, STRATEGY_HYBRID = 0, 1
 
 
 class ProgramDesc(C.Structure):
@@ -38,6 +39,7 @@ class ProgramDesc(C.Structure):
         ("reeval_mode", C.c_int32),
         ("model", C.c_int32),
         ("skip", C.c_int32),
+        ("strategy", C.c_int32),
     ]
 
 

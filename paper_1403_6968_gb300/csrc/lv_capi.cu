@@ -134,6 +134,8 @@ struct linview_program {
   void* V1 = nullptr;   // input right factor, column-major n x r_max
   void* Mr = nullptr;   // T_i^T V blocks in reverse order, p x k r_max
   void* Gpanel = nullptr;
+  void* Dh = nullptr;   // hybrid strategy: dense deltas D_{i-1}, D_i (2 x n x p, ld ldD)
+  int64_t ldD = 0;
   int64_t ldG = 0;
   // power adjoint work
   void* Gw0 = nullptr;
@@ -968,6 +970,10 @@ static linview_status iter_create(linview_program* p, const void* const* inputs,
   p->yp_q = p->xp_s;
   LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart));
   LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart));
+  if (p->d.strategy == LINVIEW_STRATEGY_HYBRID) {
+    p->ldD = rup(pp, 64);
+    LV_TRY(dalloc(p, (size_t)2 * n * p->ldD * p->elem, &p->Dh));
+  }
   return iter_reeval(p, s);
 }
 
@@ -1075,6 +1081,56 @@ static linview_status iter_propagate_b(linview_program* p, int rb, cudaStream_t 
   // B += U_b V_b^T (column-major B^T, p x n)
   LV_TRY(gemm_cm(p, false, true, pp, n, rb, 1.0, M, pp, K, fs, 1.0, p->Bm, p->ldB, s,
                  exact_mode(p)));
+  return LINVIEW_OK;
+}
+
+// Hybrid strategy (Sec. 4.3; App. B, hybrid linear model): the change of
+// every iteration is kept as one dense n x p matrix D_i instead of factors.
+// For dA = U V^T (U in Krylov block K_0, V in V1; A is the old matrix until
+// the last step):
+//   D_1 = U (V^T T_0),   D_i = A D_{i-1} + U (V^T (T_{i-1} + D_{i-1})),
+// the paper's three terms U V^T T_{i-1} + A D_{i-1} + U V^T D_{i-1} with the
+// two products by V^T taken once on the refreshed T'_{i-1} = T_{i-1} +
+// D_{i-1}; then A += U V^T.  For dB = U_b V_b^T (U_b in K_0, V_b in the first
+// block of M; A unchanged):  D_1 = U_b V_b^T,  D_i = A D_{i-1} + U_b V_b^T,
+// and B += U_b V_b^T.  Each step is one n x n x p product with A (cuBLAS,
+// IEEE arithmetic), the rank-r term and T_i += D_i.  Column-major views:
+// T_i^T, D_i^T are p x n (ld ldT, ldD), A's row-major storage is A^T.
+template <typename T>
+static linview_status iter_propagate_hybrid(linview_program* p, int r, bool b_update,
+                                            cudaStream_t s) {
+  const int64_t n = p->d.n, pp = p->d.p;
+  const int k = p->d.k;
+  const int64_t fs = p->fs;
+  const T* K = static_cast<const T*>(p->Kar);
+  const T* V1 = static_cast<const T*>(p->V1);
+  T* W = static_cast<T*>(p->Mr);  // p x r: (V^T T'_{i-1})^T, or V_b for dB
+  char* Tp = static_cast<char*>(p->Tpanel);
+  T* D[2] = {static_cast<T*>(p->Dh), static_cast<T*>(p->Dh) + n * p->ldD};
+  const View& a = p->views[0];
+  const int mode = exact_mode(p);
+  for (int i = 1; i <= k; ++i) {
+    T* dc = D[i & 1];
+    const T* dp = D[(i - 1) & 1];
+    T* ti = reinterpret_cast<T*>(Tp + (size_t)i * pp * sizeof(T));
+    const T* tprev = reinterpret_cast<const T*>(Tp + (size_t)(i - 1) * pp * sizeof(T));
+    if (!b_update)  // W^T = T'_{i-1}^T V (T'_{i-1} is already refreshed)
+      LV_TRY(gemm_cm(p, false, false, pp, r, n, 1.0, tprev, p->ldT, V1, fs, 0.0, W, pp, s, mode));
+    double beta = 0.0;
+    if (i >= 2) {  // D_i^T = D_{i-1}^T A^T
+      LV_TRY(gemm_cm(p, false, false, pp, n, n, 1.0, dp, p->ldD, a.ptr, a.ld, 0.0, dc, p->ldD, s,
+                     mode));
+      beta = 1.0;
+    }
+    // D_i^T += W U^T  (the rank-r term)
+    LV_TRY(gemm_cm(p, false, true, pp, n, r, 1.0, W, pp, K, fs, beta, dc, p->ldD, s, mode));
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_axpy_rows<T>(ti, p->ldT, dc, p->ldD, T(1), (int)n, (int)pp, s));
+  }
+  if (b_update)  // B += U_b V_b^T (column-major B^T, p x n)
+    LV_TRY(gemm_cm(p, false, true, pp, n, r, 1.0, W, pp, K, fs, 1.0, p->Bm, p->ldB, s, mode));
+  else
+    LV_TRY(run_update<T>(p, a, K, V1, r, s));
   return LINVIEW_OK;
 }
 
@@ -1290,6 +1346,10 @@ linview_status linview_create_program(const linview_program_desc* desc, const vo
       !(desc->model == LINVIEW_MODEL_SKIP &&
         (desc->kind == LINVIEW_POWER || desc->kind == LINVIEW_POWER_SUM)))
     return fail(LINVIEW_EINVAL, "model %d is not available for kind %d", desc->model, desc->kind);
+  if (desc->strategy != LINVIEW_STRATEGY_FACTORED &&
+      !(desc->strategy == LINVIEW_STRATEGY_HYBRID && desc->kind == LINVIEW_ITERATION))
+    return fail(LINVIEW_EINVAL, "strategy %d is not available for kind %d", desc->strategy,
+                desc->kind);
   int ninputs = 0;
   switch (desc->kind) {
     case LINVIEW_POWER:
@@ -1502,6 +1562,12 @@ constexpr int kKeyB = 1024;
 // The launches of one update after its factors are in place, on stream s.
 static linview_status propagate_eager(linview_program* p, int key, cudaStream_t s) {
   if (p->d.kind == LINVIEW_ITERATION) {
+    if (p->d.strategy == LINVIEW_STRATEGY_HYBRID) {
+      const bool bu = key >= kKeyB;
+      const int r = bu ? key - kKeyB : key;
+      return p->elem == 4 ? iter_propagate_hybrid<float>(p, r, bu, s)
+                          : iter_propagate_hybrid<double>(p, r, bu, s);
+    }
     if (key >= kKeyB)
       return p->elem == 4 ? iter_propagate_b<float>(p, key - kKeyB, s)
                           : iter_propagate_b<double>(p, key - kKeyB, s);

@@ -16,6 +16,7 @@ from ._lib import LinviewError  # noqa: F401
 
 KINDS = {"power": L.POWER, "power_sum": L.POWER_SUM, "iteration": L.ITERATION, "ols": L.OLS}
 MODELS = {"exp": L.MODEL_EXP, "linear": L.MODEL_LINEAR, "skip": L.MODEL_SKIP}
+STRATEGIES = {"factored": L.STRATEGY_FACTORED, "hybrid": L.STRATEGY_HYBRID}
 REEVAL = {"default": L.REEVAL_DEFAULT, "fp32": L.REEVAL_FP32, "tf32": L.REEVAL_TF32,
           "bf16x9": L.REEVAL_BF16X9, "fp64": L.REEVAL_FP64}
 
@@ -75,7 +76,8 @@ class Program:
     """
 
     def __init__(self, kind, inputs, k, r_max=1, precision="f32", p=0, m=0,
-                 correction_period=0, reeval_mode="default", model="exp", skip=0, stream=None):
+                 correction_period=0, reeval_mode="default", model="exp", skip=0,
+                 strategy="factored", stream=None):
         self.lib = L.load()
         self.precision = L.F64 if precision in ("f64", "fp64", L.F64) else L.F32
         self.np_dtype = _dtype_of(self.precision)
@@ -92,6 +94,7 @@ class Program:
         d.reeval_mode = REEVAL[reeval_mode] if isinstance(reeval_mode, str) else int(reeval_mode)
         d.model = MODELS[model] if isinstance(model, str) else int(model)
         d.skip = int(skip)
+        d.strategy = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
         on_dev = {o.on_device for o in ops}
         if len(on_dev) != 1:
             raise ValueError("inputs must all be on the device or all on the host")

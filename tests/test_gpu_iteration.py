@@ -168,3 +168,67 @@ def test_iteration_b_updates(prec, n, p, k, rb):
     got_b = prog.read_view(k + 1).cpu().numpy().astype(np.float64)
     assert rel_frob(got_b, bcur) <= tol
     prog.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,p,k,r", [(300, 5, 16, 2), (1, 1, 1, 1), (777, 64, 16, 2),
+                                     (1030, 3, 4, 4), (513, 1, 16, 1)])
+def test_iteration_hybrid_strategy(prec, n, p, k, r):
+    """Hybrid strategy (Sec. 4.3: dense dT_i, one n x n x p product per step)
+    against the oracle's hybrid evaluation (the paper's three-term rule) and
+    its re-evaluation, on updates to A (factored and row) and to B."""
+    dt = np.float64 if prec == "f64" else np.float32
+    a, b, t0 = li.iteration_inputs(n, p, seed=n + 7, dtype=dt)
+    prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=k, r_max=r, precision=prec,
+                 strategy="hybrid")
+    hyb = oi.HybridIteration(a, b, t0, k)
+    acur, bcur = a.astype(np.float64), b.astype(np.float64)
+    tol = 1e-10 if prec == "f64" else 1e-4
+    g = np.random.default_rng(n)
+    for step, (u, v) in enumerate(li.lowrank_update_stream(n, r, 3, seed=n + 8, dtype=dt)):
+        prog.apply_delta(_dev(u), _dev(v))
+        hyb.apply(u, v)
+        acur += u.astype(np.float64) @ v.astype(np.float64).T
+        if step == 1:  # a row update e_i v^T of A and a rank-1 update of B
+            i = int(g.integers(n))
+            w = (g.standard_normal(n) * 0.01).astype(dt)
+            prog.apply_row_delta(i, _dev(w))
+            e = np.zeros((n, 1))
+            e[i, 0] = 1.0
+            hyb.apply(e, w.astype(np.float64).reshape(n, 1))
+            acur[i] += w.astype(np.float64)
+            ub = g.standard_normal((n, 1)).astype(dt)
+            vb = g.standard_normal((p, 1)).astype(dt)
+            prog.apply_delta(_dev(ub), _dev(vb), input_id=1)
+            bcur += ub.astype(np.float64) @ vb.astype(np.float64).T
+            hyb = oi.HybridIteration(acur, bcur, t0, k)  # B changed: restart the oracle
+    prog.sync()
+    ref = oi.reeval(acur, bcur, t0.astype(np.float64), k)
+    for i in range(1, k + 1):
+        got = prog.read_view_host(i)
+        assert rel_frob(got, ref[i]) <= tol, i
+        assert rel_frob(got, hyb.t[i]) <= tol, i
+    assert rel_frob(prog.read_view_host(0), acur) <= tol
+    assert rel_frob(prog.read_view_host(k + 1), bcur) <= tol
+
+
+def test_iteration_hybrid_equals_factored_fp64():
+    """Both strategies maintain the same views (FP64, to rounding)."""
+    n, p, k, r = 400, 9, 8, 2
+    a, b, t0 = li.iteration_inputs(n, p, seed=31)
+    progs = [_prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=k, r_max=r, precision="f64",
+                   strategy=s) for s in ("factored", "hybrid")]
+    for u, v in li.lowrank_update_stream(n, r, 4, seed=32):
+        for pr in progs:
+            pr.apply_delta(_dev(u), _dev(v))
+    for pr in progs:
+        pr.sync()
+    for i in range(1, k + 1):
+        assert rel_frob(progs[1].read_view_host(i), progs[0].read_view_host(i)) <= 1e-11, i
+
+
+def test_strategy_validation():
+    from paper_1403_6968_gb300 import LinviewError
+    a = li.power_matrix(64, seed=1)
+    with pytest.raises(LinviewError):
+        _prog("power", [_dev(a)], k=4, precision="f64", strategy="hybrid")
