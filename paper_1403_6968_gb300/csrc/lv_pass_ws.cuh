@@ -73,9 +73,10 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
 // One row of the in-place rank-R update p_k + sum_c u_c W(col_k, c) for the
 // COLS columns of a thread.  R >= 2: the staged row u (16-byte aligned) is
 // read once and the FMAs are paired over factor columns, (u_c, u_c+1) *
-// (W(col_k, c), W(col_k, c+1)), accumulated from (p_k, 0) in increasing c
-// and finished as even + odd: a fixed order, so results are reproducible.
-// R = 1: one FMA per entry, two columns per packed FMA.
+// (W(col_k, c), W(col_k, c+1)), summed in increasing c from the first packed
+// product (no accumulator to set up) and finished as p_k + (even + odd): a
+// fixed order, so results are reproducible.  R = 1: one FMA per entry, two
+// columns per packed FMA.
 template <int R, int COLS>
 __device__ __forceinline__ void rank_update_row(const float* u, const float (&pv)[COLS],
                                                 const float2 (&wp)[COLS][R >= 2 ? R / 2 : 1],
@@ -103,10 +104,10 @@ __device__ __forceinline__ void rank_update_row(const float* u, const float (&pv
     }
 #pragma unroll
     for (int k = 0; k < COLS; ++k) {
-      float2 acc = make_float2(pv[k], 0.f);
+      float2 acc = __fmul2_rn(uu[0], wp[k][0]);
 #pragma unroll
-      for (int c2 = 0; c2 < R / 2; ++c2) acc = __ffma2_rn(uu[c2], wp[k][c2], acc);
-      out[k] = acc.x + acc.y;
+      for (int c2 = 1; c2 < R / 2; ++c2) acc = __ffma2_rn(uu[c2], wp[k][c2], acc);
+      out[k] = pv[k] + (acc.x + acc.y);
     }
   }
 }
@@ -300,6 +301,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int box = (tc * COLS) / BOXC;
   const int inbox = (tc * COLS) % BOXC;
   const bool vec_ok = (col0 + COLS <= n);
+  // the same for the whole warp (a vote, so the compiler sees a uniform
+  // branch); only the warps at the right edge of the view take the other path
+  const bool warp_vec = __all_sync(0xffffffffu, vec_ok);
   // factor core C = V^T U over this CTA's rows (FP64).  The CTA owns the
   // entries e = s + i * gC; each entry is split over LPE threads, thread li
   // taking batch rows li, li + LPE, ..., so every thread does at most
@@ -323,6 +327,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const uint32_t parity = (uint32_t)((b / S) & 1);
     const int row0 = rb + b * kBatch;
     const int nb = min(kBatch, re - row0);
+    const bool full_batch = nb == kBatch;  // the same for the whole CTA
     if (wait_or_abort(&full[st], parity, abort_flag, p.status)) {
       waited = b + 1;
       const T* Ust = Us + st * kBatch * R;
@@ -388,14 +393,14 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
           }
           if constexpr (DO_U) {
-            if (upd && (TSTORE || j < nb)) {
+            if (upd && (TSTORE || full_batch || j < nb)) {
               float o[COLS];
               rank_update_row<R, COLS>(Ust + j * R, pvs, wp, o);
               if constexpr (TSTORE) {
                 *reinterpret_cast<float4*>(sp + j * BOXC) = make_float4(o[0], o[1], o[2], o[3]);
               } else {
                 T* dst = P + (int64_t)(row0 + j) * p.ldp + col0;
-                if (vec_ok) {
+                if (warp_vec || vec_ok) {
                   *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
                 } else {
 #pragma unroll
