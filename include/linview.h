@@ -210,6 +210,19 @@ linview_status linview_reeval(linview_program* prog, void* stream);
 linview_status linview_set_reeval_mode(linview_program* prog, int reeval_mode);
 
 /* Synchronise ``stream`` and return (and clear) the latched device status. */
+/*
+ * Diagnostic of the bounded device waits (failure detection without a fault).
+ * Runs one kernel whose single wait is on an mbarrier that nothing ever
+ * completes, with a limit of limit_ns (1e6 .. 1e10).  The wait gives up after
+ * the limit and latches the timeout bit exactly as a view pass does when a
+ * copy never lands (every pass waits with limit 2 s); the device context stays
+ * usable.  Returns LINVIEW_ETIMEOUT, the expected outcome, with *waited_ns the
+ * time the wait took (>= limit_ns); LINVIEW_OK would mean the barrier
+ * completed (never expected); EINVAL for a bad limit or null pointer,
+ * EDEVICE on a CUDA error.  Synchronises ``stream``.
+ */
+linview_status linview_check_bounded_wait(int64_t limit_ns, void* stream, int64_t* waited_ns);
+
 linview_status linview_sync(linview_program* prog, void* stream);
 
 void linview_destroy(linview_program* prog);

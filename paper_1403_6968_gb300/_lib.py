@@ -101,6 +101,7 @@ _SIGS = [
     ("linview_reeval", _I, [_P, _P]),
     ("linview_set_reeval_mode", _I, [_P, _I]),
     ("linview_sync", _I, [_P, _P]),
+    ("linview_check_bounded_wait", _I, [_I64, _P, C.POINTER(_I64)]),
     ("linview_destroy", None, [_P]),
     ("linview_last_error", C.c_char_p, []),
     ("linview_adjoint_iteration", _I, [_P, _P, _I64, _P, _I64, _P]),

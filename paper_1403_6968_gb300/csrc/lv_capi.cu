@@ -1804,6 +1804,30 @@ linview_status linview_sync(linview_program* p, void* stream) {
   return LINVIEW_OK;
 }
 
+linview_status linview_check_bounded_wait(int64_t limit_ns, void* stream, int64_t* waited_ns) {
+  if (!waited_ns) return fail(LINVIEW_EINVAL, "null argument");
+  *waited_ns = 0;
+  if (limit_ns < 1000000 || limit_ns > 10000000000ll)
+    return fail(LINVIEW_EINVAL, "limit_ns must be in [1e6, 1e10]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* buf = nullptr;
+  LV_CUDA(cudaMalloc(&buf, 16));
+  unsigned* status = static_cast<unsigned*>(buf);
+  auto* waited = reinterpret_cast<unsigned long long*>(static_cast<char*>(buf) + 8);
+  cudaError_t e = cudaMemsetAsync(buf, 0, 16, s);
+  if (e == cudaSuccess) e = launch_bounded_wait_probe((uint64_t)limit_ns, status, waited, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  unsigned st = 0;
+  unsigned long long w = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&w, waited, sizeof(w), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(LINVIEW_EDEVICE, "bounded-wait probe: %s", cudaGetErrorString(e));
+  *waited_ns = (int64_t)w;
+  if (st & kStatusTimeout) return fail(LINVIEW_ETIMEOUT, "the probe's bounded wait expired");
+  return LINVIEW_OK;
+}
+
 // ---------------------------------------------------------------- adjoints
 // Reverse pass of T_i = A T_{i-1} + B, i = 1..k, from the seed G_k = dL/dT_k
 // (Gk, or 2 T_k when Gk is NULL: L = ||T_k||_F^2).

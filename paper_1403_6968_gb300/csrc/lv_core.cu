@@ -521,6 +521,28 @@ cudaError_t launch_scale_copy(T* y, int64_t ldy, const T* x, int64_t ldx, T alph
   return cudaGetLastError();
 }
 
+// Diagnostic of the bounded waits: one thread waits on an mbarrier that no
+// thread or copy ever completes; the wait gives up after limit_ns, latches
+// the timeout bit in *status exactly as a view pass does, and reports how
+// long it waited.  Nothing faults and the context stays usable.
+__global__ void bounded_wait_probe_kernel(uint64_t limit_ns, unsigned* status,
+                                          unsigned long long* waited_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    const uint64_t t0 = global_ns();
+    const bool done = mbar_wait_bounded(&bar, 0, status, limit_ns);
+    *waited_ns = done ? 0ull : (unsigned long long)(global_ns() - t0);
+  }
+}
+
+cudaError_t launch_bounded_wait_probe(uint64_t limit_ns, unsigned* status,
+                                      unsigned long long* waited_ns, cudaStream_t s) {
+  bounded_wait_probe_kernel<<<1, 32, 0, s>>>(limit_ns, status, waited_ns);
+  return cudaGetLastError();
+}
+
 #define LV_INST(T)                                                                              \
   template cudaError_t launch_gram<T>(const T*, const T*, int64_t, int, int, double*, unsigned*, \
                                       double*, unsigned*, cudaStream_t);                        \

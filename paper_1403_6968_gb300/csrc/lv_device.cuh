@@ -84,15 +84,16 @@ __device__ __forceinline__ uint64_t global_ns() {
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 // Bounded wait on phase ``parity``; returns false (and latches a timeout in
-// *status) if the barrier did not complete within kWaitLimitNs (or
-// kMaxPolls polls, whichever comes first).
+// *status) if the barrier did not complete within limit_ns (kWaitLimitNs for
+// the passes) or kMaxPolls polls, whichever comes first.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  unsigned* status) {
+                                                  unsigned* status,
+                                                  uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (long long i = 0; i < kMaxPolls; ++i) {
     if (mbar_try_wait_suspend(bar, parity)) return true;
-    if ((i & 255) == 255 && global_ns() - t0 > kWaitLimitNs) break;
+    if ((i & 255) == 255 && global_ns() - t0 > limit_ns) break;
   }
   if (status) atomicOr(status, kStatusTimeout);
   return false;

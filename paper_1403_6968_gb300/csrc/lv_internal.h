@@ -131,6 +131,10 @@ struct AssembleParams {
 template <typename T>
 cudaError_t launch_assemble(const AssembleParams& a, cudaStream_t s);
 
+// One bounded wait that always expires (diagnostic; see lv_core.cu).
+cudaError_t launch_bounded_wait_probe(uint64_t limit_ns, unsigned* status,
+                                      unsigned long long* waited_ns, cudaStream_t s);
+
 // Suffix block sums: W[:, a-block] = sum_{b >= a} V[:, b-block] (blocks of r_in).
 template <typename T>
 cudaError_t launch_suffix_sums(const T* V, T* W, int64_t fs, int n, int width, int r_in,

@@ -247,6 +247,19 @@ def level_pass(P, U, V, X=None, Y=None, do_update=True, stream=None):
            1 if do_update else 0, _stream_ptr(stream))
 
 
+def check_bounded_wait(limit_ns=20_000_000, stream=None):
+    """Run the library's bounded-wait diagnostic (a device wait on a barrier
+    that never completes, limit ``limit_ns``).  Returns the time the wait took
+    in ns once it gave up and latched its timeout, the expected outcome;
+    raises LinviewError on anything else."""
+    w = C.c_int64()
+    st = L.load().linview_check_bounded_wait(int(limit_ns), _stream_ptr(stream), C.byref(w))
+    if st != L.ETIMEOUT:
+        L.check(st, "linview_check_bounded_wait")
+        raise LinviewError(st, "linview_check_bounded_wait", "the wait did not expire")
+    return w.value
+
+
 def level_pass_noalloc(P, U, V, X=None, Y=None, do_update=True, stream=None):
     """``level_pass`` for callers that may not allocate device memory: the
     partial sums use the library's built-in 16 MiB device array instead of
