@@ -10,6 +10,22 @@ Section 4.3 and Appendix B of the paper.  A is n x n, B and T_i are n x p.
   and every += applied last;
 * hybrid, linear model (Appendix B): dT_1 = dA T_0,
       dT_i = U V^T T_{i-1} + A dT_{i-1} + U V^T dT_{i-1}   (dense n x p deltas);
+* exponential model (Section 3.3, Appendix B) for k a power of two: views
+  T_h, h = 1, 2, 4, ..., k, with the auxiliary views P_h = A^h and
+  S_h = I + A + ... + A^{h-1} (h = 1, 2, ..., k/2):
+      T_1 = A T_0 + B,  T_2h = P_h T_h + S_h B,
+      P_2h = P_h P_h,   S_2h = S_h + P_h S_h   (S_1 = I);
+  incremental for dA = u v^T, with dP_h = Q_h R_h^T, dS_h = Z_h W_h^T and
+  dT_h = U_h V_h^T from the old views (Appendix B, exponential model):
+      U_1 = u, V_1 = T_0^T v;
+      U_2h = [Q_h, P_h U_h + Q_h (R_h^T U_h), Z_h],
+      V_2h = [T_h^T R_h, V_h, B^T W_h];
+  Q_h, R_h as in Appendix A (powers), and Z_h, W_h from
+  S_2h = S_h + P_h S_h:  dS_2h = dS_h + dP_h S_h + P_h dS_h + dP_h dS_h, i.e.
+      Z_2h = [Q_h, Z_h + P_h Z_h + Q_h (R_h^T Z_h)],  W_2h = [S_h^T R_h, W_h],
+  with Z_1, W_1 empty (dS_1 = 0).  (The paper prints "dW_{i/2}" for W_{i/2}
+  and gives the width of U_i as 2i - 1, an upper bound: with dS_1 = 0 the
+  widths are 1, 2, 5, 12, 27 for i = 1, 2, 4, 8, 16 at rank 1.)
 * adjoint of L = ||T_k||_F^2: G_k = 2 T_k, G_i = A^T G_{i+1},
       dL/dB = sum_{i=1..k} G_i,   dL/dA = sum_{i=1..k} G_i T_{i-1}^T,
       dL/dT_0 = A^T G_1.
@@ -113,3 +129,65 @@ def adjoint(a, b, t0, k: int):
         db += g[i]
     dt0 = a.T @ g[1]
     return da, db, dt0
+
+
+def exp_reeval(a, b, t0, k: int):
+    """Exponential model: ({h: T_h} for h = 1, 2, 4, ..., k, {h: P_h},
+    {h: S_h}) with P_h, S_h for h = 1, 2, ..., k/2 (k a power of two)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    n = a.shape[0]
+    P, S = {1: a.copy()}, {1: np.eye(n)}
+    h = 1
+    while 2 * h <= k // 2:
+        P[2 * h] = P[h] @ P[h]
+        S[2 * h] = S[h] + P[h] @ S[h]
+        h *= 2
+    T = {1: a @ np.asarray(t0, dtype=np.float64) + b}
+    h = 1
+    while 2 * h <= k:
+        T[2 * h] = P[h] @ T[h] + S[h] @ b
+        h *= 2
+    return T, P, S
+
+
+class ExpIncrementalIteration:
+    """Views T_1, T_2, T_4, ..., T_k (with P_h, S_h, h <= k/2) maintained
+    under dA = u v^T (Appendix B, exponential model)."""
+
+    def __init__(self, a, b, t0, k: int):
+        if k < 1 or k & (k - 1):
+            raise ValueError("k must be a power of two")
+        self.k = k
+        self.a = np.asarray(a, dtype=np.float64).copy()
+        self.b = np.asarray(b, dtype=np.float64).copy()
+        self.t0 = np.asarray(t0, dtype=np.float64).copy()
+        self.t, self.p, self.s = exp_reeval(self.a, self.b, self.t0, k)
+
+    def apply(self, u, v):
+        """Returns the factors {h: U_h}, {h: V_h} of dT_h."""
+        n = self.a.shape[0]
+        u = np.asarray(u, dtype=np.float64).reshape(n, -1)
+        v = np.asarray(v, dtype=np.float64).reshape(n, -1)
+        Q, R = {1: u}, {1: v}
+        Z, W = {1: np.zeros((n, 0))}, {1: np.zeros((n, 0))}
+        U, V = {1: u}, {1: self.t0.T @ v}
+        h = 1
+        while 2 * h <= self.k:
+            P, S, T = self.p[h], self.s[h], self.t[h]
+            U[2 * h] = np.hstack([Q[h], P @ U[h] + Q[h] @ (R[h].T @ U[h]), Z[h]])
+            V[2 * h] = np.hstack([T.T @ R[h], V[h], self.b.T @ W[h]])
+            if 2 * h <= self.k // 2:
+                Q[2 * h] = np.hstack([Q[h], P @ Q[h] + Q[h] @ (R[h].T @ Q[h])])
+                R[2 * h] = np.hstack([P.T @ R[h], R[h]])
+                Z[2 * h] = np.hstack([Q[h], Z[h] + P @ Z[h] + Q[h] @ (R[h].T @ Z[h])])
+                W[2 * h] = np.hstack([S.T @ R[h], W[h]])
+            h *= 2
+        self.a += u @ v.T
+        for h in self.p:
+            self.p[h] += Q[h] @ R[h].T
+            self.s[h] += Z[h] @ W[h].T
+        for h in self.t:
+            self.t[h] += U[h] @ V[h].T
+        return U, V
+

@@ -175,3 +175,47 @@ def test_ols_inputs_are_ill_conditioned():
     assert len(cols) == round(0.1 * n)
     kappa = np.linalg.cond(x.T @ x)
     assert 5e3 < kappa < 1e5
+
+
+# ------------------------------------------------- iteration, exponential model
+@pytest.mark.parametrize("n,p,k", [(9, 3, 16), (6, 1, 2), (7, 4, 8)])
+def test_exp_reeval_matches_linear_at_powers_of_two(n, p, k):
+    """T_2h = P_h T_h + S_h B (S_h = I + ... + A^{h-1}) against the linear
+    recurrence T_i = A T_{i-1} + B, and the A = lam I closed form
+    T_h = lam^h T_0 + (1 + lam + ... + lam^{h-1}) B."""
+    a, b, t0 = li.iteration_inputs(n, p, seed=3 * n)
+    T, P, S = oi.exp_reeval(a, b, t0, k)
+    lin = oi.reeval(a, b, t0, k)
+    assert sorted(T) == [1 << j for j in range(k.bit_length())]
+    for h in T:
+        assert rel_frob(T[h], lin[h]) < 1e-12
+    for h in P:
+        assert rel_frob(P[h], np.linalg.matrix_power(a, h)) < 1e-12
+        assert rel_frob(S[h], sum(np.linalg.matrix_power(a, i) for i in range(h))) < 1e-12
+    lam = 0.7
+    T, _, _ = oi.exp_reeval(lam * np.eye(n), b, t0, k)
+    for h in T:
+        assert rel_frob(T[h], lam ** h * t0 + sum(lam ** i for i in range(h)) * b) < 1e-13
+
+
+@pytest.mark.parametrize("n,p,k,r", [(8, 3, 16, 1), (12, 5, 8, 2), (6, 1, 2, 1), (5, 2, 1, 1)])
+def test_exp_incremental_matches_reeval(n, p, k, r):
+    """The printed exponential rule (old P_h, S_h, T_h; every += last) keeps
+    T_h, P_h and S_h equal to their re-evaluation on the updated A; the width
+    of U_h follows the recurrence with dS_1 = 0: r * (1, 2, 5, 12, 27) for
+    h = 1, 2, 4, 8, 16 (the paper's 2i - 1 is an upper bound)."""
+    a, b, t0 = li.iteration_inputs(n, p, seed=n + 1)
+    inc = oi.ExpIncrementalIteration(a, b, t0, k)
+    acur = a.copy()
+    widths = {1: 1, 2: 2, 4: 5, 8: 12, 16: 27}
+    for (u, v) in li.lowrank_update_stream(n, r, 3, seed=n + 2, sigma=0.2):
+        U, V = inc.apply(u, v)
+        acur += u @ v.T
+        T, P, S = oi.exp_reeval(acur, b, t0, k)
+        for h in T:
+            assert rel_frob(inc.t[h], T[h]) < 1e-12, h
+            assert U[h].shape == (n, r * widths[h]) and V[h].shape == (p, r * widths[h])
+            assert U[h].shape[1] <= r * (2 * h - 1) or h == 1
+        for h in P:
+            assert rel_frob(inc.p[h], P[h]) < 1e-12
+            assert rel_frob(inc.s[h], S[h]) < 1e-12
