@@ -86,12 +86,15 @@ typedef struct {
   int64_t p;                 /* ITERATION: columns of B and T_i; OLS: columns of Y; otherwise 0 */
   int32_t k;                 /* POWER/POWER_SUM: highest power (a power of two >= 1 in
                                 the exponential model, >= 2 in the linear model);
-                                ITERATION: number of steps >= 1; OLS: largest row block */
+                                ITERATION: number of steps >= 1 (a power of two >= 2 in the
+                                exponential model); OLS: largest row block */
   int32_t r_max;             /* largest rank accepted by linview_apply_delta (>= 1) */
   int32_t correction_period; /* >0: re-evaluate every this many updates (residual
                                 correction of accumulated rounding); 0 = never */
   int32_t reeval_mode;       /* linview_reeval_mode used by linview_reeval and by correction */
-  int32_t model;             /* POWER/POWER_SUM: linview_model; other kinds: 0 */
+  int32_t model;             /* POWER/POWER_SUM: linview_model; ITERATION:
+                                LINVIEW_MODEL_LINEAR (views T_1..T_k) or LINVIEW_MODEL_EXP
+                                (views T_1, T_2, T_4, .., T_k; Appendix B); OLS: 0 */
   int32_t skip;              /* LINVIEW_MODEL_SKIP: the step s; otherwise 0 */
   int32_t strategy;          /* ITERATION: linview_strategy; other kinds: 0 */
 } linview_program_desc;
@@ -105,7 +108,8 @@ typedef enum {
                                     with A per step (Sec. 4.3; App. B, hybrid linear) */
 } linview_strategy;
 
-/* Iterative model of a power program (Section 3.3; Appendix A). */
+/* Iterative model of a power program (Section 3.3; Appendix A), or of an
+ * iteration program (LINEAR or EXP; Appendix B). */
 typedef enum {
   LINVIEW_MODEL_EXP = 0,     /* P_{2h} = P_h P_h: views A, A^2, A^4, ..., A^k */
   LINVIEW_MODEL_LINEAR = 1,  /* P_i = A P_{i-1}: views A, A^2, A^3, ..., A^k; r_max * k <= 64 */
@@ -174,7 +178,12 @@ linview_status linview_apply_row_block(linview_program* prog, int64_t kr, const 
  *   skip-s model (LINVIEW_MODEL_SKIP): j = P_{2^j} (j = 0..log2 s), then
  *              log2(s) + i - 1 = P_{is} (i = 2..k/s); with N such power views,
  *              POWER_SUM adds N + j - 1 = S'_h for the power view j >= 1
- *   ITERATION: 0 = A, i = T_i (i = 1..k), k + 1 = B, k + 2 = T_0
+ *   ITERATION, linear model: 0 = A, i = T_i (i = 1..k), k + 1 = B, k + 2 = T_0
+ *   ITERATION, exponential model (k = 2^L): 0 = A, 1 + j = T_{2^j} (j = 0..L),
+ *              L + 2 = B, L + 3 = T_0, then the auxiliary views L + 3 + j =
+ *              P_{2^j} (j = 1..L-1) and 2L + 2 + j = S'_{2^j} (j = 1..L-1), with
+ *              T_2h = P_h T_h + (I + S'_h - P_h) B; updates to B and the adjoints
+ *              are built for the linear model only (EUNSUPPORTED here)
  *   OLS:       0 = W (n x n), 1 = beta (n x p), 2 = X^T Y (n x p), 3 = X (m x n)
  */
 int linview_num_views(const linview_program* prog);

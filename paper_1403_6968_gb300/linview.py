@@ -76,7 +76,7 @@ class Program:
     """
 
     def __init__(self, kind, inputs, k, r_max=1, precision="f32", p=0, m=0,
-                 correction_period=0, reeval_mode="default", model="exp", skip=0,
+                 correction_period=0, reeval_mode="default", model=None, skip=0,
                  strategy="factored", stream=None):
         self.lib = L.load()
         self.precision = L.F64 if precision in ("f64", "fp64", L.F64) else L.F32
@@ -92,6 +92,8 @@ class Program:
         d.r_max = int(r_max)
         d.correction_period = int(correction_period)
         d.reeval_mode = REEVAL[reeval_mode] if isinstance(reeval_mode, str) else int(reeval_mode)
+        if model is None:  # iteration programs default to the linear model (views T_1..T_k)
+            model = "linear" if d.kind == L.ITERATION else "exp"
         d.model = MODELS[model] if isinstance(model, str) else int(model)
         d.skip = int(skip)
         d.strategy = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)

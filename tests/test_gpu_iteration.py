@@ -232,3 +232,63 @@ def test_strategy_validation():
     a = li.power_matrix(64, seed=1)
     with pytest.raises(LinviewError):
         _prog("power", [_dev(a)], k=4, precision="f64", strategy="hybrid")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n,p,k,r", [(300, 5, 16, 2), (1030, 3, 4, 1), (513, 64, 8, 2),
+                                     (64, 1, 2, 1), (777, 16, 16, 1)])
+def test_iteration_exp_model(prec, n, p, k, r):
+    """Exponential model of the general form (App. B): views T_1, T_2, .., T_k
+    (and the auxiliary P_h, S'_h) after factored and row updates of A, against
+    the oracle's re-evaluation T_2h = P_h T_h + S_h B."""
+    dt = np.float64 if prec == "f64" else np.float32
+    a, b, t0 = li.iteration_inputs(n, p, seed=n + 11, dtype=dt)
+    prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=k, r_max=r, precision=prec,
+                 model="exp")
+    L = k.bit_length() - 1
+    acur = a.astype(np.float64)
+    b64, t064 = b.astype(np.float64), t0.astype(np.float64)
+    tol = 1e-10 if prec == "f64" else 1e-4
+
+    def check():
+        prog.sync()
+        T, P, S = oi.exp_reeval(acur, b64, t064, k)
+        for j in range(L + 1):
+            assert rel_frob(prog.read_view_host(1 + j), T[1 << j]) <= tol, j
+        assert rel_frob(prog.read_view_host(0), acur) <= tol
+        for j in range(1, L):
+            h = 1 << j
+            assert rel_frob(prog.read_view_host(L + 3 + j), P[h]) <= tol, h
+            sprime = S[h] - np.eye(n) + P[h]   # S'_h = A + .. + A^h
+            assert rel_frob(prog.read_view_host(2 * L + 2 + j), sprime) <= tol, h
+
+    check()
+    g = np.random.default_rng(n)
+    for step, (u, v) in enumerate(li.lowrank_update_stream(n, r, 3, seed=n + 12, dtype=dt)):
+        prog.apply_delta(_dev(u), _dev(v))
+        acur += u.astype(np.float64) @ v.astype(np.float64).T
+        if step == 1:
+            i = int(g.integers(n))
+            w = (g.standard_normal(n) * 0.01).astype(dt)
+            prog.apply_row_delta(i, _dev(w))
+            acur[i] += w.astype(np.float64)
+    check()
+
+
+def test_iteration_exp_model_errors():
+    from paper_1403_6968_gb300 import LinviewError, _lib
+    n, p = 64, 3
+    a, b, t0 = li.iteration_inputs(n, p, seed=5)
+    with pytest.raises(LinviewError) as e:
+        _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=6, precision="f64", model="exp")
+    assert e.value.status == _lib.EINVAL
+    with pytest.raises(LinviewError):
+        _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=4, precision="f64", model="exp",
+              strategy="hybrid")
+    prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=4, precision="f64", model="exp")
+    with pytest.raises(LinviewError) as e:
+        prog.apply_delta(_dev(np.ones((n, 1))), _dev(np.ones((p, 1))), input_id=1)
+    assert e.value.status == _lib.EUNSUPPORTED
+    with pytest.raises(LinviewError) as e:
+        prog.adjoint_iteration()
+    assert e.value.status == _lib.EUNSUPPORTED
