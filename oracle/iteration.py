@@ -26,6 +26,12 @@ Section 4.3 and Appendix B of the paper.  A is n x n, B and T_i are n x p.
   with Z_1, W_1 empty (dS_1 = 0).  (The paper prints "dW_{i/2}" for W_{i/2}
   and gives the width of U_i as 2i - 1, an upper bound: with dS_1 = 0 the
   widths are 1, 2, 5, 12, 27 for i = 1, 2, 4, 8, 16 at rank 1.)
+* skip-s model (Section 3.3, Appendix B), s a power of two, k a multiple of s,
+  k >= 2s: T_1, T_2, .., T_s by the exponential model, then
+      T_i = P_s T_{i-s} + S_s B   (i = 2s, 3s, .., k),
+  and incrementally, from the old views,
+      U_i = [Q_s, P_s U_{i-s} + Q_s (R_s^T U_{i-s}), Z_s],
+      V_i = [T_{i-s}^T R_s, V_{i-s}, B^T W_s];
 * adjoint of L = ||T_k||_F^2: G_k = 2 T_k, G_i = A^T G_{i+1},
       dL/dB = sum_{i=1..k} G_i,   dL/dA = sum_{i=1..k} G_i T_{i-1}^T,
       dL/dT_0 = A^T G_1.
@@ -189,5 +195,64 @@ class ExpIncrementalIteration:
             self.s[h] += Z[h] @ W[h].T
         for h in self.t:
             self.t[h] += U[h] @ V[h].T
+        return U, V
+
+
+def skip_reeval(a, b, t0, k: int, s: int):
+    """Skip-s model: ({i: T_i} for i = 1, 2, 4, .., s, 2s, 3s, .., k,
+    {h: P_h}, {h: S_h}) with P_h, S_h for h = 1, 2, .., s."""
+    if s < 1 or s & (s - 1) or k % s or k < 2 * s:
+        raise ValueError("s a power of two, k a multiple of s, k >= 2s")
+    T, P, S = exp_reeval(a, b, t0, s)
+    h = max(P)
+    if 2 * h == s:  # exp_reeval stops at s/2: P_s, S_s by one more squaring
+        P[s] = P[h] @ P[h]
+        S[s] = S[h] + P[h] @ S[h]
+    b = np.asarray(b, dtype=np.float64)
+    for i in range(2 * s, k + 1, s):
+        T[i] = P[s] @ T[i - s] + S[s] @ b
+    return T, P, S
+
+
+class SkipIncrementalIteration:
+    """Views T_1, T_2, .., T_s (powers of two), T_2s, .., T_k with P_h, S_h
+    (h = 1, 2, .., s) maintained under dA = u v^T (Appendix B, skip model)."""
+
+    def __init__(self, a, b, t0, k: int, s: int):
+        self.k, self.s = k, s
+        self.a = np.asarray(a, dtype=np.float64).copy()
+        self.b = np.asarray(b, dtype=np.float64).copy()
+        self.t0 = np.asarray(t0, dtype=np.float64).copy()
+        self.t, self.p, self.sv = skip_reeval(self.a, self.b, self.t0, k, s)
+
+    def apply(self, u, v):
+        """Returns the factors {i: U_i}, {i: V_i} of dT_i."""
+        n = self.a.shape[0]
+        u = np.asarray(u, dtype=np.float64).reshape(n, -1)
+        v = np.asarray(v, dtype=np.float64).reshape(n, -1)
+        Q, R = {1: u}, {1: v}
+        Z, W = {1: np.zeros((n, 0))}, {1: np.zeros((n, 0))}
+        U, V = {1: u}, {1: self.t0.T @ v}
+        h = 1
+        while 2 * h <= self.s:  # exponential part: factors up to h = s
+            P, S, T = self.p[h], self.sv[h], self.t[h]
+            U[2 * h] = np.hstack([Q[h], P @ U[h] + Q[h] @ (R[h].T @ U[h]), Z[h]])
+            V[2 * h] = np.hstack([T.T @ R[h], V[h], self.b.T @ W[h]])
+            Q[2 * h] = np.hstack([Q[h], P @ Q[h] + Q[h] @ (R[h].T @ Q[h])])
+            R[2 * h] = np.hstack([P.T @ R[h], R[h]])
+            Z[2 * h] = np.hstack([Q[h], Z[h] + P @ Z[h] + Q[h] @ (R[h].T @ Z[h])])
+            W[2 * h] = np.hstack([S.T @ R[h], W[h]])
+            h *= 2
+        s = self.s
+        Ps = self.p[s]
+        for i in range(2 * s, self.k + 1, s):
+            U[i] = np.hstack([Q[s], Ps @ U[i - s] + Q[s] @ (R[s].T @ U[i - s]), Z[s]])
+            V[i] = np.hstack([self.t[i - s].T @ R[s], V[i - s], self.b.T @ W[s]])
+        self.a += u @ v.T
+        for h in self.p:
+            self.p[h] += Q[h] @ R[h].T
+            self.sv[h] += Z[h] @ W[h].T
+        for i in self.t:
+            self.t[i] += U[i] @ V[i].T
         return U, V
 

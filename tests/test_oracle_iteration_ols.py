@@ -219,3 +219,56 @@ def test_exp_incremental_matches_reeval(n, p, k, r):
         for h in P:
             assert rel_frob(inc.p[h], P[h]) < 1e-12
             assert rel_frob(inc.s[h], S[h]) < 1e-12
+
+
+# ------------------------------------------------------ iteration, skip model
+@pytest.mark.parametrize("n,p,k,s,r", [(8, 3, 16, 4, 1), (9, 2, 8, 2, 2), (6, 1, 4, 1, 1),
+                                       (7, 3, 16, 8, 1), (5, 2, 6, 2, 1)])
+def test_skip_incremental_matches_reeval(n, p, k, s, r):
+    """Skip-s model: re-evaluation T_i = P_s T_{i-s} + S_s B against the linear
+    recurrence, and the printed incremental rule against it after updates."""
+    a, b, t0 = li.iteration_inputs(n, p, seed=n + 5)
+    inc = oi.SkipIncrementalIteration(a, b, t0, k, s)
+    expect = sorted({1 << j for j in range(s.bit_length())} | set(range(2 * s, k + 1, s)))
+    assert sorted(inc.t) == expect
+    acur = a.copy()
+    for (u, v) in li.lowrank_update_stream(n, r, 3, seed=n + 6, sigma=0.2):
+        U, V = inc.apply(u, v)
+        acur += u @ v.T
+        T, P, S = oi.skip_reeval(acur, b, t0, k, s)
+        lin = oi.reeval(acur, b, t0, k)
+        for i in T:
+            assert rel_frob(T[i], lin[i]) < 1e-12, i
+            assert rel_frob(inc.t[i], T[i]) < 1e-12, i
+        for h in P:
+            assert rel_frob(inc.p[h], P[h]) < 1e-12
+            assert rel_frob(inc.sv[h], S[h]) < 1e-12
+
+
+def test_skip_special_cases_and_widths():
+    """s = k/2 is the exponential model and s = 1 the linear model (same views,
+    same factor widths); at s = 4, k = 16 the widths follow the recurrence
+    w_i = r s + w_{i-s} + (width of Z_s): r * (1, 2, 5, 12, 19, 26)."""
+    n, p = 7, 2
+    a, b, t0 = li.iteration_inputs(n, p, seed=41)
+    (u, v), = li.lowrank_update_stream(n, 1, 1, seed=42, sigma=0.2)
+    sk = oi.SkipIncrementalIteration(a, b, t0, 16, 8)
+    ex = oi.ExpIncrementalIteration(a, b, t0, 16)
+    Us, _ = sk.apply(u, v)
+    Ue, _ = ex.apply(u, v)
+    assert sorted(Us) == sorted(Ue)
+    for i in Us:
+        assert Us[i].shape == Ue[i].shape
+        assert rel_frob(sk.t[i], ex.t[i]) < 1e-13
+    sk1 = oi.SkipIncrementalIteration(a, b, t0, 5, 1)
+    lin = oi.IncrementalIteration(a, b, t0, 5)
+    U1, _ = sk1.apply(u, v)
+    Ul, _ = lin.apply(u, v)
+    for i in range(1, 6):
+        assert U1[i].shape == Ul[i].shape
+        assert rel_frob(sk1.t[i], lin.t[i]) < 1e-13
+    sk4 = oi.SkipIncrementalIteration(a, b, t0, 16, 4)
+    U4, _ = sk4.apply(u, v)
+    assert {i: U4[i].shape[1] for i in U4} == {1: 1, 2: 2, 4: 5, 8: 12, 12: 19, 16: 26}
+    with pytest.raises(ValueError):
+        oi.SkipIncrementalIteration(a, b, t0, 6, 4)
