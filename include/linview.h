@@ -87,14 +87,16 @@ typedef struct {
   int32_t k;                 /* POWER/POWER_SUM: highest power (a power of two >= 1 in
                                 the exponential model, >= 2 in the linear model);
                                 ITERATION: number of steps >= 1 (a power of two >= 2 in the
-                                exponential model); OLS: largest row block */
+                                exponential model, a multiple of s >= 2s in the skip
+                                model); OLS: largest row block */
   int32_t r_max;             /* largest rank accepted by linview_apply_delta (>= 1) */
   int32_t correction_period; /* >0: re-evaluate every this many updates (residual
                                 correction of accumulated rounding); 0 = never */
   int32_t reeval_mode;       /* linview_reeval_mode used by linview_reeval and by correction */
   int32_t model;             /* POWER/POWER_SUM: linview_model; ITERATION:
-                                LINVIEW_MODEL_LINEAR (views T_1..T_k) or LINVIEW_MODEL_EXP
-                                (views T_1, T_2, T_4, .., T_k; Appendix B); OLS: 0 */
+                                LINVIEW_MODEL_LINEAR (views T_1..T_k), LINVIEW_MODEL_EXP
+                                (views T_1, T_2, T_4, .., T_k) or LINVIEW_MODEL_SKIP
+                                (T_1, T_2, .., T_s, T_2s, .., T_k; Appendix B); OLS: 0 */
   int32_t skip;              /* LINVIEW_MODEL_SKIP: the step s; otherwise 0 */
   int32_t strategy;          /* ITERATION: linview_strategy; other kinds: 0 */
 } linview_program_desc;
@@ -179,11 +181,14 @@ linview_status linview_apply_row_block(linview_program* prog, int64_t kr, const 
  *              log2(s) + i - 1 = P_{is} (i = 2..k/s); with N such power views,
  *              POWER_SUM adds N + j - 1 = S'_h for the power view j >= 1
  *   ITERATION, linear model: 0 = A, i = T_i (i = 1..k), k + 1 = B, k + 2 = T_0
- *   ITERATION, exponential model (k = 2^L): 0 = A, 1 + j = T_{2^j} (j = 0..L),
- *              L + 2 = B, L + 3 = T_0, then the auxiliary views L + 3 + j =
- *              P_{2^j} (j = 1..L-1) and 2L + 2 + j = S'_{2^j} (j = 1..L-1), with
- *              T_2h = P_h T_h + (I + S'_h - P_h) B; updates to B and the adjoints
- *              are built for the linear model only (EUNSUPPORTED here)
+ *   ITERATION, skip-s model (exponential model: s = k/2): with the T views
+ *              T_1, T_2, T_4, .., T_s, T_2s, T_3s, .., T_k (NT = log2(s) + k/s of
+ *              them): 0 = A, 1 + j = the j-th T view (j = 0..NT-1), NT + 1 = B,
+ *              NT + 2 = T_0, then the auxiliary views NT + 2 + l = P_{2^l} and
+ *              NT + 2 + log2(s) + l = S'_{2^l} (l = 1..log2 s), with
+ *              T_2h = P_h T_h + S_h B (h < s), T_i = P_s T_{i-s} + S_s B (i > s),
+ *              S_h = I + S'_h - P_h; updates to B and the adjoints are built
+ *              for the linear model only (EUNSUPPORTED here)
  *   OLS:       0 = W (n x n), 1 = beta (n x p), 2 = X^T Y (n x p), 3 = X (m x n)
  */
 int linview_num_views(const linview_program* prog);

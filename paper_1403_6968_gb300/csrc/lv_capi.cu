@@ -142,6 +142,7 @@ struct linview_program {
   void* Yar[2] = {nullptr, nullptr};  // p x r_max k, column-major (ld p)
   void* What = nullptr;               // n x Rcap, column-major (fs)
   void* XtV = nullptr;                // (r_max k) x Rcap
+  int ie_s = 0, ie_Ls = 0, ie_NT = 0;  // skip step s (k/2 for EXP), log2 s, number of T views
   int64_t ldG = 0;
   // power adjoint work
   void* Gw0 = nullptr;
@@ -943,15 +944,17 @@ static linview_status iter_reeval(linview_program* p, cudaStream_t s) {
   return LINVIEW_OK;
 }
 
+// exponential or skip model of an iteration program
 static bool iter_exp(const linview_program* p) {
-  return p->d.kind == LINVIEW_ITERATION && p->d.model == LINVIEW_MODEL_EXP;
+  return p->d.kind == LINVIEW_ITERATION &&
+         (p->d.model == LINVIEW_MODEL_EXP || p->d.model == LINVIEW_MODEL_SKIP);
 }
-static linview_status iter_exp_create(linview_program* p, const void* const* inputs,
-                                      const int64_t* lds, int on_dev, cudaStream_t s);
+static linview_status iter_sk_create(linview_program* p, const void* const* inputs,
+                                     const int64_t* lds, int on_dev, cudaStream_t s);
 
 static linview_status iter_create(linview_program* p, const void* const* inputs,
                                   const int64_t* lds, int on_dev, cudaStream_t s) {
-  if (iter_exp(p)) return iter_exp_create(p, inputs, lds, on_dev, s);
+  if (iter_exp(p)) return iter_sk_create(p, inputs, lds, on_dev, s);
   const int64_t n = p->d.n, pp = p->d.p;
   const int k = p->d.k;
   if (pp < 1) return fail(LINVIEW_EINVAL, "p must be >= 1");
@@ -1148,24 +1151,57 @@ static linview_status iter_propagate_hybrid(linview_program* p, int r, bool b_up
 }
 
 // ---------------------------------------------------------------------------
-// general form, exponential model (Section 3.3; Appendix B), k = 2^L:
-// views T_h for h = 1, 2, 4, ..., k with the auxiliary views P_h = A^h and
-// S'_h = A + ... + A^h (h = 2, ..., k/2; P_1 = S'_1 = A):
-//   T_1 = A T_0 + B,  T_2h = P_h T_h + S_h B,  S_h = I + S'_h - P_h.
-// View ids: 0 = A, 1 + j = T_{2^j} (j = 0..L), L + 2 = B, L + 3 = T_0, then
-// P_2 .. P_{k/2}, then S'_2 .. S'_{k/2}.
+// general form, exponential and skip-s models (Section 3.3; Appendix B).  The
+// skip-s model (s a power of two, k a multiple of s, k >= 2s) keeps
+//   T_1, T_2, T_4, .., T_s  by the exponential rule T_2h = P_h T_h + S_h B,
+//   T_2s, T_3s, .., T_k     by T_i = P_s T_{i-s} + S_s B,
+// with the auxiliary views P_h = A^h and S'_h = A + .. + A^h (h = 2, .., s;
+// P_1 = S'_1 = A) and S_h = I + S'_h - P_h; the exponential model is the
+// skip model with s = k/2 (T_1, T_2, .., T_k at powers of two).
+// View ids: 0 = A, 1 + j = the j-th T view (j = 0..NT-1, NT = log2(s) + k/s),
+// NT + 1 = B, NT + 2 = T_0, NT + 2 + l = P_{2^l} (l = 1..log2 s),
+// NT + 2 + log2(s) + l = S'_{2^l} (l = 1..log2 s).
 // ---------------------------------------------------------------------------
 static View& ie_T(linview_program* p, int j) { return p->views[1 + j]; }
-static View& ie_P(linview_program* p, int l) { return l == 0 ? p->views[0] : p->views[p->L + 3 + l]; }
-static View& ie_S(linview_program* p, int l) { return p->views[p->L + 3 + (p->L - 1) + l]; }
+static View& ie_P(linview_program* p, int l) {
+  return l == 0 ? p->views[0] : p->views[p->ie_NT + 2 + l];
+}
+static View& ie_S(linview_program* p, int l) {  // S'_{2^l}; S'_1 = A
+  return l == 0 ? p->views[0] : p->views[p->ie_NT + 2 + p->ie_Ls + l];
+}
 
-static linview_status iter_exp_reeval(linview_program* p, cudaStream_t s) {
+// t2 = B + P (th - B) + S' B  (= P th + S B with S = I + S' - P)
+static linview_status iter_sk_next(linview_program* p, const View& th, View& t2, const View& ph,
+                                   const View& sh, cudaStream_t s) {
   const int64_t n = p->d.n, pp = p->d.p;
-  const int L = p->L, mode = reeval_mode(p), e = p->elem;
+  const int mode = reeval_mode(p), e = p->elem;
+  const View& b = p->views[p->ie_NT + 1];
+  LV_CUDA(cudaMemcpy2DAsync(p->Dh, p->ldD * e, th.ptr, th.ld * e, pp * e, n,
+                            cudaMemcpyDeviceToDevice, s));
+  if (e == 4)
+    LV_CUDA(launch_axpy_rows<float>(static_cast<float*>(p->Dh), p->ldD,
+                                    static_cast<const float*>(b.ptr), b.ld, -1.f, (int)n, (int)pp,
+                                    s));
+  else
+    LV_CUDA(launch_axpy_rows<double>(static_cast<double*>(p->Dh), p->ldD,
+                                     static_cast<const double*>(b.ptr), b.ld, -1.0, (int)n,
+                                     (int)pp, s));
+  LV_CUDA(cudaMemcpy2DAsync(t2.ptr, t2.ld * e, b.ptr, b.ld * e, pp * e, n,
+                            cudaMemcpyDeviceToDevice, s));
+  LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, ph.ptr, ph.ld, p->Dh, p->ldD, 1.0, t2.ptr, t2.ld,
+                 s, mode));
+  LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, sh.ptr, sh.ld, b.ptr, b.ld, 1.0, t2.ptr, t2.ld, s,
+                 mode));
+  return LINVIEW_OK;
+}
+
+static linview_status iter_sk_reeval(linview_program* p, cudaStream_t s) {
+  const int64_t n = p->d.n, pp = p->d.p;
+  const int Ls = p->ie_Ls, mode = reeval_mode(p), e = p->elem;
   View& a = p->views[0];
-  for (int l = 1; l < L; ++l) {  // P_2h = P_h P_h, S'_2h = S'_h + P_h S'_h
+  for (int l = 1; l <= Ls; ++l) {  // P_2h = P_h P_h, S'_2h = S'_h + P_h S'_h
     View& ph = ie_P(p, l - 1);
-    const View& sh = (l == 1) ? a : ie_S(p, l - 1);
+    const View& sh = ie_S(p, l - 1);
     LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, ph.ptr, ph.ld, ph.ptr, ph.ld, 0.0,
                    ie_P(p, l).ptr, ie_P(p, l).ld, s, mode));
     View& s2 = ie_S(p, l);
@@ -1174,69 +1210,63 @@ static linview_status iter_exp_reeval(linview_program* p, cudaStream_t s) {
     LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, ph.ptr, ph.ld, sh.ptr, sh.ld, 1.0, s2.ptr,
                    s2.ld, s, mode));
   }
-  const View& b = p->views[L + 2];
-  const View& t0 = p->views[L + 3];
+  const View& b = p->views[p->ie_NT + 1];
+  const View& t0 = p->views[p->ie_NT + 2];
   View& t1 = ie_T(p, 0);  // T_1 = A T_0 + B
   LV_CUDA(cudaMemcpy2DAsync(t1.ptr, t1.ld * e, b.ptr, b.ld * e, pp * e, n,
                             cudaMemcpyDeviceToDevice, s));
   LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, a.ptr, a.ld, t0.ptr, t0.ld, 1.0, t1.ptr, t1.ld,
                  s, mode));
-  for (int l = 0; l < L; ++l) {  // T_2h = B + P_h (T_h - B) + S'_h B
-    View& th = ie_T(p, l);
-    View& t2 = ie_T(p, l + 1);
-    View& ph = ie_P(p, l);
-    const View& sh = (l == 0) ? a : ie_S(p, l);
-    LV_CUDA(cudaMemcpy2DAsync(p->Dh, p->ldD * e, th.ptr, th.ld * e, pp * e, n,
-                              cudaMemcpyDeviceToDevice, s));
-    if (e == 4)
-      LV_CUDA(launch_axpy_rows<float>(static_cast<float*>(p->Dh), p->ldD,
-                                      static_cast<const float*>(b.ptr), b.ld, -1.f, (int)n,
-                                      (int)pp, s));
-    else
-      LV_CUDA(launch_axpy_rows<double>(static_cast<double*>(p->Dh), p->ldD,
-                                       static_cast<const double*>(b.ptr), b.ld, -1.0, (int)n,
-                                       (int)pp, s));
-    LV_CUDA(cudaMemcpy2DAsync(t2.ptr, t2.ld * e, b.ptr, b.ld * e, pp * e, n,
-                              cudaMemcpyDeviceToDevice, s));
-    LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, ph.ptr, ph.ld, p->Dh, p->ldD, 1.0, t2.ptr,
-                   t2.ld, s, mode));
-    LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, sh.ptr, sh.ld, b.ptr, b.ld, 1.0, t2.ptr,
-                   t2.ld, s, mode));
-  }
+  for (int l = 0; l < Ls; ++l)  // T_2h from T_h, h = 2^l
+    LV_TRY(iter_sk_next(p, ie_T(p, l), ie_T(p, l + 1), ie_P(p, l), ie_S(p, l), s));
+  for (int j = Ls + 1; j < p->ie_NT; ++j)  // T_i from T_{i-s}
+    LV_TRY(iter_sk_next(p, ie_T(p, j - 1), ie_T(p, j), ie_P(p, Ls), ie_S(p, Ls), s));
   return LINVIEW_OK;
 }
 
-static linview_status iter_exp_create(linview_program* p, const void* const* inputs,
-                                      const int64_t* lds, int on_dev, cudaStream_t s) {
+static linview_status iter_sk_create(linview_program* p, const void* const* inputs,
+                                     const int64_t* lds, int on_dev, cudaStream_t s) {
   const int64_t n = p->d.n, pp = p->d.p;
   const int k = p->d.k;
   if (pp < 1) return fail(LINVIEW_EINVAL, "p must be >= 1");
-  if (k < 2 || !is_pow2(k))
-    return fail(LINVIEW_EINVAL, "the exponential model needs k a power of two >= 2 (k=%d)", k);
+  int sk = 0;
+  if (p->d.model == LINVIEW_MODEL_EXP) {
+    if (k < 2 || !is_pow2(k))
+      return fail(LINVIEW_EINVAL, "the exponential model needs k a power of two >= 2 (k=%d)", k);
+    sk = k / 2;
+  } else {
+    sk = p->d.skip;
+    if (!is_pow2(sk) || k % sk != 0 || k < 2 * sk)
+      return fail(LINVIEW_EINVAL,
+                  "the skip model needs s a power of two, k a multiple of s, k >= 2s (k=%d s=%d)",
+                  k, sk);
+  }
   if ((int64_t)p->d.r_max * k > 128)
     return fail(LINVIEW_EUNSUPPORTED, "r_max*k=%lld exceeds 128", (long long)p->d.r_max * k);
   if (p->d.strategy != LINVIEW_STRATEGY_FACTORED)
-    return fail(LINVIEW_EINVAL, "the exponential model takes the factored strategy");
+    return fail(LINVIEW_EINVAL, "the exponential and skip models take the factored strategy");
   if (lds[0] < n || lds[1] < pp || lds[2] < pp) return fail(LINVIEW_ESHAPE, "bad leading dims");
-  const int L = ilog2(k);
-  p->L = L;
+  p->ie_s = sk;
+  p->ie_Ls = ilog2(sk);
+  p->ie_NT = p->ie_Ls + k / sk;
+  const int NT = p->ie_NT, Ls = p->ie_Ls;
   LV_TRY(add_square_view(p, n));  // A = P_1
-  p->ldT = rup((int64_t)(L + 2) * pp, 64);
+  p->ldT = rup((int64_t)(NT + 1) * pp, 64);
   LV_TRY(dalloc(p, (size_t)n * p->ldT * p->elem, &p->Tpanel));
   p->ldB = rup(pp, 64);
   LV_TRY(dalloc(p, (size_t)n * p->ldB * p->elem, &p->Bm));
   char* tp = static_cast<char*>(p->Tpanel);
-  for (int j = 0; j <= L; ++j)  // T_{2^j} in panel block j + 1
+  for (int j = 0; j < NT; ++j)  // the j-th T view in panel block j + 1
     LV_TRY(add_rect_view(p, tp + (size_t)(j + 1) * pp * p->elem, n, pp, p->ldT));
   LV_TRY(add_rect_view(p, p->Bm, n, pp, p->ldB));
   LV_TRY(add_rect_view(p, p->Tpanel, n, pp, p->ldT));  // T_0 in block 0
-  for (int l = 1; l < L; ++l) LV_TRY(add_square_view(p, n));  // P_2 .. P_{k/2}
-  for (int l = 1; l < L; ++l) LV_TRY(add_square_view(p, n));  // S'_2 .. S'_{k/2}
+  for (int l = 1; l <= Ls; ++l) LV_TRY(add_square_view(p, n));  // P_2 .. P_s
+  for (int l = 1; l <= Ls; ++l) LV_TRY(add_square_view(p, n));  // S'_2 .. S'_s
   LV_TRY(copy_in(p->views[0].ptr, p->views[0].ld, inputs[0], lds[0], n, n, p->elem, on_dev, s));
   LV_TRY(copy_in(p->Bm, p->ldB, inputs[1], lds[1], n, pp, p->elem, on_dev, s));
   LV_TRY(copy_in(p->Tpanel, p->ldT, inputs[2], lds[2], n, pp, p->elem, on_dev, s));
   p->fs = rup(n, 64);
-  p->Rcap = p->d.r_max * k / 2;  // U_h, V_h up to h = k/2
+  p->Rcap = p->d.r_max * sk;  // U_h, V_h up to h = s
   const int64_t ck = (int64_t)p->d.r_max * k;  // width of the factors of dT_k
   const size_t fb = (size_t)p->fs * p->Rcap * p->elem;
   LV_TRY(dalloc(p, fb, &p->Uar));
@@ -1249,116 +1279,139 @@ static linview_status iter_exp_create(linview_program* p, const void* const* inp
   LV_TRY(dalloc(p, (size_t)ck * p->Rcap * p->elem, &p->XtV));
   const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
   p->part_cs = p->fs;
-  p->xp_s = (int64_t)p->Rcap * p->part_cs;  // widest products block: X_{k/2} (Rcap columns)
-  p->yp_q = p->xp_s;
+  p->xp_s = ck * p->part_cs;  // widest products block: P_s X_{k-s}
+  p->yp_q = (int64_t)p->Rcap * p->part_cs;
   LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart));
   LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart));
   p->ldD = rup(pp, 64);
   LV_TRY(dalloc(p, (size_t)n * p->ldD * p->elem, &p->Dh));
   LV_TRY(ensure_stage(p, (size_t)2 * n * p->d.r_max * p->elem));
-  return iter_exp_reeval(p, s);
+  return iter_sk_reeval(p, s);
 }
 
-// Incremental exponential model for dA = U_1 V_1^T (U_1 in the U arena, V_1
-// at the right end of the V arena).  The powers part is Appendix A's
-// exponential model (P_h, and S'_h by the suffix block sums W^_h of V_h).
-// The factors of dT_h = X_h Y_h^T follow Appendix B's rule
-//   U_2h = [Q_h, P_h U_h + Q_h (R_h^T U_h), Z_h],  V_2h = [T_h^T R_h, V_h, B^T W_h]
+// Incremental exponential / skip model for dA = U_1 V_1^T (U_1 in the U
+// arena, V_1 at the right end of the V arena).  The powers part is Appendix
+// A's exponential model up to P_s (and S'_h by the suffix block sums W^_h of
+// V_h).  The factors of dT_i = X_i Y_i^T follow Appendix B's rule
+//   U_i = [Q_h, P_h U_j + Q_h (R_h^T U_j), Z_h],  V_i = [T_j^T R_h, V_j, B^T W_h]
+// (i = 2h, j = h in the exponential part; h = s, j = i - s in the skip part)
 // with Q_h = U_h, R_h = V_h and dS_h = Z_h W_h^T = U_h (W^_h - V_h)^T
-// (S_h = I + S'_h - P_h); its Q_h and Z_h blocks are both U_h, so they merge:
-//   X_2h = [U_h, P_h X_h],
-//   Y_2h = [T_h^T V_h + Y_h (X_h^T V_h) + B^T (W^_h - V_h), Y_h],
-// X_1 = U_1, Y_1 = T_0^T V_1 (width r h for dT_h).  Per level: the small
-// products from the old T_h, T_h += X_h Y_h^T, one products pass over the old
-// P_h for P_h X_h, then the level pass on P_h and the update of S'_h.
+// (S_h = I + S'_h - P_h), so the Q_h and Z_h blocks, both U_h, merge:
+//   X_i = [U_h, P_h X_j],
+//   Y_i = [T_j^T V_h + Y_j (X_j^T V_h) + B^T (W^_h - V_h), Y_j],
+// X_1 = U_1, Y_1 = T_0^T V_1.  Each step takes the small products from the
+// old T_j, then T_j += X_j Y_j^T, and one products pass over the old P_h for
+// P_h X_j.  The exponential part runs App. A's level pass on P_h (h < s)
+// after its step; P_s, used by every skip step, is refreshed after them.
 template <typename T>
-static linview_status iter_exp_propagate(linview_program* p, int r, cudaStream_t s) {
+static linview_status iter_sk_step(linview_program* p, int cur, View& tj, const View& ph, int rh,
+                                   int c, const T* Vh, bool with_b, cudaStream_t s) {
   const int n = (int)p->d.n;
   const int64_t pp = p->d.p;
-  const int L = p->L;
   const int64_t fs = p->fs;
   const int mode = exact_mode(p);
+  const View& b = p->views[p->ie_NT + 1];
+  T* Xc = static_cast<T*>(p->Xar[cur]);
+  T* Yc = static_cast<T*>(p->Yar[cur]);
+  T* Xn = static_cast<T*>(p->Xar[cur ^ 1]);
+  T* Yn = static_cast<T*>(p->Yar[cur ^ 1]);
+  T* XtV = static_cast<T*>(p->XtV);
+  // first block of Y_i (column-major p x rh): T_j^T V_h + Y_j (X_j^T V_h)
+  LV_TRY(gemm_cm(p, false, false, pp, rh, n, 1.0, tj.ptr, tj.ld, Vh, fs, 0.0, Yn, pp, s, mode));
+  LV_TRY(gemm_cm(p, true, false, c, rh, n, 1.0, Xc, fs, Vh, fs, 0.0, XtV, c, s, mode));
+  LV_TRY(gemm_cm(p, false, false, pp, rh, c, 1.0, Yc, pp, XtV, c, 1.0, Yn, pp, s, mode));
+  if (with_b) {  // + B^T (W^_h - V_h) (W^_h in the What arena; dS_1 = 0)
+    LV_TRY(gemm_cm(p, false, false, pp, rh, n, 1.0, b.ptr, b.ld, p->What, fs, 1.0, Yn, pp, s,
+                   mode));
+    LV_TRY(gemm_cm(p, false, false, pp, rh, n, -1.0, b.ptr, b.ld, Vh, fs, 1.0, Yn, pp, s, mode));
+  }
+  LV_CUDA(cudaMemcpyAsync(Yn + (int64_t)rh * pp, Yc, sizeof(T) * pp * c, cudaMemcpyDeviceToDevice,
+                          s));
+  // T_j += X_j Y_j^T  (column-major T_j^T, p x n)
+  LV_TRY(gemm_cm(p, false, true, pp, n, c, 1.0, Yc, pp, Xc, fs, 1.0, tj.ptr, tj.ld, s, mode));
+  // X_i = [U_h, P_h X_j] from the old P_h
+  const PassGeom g = fused_geom(sizeof(T), n, p->sms);
+  LV_TRY(run_products_update<T>(p, ph, c, Xc, nullptr, nullptr, nullptr, s));
+  {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, c,
+                                   Xn + (int64_t)rh * fs, fs, s));
+  }
+  LV_CUDA(cudaMemcpyAsync(Xn, p->Uar, sizeof(T) * fs * rh, cudaMemcpyDeviceToDevice, s));
+  return LINVIEW_OK;
+}
+
+template <typename T>
+static linview_status iter_sk_propagate(linview_program* p, int r, cudaStream_t s) {
+  const int n = (int)p->d.n;
+  const int64_t pp = p->d.p;
+  const int k = p->d.k, sk = p->ie_s, Ls = p->ie_Ls, NT = p->ie_NT;
+  const int64_t fs = p->fs;
   T* U = static_cast<T*>(p->Uar);
   T* V = static_cast<T*>(p->Var);
   T* Wh = static_cast<T*>(p->What);
-  T* XtV = static_cast<T*>(p->XtV);
-  const View& b = p->views[L + 2];
-  const View& t0 = p->views[L + 3];
+  const View& t0 = p->views[NT + 2];
   const PassGeom g = fused_geom(sizeof(T), n, p->sms);
   int cur = 0;
-  {  // X_1 = U_1, Y_1 = T_0^T V_1
-    T* X0 = static_cast<T*>(p->Xar[0]);
-    LV_CUDA(cudaMemcpyAsync(X0, U, sizeof(T) * fs * r, cudaMemcpyDeviceToDevice, s));
-    LV_TRY(gemm_cm(p, false, false, pp, r, n, 1.0, t0.ptr, t0.ld, V + (int64_t)(p->Rcap - r) * fs,
-                   fs, 0.0, p->Yar[0], pp, s, mode));
-  }
-  for (int l = 0; l < L; ++l) {
-    const int rh = r << l;  // width of U_h, V_h and of X_h, Y_h
+  // X_1 = U_1, Y_1 = T_0^T V_1
+  LV_CUDA(cudaMemcpyAsync(p->Xar[0], U, sizeof(T) * fs * r, cudaMemcpyDeviceToDevice, s));
+  LV_TRY(gemm_cm(p, false, false, pp, r, n, 1.0, t0.ptr, t0.ld, V + (int64_t)(p->Rcap - r) * fs,
+                 fs, 0.0, p->Yar[0], pp, s, exact_mode(p)));
+  for (int l = 0; l < Ls; ++l) {  // exponential part: T_2h from T_h, h = 2^l < s
+    const int rh = r << l;
     T* Vh = V + (int64_t)(p->Rcap - rh) * fs;
-    View& th = ie_T(p, l);
-    T* Xc = static_cast<T*>(p->Xar[cur]);
-    T* Yc = static_cast<T*>(p->Yar[cur]);
-    T* Xn = static_cast<T*>(p->Xar[cur ^ 1]);
-    T* Yn = static_cast<T*>(p->Yar[cur ^ 1]);
-    // first block of Y_2h (column-major p x rh): T_h^T V_h + Y_h (X_h^T V_h)
-    LV_TRY(gemm_cm(p, false, false, pp, rh, n, 1.0, th.ptr, th.ld, Vh, fs, 0.0, Yn, pp, s, mode));
-    LV_TRY(gemm_cm(p, true, false, rh, rh, n, 1.0, Xc, fs, Vh, fs, 0.0, XtV, rh, s, mode));
-    LV_TRY(gemm_cm(p, false, false, pp, rh, rh, 1.0, Yc, pp, XtV, rh, 1.0, Yn, pp, s, mode));
-    if (l >= 1) {  // + B^T (W^_h - V_h)  (dS_1 = 0)
+    if (l >= 1) {
       ProfScope ps(p, s, 0.0);
       LV_CUDA(launch_suffix_sums<T>(Vh, Wh, fs, n, rh, r, s));
-      LV_TRY(gemm_cm(p, false, false, pp, rh, n, 1.0, b.ptr, b.ld, Wh, fs, 1.0, Yn, pp, s, mode));
-      LV_TRY(gemm_cm(p, false, false, pp, rh, n, -1.0, b.ptr, b.ld, Vh, fs, 1.0, Yn, pp, s, mode));
     }
-    LV_CUDA(cudaMemcpyAsync(Yn + (int64_t)rh * pp, Yc, sizeof(T) * pp * rh,
-                            cudaMemcpyDeviceToDevice, s));
-    // T_h += X_h Y_h^T  (column-major T_h^T, p x n)
-    LV_TRY(gemm_cm(p, false, true, pp, n, rh, 1.0, Yc, pp, Xc, fs, 1.0, th.ptr, th.ld, s, mode));
-    // X_2h = [U_h, P_h X_h] from the old P_h
     View& ph = ie_P(p, l);
-    LV_TRY(run_products_update<T>(p, ph, rh, Xc, nullptr, nullptr, nullptr, s));
-    {
-      ProfScope ps(p, s, 0.0);
-      LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, rh,
-                                     Xn + (int64_t)rh * fs, fs, s));
-    }
-    LV_CUDA(cudaMemcpyAsync(Xn, U, sizeof(T) * fs * rh, cudaMemcpyDeviceToDevice, s));
-    // the powers part at level h (Appendix A): P_h and S'_h refreshed,
-    // U_2h, V_2h assembled while h < k/2
+    LV_TRY(iter_sk_step<T>(p, cur, ie_T(p, l), ph, rh, rh, Vh, l >= 1, s));
+    cur ^= 1;
+    // App. A's level pass on P_h, the update of S'_h, the assembly of U_2h, V_2h
     const bool fused = rh <= kMaxFusedR;
-    if (l < L - 1) {
-      if (!fused) {
-        ProfScope ps(p, s, 0.0);
-        LV_CUDA((launch_gram<T>(Vh, U, fs, n, rh, p->Cpart, p->ticket, p->C, p->status, s)));
-      }
-      LV_TRY(run_products_update<T>(p, ph, rh, U, Vh, U, Vh, s, fused ? p->Cpart : nullptr));
-      AssembleParams a{};
-      a.n = n;
-      a.r_h = rh;
-      a.fs = fs;
-      a.Xpart = p->Xpart;
-      a.gC = g.gC;
-      a.xp_s = p->xp_s;
-      a.Ypart = p->Ypart;
-      a.gR = g.gR;
-      a.yp_q = p->yp_q;
-      a.part_cs = p->part_cs;
-      a.C = fused ? p->Cpart : p->C;
-      a.nC = fused ? g.gR : 1;
-      a.Uh = U;
-      a.Unew = U + (int64_t)rh * fs;
-      a.Ynew = V + (int64_t)(p->Rcap - 2 * rh) * fs;
+    if (!fused) {
       ProfScope ps(p, s, 0.0);
-      LV_CUDA(launch_assemble<T>(a, s));
-    } else {
-      LV_TRY(run_update<T>(p, ph, U, Vh, rh, s));
+      LV_CUDA((launch_gram<T>(Vh, U, fs, n, rh, p->Cpart, p->ticket, p->C, p->status, s)));
     }
+    LV_TRY(run_products_update<T>(p, ph, rh, U, Vh, U, Vh, s, fused ? p->Cpart : nullptr));
     if (l >= 1) LV_TRY(run_update<T>(p, ie_S(p, l), U, Wh, rh, s));  // dS'_h = U_h W^_h^T
+    AssembleParams a{};
+    a.n = n;
+    a.r_h = rh;
+    a.fs = fs;
+    a.Xpart = p->Xpart;
+    a.gC = g.gC;
+    a.xp_s = p->xp_s;
+    a.Ypart = p->Ypart;
+    a.gR = g.gR;
+    a.yp_q = p->yp_q;
+    a.part_cs = p->part_cs;
+    a.C = fused ? p->Cpart : p->C;
+    a.nC = fused ? g.gR : 1;
+    a.Uh = U;
+    a.Unew = U + (int64_t)rh * fs;
+    a.Ynew = V + (int64_t)(p->Rcap - 2 * rh) * fs;
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_assemble<T>(a, s));
+  }
+  // skip part: T_i from T_{i-s} with the old P_s, i = 2s, .., k
+  const int rs = r * sk;
+  T* Vs = V + (int64_t)(p->Rcap - rs) * fs;
+  if (Ls >= 1) {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_suffix_sums<T>(Vs, Wh, fs, n, rs, r, s));
+  }
+  for (int j = Ls + 1; j < NT; ++j) {
+    const int c = (j - Ls) * rs;  // width of the factors of T_{i-s}
+    LV_TRY(iter_sk_step<T>(p, cur, ie_T(p, j - 1), ie_P(p, Ls), rs, c, Vs, Ls >= 1, s));
     cur ^= 1;
   }
-  // T_k += X_k Y_k^T
-  LV_TRY(gemm_cm(p, false, true, pp, n, (int64_t)r << L, 1.0, p->Yar[cur], pp, p->Xar[cur], fs,
-                 1.0, ie_T(p, L).ptr, ie_T(p, L).ld, s, mode));
+  // T_k += X_k Y_k^T, then P_s and S'_s
+  View& tk = ie_T(p, NT - 1);
+  LV_TRY(gemm_cm(p, false, true, pp, n, (int64_t)r * k, 1.0, p->Yar[cur], pp, p->Xar[cur], fs,
+                 1.0, tk.ptr, tk.ld, s, exact_mode(p)));
+  LV_TRY(run_update<T>(p, ie_P(p, Ls), U, Vs, rs, s));
+  if (Ls >= 1) LV_TRY(run_update<T>(p, ie_S(p, Ls), U, Wh, rs, s));
   return LINVIEW_OK;
 }
 
@@ -1573,7 +1626,8 @@ linview_status linview_create_program(const linview_program_desc* desc, const vo
         (desc->kind == LINVIEW_POWER || desc->kind == LINVIEW_POWER_SUM ||
          desc->kind == LINVIEW_ITERATION)) &&
       !(desc->model == LINVIEW_MODEL_SKIP &&
-        (desc->kind == LINVIEW_POWER || desc->kind == LINVIEW_POWER_SUM)))
+        (desc->kind == LINVIEW_POWER || desc->kind == LINVIEW_POWER_SUM ||
+         desc->kind == LINVIEW_ITERATION)))
     return fail(LINVIEW_EINVAL, "model %d is not available for kind %d", desc->model, desc->kind);
   if (desc->strategy != LINVIEW_STRATEGY_FACTORED &&
       !(desc->strategy == LINVIEW_STRATEGY_HYBRID && desc->kind == LINVIEW_ITERATION))
@@ -1751,7 +1805,7 @@ linview_status linview_reeval(linview_program* p, void* stream) {
   switch (p->d.kind) {
     case LINVIEW_POWER:
     case LINVIEW_POWER_SUM: return powers_reeval(p, s);
-    case LINVIEW_ITERATION: return iter_exp(p) ? iter_exp_reeval(p, s) : iter_reeval(p, s);
+    case LINVIEW_ITERATION: return iter_exp(p) ? iter_sk_reeval(p, s) : iter_reeval(p, s);
     case LINVIEW_OLS: return p->elem == 4 ? ols_reeval_t<float>(p, s) : ols_reeval_t<double>(p, s);
     default: return fail(LINVIEW_EUNSUPPORTED, "reeval for kind %d", p->d.kind);
   }
@@ -1792,8 +1846,8 @@ constexpr int kKeyB = 1024;
 static linview_status propagate_eager(linview_program* p, int key, cudaStream_t s) {
   if (p->d.kind == LINVIEW_ITERATION) {
     if (iter_exp(p))
-      return p->elem == 4 ? iter_exp_propagate<float>(p, key, s)
-                          : iter_exp_propagate<double>(p, key, s);
+      return p->elem == 4 ? iter_sk_propagate<float>(p, key, s)
+                          : iter_sk_propagate<double>(p, key, s);
     if (p->d.strategy == LINVIEW_STRATEGY_HYBRID) {
       const bool bu = key >= kKeyB;
       const int r = bu ? key - kKeyB : key;

@@ -235,32 +235,38 @@ def test_strategy_validation():
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("n,p,k,r", [(300, 5, 16, 2), (1030, 3, 4, 1), (513, 64, 8, 2),
-                                     (64, 1, 2, 1), (777, 16, 16, 1)])
-def test_iteration_exp_model(prec, n, p, k, r):
-    """Exponential model of the general form (App. B): views T_1, T_2, .., T_k
-    (and the auxiliary P_h, S'_h) after factored and row updates of A, against
-    the oracle's re-evaluation T_2h = P_h T_h + S_h B."""
+@pytest.mark.parametrize("n,p,k,r,model,s", [(300, 5, 16, 2, "exp", 8), (1030, 3, 4, 1, "exp", 2),
+                                             (513, 64, 8, 2, "exp", 4), (64, 1, 2, 1, "exp", 1),
+                                             (777, 16, 16, 1, "skip", 4), (300, 7, 8, 2, "skip", 2),
+                                             (129, 3, 5, 1, "skip", 1), (1030, 9, 12, 1, "skip", 4)])
+def test_iteration_exp_and_skip_models(prec, n, p, k, r, model, s):
+    """Exponential and skip-s models of the general form (App. B): the views
+    T_1, T_2, .., T_s, T_2s, .., T_k (and the auxiliary P_h, S'_h) after factored
+    and row updates of A, against the oracle's re-evaluation."""
     dt = np.float64 if prec == "f64" else np.float32
     a, b, t0 = li.iteration_inputs(n, p, seed=n + 11, dtype=dt)
-    prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=k, r_max=r, precision=prec,
-                 model="exp")
-    L = k.bit_length() - 1
+    kw = {"model": model} if model == "exp" else {"model": "skip", "skip": s}
+    prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=k, r_max=r, precision=prec, **kw)
+    Ls = s.bit_length() - 1
+    tidx = [1 << j for j in range(Ls + 1)] + list(range(2 * s, k + 1, s))
+    NT = len(tidx)
+    assert prog.num_views() == 1 + NT + 2 + 2 * Ls
     acur = a.astype(np.float64)
     b64, t064 = b.astype(np.float64), t0.astype(np.float64)
     tol = 1e-10 if prec == "f64" else 1e-4
 
     def check():
         prog.sync()
-        T, P, S = oi.exp_reeval(acur, b64, t064, k)
-        for j in range(L + 1):
-            assert rel_frob(prog.read_view_host(1 + j), T[1 << j]) <= tol, j
+        T, P, S = oi.skip_reeval(acur, b64, t064, k, s)
+        for j, i in enumerate(tidx):
+            assert rel_frob(prog.read_view_host(1 + j), T[i]) <= tol, i
         assert rel_frob(prog.read_view_host(0), acur) <= tol
-        for j in range(1, L):
-            h = 1 << j
-            assert rel_frob(prog.read_view_host(L + 3 + j), P[h]) <= tol, h
+        assert rel_frob(prog.read_view_host(NT + 1), b64) <= tol
+        for l in range(1, Ls + 1):
+            h = 1 << l
+            assert rel_frob(prog.read_view_host(NT + 2 + l), P[h]) <= tol, h
             sprime = S[h] - np.eye(n) + P[h]   # S'_h = A + .. + A^h
-            assert rel_frob(prog.read_view_host(2 * L + 2 + j), sprime) <= tol, h
+            assert rel_frob(prog.read_view_host(NT + 2 + Ls + l), sprime) <= tol, h
 
     check()
     g = np.random.default_rng(n)
@@ -281,6 +287,10 @@ def test_iteration_exp_model_errors():
     a, b, t0 = li.iteration_inputs(n, p, seed=5)
     with pytest.raises(LinviewError) as e:
         _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=6, precision="f64", model="exp")
+    assert e.value.status == _lib.EINVAL
+    with pytest.raises(LinviewError) as e:  # k must be a multiple of s and >= 2s
+        _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=6, precision="f64", model="skip",
+              skip=4)
     assert e.value.status == _lib.EINVAL
     with pytest.raises(LinviewError):
         _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=4, precision="f64", model="exp",
