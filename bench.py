@@ -604,19 +604,23 @@ def iteration_p_sweep(args, seed=0, k=16, steps=6, ps=(1, 16, 128, 1024)):
         row["hybrid_ms"] = _event_ms(lambda j: hyb.apply_row_delta(*ups[2 + j]), steps)
         hyb.sync()
         hyb.close()
-        # exponential model (views T_1, T_2, T_4, .., T_k; auxiliary P_h, S'_h)
-        ex = Program("iteration", [a, b, t0], k=k, r_max=1, model="exp")
-        for i, v in ups[:2]:
-            ex.apply_row_delta(i, v)
-        row["exp_model_ms"] = _event_ms(lambda j: ex.apply_row_delta(*ups[2 + j]), steps)
-        ex.sync()
-        ex.close()
+        # exponential model (views T_1, T_2, T_4, .., T_k) and skip-4 model (T_1,
+        # T_2, T_4, T_8, T_12, T_16), with their auxiliary P_h, S'_h views
+        for key, kw in (("exp_model_ms", {"model": "exp"}),
+                        ("skip4_model_ms", {"model": "skip", "skip": 4})):
+            ex = Program("iteration", [a, b, t0], k=k, r_max=1, **kw)
+            for i, v in ups[:2]:
+                ex.apply_row_delta(i, v)
+            row[key] = _event_ms(lambda j: ex.apply_row_delta(*ups[2 + j]), steps)
+            ex.sync()
+            ex.close()
         rows.append(row)
     return {"n": n, "k": k, "B": "0", "update": "rank-1 row of A", "rows": rows,
             "note": "incremental = factored deltas, linear model (Krylov reuse); hybrid = "
-                    "dense deltas D_i = A D_{i-1} + rank-1 term; exp_model = factored deltas, "
-                    "exponential model (views T_1, T_2, T_4, .., T_k only, with P_h and S'_h "
-                    "views); re-evaluation = k products A T_i"}
+                    "dense deltas D_i = A D_{i-1} + rank-1 term; exp_model / skip4_model = "
+                    "factored deltas, exponential / skip-4 model (views T_1, T_2, T_4, .., T_k "
+                    "/ T_1, T_2, T_4, T_8, T_12, T_16, with P_h and S'_h views); "
+                    "re-evaluation = k products A T_i"}
 
 
 def gd_regression(seed=0, n=4096, m=4096, p=1024, k=16, steps=6):
