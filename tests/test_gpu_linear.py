@@ -91,8 +91,8 @@ def test_linear_model_errors():
     with pytest.raises(LinviewError):
         Program("power", [a], k=1, r_max=1, model="linear")
     it = li.iteration_inputs(64, 2, seed=1, dtype=np.float32)
-    with pytest.raises(LinviewError):
-        Program("iteration", list(it), k=4, r_max=1, model="linear")
+    with pytest.raises(LinviewError):  # the skip step must be a power of two
+        Program("iteration", list(it), k=6, r_max=1, model="skip", skip=3)
     prog = Program("power", [a], k=4, r_max=1, model="linear")
     g = torch.zeros((64, 64), device="cuda")
     with pytest.raises(LinviewError):
