@@ -197,6 +197,25 @@ class ExpIncrementalIteration:
             self.t[h] += U[h] @ V[h].T
         return U, V
 
+    def apply_b(self, ub, vb):
+        """dB = U_b V_b^T with A unchanged (derived from the recurrence; the
+        paper omits changes in B, Section 4.3.2): P_h and S_h are unchanged,
+        dT_1 = dB and dT_2h = P_h dT_h + S_h dB, i.e.
+        U_1 = U_b, V_1 = V_b, U_2h = [P_h U_h, S_h U_b], V_2h = [V_h, V_b]."""
+        n, p = self.b.shape
+        ub = np.asarray(ub, dtype=np.float64).reshape(n, -1)
+        vb = np.asarray(vb, dtype=np.float64).reshape(p, -1)
+        U, V = {1: ub}, {1: vb}
+        h = 1
+        while 2 * h <= self.k:
+            U[2 * h] = np.hstack([self.p[h] @ U[h], self.s[h] @ ub])
+            V[2 * h] = np.hstack([V[h], vb])
+            h *= 2
+        self.b += ub @ vb.T
+        for h in self.t:
+            self.t[h] += U[h] @ V[h].T
+        return U, V
+
 
 def skip_reeval(a, b, t0, k: int, s: int):
     """Skip-s model: ({i: T_i} for i = 1, 2, 4, .., s, 2s, 3s, .., k,
@@ -252,6 +271,28 @@ class SkipIncrementalIteration:
         for h in self.p:
             self.p[h] += Q[h] @ R[h].T
             self.sv[h] += Z[h] @ W[h].T
+        for i in self.t:
+            self.t[i] += U[i] @ V[i].T
+        return U, V
+
+    def apply_b(self, ub, vb):
+        """dB = U_b V_b^T with A unchanged (derived from the recurrences):
+        dT_1 = dB, dT_2h = P_h dT_h + S_h dB (h < s), dT_i = P_s dT_{i-s} + S_s dB
+        (i > s), i.e. U_i = [P U_j, S U_b], V_i = [V_j, V_b]."""
+        n, p = self.b.shape
+        ub = np.asarray(ub, dtype=np.float64).reshape(n, -1)
+        vb = np.asarray(vb, dtype=np.float64).reshape(p, -1)
+        U, V = {1: ub}, {1: vb}
+        h = 1
+        while 2 * h <= self.s:
+            U[2 * h] = np.hstack([self.p[h] @ U[h], self.sv[h] @ ub])
+            V[2 * h] = np.hstack([V[h], vb])
+            h *= 2
+        s = self.s
+        for i in range(2 * s, self.k + 1, s):
+            U[i] = np.hstack([self.p[s] @ U[i - s], self.sv[s] @ ub])
+            V[i] = np.hstack([V[i - s], vb])
+        self.b += ub @ vb.T
         for i in self.t:
             self.t[i] += U[i] @ V[i].T
         return U, V

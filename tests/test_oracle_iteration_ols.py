@@ -272,3 +272,36 @@ def test_skip_special_cases_and_widths():
     assert {i: U4[i].shape[1] for i in U4} == {1: 1, 2: 2, 4: 5, 8: 12, 12: 19, 16: 26}
     with pytest.raises(ValueError):
         oi.SkipIncrementalIteration(a, b, t0, 6, 4)
+
+
+@pytest.mark.parametrize("k,s", [(16, 8), (16, 4), (8, 2), (5, 1)])
+def test_exp_skip_b_updates_match_reeval(k, s):
+    """Updates to B in the exponential / skip models (dT_1 = dB,
+    dT_2h = P_h dT_h + S_h dB, dT_i = P_s dT_{i-s} + S_s dB), interleaved with
+    updates to A, against re-evaluation on the current A and B; and the
+    A = lam I closed form dT_i = (1 + lam + .. + lam^{i-1}) dB."""
+    n, p = 9, 3
+    a, b, t0 = li.iteration_inputs(n, p, seed=k + s)
+    inc = (oi.ExpIncrementalIteration(a, b, t0, k) if s == k // 2
+           else oi.SkipIncrementalIteration(a, b, t0, k, s))
+    acur, bcur = a.copy(), b.copy()
+    g = np.random.default_rng(k * s)
+    for step in range(4):
+        if step % 2:
+            u, v = g.standard_normal((n, 2)) * 0.2, g.standard_normal((n, 2)) * 0.2
+            inc.apply(u, v)
+            acur += u @ v.T
+        else:
+            ub, vb = g.standard_normal((n, 2)), g.standard_normal((p, 2))
+            inc.apply_b(ub, vb)
+            bcur += ub @ vb.T
+        T, _, _ = oi.skip_reeval(acur, bcur, t0, k, s)
+        for i in T:
+            assert rel_frob(inc.t[i], T[i]) < 1e-12, i
+    lam = 0.6
+    inc = oi.SkipIncrementalIteration(lam * np.eye(n), b, t0, k, s)
+    before = {i: t.copy() for i, t in inc.t.items()}
+    ub, vb = g.standard_normal((n, 1)), g.standard_normal((p, 1))
+    inc.apply_b(ub, vb)
+    for i in inc.t:
+        assert rel_frob(inc.t[i] - before[i], sum(lam ** j for j in range(i)) * (ub @ vb.T)) < 1e-12
