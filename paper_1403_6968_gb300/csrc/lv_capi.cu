@@ -1277,6 +1277,7 @@ static linview_status iter_sk_create(linview_program* p, const void* const* inpu
     LV_TRY(dalloc(p, (size_t)pp * ck * p->elem, &p->Yar[i]));
   }
   LV_TRY(dalloc(p, (size_t)ck * p->Rcap * p->elem, &p->XtV));
+  LV_TRY(dalloc(p, (size_t)pp * p->d.r_max * p->elem, &p->Mr));  // V_b of an update to B
   const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
   p->part_cs = p->fs;
   p->xp_s = ck * p->part_cs;  // widest products block: P_s X_{k-s}
@@ -1412,6 +1413,87 @@ static linview_status iter_sk_propagate(linview_program* p, int r, cudaStream_t 
                  1.0, tk.ptr, tk.ld, s, exact_mode(p)));
   LV_TRY(run_update<T>(p, ie_P(p, Ls), U, Vs, rs, s));
   if (Ls >= 1) LV_TRY(run_update<T>(p, ie_S(p, Ls), U, Wh, rs, s));
+  return LINVIEW_OK;
+}
+
+// Updates to B, dB = U_b V_b^T (U_b in the U arena, V_b in Mr, p x rb) with
+// A unchanged, so P_h and S_h are unchanged (derived from the recurrences;
+// the paper omits changes in B, Section 4.3.2):
+//   dT_1 = dB,  dT_i = P dT_j + S dB  (P, S = P_h, S_h with j = h, i = 2h in
+//   the exponential part; P_s, S_s with j = i - s in the skip part), i.e.
+//   X_1 = U_b, Y_1 = V_b,  X_i = [P X_j, S U_b],  Y_i = [Y_j, V_b],
+// with S U_b = U_b + S' U_b - P U_b (S_1 = I).  Each step: T_j += X_j Y_j^T,
+// one products pass over P with [X_j | U_b] and, for S' != A, one over S'
+// with U_b; B += U_b V_b^T at the end.
+template <typename T>
+static linview_status iter_sk_step_b(linview_program* p, int cur, int c, int rb, View& tj,
+                                     const View& ph, const View* sh, cudaStream_t s) {
+  const int n = (int)p->d.n;
+  const int64_t pp = p->d.p;
+  const int64_t fs = p->fs;
+  const int mode = exact_mode(p);
+  const T* Ub = static_cast<const T*>(p->Uar);
+  const T* Vb = static_cast<const T*>(p->Mr);
+  T* Xc = static_cast<T*>(p->Xar[cur]);
+  T* Yc = static_cast<T*>(p->Yar[cur]);
+  T* Xn = static_cast<T*>(p->Xar[cur ^ 1]);
+  T* Yn = static_cast<T*>(p->Yar[cur ^ 1]);
+  T* tmp = static_cast<T*>(p->What);
+  const PassGeom g = fused_geom(sizeof(T), n, p->sms);
+  // T_j += X_j Y_j^T
+  LV_TRY(gemm_cm(p, false, true, pp, n, c, 1.0, Yc, pp, Xc, fs, 1.0, tj.ptr, tj.ld, s, mode));
+  // [P X_j | P U_b] in one products pass over P
+  LV_CUDA(cudaMemcpyAsync(Xc + (int64_t)c * fs, Ub, sizeof(T) * fs * rb, cudaMemcpyDeviceToDevice,
+                          s));
+  LV_TRY(run_products_update<T>(p, ph, c + rb, Xc, nullptr, nullptr, nullptr, s));
+  {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n,
+                                   c + rb, Xn, fs, s));
+  }
+  // second block S U_b = U_b + S' U_b - P U_b  (U_b when S = I)
+  T* blk = Xn + (int64_t)c * fs;  // column-major n x rb, seen as rb rows of n (ld fs)
+  {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_scale_copy<T>(blk, fs, blk, fs, T(sh ? -1 : 0), rb, n, s));
+    LV_CUDA(launch_axpy_rows<T>(blk, fs, Ub, fs, T(1), rb, n, s));
+  }
+  if (sh) {
+    LV_TRY(run_products_update<T>(p, *sh, rb, Ub, nullptr, nullptr, nullptr, s));
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, rb,
+                                   tmp, fs, s));
+    LV_CUDA(launch_axpy_rows<T>(blk, fs, tmp, fs, T(1), rb, n, s));
+  }
+  // Y_i = [Y_j, V_b]
+  LV_CUDA(cudaMemcpyAsync(Yn, Yc, sizeof(T) * pp * c, cudaMemcpyDeviceToDevice, s));
+  LV_CUDA(cudaMemcpyAsync(Yn + (int64_t)c * pp, Vb, sizeof(T) * pp * rb, cudaMemcpyDeviceToDevice,
+                          s));
+  return LINVIEW_OK;
+}
+
+template <typename T>
+static linview_status iter_sk_propagate_b(linview_program* p, int rb, cudaStream_t s) {
+  const int n = (int)p->d.n;
+  const int64_t pp = p->d.p;
+  const int Ls = p->ie_Ls, NT = p->ie_NT;
+  const int64_t fs = p->fs;
+  LV_CUDA(cudaMemcpyAsync(p->Xar[0], p->Uar, sizeof(T) * fs * rb, cudaMemcpyDeviceToDevice, s));
+  LV_CUDA(cudaMemcpyAsync(p->Yar[0], p->Mr, sizeof(T) * pp * rb, cudaMemcpyDeviceToDevice, s));
+  int cur = 0, c = rb;
+  for (int j = 1; j < NT; ++j) {  // the j-th T view from the (j-1)-th
+    const int l = j <= Ls ? j - 1 : Ls;  // P_{2^l}, S'_{2^l} (S_1 = I)
+    LV_TRY(iter_sk_step_b<T>(p, cur, c, rb, ie_T(p, j - 1), ie_P(p, l),
+                             l >= 1 ? &ie_S(p, l) : nullptr, s));
+    cur ^= 1;
+    c += rb;
+  }
+  View& tk = ie_T(p, NT - 1);
+  LV_TRY(gemm_cm(p, false, true, pp, n, c, 1.0, p->Yar[cur], pp, p->Xar[cur], fs, 1.0, tk.ptr,
+                 tk.ld, s, exact_mode(p)));
+  // B += U_b V_b^T (column-major B^T, p x n)
+  LV_TRY(gemm_cm(p, false, true, pp, n, rb, 1.0, p->Mr, pp, p->Uar, fs, 1.0, p->Bm, p->ldB, s,
+                 exact_mode(p)));
   return LINVIEW_OK;
 }
 
@@ -1845,9 +1927,13 @@ constexpr int kKeyB = 1024;
 // The launches of one update after its factors are in place, on stream s.
 static linview_status propagate_eager(linview_program* p, int key, cudaStream_t s) {
   if (p->d.kind == LINVIEW_ITERATION) {
-    if (iter_exp(p))
+    if (iter_exp(p)) {
+      if (key >= kKeyB)
+        return p->elem == 4 ? iter_sk_propagate_b<float>(p, key - kKeyB, s)
+                            : iter_sk_propagate_b<double>(p, key - kKeyB, s);
       return p->elem == 4 ? iter_sk_propagate<float>(p, key, s)
                           : iter_sk_propagate<double>(p, key, s);
+    }
     if (p->d.strategy == LINVIEW_STRATEGY_HYBRID) {
       const bool bu = key >= kKeyB;
       const int r = bu ? key - kKeyB : key;
@@ -1971,14 +2057,17 @@ static linview_status apply_b_delta(linview_program* p, int r, const void* U, in
     ldu = r;
     ldv = r;
   }
+  // U_b into Krylov block K_0 (linear model) or the U arena (exponential and
+  // skip models); V_b into M (p x rank)
+  void* ub_dst = iter_exp(p) ? p->Uar : p->Kar;
   if (p->elem == 4) {
-    LV_CUDA(launch_rm_to_cm<float>(static_cast<const float*>(u), ldu, static_cast<float*>(p->Kar),
+    LV_CUDA(launch_rm_to_cm<float>(static_cast<const float*>(u), ldu, static_cast<float*>(ub_dst),
                                    p->fs, (int)n, r, s));
     LV_CUDA(launch_rm_to_cm<float>(static_cast<const float*>(v), ldv, static_cast<float*>(p->Mr),
                                    pp, (int)pp, r, s));
   } else {
     LV_CUDA(launch_rm_to_cm<double>(static_cast<const double*>(u), ldu,
-                                    static_cast<double*>(p->Kar), p->fs, (int)n, r, s));
+                                    static_cast<double*>(ub_dst), p->fs, (int)n, r, s));
     LV_CUDA(launch_rm_to_cm<double>(static_cast<const double*>(v), ldv,
                                     static_cast<double*>(p->Mr), pp, (int)pp, r, s));
   }
@@ -2000,8 +2089,6 @@ linview_status linview_apply_delta(linview_program* p, int input_id, int64_t ran
   if (ldu < rank || ldv < rank) return fail(LINVIEW_ESHAPE, "ldu/ldv < rank");
   LV_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (b_update && iter_exp(p))
-    return fail(LINVIEW_EUNSUPPORTED, "updates to B in the exponential model are not built");
   if (b_update) return apply_b_delta(p, (int)rank, U, ldu, V, ldv, on_device, s);
   const int64_t n = p->d.n;
   const int r = (int)rank;

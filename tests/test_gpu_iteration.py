@@ -242,7 +242,8 @@ def test_strategy_validation():
 def test_iteration_exp_and_skip_models(prec, n, p, k, r, model, s):
     """Exponential and skip-s models of the general form (App. B): the views
     T_1, T_2, .., T_s, T_2s, .., T_k (and the auxiliary P_h, S'_h) after factored
-    and row updates of A, against the oracle's re-evaluation."""
+    and row updates of A and an update to B, against the oracle's
+    re-evaluation."""
     dt = np.float64 if prec == "f64" else np.float32
     a, b, t0 = li.iteration_inputs(n, p, seed=n + 11, dtype=dt)
     kw = {"model": model} if model == "exp" else {"model": "skip", "skip": s}
@@ -278,6 +279,10 @@ def test_iteration_exp_and_skip_models(prec, n, p, k, r, model, s):
             w = (g.standard_normal(n) * 0.01).astype(dt)
             prog.apply_row_delta(i, _dev(w))
             acur[i] += w.astype(np.float64)
+            ub = g.standard_normal((n, r)).astype(dt)
+            vb = g.standard_normal((p, r)).astype(dt)
+            prog.apply_delta(_dev(ub), _dev(vb), input_id=1)
+            b64 += ub.astype(np.float64) @ vb.astype(np.float64).T
     check()
 
 
@@ -296,9 +301,6 @@ def test_iteration_exp_model_errors():
         _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=4, precision="f64", model="exp",
               strategy="hybrid")
     prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=4, precision="f64", model="exp")
-    with pytest.raises(LinviewError) as e:
-        prog.apply_delta(_dev(np.ones((n, 1))), _dev(np.ones((p, 1))), input_id=1)
-    assert e.value.status == _lib.EUNSUPPORTED
     with pytest.raises(LinviewError) as e:
         prog.adjoint_iteration()
     assert e.value.status == _lib.EUNSUPPORTED
