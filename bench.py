@@ -679,6 +679,20 @@ def gd_regression(seed=0, n=4096, m=4096, p=1024, k=16, steps=6):
         out[f"reeval_{mode}_ms"] = _event_ms(lambda j: prog.reeval(), 2)
     prog.sync()
     prog.close()
+    # the same row replacements in the exponential and skip-4 models (views
+    # T_1, T_2, T_4, .., T_16 / T_1, T_2, T_4, T_8, T_12, T_16; Section 6's
+    # comparison of the iterative models), each on its own program
+    a_dev, b_dev = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    for key, kw in (("exp_model", {"model": "exp"}),
+                    ("skip4_model", {"model": "skip", "skip": 4})):
+        prog = Program("iteration", [a_dev, b_dev,
+                                     torch.zeros((n, p), dtype=torch.float32, device="cuda")],
+                       k=k, r_max=2, **kw)
+        replace_row(0)
+        replace_row(1)
+        out[f"{key}_ms_per_row_replacement"] = _event_ms(lambda j: replace_row(2 + j), steps)
+        prog.sync()
+        prog.close()
     out["speedup_vs_bf16x9_reeval"] = out["reeval_bf16x9_ms"] / inc
     out["note"] = ("incremental: the rank-2 dA and rank-1 dB of a row replacement; "
                    "re-evaluation: T_i = A T_{i-1} + B for i = 1..k")
