@@ -187,8 +187,8 @@ linview_status linview_apply_row_block(linview_program* prog, int64_t kr, const 
  *              NT + 2 = T_0, then the auxiliary views NT + 2 + l = P_{2^l} and
  *              NT + 2 + log2(s) + l = S'_{2^l} (l = 1..log2 s), with
  *              T_2h = P_h T_h + S_h B (h < s), T_i = P_s T_{i-s} + S_s B (i > s),
- *              S_h = I + S'_h - P_h; updates to B (dT_i = P dT_j + S dB) are
- *              built, the adjoints for the linear model only (EUNSUPPORTED here)
+ *              S_h = I + S'_h - P_h; updates to B: dT_i = P dT_j + S dB; the
+ *              adjoints recompute T_0 .. T_k from (A, B, T_0) first
  *   OLS:       0 = W (n x n), 1 = beta (n x p), 2 = X^T Y (n x p), 3 = X (m x n)
  */
 int linview_num_views(const linview_program* prog);

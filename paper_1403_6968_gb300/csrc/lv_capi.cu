@@ -143,6 +143,8 @@ struct linview_program {
   void* What = nullptr;               // n x Rcap, column-major (fs)
   void* XtV = nullptr;                // (r_max k) x Rcap
   int ie_s = 0, ie_Ls = 0, ie_NT = 0;  // skip step s (k/2 for EXP), log2 s, number of T views
+  void* Tfull = nullptr;  // T_0 .. T_k recomputed for the adjoint (exponential / skip)
+  int64_t ldTf = 0;
   int64_t ldG = 0;
   // power adjoint work
   void* Gw0 = nullptr;
@@ -2211,8 +2213,6 @@ static linview_status adjoint_iteration(linview_program* p, const void* Gk, int6
                                         int64_t ld_dT0, void* stream) {
   if (!p) return fail(LINVIEW_EINVAL, "null program");
   if (p->d.kind != LINVIEW_ITERATION) return fail(LINVIEW_EINVAL, "not an iteration program");
-  if (iter_exp(p))
-    return fail(LINVIEW_EUNSUPPORTED, "the adjoint is built for the linear model (views T_1..T_k)");
   const int64_t n = p->d.n, pp = p->d.p;
   const int k = p->d.k;
   if ((dA && ld_dA < n) || (dB && ld_dB < pp) || (Gk && ldg < pp) || (dT0 && ld_dT0 < pp))
@@ -2227,11 +2227,33 @@ static linview_status adjoint_iteration(linview_program* p, const void* Gk, int6
   const int e = p->elem;
   char* G = static_cast<char*>(p->Gpanel);
   char* T = static_cast<char*>(p->Tpanel);
+  int64_t ldT = p->ldT;
   View& a = p->views[0];
+  if (iter_exp(p)) {
+    // the exponential and skip models keep only some T_i: the reverse pass
+    // needs T_0 .. T_k, recomputed here as T_i = A T_{i-1} + B (the same
+    // function of (A, B, T_0), so the same gradient)
+    if (!p->Tfull) {
+      p->ldTf = rup((int64_t)(k + 1) * pp, 64);
+      LV_TRY(dalloc(p, (size_t)n * p->ldTf * p->elem, &p->Tfull));
+    }
+    T = static_cast<char*>(p->Tfull);
+    ldT = p->ldTf;
+    const View& t0 = p->views[p->ie_NT + 2];
+    LV_CUDA(cudaMemcpy2DAsync(T, ldT * e, t0.ptr, t0.ld * e, pp * e, n, cudaMemcpyDeviceToDevice,
+                              s));
+    for (int i = 1; i <= k; ++i) {
+      char* ti = T + (size_t)i * pp * e;
+      LV_CUDA(cudaMemcpy2DAsync(ti, ldT * e, p->Bm, p->ldB * e, pp * e, n,
+                                cudaMemcpyDeviceToDevice, s));
+      LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, a.ptr, a.ld, T + (size_t)(i - 1) * pp * e,
+                     ldT, 1.0, ti, ldT, s, mode));
+    }
+  }
   // G_k = seed; G_i = A^T G_{i+1}
   void* gk = G + (size_t)(k - 1) * pp * e;
   const void* src = Gk ? Gk : T + (size_t)k * pp * e;
-  const int64_t lds = Gk ? ldg : p->ldT;
+  const int64_t lds = Gk ? ldg : ldT;
   if (e == 4)
     LV_CUDA(launch_scale_copy<float>(static_cast<float*>(gk), p->ldG,
                                      static_cast<const float*>(src), lds, Gk ? 1.0f : 2.0f,
@@ -2262,7 +2284,7 @@ static linview_status adjoint_iteration(linview_program* p, const void* Gk, int6
   }
   if (dA) {
     // dA = [G_1 .. G_k] [T_0 .. T_{k-1}]^T, one GEMM with inner dimension k p
-    LV_TRY(gemm_rm(p, false, true, n, n, (int64_t)k * pp, 1.0, G, p->ldG, T, p->ldT, 0.0, dA,
+    LV_TRY(gemm_rm(p, false, true, n, n, (int64_t)k * pp, 1.0, G, p->ldG, T, ldT, 0.0, dA,
                    ld_dA, s, mode));
   }
   if (dT0) {

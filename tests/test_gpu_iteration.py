@@ -300,7 +300,28 @@ def test_iteration_exp_model_errors():
     with pytest.raises(LinviewError):
         _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=4, precision="f64", model="exp",
               strategy="hybrid")
-    prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=4, precision="f64", model="exp")
-    with pytest.raises(LinviewError) as e:
-        prog.adjoint_iteration()
-    assert e.value.status == _lib.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("prec,model,s", [("f64", "exp", 4), ("f64", "skip", 2), ("f32", "skip", 4)])
+def test_iteration_adjoint_exp_and_skip_models(prec, model, s):
+    """The adjoint of L = ||T_k||_F^2 does not depend on the iterative model:
+    exponential and skip programs (which keep only some T_i) give the oracle's
+    gradients after updates."""
+    n, p, k = 256, 8, 8
+    dt = np.float64 if prec == "f64" else np.float32
+    a, b, t0 = li.iteration_inputs(n, p, seed=77, dtype=dt)
+    kw = {"model": "exp"} if model == "exp" else {"model": "skip", "skip": s}
+    prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=k, r_max=2, precision=prec, **kw)
+    acur = a.astype(np.float64)
+    for u, v in li.lowrank_update_stream(n, 2, 2, seed=78, dtype=dt):
+        prog.apply_delta(_dev(u), _dev(v))
+        acur += u.astype(np.float64) @ v.astype(np.float64).T
+    tdt = torch.float64 if prec == "f64" else torch.float32
+    dA = torch.zeros((n, n), dtype=tdt, device="cuda")
+    dB = torch.zeros((n, p), dtype=tdt, device="cuda")
+    prog.adjoint_iteration(dA, dB)
+    torch.cuda.synchronize()
+    ra, rb, _ = oi.adjoint(acur, b.astype(np.float64), t0.astype(np.float64), k)
+    tol = 1e-10 if prec == "f64" else 1e-4
+    assert rel_frob(dA.cpu().numpy(), ra) <= tol
+    assert rel_frob(dB.cpu().numpy(), rb) <= tol
