@@ -241,6 +241,31 @@ def test_full_size_sampled_rows():
     check()
 
 
+def test_full_size_bench_configuration():
+    """The bench's own program and launch configuration (A^16 and S', n = 8192,
+    FP32, r_max = 1: in-pass suffix sums, sums passes on the side stream, graph
+    replays) after a stream of row updates; sampled rows, including the
+    updated ones, vs the oracle computed row by row."""
+    n, k = 8192, 16
+    a = li.power_matrix(n, seed=0, dtype=np.float32)
+    prog = _prog("power_sum", [_dev(a)], k=k, r_max=1)
+    acur = a.astype(np.float64)
+    ups = li.row_update_stream(n, 8, seed=5, dtype=np.float32)
+    for i, v in ups:
+        prog.apply_row_delta(i, _dev(v))
+        acur[i] += v
+    prog.sync()
+    rows = sorted({0, 4097, n - 1} | {int(i) for i, _ in ups[:3]})
+    pr, sr = op.power_rows(acur, rows, k)
+    L = 4
+    for j in range(L + 1):
+        got = prog.read_view_host(j)[rows]
+        assert rel_frob(got, pr[1 << j]) <= TOL["f32"], (j, rel_frob(got, pr[1 << j]))
+    for j in range(1, L + 1):
+        got = prog.read_view_host(L + j)[rows]
+        assert rel_frob(got, sr[1 << j]) <= TOL["f32"], j
+
+
 def test_profiling_inside_graph_replays():
     """Per-pass timing runs inside the replayed graphs (instrumented copies)
     and changes no result bit."""
