@@ -55,6 +55,7 @@ def _args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-rank4", action="store_true")
     ap.add_argument("--no-ksweep", action="store_true")
+    ap.add_argument("--no-ols", action="store_true", help="skip the OLS row-block section")
     ap.add_argument("--no-general", action="store_true")
     return ap.parse_args()
 
@@ -458,6 +459,8 @@ def run_ours(args):
     if not args.no_general:
         section("iteration_p_sweep", lambda: iteration_p_sweep(args, seed=rank))
         section("gd_regression", lambda: gd_regression(seed=rank))
+    if not args.no_ols:
+        section("ols_row_blocks", lambda: ols_sweep(seed=rank))
     if rank == 0 and not args.no_serving:
         section("serving", lambda: serving_sweep(args, seed=rank))
         section("zipf_batches", lambda: zipf_batches(args, seed=rank))
@@ -697,6 +700,42 @@ def gd_regression(seed=0, n=4096, m=4096, p=1024, k=16, steps=6):
     out["note"] = ("incremental: the rank-2 dA and rank-1 dB of a row replacement; "
                    "re-evaluation: T_i = A T_{i-1} + B for i = 1..k")
     return out
+
+
+def ols_sweep(seed=0, m=65536, n=4096, p=16, ks=(1, 4, 16), steps=6):
+    """OLS (Section 4.1) at m = 65536, n = 4096, p = 16: X ~ N(0, 1) with a
+    fixed 10% of its columns scaled by 1e-2 (kappa(X^T X) ~ 3e4), Y ~ N(0, 1);
+    an update replaces k rows of X by fresh rows with the same scaling.  Per
+    k: the incremental refresh of W = (X^T X)^-1 and beta (block Woodbury,
+    FP32 views, FP64 2k x 2k core) against the re-evaluation (FP64 X^T X by
+    row chunks, Cholesky inverse)."""
+    import numpy as np
+    import torch
+    import linview_inputs as li
+    from paper_1403_6968_gb300 import Program
+
+    x, y, _ = li.ols_inputs(m, n, p, seed=seed, dtype=np.float32)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    rows = []
+    for k in ks:
+        prog = Program("ols", [xd, yd], k=k)
+        ups = li.ols_row_replacements(m, n, k, steps + 2, seed=seed + k, dtype=np.float32)
+        dev = [(r_, torch.from_numpy(nw).cuda()) for r_, nw in ups]
+        for r_, nw in dev[:2]:
+            prog.apply_row_block(r_, nw)
+        inc = _event_ms(lambda j: prog.apply_row_block(*dev[2 + j]), steps)
+        prog.reeval()
+        re = _event_ms(lambda j: prog.reeval(), 1)
+        prog.sync()
+        prog.close()
+        # W read twice and written once (two passes), 4 bytes per entry
+        gbs = 3.0 * n * n * 4 / (inc / 1e3) / 1e9
+        rows.append({"k": k, "incremental_ms": inc, "reeval_fp64_ms": re,
+                     "speedup": re / inc, "w_pass_gbs": gbs})
+    return {"m": m, "n": n, "p": p, "rows": rows,
+            "note": "incremental: block Woodbury on W (FP32, two passes) with an FP64 2k x 2k "
+                    "core and the beta refresh; re-evaluation: FP64 X^T X, Cholesky inverse, "
+                    "beta = W X^T Y"}
 
 
 def serving_sweep(args, seed=0):
