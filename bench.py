@@ -461,6 +461,8 @@ def run_ours(args):
         section("gd_regression", lambda: gd_regression(seed=rank))
     if not args.no_ols:
         section("ols_row_blocks", lambda: ols_sweep(seed=rank))
+    if not args.no_general:
+        section("iteration_adjoint", lambda: iteration_adjoint(seed=rank))
     if rank == 0 and not args.no_serving:
         section("serving", lambda: serving_sweep(args, seed=rank))
         section("zipf_batches", lambda: zipf_batches(args, seed=rank))
@@ -699,6 +701,41 @@ def gd_regression(seed=0, n=4096, m=4096, p=1024, k=16, steps=6):
     out["speedup_vs_bf16x9_reeval"] = out["reeval_bf16x9_ms"] / inc
     out["note"] = ("incremental: the rank-2 dA and rank-1 dB of a row replacement; "
                    "re-evaluation: T_i = A T_{i-1} + B for i = 1..k")
+    return out
+
+
+def iteration_adjoint(seed=0, n=8192, p=64, k=16, r=2, steps=6):
+    """The differentiation workload: T_i = A T_{i-1} + B, n = 8192, p = 64,
+    k = 16, rank-2 updates of A (U, V ~ N(0, 0.01^2)): the incremental
+    refresh of T_1..T_16, the re-evaluation, and the adjoint of
+    L = ||T_16||_F^2 (dL/dA and dL/dB: 15 products A^T G and one
+    n x n x k p GEMM)."""
+    import numpy as np
+    import torch
+    import linview_inputs as li
+    from paper_1403_6968_gb300 import Program
+
+    a, b, t0 = li.iteration_inputs(n, p, seed=seed, dtype=np.float32)
+    prog = Program("iteration", [torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(),
+                                 torch.from_numpy(t0).cuda()], k=k, r_max=r)
+    ups = [tuple(torch.from_numpy(x).cuda() for x in uv)
+           for uv in li.lowrank_update_stream(n, r, steps + 2, seed=seed + 1, dtype=np.float32)]
+    for u, v in ups[:2]:
+        prog.apply_delta(u, v)
+    inc = _event_ms(lambda j: prog.apply_delta(*ups[2 + j]), steps)
+    dA = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    dB = torch.empty((n, p), dtype=torch.float32, device="cuda")
+    prog.adjoint_iteration(dA, dB)
+    adj = _event_ms(lambda j: prog.adjoint_iteration(dA, dB), 3)
+    out = {"n": n, "p": p, "k": k, "rank": r, "incremental_ms": inc, "adjoint_ms": adj}
+    for mode in ("bf16x9", "tf32", "fp32"):
+        prog.set_reeval_mode(mode)
+        prog.reeval()
+        out[f"reeval_{mode}_ms"] = _event_ms(lambda j: prog.reeval(), 2)
+    prog.sync()
+    prog.close()
+    out["note"] = ("incremental: rank-2 dA, linear model with Krylov reuse (15 products of A "
+                   "with the newest 2 columns); adjoint: dL/dA and dL/dB of ||T_16||_F^2")
     return out
 
 
