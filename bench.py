@@ -459,6 +459,7 @@ def run_ours(args):
     if not args.no_general:
         section("iteration_p_sweep", lambda: iteration_p_sweep(args, seed=rank))
         section("gd_regression", lambda: gd_regression(seed=rank))
+    section("small_fp64", lambda: small_fp64(seed=rank))
     if not args.no_ols:
         section("ols_row_blocks", lambda: ols_sweep(seed=rank))
     if not args.no_general:
@@ -702,6 +703,35 @@ def gd_regression(seed=0, n=4096, m=4096, p=1024, k=16, steps=6):
     out["note"] = ("incremental: the rank-2 dA and rank-1 dB of a row replacement; "
                    "re-evaluation: T_i = A T_{i-1} + B for i = 1..k")
     return out
+
+
+def small_fp64(seed=0, n=256, k=8, steps=20):
+    """The small FP64 case: A^8 (views A, A^2, A^4, A^8), n = 256, rank-1 row
+    updates; everything is L2-resident, so this is latency (launches and
+    dependent small kernels), reported per refresh."""
+    import numpy as np
+    import torch
+    import linview_inputs as li
+    from paper_1403_6968_gb300 import Program
+
+    a = li.power_matrix(n, seed=seed, dtype=np.float64)
+    prog = Program("power", [torch.from_numpy(a).cuda()], k=k, precision="f64")
+    ups = [(i, torch.from_numpy(v).cuda())
+           for i, v in li.row_update_stream(n, steps + 3, seed=seed + 1, dtype=np.float64)]
+    for i, v in ups[:3]:
+        prog.apply_row_delta(i, v)
+    stream = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for t in range(steps):
+        prog.apply_row_delta(*ups[3 + t])
+        evs[t + 1].record(stream)
+    torch.cuda.synchronize()
+    lat = [evs[t].elapsed_time(evs[t + 1]) * 1e3 for t in range(steps)]
+    prog.close()
+    return {"n": n, "k": k, "precision": "f64", "p50_us": float(np.median(lat)),
+            "p99_us": float(np.percentile(lat, 99)), "steps": steps}
 
 
 def iteration_adjoint(seed=0, n=8192, p=64, k=16, r=2, steps=6):
