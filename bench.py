@@ -376,13 +376,17 @@ def run_ours(args):
     if args.reeval_steps > 0:
         samp = [0, n // 3, n - 1]
 
+        # every view: P_1 .. P_16 (ids 0..L), S'_2 .. S'_16 (ids L+1..2L)
+        vname = {j: f"P{1 << j}" for j in range(L + 1)}
+        vname.update({L + j: f"S{1 << j}" for j in range(1, L + 1)})
+
         def rows_of():
             torch.cuda.synchronize()
-            return {j: prog.read_view_rows(j, 0, n)[samp].astype(np.float64) for j in (L, 2 * L)}
+            return {j: prog.read_view_rows(j, 0, n)[samp].astype(np.float64) for j in vname}
 
         def rel(x, y):
-            return {("P16" if j == L else "S16"): float(np.linalg.norm(x[j] - y[j]) /
-                                                        np.linalg.norm(y[j])) for j in x}
+            return {vname[j]: float(np.linalg.norm(x[j] - y[j]) / np.linalg.norm(y[j]))
+                    for j in x}
 
         inc_rows = rows_of()
         prog.set_reeval_mode("fp32")
