@@ -93,6 +93,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     fence_mbar_init();
   }
   __syncthreads();
+  // launched with programmatic stream serialisation: everything below may
+  // read what the kernel before wrote
+  griddep_wait();
+  griddep_launch_dependents();
 
   // boxes of this strip that lie inside the matrix
   int nbox = 0;
@@ -344,6 +348,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     fence_mbar_init();
   }
   __syncthreads();
+  // launched with programmatic stream serialisation: everything below may
+  // read what the kernel before wrote
+  griddep_wait();
+  griddep_launch_dependents();
   int nbox = 0;
 #pragma unroll
   for (int b = 0; b < NB; ++b) nbox += (strip0 + b * BOXC < n) ? 1 : 0;
@@ -549,12 +557,8 @@ static cudaError_t launch_fused_t(const PassParams& p, const CUtensorMap& tm, cu
         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (configured != cudaSuccess) return configured;
   }
-  if constexpr (kWs) {
-    const cudaError_t e = launch_pdl(kfn, p.gC * p.gR, kThreads, smem, s, tm, p);
-    if (e != cudaSuccess) return e;
-  } else {
-    kfn<<<p.gC * p.gR, kThreads, smem, s>>>(tm, p);
-  }
+  const cudaError_t e = launch_pdl(kfn, p.gC * p.gR, kThreads, smem, s, tm, p);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -608,12 +612,8 @@ static cudaError_t launch_update_t(const PassParams& p, const CUtensorMap& tm, c
         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (configured != cudaSuccess) return configured;
   }
-  if constexpr (kWs) {
-    const cudaError_t e = launch_pdl(kfn, p.gC * p.gR, kThreads, smem, s, tm, p);
-    if (e != cudaSuccess) return e;
-  } else {
-    kfn<<<p.gC * p.gR, kThreads, smem, s>>>(tm, p);
-  }
+  const cudaError_t e = launch_pdl(kfn, p.gC * p.gR, kThreads, smem, s, tm, p);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
