@@ -795,18 +795,26 @@ def ols_sweep(seed=0, m=65536, n=4096, p=16, ks=(1, 4, 16), steps=6):
         for r_, nw in dev[:2]:
             prog.apply_row_block(r_, nw)
         inc = _event_ms(lambda j: prog.apply_row_block(*dev[2 + j]), steps)
+        prog.sync()
+        w_inc, b_inc = prog.read_view_host(0), prog.read_view_host(1)
         prog.reeval()
         re = _event_ms(lambda j: prog.reeval(), 1)
         prog.sync()
+        w_re, b_re = prog.read_view_host(0), prog.read_view_host(1)
         prog.close()
+        errs = {name: float(np.linalg.norm((a.astype(np.float64) - b.astype(np.float64)).ravel())
+                            / np.linalg.norm(b.astype(np.float64).ravel()))
+                for name, a, b in (("W", w_inc, w_re), ("beta", b_inc, b_re))}
         # W read twice and written once (two passes), 4 bytes per entry
         gbs = 3.0 * n * n * 4 / (inc / 1e3) / 1e9
         rows.append({"k": k, "incremental_ms": inc, "reeval_fp64_ms": re,
-                     "speedup": re / inc, "w_pass_gbs": gbs})
+                     "speedup": re / inc, "w_pass_gbs": gbs,
+                     "rel_err_vs_reeval": errs})
     return {"m": m, "n": n, "p": p, "rows": rows,
             "note": "incremental: block Woodbury on W (FP32, two passes) with an FP64 2k x 2k "
-                    "core and the beta refresh; re-evaluation: FP64 X^T X, Cholesky inverse, "
-                    "beta = W X^T Y"}
+                    "core and the factored beta refresh (no pass over W); re-evaluation: FP64 "
+                    "X^T X, Cholesky inverse, beta = W X^T Y; rel_err_vs_reeval: the views after "
+                    f"{steps + 2} updates against the re-evaluation that follows them"}
 
 
 def serving_sweep(args, seed=0):

@@ -163,8 +163,12 @@ linview_status linview_apply_row_delta(linview_program* prog, int input_id, int6
  * OLS only: replace ``kr`` distinct rows of X (indices ``rows``, host array)
  * by ``new_rows`` (kr x n, row-major, ld).  Y is unchanged.  W is maintained
  * by block Woodbury with an FP64 2kr x 2kr core (the rank-2kr generalisation
- * of the two Sherman-Morrison steps of Example 3.3), beta = W X^T Y.
- * Errors: EINVAL, ESHAPE (kr > desc.k), ESINGULAR (latched, see linview_sync).
+ * of the two Sherman-Morrison steps of Example 3.3); beta = W X^T Y is
+ * refreshed from the same factors (the delta of a product, Section 3.2), with
+ * no further pass over W.
+ * Errors: EINVAL, ESHAPE (kr > desc.k), ESINGULAR (latched, see linview_sync):
+ * W is then left as it was while X and X^T Y hold the new rows, so the views
+ * no longer agree with X until linview_reeval succeeds.
  */
 linview_status linview_apply_row_block(linview_program* prog, int64_t kr, const int64_t* rows,
                                        const void* new_rows, int64_t ld, int on_device,

@@ -20,6 +20,7 @@
 #include "../../include/linview.h"
 #include "lv_device.cuh"
 #include "lv_internal.h"
+#include "lv_ols.h"
 
 using namespace lv;
 
@@ -157,7 +158,7 @@ struct linview_program {
   void* XtYc = nullptr;   // column-major mirror of X^T Y (n x p, fs)
   void* Gf = nullptr;     // G = W U, column-major n x 2k
   void* Wuf = nullptr;    // -G M^{-1}, column-major n x 2k
-  void* betac = nullptr;  // beta, column-major n x p
+  void* Hols = nullptr;   // Wu^T C', 2k x p (the factored beta refresh)
   void* Yr = nullptr;     // Y rows of the block, k x p
   int64_t* rows_d = nullptr;
   double* Minv = nullptr;
@@ -1611,7 +1612,7 @@ static linview_status ols_create(linview_program* p, const void* const* inputs,
   LV_TRY(dalloc(p, (size_t)p->fs * kk * p->elem, &p->Uar));
   LV_TRY(dalloc(p, (size_t)p->fs * kk * p->elem, &p->Gf));
   LV_TRY(dalloc(p, (size_t)p->fs * kk * p->elem, &p->Wuf));
-  LV_TRY(dalloc(p, (size_t)p->fs * pp * p->elem, &p->betac));
+  LV_TRY(dalloc(p, (size_t)kk * pp * p->elem, &p->Hols));
   LV_TRY(dalloc(p, (size_t)kmax * pp * p->elem, &p->Yr));
   LV_TRY(dalloc(p, sizeof(int64_t) * kmax, &t));
   p->rows_d = static_cast<int64_t*>(t);
@@ -1677,13 +1678,14 @@ static linview_status ols_replace_t(linview_program* p, int kr, const void* nrow
   LV_CUDA(launch_xty_update<T>(static_cast<T*>(xty.ptr), xty.ld, static_cast<T*>(p->XtYc), fs, U,
                                n, pp, kr, static_cast<const T*>(p->Yr), s));
   p->all_launches += 2;
-  LV_TRY(run_products_update<T>(p, w, pp, static_cast<const T*>(p->XtYc), nullptr, nullptr,
-                                nullptr, s));
+  // beta' = beta + (G_1 - G_2) Y_R + G (Wu^T C'): from the factors, no pass over W
   View& beta = p->views[kOlsBeta];
-  LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, pp,
-                                 static_cast<T*>(p->betac), fs, s));
-  LV_CUDA(launch_cm_to_rm<T>(static_cast<const T*>(p->betac), fs, static_cast<T*>(beta.ptr),
-                             beta.ld, n, pp, s));
+  {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_beta_update<T>(static_cast<T*>(beta.ptr), beta.ld, G, Wu,
+                                  static_cast<const T*>(p->XtYc), fs, n, pp, kr,
+                                  static_cast<const T*>(p->Yr), static_cast<T*>(p->Hols), s));
+  }
   p->all_launches += 2;
   return LINVIEW_OK;
 }

@@ -5,14 +5,19 @@
 // (n x 2k) and C = diag(I_k, -I_k); W = Z^{-1} then follows from block
 // Woodbury (the rank-2k form of the paper's two Sherman-Morrison steps):
 //   G = W U,  M = C^{-1} + U^T G (2k x 2k, FP64),  W' = W - G M^{-1} G^T.
-// The view passes (products G = W U, beta = W' X^T Y; update W += G Wu^T)
-// run in the shared pass kernels; this file holds the small pieces: row
-// gather/scatter, the FP64 core inverse, Wu = -G M^{-1}, the X^T Y update and
-// the re-evaluation helpers.
+// beta' = W' C' with C' = X^T Y + D^T Y_R (D = X'_R - X_R) is refreshed from
+// factors only, with no pass over W:
+//   W C' = beta + W D^T Y_R = beta + (G_1 - G_2) Y_R   (G_1, G_2: the halves of G)
+//   W' C' = W C' + G (Wu^T C'),  Wu = -G M^{-1},
+// i.e. the delta rule of a product applied to beta = W (X^T Y).
+// The view passes (G = W U; W += G Wu^T) run in the shared pass kernels;
+// this file holds the small pieces: row gather/scatter, the FP64 core
+// inverse, Wu, the X^T Y and beta updates and the re-evaluation helpers.
 #include <cuda_runtime.h>
 
 #include "lv_device.cuh"
 #include "lv_internal.h"
+#include "lv_ols.h"
 
 namespace lv {
 
@@ -38,88 +43,122 @@ __global__ void scatter_rows_kernel(T* X, int64_t ldx, const int64_t* rows, int 
   X[rows[t] * ldx + j] = src[t * ts + j];
 }
 
-// Minv = (diag(c) + S)^{-1} for the kk x kk FP64 matrix S (row-major) with
-// c = (+1 x kpos, -1 x (kk - kpos)); Gauss-Jordan with partial pivoting in one
-// CTA.  A pivot below 1e-13 * max|entry| latches kStatusSingular.
-__global__ void core_inverse_kernel(const double* S, int kk, int kpos, double* Minv,
-                                    unsigned* status) {
-  extern __shared__ double a[];  // kk x 2kk augmented [M | I]
-  __shared__ int piv;
-  __shared__ double scale;
+// Minv = (diag(c) + S)^{-1} for the kk x kk FP64 matrix S (row-major, kk <=
+// 64) with c = (+1 x kpos, -1 x (kk - kpos)): Gauss-Jordan elimination with
+// partial pivoting on the augmented [M | I] in one CTA of 32 x 16 threads.
+// Each column step reads one copy of the augmented matrix and writes the
+// other: warp 0 picks the pivot (largest magnitude in the column, the first
+// row on ties) and scales the pivot row; then every thread writes its
+// elements of the next copy with the pivot row swapped into place.  Two
+// barriers per column; the FP64 work (about 1.5 kk^3 FMAs) is spread over
+// all 512 threads.  A pivot at or below 1e-13 * max|M| latches
+// kStatusSingular and the result is zero.
+constexpr int kInvTx = 32, kInvTy = 16;
+
+size_t core_inverse_smem(int kk) { return sizeof(double) * ((size_t)4 * kk * kk + 3 * kk); }
+
+__global__ void __launch_bounds__(kInvTx * kInvTy)
+    core_inverse_kernel(const double* S, int kk, int kpos, double* Minv, unsigned* status) {
+  extern __shared__ double inv_sm[];
   const int w = 2 * kk;
-  for (int e = threadIdx.x; e < kk * w; e += blockDim.x) {
-    const int i = e / w, j = e % w;
-    double v;
-    if (j < kk) v = S[i * kk + j] + (i == j ? (i < kpos ? 1.0 : -1.0) : 0.0);
-    else v = (j - kk == i) ? 1.0 : 0.0;
-    a[e] = v;
-  }
+  double* cur = inv_sm;           // kk x w
+  double* nxt = cur + kk * w;     // kk x w
+  double* prow = nxt + kk * w;    // w: the pivot row divided by the pivot
+  double* fcol = prow + w;        // kk: column col before the step
+  __shared__ double wmax[kInvTy];
+  __shared__ int s_piv, s_sing;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  double m = 0.0;
+  for (int i = ty; i < kk; i += kInvTy)
+    for (int j = tx; j < w; j += kInvTx) {
+      double v;
+      if (j < kk) {
+        v = S[i * kk + j] + (i == j ? (i < kpos ? 1.0 : -1.0) : 0.0);
+        m = fmax(m, fabs(v));
+      } else {
+        v = (j - kk == i) ? 1.0 : 0.0;
+      }
+      cur[i * w + j] = v;
+    }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (tx == 0) wmax[ty] = m;
+  if (tx == 0 && ty == 0) s_sing = 0;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int i = 0; i < kk; ++i)
-      for (int j = 0; j < kk; ++j) m = fmax(m, fabs(a[i * w + j]));
-    scale = m;
-  }
-  __syncthreads();
-  bool singular = false;
+  double scale = 0.0;
+  for (int t = 0; t < kInvTy; ++t) scale = fmax(scale, wmax[t]);
+  const double tiny = 1e-13 * scale;
   for (int col = 0; col < kk; ++col) {
-    if (threadIdx.x == 0) {
-      int best = col;
-      double bv = fabs(a[col * w + col]);
-      for (int i = col + 1; i < kk; ++i) {
-        const double v = fabs(a[i * w + col]);
-        if (v > bv) { bv = v; best = i; }
+    if (ty == 0) {
+      double bv = -1.0;
+      int bi = kk;
+      for (int i = col + tx; i < kk; i += kInvTx) {
+        const double v = fabs(cur[i * w + col]);
+        if (v > bv) { bv = v; bi = i; }
       }
-      piv = best;
-      if (!(bv > 1e-13 * scale)) atomicOr(status, kStatusSingular);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (bi >= kk) bi = col;  // the column is all NaN
+      if (!(bv > tiny) && tx == 0) {
+        s_sing = 1;
+        atomicOr(status, kStatusSingular);
+      }
+      const double r = 1.0 / cur[bi * w + col];
+      for (int j = tx; j < w; j += kInvTx) prow[j] = cur[bi * w + j] * r;
+      for (int i = tx; i < kk; i += kInvTx) fcol[i] = cur[i * w + col];
+      if (tx == 0) s_piv = bi;
     }
     __syncthreads();
-    const int pr = piv;
-    if (!(fabs(a[pr * w + col]) > 1e-13 * scale)) singular = true;
-    if (pr != col) {
-      for (int j = threadIdx.x; j < w; j += blockDim.x) {
-        const double t = a[col * w + j];
-        a[col * w + j] = a[pr * w + j];
-        a[pr * w + j] = t;
+    const int piv = s_piv;
+    for (int i = ty; i < kk; i += kInvTy) {
+      const int src = (i == col) ? piv : (i == piv ? col : i);  // rows col and piv swap
+      const double f = fcol[src];
+      const double* a = cur + src * w;
+      double* o = nxt + i * w;
+      for (int j = tx; j < w; j += kInvTx) {
+        double v;
+        if (i == col) v = (j == col) ? 1.0 : prow[j];
+        else if (j == col) v = 0.0;
+        else if (j < col) v = a[j];  // finished columns: prow[j] is 0 there
+        else v = fma(-f, prow[j], a[j]);
+        o[j] = v;
       }
     }
     __syncthreads();
-    const double d = a[col * w + col];
-    __syncthreads();
-    for (int j = threadIdx.x; j < w; j += blockDim.x) a[col * w + j] /= d;
-    __syncthreads();
-    for (int e = threadIdx.x; e < kk * w; e += blockDim.x) {
-      const int i = e / w, j = e % w;
-      if (i != col) {
-        const double f = a[i * w + col];
-        if (j != col) a[e] -= f * a[col * w + j];
-      }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kk; i += blockDim.x)
-      if (i != col) a[i * w + col] = 0.0;
-    __syncthreads();
+    double* t = cur;
+    cur = nxt;
+    nxt = t;
   }
-  for (int e = threadIdx.x; e < kk * kk; e += blockDim.x) {
-    const int i = e / kk, j = e % kk;
-    Minv[e] = singular ? 0.0 : a[i * w + kk + j];
-  }
+  const bool singular = s_sing != 0;
+  for (int i = ty; i < kk; i += kInvTy)
+    for (int j = tx; j < kk; j += kInvTx) Minv[i * kk + j] = singular ? 0.0 : cur[i * w + kk + j];
 }
 
-// Wu(:, c) = - sum_c' G(:, c') Minv(c', c)   (FP64 accumulation)
+// Wu(:, c) = - sum_c' G(:, c') Minv(c', c) in FP64; a thread computes two
+// columns c = 2 blockIdx.y, 2 blockIdx.y + 1 of one row j (kk is even).
 template <typename T>
 __global__ void wu_kernel(const T* G, int64_t fs, int n, int kk, const double* Minv, T* Wu) {
-  extern __shared__ double ms[];
-  for (int e = threadIdx.x; e < kk * kk; e += blockDim.x) ms[e] = Minv[e];
+  __shared__ double ms[64][2];
+  const int c = 2 * blockIdx.y;
+  for (int e = threadIdx.x; e < kk; e += blockDim.x) {
+    ms[e][0] = Minv[e * kk + c];
+    ms[e][1] = Minv[e * kk + c + 1];
+  }
   __syncthreads();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  for (int c = 0; c < kk; ++c) {
-    double acc = 0.0;
-    for (int c2 = 0; c2 < kk; ++c2) acc = fma((double)G[(int64_t)c2 * fs + j], ms[c2 * kk + c], acc);
-    Wu[(int64_t)c * fs + j] = (T)(-acc);
+  double a0 = 0.0, a1 = 0.0;
+  for (int c2 = 0; c2 < kk; ++c2) {
+    const double g = (double)G[(int64_t)c2 * fs + j];
+    a0 = fma(g, ms[c2][0], a0);
+    a1 = fma(g, ms[c2][1], a1);
   }
+  Wu[(int64_t)c * fs + j] = (T)(-a0);
+  Wu[(int64_t)(c + 1) * fs + j] = (T)(-a1);
 }
 
 // X^T Y += (X'_R - X_R)^T Y_R.  U holds X'_R^T in columns [0, k) and X_R^T in
@@ -139,6 +178,48 @@ __global__ void xty_update_kernel(T* xty, int64_t ld, T* xtyc, int64_t fs, const
   }
   xty[(int64_t)j * ld + c] = (T)acc;
   xtyc[(int64_t)c * fs + j] = (T)acc;
+}
+
+// H(c2, c) = sum_j Wu(j, c2) C(j, c) for column-major Wu (n x kk) and C
+// (n x p), column stride fs; one CTA per entry (blockIdx.x = c * kk + c2),
+// per-thread partial sums in T, combined in FP64 in a fixed order.  H is
+// kk x p row-major.
+template <typename T>
+__global__ void __launch_bounds__(256) wtc_kernel(const T* Wu, const T* Cc, int64_t fs, int n,
+                                                  int kk, int p, T* H) {
+  __shared__ double part[8];
+  const int c2 = blockIdx.x % kk, c = blockIdx.x / kk;
+  const T* a = Wu + (int64_t)c2 * fs;
+  const T* b = Cc + (int64_t)c * fs;
+  T acc = 0;
+  for (int j = threadIdx.x; j < n; j += 256) acc += a[j] * b[j];
+  double d = (double)acc;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += part[i];
+    H[c2 * p + c] = (T)t;
+  }
+}
+
+// beta(j, c) += sum_t (G(j, t) - G(j, k + t)) Y_R(t, c) + sum_c2 G(j, c2) H(c2, c)
+// (the factored beta refresh above); G column-major (fs), Y_R k x p and H
+// 2k x p row-major, beta row-major (ld).
+template <typename T>
+__global__ void beta_update_kernel(T* beta, int64_t ld, const T* G, int64_t fs, int n, int p,
+                                   int k, const T* Yr, const T* H) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * p) return;
+  int j, c;
+  split_index(idx, p, j, c);
+  T acc = 0;
+  for (int t = 0; t < k; ++t)
+    acc += (G[(int64_t)t * fs + j] - G[(int64_t)(k + t) * fs + j]) * Yr[t * p + c];
+  for (int c2 = 0; c2 < 2 * k; ++c2) acc += G[(int64_t)c2 * fs + j] * H[c2 * p + c];
+  beta[(int64_t)j * ld + c] += acc;
 }
 
 // dst (double, row-major rows x cols, ldd) = (double) src (T, lds)
@@ -202,15 +283,31 @@ cudaError_t launch_scatter_rows(T* X, int64_t ldx, const int64_t* rows, int k, i
 
 cudaError_t launch_core_inverse(const double* S, int kk, int kpos, double* Minv, unsigned* status,
                                 cudaStream_t s) {
-  const size_t smem = sizeof(double) * (size_t)kk * 2 * kk;
-  core_inverse_kernel<<<1, kThreads, smem, s>>>(S, kk, kpos, Minv, status);
+  if (kk < 1 || kk > 64) return cudaErrorInvalidValue;
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(core_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)core_inverse_smem(64));
+  if (configured != cudaSuccess) return configured;
+  core_inverse_kernel<<<1, dim3(kInvTx, kInvTy), core_inverse_smem(kk), s>>>(S, kk, kpos, Minv,
+                                                                           status);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_wu(const T* G, int64_t fs, int n, int kk, const double* Minv, T* Wu,
                       cudaStream_t s) {
-  wu_kernel<T><<<blocks_for(n), kThreads, sizeof(double) * kk * kk, s>>>(G, fs, n, kk, Minv, Wu);
+  if (kk < 2 || kk > 64 || (kk & 1)) return cudaErrorInvalidValue;
+  wu_kernel<T><<<dim3(blocks_for(n), kk / 2), kThreads, 0, s>>>(G, fs, n, kk, Minv, Wu);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_beta_update(T* beta, int64_t ld, const T* G, const T* Wu, const T* Cc,
+                               int64_t fs, int n, int p, int k, const T* Yr, T* H,
+                               cudaStream_t s) {
+  wtc_kernel<T><<<(unsigned)(2 * k * p), 256, 0, s>>>(Wu, Cc, fs, n, 2 * k, p, H);
+  beta_update_kernel<T><<<blocks_for((int64_t)n * p), kThreads, 0, s>>>(beta, ld, G, fs, n, p, k,
+                                                                        Yr, H);
   return cudaGetLastError();
 }
 
@@ -253,6 +350,8 @@ cudaError_t launch_from_double(const double* src, int64_t lds, T* dst, int64_t l
   template cudaError_t launch_scatter_rows<T>(T*, int64_t, const int64_t*, int, int, const T*,    \
                                               int64_t, cudaStream_t);                            \
   template cudaError_t launch_wu<T>(const T*, int64_t, int, int, const double*, T*, cudaStream_t); \
+  template cudaError_t launch_beta_update<T>(T*, int64_t, const T*, const T*, const T*, int64_t,  \
+                                             int, int, int, const T*, T*, cudaStream_t);         \
   template cudaError_t launch_xty_update<T>(T*, int64_t, T*, int64_t, const T*, int, int, int,    \
                                             const T*, cudaStream_t);                             \
   template cudaError_t launch_to_double<T>(const T*, int64_t, double*, int64_t, int, int,         \

@@ -33,7 +33,7 @@ def _dev(x):
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("m,n,p,k", [(2000, 200, 4, 1), (3000, 257, 3, 4), (4096, 512, 16, 16),
-                                     (100, 30, 1, 5)])
+                                     (100, 30, 1, 5), (1500, 100, 2, 32)])
 def test_row_block_updates(prec, m, n, p, k):
     dt = np.float64 if prec == "f64" else np.float32
     x, y, _ = li.ols_inputs(m, n, p, seed=m + n, dtype=dt)
@@ -73,6 +73,23 @@ def test_host_rows_and_errors():
         prog.apply_row_block(list(range(k + 1)), np.zeros((k + 1, n)))
     assert e.value.name == "ESHAPE"
     assert rel_frob(prog.read_view_host(0), ref.w) <= 1e-10
+
+
+def test_singular_core_is_reported():
+    """X = I (16 x 16): replacing row 0 by zeros makes X'^T X' singular, so the
+    Woodbury core M = diag(1, -1) + U^T W U = [[1, 0], [0, 0]] is exactly
+    singular; the device latches ESINGULAR and W is left as it was."""
+    from paper_1403_6968_gb300 import LinviewError
+    n = 16
+    x = np.eye(n)
+    y = np.arange(2 * n, dtype=np.float64).reshape(n, 2)
+    prog = _prog("ols", [x, y], k=1, precision="f64")
+    prog.sync()
+    prog.apply_row_block([0], np.zeros((1, n)))
+    with pytest.raises(LinviewError) as e:
+        prog.sync()
+    assert e.value.name == "ESINGULAR"
+    assert np.array_equal(prog.read_view_host(0), np.eye(n))
 
 
 def test_reeval_resets_to_fresh_inverse():
