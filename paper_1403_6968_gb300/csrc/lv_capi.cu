@@ -407,7 +407,8 @@ static linview_status run_update(linview_program* p, const View& v, const T* Uu,
     pp.suffix_rin = suffix_rin;  // host guarantees a single chunk when set
     pp.tma_store = v.tma_store ? 1 : 0;
     ProfScope ps(p, s, 2.0 * (double)v.rows * (double)v.rows * sizeof(T), 2);
-    LV_CUDA((launch_update<T>(pp, v.tmap, w, s)));
+    // a block after the first follows a pass that wrote this view
+    LV_CUDA((launch_update<T>(pp, v.tmap, w, s, /*programmatic=*/c0 == 0)));
   }
   return LINVIEW_OK;
 }

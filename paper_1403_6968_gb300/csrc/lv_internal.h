@@ -99,12 +99,18 @@ cudaError_t launch_tc_update(const CUtensorMap& tmP, const CUtensorMap& tmA,
                              int num_sms, unsigned* status, cudaStream_t s);
 
 // Launchers (return cudaGetLastError()).  R is the runtime factor width,
-// bucketed internally to a compiled width.
+// bucketed internally to a compiled width.  The passes are launched with
+// programmatic stream serialisation, and the FP32 passes request their first
+// view tiles before waiting on the kernel before them: that kernel must not
+// write the view.  An update launched right after another pass that wrote
+// the same view (the second block of a wide update) takes programmatic =
+// false: a plain launch, which starts only once that kernel has completed.
 template <typename T>
 cudaError_t launch_fused(const PassParams& p, const CUtensorMap& tm, int R, int mode,
                          cudaStream_t s);
 template <typename T>
-cudaError_t launch_update(const PassParams& p, const CUtensorMap& tm, int R, cudaStream_t s);
+cudaError_t launch_update(const PassParams& p, const CUtensorMap& tm, int R, cudaStream_t s,
+                          bool programmatic = true);
 
 // Factor cores and assembly (lv_core.cu).
 // C (r x r, FP64, row-major) = V^T U over n rows; deterministic two-level

@@ -114,7 +114,8 @@ cudaError_t run(lv::PassParams base, const CUtensorMap& tm, int n, int r, int sm
       pp.gC = gu.gC;
       pp.gR = gu.gR;
       pp.rows_per_cta = gu.rows_per_cta;
-      e = launch_update<T>(pp, tm, w, s);
+      // a block after the first follows a pass that wrote this view
+      e = launch_update<T>(pp, tm, w, s, /*programmatic=*/c0 == 0);
       if (e != cudaSuccess) return e;
     }
   }

@@ -587,7 +587,8 @@ cudaError_t launch_fused(const PassParams& p, const CUtensorMap& tm, int R, int 
 }
 
 template <typename T, int R, int COLS>
-static cudaError_t launch_update_t(const PassParams& p, const CUtensorMap& tm, cudaStream_t s) {
+static cudaError_t launch_update_t(const PassParams& p, const CUtensorMap& tm, cudaStream_t s,
+                                   bool programmatic) {
   constexpr int STRIP = kThreads * COLS;
   constexpr bool kWs = std::is_same<T, float>::value;
   const size_t smem =
@@ -612,6 +613,10 @@ static cudaError_t launch_update_t(const PassParams& p, const CUtensorMap& tm, c
         cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (configured != cudaSuccess) return configured;
   }
+  if (!programmatic) {
+    kfn<<<p.gC * p.gR, kThreads, smem, s>>>(tm, p);
+    return cudaGetLastError();
+  }
   const cudaError_t e = launch_pdl(kfn, p.gC * p.gR, kThreads, smem, s, tm, p);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -619,25 +624,25 @@ static cudaError_t launch_update_t(const PassParams& p, const CUtensorMap& tm, c
 
 template <>
 cudaError_t launch_update<float>(const PassParams& p, const CUtensorMap& tm, int R,
-                                 cudaStream_t s) {
-  if (R <= 1) return launch_update_t<float, 1, 2>(p, tm, s);
-  if (R <= 2) return launch_update_t<float, 2, 2>(p, tm, s);
-  if (R <= 4) return launch_update_t<float, 4, 2>(p, tm, s);
-  if (R <= 8) return launch_update_t<float, 8, 2>(p, tm, s);
-  if (R <= 16) return launch_update_t<float, 16, 2>(p, tm, s);
-  if (R <= 32) return launch_update_t<float, 32, 2>(p, tm, s);
+                                 cudaStream_t s, bool programmatic) {
+  if (R <= 1) return launch_update_t<float, 1, 2>(p, tm, s, programmatic);
+  if (R <= 2) return launch_update_t<float, 2, 2>(p, tm, s, programmatic);
+  if (R <= 4) return launch_update_t<float, 4, 2>(p, tm, s, programmatic);
+  if (R <= 8) return launch_update_t<float, 8, 2>(p, tm, s, programmatic);
+  if (R <= 16) return launch_update_t<float, 16, 2>(p, tm, s, programmatic);
+  if (R <= 32) return launch_update_t<float, 32, 2>(p, tm, s, programmatic);
   return cudaErrorInvalidValue;
 }
 
 template <>
 cudaError_t launch_update<double>(const PassParams& p, const CUtensorMap& tm, int R,
-                                  cudaStream_t s) {
-  if (R <= 1) return launch_update_t<double, 1, 2>(p, tm, s);
-  if (R <= 2) return launch_update_t<double, 2, 2>(p, tm, s);
-  if (R <= 4) return launch_update_t<double, 4, 2>(p, tm, s);
-  if (R <= 8) return launch_update_t<double, 8, 2>(p, tm, s);
-  if (R <= 16) return launch_update_t<double, 16, 2>(p, tm, s);
-  if (R <= 32) return launch_update_t<double, 32, 1>(p, tm, s);
+                                  cudaStream_t s, bool programmatic) {
+  if (R <= 1) return launch_update_t<double, 1, 2>(p, tm, s, programmatic);
+  if (R <= 2) return launch_update_t<double, 2, 2>(p, tm, s, programmatic);
+  if (R <= 4) return launch_update_t<double, 4, 2>(p, tm, s, programmatic);
+  if (R <= 8) return launch_update_t<double, 8, 2>(p, tm, s, programmatic);
+  if (R <= 16) return launch_update_t<double, 16, 2>(p, tm, s, programmatic);
+  if (R <= 32) return launch_update_t<double, 32, 1>(p, tm, s, programmatic);
   return cudaErrorInvalidValue;
 }
 

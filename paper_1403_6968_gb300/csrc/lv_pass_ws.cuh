@@ -656,7 +656,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   };
   int issued = 0;
   // first tiles of the view before waiting on the previous kernel (see the
-  // fused pass); the factor rows after
+  // fused pass; a block of a wide update that follows another block on the
+  // same view is launched without programmatic serialisation, so its
+  // predecessor has completed); the factor rows after
   if (warp == 0)
     for (int b = 0; b < S && b < nbatch; ++b) produce_tile(b);
   griddep_wait();
