@@ -377,17 +377,20 @@ static linview_status run_update(linview_program* p, const View& v, const T* Uu,
   float* tB = tcset ? p->tcB2 : p->tcB;
   const CUtensorMap& mA = tcset ? p->tmA2 : p->tmA;
   const CUtensorMap& mB = tcset ? p->tmB2 : p->tmB;
-  for (int c0 = 0; c0 < r; c0 += MU) {
-    const int w = (r - c0 < MU) ? (r - c0) : MU;
+  for (int c0 = 0; c0 < r;) {
+    int w = (r - c0 < MU) ? (r - c0) : MU;
     if constexpr (sizeof(T) == 4) {
-      // blocks wider than the CUDA-core pass sustains go to the tensor cores
-      if (tA && w > kMaxProductR && suffix_rin == 0) {
+      // blocks wider than the CUDA-core pass sustains go to the tensor cores,
+      // up to kMaxTcR columns per pass
+      if (tA && r - c0 > kMaxProductR && suffix_rin == 0) {
+        w = (r - c0 < kMaxTcR) ? (r - c0) : kMaxTcR;
         ProfScope ps(p, s, 2.0 * (double)v.rows * (double)v.rows * sizeof(T), 2);
         LV_CUDA(launch_tc_update(v.tmap_tc, mA, mB, static_cast<float*>(v.ptr), v.ld, tA, tB,
                                  reinterpret_cast<const float*>(Uu) + (int64_t)c0 * p->fs,
                                  reinterpret_cast<const float*>(Wu) + (int64_t)c0 * p->fs, p->fs,
                                  (int)v.rows, w, p->sms, p->status, s));
         p->all_launches++;  // the split kernel
+        c0 += w;
         continue;
       }
     }
@@ -409,6 +412,7 @@ static linview_status run_update(linview_program* p, const View& v, const T* Uu,
     ProfScope ps(p, s, 2.0 * (double)v.rows * (double)v.rows * sizeof(T), 2);
     // a block after the first follows a pass that wrote this view
     LV_CUDA((launch_update<T>(pp, v.tmap, w, s, /*programmatic=*/c0 == 0)));
+    c0 += w;
   }
   return LINVIEW_OK;
 }
@@ -713,16 +717,16 @@ static linview_status powers_create(linview_program* p, const void* const* input
     LV_TRY(dalloc(p, (size_t)tc_split_floats(n) * sizeof(float), &tc));
     p->tcA = static_cast<float*>(tc);
     p->tcB = p->tcA + tc_split_floats(n) / 2;
-    if (!make_tmap_sw128(&p->tmA, p->tcA, 64, n, 64, 128) ||
-        !make_tmap_sw128(&p->tmB, p->tcB, 64, n, 64, 64))
+    if (!make_tmap_sw128(&p->tmA, p->tcA, 128, n, 128, 128) ||
+        !make_tmap_sw128(&p->tmB, p->tcB, 128, n, 128, 32))
       return fail(LINVIEW_EDEVICE, "cuTensorMapEncodeTiled failed for the split factors");
     if (wide_sums) {  // the sums updates on the side stream have their own
       void* tc2 = nullptr;
       LV_TRY(dalloc(p, (size_t)tc_split_floats(n) * sizeof(float), &tc2));
       p->tcA2 = static_cast<float*>(tc2);
       p->tcB2 = p->tcA2 + tc_split_floats(n) / 2;
-      if (!make_tmap_sw128(&p->tmA2, p->tcA2, 64, n, 64, 128) ||
-          !make_tmap_sw128(&p->tmB2, p->tcB2, 64, n, 64, 64))
+      if (!make_tmap_sw128(&p->tmA2, p->tcA2, 128, n, 128, 128) ||
+          !make_tmap_sw128(&p->tmB2, p->tcB2, 128, n, 128, 32))
         return fail(LINVIEW_EDEVICE, "cuTensorMapEncodeTiled failed for the split factors");
     }
   }
@@ -2392,8 +2396,8 @@ linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp
     LV_CUDA(cudaMallocAsync(&tcs, (size_t)tc_split_floats(n) * sizeof(float), s));
     tmp.tcA = static_cast<float*>(tcs);
     tmp.tcB = tmp.tcA + tc_split_floats(n) / 2;
-    if (!make_tmap_sw128(&tmp.tmA, tmp.tcA, 64, n, 64, 128) ||
-        !make_tmap_sw128(&tmp.tmB, tmp.tcB, 64, n, 64, 64) ||
+    if (!make_tmap_sw128(&tmp.tmA, tmp.tcA, 128, n, 128, 128) ||
+        !make_tmap_sw128(&tmp.tmB, tmp.tcB, 128, n, 128, 32) ||
         !make_tmap_sw128(&v.tmap_tc, P, n, n, ldp, 128)) {
       cudaFreeAsync(tcs, s);
       return fail(LINVIEW_EDEVICE, "tensor map encode failed");

@@ -86,13 +86,14 @@ bool make_tmap(CUtensorMap* out, const void* base, int elem_bytes, int64_t cols,
 bool make_tmap_sw128(CUtensorMap* out, const void* base, int64_t cols, int64_t rows, int64_t ld,
                      int box_rows);
 // Floats of the split-factor scratch of the tensor-core update pass (A_cat
-// then B_cat, n x 64 each).
+// then B_cat, n x 128 each).
 int64_t tc_split_floats(int64_t n);
-// Tensor-core update pass P += U W^T (FP32 view, 17 <= r <= 32 factor
+constexpr int kMaxTcR = 64;  // widest factor block of one tensor-core update pass
+// Tensor-core update pass P += U W^T (FP32 view, 17 <= r <= 64 factor
 // columns, split TF32): splits U, W into the scratch, then one persistent
-// launch over 128 x 64 tiles.  tmP: make_tmap_sw128 over the view P (box
-// rows 128, row stride ldp); tmA / tmB: over A_cat (box rows 128) / B_cat
-// (box rows 64).
+// launch over 128 x 64 tiles (r <= 32) or 128 x 32 tiles (r > 32).  tmP:
+// make_tmap_sw128 over the view P (box rows 128, row stride ldp); tmA / tmB:
+// over A_cat (128 columns, box rows 128) / B_cat (128 columns, box rows 32).
 cudaError_t launch_tc_update(const CUtensorMap& tmP, const CUtensorMap& tmA,
                              const CUtensorMap& tmB, float* P, int64_t ldp, float* Acat,
                              float* Bcat, const float* U, const float* W, int64_t fs, int n, int r,

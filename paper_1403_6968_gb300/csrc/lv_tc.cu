@@ -1,5 +1,5 @@
 // Tensor-core update pass (tcgen05, sm_103a): P += U W^T for a factor block
-// of 17..32 columns, the in-place rank-r refresh of a view (App. A, the
+// of 17..64 columns, the in-place rank-r refresh of a view (App. A, the
 // "P_h += U_h V_h^T" step; the final P_k update) once r is past what the
 // shared-memory broadcasts of the CUDA-core pass sustain at HBM speed.
 //
@@ -8,21 +8,26 @@
 // TF32) and lo = x - hi (exact in FP32), and
 //   U W^T ~= hi(U) hi(W)^T + lo(U) hi(W)^T + hi(U) lo(W)^T
 // accumulated in FP32 in tensor memory: about 2^-22 relative error per
-// product, i.e. FP32 accuracy for the delta.  A = [hi(U) | lo(U)] and
-// B = [hi(W) | lo(W)] (row-major, 32 columns per half, zero padded); the
-// three products are one MMA chain over the K-chunk pairs (hi, hi), (lo, hi),
-// (hi, lo).
+// product, i.e. FP32 accuracy for the delta.  A_cat = [hi(U) | lo(U)] and
+// B_cat = [hi(W) | lo(W)] are row-major n x 128 (hi in columns 0..63, lo in
+// 64..127, zero padded past r); the three products are one MMA chain over
+// the K-chunk pairs (hi, hi), (lo, hi), (hi, lo).
 //
-// Tiles: 128 rows x 64 columns of P.  A persistent grid (one CTA per SM)
-// walks the tiles row-block by row-block; per CTA:
-//   warp 0     TMA producer: A block (48 KB, reloaded when the row block
-//              changes), B tile (double buffered) and P tile (4 stages);
-//   warp 1     allocates 128 TMEM columns (two 64-column FP32 accumulators)
-//              and issues the MMAs from one thread;
+// Two shapes, chosen by the block width r, both 224 KB of shared memory:
+//   RP = 32: tiles of 128 rows x 64 columns of P, A block 32 KB, B tile
+//            16 KB (double buffered), 5 P stages of 32 KB;
+//   RP = 64: tiles of 128 rows x 32 columns, A block 64 KB, B tile 16 KB
+//            (double buffered), 8 P stages of 16 KB.
+// A persistent grid (one CTA per SM) walks the tiles row-block by
+// row-block; per CTA:
+//   warp 0     TMA producer: A block (reloaded when the row block changes),
+//              B tile and P tile;
+//   warp 1     allocates 2 x BN TMEM columns (two FP32 accumulators) and
+//              issues the MMAs from one thread;
 //   warps 2-5  epilogue: TMEM -> registers, + P (shared, 128B-swizzled),
 //              back to shared memory, TMA store (by one thread once the four
 //              warps have arrived on an mbarrier; a stage is released when
-//              its store has been read out, up to 2 stores in flight).
+//              its store has been read out, one store in flight).
 // Every mbarrier wait is bounded; an expired wait latches LINVIEW_ETIMEOUT,
 // aborts the CTA's loops, drains the copies in flight and frees the TMEM.
 #include <cuda_runtime.h>
@@ -36,28 +41,36 @@ namespace lv {
 namespace {
 
 constexpr int kBM = 128;                 // tile rows (MMA M)
-constexpr int kBN = 64;                  // tile columns (MMA N)
-constexpr int kRp = 32;                  // factor columns per block (padded)
-constexpr int kK = 2 * kRp;              // columns of A_cat / B_cat: hi and lo halves
-constexpr int kKC = kK / 32;             // 128-byte K chunks (32 floats): hi, lo
+constexpr int kSplitCols = 128;          // columns of A_cat / B_cat: hi 0..63, lo 64..127
 constexpr int kTcThreads = 192;
-constexpr uint32_t kABytes = kKC * kBM * 128;   // 32 KB
-constexpr uint32_t kBBytes = kKC * kBN * 128;   // 16 KB
-constexpr uint32_t kPBytes = 2 * kBM * 128;     // 32 KB (two 32-column boxes)
-constexpr int kPS = 5;                          // P tile stages
-constexpr int kStoresInFlight = 1;              // TMA stores not yet read out
-constexpr uint32_t kTmemCols = 2 * kBN;         // two accumulators
+constexpr int kStoresInFlight = 1;       // TMA stores not yet read out
 
-// shared-memory layout (offsets from a 1024-byte aligned base)
-constexpr uint32_t kOffA = 0;
-constexpr uint32_t kOffB = kOffA + kABytes;          // 2 buffers
-constexpr uint32_t kOffP = kOffB + 2 * kBBytes;      // kPS buffers
-constexpr uint32_t kOffBar = kOffP + kPS * kPBytes;
-constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;  // + alignment slack
-
-// instruction descriptor: D F32, A/B TF32, both K-major, N = 64, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
+// Shape of one variant: RP factor columns (padded), BN tile columns.
+template <int RP>
+struct TcShape {
+  static constexpr int BN = RP == 32 ? 64 : 32;        // tile columns (MMA N)
+  static constexpr int H = RP / 32;                    // 128-byte K chunks per half
+  static constexpr int KC = 2 * H;                     // chunks: hi 0..H-1, lo H..2H-1
+  static constexpr uint32_t ABytes = KC * kBM * 128;   // A block
+  static constexpr uint32_t BBytes = KC * BN * 128;    // B tile (one buffer)
+  static constexpr int PBoxes = BN / 32;               // 32-column boxes per P tile
+  static constexpr uint32_t PBytes = PBoxes * kBM * 128;
+  static constexpr int PS = RP == 32 ? 5 : 8;          // P tile stages
+  static constexpr uint32_t TmemCols = 2 * BN;         // two accumulators
+  static constexpr uint32_t OffA = 0;
+  static constexpr uint32_t OffB = OffA + ABytes;      // 2 buffers
+  static constexpr uint32_t OffP = OffB + 2 * BBytes;  // PS buffers
+  static constexpr uint32_t OffBar = OffP + PS * PBytes;
+  static constexpr uint32_t SmemBytes = OffBar + 512 + 1024;  // + alignment slack
+  // instruction descriptor: D F32, A/B TF32, both K-major, N = BN, M = 128
+  static constexpr uint32_t Idesc = (1u << 4) | (2u << 7) | (2u << 10) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+  // column of A_cat / B_cat where K chunk kc starts
+  static __host__ __device__ constexpr int chunk_x(int kc) { return (kc / H) * 64 + (kc % H) * 32; }
+};
+constexpr int kMaxPS = 8;
+static_assert(TcShape<32>::SmemBytes <= 232448 && TcShape<64>::SmemBytes <= 232448,
+              "shared memory per CTA");
 
 // shared-memory matrix descriptor: K-major operand in 128-byte swizzled rows,
 // 8-row groups 1024 bytes apart (the layout TMA writes with SWIZZLE_128B)
@@ -115,12 +128,13 @@ __device__ __forceinline__ void tmem_wait_ld() {
 struct TcBars {
   uint64_t a_full;
   uint64_t b_full[2], b_empty[2];
-  uint64_t p_full[kPS], p_empty[kPS];
+  uint64_t p_full[kMaxPS], p_empty[kMaxPS];
   uint64_t acc_full[2], acc_empty[2];
-  uint64_t ep_done[kPS];  // the 4 epilogue warps have written their rows of a P tile
+  uint64_t ep_done[kMaxPS];  // the 4 epilogue warps have written their rows of a P tile
   uint32_t tmem_base;
   int abort;
 };
+static_assert(sizeof(TcBars) <= 512, "barrier block");
 
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                         unsigned* status) {
@@ -131,23 +145,27 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile
 }
 
 // P (n x n, row-major, tensor map tmP: box 32 x 128, 128B swizzle) +=
-// A_cat B_cat^T with A_cat, B_cat n x 64 row-major (tmA: box 32 x 128,
-// tmB: box 32 x 64, both 128B swizzle).
+// A_cat B_cat^T with A_cat, B_cat n x 128 row-major (tmA: box 32 x 128,
+// tmB: box 32 x 32, both 128B swizzle); RP = 32 reads K chunks (hi 0..31,
+// lo 64..95), RP = 64 reads all four.
+template <int RP>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_update_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, float* P, int64_t ldp, int n,
                      unsigned* status) {
+  using Sh = TcShape<RP>;
+  constexpr int BN = Sh::BN, KC = Sh::KC, H = Sh::H, PS = Sh::PS;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   const uint32_t raw = smem_u32(tc_smem_raw);
   unsigned char* base = tc_smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  TcBars* bars = reinterpret_cast<TcBars*>(base + kOffBar);
+  TcBars* bars = reinterpret_cast<TcBars*>(base + Sh::OffBar);
   volatile int* abort_flag = &bars->abort;
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
 
   const int nrb = (n + kBM - 1) / kBM;
-  const int ncb = (n + kBN - 1) / kBN;
+  const int ncb = (n + BN - 1) / BN;
   const long long T = (long long)nrb * ncb;
   const long long t0 = T * blockIdx.x / gridDim.x;
   const long long t1 = T * (blockIdx.x + 1) / gridDim.x;
@@ -164,7 +182,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(&bars->acc_full[i], 1);
       mbar_init(&bars->acc_empty[i], 4);  // one arrival per epilogue warp
     }
-    for (int i = 0; i < kPS; ++i) {
+    for (int i = 0; i < PS; ++i) {
       mbar_init(&bars->p_full[i], 1);
       mbar_init(&bars->p_empty[i], 1);
       mbar_init(&bars->ep_done[i], 4);
@@ -172,10 +190,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     bars->abort = 0;
     fence_mbar_init();
   }
-  if (warp == 1) {  // TMEM: two 64-column FP32 accumulators
+  if (warp == 1) {  // TMEM: two BN-column FP32 accumulators
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&bars->tmem_base)),
-                 "r"(kTmemCols)
+                 "r"(Sh::TmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -199,23 +217,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 status))
             break;
           fence_proxy_async();
-          mbar_arrive_expect_tx(&bars->a_full, kABytes);
-          for (int kc = 0; kc < kKC; ++kc)
-            tma_load_2d(base + kOffA + kc * kBM * 128, &tmA, kc * 32, rb * kBM, &bars->a_full);
+          mbar_arrive_expect_tx(&bars->a_full, Sh::ABytes);
+          for (int kc = 0; kc < KC; ++kc)
+            tma_load_2d(base + Sh::OffA + kc * kBM * 128, &tmA, Sh::chunk_x(kc), rb * kBM,
+                        &bars->a_full);
           ++a_issued;
           cur_rb = rb;
         }
         if (use >= 1 && !tc_wait(&bars->b_empty[buf], (use - 1) & 1, abort_flag, status)) break;
-        mbar_arrive_expect_tx(&bars->b_full[buf], kBBytes);
-        for (int kc = 0; kc < kKC; ++kc)
-          tma_load_2d(base + kOffB + buf * kBBytes + kc * kBN * 128, &tmB, kc * 32, cb * kBN,
-                      &bars->b_full[buf]);
+        mbar_arrive_expect_tx(&bars->b_full[buf], Sh::BBytes);
+        for (int kc = 0; kc < KC; ++kc)
+          for (int sb = 0; sb < BN / 32; ++sb)  // 32-row boxes
+            tma_load_2d(base + Sh::OffB + buf * Sh::BBytes + (kc * BN + sb * 32) * 128, &tmB,
+                        Sh::chunk_x(kc), cb * BN + sb * 32, &bars->b_full[buf]);
         ++b_issued;
-        const int ps = i % kPS, puse = i / kPS;
+        const int ps = i % PS, puse = i / PS;
         if (puse >= 1 && !tc_wait(&bars->p_empty[ps], (puse - 1) & 1, abort_flag, status)) break;
-        mbar_arrive_expect_tx(&bars->p_full[ps], kPBytes);
-        for (int h = 0; h < 2; ++h)
-          tma_load_2d(base + kOffP + ps * kPBytes + h * kBM * 128, &tmP, cb * kBN + 32 * h,
+        mbar_arrive_expect_tx(&bars->p_full[ps], Sh::PBytes);
+        for (int h = 0; h < Sh::PBoxes; ++h)
+          tma_load_2d(base + Sh::OffP + ps * Sh::PBytes + h * kBM * 128, &tmP, cb * BN + 32 * h,
                       rb * kBM, &bars->p_full[ps]);
         ++p_issued;
       }
@@ -225,7 +245,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int j = 0; j < b_issued; ++j)
           mbar_wait_bounded(&bars->b_full[j & 1], (j >> 1) & 1, nullptr);
         for (int j = 0; j < p_issued; ++j)
-          mbar_wait_bounded(&bars->p_full[j % kPS], (j / kPS) & 1, nullptr);
+          mbar_wait_bounded(&bars->p_full[j % PS], (j / PS) & 1, nullptr);
       }
     }
   } else if (warp == 1) {
@@ -244,19 +264,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (!tc_wait(&bars->b_full[buf], use & 1, abort_flag, status)) break;
         if (use >= 1 && !tc_wait(&bars->acc_empty[buf], (use - 1) & 1, abort_flag, status)) break;
         tc_fence_after();
-        const uint32_t d = tmem + buf * kBN;
-        const uint32_t a0 = smem_u32(base + kOffA);
-        const uint32_t b0 = smem_u32(base + kOffB + buf * kBBytes);
-        // (A chunk, B chunk): hi*hi, lo*hi, hi*lo
+        const uint32_t d = tmem + buf * BN;
+        const uint32_t a0 = smem_u32(base + Sh::OffA);
+        const uint32_t b0 = smem_u32(base + Sh::OffB + buf * Sh::BBytes);
+        // (A half, B half): hi*hi, lo*hi, hi*lo; each over the H chunks of a half
         constexpr int kPairA[3] = {0, 1, 0};
         constexpr int kPairB[3] = {0, 0, 1};
 #pragma unroll
         for (int pr = 0; pr < 3; ++pr) {
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {  // K = 8 per MMA: 32 bytes of a 128-byte row
-            const uint64_t ad = sw128_desc(a0 + kPairA[pr] * kBM * 128 + kk * 32);
-            const uint64_t bd = sw128_desc(b0 + kPairB[pr] * kBN * 128 + kk * 32);
-            tc_mma(d, ad, bd, kIdesc, (pr | kk) != 0 ? 1u : 0u);
+          for (int hk = 0; hk < H; ++hk) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {  // K = 8 per MMA: 32 bytes of a 128-byte row
+              const uint64_t ad = sw128_desc(a0 + (kPairA[pr] * H + hk) * kBM * 128 + kk * 32);
+              const uint64_t bd = sw128_desc(b0 + (kPairB[pr] * H + hk) * BN * 128 + kk * 32);
+              tc_mma(d, ad, bd, Sh::Idesc, (pr | hk | kk) != 0 ? 1u : 0u);
+            }
           }
         }
         tc_commit(&bars->b_empty[buf]);
@@ -282,16 +305,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const long long t = t0 + i;
       const int rb = (int)(t / ncb), cb = (int)(t % ncb);
       const int buf = i & 1, use = i >> 1;
-      const int ps = i % kPS, puse = i / kPS;
+      const int ps = i % PS, puse = i / PS;
       bool ok = tc_wait(&bars->acc_full[buf], use & 1, abort_flag, status) &&
                 tc_wait(&bars->p_full[ps], puse & 1, abort_flag, status);
       // the TMEM loads below are warp-collective: the warp leaves together
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      float acc[kBN];
-      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + buf * kBN;
+      float acc[BN];
+      const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + buf * BN;
 #pragma unroll
-      for (int q = 0; q < kBN / 16; ++q) {
+      for (int q = 0; q < BN / 16; ++q) {
         float v[16];
         tmem_ld16(ta + q * 16, v);
 #pragma unroll
@@ -301,13 +324,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
-      // P tile: two 32-column boxes, rows of 128 bytes, 16-byte chunk j of
-      // row r stored at chunk j ^ (r % 8)
-      unsigned char* pt = base + kOffP + ps * kPBytes;
+      // P tile: BN / 32 boxes of 32 columns, rows of 128 bytes, 16-byte chunk
+      // j of row r stored at chunk j ^ (r % 8)
+      unsigned char* pt = base + Sh::OffP + ps * Sh::PBytes;
       const bool direct = ragged && cb == ncb - 1;
       const int grow = rb * kBM + row;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < Sh::PBoxes; ++h) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           float4* q = reinterpret_cast<float4*>(pt + h * kBM * 128 + row * 128 +
@@ -321,7 +344,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           if (!direct) {
             *q = pv;
           } else if (grow < n) {
-            const int gc = cb * kBN + c;
+            const int gc = cb * BN + c;
             float* dst = P + (int64_t)grow * ldp + gc;
             if (gc + 0 < n) dst[0] = pv.x;
             if (gc + 1 < n) dst[1] = pv.y;
@@ -340,13 +363,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (leader) {
         if (tc_wait(&bars->ep_done[ps], puse & 1, abort_flag, status)) {
           if (!direct) {
-            tma_store_2d(&tmP, pt, cb * kBN, rb * kBM);
-            tma_store_2d(&tmP, pt + kBM * 128, cb * kBN + 32, rb * kBM);
+            for (int h = 0; h < Sh::PBoxes; ++h)
+              tma_store_2d(&tmP, pt + h * kBM * 128, cb * BN + 32 * h, rb * kBM);
           }
           bulk_commit();  // one group per tile (empty for a ragged edge tile)
           // the store group of tile i - kStoresInFlight has read its stage
           bulk_wait_read<kStoresInFlight>();
-          if (i >= kStoresInFlight) mbar_arrive(&bars->p_empty[(i - kStoresInFlight) % kPS]);
+          if (i >= kStoresInFlight) mbar_arrive(&bars->p_empty[(i - kStoresInFlight) % PS]);
         } else {
           stop = true;
         }
@@ -360,23 +383,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kTmemCols)
+                 "r"(Sh::TmemCols)
                  : "memory");
   }
 }
 
-// A_cat = [hi(U) | lo(U)], B_cat = [hi(W) | lo(W)] (n x 64, row-major) from
-// column-major U, W (column stride fs, r <= 32 columns).
-// A block of 256 threads transposes 32 rows through shared memory: reads run
-// down the factor columns, writes along the rows.
+// A_cat = [hi(U) | lo(U)], B_cat = [hi(W) | lo(W)] (n x 128, row-major: hi in
+// columns 0..63, lo in 64..127) from column-major U, W (column stride fs,
+// r <= 64 columns); the first ``half`` columns of each half are written (32
+// or 64: the columns the variant reads), zero past r.  A block of 256
+// threads transposes 32 rows through shared memory: reads run down the
+// factor columns, writes along the rows.
 __global__ void __launch_bounds__(256) tc_split_kernel(const float* __restrict__ U,
                                                        const float* __restrict__ W, int64_t fs,
-                                                       int n, int r, float* __restrict__ Acat,
+                                                       int n, int r, int half,
+                                                       float* __restrict__ Acat,
                                                        float* __restrict__ Bcat) {
-  __shared__ float su[kRp][33], sw[kRp][33];
+  __shared__ float su[64][33], sw[64][33];
   const int row0 = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 warps
-  for (int c = ty; c < kRp; c += 8) {
+  for (int c = ty; c < half; c += 8) {
     const int i = row0 + tx;
     const bool ok = c < r && i < n;
     su[c][tx] = ok ? U[(int64_t)c * fs + i] : 0.f;
@@ -386,15 +412,17 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const float* __restrict__
   for (int j = ty; j < 32; j += 8) {
     const int i = row0 + j;
     if (i >= n) break;
-    const float u = su[tx][j], w = sw[tx][j];
-    const float uh = __uint_as_float(__float_as_uint(u) & 0xFFFFE000u);
-    const float wh = __uint_as_float(__float_as_uint(w) & 0xFFFFE000u);
-    float* a = Acat + (int64_t)i * kK;
-    float* b = Bcat + (int64_t)i * kK;
-    a[tx] = uh;
-    a[kRp + tx] = u - uh;
-    b[tx] = wh;
-    b[kRp + tx] = w - wh;
+    float* a = Acat + (int64_t)i * kSplitCols;
+    float* b = Bcat + (int64_t)i * kSplitCols;
+    for (int c = tx; c < half; c += 32) {
+      const float u = su[c][j], w = sw[c][j];
+      const float uh = __uint_as_float(__float_as_uint(u) & 0xFFFFE000u);
+      const float wh = __uint_as_float(__float_as_uint(w) & 0xFFFFE000u);
+      a[c] = uh;
+      a[64 + c] = u - uh;
+      b[c] = wh;
+      b[64 + c] = w - wh;
+    }
   }
 }
 
@@ -427,21 +455,31 @@ bool make_tmap_sw128(CUtensorMap* out, const void* base, int64_t cols, int64_t r
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int64_t tc_split_floats(int64_t n) { return 2 * n * kK; }
+int64_t tc_split_floats(int64_t n) { return 2 * n * kSplitCols; }
+
+template <int RP>
+static cudaError_t launch_tc_t(const CUtensorMap& tmP, const CUtensorMap& tmA,
+                               const CUtensorMap& tmB, float* P, int64_t ldp, int n, int num_sms,
+                               unsigned* status, cudaStream_t s) {
+  using Sh = TcShape<RP>;
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      tc_update_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SmemBytes);
+  if (configured != cudaSuccess) return configured;
+  const long long T = (long long)((n + kBM - 1) / kBM) * ((n + Sh::BN - 1) / Sh::BN);
+  const int grid = (int)(T < num_sms ? T : num_sms);
+  tc_update_kernel<RP><<<grid, kTcThreads, Sh::SmemBytes, s>>>(tmP, tmA, tmB, P, ldp, n, status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tc_update(const CUtensorMap& tmP, const CUtensorMap& tmA,
                              const CUtensorMap& tmB, float* P, int64_t ldp, float* Acat,
                              float* Bcat, const float* U, const float* W, int64_t fs, int n, int r,
                              int num_sms, unsigned* status, cudaStream_t s) {
-  if (r < 1 || r > kRp) return cudaErrorInvalidValue;
-  tc_split_kernel<<<(n + 31) / 32, 256, 0, s>>>(U, W, fs, n, r, Acat, Bcat);
-  static const cudaError_t configured = cudaFuncSetAttribute(
-      tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-  if (configured != cudaSuccess) return configured;
-  const long long T = (long long)((n + kBM - 1) / kBM) * ((n + kBN - 1) / kBN);
-  const int grid = (int)(T < num_sms ? T : num_sms);
-  tc_update_kernel<<<grid, kTcThreads, kSmemBytes, s>>>(tmP, tmA, tmB, P, ldp, n, status);
-  return cudaGetLastError();
+  if (r < 1 || r > kMaxTcR) return cudaErrorInvalidValue;
+  const int half = r <= 32 ? 32 : 64;
+  tc_split_kernel<<<(n + 31) / 32, 256, 0, s>>>(U, W, fs, n, r, half, Acat, Bcat);
+  if (half == 32) return launch_tc_t<32>(tmP, tmA, tmB, P, ldp, n, num_sms, status, s);
+  return launch_tc_t<64>(tmP, tmA, tmB, P, ldp, n, num_sms, status, s);
 }
 
 }  // namespace lv

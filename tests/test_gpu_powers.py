@@ -109,7 +109,8 @@ def test_matches_oracle_incremental(prec):
 @pytest.mark.parametrize("n,r,upd", [(1, 1, True), (5, 3, True), (300, 8, True), (1000, 8, False),
                                      (1031, 16, True), (2048, 64, True), (640, 24, False),
                                      (777, 1, True), (1029, 2, True), (1030, 4, True),
-                                     (1032, 16, True), (1036, 2, True), (300, 40, True)])
+                                     (1032, 16, True), (1036, 2, True), (300, 40, True),
+                                     (301, 48, True)])
 def test_level_pass_kernel(prec, n, r, upd):
     """One Appendix-A level pass (P U, P^T V, P += U V^T) on caller memory."""
     from paper_1403_6968_gb300 import level_pass
