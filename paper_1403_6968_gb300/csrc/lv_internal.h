@@ -91,7 +91,7 @@ int64_t tc_split_floats(int64_t n);
 constexpr int kMaxTcR = 64;  // widest factor block of one tensor-core update pass
 // Tensor-core update pass P += U W^T (FP32 view, 17 <= r <= 64 factor
 // columns, split TF32): splits U, W into the scratch, then one persistent
-// launch over 128 x 64 tiles (r <= 32) or 128 x 32 tiles (r > 32).  tmP:
+// launch over 128 x 64 tiles.  tmP:
 // make_tmap_sw128 over the view P (box rows 128, row stride ldp); tmA / tmB:
 // over A_cat (128 columns, box rows 128) / B_cat (128 columns, box rows 32).
 cudaError_t launch_tc_update(const CUtensorMap& tmP, const CUtensorMap& tmA,

@@ -16,8 +16,8 @@
 // Two shapes, chosen by the block width r, both 224 KB of shared memory:
 //   RP = 32: tiles of 128 rows x 64 columns of P, A block 32 KB, B tile
 //            16 KB (double buffered), 5 P stages of 32 KB;
-//   RP = 64: tiles of 128 rows x 32 columns, A block 64 KB, B tile 16 KB
-//            (double buffered), 8 P stages of 16 KB.
+//   RP = 64: tiles of 128 rows x 64 columns, A block 64 KB, B tile 32 KB
+//            (double buffered), 3 P stages of 32 KB.
 // A persistent grid (one CTA per SM) walks the tiles row-block by
 // row-block; per CTA:
 //   warp 0     TMA producer: A block (reloaded when the row block changes),
@@ -48,14 +48,14 @@ constexpr int kStoresInFlight = 1;       // TMA stores not yet read out
 // Shape of one variant: RP factor columns (padded), BN tile columns.
 template <int RP>
 struct TcShape {
-  static constexpr int BN = RP == 32 ? 64 : 32;        // tile columns (MMA N)
+  static constexpr int BN = 64;                        // tile columns (MMA N)
   static constexpr int H = RP / 32;                    // 128-byte K chunks per half
   static constexpr int KC = 2 * H;                     // chunks: hi 0..H-1, lo H..2H-1
   static constexpr uint32_t ABytes = KC * kBM * 128;   // A block
   static constexpr uint32_t BBytes = KC * BN * 128;    // B tile (one buffer)
   static constexpr int PBoxes = BN / 32;               // 32-column boxes per P tile
   static constexpr uint32_t PBytes = PBoxes * kBM * 128;
-  static constexpr int PS = RP == 32 ? 5 : 8;          // P tile stages
+  static constexpr int PS = RP == 32 ? 5 : 3;          // P tile stages
   static constexpr uint32_t TmemCols = 2 * BN;         // two accumulators
   static constexpr uint32_t OffA = 0;
   static constexpr uint32_t OffB = OffA + ABytes;      // 2 buffers
