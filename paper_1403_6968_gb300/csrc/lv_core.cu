@@ -429,25 +429,6 @@ cudaError_t launch_rm_to_cm(const T* src, int64_t ld, T* dst, int64_t fs, int ro
 }
 
 template <typename T>
-__global__ void cm_to_rm_kernel(const T* src, int64_t fs, T* dst, int64_t ld, int rows, int cols) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)rows * cols) return;
-  int j, c;
-  split_index(idx, cols, j, c);
-  dst[(int64_t)j * ld + c] = src[(int64_t)c * fs + j];
-}
-
-template <typename T>
-cudaError_t launch_cm_to_rm(const T* src, int64_t fs, T* dst, int64_t ld, int rows, int cols,
-                            cudaStream_t s) {
-  const int64_t tot = (int64_t)rows * cols;
-  if (tot == 0) return cudaSuccess;
-  cm_to_rm_kernel<T><<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-      src, fs, dst, ld, rows, cols);
-  return cudaGetLastError();
-}
-
-template <typename T>
 __global__ void unit_column_kernel(T* dst, int n, int row) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) dst[j] = (j == row) ? T(1) : T(0);
@@ -549,8 +530,6 @@ cudaError_t launch_bounded_wait_probe(uint64_t limit_ns, unsigned* status,
   template cudaError_t launch_assemble<T>(const AssembleParams&, cudaStream_t);                  \
   template cudaError_t launch_suffix_sums<T>(const T*, T*, int64_t, int, int, int, cudaStream_t); \
   template cudaError_t launch_rm_to_cm<T>(const T*, int64_t, T*, int64_t, int, int,               \
-                                          cudaStream_t);                                        \
-  template cudaError_t launch_cm_to_rm<T>(const T*, int64_t, T*, int64_t, int, int,               \
                                           cudaStream_t);                                        \
   template cudaError_t launch_unit_column<T>(T*, int, int, cudaStream_t);                        \
   template cudaError_t launch_sum_partials<T>(const T*, int, int64_t, int64_t, int, int, T*,      \

@@ -152,9 +152,6 @@ cudaError_t launch_suffix_sums(const T* V, T* W, int64_t fs, int n, int width, i
 template <typename T>
 cudaError_t launch_rm_to_cm(const T* src, int64_t ld, T* dst, int64_t fs, int rows, int cols,
                             cudaStream_t s);
-template <typename T>
-cudaError_t launch_cm_to_rm(const T* src, int64_t fs, T* dst, int64_t ld, int rows, int cols,
-                            cudaStream_t s);
 // e_row as one column (column-major, n rows).
 template <typename T>
 cudaError_t launch_unit_column(T* dst, int n, int row, cudaStream_t s);
