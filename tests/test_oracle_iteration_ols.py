@@ -168,6 +168,32 @@ def test_woodbury_row_blocks_vs_sm_and_lstsq(k):
     assert rel_frob(a.beta, beta_ls) < 1e-8
 
 
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_factored_beta_refresh_reaches_the_definition(k):
+    """The CUDA path refreshes beta = W (X^T Y) by the delta of a product
+    (Section 3.2) instead of recomputing W' C': with U = [X'_R^T, X_R^T],
+    G = W U = [G_1, G_2], Wu = -G M^-1 (M = diag(I, -I) + U^T G),
+    C' = X^T Y + (X'_R - X_R)^T Y_R and W' = W + G Wu^T,
+        W' C' = beta + (G_1 - G_2) Y_R + G (Wu^T C').
+    Checked against the oracle's beta (its definition W' C') over a few
+    replacements, each starting from the previous refreshed beta."""
+    m, n, p = 300, 20, 3
+    x, y, _ = li.ols_inputs(m, n, p, seed=11)
+    ref = oo.IncrementalOLS(x, y)
+    w, beta, xty = ref.w.copy(), ref.beta.copy(), ref.xty.copy()
+    for rows, new in li.ols_row_replacements(m, n, k, 4, seed=12):
+        u = np.concatenate([new.T, ref.x[rows].T], axis=1)
+        g = w @ u
+        core = np.diag([1.0] * k + [-1.0] * k) + u.T @ g
+        wu = -np.linalg.solve(core.T, g.T).T          # -G M^-1
+        xty = xty + (new - ref.x[rows]).T @ y[rows]
+        beta = beta + (g[:, :k] - g[:, k:]) @ y[rows] + g @ (wu.T @ xty)
+        w = w + g @ wu.T
+        ref.replace_rows(rows, new)
+        assert rel_frob(w, ref.w) < 1e-12
+        assert rel_frob(beta, ref.beta) < 1e-10
+
+
 def test_ols_inputs_are_ill_conditioned():
     # 10% of columns scaled by 1e-2: kappa(X^T X) ~ 1e4 x ((sqrt m + sqrt n)/(sqrt m - sqrt n))^2
     m, n = 4096, 128
