@@ -1655,7 +1655,7 @@ static linview_status ols_replace_t(linview_program* p, int kr, const void* nrow
   LV_CUDA(launch_gather_rows<T>(static_cast<const T*>(p->Yd), p->ldY, p->rows_d, kr, pp,
                                 static_cast<T*>(p->Yr), pp, 1, s));
   p->all_launches += 2;
-  // G = W U (one read of W per 8 columns)
+  // G = W U (one read of W per 16 columns in FP32, per 8 in FP64)
   LV_TRY(run_products_update<T>(p, w, kk, U, nullptr, nullptr, nullptr, s));
   {
     ProfScope ps(p, s, 0.0);
