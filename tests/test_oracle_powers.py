@@ -301,3 +301,26 @@ def test_skip_sums_recurrence_is_the_definition(k, s):
     for h, v in sm.items():
         ref = sum(np.linalg.matrix_power(a, i) for i in range(1, h + 1))
         assert rel_frob(v, ref) < 1e-13
+
+
+def test_level_products_by_loops_and_the_squaring_rule():
+    """One Appendix-A level, (P U, P^T V, P + U V^T), against explicit sums
+    over small integers (exact), and its use in the rule for the next power:
+    (P + U V^T)^2 - P^2 = U_2 V_2^T with U_2 = [U, P U + U (V^T U)],
+    V_2 = [P^T V, V]."""
+    g = np.random.default_rng(7)
+    n, r = 5, 2
+    p = g.integers(-3, 4, (n, n)).astype(np.float64)   # not symmetric
+    u = g.integers(-3, 4, (n, r)).astype(np.float64)
+    v = g.integers(-3, 4, (n, r)).astype(np.float64)
+    assert not np.array_equal(p, p.T)
+    x, y, p_new = op.level_products(p, u, v)
+    for i in range(n):
+        for c in range(r):
+            assert x[i, c] == sum(p[i, j] * u[j, c] for j in range(n))
+            assert y[i, c] == sum(p[j, i] * v[j, c] for j in range(n))
+        for j in range(n):
+            assert p_new[i, j] == p[i, j] + sum(u[i, c] * v[j, c] for c in range(r))
+    u2 = np.concatenate([u, x + u @ (v.T @ u)], axis=1)
+    v2 = np.concatenate([y, v], axis=1)
+    assert np.array_equal(p_new @ p_new - p @ p, u2 @ v2.T)
