@@ -324,3 +324,18 @@ def test_level_products_by_loops_and_the_squaring_rule():
     u2 = np.concatenate([u, x + u @ (v.T @ u)], axis=1)
     v2 = np.concatenate([y, v], axis=1)
     assert np.array_equal(p_new @ p_new - p @ p, u2 @ v2.T)
+
+
+@pytest.mark.parametrize("k,s", [(16, 4), (16, 2), (12, 4), (8, 8)])
+def test_skip_powers_against_library_matrix_power(k, s):
+    """Skip-s model views (squarings up to A^s, then A^i = A^s A^(i-s)) equal
+    numpy.linalg.matrix_power at every maintained h; small integers keep the
+    products exact."""
+    g = np.random.default_rng(k * 10 + s)
+    a = g.integers(-1, 2, (6, 6)).astype(np.float64)
+    got = op.skip_powers(a, k, s)
+    hs = sorted(got)
+    assert hs == sorted(set([1 << j for j in range(s.bit_length()) if (1 << j) <= s] +
+                            list(range(2 * s, k + 1, s))))
+    for h in hs:
+        assert np.array_equal(got[h], np.linalg.matrix_power(a, h)), h
