@@ -48,7 +48,8 @@ def _args():
     ap.add_argument("--k", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--reeval-steps", type=int, default=3)
-    ap.add_argument("--cpu-sample", type=int, default=3, help="oracle updates timed")
+    ap.add_argument("--cpu-sample", type=int, default=12,
+                    help="oracle updates timed (about 10 s of host work at n = 8192)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--serve-rates", default="1e2,1e3,3e3,1e4,3e4,1e5",
