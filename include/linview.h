@@ -294,17 +294,23 @@ linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp
  * counterpart: this entry exists for callers that may not allocate device
  * memory on their call path (a process or engine plugin that reserved the GPU's
  * memory up front, or a latency-critical loop that must avoid the implicit
- * synchronisation of cudaMalloc/cudaFree).  Arguments, layouts and results are
- * those of linview_level_pass; the cross-block partial sums live in one array
- * built into the library (16 MiB of device memory, held on every GPU that
- * loads the library until the process exits) instead of stream-ordered
- * allocations.  Sizes whose partial sums do not fit (roughly n * r beyond
- * 8192 * 8 for FP32 on a 152-SM GPU) return LINVIEW_ESHAPE with the needed
- * byte count.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture.  All calls share the array and it keeps the last call's contents:
- * calls whose work overlaps on the GPU race on it and must be serialised.
- * The call synchronises ``stream`` before returning (to read the status word).
+ * synchronisation of cudaMalloc/cudaFree).  Arguments and layouts are those of
+ * linview_level_pass; the cross-block partial sums live in one array built
+ * into the library (16 MiB of device memory, reserved on a device once the
+ * library's kernels are first used there -- CUDA's lazy module loading -- and
+ * held until the process exits) instead of stream-ordered allocations.  It
+ * launches the allocating entry's products passes and reductions; FP32 updates
+ * wider than 16 columns run on the CUDA-core update pass instead of the
+ * tensor-core pass (which needs a factor scratch buffer), so for those the two
+ * entries agree within FP32 rounding rather than bit for bit.  Sizes whose
+ * partial sums do not fit (roughly n * r beyond 8192 * 8 for FP32 on a 152-SM
+ * GPU) return LINVIEW_ESHAPE with the needed byte count, before the array is
+ * touched.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture begins.  All calls share the array and it keeps the last
+ * call's contents: calls whose work overlaps on the GPU race on it and must be
+ * serialised.  The call synchronises ``stream`` before returning (to read the
+ * status word).
  */
 linview_status linview_level_pass_noalloc(int precision, int64_t n, void* P, int64_t ldp,
                                           const void* U, const void* V, int64_t ldf, int64_t r,

@@ -7,17 +7,24 @@
 // latency-critical loop that cannot afford the implicit device-wide
 // synchronisation a cudaMalloc/cudaFree may cause.  linview_level_pass gets
 // its cross-block partial sums from the stream-ordered allocator; this
-// variant takes them from one fixed array compiled into the library instead,
-// and otherwise launches exactly the same kernels.
+// variant takes them from one fixed array compiled into the library instead.
+// It launches the same products passes (FP32 in blocks of 16 columns, FP64
+// in blocks of 8) and the same partial-sum reductions.  One difference: FP32
+// updates wider than 16 columns run on the CUDA-core update pass here (in
+// blocks of 32), where the allocating entry splits the factors into a scratch
+// buffer for the tensor-core pass; both are FP32-accurate, so those results
+// agree within FP32 rounding, not bit for bit.
 //
 // The array is a file-scope __device__ variable of kNoAllocScratchBytes
-// (16 MiB): every GPU that loads the library keeps those 16 MiB reserved until
-// the process exits.  Host code cannot use the variable's name as a device
+// (16 MiB).  Under CUDA's lazy module loading it is reserved on a device once
+// the library's kernels are first used there, and stays reserved until the
+// process exits.  Host code cannot use the variable's name as a device
 // address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it; make that
-// first call before capturing any work into a stream graph.  All calls share
-// the array and it keeps whatever the last call left in it, so two calls whose
-// work overlaps on the GPU (e.g. on two streams) race on it: serialise them.
+// cudaGetSymbolAddress (with that device current) and caches it per device;
+// make that first call before any stream capture begins.  All calls share
+// the array and it keeps whatever the last call left in it, so two calls
+// whose work overlaps on the GPU (e.g. on two streams) race on it: serialise
+// them.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -62,9 +69,11 @@ cudaError_t scratch_address(void** out) {
 
 int64_t rup64(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
-// Same launch sequence as the allocating entry point: fused products (+
-// update) in blocks of at most kMaxFusedR columns, update-only passes for the
-// rest, then the fixed-order sums of the partials into X and Y.
+// The allocating entry point's launch sequence: one fused products + update
+// pass up to kMaxFusedR columns, else products-only passes in blocks of
+// kMaxProductR (FP32) or kMaxFusedR (FP64) columns and update-only passes of
+// up to kMaxUpdateR columns, then the fixed-order sums of the partials into X
+// and Y.
 template <typename T>
 cudaError_t run(lv::PassParams base, const CUtensorMap& tm, int n, int r, int sms, const T* U,
                 const T* V, T* X, T* Y, bool do_update, cudaStream_t s) {
@@ -87,8 +96,9 @@ cudaError_t run(lv::PassParams base, const CUtensorMap& tm, int n, int r, int sm
       if (e != cudaSuccess) return e;
       do_update = false;
     } else {
-      for (int c0 = 0; c0 < r; c0 += kMaxFusedR) {
-        const int w = (r - c0 < kMaxFusedR) ? (r - c0) : kMaxFusedR;
+      constexpr int MW = sizeof(T) == 4 ? kMaxProductR : kMaxFusedR;
+      for (int c0 = 0; c0 < r; c0 += MW) {
+        const int w = (r - c0 < MW) ? (r - c0) : MW;
         PassParams pp = base;
         pp.Xf = U + (int64_t)c0 * base.fs;
         pp.Yf = V + (int64_t)c0 * base.fs;

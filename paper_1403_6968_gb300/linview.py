@@ -229,19 +229,57 @@ class Program:
             pass
 
 
+def _check_pass_operands(P, U, V, X, Y):
+    """Host-side checks of a level pass's operands, before any launch: P is a
+    2-D CUDA float32/float64 tensor with unit inner stride and at least
+    P.shape[0] columns; U, V (and X, Y when given) are r x n row-major CUDA
+    tensors (each row one factor column) on P's device, of P's dtype, with
+    unit inner stride, n = P.shape[0] columns at least and one common row
+    stride.  Raises ValueError, so that a wrong call never becomes an
+    out-of-bounds device access.  Returns (n, r, ldf)."""
+    if getattr(P, "dim", lambda: 0)() != 2:
+        raise ValueError("P must be a 2-D tensor")
+    if not P.is_cuda:
+        raise ValueError("P must be a CUDA tensor")
+    if str(P.dtype) not in ("torch.float32", "torch.float64"):
+        raise ValueError(f"P must be float32 or float64, got {P.dtype}")
+    n = P.shape[0]
+    if n < 1 or P.shape[1] < n:
+        raise ValueError(f"P must be n x n (n >= 1), got {tuple(P.shape)}")
+    if P.stride(1) != 1:
+        raise ValueError("P must have unit inner stride (row-major)")
+    if getattr(U, "dim", lambda: 0)() != 2:
+        raise ValueError("U must be a 2-D (r, n) tensor")
+    r = U.shape[0]
+    ldf = U.stride(0)
+    for name, t in (("U", U), ("V", V), ("X", X), ("Y", Y)):
+        if t is None:
+            if name in ("U", "V"):
+                raise ValueError(f"{name} is required")
+            continue
+        if t.dim() != 2:
+            raise ValueError(f"{name} must be a 2-D (r, n) tensor")
+        if not t.is_cuda or t.device != P.device:
+            raise ValueError(f"{name} must be a CUDA tensor on P's device ({P.device})")
+        if t.dtype != P.dtype:
+            raise ValueError(f"{name} has dtype {t.dtype}, P has {P.dtype}")
+        if t.stride(1) != 1:
+            raise ValueError(f"{name} must have unit inner stride")
+        if t.shape[0] != r or t.stride(0) != ldf:
+            raise ValueError("U, V, X, Y must share shape (r, n) and row stride")
+        if t.shape[1] < n:
+            raise ValueError(f"{name} has {t.shape[1]} columns, fewer than n = {n}")
+    return n, r, ldf
+
+
 def level_pass(P, U, V, X=None, Y=None, do_update=True, stream=None):
     """One exponential-model level pass on caller tensors (all CUDA).
 
     P: n x n (row-major); U, V, X, Y: column-major n x r given as r x n
     row-major tensors (each row one factor column, i.e. U_cm = U.T)."""
     torch = _torch()
-    n = P.shape[0]
+    n, r, ldf = _check_pass_operands(P, U, V, X, Y)
     prec = L.F64 if P.dtype == torch.float64 else L.F32
-    r = U.shape[0]
-    ldf = U.stride(0)
-    for t in (V, X, Y):
-        if t is not None and (t.shape[0] != r or t.stride(0) != ldf):
-            raise ValueError("U, V, X, Y must share shape (r, n) and stride")
     L.call("linview_level_pass", prec, n, C.c_void_p(P.data_ptr()), P.stride(0),
            C.c_void_p(U.data_ptr()), C.c_void_p(V.data_ptr()), ldf, r,
            C.c_void_p(X.data_ptr()) if X is not None else None,
@@ -269,13 +307,8 @@ def level_pass_noalloc(P, U, V, X=None, Y=None, do_update=True, stream=None):
     include/linview.h for the size limit and the rule that overlapping calls
     must be serialised)."""
     torch = _torch()
-    n = P.shape[0]
+    n, r, ldf = _check_pass_operands(P, U, V, X, Y)
     prec = L.F64 if P.dtype == torch.float64 else L.F32
-    r = U.shape[0]
-    ldf = U.stride(0)
-    for t in (V, X, Y):
-        if t is not None and (t.shape[0] != r or t.stride(0) != ldf):
-            raise ValueError("U, V, X, Y must share shape (r, n) and stride")
     L.call("linview_level_pass_noalloc", prec, n, C.c_void_p(P.data_ptr()), P.stride(0),
            C.c_void_p(U.data_ptr()), C.c_void_p(V.data_ptr()), ldf, r,
            C.c_void_p(X.data_ptr()) if X is not None else None,

@@ -78,3 +78,28 @@ def test_noalloc_update_only_and_size_limit():
     with pytest.raises(LinviewError) as e:
         level_pass_noalloc(P, U, U, X, X.clone(), do_update=False)
     assert e.value.name == "ESHAPE" and "scratch" in str(e.value)
+
+
+def test_noalloc_after_rejection_still_matches():
+    """A size rejection (ESHAPE) is decided before the built-in array is
+    touched: a valid call right after it still matches the allocating entry."""
+    from paper_1403_6968_gb300 import LinviewError, level_pass, level_pass_noalloc
+    big = 16384
+    P = torch.zeros((big, big), dtype=torch.float32, device="cuda")
+    U = torch.zeros((16, big), dtype=torch.float32, device="cuda")
+    with pytest.raises(LinviewError) as e:
+        level_pass_noalloc(P, U, U, U.clone(), U.clone(), do_update=False)
+    assert e.value.name == "ESHAPE"
+    del P, U
+    n, r = 1000, 5
+    g = torch.Generator(device="cpu").manual_seed(7)
+    p0 = torch.randn((n, n), generator=g).cuda()
+    u = torch.randn((r, n), generator=g).cuda()
+    v = torch.randn((r, n), generator=g).cuda()
+    pa, pb = p0.clone(), p0.clone()
+    xa, ya = torch.empty_like(u), torch.empty_like(u)
+    xb, yb = torch.full_like(u, float("nan")), torch.full_like(u, float("nan"))
+    level_pass(pa, u, v, xa, ya, do_update=True)
+    level_pass_noalloc(pb, u, v, xb, yb, do_update=True)
+    torch.cuda.synchronize()
+    assert _rel(xb, xa) <= 1e-5 and _rel(yb, ya) <= 1e-5 and _rel(pb, pa) <= 1e-5
