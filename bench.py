@@ -215,6 +215,26 @@ def cpu_oracle_rate(n, k, updates, seed=0):
     return updates / dt, dt, setup
 
 
+def cpu_oracle_errors(a32, ups, rows, gpu_rows, k):
+    """Part of the CPU-baseline leg: the FP64 oracle's rows ``rows`` of every
+    view after the row updates ``ups`` (applied in order to the FP32-rounded
+    A promoted to FP64), against the same rows read back from the GPU views
+    (``gpu_rows``: name -> array).  Returns the per-view relative Frobenius
+    errors and their maximum."""
+    import numpy as np
+    from oracle import powers as op
+    from oracle.metrics import rel_frob
+    a = a32.astype(np.float64)
+    for i, v in ups:
+        a[i] += v.astype(np.float64)
+    pr, sr = op.power_rows(a, rows, k)
+    errs = {}
+    for name, got in gpu_rows.items():
+        h = int(name[1:])
+        errs[name] = rel_frob(got, (pr if name[0] == "P" else sr)[h])
+    return errs
+
+
 def _cores():
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(var):
@@ -378,6 +398,20 @@ def run_ours(args):
         e2e = {"value": ws * E / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
                "d2h_bytes_per_step": 4 * n, "steps": E}
 
+    # rows of every view after all the updates so far (the timed stream, the
+    # roofline window and the e2e region), for the error against the FP64
+    # oracle: the last 8 updated rows and 8 fixed ones
+    applied = W1 + K + KR + (E if E > 0 else 0)
+    chk_rows = sorted(set(rows[applied - 8:applied]) |
+                      {0, 1, n // 7, n // 3, n // 2, (2 * n) // 3, n - 2, n - 1})
+    torch.cuda.synchronize()
+    gpu_rows = {}
+    for j in range(L + 1):
+        gpu_rows[f"P{1 << j}"] = np.stack([prog.read_view_rows(j, i, 1)[0] for i in chk_rows])
+    for j in range(1, L + 1):
+        gpu_rows[f"S{1 << j}"] = np.stack([prog.read_view_rows(L + j, i, 1)[0]
+                                           for i in chk_rows])
+
     # GPU re-evaluation of the same views (the paper's re-evaluation strategy:
     # apply dA to A, recompute every view) in three GEMM arithmetics.  Errors
     # are taken at one fixed A: each mode's views vs the IEEE-FP32 re-evaluation
@@ -452,6 +486,13 @@ def run_ours(args):
            "roofline": roof, "e2e": e2e, "gpu_launches": launches_timed,
            "reeval": reeval, "speedup": speed, "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        errs = cpu_oracle_errors(a, ups[:applied], chk_rows, gpu_rows, k)
+        out["oracle_rel_err"] = {
+            "per_view": errs, "max": max(errs.values()), "tolerance": 1e-4,
+            "rows": len(chk_rows), "after_updates": applied,
+            "how": "sampled rows (the last 8 updated rows and 8 fixed ones) of every view "
+                   "after all the updates of the run so far, against the FP64 oracle's rows "
+                   "of A^h and S'_h computed row by row on the updated A"}
         rate, dt, setup = cpu_oracle_rate(n, k, args.cpu_sample)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": _cores(), "kind": "oracle",
                                "sample": f"{args.cpu_sample} rank-1 row updates of the same "

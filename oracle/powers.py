@@ -141,6 +141,39 @@ def power_rows(a: np.ndarray, rows, k: int):
     return pw, sm
 
 
+def power_rows_factored(a0: np.ndarray, u: np.ndarray, v: np.ndarray, rows, k: int):
+    """Rows ``rows`` of every A^h and S'_h (h in levels(k)) for the matrix
+    A = A0 + U V^T held in factored form (U, V: n x q, the sum of the updates
+    applied so far, Sec. 3.2), by the plain definition of power_rows:
+    r <- e_i^T A, then r <- r A, where each product with A is taken as
+    r A0 + (r U) V^T (the product distributes over the sum).  The n x n
+    matrix A is never formed, so a long stream of rank-r updates at large n
+    costs q extra columns instead of an n^2 update per step.
+
+    Returns (powers, sums) as power_rows does.
+    """
+    a0 = np.asarray(a0, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64).reshape(a0.shape[0], -1)
+    v = np.asarray(v, dtype=np.float64).reshape(a0.shape[0], -1)
+    rows = np.asarray(rows, dtype=np.int64)
+
+    def times_a(x):
+        return x @ a0 + (x @ u) @ v.T
+
+    cur = a0[rows, :] + u[rows, :] @ v.T
+    acc = cur.copy()
+    want = set(levels(k))
+    pw, sm = {}, {}
+    for e in range(1, k + 1):
+        if e > 1:
+            cur = times_a(cur)
+            acc = acc + cur
+        if e in want:
+            pw[e] = cur.copy()
+            sm[e] = acc.copy()
+    return pw, sm
+
+
 def level_products(p, u, v):
     """One level of Appendix A on a view P_h with factors U_h, V_h:
     (P_h U_h, P_h^T V_h, P_h + U_h V_h^T), products on the view before the

@@ -100,6 +100,51 @@ def _body_serve_alone_vs_mix():
         assert rel_frob(alone, ref) <= TOL, (i, n)
 
 
+def _body_serve_alone_vs_mix_full_sizes():
+    """The serving workload's own view sizes (n in {1024, 2048, 4096, 8192},
+    A^16, FP32): the mixed, coalesced result of every view equals the view
+    refreshed alone (whole A^16 view) and the FP64 oracle on 16 sampled rows,
+    computed row by row on A0 + sum_j U_j V_j^T."""
+    P = _pkg()
+    sizes = [4096, 8192, 1024, 2048]
+    a0 = [li.power_matrix(n, seed=60 + i, dtype=np.float32) for i, n in enumerate(sizes)]
+    count = 40
+    t_s, views, ranks, factors, offsets = li.serving_trace(sizes, count, rate=5e4, seed=61)
+    srv = P.Server(max_inflight=3, r_cap=8)
+    try:
+        ids = [srv.add_view(a, K) for a in a0]
+        assert all(srv.view_state(i) == "resident" for i in ids)
+        srv.replay(t_s, views, ranks, factors, offsets)
+        srv.drain(timeout_s=180)
+        recs = srv.poll()
+        st = srv.stats()
+        assert len(recs) == count and st["failed"] == 0
+        assert all(r["status"] == 0 for r in recs)
+        assert max(r["batch_size"] for r in recs) > 1 and st["max_inflight_seen"] >= 2
+        mixed = {i: srv.program(i).read_view(L).cpu().numpy() for i in ids}
+    finally:
+        srv.close()
+    g = np.random.default_rng(62)
+    for i, n in enumerate(sizes):
+        reqs = [li.trace_factors(sizes, views, ranks, factors, offsets, j)
+                for j in range(count) if views[j] == i]
+        prog = P.Program("power", [a0[i]], k=K, r_max=8)
+        for u, v in reqs:
+            prog.apply_delta(u, v)
+        alone = prog.read_view(L).cpu().numpy()
+        prog.close()
+        assert rel_frob(mixed[i], alone) <= TOL, (i, n)
+        rows = sorted(set(int(x) for x in g.choice(n, 16, replace=False)))
+        if reqs:
+            uall = np.concatenate([u for u, _ in reqs], axis=1)
+            vall = np.concatenate([v for _, v in reqs], axis=1)
+        else:
+            uall = vall = np.zeros((n, 1))
+        pr, _ = op.power_rows_factored(a0[i], uall, vall, rows, K)
+        assert rel_frob(mixed[i][rows], pr[K]) <= TOL, (i, n)
+        assert rel_frob(alone[rows], pr[K]) <= TOL, (i, n)
+
+
 def _body_serve_admission_by_memory():
     P = _pkg()
     n = 512
@@ -216,6 +261,10 @@ def _run_child(body, timeout=300):
 
 def test_serve_alone_vs_mix():
     _run_child("serve_alone_vs_mix")
+
+
+def test_serve_alone_vs_mix_full_sizes():
+    _run_child("serve_alone_vs_mix_full_sizes", timeout=600)
 
 
 def test_serve_admission_by_memory():

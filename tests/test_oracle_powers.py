@@ -217,6 +217,35 @@ def test_power_rows_match_reeval():
         assert rel_frob(sr[h], sum(lin[j][rows] for j in range(h))) < 1e-13
 
 
+def test_power_rows_factored_against_library_power():
+    """Rows of (A0 + U V^T)^h and of S'_h from the factored form vs
+    numpy.linalg.matrix_power of the formed matrix (a library routine), for a
+    row-update stream (U = unit columns) and a dense rank-12 sum."""
+    n, k = 24, 16
+    a0 = li.power_matrix(n, seed=11)
+    rows = [0, 5, 23]
+    ups = li.row_update_stream(n, 7, seed=12)
+    u_row = np.zeros((n, len(ups)))
+    v_row = np.zeros((n, len(ups)))
+    for j, (i, v) in enumerate(ups):
+        u_row[i, j] = 1.0
+        v_row[:, j] = v
+    g = np.random.default_rng(13)
+    u_dense = g.standard_normal((n, 12)) * 0.05
+    v_dense = g.standard_normal((n, 12)) * 0.05
+    for u, v in ((u_row, v_row), (u_dense, v_dense)):
+        a = a0 + u @ v.T
+        pr, sr = op.power_rows_factored(a0, u, v, rows, k)
+        for h in op.levels(k):
+            ref = np.linalg.matrix_power(a, h)[rows]
+            assert rel_frob(pr[h], ref) < 1e-13, h
+            sref = sum(np.linalg.matrix_power(a, j)[rows] for j in range(1, h + 1))
+            assert rel_frob(sr[h], sref) < 1e-13, h
+    # a dropped factor term is visible: the update is not negligible
+    pr0, _ = op.power_rows_factored(a0, u_dense * 0.0, v_dense, rows, k)
+    assert rel_frob(pr0[16], np.linalg.matrix_power(a0 + u_dense @ v_dense.T, 16)[rows]) > 1e-6
+
+
 def _fd_power_grad(a, k, g, e, step=1e-4):
     def loss(x):
         return float(np.sum(g * op.linear_powers(x, k)[-1]))
