@@ -69,13 +69,18 @@ typedef enum {
 
 typedef enum { LINVIEW_F64 = 0, LINVIEW_F32 = 1 } linview_precision;
 
-/* GEMM arithmetic used by linview_reeval (the re-evaluation strategy). */
+/* GEMM arithmetic used by linview_reeval (the re-evaluation strategy) and by
+ * residual correction.  The default is the library's own GEMM; the cuBLAS
+ * arithmetics (FP32, TF32, BF16X9) are comparison denominators, selected
+ * explicitly, for power and iteration programs. */
 typedef enum {
-  LINVIEW_REEVAL_DEFAULT = 0, /* FP64 programs: DGEMM; FP32 programs: LINVIEW_REEVAL_FP32 */
-  LINVIEW_REEVAL_FP32 = 1,    /* IEEE FP32 GEMM on the CUDA cores (cuBLAS, pedantic) */
-  LINVIEW_REEVAL_TF32 = 2,    /* one TF32 tensor-core pass (fast, ~1e-3 relative) */
-  LINVIEW_REEVAL_BF16X9 = 3,  /* FP32 emulated by nine BF16 tensor-core products */
-  LINVIEW_REEVAL_FP64 = 4     /* DGEMM (FP64 programs) */
+  LINVIEW_REEVAL_DEFAULT = 0, /* FP64 programs: LINVIEW_REEVAL_FP64; FP32: LINVIEW_REEVAL_TC3 */
+  LINVIEW_REEVAL_FP32 = 1,    /* comparison: IEEE FP32 GEMM on the CUDA cores (cuBLAS, pedantic) */
+  LINVIEW_REEVAL_TF32 = 2,    /* comparison: one TF32 tensor-core pass (cuBLAS; ~1e-3 relative) */
+  LINVIEW_REEVAL_BF16X9 = 3,  /* comparison: FP32 emulated by nine BF16 products (cuBLAS) */
+  LINVIEW_REEVAL_FP64 = 4,    /* FP64 programs: the library's FP64 GEMM on the CUDA cores */
+  LINVIEW_REEVAL_TC3 = 5      /* FP32 programs: the library's tcgen05 GEMM in split TF32
+                                 (three TF32 products per operand pair, FP32 accuracy) */
 } linview_reeval_mode;
 
 typedef struct {
@@ -99,6 +104,28 @@ typedef struct {
                                 (T_1, T_2, .., T_s, T_2s, .., T_k; Appendix B); OLS: 0 */
   int32_t skip;              /* LINVIEW_MODEL_SKIP: the step s; otherwise 0 */
   int32_t strategy;          /* ITERATION: linview_strategy; other kinds: 0 */
+  /*
+   * Device memory of the program (its materialised views, Example 3.8's
+   * "A += ...; B += ..." targets, the factor arenas and the passes' scratch).
+   * Both NULL: the library calls cudaMalloc / cudaFree.  Otherwise every device
+   * allocation the program makes -- at creation and the few made lazily by
+   * later calls (host-factor staging, adjoint and re-evaluation work space) --
+   * is alloc(bytes, stream, alloc_ctx), with ``stream`` the cudaStream_t of the
+   * call that needs it (the memory is first used there, in stream order);
+   * alloc returns a device pointer, 256-byte aligned, or NULL (the call then
+   * fails with LINVIEW_ENOMEM).  Sizes are multiples of 512 bytes.  Each block
+   * is returned exactly once, by free(ptr, bytes, NULL, alloc_ctx) inside
+   * linview_destroy after the device has finished all of the program's work;
+   * temporary blocks of a single call are returned by that call as
+   * free(ptr, bytes, stream, alloc_ctx) in its stream order.  This is how a
+   * caching allocator (PyTorch's) owns the program's memory; the library never
+   * frees memory it did not obtain this way.  The callbacks are called from the
+   * thread making the library call.  linview_program_device_bytes counts the
+   * blocks the program holds.
+   */
+  void* (*alloc)(size_t bytes, void* stream, void* alloc_ctx);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* alloc_ctx);
+  void* alloc_ctx;
 } linview_program_desc;
 
 /* Evaluation strategy of an iteration program's updates (Section 4.3). */
@@ -288,6 +315,29 @@ linview_status linview_adjoint_power(linview_program* prog, const void* G, int64
 linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp, const void* U,
                                   const void* V, int64_t ldf, int64_t r, void* X, void* Y,
                                   int do_update, void* stream);
+
+/*
+ * The library's own dense product on caller device memory: the contraction of
+ * the re-evaluation strategy's squarings and sums (Section 4.2.2,
+ * "Re-evaluation"; Table 1) and of the reverse pass, as a stand-alone
+ * operation.
+ *   C (M x N) = alpha op(A) op(B) + beta C,  all row-major; op(X) = X^T when
+ *   the flag (ta / tb) is set.  A is M x K (ld >= K), or K x M when ta
+ *   (ld >= M); B is K x N (ld >= N), or N x K when tb (ld >= K).  beta = 0
+ *   ignores C's old contents.  M = 0 or N = 0 is an empty product (OK, no
+ *   pointer is read); K >= 1.
+ *  precision LINVIEW_F32: the tcgen05 split-TF32 GEMM (FP32 accuracy, three
+ *   TF32 products per operand pair, FP32 accumulation) when M >= 128,
+ *   N >= 32 and K >= 128, else the CUDA-core GEMM in FP32; LINVIEW_F64: the
+ *   FP64 CUDA-core GEMM.
+ * Temporary device memory (split operands, partial sums) is allocated
+ * stream-ordered on ``stream`` and released before the call returns; the call
+ * synchronises ``stream``.  Errors: EINVAL, ESHAPE, ENOMEM, ETIMEOUT (a
+ * bounded device wait expired), EDEVICE.
+ */
+linview_status linview_gemm(int precision, int ta, int tb, int64_t M, int64_t N, int64_t K,
+                            double alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                            double beta, void* C, int64_t ldc, void* stream);
 
 /*
  * linview_level_pass without any device allocation.  The paper has no

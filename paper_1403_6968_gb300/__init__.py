@@ -7,5 +7,5 @@ marshals torch tensors and streams.  Build with ``python -m
 paper_1403_6968_gb300.build``.
 """
 from .linview import (Program, LinviewError, Server, level_pass, level_pass_noalloc,  # noqa: F401
-                      estimate_device_bytes, program_device_bytes, check_bounded_wait)
+                      estimate_device_bytes, program_device_bytes, check_bounded_wait, gemm)
 from . import _lib  # noqa: F401

@@ -20,7 +20,7 @@ POWER, POWER_SUM, ITERATION, OLS = range(4)
 # linview_precision
 F64, F32 = 0, 1
 # linview_reeval_mode
-REEVAL_DEFAULT, REEVAL_FP32, REEVAL_TF32, REEVAL_BF16X9, REEVAL_FP64 = range(5)
+REEVAL_DEFAULT, REEVAL_FP32, REEVAL_TF32, REEVAL_BF16X9, REEVAL_FP64, REEVAL_TC3 = range(6)
 # linview_model
 MODEL_EXP, MODEL_LINEAR, MODEL_SKIP = 0, 1, 2
 STRATEGY_FACTORED, STRATEGY_HYBRID = 0, 1
@@ -40,7 +40,15 @@ class ProgramDesc(C.Structure):
         ("model", C.c_int32),
         ("skip", C.c_int32),
         ("strategy", C.c_int32),
+        ("alloc", C.c_void_p),
+        ("free", C.c_void_p),
+        ("alloc_ctx", C.c_void_p),
     ]
+
+
+# device-memory callbacks of linview_program_desc
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
 
 class Completion(C.Structure):
@@ -107,6 +115,8 @@ _SIGS = [
     ("linview_adjoint_iteration", _I, [_P, _P, _I64, _P, _I64, _P]),
     ("linview_adjoint_iteration_seed", _I, [_P, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P]),
     ("linview_adjoint_power", _I, [_P, _P, _I64, _P, _I64, _P]),
+    ("linview_gemm", _I, [_I, _I, _I, _I64, _I64, _I64, C.c_double, _P, _I64, _P, _I64,
+                          C.c_double, _P, _I64, _P]),
     ("linview_level_pass", _I, [_I, _I64, _P, _I64, _P, _P, _I64, _I64, _P, _P, _I, _P]),
     ("linview_level_pass_noalloc", _I, [_I, _I64, _P, _I64, _P, _P, _I64, _I64, _P, _P, _I, _P]),
     ("linview_set_profiling", _I, [_P, _I]),

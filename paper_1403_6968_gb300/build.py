@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblinview.so")
-SOURCES = ["lv_pass.cu", "lv_core.cu", "lv_ols.cu", "lv_capi.cu", "lv_noalloc.cu", "lv_serve.cu", "lv_tc.cu"]
+SOURCES = ["lv_pass.cu", "lv_core.cu", "lv_ols.cu", "lv_capi.cu", "lv_noalloc.cu", "lv_serve.cu", "lv_tc.cu", "lv_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -76,6 +77,9 @@ linview_status lv_set_error(linview_status st, const char* fmt, ...) {
 
 static int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
+// split-K partials of the CUDA-core GEMM, per program
+constexpr size_t kGemmWorkBytes = size_t(4) << 20;
+
 // ---------------------------------------------------------------------------
 // program
 // ---------------------------------------------------------------------------
@@ -89,13 +93,13 @@ struct View {
 };
 
 struct linview_program {
-  linview_program_desc d;
+  linview_program_desc d = {};
   int elem = 4;
   int device = 0;
   int sms = 148;
   cublasHandle_t blas = nullptr;
   cusolverDnHandle_t solver = nullptr;
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;  // (pointer, bytes) of every device allocation
   int64_t bytes = 0;  // sum of the device allocations in allocs
   std::vector<View> views;
   int L = 0;    // log2 k for powers
@@ -150,6 +154,13 @@ struct linview_program {
   // power adjoint work
   void* Gw0 = nullptr;
   void* Gw1 = nullptr;
+  // own GEMMs: split-K partials of the CUDA-core GEMM (program-owned, so that
+  // captured propagations can use it) and, for the hybrid strategy (FP32),
+  // persistent split operands of the tensor-core GEMM
+  void* gwork = nullptr;
+  int64_t gwork_elems = 0;
+  float* hyA = nullptr;  // split rows of the old A (n x tc_split_ld(n))
+  float* hyB = nullptr;  // split rows of D_{i-1}^T (p x tc_split_ld(n))
   // OLS: X (m x n), Y (m x p) on the device; views W, beta, X^T Y, X
   void* Xd = nullptr;
   int64_t ldX = 0;
@@ -210,17 +221,35 @@ struct linview_program {
   int64_t all_launches = 0;
 };
 
-static linview_status dalloc(linview_program* p, size_t bytes, void** out) {
+// Every device allocation of a program is rounded up to kAllocAlign bytes
+// (the caching allocators' granule), so that the program's byte count equals
+// what an allocator behind the callbacks hands out.
+constexpr int64_t kAllocAlign = 512;
+static int64_t alloc_bytes(int64_t b) { return rup(b > 0 ? b : 1, kAllocAlign); }
+
+// A program's device memory: from the caller's allocator when the
+// descriptor supplies one (e.g. PyTorch's caching allocator), else
+// cudaMalloc.  Zero-filled in stream order on s.
+static linview_status dalloc(linview_program* p, size_t bytes_in, void** out, cudaStream_t s) {
+  const size_t bytes = (size_t)alloc_bytes((int64_t)bytes_in);
   void* ptr = nullptr;
-  if (bytes == 0) bytes = 256;
-  cudaError_t e = cudaMalloc(&ptr, bytes);
-  if (e != cudaSuccess) {
-    (void)cudaGetLastError();
-    return fail(LINVIEW_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  if (p->d.alloc) {
+    ptr = p->d.alloc(bytes, static_cast<void*>(s), p->d.alloc_ctx);
+    if (!ptr) return fail(LINVIEW_ENOMEM, "the caller's allocator returned NULL for %zu bytes", bytes);
+    if (reinterpret_cast<uintptr_t>(ptr) % 256 != 0) {
+      if (p->d.free) p->d.free(ptr, bytes, static_cast<void*>(s), p->d.alloc_ctx);
+      return fail(LINVIEW_EINVAL, "the caller's allocator returned memory not 256-byte aligned");
+    }
+  } else {
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(LINVIEW_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
   }
-  p->allocs.push_back(ptr);
+  p->allocs.push_back({ptr, bytes});
   p->bytes += (int64_t)bytes;
-  LV_CUDA(cudaMemset(ptr, 0, bytes));
+  LV_CUDA(cudaMemsetAsync(ptr, 0, bytes, s));
   *out = ptr;
   return LINVIEW_OK;
 }
@@ -238,13 +267,13 @@ static int64_t square_view_bytes(int64_t n, int elem) {
   return rup(n, kBatch) * rup(n, 256) * elem;
 }
 
-static linview_status add_square_view(linview_program* p, int64_t n) {
+static linview_status add_square_view(linview_program* p, int64_t n, cudaStream_t s) {
   View v;
   v.rows = n;
   v.cols = n;
   v.ld = rup(n, 256);
   const int64_t rows_pad = rup(n, kBatch);
-  LV_TRY(dalloc(p, (size_t)square_view_bytes(n, p->elem), &v.ptr));
+  LV_TRY(dalloc(p, (size_t)square_view_bytes(n, p->elem), &v.ptr, s));
   v.square = true;
   v.tma_store = (v.ld * p->elem) % 16 == 0;
   if (!make_tmap(&v.tmap, v.ptr, p->elem, v.ld, rows_pad, v.ld))
@@ -276,10 +305,10 @@ static linview_status copy_in(void* dst, int64_t ldd, const void* src, int64_t l
   return LINVIEW_OK;
 }
 
-static linview_status ensure_stage(linview_program* p, size_t bytes) {
+static linview_status ensure_stage(linview_program* p, size_t bytes, cudaStream_t s) {
   if (p->stage_bytes >= bytes) return LINVIEW_OK;
   void* np = nullptr;
-  LV_TRY(dalloc(p, bytes, &np));
+  LV_TRY(dalloc(p, bytes, &np, s));
   p->stage = np;
   p->stage_bytes = bytes;
   return LINVIEW_OK;
@@ -484,10 +513,214 @@ static int exact_mode(const linview_program* p) {
   return p->elem == 8 ? LINVIEW_REEVAL_FP64 : LINVIEW_REEVAL_FP32;
 }
 
+// the program's re-evaluation arithmetic: the library's own GEMM (split-TF32
+// tensor cores for FP32, FP64 CUDA cores for FP64) unless a library
+// comparison mode was selected
 static int reeval_mode(const linview_program* p) {
   int m = p->d.reeval_mode;
-  if (m == LINVIEW_REEVAL_DEFAULT) m = (p->elem == 8) ? LINVIEW_REEVAL_FP64 : LINVIEW_REEVAL_FP32;
+  if (m == LINVIEW_REEVAL_DEFAULT) m = (p->elem == 8) ? LINVIEW_REEVAL_FP64 : LINVIEW_REEVAL_TC3;
   return m;
+}
+
+// ---------------------------------------------------------------------------
+// own GEMMs (lv_gemm.cu): the dense contractions of re-evaluation, of the
+// reverse pass and of the general form
+// ---------------------------------------------------------------------------
+// Rows of an operand: element (i, k) at X[i * rs + k * cs].
+struct Opnd {
+  const void* p;
+  int64_t rs, cs;
+};
+static Opnd rows_of(const void* X, int64_t ld) { return {X, ld, 1}; }  // rows of row-major X
+static Opnd cols_of(const void* X, int64_t ld) { return {X, 1, ld}; }  // rows of X^T
+
+// The library's stream-ordered pool for the temporary memory of calls whose
+// program has no allocator callbacks, one per device.  It keeps up to
+// kPoolKeepBytes of freed memory mapped (the default pool returns everything
+// at each synchronisation, so a call that needs a large temporary, e.g. the
+// split operands of an n = 8192 product, would map it again every time).
+constexpr uint64_t kPoolKeepBytes = uint64_t(4) << 30;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {nullptr};
+
+static cudaError_t library_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = kPoolKeepBytes;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pools[dev] = pool;
+  }
+  *out = g_pools[dev];
+  return cudaSuccess;
+}
+
+// Temporary device memory of one call, returned in stream order at the end
+// of that call (through the caller's allocator when the program has one,
+// else from the library's pool).
+static linview_status talloc(linview_program* p, size_t bytes_in, void** out, cudaStream_t s) {
+  const size_t bytes = (size_t)alloc_bytes((int64_t)bytes_in);
+  void* ptr = nullptr;
+  if (p->d.alloc) {
+    ptr = p->d.alloc(bytes, static_cast<void*>(s), p->d.alloc_ctx);
+    if (!ptr) return fail(LINVIEW_ENOMEM, "the caller's allocator returned NULL for %zu bytes", bytes);
+  } else {
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = library_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&ptr, bytes, pool, s);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(LINVIEW_ENOMEM, "cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  *out = ptr;
+  return LINVIEW_OK;
+}
+static void tfree(linview_program* p, void* ptr, size_t bytes_in, cudaStream_t s) {
+  if (!ptr) return;
+  const size_t bytes = (size_t)alloc_bytes((int64_t)bytes_in);
+  if (p->d.free)
+    p->d.free(ptr, bytes, static_cast<void*>(s), p->d.alloc_ctx);
+  else
+    cudaFreeAsync(ptr, s);
+}
+
+// Split-operand scratch of the tensor-core GEMM: rows of A_s then of B_s.
+struct TcScratch {
+  float* a = nullptr;
+  float* b = nullptr;
+  int64_t a_rows = 0, b_rows = 0, K = 0;
+  void* block = nullptr;  // temporary block owned by this scratch (null: borrowed)
+  size_t bytes = 0;
+  linview_program* p = nullptr;
+  cudaStream_t s = nullptr;
+  ~TcScratch() {
+    if (block) tfree(p, block, bytes, s);
+  }
+};
+
+// Temporary split scratch for products with up to a_rows x K and b_rows x K
+// operands (FP32 programs; FP64 programs take the CUDA-core path and get none).
+static linview_status tc_scratch(linview_program* p, TcScratch* sc, int64_t a_rows, int64_t b_rows,
+                                 int64_t K, cudaStream_t s) {
+  if (p->elem != 4 || a_rows < 128) return LINVIEW_OK;  // such products run on the CUDA cores
+  const int64_t ld = tc_split_ld(K);
+  const size_t abytes = (size_t)alloc_bytes(a_rows * ld * 4);
+  const size_t bytes = abytes + (size_t)b_rows * ld * 4;
+  void* blk = nullptr;
+  LV_TRY(talloc(p, bytes, &blk, s));
+  sc->block = blk;
+  sc->bytes = bytes;
+  sc->p = p;
+  sc->s = s;
+  sc->a = static_cast<float*>(blk);
+  sc->b = reinterpret_cast<float*>(static_cast<char*>(blk) + abytes);
+  sc->a_rows = a_rows;
+  sc->b_rows = b_rows;
+  sc->K = K;
+  return LINVIEW_OK;
+}
+
+// Products that go to the tensor cores (FP32, dense enough to fill tiles);
+// the rest run on the CUDA cores.
+static bool tc_eligible(const linview_program* p, const TcScratch* sc, int64_t M, int64_t N,
+                        int64_t K) {
+  return p->elem == 4 && sc && sc->a && M >= 128 && N >= 32 && K >= 128 && M <= sc->a_rows &&
+         N <= sc->b_rows && K <= sc->K;
+}
+
+// D (M x N, row-major, ldd) = alpha sum_k a(m, k) b(n, k) + beta C (C row-major,
+// ldc; may be D; beta == 0 ignores it), with a = rows of op(A) (M x K) and b =
+// rows of op(B)^T (N x K).  FP32 with scratch: split TF32 on the tensor cores
+// (a_ready / b_ready: the scratch already holds that operand's split rows);
+// otherwise the CUDA-core GEMM in the program's arithmetic.
+static linview_status gemm_ab(linview_program* p, int64_t M, int64_t N, int64_t K, double alpha,
+                              Opnd a, Opnd b, double beta, const void* C, int64_t ldc, void* D,
+                              int64_t ldd, cudaStream_t s, TcScratch* sc = nullptr,
+                              bool a_ready = false, bool b_ready = false) {
+  if (M <= 0 || N <= 0) return LINVIEW_OK;
+  const int e = p->elem;
+  if (tc_eligible(p, sc, M, N, K)) {
+    const int64_t ld = tc_split_ld(K);
+    if (!a_ready) {
+      LV_CUDA(launch_split_rows(static_cast<const float*>(a.p), a.rs, a.cs, (int)M, (int)K, sc->a,
+                                ld, s));
+      p->all_launches++;
+    }
+    if (!b_ready) {
+      LV_CUDA(launch_split_rows(static_cast<const float*>(b.p), b.rs, b.cs, (int)N, (int)K, sc->b,
+                                ld, s));
+      p->all_launches++;
+    }
+    LV_CUDA(launch_tc_gemm(sc->a, sc->b, (int)M, (int)N, (int)K, static_cast<float*>(D), ldd,
+                           static_cast<const float*>(C), ldc, (float)alpha, (float)beta, p->sms,
+                           p->status, s));
+    p->all_launches++;
+    return LINVIEW_OK;
+  }
+  if (beta != 0.0 && C != D)
+    LV_CUDA(cudaMemcpy2DAsync(D, ldd * e, C, ldc * e, N * e, M, cudaMemcpyDeviceToDevice, s));
+  // B(k, n) = b(n, k): k stride b.cs, n stride b.rs
+  if (e == 4)
+    LV_CUDA(launch_gemm_simt<float>((int)M, (int)N, (int)K, (float)alpha,
+                                    static_cast<const float*>(a.p), a.rs, a.cs,
+                                    static_cast<const float*>(b.p), b.cs, b.rs, (float)beta,
+                                    static_cast<float*>(D), ldd, 1, static_cast<float*>(p->gwork),
+                                    p->gwork_elems, p->sms, s));
+  else
+    LV_CUDA(launch_gemm_simt<double>((int)M, (int)N, (int)K, alpha, static_cast<const double*>(a.p),
+                                     a.rs, a.cs, static_cast<const double*>(b.p), b.cs, b.rs, beta,
+                                     static_cast<double*>(D), ldd, 1,
+                                     static_cast<double*>(p->gwork), p->gwork_elems, p->sms, s));
+  p->all_launches += 2;
+  return LINVIEW_OK;
+}
+
+// Column-major products of the factor arenas, C (M x N, column stride ldc) =
+// alpha op(A) op(B) + beta C with A, B column-major (lda, ldb): the CUDA-core
+// GEMM with the program's split-K partials (small products of the general
+// form, captured into the propagation graphs).
+static linview_status gemm_cm_own(linview_program* p, bool ta, bool tb, int64_t M, int64_t N,
+                                  int64_t K, double alpha, const void* A, int64_t lda,
+                                  const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
+                                  cudaStream_t s) {
+  if (M <= 0 || N <= 0) return LINVIEW_OK;
+  // column-major X(i, j) = X[i + j ld]; op(A)(m, k), op(B)(k, n)
+  const int64_t a_rs = ta ? lda : 1, a_cs = ta ? 1 : lda;
+  const int64_t b_rs = tb ? ldb : 1, b_cs = tb ? 1 : ldb;
+  if (p->elem == 4)
+    LV_CUDA(launch_gemm_simt<float>((int)M, (int)N, (int)K, (float)alpha,
+                                    static_cast<const float*>(A), a_rs, a_cs,
+                                    static_cast<const float*>(B), b_rs, b_cs, (float)beta,
+                                    static_cast<float*>(C), 1, ldc, static_cast<float*>(p->gwork),
+                                    p->gwork_elems, p->sms, s));
+  else
+    LV_CUDA(launch_gemm_simt<double>((int)M, (int)N, (int)K, alpha, static_cast<const double*>(A),
+                                     a_rs, a_cs, static_cast<const double*>(B), b_rs, b_cs, beta,
+                                     static_cast<double*>(C), 1, ldc,
+                                     static_cast<double*>(p->gwork), p->gwork_elems, p->sms, s));
+  p->all_launches += 2;
+  return LINVIEW_OK;
+}
+
+// Comparison modes of the re-evaluation: library GEMMs, selected explicitly.
+static bool library_mode(int mode) {
+  return mode == LINVIEW_REEVAL_FP32 || mode == LINVIEW_REEVAL_TF32 ||
+         mode == LINVIEW_REEVAL_BF16X9;
 }
 
 // ---------------------------------------------------------------------------
@@ -534,11 +767,17 @@ static linview_status linear_reeval(linview_program* p, cudaStream_t s) {
   const int k = p->d.k;
   const int mode = reeval_mode(p);
   View& a = p->views[0];
+  TcScratch sc;
+  if (!library_mode(mode)) LV_TRY(tc_scratch(p, &sc, n, n, n, s));
   for (int i = 2; i <= k; ++i) {
     View& prev = p->views[i - 2];
     View& c = p->views[i - 1];
-    LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, prev.ptr, prev.ld, a.ptr, a.ld, 0.0, c.ptr, c.ld,
-                   s, mode));
+    if (library_mode(mode))
+      LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, prev.ptr, prev.ld, a.ptr, a.ld, 0.0, c.ptr,
+                     c.ld, s, mode));
+    else  // A^T's rows are split once
+      LV_TRY(gemm_ab(p, n, n, n, 1.0, rows_of(prev.ptr, prev.ld), cols_of(a.ptr, a.ld), 0.0,
+                     nullptr, 0, c.ptr, c.ld, s, &sc, false, i > 2));
   }
   if (has_sums(p)) {
     View& sv = p->views[k];
@@ -565,36 +804,37 @@ static linview_status linear_reeval(linview_program* p, cudaStream_t s) {
 static linview_status skip_reeval(linview_program* p, cudaStream_t s) {
   const int64_t n = p->d.n;
   const int mode = reeval_mode(p);
+  const bool lib = library_mode(mode);
   const int Ls = ilog2(p->d.skip);
-  for (int l = 0; l < Ls; ++l) {
-    View& a = pview(p, l);
-    View& c = pview(p, l + 1);
-    LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, a.ptr, a.ld, a.ptr, a.ld, 0.0, c.ptr, c.ld, s,
-                   mode));
-  }
+  TcScratch sc;
+  if (!lib) LV_TRY(tc_scratch(p, &sc, n, n, n, s));
+  // out = pm prev (+ add)
+  auto prod = [&](View& pm, View& prev, View* add, View& out, bool a_ready) -> linview_status {
+    if (lib) {
+      if (add)
+        LV_CUDA(cudaMemcpy2DAsync(out.ptr, out.ld * p->elem, add->ptr, add->ld * p->elem,
+                                  n * p->elem, n, cudaMemcpyDeviceToDevice, s));
+      return gemm_rm(p, false, false, n, n, n, 1.0, pm.ptr, pm.ld, prev.ptr, prev.ld,
+                     add ? 1.0 : 0.0, out.ptr, out.ld, s, mode);
+    }
+    return gemm_ab(p, n, n, n, 1.0, rows_of(pm.ptr, pm.ld), cols_of(prev.ptr, prev.ld),
+                   add ? 1.0 : 0.0, add ? add->ptr : nullptr, add ? add->ld : 0, out.ptr, out.ld,
+                   s, &sc, a_ready, false);
+  };
+  for (int l = 0; l < Ls; ++l) LV_TRY(prod(pview(p, l), pview(p, l), nullptr, pview(p, l + 1), false));
   View& ps = pview(p, Ls);
-  for (int i = 2; i <= p->d.k / p->d.skip; ++i) {
-    View& prev = pview(p, Ls + i - 2);
-    View& c = pview(p, Ls + i - 1);
-    LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, ps.ptr, ps.ld, prev.ptr, prev.ld, 0.0, c.ptr,
-                   c.ld, s, mode));
-  }
+  for (int i = 2; i <= p->d.k / p->d.skip; ++i)  // P_s's rows are split once
+    LV_TRY(prod(ps, pview(p, Ls + i - 2), nullptr, pview(p, Ls + i - 1), i > 2));
   if (has_sums(p)) {
     // S'_{2h} = P_h S'_h + S'_h up to s (S'_1 = A), then S'_i = P_s S'_{i-s} + S'_s
-    auto sum_step = [&](View& pm, View& prev, View& add, View& out) -> linview_status {
-      LV_CUDA(cudaMemcpy2DAsync(out.ptr, out.ld * p->elem, add.ptr, add.ld * p->elem,
-                                n * p->elem, n, cudaMemcpyDeviceToDevice, s));
-      return gemm_rm(p, false, false, n, n, n, 1.0, pm.ptr, pm.ld, prev.ptr, prev.ld, 1.0,
-                     out.ptr, out.ld, s, mode);
-    };
     for (int l = 0; l < Ls; ++l) {
       View& sh = (l == 0) ? pview(p, 0) : sview(p, l);
-      LV_TRY(sum_step(pview(p, l), sh, sh, sview(p, l + 1)));
+      LV_TRY(prod(pview(p, l), sh, &sh, sview(p, l + 1), false));
     }
     View& ss = (Ls == 0) ? pview(p, 0) : sview(p, Ls);
     for (int i = 2; i <= p->d.k / p->d.skip; ++i) {
       View& prev = (Ls + i - 2 == 0) ? pview(p, 0) : sview(p, Ls + i - 2);
-      LV_TRY(sum_step(ps, prev, ss, sview(p, Ls + i - 1)));
+      LV_TRY(prod(ps, prev, &ss, sview(p, Ls + i - 1), false));
     }
   }
   return LINVIEW_OK;
@@ -605,21 +845,41 @@ static linview_status powers_reeval(linview_program* p, cudaStream_t s) {
   if (p->d.model == LINVIEW_MODEL_SKIP) return skip_reeval(p, s);
   const int64_t n = p->d.n;
   const int mode = reeval_mode(p);
-  for (int l = 0; l < p->L; ++l) {
-    View& a = pview(p, l);
-    View& c = pview(p, l + 1);
-    LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, a.ptr, a.ld, a.ptr, a.ld, 0.0, c.ptr, c.ld, s,
-                   mode));
-  }
-  if (has_sums(p)) {
+  if (library_mode(mode)) {  // comparison: library GEMMs
     for (int l = 0; l < p->L; ++l) {
-      View& ph = pview(p, l);
+      View& a = pview(p, l);
+      View& c = pview(p, l + 1);
+      LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, a.ptr, a.ld, a.ptr, a.ld, 0.0, c.ptr, c.ld, s,
+                     mode));
+    }
+    if (has_sums(p)) {
+      for (int l = 0; l < p->L; ++l) {
+        View& ph = pview(p, l);
+        View& sh = (l == 0) ? pview(p, 0) : sview(p, l);
+        View& s2 = sview(p, l + 1);
+        LV_CUDA(cudaMemcpy2DAsync(s2.ptr, s2.ld * p->elem, sh.ptr, sh.ld * p->elem, n * p->elem,
+                                  n, cudaMemcpyDeviceToDevice, s));
+        LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, ph.ptr, ph.ld, sh.ptr, sh.ld, 1.0, s2.ptr,
+                       s2.ld, s, mode));
+      }
+    }
+    return LINVIEW_OK;
+  }
+  // own GEMM, level by level: P_2h = P_h P_h, then S'_2h = P_h S'_h + S'_h with
+  // P_h's split rows reused (Table 1, exponential model)
+  TcScratch sc;
+  LV_TRY(tc_scratch(p, &sc, n, n, n, s));
+  const bool sums = has_sums(p);
+  for (int l = 0; l < p->L; ++l) {
+    View& ph = pview(p, l);
+    View& c = pview(p, l + 1);
+    LV_TRY(gemm_ab(p, n, n, n, 1.0, rows_of(ph.ptr, ph.ld), cols_of(ph.ptr, ph.ld), 0.0, nullptr,
+                   0, c.ptr, c.ld, s, &sc));
+    if (sums) {
       View& sh = (l == 0) ? pview(p, 0) : sview(p, l);
       View& s2 = sview(p, l + 1);
-      LV_CUDA(cudaMemcpy2DAsync(s2.ptr, s2.ld * p->elem, sh.ptr, sh.ld * p->elem, n * p->elem, n,
-                                cudaMemcpyDeviceToDevice, s));
-      LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, ph.ptr, ph.ld, sh.ptr, sh.ld, 1.0, s2.ptr,
-                     s2.ld, s, mode));
+      LV_TRY(gemm_ab(p, n, n, n, 1.0, rows_of(ph.ptr, ph.ld), cols_of(sh.ptr, sh.ld), 1.0, sh.ptr,
+                     sh.ld, s2.ptr, s2.ld, s, &sc, /*a_ready=*/true));
     }
   }
   return LINVIEW_OK;
@@ -659,17 +919,18 @@ static bool powers_uses_tc(const linview_program_desc& d) {
 static int64_t powers_device_bytes(const linview_program_desc& d, int sms) {
   const int elem = d.precision == LINVIEW_F64 ? 8 : 4;
   const int64_t n = d.n;
-  int64_t b = (int64_t)sizeof(unsigned) * 4 + (int64_t)sizeof(double) * 64 * 64 +
-              (int64_t)cpart_bytes(n);
-  b += powers_num_views(d) * square_view_bytes(n, elem);
+  int64_t b = alloc_bytes((int64_t)sizeof(unsigned) * 4) +
+              alloc_bytes((int64_t)sizeof(double) * 64 * 64) + alloc_bytes((int64_t)cpart_bytes(n)) +
+              alloc_bytes((int64_t)kGemmWorkBytes);
+  b += powers_num_views(d) * alloc_bytes(square_view_bytes(n, elem));
   const int64_t Rcap = (int64_t)d.r_max * d.k;
   const int64_t fs = rup(n, 64);
-  b += (powers_wide_sums(d) ? 3 : 2) * fs * Rcap * elem;
+  b += (powers_wide_sums(d) ? 3 : 2) * alloc_bytes(fs * Rcap * elem);
   const PassGeom g = fused_geom(elem, (int)n, sms);
   const int64_t half = Rcap / 2 > 0 ? Rcap / 2 : 1;
-  b += (int64_t)g.gC * half * fs * elem + (int64_t)g.gR * half * fs * elem;
-  b += 2 * n * d.r_max * elem;
-  if (powers_uses_tc(d)) b += tc_split_floats(n) * 4 * (powers_wide_sums(d) ? 2 : 1);
+  b += alloc_bytes((int64_t)g.gC * half * fs * elem) + alloc_bytes((int64_t)g.gR * half * fs * elem);
+  b += alloc_bytes(2 * n * d.r_max * elem);
+  if (powers_uses_tc(d)) b += alloc_bytes(tc_split_floats(n) * 4) * (powers_wide_sums(d) ? 2 : 1);
   return b;
 }
 
@@ -691,7 +952,7 @@ static linview_status powers_create(linview_program* p, const void* const* input
   const bool wide_sums = powers_wide_sums(p->d);
   if (lds[0] < n) return fail(LINVIEW_ESHAPE, "ld of A (%lld) < n", (long long)lds[0]);
   const int nviews = powers_num_views(p->d);
-  for (int l = 0; l < nviews; ++l) LV_TRY(add_square_view(p, n));
+  for (int l = 0; l < nviews; ++l) LV_TRY(add_square_view(p, n, s));
   p->npv = p->d.model == LINVIEW_MODEL_EXP      ? p->L + 1
            : p->d.model == LINVIEW_MODEL_SKIP ? ilog2(p->d.skip) + k / p->d.skip
                                               : k;
@@ -699,22 +960,22 @@ static linview_status powers_create(linview_program* p, const void* const* input
   p->Rcap = p->d.r_max * k;
   p->fs = rup(n, 64);
   const size_t fbytes = (size_t)p->fs * p->Rcap * p->elem;
-  LV_TRY(dalloc(p, fbytes, &p->Uar));
-  LV_TRY(dalloc(p, fbytes, &p->Var));
-  if (wide_sums) LV_TRY(dalloc(p, fbytes, &p->Wsum));
+  LV_TRY(dalloc(p, fbytes, &p->Uar, s));
+  LV_TRY(dalloc(p, fbytes, &p->Var, s));
+  if (wide_sums) LV_TRY(dalloc(p, fbytes, &p->Wsum, s));
   const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
   const int half = (p->Rcap / 2 > 0) ? p->Rcap / 2 : 1;
   p->part_cs = p->fs;
   p->xp_s = (int64_t)half * p->part_cs;
   p->yp_q = (int64_t)half * p->part_cs;
-  LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart));
-  LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart));
+  LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart, s));
+  LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart, s));
   // host-side update factors are staged here (allocated now so that an
   // update never allocates)
-  LV_TRY(ensure_stage(p, (size_t)2 * n * p->d.r_max * p->elem));
+  LV_TRY(ensure_stage(p, (size_t)2 * n * p->d.r_max * p->elem, s));
   if (powers_uses_tc(p->d)) {
     void* tc = nullptr;
-    LV_TRY(dalloc(p, (size_t)tc_split_floats(n) * sizeof(float), &tc));
+    LV_TRY(dalloc(p, (size_t)tc_split_floats(n) * sizeof(float), &tc, s));
     p->tcA = static_cast<float*>(tc);
     p->tcB = p->tcA + tc_split_floats(n) / 2;
     if (!make_tmap_sw128(&p->tmA, p->tcA, 128, n, 128, 128) ||
@@ -722,7 +983,7 @@ static linview_status powers_create(linview_program* p, const void* const* input
       return fail(LINVIEW_EDEVICE, "cuTensorMapEncodeTiled failed for the split factors");
     if (wide_sums) {  // the sums updates on the side stream have their own
       void* tc2 = nullptr;
-      LV_TRY(dalloc(p, (size_t)tc_split_floats(n) * sizeof(float), &tc2));
+      LV_TRY(dalloc(p, (size_t)tc_split_floats(n) * sizeof(float), &tc2, s));
       p->tcA2 = static_cast<float*>(tc2);
       p->tcB2 = p->tcA2 + tc_split_floats(n) / 2;
       if (!make_tmap_sw128(&p->tmA2, p->tcA2, 128, n, 128, 128) ||
@@ -941,13 +1202,20 @@ static linview_status iter_reeval(linview_program* p, cudaStream_t s) {
   const int mode = reeval_mode(p);
   View& a = p->views[0];
   char* T = static_cast<char*>(p->Tpanel);
+  TcScratch sc;
+  if (!library_mode(mode)) LV_TRY(tc_scratch(p, &sc, n, pp, n, s));
   for (int i = 1; i <= k; ++i) {
     void* ti = T + (size_t)i * pp * p->elem;
     void* tp = T + (size_t)(i - 1) * pp * p->elem;
-    LV_CUDA(cudaMemcpy2DAsync(ti, p->ldT * p->elem, p->Bm, p->ldB * p->elem, pp * p->elem, n,
-                              cudaMemcpyDeviceToDevice, s));
-    LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, a.ptr, a.ld, tp, p->ldT, 1.0, ti, p->ldT, s,
-                   mode));
+    if (library_mode(mode)) {
+      LV_CUDA(cudaMemcpy2DAsync(ti, p->ldT * p->elem, p->Bm, p->ldB * p->elem, pp * p->elem, n,
+                                cudaMemcpyDeviceToDevice, s));
+      LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, a.ptr, a.ld, tp, p->ldT, 1.0, ti, p->ldT, s,
+                     mode));
+    } else {  // T_i = A T_{i-1} + B, A's rows split once
+      LV_TRY(gemm_ab(p, n, pp, n, 1.0, rows_of(a.ptr, a.ld), cols_of(tp, p->ldT), 1.0, p->Bm,
+                     p->ldB, ti, p->ldT, s, &sc, i > 1));
+    }
   }
   return LINVIEW_OK;
 }
@@ -970,11 +1238,11 @@ static linview_status iter_create(linview_program* p, const void* const* inputs,
   if (p->d.r_max > kMaxFusedR)
     return fail(LINVIEW_EUNSUPPORTED, "iteration programs accept rank <= %d", kMaxFusedR);
   if (lds[0] < n || lds[1] < pp || lds[2] < pp) return fail(LINVIEW_ESHAPE, "bad leading dims");
-  LV_TRY(add_square_view(p, n));
+  LV_TRY(add_square_view(p, n, s));
   p->ldT = rup((int64_t)(k + 1) * pp, 64);
-  LV_TRY(dalloc(p, (size_t)n * p->ldT * p->elem, &p->Tpanel));
+  LV_TRY(dalloc(p, (size_t)n * p->ldT * p->elem, &p->Tpanel, s));
   p->ldB = rup(pp, 64);
-  LV_TRY(dalloc(p, (size_t)n * p->ldB * p->elem, &p->Bm));
+  LV_TRY(dalloc(p, (size_t)n * p->ldB * p->elem, &p->Bm, s));
   for (int i = 1; i <= k; ++i)
     LV_TRY(add_rect_view(p, static_cast<char*>(p->Tpanel) + (size_t)i * pp * p->elem, n, pp,
                          p->ldT));
@@ -985,18 +1253,25 @@ static linview_status iter_create(linview_program* p, const void* const* inputs,
   LV_TRY(copy_in(p->Tpanel, p->ldT, inputs[2], lds[2], n, pp, p->elem, on_dev, s));
   p->fs = rup(n, 64);
   p->Rcap = p->d.r_max * k;
-  LV_TRY(dalloc(p, (size_t)p->fs * p->Rcap * p->elem, &p->Kar));
-  LV_TRY(dalloc(p, (size_t)p->fs * p->d.r_max * p->elem, &p->V1));
-  LV_TRY(dalloc(p, (size_t)pp * p->Rcap * p->elem, &p->Mr));
+  LV_TRY(dalloc(p, (size_t)p->fs * p->Rcap * p->elem, &p->Kar, s));
+  LV_TRY(dalloc(p, (size_t)p->fs * p->d.r_max * p->elem, &p->V1, s));
+  LV_TRY(dalloc(p, (size_t)pp * p->Rcap * p->elem, &p->Mr, s));
   const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
   p->part_cs = p->fs;
   p->xp_s = (int64_t)kMaxFusedR * p->part_cs;
   p->yp_q = p->xp_s;
-  LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart));
-  LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart));
+  LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart, s));
+  LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart, s));
   if (p->d.strategy == LINVIEW_STRATEGY_HYBRID) {
     p->ldD = rup(pp, 64);
-    LV_TRY(dalloc(p, (size_t)2 * n * p->ldD * p->elem, &p->Dh));
+    LV_TRY(dalloc(p, (size_t)2 * n * p->ldD * p->elem, &p->Dh, s));
+    if (p->elem == 4 && n >= 128 && pp >= 32) {  // products A D_{i-1} on the tensor cores
+      void* t = nullptr;
+      LV_TRY(dalloc(p, (size_t)n * tc_split_ld(n) * 4, &t, s));
+      p->hyA = static_cast<float*>(t);
+      LV_TRY(dalloc(p, (size_t)pp * tc_split_ld(n) * 4, &t, s));
+      p->hyB = static_cast<float*>(t);
+    }
   }
   return iter_reeval(p, s);
 }
@@ -1023,8 +1298,8 @@ static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) 
   // column-major view: T_i is p x n (ld ldT), V is n x r (ld fs)
   for (int i = 0; i < k; ++i) {
     const void* ti = Tp + (size_t)i * pp * sizeof(T);
-    LV_TRY(gemm_cm(p, false, false, pp, r, n, 1.0, ti, p->ldT, V1, fs, 0.0,
-                   M + (int64_t)(k - 1 - i) * r * pp, pp, s, exact_mode(p)));
+    LV_TRY(gemm_cm_own(p, false, false, pp, r, n, 1.0, ti, p->ldT, V1, fs, 0.0,
+                   M + (int64_t)(k - 1 - i) * r * pp, pp, s));
   }
   if (k >= 2) {
     {
@@ -1064,8 +1339,7 @@ static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) 
   for (int i = 1; i <= k; ++i) {
     void* ti = Tp + (size_t)i * pp * sizeof(T);
     const T* mc = M + (int64_t)(k - i) * r * pp;
-    LV_TRY(gemm_cm(p, false, true, pp, n, (int64_t)i * r, 1.0, mc, pp, K, fs, 1.0, ti, p->ldT, s,
-                   exact_mode(p)));
+    LV_TRY(gemm_cm_own(p, false, true, pp, n, (int64_t)i * r, 1.0, mc, pp, K, fs, 1.0, ti, p->ldT, s));
   }
   return LINVIEW_OK;
 }
@@ -1099,12 +1373,10 @@ static linview_status iter_propagate_b(linview_program* p, int rb, cudaStream_t 
   // T_i += [K_0 .. K_{i-1}] [V_b .. V_b]^T; column-major T_i^T (p x n)
   for (int i = 1; i <= k; ++i) {
     void* ti = Tp + (size_t)i * pp * sizeof(T);
-    LV_TRY(gemm_cm(p, false, true, pp, n, (int64_t)i * rb, 1.0, M, pp, K, fs, 1.0, ti, p->ldT, s,
-                   exact_mode(p)));
+    LV_TRY(gemm_cm_own(p, false, true, pp, n, (int64_t)i * rb, 1.0, M, pp, K, fs, 1.0, ti, p->ldT, s));
   }
   // B += U_b V_b^T (column-major B^T, p x n)
-  LV_TRY(gemm_cm(p, false, true, pp, n, rb, 1.0, M, pp, K, fs, 1.0, p->Bm, p->ldB, s,
-                 exact_mode(p)));
+  LV_TRY(gemm_cm_own(p, false, true, pp, n, rb, 1.0, M, pp, K, fs, 1.0, p->Bm, p->ldB, s));
   return LINVIEW_OK;
 }
 
@@ -1132,27 +1404,38 @@ static linview_status iter_propagate_hybrid(linview_program* p, int r, bool b_up
   char* Tp = static_cast<char*>(p->Tpanel);
   T* D[2] = {static_cast<T*>(p->Dh), static_cast<T*>(p->Dh) + n * p->ldD};
   const View& a = p->views[0];
-  const int mode = exact_mode(p);
+  // FP32: D_i = A D_{i-1} on the tensor cores, the old A's split rows taken
+  // once per propagation into the program's persistent split buffers
+  TcScratch hy;
+  if (p->hyA) {
+    hy.a = p->hyA;
+    hy.b = p->hyB;
+    hy.a_rows = n;
+    hy.b_rows = pp;
+    hy.K = n;
+  }
+  bool a_split = false;
   for (int i = 1; i <= k; ++i) {
     T* dc = D[i & 1];
     const T* dp = D[(i - 1) & 1];
     T* ti = reinterpret_cast<T*>(Tp + (size_t)i * pp * sizeof(T));
     const T* tprev = reinterpret_cast<const T*>(Tp + (size_t)(i - 1) * pp * sizeof(T));
     if (!b_update)  // W^T = T'_{i-1}^T V (T'_{i-1} is already refreshed)
-      LV_TRY(gemm_cm(p, false, false, pp, r, n, 1.0, tprev, p->ldT, V1, fs, 0.0, W, pp, s, mode));
+      LV_TRY(gemm_cm_own(p, false, false, pp, r, n, 1.0, tprev, p->ldT, V1, fs, 0.0, W, pp, s));
     double beta = 0.0;
-    if (i >= 2) {  // D_i^T = D_{i-1}^T A^T
-      LV_TRY(gemm_cm(p, false, false, pp, n, n, 1.0, dp, p->ldD, a.ptr, a.ld, 0.0, dc, p->ldD, s,
-                     mode));
+    if (i >= 2) {  // D_i = A D_{i-1}
+      LV_TRY(gemm_ab(p, n, pp, n, 1.0, rows_of(a.ptr, a.ld), cols_of(dp, p->ldD), 0.0, nullptr, 0,
+                     dc, p->ldD, s, p->hyA ? &hy : nullptr, a_split));
+      a_split = true;
       beta = 1.0;
     }
     // D_i^T += W U^T  (the rank-r term)
-    LV_TRY(gemm_cm(p, false, true, pp, n, r, 1.0, W, pp, K, fs, beta, dc, p->ldD, s, mode));
+    LV_TRY(gemm_cm_own(p, false, true, pp, n, r, 1.0, W, pp, K, fs, beta, dc, p->ldD, s));
     ProfScope ps(p, s, 0.0);
     LV_CUDA(launch_axpy_rows<T>(ti, p->ldT, dc, p->ldD, T(1), (int)n, (int)pp, s));
   }
   if (b_update)  // B += U_b V_b^T (column-major B^T, p x n)
-    LV_TRY(gemm_cm(p, false, true, pp, n, r, 1.0, W, pp, K, fs, 1.0, p->Bm, p->ldB, s, mode));
+    LV_TRY(gemm_cm_own(p, false, true, pp, n, r, 1.0, W, pp, K, fs, 1.0, p->Bm, p->ldB, s));
   else
     LV_TRY(run_update<T>(p, a, K, V1, r, s));
   return LINVIEW_OK;
@@ -1180,7 +1463,7 @@ static View& ie_S(linview_program* p, int l) {  // S'_{2^l}; S'_1 = A
 
 // t2 = B + P (th - B) + S' B  (= P th + S B with S = I + S' - P)
 static linview_status iter_sk_next(linview_program* p, const View& th, View& t2, const View& ph,
-                                   const View& sh, cudaStream_t s) {
+                                   const View& sh, cudaStream_t s, TcScratch* sc) {
   const int64_t n = p->d.n, pp = p->d.p;
   const int mode = reeval_mode(p), e = p->elem;
   const View& b = p->views[p->ie_NT + 1];
@@ -1194,41 +1477,62 @@ static linview_status iter_sk_next(linview_program* p, const View& th, View& t2,
     LV_CUDA(launch_axpy_rows<double>(static_cast<double*>(p->Dh), p->ldD,
                                      static_cast<const double*>(b.ptr), b.ld, -1.0, (int)n,
                                      (int)pp, s));
-  LV_CUDA(cudaMemcpy2DAsync(t2.ptr, t2.ld * e, b.ptr, b.ld * e, pp * e, n,
-                            cudaMemcpyDeviceToDevice, s));
-  LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, ph.ptr, ph.ld, p->Dh, p->ldD, 1.0, t2.ptr, t2.ld,
-                 s, mode));
-  LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, sh.ptr, sh.ld, b.ptr, b.ld, 1.0, t2.ptr, t2.ld, s,
-                 mode));
-  return LINVIEW_OK;
+  if (library_mode(mode)) {
+    LV_CUDA(cudaMemcpy2DAsync(t2.ptr, t2.ld * e, b.ptr, b.ld * e, pp * e, n,
+                              cudaMemcpyDeviceToDevice, s));
+    LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, ph.ptr, ph.ld, p->Dh, p->ldD, 1.0, t2.ptr,
+                   t2.ld, s, mode));
+    return gemm_rm(p, false, false, n, pp, n, 1.0, sh.ptr, sh.ld, b.ptr, b.ld, 1.0, t2.ptr, t2.ld,
+                   s, mode);
+  }
+  LV_TRY(gemm_ab(p, n, pp, n, 1.0, rows_of(ph.ptr, ph.ld), cols_of(p->Dh, p->ldD), 1.0, b.ptr,
+                 b.ld, t2.ptr, t2.ld, s, sc));
+  return gemm_ab(p, n, pp, n, 1.0, rows_of(sh.ptr, sh.ld), cols_of(b.ptr, b.ld), 1.0, t2.ptr,
+                 t2.ld, t2.ptr, t2.ld, s, sc);
 }
 
 static linview_status iter_sk_reeval(linview_program* p, cudaStream_t s) {
   const int64_t n = p->d.n, pp = p->d.p;
   const int Ls = p->ie_Ls, mode = reeval_mode(p), e = p->elem;
+  const bool lib = library_mode(mode);
   View& a = p->views[0];
+  TcScratch sc;
+  if (!lib) LV_TRY(tc_scratch(p, &sc, n, n, n, s));
   for (int l = 1; l <= Ls; ++l) {  // P_2h = P_h P_h, S'_2h = S'_h + P_h S'_h
     View& ph = ie_P(p, l - 1);
     const View& sh = ie_S(p, l - 1);
-    LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, ph.ptr, ph.ld, ph.ptr, ph.ld, 0.0,
-                   ie_P(p, l).ptr, ie_P(p, l).ld, s, mode));
+    View& p2 = ie_P(p, l);
     View& s2 = ie_S(p, l);
-    LV_CUDA(cudaMemcpy2DAsync(s2.ptr, s2.ld * e, sh.ptr, sh.ld * e, n * e, n,
-                              cudaMemcpyDeviceToDevice, s));
-    LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, ph.ptr, ph.ld, sh.ptr, sh.ld, 1.0, s2.ptr,
-                   s2.ld, s, mode));
+    if (lib) {
+      LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, ph.ptr, ph.ld, ph.ptr, ph.ld, 0.0, p2.ptr,
+                     p2.ld, s, mode));
+      LV_CUDA(cudaMemcpy2DAsync(s2.ptr, s2.ld * e, sh.ptr, sh.ld * e, n * e, n,
+                                cudaMemcpyDeviceToDevice, s));
+      LV_TRY(gemm_rm(p, false, false, n, n, n, 1.0, ph.ptr, ph.ld, sh.ptr, sh.ld, 1.0, s2.ptr,
+                     s2.ld, s, mode));
+    } else {
+      LV_TRY(gemm_ab(p, n, n, n, 1.0, rows_of(ph.ptr, ph.ld), cols_of(ph.ptr, ph.ld), 0.0,
+                     nullptr, 0, p2.ptr, p2.ld, s, &sc));
+      LV_TRY(gemm_ab(p, n, n, n, 1.0, rows_of(ph.ptr, ph.ld), cols_of(sh.ptr, sh.ld), 1.0,
+                     sh.ptr, sh.ld, s2.ptr, s2.ld, s, &sc, /*a_ready=*/true));
+    }
   }
   const View& b = p->views[p->ie_NT + 1];
   const View& t0 = p->views[p->ie_NT + 2];
   View& t1 = ie_T(p, 0);  // T_1 = A T_0 + B
-  LV_CUDA(cudaMemcpy2DAsync(t1.ptr, t1.ld * e, b.ptr, b.ld * e, pp * e, n,
-                            cudaMemcpyDeviceToDevice, s));
-  LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, a.ptr, a.ld, t0.ptr, t0.ld, 1.0, t1.ptr, t1.ld,
-                 s, mode));
+  if (lib) {
+    LV_CUDA(cudaMemcpy2DAsync(t1.ptr, t1.ld * e, b.ptr, b.ld * e, pp * e, n,
+                              cudaMemcpyDeviceToDevice, s));
+    LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, a.ptr, a.ld, t0.ptr, t0.ld, 1.0, t1.ptr,
+                   t1.ld, s, mode));
+  } else {
+    LV_TRY(gemm_ab(p, n, pp, n, 1.0, rows_of(a.ptr, a.ld), cols_of(t0.ptr, t0.ld), 1.0, b.ptr,
+                   b.ld, t1.ptr, t1.ld, s, &sc));
+  }
   for (int l = 0; l < Ls; ++l)  // T_2h from T_h, h = 2^l
-    LV_TRY(iter_sk_next(p, ie_T(p, l), ie_T(p, l + 1), ie_P(p, l), ie_S(p, l), s));
+    LV_TRY(iter_sk_next(p, ie_T(p, l), ie_T(p, l + 1), ie_P(p, l), ie_S(p, l), s, &sc));
   for (int j = Ls + 1; j < p->ie_NT; ++j)  // T_i from T_{i-s}
-    LV_TRY(iter_sk_next(p, ie_T(p, j - 1), ie_T(p, j), ie_P(p, Ls), ie_S(p, Ls), s));
+    LV_TRY(iter_sk_next(p, ie_T(p, j - 1), ie_T(p, j), ie_P(p, Ls), ie_S(p, Ls), s, &sc));
   return LINVIEW_OK;
 }
 
@@ -1258,18 +1562,18 @@ static linview_status iter_sk_create(linview_program* p, const void* const* inpu
   p->ie_Ls = ilog2(sk);
   p->ie_NT = p->ie_Ls + k / sk;
   const int NT = p->ie_NT, Ls = p->ie_Ls;
-  LV_TRY(add_square_view(p, n));  // A = P_1
+  LV_TRY(add_square_view(p, n, s));  // A = P_1
   p->ldT = rup((int64_t)(NT + 1) * pp, 64);
-  LV_TRY(dalloc(p, (size_t)n * p->ldT * p->elem, &p->Tpanel));
+  LV_TRY(dalloc(p, (size_t)n * p->ldT * p->elem, &p->Tpanel, s));
   p->ldB = rup(pp, 64);
-  LV_TRY(dalloc(p, (size_t)n * p->ldB * p->elem, &p->Bm));
+  LV_TRY(dalloc(p, (size_t)n * p->ldB * p->elem, &p->Bm, s));
   char* tp = static_cast<char*>(p->Tpanel);
   for (int j = 0; j < NT; ++j)  // the j-th T view in panel block j + 1
     LV_TRY(add_rect_view(p, tp + (size_t)(j + 1) * pp * p->elem, n, pp, p->ldT));
   LV_TRY(add_rect_view(p, p->Bm, n, pp, p->ldB));
   LV_TRY(add_rect_view(p, p->Tpanel, n, pp, p->ldT));  // T_0 in block 0
-  for (int l = 1; l <= Ls; ++l) LV_TRY(add_square_view(p, n));  // P_2 .. P_s
-  for (int l = 1; l <= Ls; ++l) LV_TRY(add_square_view(p, n));  // S'_2 .. S'_s
+  for (int l = 1; l <= Ls; ++l) LV_TRY(add_square_view(p, n, s));  // P_2 .. P_s
+  for (int l = 1; l <= Ls; ++l) LV_TRY(add_square_view(p, n, s));  // S'_2 .. S'_s
   LV_TRY(copy_in(p->views[0].ptr, p->views[0].ld, inputs[0], lds[0], n, n, p->elem, on_dev, s));
   LV_TRY(copy_in(p->Bm, p->ldB, inputs[1], lds[1], n, pp, p->elem, on_dev, s));
   LV_TRY(copy_in(p->Tpanel, p->ldT, inputs[2], lds[2], n, pp, p->elem, on_dev, s));
@@ -1277,24 +1581,24 @@ static linview_status iter_sk_create(linview_program* p, const void* const* inpu
   p->Rcap = p->d.r_max * sk;  // U_h, V_h up to h = s
   const int64_t ck = (int64_t)p->d.r_max * k;  // width of the factors of dT_k
   const size_t fb = (size_t)p->fs * p->Rcap * p->elem;
-  LV_TRY(dalloc(p, fb, &p->Uar));
-  LV_TRY(dalloc(p, fb, &p->Var));
-  LV_TRY(dalloc(p, fb, &p->What));
+  LV_TRY(dalloc(p, fb, &p->Uar, s));
+  LV_TRY(dalloc(p, fb, &p->Var, s));
+  LV_TRY(dalloc(p, fb, &p->What, s));
   for (int i = 0; i < 2; ++i) {
-    LV_TRY(dalloc(p, (size_t)p->fs * ck * p->elem, &p->Xar[i]));
-    LV_TRY(dalloc(p, (size_t)pp * ck * p->elem, &p->Yar[i]));
+    LV_TRY(dalloc(p, (size_t)p->fs * ck * p->elem, &p->Xar[i], s));
+    LV_TRY(dalloc(p, (size_t)pp * ck * p->elem, &p->Yar[i], s));
   }
-  LV_TRY(dalloc(p, (size_t)ck * p->Rcap * p->elem, &p->XtV));
-  LV_TRY(dalloc(p, (size_t)pp * p->d.r_max * p->elem, &p->Mr));  // V_b of an update to B
+  LV_TRY(dalloc(p, (size_t)ck * p->Rcap * p->elem, &p->XtV, s));
+  LV_TRY(dalloc(p, (size_t)pp * p->d.r_max * p->elem, &p->Mr, s));  // V_b of an update to B
   const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
   p->part_cs = p->fs;
   p->xp_s = ck * p->part_cs;  // widest products block: P_s X_{k-s}
   p->yp_q = (int64_t)p->Rcap * p->part_cs;
-  LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart));
-  LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart));
+  LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart, s));
+  LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart, s));
   p->ldD = rup(pp, 64);
-  LV_TRY(dalloc(p, (size_t)n * p->ldD * p->elem, &p->Dh));
-  LV_TRY(ensure_stage(p, (size_t)2 * n * p->d.r_max * p->elem));
+  LV_TRY(dalloc(p, (size_t)n * p->ldD * p->elem, &p->Dh, s));
+  LV_TRY(ensure_stage(p, (size_t)2 * n * p->d.r_max * p->elem, s));
   return iter_sk_reeval(p, s);
 }
 
@@ -1326,18 +1630,17 @@ static linview_status iter_sk_step(linview_program* p, int cur, View& tj, const 
   T* Yn = static_cast<T*>(p->Yar[cur ^ 1]);
   T* XtV = static_cast<T*>(p->XtV);
   // first block of Y_i (column-major p x rh): T_j^T V_h + Y_j (X_j^T V_h)
-  LV_TRY(gemm_cm(p, false, false, pp, rh, n, 1.0, tj.ptr, tj.ld, Vh, fs, 0.0, Yn, pp, s, mode));
-  LV_TRY(gemm_cm(p, true, false, c, rh, n, 1.0, Xc, fs, Vh, fs, 0.0, XtV, c, s, mode));
-  LV_TRY(gemm_cm(p, false, false, pp, rh, c, 1.0, Yc, pp, XtV, c, 1.0, Yn, pp, s, mode));
+  LV_TRY(gemm_cm_own(p, false, false, pp, rh, n, 1.0, tj.ptr, tj.ld, Vh, fs, 0.0, Yn, pp, s));
+  LV_TRY(gemm_cm_own(p, true, false, c, rh, n, 1.0, Xc, fs, Vh, fs, 0.0, XtV, c, s));
+  LV_TRY(gemm_cm_own(p, false, false, pp, rh, c, 1.0, Yc, pp, XtV, c, 1.0, Yn, pp, s));
   if (with_b) {  // + B^T (W^_h - V_h) (W^_h in the What arena; dS_1 = 0)
-    LV_TRY(gemm_cm(p, false, false, pp, rh, n, 1.0, b.ptr, b.ld, p->What, fs, 1.0, Yn, pp, s,
-                   mode));
-    LV_TRY(gemm_cm(p, false, false, pp, rh, n, -1.0, b.ptr, b.ld, Vh, fs, 1.0, Yn, pp, s, mode));
+    LV_TRY(gemm_cm_own(p, false, false, pp, rh, n, 1.0, b.ptr, b.ld, p->What, fs, 1.0, Yn, pp, s));
+    LV_TRY(gemm_cm_own(p, false, false, pp, rh, n, -1.0, b.ptr, b.ld, Vh, fs, 1.0, Yn, pp, s));
   }
   LV_CUDA(cudaMemcpyAsync(Yn + (int64_t)rh * pp, Yc, sizeof(T) * pp * c, cudaMemcpyDeviceToDevice,
                           s));
   // T_j += X_j Y_j^T  (column-major T_j^T, p x n)
-  LV_TRY(gemm_cm(p, false, true, pp, n, c, 1.0, Yc, pp, Xc, fs, 1.0, tj.ptr, tj.ld, s, mode));
+  LV_TRY(gemm_cm_own(p, false, true, pp, n, c, 1.0, Yc, pp, Xc, fs, 1.0, tj.ptr, tj.ld, s));
   // X_i = [U_h, P_h X_j] from the old P_h
   const PassGeom g = fused_geom(sizeof(T), n, p->sms);
   LV_TRY(run_products_update<T>(p, ph, c, Xc, nullptr, nullptr, nullptr, s));
@@ -1364,8 +1667,8 @@ static linview_status iter_sk_propagate(linview_program* p, int r, cudaStream_t 
   int cur = 0;
   // X_1 = U_1, Y_1 = T_0^T V_1
   LV_CUDA(cudaMemcpyAsync(p->Xar[0], U, sizeof(T) * fs * r, cudaMemcpyDeviceToDevice, s));
-  LV_TRY(gemm_cm(p, false, false, pp, r, n, 1.0, t0.ptr, t0.ld, V + (int64_t)(p->Rcap - r) * fs,
-                 fs, 0.0, p->Yar[0], pp, s, exact_mode(p)));
+  LV_TRY(gemm_cm_own(p, false, false, pp, r, n, 1.0, t0.ptr, t0.ld, V + (int64_t)(p->Rcap - r) * fs,
+                 fs, 0.0, p->Yar[0], pp, s));
   for (int l = 0; l < Ls; ++l) {  // exponential part: T_2h from T_h, h = 2^l < s
     const int rh = r << l;
     T* Vh = V + (int64_t)(p->Rcap - rh) * fs;
@@ -1417,8 +1720,8 @@ static linview_status iter_sk_propagate(linview_program* p, int r, cudaStream_t 
   }
   // T_k += X_k Y_k^T, then P_s and S'_s
   View& tk = ie_T(p, NT - 1);
-  LV_TRY(gemm_cm(p, false, true, pp, n, (int64_t)r * k, 1.0, p->Yar[cur], pp, p->Xar[cur], fs,
-                 1.0, tk.ptr, tk.ld, s, exact_mode(p)));
+  LV_TRY(gemm_cm_own(p, false, true, pp, n, (int64_t)r * k, 1.0, p->Yar[cur], pp, p->Xar[cur], fs,
+                 1.0, tk.ptr, tk.ld, s));
   LV_TRY(run_update<T>(p, ie_P(p, Ls), U, Vs, rs, s));
   if (Ls >= 1) LV_TRY(run_update<T>(p, ie_S(p, Ls), U, Wh, rs, s));
   return LINVIEW_OK;
@@ -1449,7 +1752,7 @@ static linview_status iter_sk_step_b(linview_program* p, int cur, int c, int rb,
   T* tmp = static_cast<T*>(p->What);
   const PassGeom g = fused_geom(sizeof(T), n, p->sms);
   // T_j += X_j Y_j^T
-  LV_TRY(gemm_cm(p, false, true, pp, n, c, 1.0, Yc, pp, Xc, fs, 1.0, tj.ptr, tj.ld, s, mode));
+  LV_TRY(gemm_cm_own(p, false, true, pp, n, c, 1.0, Yc, pp, Xc, fs, 1.0, tj.ptr, tj.ld, s));
   // [P X_j | P U_b] in one products pass over P
   LV_CUDA(cudaMemcpyAsync(Xc + (int64_t)c * fs, Ub, sizeof(T) * fs * rb, cudaMemcpyDeviceToDevice,
                           s));
@@ -1497,11 +1800,10 @@ static linview_status iter_sk_propagate_b(linview_program* p, int rb, cudaStream
     c += rb;
   }
   View& tk = ie_T(p, NT - 1);
-  LV_TRY(gemm_cm(p, false, true, pp, n, c, 1.0, p->Yar[cur], pp, p->Xar[cur], fs, 1.0, tk.ptr,
-                 tk.ld, s, exact_mode(p)));
+  LV_TRY(gemm_cm_own(p, false, true, pp, n, c, 1.0, p->Yar[cur], pp, p->Xar[cur], fs, 1.0, tk.ptr,
+                 tk.ld, s));
   // B += U_b V_b^T (column-major B^T, p x n)
-  LV_TRY(gemm_cm(p, false, true, pp, n, rb, 1.0, p->Mr, pp, p->Uar, fs, 1.0, p->Bm, p->ldB, s,
-                 exact_mode(p)));
+  LV_TRY(gemm_cm_own(p, false, true, pp, n, rb, 1.0, p->Mr, pp, p->Uar, fs, 1.0, p->Bm, p->ldB, s));
   return LINVIEW_OK;
 }
 
@@ -1526,13 +1828,13 @@ static linview_status ols_reeval_t(linview_program* p, cudaStream_t s) {
   const int64_t ch = p->ols_chunk;
   if (!p->Z64) {
     void* t;
-    LV_TRY(dalloc(p, sizeof(double) * n * n, &t)); p->Z64 = static_cast<double*>(t);
-    LV_TRY(dalloc(p, sizeof(double) * n * n, &t)); p->W64 = static_cast<double*>(t);
-    LV_TRY(dalloc(p, sizeof(double) * ch * n, &t)); p->X64 = static_cast<double*>(t);
-    LV_TRY(dalloc(p, sizeof(double) * ch * pp, &t)); p->Y64 = static_cast<double*>(t);
-    LV_TRY(dalloc(p, sizeof(double) * n * pp, &t)); p->XtY64 = static_cast<double*>(t);
-    LV_TRY(dalloc(p, sizeof(double) * n * pp, &t)); p->B64 = static_cast<double*>(t);
-    LV_TRY(dalloc(p, sizeof(int) * 4, &t)); p->solver_info = static_cast<int*>(t);
+    LV_TRY(dalloc(p, sizeof(double) * n * n, &t, s)); p->Z64 = static_cast<double*>(t);
+    LV_TRY(dalloc(p, sizeof(double) * n * n, &t, s)); p->W64 = static_cast<double*>(t);
+    LV_TRY(dalloc(p, sizeof(double) * ch * n, &t, s)); p->X64 = static_cast<double*>(t);
+    LV_TRY(dalloc(p, sizeof(double) * ch * pp, &t, s)); p->Y64 = static_cast<double*>(t);
+    LV_TRY(dalloc(p, sizeof(double) * n * pp, &t, s)); p->XtY64 = static_cast<double*>(t);
+    LV_TRY(dalloc(p, sizeof(double) * n * pp, &t, s)); p->B64 = static_cast<double*>(t);
+    LV_TRY(dalloc(p, sizeof(int) * 4, &t, s)); p->solver_info = static_cast<int*>(t);
   }
   if (!p->solver && cusolverDnCreate(&p->solver) != CUSOLVER_STATUS_SUCCESS)
     return fail(LINVIEW_EDEVICE, "cusolverDnCreate failed");
@@ -1561,7 +1863,7 @@ static linview_status ols_reeval_t(linview_program* p, cudaStream_t s) {
                                           (int)n, &l2));
     p->solver_lwork = l1 > l2 ? l1 : l2;
     void* t;
-    LV_TRY(dalloc(p, sizeof(double) * (size_t)p->solver_lwork, &t));
+    LV_TRY(dalloc(p, sizeof(double) * (size_t)p->solver_lwork, &t, s));
     p->solver_work = static_cast<double*>(t);
   }
   LV_SOLVER(cusolverDnDpotrf(p->solver, CUBLAS_FILL_MODE_LOWER, (int)n, p->Z64, (int)n,
@@ -1598,38 +1900,38 @@ static linview_status ols_create(linview_program* p, const void* const* inputs,
   if (2 * kmax > 64) return fail(LINVIEW_EUNSUPPORTED, "row blocks are limited to k <= 32");
   if (lds[0] < n || lds[1] < pp) return fail(LINVIEW_ESHAPE, "bad leading dims");
   p->fs = rup(n, 64);
-  LV_TRY(add_square_view(p, n));                     // W
+  LV_TRY(add_square_view(p, n, s));                     // W
   const int64_t ldp = rup(pp, 4);
   void* t;
-  LV_TRY(dalloc(p, (size_t)n * ldp * p->elem, &t));   // beta
+  LV_TRY(dalloc(p, (size_t)n * ldp * p->elem, &t, s));   // beta
   LV_TRY(add_rect_view(p, t, n, pp, ldp));
-  LV_TRY(dalloc(p, (size_t)n * ldp * p->elem, &t));   // X^T Y
+  LV_TRY(dalloc(p, (size_t)n * ldp * p->elem, &t, s));   // X^T Y
   LV_TRY(add_rect_view(p, t, n, pp, ldp));
   p->ldX = rup(n, 64);
-  LV_TRY(dalloc(p, (size_t)m * p->ldX * p->elem, &p->Xd));
+  LV_TRY(dalloc(p, (size_t)m * p->ldX * p->elem, &p->Xd, s));
   LV_TRY(add_rect_view(p, p->Xd, m, n, p->ldX));
   p->ldY = ldp;
-  LV_TRY(dalloc(p, (size_t)m * p->ldY * p->elem, &p->Yd));
+  LV_TRY(dalloc(p, (size_t)m * p->ldY * p->elem, &p->Yd, s));
   LV_TRY(copy_in(p->Xd, p->ldX, inputs[0], lds[0], m, n, p->elem, on_dev, s));
   LV_TRY(copy_in(p->Yd, p->ldY, inputs[1], lds[1], m, pp, p->elem, on_dev, s));
   const int kk = 2 * kmax;
-  LV_TRY(dalloc(p, (size_t)p->fs * pp * p->elem, &p->XtYc));
-  LV_TRY(dalloc(p, (size_t)p->fs * kk * p->elem, &p->Uar));
-  LV_TRY(dalloc(p, (size_t)p->fs * kk * p->elem, &p->Gf));
-  LV_TRY(dalloc(p, (size_t)p->fs * kk * p->elem, &p->Wuf));
-  LV_TRY(dalloc(p, (size_t)kk * pp * p->elem, &p->Hols));
-  LV_TRY(dalloc(p, (size_t)kmax * pp * p->elem, &p->Yr));
-  LV_TRY(dalloc(p, sizeof(int64_t) * kmax, &t));
+  LV_TRY(dalloc(p, (size_t)p->fs * pp * p->elem, &p->XtYc, s));
+  LV_TRY(dalloc(p, (size_t)p->fs * kk * p->elem, &p->Uar, s));
+  LV_TRY(dalloc(p, (size_t)p->fs * kk * p->elem, &p->Gf, s));
+  LV_TRY(dalloc(p, (size_t)p->fs * kk * p->elem, &p->Wuf, s));
+  LV_TRY(dalloc(p, (size_t)kk * pp * p->elem, &p->Hols, s));
+  LV_TRY(dalloc(p, (size_t)kmax * pp * p->elem, &p->Yr, s));
+  LV_TRY(dalloc(p, sizeof(int64_t) * kmax, &t, s));
   p->rows_d = static_cast<int64_t*>(t);
-  LV_TRY(dalloc(p, sizeof(double) * kk * kk, &t));
+  LV_TRY(dalloc(p, sizeof(double) * kk * kk, &t, s));
   p->Minv = static_cast<double*>(t);
   const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
   p->part_cs = p->fs;
   const int64_t width = (kk > pp) ? kk : pp;
   p->xp_s = rup(width, kMaxFusedR) * p->part_cs;
   p->yp_q = p->xp_s;
-  LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart));
-  LV_TRY(dalloc(p, (size_t)g.gR * kMaxFusedR * p->part_cs * p->elem, &p->Ypart));
+  LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart, s));
+  LV_TRY(dalloc(p, (size_t)g.gR * kMaxFusedR * p->part_cs * p->elem, &p->Ypart, s));
   p->ols_chunk = m < 8192 ? m : 8192;
   return p->elem == 4 ? ols_reeval_t<float>(p, s) : ols_reeval_t<double>(p, s);
 }
@@ -1712,6 +2014,8 @@ linview_status linview_create_program(const linview_program_desc* desc, const vo
   if (desc->n < 1 || desc->n > (1 << 20)) return fail(LINVIEW_EINVAL, "bad n=%lld", (long long)desc->n);
   if (desc->r_max < 1) return fail(LINVIEW_EINVAL, "r_max must be >= 1");
   if (desc->correction_period < 0) return fail(LINVIEW_EINVAL, "correction_period < 0");
+  if ((desc->alloc == nullptr) != (desc->free == nullptr))
+    return fail(LINVIEW_EINVAL, "alloc and free must both be given or both be NULL");
   if (desc->model != LINVIEW_MODEL_EXP &&
       !(desc->model == LINVIEW_MODEL_LINEAR &&
         (desc->kind == LINVIEW_POWER || desc->kind == LINVIEW_POWER_SUM ||
@@ -1751,19 +2055,25 @@ linview_status linview_create_program(const linview_program_desc* desc, const vo
   }
   if (st == LINVIEW_OK) {
     void* tmp = nullptr;
-    st = dalloc(p, sizeof(unsigned) * 4, &tmp);
+    st = dalloc(p, sizeof(unsigned) * 4, &tmp, s);
     p->status = static_cast<unsigned*>(tmp);
     p->ticket = p->status + 1;
   }
   if (st == LINVIEW_OK) {
     void* tmp = nullptr;
-    st = dalloc(p, sizeof(double) * 64 * 64, &tmp);
+    st = dalloc(p, sizeof(double) * 64 * 64, &tmp, s);
     p->C = static_cast<double*>(tmp);
   }
   if (st == LINVIEW_OK) {
     void* tmp = nullptr;
-    st = dalloc(p, cpart_bytes(desc->n), &tmp);
+    st = dalloc(p, cpart_bytes(desc->n), &tmp, s);
     p->Cpart = static_cast<double*>(tmp);
+  }
+  if (st == LINVIEW_OK) {  // split-K partials of the CUDA-core GEMM
+    void* tmp = nullptr;
+    st = dalloc(p, kGemmWorkBytes, &tmp, s);
+    p->gwork = tmp;
+    p->gwork_elems = (int64_t)kGemmWorkBytes / p->elem;
   }
   if (st == LINVIEW_OK) {
     switch (desc->kind) {
@@ -1789,7 +2099,12 @@ void linview_destroy(linview_program* p) {
   if (!p) return;
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
-  for (void* a : p->allocs) cudaFree(a);
+  for (auto& a : p->allocs) {
+    if (p->d.free)
+      p->d.free(a.first, a.second, nullptr, p->d.alloc_ctx);
+    else if (!p->d.alloc)
+      cudaFree(a.first);
+  }
   for (auto& ge : p->graphs) cudaGraphExecDestroy(ge.exec);
   for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   for (cudaEvent_t e : p->gev_pool) cudaEventDestroy(e);
@@ -1904,7 +2219,7 @@ linview_status linview_reeval(linview_program* p, void* stream) {
 
 linview_status linview_set_reeval_mode(linview_program* p, int mode) {
   if (!p) return fail(LINVIEW_EINVAL, "null program");
-  if (mode < LINVIEW_REEVAL_DEFAULT || mode > LINVIEW_REEVAL_FP64)
+  if (mode < LINVIEW_REEVAL_DEFAULT || mode > LINVIEW_REEVAL_TC3)
     return fail(LINVIEW_EINVAL, "bad reeval mode %d", mode);
   if (p->elem == 8 && mode != LINVIEW_REEVAL_DEFAULT && mode != LINVIEW_REEVAL_FP64)
     return fail(LINVIEW_EINVAL, "FP64 programs re-evaluate in FP64");
@@ -2057,7 +2372,7 @@ static linview_status apply_b_delta(linview_program* p, int r, const void* U, in
   const void* u = U;
   const void* v = V;
   if (!on_device) {
-    LV_TRY(ensure_stage(p, (size_t)(n + pp) * r * p->elem));
+    LV_TRY(ensure_stage(p, (size_t)(n + pp) * r * p->elem, s));
     char* st = static_cast<char*>(p->stage);
     LV_TRY(copy_in(st, r, U, ldu, n, r, p->elem, 0, s));
     LV_TRY(copy_in(st + (size_t)n * r * p->elem, r, V, ldv, pp, r, p->elem, 0, s));
@@ -2104,7 +2419,7 @@ linview_status linview_apply_delta(linview_program* p, int input_id, int64_t ran
   const void* u = U;
   const void* v = V;
   if (!on_device) {
-    LV_TRY(ensure_stage(p, (size_t)2 * n * r * p->elem));
+    LV_TRY(ensure_stage(p, (size_t)2 * n * r * p->elem, s));
     char* st = static_cast<char*>(p->stage);
     LV_TRY(copy_in(st, r, U, ldu, n, r, p->elem, 0, s));
     LV_TRY(copy_in(st + (size_t)n * r * p->elem, r, V, ldv, n, r, p->elem, 0, s));
@@ -2228,34 +2543,33 @@ static linview_status adjoint_iteration(linview_program* p, const void* Gk, int6
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!p->Gpanel) {
     p->ldG = rup((int64_t)k * pp, 64);
-    LV_TRY(dalloc(p, (size_t)n * p->ldG * p->elem, &p->Gpanel));
+    LV_TRY(dalloc(p, (size_t)n * p->ldG * p->elem, &p->Gpanel, s));
   }
-  const int mode = exact_mode(p);
   const int e = p->elem;
   char* G = static_cast<char*>(p->Gpanel);
   char* T = static_cast<char*>(p->Tpanel);
   int64_t ldT = p->ldT;
   View& a = p->views[0];
+  // split operands of the tensor-core products (FP32): up to n rows each, inner
+  // length up to max(n, k p)
+  TcScratch sc;
+  LV_TRY(tc_scratch(p, &sc, n, n, n > k * pp ? n : k * pp, s));
   if (iter_exp(p)) {
     // the exponential and skip models keep only some T_i: the reverse pass
     // needs T_0 .. T_k, recomputed here as T_i = A T_{i-1} + B (the same
     // function of (A, B, T_0), so the same gradient)
     if (!p->Tfull) {
       p->ldTf = rup((int64_t)(k + 1) * pp, 64);
-      LV_TRY(dalloc(p, (size_t)n * p->ldTf * p->elem, &p->Tfull));
+      LV_TRY(dalloc(p, (size_t)n * p->ldTf * p->elem, &p->Tfull, s));
     }
     T = static_cast<char*>(p->Tfull);
     ldT = p->ldTf;
     const View& t0 = p->views[p->ie_NT + 2];
     LV_CUDA(cudaMemcpy2DAsync(T, ldT * e, t0.ptr, t0.ld * e, pp * e, n, cudaMemcpyDeviceToDevice,
                               s));
-    for (int i = 1; i <= k; ++i) {
-      char* ti = T + (size_t)i * pp * e;
-      LV_CUDA(cudaMemcpy2DAsync(ti, ldT * e, p->Bm, p->ldB * e, pp * e, n,
-                                cudaMemcpyDeviceToDevice, s));
-      LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, a.ptr, a.ld, T + (size_t)(i - 1) * pp * e,
-                     ldT, 1.0, ti, ldT, s, mode));
-    }
+    for (int i = 1; i <= k; ++i)
+      LV_TRY(gemm_ab(p, n, pp, n, 1.0, rows_of(a.ptr, a.ld), cols_of(T + (size_t)(i - 1) * pp * e, ldT),
+                     1.0, p->Bm, p->ldB, T + (size_t)i * pp * e, ldT, s, &sc, i > 1));
   }
   // G_k = seed; G_i = A^T G_{i+1}
   void* gk = G + (size_t)(k - 1) * pp * e;
@@ -2270,11 +2584,19 @@ static linview_status adjoint_iteration(linview_program* p, const void* Gk, int6
                                       static_cast<const double*>(src), lds, Gk ? 1.0 : 2.0,
                                       (int)n, (int)pp, s));
   p->all_launches++;
+  // the rows of A^T are split once for all the products A^T G
+  bool at_split = false;
   for (int i = k - 1; i >= 1; --i) {
     void* gi = G + (size_t)(i - 1) * pp * e;
     void* gn = G + (size_t)i * pp * e;
-    LV_TRY(gemm_rm(p, true, false, n, pp, n, 1.0, a.ptr, a.ld, gn, p->ldG, 0.0, gi, p->ldG, s,
-                   mode));
+    LV_TRY(gemm_ab(p, n, pp, n, 1.0, cols_of(a.ptr, a.ld), cols_of(gn, p->ldG), 0.0, nullptr, 0,
+                   gi, p->ldG, s, &sc, at_split));
+    at_split = true;
+  }
+  if (dT0) {
+    // dL/dT_0 = A^T G_1
+    LV_TRY(gemm_ab(p, n, pp, n, 1.0, cols_of(a.ptr, a.ld), cols_of(G, p->ldG), 0.0, nullptr, 0,
+                   dT0, ld_dT0, s, &sc, at_split));
   }
   if (dB) {
     LV_CUDA(cudaMemcpy2DAsync(dB, ld_dB * e, G, p->ldG * e, pp * e, n, cudaMemcpyDeviceToDevice, s));
@@ -2290,14 +2612,9 @@ static linview_status adjoint_iteration(linview_program* p, const void* Gk, int6
     }
   }
   if (dA) {
-    // dA = [G_1 .. G_k] [T_0 .. T_{k-1}]^T, one GEMM with inner dimension k p
-    LV_TRY(gemm_rm(p, false, true, n, n, (int64_t)k * pp, 1.0, G, p->ldG, T, ldT, 0.0, dA,
-                   ld_dA, s, mode));
-  }
-  if (dT0) {
-    // dL/dT_0 = A^T G_1
-    LV_TRY(gemm_rm(p, true, false, n, pp, n, 1.0, a.ptr, a.ld, G, p->ldG, 0.0, dT0, ld_dT0, s,
-                   mode));
+    // dA = [G_1 .. G_k] [T_0 .. T_{k-1}]^T, one product with inner dimension k p
+    LV_TRY(gemm_ab(p, n, n, (int64_t)k * pp, 1.0, rows_of(G, p->ldG), rows_of(T, ldT), 0.0,
+                   nullptr, 0, dA, ld_dA, s, &sc));
   }
   return LINVIEW_OK;
 }
@@ -2328,24 +2645,67 @@ linview_status linview_adjoint_power(linview_program* p, const void* G, int64_t 
   const int e = p->elem;
   const int64_t ldw = rup(n, 64);
   if (!p->Gw0) {
-    LV_TRY(dalloc(p, (size_t)n * ldw * e, &p->Gw0));
-    LV_TRY(dalloc(p, (size_t)n * ldw * e, &p->Gw1));
+    LV_TRY(dalloc(p, (size_t)n * ldw * e, &p->Gw0, s));
+    LV_TRY(dalloc(p, (size_t)n * ldw * e, &p->Gw1, s));
   }
-  const int mode = exact_mode(p);
   LV_CUDA(cudaMemcpy2DAsync(p->Gw0, ldw * e, G, ldg * e, n * e, n, cudaMemcpyDeviceToDevice, s));
   void* cur = p->Gw0;
   void* nxt = p->Gw1;
+  TcScratch sc;
+  LV_TRY(tc_scratch(p, &sc, n, n, n, s));
   // Gbar_h = Gbar_{2h} P_h^T + P_h^T Gbar_{2h}, h = k/2, ..., 1
   for (int l = p->L - 1; l >= 0; --l) {
     View& ph = pview(p, l);
-    LV_TRY(gemm_rm(p, false, true, n, n, n, 1.0, cur, ldw, ph.ptr, ph.ld, 0.0, nxt, ldw, s, mode));
-    LV_TRY(gemm_rm(p, true, false, n, n, n, 1.0, ph.ptr, ph.ld, cur, ldw, 1.0, nxt, ldw, s, mode));
+    LV_TRY(gemm_ab(p, n, n, n, 1.0, rows_of(cur, ldw), rows_of(ph.ptr, ph.ld), 0.0, nullptr, 0,
+                   nxt, ldw, s, &sc));
+    LV_TRY(gemm_ab(p, n, n, n, 1.0, cols_of(ph.ptr, ph.ld), cols_of(cur, ldw), 1.0, nxt, ldw, nxt,
+                   ldw, s, &sc));
     void* t = cur;
     cur = nxt;
     nxt = t;
   }
   LV_CUDA(cudaMemcpy2DAsync(dA, ld_dA * e, cur, ldw * e, n * e, n, cudaMemcpyDeviceToDevice, s));
   return LINVIEW_OK;
+}
+
+// ------------------------------------------------------ stand-alone product
+linview_status linview_gemm(int precision, int ta, int tb, int64_t M, int64_t N, int64_t K,
+                            double alpha, const void* A, int64_t lda, const void* B, int64_t ldb,
+                            double beta, void* C, int64_t ldc, void* stream) {
+  if (precision != LINVIEW_F32 && precision != LINVIEW_F64)
+    return fail(LINVIEW_EINVAL, "bad precision");
+  if (M < 0 || N < 0 || K < 1 || M > (1 << 30) || N > (1 << 30) || K > (1 << 30))
+    return fail(LINVIEW_EINVAL, "need M, N >= 0 and K >= 1");
+  if (M == 0 || N == 0) return LINVIEW_OK;  // empty result: nothing to read or write
+  if (!A || !B || !C) return fail(LINVIEW_EINVAL, "null argument");
+  if (ldc < N || lda < (ta ? M : K) || ldb < (tb ? K : N))
+    return fail(LINVIEW_ESHAPE, "leading dimension smaller than the row length");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  linview_program tmp;  // borrowed machinery, no views owned
+  tmp.elem = precision == LINVIEW_F64 ? 8 : 4;
+  cudaGetDevice(&tmp.device);
+  cudaDeviceGetAttribute(&tmp.sms, cudaDevAttrMultiProcessorCount, tmp.device);
+  void* work = nullptr;
+  LV_TRY(talloc(&tmp, kGemmWorkBytes + 256, &work, s));
+  tmp.status = static_cast<unsigned*>(work);
+  tmp.gwork = static_cast<char*>(work) + 256;
+  tmp.gwork_elems = (int64_t)kGemmWorkBytes / tmp.elem;
+  cudaError_t ce = cudaMemsetAsync(work, 0, 256, s);
+  linview_status st = ce == cudaSuccess ? LINVIEW_OK : fail(LINVIEW_EDEVICE, "memset failed");
+  if (st == LINVIEW_OK) {
+    TcScratch sc;
+    st = tc_scratch(&tmp, &sc, M, N, K, s);
+    // op(A) rows; op(B)^T rows (op(B) is K x N)
+    const Opnd a = ta ? cols_of(A, lda) : rows_of(A, lda);
+    const Opnd b = tb ? rows_of(B, ldb) : cols_of(B, ldb);
+    if (st == LINVIEW_OK) st = gemm_ab(&tmp, M, N, K, alpha, a, b, beta, C, ldc, C, ldc, s, &sc);
+  }
+  unsigned hs = 0;
+  cudaMemcpyAsync(&hs, tmp.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  tfree(&tmp, work, kGemmWorkBytes + 256, s);
+  LV_CUDA(cudaStreamSynchronize(s));
+  if (st == LINVIEW_OK && (hs & kStatusTimeout)) st = fail(LINVIEW_ETIMEOUT, "bounded wait expired");
+  return st;
 }
 
 // ------------------------------------------------------ stand-alone level pass

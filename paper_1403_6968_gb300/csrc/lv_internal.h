@@ -99,6 +99,30 @@ cudaError_t launch_tc_update(const CUtensorMap& tmP, const CUtensorMap& tmA,
                              float* Bcat, const float* U, const float* W, int64_t fs, int n, int r,
                              int num_sms, unsigned* status, cudaStream_t s);
 
+// Own dense GEMMs (lv_gemm.cu).
+// Split-TF32 operand rows: rows x tc_split_ld(K) floats, row i = [hi | lo]
+// (each half rup(K, 32) long, zero past K).
+int64_t tc_split_ld(int64_t K);
+// Split the rows of op(X) (element (i, k) at X[i * rs + k * cs], rs or cs == 1)
+// into dst (ldd >= tc_split_ld(K)).
+cudaError_t launch_split_rows(const float* X, int64_t rs, int64_t cs, int rows, int K, float* dst,
+                              int64_t ldd, cudaStream_t s);
+// D (M x N, row-major, ldd) = alpha A_s B_s^T + beta C on the tensor cores
+// (split TF32, FP32 accumulation), A_s / B_s split rows of inner length K
+// (16-byte aligned).  C may alias D (beta == 0 ignores it).
+cudaError_t launch_tc_gemm(const float* As, const float* Bs, int M, int N, int K, float* D,
+                           int64_t ldd, const float* C, int64_t ldc, float alpha, float beta,
+                           int num_sms, unsigned* status, cudaStream_t s);
+// C (M x N) = alpha A B + beta C on the CUDA cores, A(m, k) = A[m a_rs + k a_cs],
+// B(k, n) = B[k b_rs + n b_cs], C(m, n) = C[m c_rs + n c_cs]; long inner
+// dimensions are split over ``work`` (work_elems elements, may be null) and
+// the partials summed in a fixed order.
+template <typename T>
+cudaError_t launch_gemm_simt(int M, int N, int K, T alpha, const T* A, int64_t a_rs, int64_t a_cs,
+                             const T* B, int64_t b_rs, int64_t b_cs, T beta, T* C, int64_t c_rs,
+                             int64_t c_cs, T* work, int64_t work_elems, int num_sms,
+                             cudaStream_t s);
+
 // Launchers (return cudaGetLastError()).  R is the runtime factor width,
 // bucketed internally to a compiled width.  The passes are launched with
 // programmatic stream serialisation, and the FP32 passes request their first

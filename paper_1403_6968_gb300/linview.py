@@ -18,7 +18,7 @@ KINDS = {"power": L.POWER, "power_sum": L.POWER_SUM, "iteration": L.ITERATION, "
 MODELS = {"exp": L.MODEL_EXP, "linear": L.MODEL_LINEAR, "skip": L.MODEL_SKIP}
 STRATEGIES = {"factored": L.STRATEGY_FACTORED, "hybrid": L.STRATEGY_HYBRID}
 REEVAL = {"default": L.REEVAL_DEFAULT, "fp32": L.REEVAL_FP32, "tf32": L.REEVAL_TF32,
-          "bf16x9": L.REEVAL_BF16X9, "fp64": L.REEVAL_FP64}
+          "bf16x9": L.REEVAL_BF16X9, "fp64": L.REEVAL_FP64, "tc3": L.REEVAL_TC3}
 
 
 def _torch():
@@ -30,6 +30,54 @@ def _stream_ptr(stream=None):
     torch = _torch()
     s = torch.cuda.current_stream() if stream is None else stream
     return C.c_void_p(s.cuda_stream)
+
+
+_TORCH_CB = None
+_LIVE = None
+
+
+def _torch_allocator():
+    """The (alloc, free) callbacks that hand a program's device memory to
+    PyTorch's caching allocator (module-level, so they outlive every program).
+    ``alloc_ctx`` carries the device index + 1."""
+    global _TORCH_CB
+    if _TORCH_CB is None:
+        torch = _torch()
+
+        def alloc(nbytes, stream, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device=int(ctx or 1) - 1,
+                                                          stream=int(stream or 0))
+            except Exception:  # out of memory: the library reports ENOMEM
+                return None
+
+        def free(ptr, nbytes, stream, ctx):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        _TORCH_CB = (L.ALLOC_FN(alloc), L.FREE_FN(free))
+    return _TORCH_CB
+
+
+def _track(prog):
+    """Programs whose memory belongs to PyTorch are destroyed at exit, while
+    PyTorch can still take the memory back."""
+    global _LIVE
+    import atexit
+    import weakref
+    if _LIVE is None:
+        _LIVE = weakref.WeakSet()
+
+        def close_all():
+            for pr in list(_LIVE):
+                try:
+                    pr.close()
+                except Exception:
+                    pass
+        atexit.register(close_all)
+    _LIVE.add(prog)
 
 
 def _dtype_of(precision):
@@ -72,12 +120,16 @@ class Program:
     """A maintained program (powers, sums of powers, iteration, OLS).
 
     ``inputs`` are torch tensors (CUDA or CPU) or numpy arrays, all of the
-    program's element type (float32 or float64).
+    program's element type (float32 or float64).  ``allocator="torch"`` (the
+    default) gives the program's device memory to PyTorch's caching allocator
+    through the descriptor's alloc/free callbacks (so ``torch.cuda.
+    memory_allocated()`` counts it); ``allocator=None`` lets the library call
+    cudaMalloc itself.
     """
 
     def __init__(self, kind, inputs, k, r_max=1, precision="f32", p=0, m=0,
                  correction_period=0, reeval_mode="default", model=None, skip=0,
-                 strategy="factored", stream=None):
+                 strategy="factored", stream=None, allocator="torch"):
         self.lib = L.load()
         self.precision = L.F64 if precision in ("f64", "fp64", L.F64) else L.F32
         self.np_dtype = _dtype_of(self.precision)
@@ -97,6 +149,14 @@ class Program:
         d.model = MODELS[model] if isinstance(model, str) else int(model)
         d.skip = int(skip)
         d.strategy = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        if allocator == "torch":
+            torch = _torch()
+            fa, ff = _torch_allocator()
+            d.alloc = C.cast(fa, C.c_void_p).value
+            d.free = C.cast(ff, C.c_void_p).value
+            d.alloc_ctx = torch.cuda.current_device() + 1
+        elif allocator is not None:
+            raise ValueError("allocator must be 'torch' or None")
         on_dev = {o.on_device for o in ops}
         if len(on_dev) != 1:
             raise ValueError("inputs must all be on the device or all on the host")
@@ -107,6 +167,8 @@ class Program:
                C.byref(h))
         self.h = h
         self.desc = d
+        if allocator == "torch":
+            _track(self)
         self.n = d.n
         self.k = d.k
 
@@ -285,6 +347,26 @@ def level_pass(P, U, V, X=None, Y=None, do_update=True, stream=None):
            C.c_void_p(X.data_ptr()) if X is not None else None,
            C.c_void_p(Y.data_ptr()) if Y is not None else None,
            1 if do_update else 0, _stream_ptr(stream))
+
+
+def gemm(a, b, c, alpha=1.0, beta=0.0, ta=False, tb=False, stream=None):
+    """c = alpha op(a) op(b) + beta c with the library's own GEMM (CUDA
+    tensors, row-major, float32 or float64, unit inner stride)."""
+    torch = _torch()
+    for name, t in (("a", a), ("b", b), ("c", c)):
+        if t.dim() != 2 or not t.is_cuda or t.stride(1) != 1 or t.dtype != c.dtype:
+            raise ValueError(f"{name} must be a 2-D CUDA tensor of c's dtype with unit inner stride")
+        if t.device != c.device:
+            raise ValueError(f"{name} is not on c's device")
+    M, N = c.shape
+    K = a.shape[0] if ta else a.shape[1]
+    if (a.shape[1] if ta else a.shape[0]) != M or (b.shape[1] if tb else b.shape[0]) != K or \
+            (b.shape[0] if tb else b.shape[1]) != N:
+        raise ValueError("shapes of op(a), op(b) and c do not match")
+    prec = L.F64 if c.dtype == torch.float64 else L.F32
+    L.call("linview_gemm", prec, int(ta), int(tb), M, N, K, float(alpha),
+           C.c_void_p(a.data_ptr()), a.stride(0), C.c_void_p(b.data_ptr()), b.stride(0),
+           float(beta), C.c_void_p(c.data_ptr()), c.stride(0), _stream_ptr(stream))
 
 
 def check_bounded_wait(limit_ns=20_000_000, stream=None):
