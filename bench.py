@@ -60,6 +60,15 @@ def _args():
     ap.add_argument("--no-ksweep", action="store_true")
     ap.add_argument("--no-ols", action="store_true", help="skip the OLS row-block section")
     ap.add_argument("--no-general", action="store_true")
+    ap.add_argument("--gemm-n", type=int, default=8192, help="size of the gemm section's products")
+    ap.add_argument("--no-gemm", action="store_true")
+    ap.add_argument("--no-drift", action="store_true",
+                    help="skip the residual-correction drift section (two 200-update streams)")
+    ap.add_argument("--only", default=None,
+                    choices=["rank4_stream", "k_sweep", "iteration_p_sweep", "gd_regression",
+                             "small_fp64", "ols_row_blocks", "iteration_adjoint", "serving",
+                             "zipf_batches", "drift", "gemm"],
+                    help="run one secondary section alone (no headline line): profiling")
     return ap.parse_args()
 
 
@@ -174,10 +183,15 @@ def _peaks():
 
 
 def _pass_source_hash():
-    """Hash of the view-pass kernel sources (a capture is stale once they change)."""
+    """Hash of the view-pass kernel sources and of the parameter block they
+    take (a capture is stale once either changes)."""
     h = hashlib.sha256()
-    for f in ("lv_pass.cu", "lv_pass_ws.cuh", "lv_device.cuh", "lv_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1403_6968_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_1403_6968_gb300", "csrc")
+    for f in ("lv_pass.cu", "lv_pass_ws.cuh", "lv_device.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    hdr = open(os.path.join(csrc, "lv_internal.h"), "rb").read()
+    a = hdr.index(b"struct PassParams {")
+    h.update(hdr[a:hdr.index(b"};", a)])
     return h.hexdigest()[:16]
 
 
@@ -235,6 +249,37 @@ def cpu_oracle_errors(a32, ups, rows, row_sets, k):
             h = int(name[1:])
             errs[name] = rel_frob(got, (pr if name[0] == "P" else sr)[h])
         out[set_name] = errs
+    return out
+
+
+def drift_oracle_errors(d, a32, k):
+    """Part of the CPU-baseline leg: the FP64 oracle's rows at every checked
+    update of a drift_streams run, against the GPU rows of both runs."""
+    import numpy as np
+    from oracle import powers as op
+    from oracle.metrics import rel_frob
+    a0 = a32.astype(np.float64)
+    out = {}
+    for name, st in d["streams"].items():
+        ups = st["ups"]
+        res = {cp: {} for cp in st["runs"]}
+        for t in d["checks"]:
+            rows = st["runs"][0]["rows_at"][t]["rows"]
+            if name == "rank1":
+                a = a0.copy()
+                for i, v in ups[:t]:
+                    a[i] += v.astype(np.float64)
+                pr, sr = op.power_rows(a, rows, k)
+            else:
+                u = np.concatenate([x for x, _ in ups[:t]], axis=1)
+                v = np.concatenate([y for _, y in ups[:t]], axis=1)
+                pr, sr = op.power_rows_factored(a0, u, v, rows, k)
+            for cp, run in st["runs"].items():
+                got = run["rows_at"][t]
+                assert got["rows"] == rows
+                res[cp][t] = {nm: rel_frob(x, (pr if nm[0] == "P" else sr)[int(nm[1:])])
+                              for nm, x in got["views"].items()}
+        out[name] = res
     return out
 
 
@@ -300,7 +345,7 @@ def run_ours(args):
     K, W, E = args.steps, args.warmup, args.e2e_steps
     a = li.power_matrix(n, seed=rank, dtype=np.float32)
     KR = min(K, 16)  # updates of the roofline region (one per instrumented graph copy)
-    ups = li.row_update_stream(n, W + 1 + K + KR + E + args.reeval_steps + 1, seed=rank,
+    ups = li.row_update_stream(n, W + 1 + K + KR + E + 4 * args.reeval_steps + 1, seed=rank,
                                dtype=np.float32)
     dev_v = [torch.from_numpy(v).cuda() for _, v in ups]
     rows = [i for i, _ in ups]
@@ -435,21 +480,29 @@ def run_ours(args):
                 rr[f"S{1 << j}"] = np.stack([prog.read_view_rows(L + j, i, 1)[0]
                                              for i in chk_rows])
             reeval_rows[mode] = rr
+        # re-evaluation strategy per update: apply dA to A (a level pass,
+        # 0.3 ms, untimed), then recompute every view (timed with CUDA events);
+        # each arithmetic warmed up once first (library set-up, work space)
         aptr, ald = prog.view_device_ptr(0)
+        ti = W1 + K + KR + E
         for mode in modes:
             prog.set_reeval_mode(mode)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            prog.reeval()
+            tot = 0.0
             for t in range(args.reeval_steps):
-                ti = W1 + K + KR + E + t
                 u = torch.zeros((1, n), dtype=torch.float32, device="cuda")
                 u[0, rows[ti]] = 1.0
                 _apply_to_a(aptr, ald, n, u, dev_v[ti].reshape(1, n))
+                ti += 1
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
                 prog.reeval()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / args.reeval_steps
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            ms = tot / args.reeval_steps
             reeval[mode] = {"refreshes_per_s": 1e3 / ms, "ms_per_refresh": ms,
                             "gemm": "own tcgen05 split TF32" if mode == "tc3" else "cuBLAS"}
         prog.set_reeval_mode("default")
@@ -510,6 +563,11 @@ def run_ours(args):
 
     if not args.no_rank4:
         section("rank4_stream", lambda: rank_stream(args, 4, seed=rank))
+    if not args.no_gemm:
+        section("gemm", lambda: gemm_section(args))
+    if not args.no_drift and ws == 1:
+        section("drift", lambda: drift_report(drift_streams(args), _drift_a(args), k,
+                                              not args.no_cpu_baseline))
     if not args.no_ksweep:
         section("k_sweep", lambda: k_sweep(args, seed=rank))
     if not args.no_general:
@@ -567,6 +625,144 @@ def rank_stream(args, r, seed=0, steps=20, warmup=3):
             "achieved_refresh_gbs": alg / (tot_ms / steps / 1e3) / 1e9,
             "note": "achieved GB/s counts each of the 9 views read and written once per "
                     "refresh (the method's minimum traffic)"}
+
+
+def drift_streams(args, seed=0, count=200, period=64, checks=(1, 50, 100, 150, 200)):
+    """Residual correction, measured: the powers + sums program (A^16 and S',
+    n = 8192, FP32) under the 200-update rank-1 row stream and the 200-update
+    rank-4 stream, once without correction and once re-evaluated every
+    ``period`` updates (the library's own split-TF32 GEMM).  At the checked
+    updates, sampled rows of every view are read back; the CPU-baseline leg
+    compares them with the FP64 oracle (drift_oracle_errors).  Reports the
+    time of an ordinary update and of a correcting one."""
+    import numpy as np
+    import torch
+    import linview_inputs as li
+    from paper_1403_6968_gb300 import Program
+
+    n, k = args.n, args.k
+    L = k.bit_length() - 1
+    a = li.power_matrix(n, seed=seed, dtype=np.float32)
+    g = np.random.default_rng(4321)
+    fixed = sorted(set(int(i) for i in g.choice(n, 14, replace=False)) | {0, n - 1})
+    vnames = [f"P{1 << j}" for j in range(L + 1)] + [f"S{1 << j}" for j in range(1, L + 1)]
+    vids = list(range(L + 1)) + [L + j for j in range(1, L + 1)]
+    streams = {}
+    for rank in (1, 4):
+        if rank == 1:
+            ups = li.row_update_stream(n, count, seed=seed, dtype=np.float32)
+            dev = [(int(i), torch.from_numpy(v).cuda()) for i, v in ups]
+        else:
+            ups = li.lowrank_update_stream(n, 4, count, seed=seed, dtype=np.float32)
+            dev = [(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda()) for u, v in ups]
+        runs = {}
+        for cp in (0, period):
+            prog = Program("power_sum", [torch.from_numpy(a).cuda()], k=k, r_max=rank,
+                           correction_period=cp)
+            stream = torch.cuda.current_stream()
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(count + 1)]
+            rows_at = {}
+            torch.cuda.synchronize()
+            evs[0].record(stream)
+            for t in range(1, count + 1):
+                if rank == 1:
+                    prog.apply_row_delta(*dev[t - 1])
+                else:
+                    prog.apply_delta(*dev[t - 1])
+                evs[t].record(stream)
+                if t in checks:
+                    rows = sorted(set(fixed) | ({dev[t - 1][0]} if rank == 1 else set()))
+                    torch.cuda.synchronize()
+                    rows_at[t] = {"rows": rows, "views": {
+                        nm: np.stack([prog.read_view_rows(vid, i, 1)[0] for i in rows])
+                        for nm, vid in zip(vnames, vids)}}
+                    evs[t].synchronize()
+            torch.cuda.synchronize()
+            # per-update times (an event pair per update; the checks happen
+            # outside the measured intervals only for the update they follow)
+            ms = [evs[t - 1].elapsed_time(evs[t]) for t in range(1, count + 1)
+                  if (t - 1) not in checks]
+            corr = [evs[t - 1].elapsed_time(evs[t]) for t in range(1, count + 1)
+                    if cp and t % cp == 0 and (t - 1) not in checks]
+            plain = [evs[t - 1].elapsed_time(evs[t]) for t in range(1, count + 1)
+                     if not (cp and t % cp == 0) and (t - 1) not in checks]
+            runs[cp] = {"rows_at": rows_at,
+                        "ms_per_update": float(np.mean(ms)),
+                        "ms_plain_update": float(np.median(plain)),
+                        "ms_correcting_update": float(np.median(corr)) if corr else None}
+            prog.close()
+        streams[f"rank{rank}"] = {"ups": ups, "runs": runs}
+    return {"n": n, "k": k, "updates": count, "correction_period": period,
+            "checks": list(checks), "streams": streams}
+
+
+def drift_report(d, a32, k, with_oracle):
+    """The JSON form of a drift_streams result; with_oracle: add the FP64
+    oracle errors (part of the CPU-baseline leg)."""
+    out = {"n": d["n"], "k": d["k"], "updates": d["updates"],
+           "correction_period": d["correction_period"], "checks": d["checks"], "streams": {}}
+    errs = drift_oracle_errors(d, a32, k) if with_oracle else None
+    for name, st in d["streams"].items():
+        rep = {}
+        for cp, run in st["runs"].items():
+            key = "no_correction" if cp == 0 else f"corrected_every_{cp}"
+            r = {"ms_per_update": run["ms_per_update"], "ms_plain_update": run["ms_plain_update"],
+                 "ms_correcting_update": run["ms_correcting_update"]}
+            if errs is not None:
+                e = errs[name][cp]
+                r["oracle_rel_err_max_at"] = {str(t): max(v.values()) for t, v in e.items()}
+                last = max(e)
+                r["oracle_rel_err_per_view_at_last"] = e[last]
+            rep[key] = r
+        out["streams"][name] = rep
+    out["how"] = ("sampled rows (14 fixed, plus the updated row for row updates) of all 9 views "
+                  "at the checked updates vs the FP64 oracle's rows computed from the plain "
+                  "definition on the updated A; times are CUDA-event intervals per update")
+    return out
+
+
+def gemm_section(args, reps=3):
+    """The library's own GEMM on the workloads' products: the n^3 squaring of
+    re-evaluation, dA = [G][T]^T of the adjoint (inner dimension k p = 1024)
+    and the n x n x p product of the iteration (p = 64), FP32 in split TF32
+    on tcgen05.  Effective TFLOP/s counts 2 M N K; the tensor pipe runs three
+    TF32 products per output, so its roofline is 3 x that against the TF32
+    peak (the measured dense BF16 peak x 1/2, the nominal TF32 : BF16 ratio).
+    cuBLAS TF32 (one product, ~1e-3 relative) and IEEE FP32 are timed beside
+    it for context."""
+    import torch
+    from paper_1403_6968_gb300 import gemm
+    peaks = _peaks()
+    bf16 = peaks.get("bf16_tflops") if peaks else 1900.0
+    tf32_peak = 0.5 * bf16
+    n = args.gemm_n
+    shapes = [(n, n, n), (n, n, 1024), (n, 64, n)]
+    g = torch.Generator(device="cuda").manual_seed(0)
+    rows = []
+    for (M, N, K) in shapes:
+        a = torch.randn(M, K, device="cuda", generator=g)
+        b = torch.randn(K, N, device="cuda", generator=g)
+        c = torch.empty(M, N, device="cuda")
+        gemm(a, b, c)  # warm-up: tensor maps, kernel attributes, the memory pool
+        own = _event_ms(lambda j: gemm(a, b, c), reps)
+        ref = a.double() @ b.double()
+        err = float((c.double() - ref).norm() / ref.norm())
+        del ref
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True
+        torch.matmul(a, b, out=c)  # warm-up
+        t_tf32 = _event_ms(lambda j: torch.matmul(a, b, out=c), reps)
+        torch.backends.cuda.matmul.allow_tf32 = False
+        torch.matmul(a, b, out=c)
+        t_fp32 = _event_ms(lambda j: torch.matmul(a, b, out=c), reps)
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        eff = 2.0 * M * N * K / (own / 1e3) / 1e12
+        rows.append({"M": M, "N": N, "K": K, "own_ms": own, "own_tflops_effective": eff,
+                     "tensor_pipe_tflops": 3 * eff, "tensor_frac_of_tf32_peak": 3 * eff / tf32_peak,
+                     "rel_err_vs_fp64": err, "cublas_tf32_ms": t_tf32, "cublas_fp32_ms": t_fp32})
+    return {"rows": rows, "tf32_peak_tflops": tf32_peak,
+            "peak_source": ("measured bf16 x 0.5" if peaks else "fallback bf16 x 0.5"),
+            "note": "own_ms includes splitting both operands into [hi | lo] rows (one pass each)"}
 
 
 def k_sweep(args, seed=0, steps=8, warmup=2, ks=(2, 4, 8, 16, 32)):
@@ -972,12 +1168,42 @@ def _apply_to_a(aptr, ald, n, u, v):
            C.c_void_p(v.data_ptr()), n, 1, None, None, 1, _stream_ptr())
 
 
+def _drift_a(args, seed=0):
+    import numpy as np
+    import linview_inputs as li
+    return li.power_matrix(args.n, seed=seed, dtype=np.float32)
+
+
+def run_only(args):
+    """One secondary section alone on GPU 0, its result as one JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    fns = {"rank4_stream": lambda: rank_stream(args, 4),
+           "k_sweep": lambda: k_sweep(args),
+           "iteration_p_sweep": lambda: iteration_p_sweep(args),
+           "gd_regression": lambda: gd_regression(),
+           "small_fp64": lambda: small_fp64(),
+           "ols_row_blocks": lambda: ols_sweep(),
+           "iteration_adjoint": lambda: iteration_adjoint(),
+           "serving": lambda: serving_sweep(args),
+           "zipf_batches": lambda: zipf_batches(args),
+           "gemm": lambda: gemm_section(args),
+           "drift": lambda: drift_report(drift_streams(args), _drift_a(args), args.k,
+                                         not args.no_cpu_baseline)}
+    print(json.dumps({"section": args.only, args.only: fns[args.only]()}), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_ours(args)
 
 

@@ -694,10 +694,13 @@ static linview_status gemm_ab(linview_program* p, int64_t M, int64_t N, int64_t 
 // alpha op(A) op(B) + beta C with A, B column-major (lda, ldb): the CUDA-core
 // GEMM with the program's split-K partials (small products of the general
 // form, captured into the propagation graphs).
+// (batch > 1: ``batch`` such products, entry b at A + b a_bs, B + b b_bs,
+// C + b c_bs elements, strides possibly negative, in one launch)
 static linview_status gemm_cm_own(linview_program* p, bool ta, bool tb, int64_t M, int64_t N,
                                   int64_t K, double alpha, const void* A, int64_t lda,
                                   const void* B, int64_t ldb, double beta, void* C, int64_t ldc,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int batch = 1, int64_t a_bs = 0,
+                                  int64_t b_bs = 0, int64_t c_bs = 0) {
   if (M <= 0 || N <= 0) return LINVIEW_OK;
   // column-major X(i, j) = X[i + j ld]; op(A)(m, k), op(B)(k, n)
   const int64_t a_rs = ta ? lda : 1, a_cs = ta ? 1 : lda;
@@ -707,12 +710,13 @@ static linview_status gemm_cm_own(linview_program* p, bool ta, bool tb, int64_t 
                                     static_cast<const float*>(A), a_rs, a_cs,
                                     static_cast<const float*>(B), b_rs, b_cs, (float)beta,
                                     static_cast<float*>(C), 1, ldc, static_cast<float*>(p->gwork),
-                                    p->gwork_elems, p->sms, s));
+                                    p->gwork_elems, p->sms, s, batch, a_bs, b_bs, c_bs));
   else
     LV_CUDA(launch_gemm_simt<double>((int)M, (int)N, (int)K, alpha, static_cast<const double*>(A),
                                      a_rs, a_cs, static_cast<const double*>(B), b_rs, b_cs, beta,
                                      static_cast<double*>(C), 1, ldc,
-                                     static_cast<double*>(p->gwork), p->gwork_elems, p->sms, s));
+                                     static_cast<double*>(p->gwork), p->gwork_elems, p->sms, s,
+                                     batch, a_bs, b_bs, c_bs));
   p->all_launches += 2;
   return LINVIEW_OK;
 }
@@ -1294,13 +1298,10 @@ static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) 
   View& a = p->views[0];
   const PassGeom g = fused_geom(sizeof(T), n, p->sms);
   // M_i = T_i^T V (old T_i), stored at block k-1-i so that [M_{i-1} .. M_0]
-  // is one contiguous p x (i r) slab.
-  // column-major view: T_i is p x n (ld ldT), V is n x r (ld fs)
-  for (int i = 0; i < k; ++i) {
-    const void* ti = Tp + (size_t)i * pp * sizeof(T);
-    LV_TRY(gemm_cm_own(p, false, false, pp, r, n, 1.0, ti, p->ldT, V1, fs, 0.0,
-                   M + (int64_t)(k - 1 - i) * r * pp, pp, s));
-  }
+  // is one contiguous p x (i r) slab; all k products in one batched launch
+  // (column-major view: T_i is p x n (ld ldT) at panel block i, V is n x r (ld fs))
+  LV_TRY(gemm_cm_own(p, false, false, pp, r, n, 1.0, Tp, p->ldT, V1, fs, 0.0,
+                     M + (int64_t)(k - 1) * r * pp, pp, s, k, pp, 0, -(int64_t)r * pp));
   if (k >= 2) {
     {
       ProfScope ps(p, s, 0.0);

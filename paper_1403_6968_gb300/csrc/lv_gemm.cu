@@ -394,22 +394,28 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float* __restrict
 constexpr int kSB = 64;   // tile
 constexpr int kSK = 16;   // inner chunk
 
-// One tile of C (or of a split's partial): acc = sum over k in [k0, k1) of
-// A(m, k) B(k, n) with A(m, k) = A[m * a_rs + k * a_cs], B(k, n) = B[k * b_rs +
-// n * b_cs].  splits == 1: C(m, n) = alpha acc + beta C(m, n) (C(m, n) at
-// C[m * c_rs + n * c_cs]); else the partial goes to work[split][m][n].
+// One tile of C (or of a split's partial) of product z / splits of a batch:
+// acc = sum over k in [k0, k1) of A(m, k) B(k, n) with A(m, k) = A[m * a_rs +
+// k * a_cs], B(k, n) = B[k * b_rs + n * b_cs], the operands of batch entry b
+// at A + b * a_bs, B + b * b_bs, C + b * c_bs (strides may be negative).
+// splits == 1: C(m, n) = alpha acc + beta C(m, n) (C(m, n) at C[m * c_rs +
+// n * c_cs]); else the partial goes to work[b][split][m][n].
 template <typename T>
-__global__ void __launch_bounds__(256) gemm_simt_kernel(int M, int N, int K, int kchunk, T alpha,
-                                                        const T* __restrict__ A, int64_t a_rs,
-                                                        int64_t a_cs, const T* __restrict__ B,
-                                                        int64_t b_rs, int64_t b_cs, T beta, T* C,
-                                                        int64_t c_rs, int64_t c_cs, T* work) {
+__global__ void __launch_bounds__(256) gemm_simt_kernel(int M, int N, int K, int kchunk, int splits,
+                                                        T alpha, const T* __restrict__ A,
+                                                        int64_t a_rs, int64_t a_cs, int64_t a_bs,
+                                                        const T* __restrict__ B, int64_t b_rs,
+                                                        int64_t b_cs, int64_t b_bs, T beta, T* C,
+                                                        int64_t c_rs, int64_t c_cs, int64_t c_bs,
+                                                        T* work) {
   __shared__ T As[kSK][kSB + 1];
   __shared__ T Bs[kSK][kSB + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * kSB, n0 = blockIdx.x * kSB;
-  const int split = blockIdx.z;
+  const int bz = blockIdx.z / splits, split = blockIdx.z % splits;
+  A += (int64_t)bz * a_bs;
+  B += (int64_t)bz * b_bs;
   const int kbeg = split * kchunk;
   const int kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
   T acc[4][4];
@@ -460,6 +466,8 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(int M, int N, int K, int
     }
     __syncthreads();
   }
+  T* Cb = C + (int64_t)bz * c_bs;
+  T* wb = work ? work + ((int64_t)bz * splits + split) * M * N : nullptr;
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
     const int m = m0 + ty + 16 * x;
@@ -468,28 +476,40 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(int M, int N, int K, int
     for (int y = 0; y < 4; ++y) {
       const int n = n0 + tx + 16 * y;
       if (n >= N) continue;
-      if (work) {
-        work[((int64_t)split * M + m) * N + n] = acc[x][y];
+      if (wb) {
+        wb[(int64_t)m * N + n] = acc[x][y];
       } else {
-        T* c = C + (int64_t)m * c_rs + (int64_t)n * c_cs;
+        T* c = Cb + (int64_t)m * c_rs + (int64_t)n * c_cs;
         *c = beta == T(0) ? alpha * acc[x][y] : alpha * acc[x][y] + beta * *c;
       }
     }
   }
 }
 
-// C(m, n) = alpha sum_s work[s][m][n] + beta C(m, n), splits summed in order
+// C(m, n) of batch entry b = alpha sum_s work[b][s][m][n] + beta C(m, n): one
+// warp per output, lanes over the splits, then a fixed shuffle tree
+// (deterministic).
 template <typename T>
-__global__ void gemm_reduce_kernel(int M, int N, int splits, T alpha, const T* __restrict__ work,
-                                   T beta, T* C, int64_t c_rs, int64_t c_cs) {
-  const int64_t total = (int64_t)M * N;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
+__global__ void gemm_reduce_kernel(int M, int N, int splits, int batch, T alpha,
+                                   const T* __restrict__ work, T beta, T* C, int64_t c_rs,
+                                   int64_t c_cs, int64_t c_bs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t mn = (int64_t)M * N;
+  const int64_t total = mn * batch;
+  const int64_t wpb = blockDim.x / 32;
+  for (int64_t o = blockIdx.x * wpb + (threadIdx.x >> 5); o < total; o += (int64_t)gridDim.x * wpb) {
+    const int b = (int)(o / mn);
+    const int64_t e = o - (int64_t)b * mn;
+    const T* w = work + (int64_t)b * splits * mn + e;
     T s = T(0);
-    for (int q = 0; q < splits; ++q) s += work[(int64_t)q * total + e];
-    const int m = (int)(e / N), n = (int)(e - (int64_t)m * N);
-    T* c = C + (int64_t)m * c_rs + (int64_t)n * c_cs;
-    *c = beta == T(0) ? alpha * s : alpha * s + beta * *c;
+    for (int q = lane; q < splits; q += 32) s += w[(int64_t)q * mn];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+      const int m = (int)(e / N), n = (int)(e - (int64_t)m * N);
+      T* c = C + (int64_t)b * c_bs + (int64_t)m * c_rs + (int64_t)n * c_cs;
+      *c = beta == T(0) ? alpha * s : alpha * s + beta * *c;
+    }
   }
 }
 
@@ -550,12 +570,12 @@ cudaError_t launch_tc_gemm(const float* As, const float* Bs, int M, int N, int K
                               num_sms, status, s);
 }
 
-static int gemm_simt_splits(int M, int N, int K, int num_sms, int64_t work_elems) {
-  const int64_t tiles = (int64_t)((M + kSB - 1) / kSB) * ((N + kSB - 1) / kSB);
+static int gemm_simt_splits(int M, int N, int K, int batch, int num_sms, int64_t work_elems) {
+  const int64_t tiles = (int64_t)((M + kSB - 1) / kSB) * ((N + kSB - 1) / kSB) * batch;
   int splits = 1;
   // split long inner dimensions until about two waves of CTAs are running
-  while (tiles * splits < 2 * num_sms && K / (splits * 2) >= 4 * kSK &&
-         (int64_t)(splits * 2) * M * N <= work_elems)
+  while (tiles * splits < 2 * num_sms && K / (splits * 2) >= 8 * kSK &&
+         (int64_t)(splits * 2) * M * N * batch <= work_elems)
     splits *= 2;
   return splits;
 }
@@ -564,28 +584,31 @@ template <typename T>
 cudaError_t launch_gemm_simt(int M, int N, int K, T alpha, const T* A, int64_t a_rs, int64_t a_cs,
                              const T* B, int64_t b_rs, int64_t b_cs, T beta, T* C, int64_t c_rs,
                              int64_t c_cs, T* work, int64_t work_elems, int num_sms,
-                             cudaStream_t s) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
+                             cudaStream_t s, int batch, int64_t a_bs, int64_t b_bs,
+                             int64_t c_bs) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   if (K <= 0) return cudaErrorInvalidValue;
-  const int splits = work ? gemm_simt_splits(M, N, K, num_sms, work_elems) : 1;
+  const int splits = work ? gemm_simt_splits(M, N, K, batch, num_sms, work_elems) : 1;
   const int kchunk = ((K + splits - 1) / splits + kSK - 1) / kSK * kSK;
-  dim3 grid((N + kSB - 1) / kSB, (M + kSB - 1) / kSB, splits);
-  gemm_simt_kernel<T><<<grid, 256, 0, s>>>(M, N, K, kchunk, alpha, A, a_rs, a_cs, B, b_rs, b_cs,
-                                           beta, C, c_rs, c_cs, splits > 1 ? work : nullptr);
+  dim3 grid((N + kSB - 1) / kSB, (M + kSB - 1) / kSB, splits * batch);
+  gemm_simt_kernel<T><<<grid, 256, 0, s>>>(M, N, K, kchunk, splits, alpha, A, a_rs, a_cs, a_bs, B,
+                                           b_rs, b_cs, b_bs, beta, C, c_rs, c_cs, c_bs,
+                                           splits > 1 ? work : nullptr);
   if (splits == 1) return cudaGetLastError();
-  const int64_t total = (int64_t)M * N;
-  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-  gemm_reduce_kernel<T><<<blocks, 256, 0, s>>>(M, N, splits, alpha, work, beta, C, c_rs, c_cs);
+  const int64_t outs = (int64_t)M * N * batch;
+  const int blocks = (int)((outs + 7) / 8 < 4096 ? (outs + 7) / 8 : 4096);
+  gemm_reduce_kernel<T><<<blocks, 256, 0, s>>>(M, N, splits, batch, alpha, work, beta, C, c_rs,
+                                               c_cs, c_bs);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_gemm_simt<float>(int, int, int, float, const float*, int64_t, int64_t,
                                              const float*, int64_t, int64_t, float, float*,
-                                             int64_t, int64_t, float*, int64_t, int,
-                                             cudaStream_t);
+                                             int64_t, int64_t, float*, int64_t, int, cudaStream_t,
+                                             int, int64_t, int64_t, int64_t);
 template cudaError_t launch_gemm_simt<double>(int, int, int, double, const double*, int64_t,
                                               int64_t, const double*, int64_t, int64_t, double,
                                               double*, int64_t, int64_t, double*, int64_t, int,
-                                              cudaStream_t);
+                                              cudaStream_t, int, int64_t, int64_t, int64_t);
 
 }  // namespace lv

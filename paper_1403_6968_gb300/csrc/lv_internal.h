@@ -116,12 +116,14 @@ cudaError_t launch_tc_gemm(const float* As, const float* Bs, int M, int N, int K
 // C (M x N) = alpha A B + beta C on the CUDA cores, A(m, k) = A[m a_rs + k a_cs],
 // B(k, n) = B[k b_rs + n b_cs], C(m, n) = C[m c_rs + n c_cs]; long inner
 // dimensions are split over ``work`` (work_elems elements, may be null) and
-// the partials summed in a fixed order.
+// the partials summed in a fixed order.  ``batch`` products at once: entry b
+// reads A + b a_bs, B + b b_bs and writes C + b c_bs (strides may be negative).
 template <typename T>
 cudaError_t launch_gemm_simt(int M, int N, int K, T alpha, const T* A, int64_t a_rs, int64_t a_cs,
                              const T* B, int64_t b_rs, int64_t b_cs, T beta, T* C, int64_t c_rs,
                              int64_t c_cs, T* work, int64_t work_elems, int num_sms,
-                             cudaStream_t s);
+                             cudaStream_t s, int batch = 1, int64_t a_bs = 0, int64_t b_bs = 0,
+                             int64_t c_bs = 0);
 
 // Launchers (return cudaGetLastError()).  R is the runtime factor width,
 // bucketed internally to a compiled width.  The passes are launched with
