@@ -61,13 +61,16 @@ def _args():
     ap.add_argument("--no-ols", action="store_true", help="skip the OLS row-block section")
     ap.add_argument("--no-general", action="store_true")
     ap.add_argument("--gemm-n", type=int, default=8192, help="size of the gemm section's products")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the general form at the paper's n = 30000")
     ap.add_argument("--no-gemm", action="store_true")
     ap.add_argument("--no-drift", action="store_true",
                     help="skip the residual-correction drift section (two 200-update streams)")
     ap.add_argument("--only", default=None,
                     choices=["rank4_stream", "k_sweep", "iteration_p_sweep", "gd_regression",
                              "small_fp64", "ols_row_blocks", "iteration_adjoint", "serving",
-                             "zipf_batches", "drift", "gemm"],
+                             "zipf_batches", "drift", "gemm", "iteration_p_sweep_n30000",
+                             "gd_regression_n30000"],
                     help="run one secondary section alone (no headline line): profiling")
     return ap.parse_args()
 
@@ -573,6 +576,11 @@ def run_ours(args):
     if not args.no_general:
         section("iteration_p_sweep", lambda: iteration_p_sweep(args, seed=rank))
         section("gd_regression", lambda: gd_regression(seed=rank))
+    if not args.no_general and not args.no_large:
+        # the paper's sizes for the general form (Section 6: n = 30K, p up to 1000)
+        section("iteration_p_sweep_n30000",
+                lambda: iteration_p_sweep(args, seed=rank, steps=3, n=30000))
+        section("gd_regression_n30000", lambda: gd_regression_device(seed=rank))
     section("small_fp64", lambda: small_fp64(seed=rank))
     if not args.no_ols:
         section("ols_row_blocks", lambda: ols_sweep(seed=rank))
@@ -827,22 +835,30 @@ def _event_ms(fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def iteration_p_sweep(args, seed=0, k=16, steps=6, ps=(1, 16, 128, 1024)):
-    """General form with B = 0 (Section 6, "B=0"): T_{i+1} = A T_i, n = 8192,
-    k = 16, against the width p of T: per-update refresh of T_1..T_k
-    (rank-1 row updates of A) vs re-evaluation (k products A T_i)."""
+def iteration_p_sweep(args, seed=0, k=16, steps=6, ps=(1, 16, 128, 1024), n=None):
+    """General form with B = 0 (Section 6, "B=0"): T_{i+1} = A T_i, n = 8192
+    (or ``n``), k = 16, against the width p of T: per-update refresh of
+    T_1..T_k (rank-1 row updates of A) vs re-evaluation (k products A T_i)."""
     import numpy as np
     import torch
     import linview_inputs as li
     from paper_1403_6968_gb300 import Program
 
-    n = args.n
-    a = torch.from_numpy(li.power_matrix(n, seed=seed, dtype=np.float32)).cuda()
+    n = n or args.n
+    if n > 16384:  # the paper's size: A and T_0 drawn by a seeded device generator
+        gen = torch.Generator(device="cuda").manual_seed(2000 + seed)
+        a = torch.randn((n, n), generator=gen, device="cuda") / (2.0 * np.sqrt(n))
+    else:
+        gen = None
+        a = torch.from_numpy(li.power_matrix(n, seed=seed, dtype=np.float32)).cuda()
     ups = [(i, torch.from_numpy(v).cuda())
            for i, v in li.row_update_stream(n, steps + 2, seed=seed + 3, dtype=np.float32)]
     rows = []
     for p in ps:
-        t0 = torch.from_numpy(li.normal((n, p), seed=seed + p, dtype=np.float32)).cuda()
+        if gen is not None:
+            t0 = torch.randn((n, p), generator=gen, device="cuda")
+        else:
+            t0 = torch.from_numpy(li.normal((n, p), seed=seed + p, dtype=np.float32)).cuda()
         b = torch.zeros((n, p), dtype=torch.float32, device="cuda")
         prog = Program("iteration", [a, b, t0], k=k, r_max=1)
         for i, v in ups[:2]:
@@ -873,12 +889,86 @@ def iteration_p_sweep(args, seed=0, k=16, steps=6, ps=(1, 16, 128, 1024)):
             ex.sync()
             ex.close()
         rows.append(row)
-    return {"n": n, "k": k, "B": "0", "update": "rank-1 row of A", "rows": rows,
+    return {"n": n, "k": k, "B": "0", "update": "rank-1 row of A", "steps": steps, "rows": rows,
             "note": "incremental = factored deltas, linear model (Krylov reuse); hybrid = "
                     "dense deltas D_i = A D_{i-1} + rank-1 term; exp_model / skip4_model = "
                     "factored deltas, exponential / skip-4 model (views T_1, T_2, T_4, .., T_k "
                     "/ T_1, T_2, T_4, T_8, T_12, T_16, with P_h and S'_h views); "
                     "re-evaluation = k products A T_i"}
+
+
+def gd_regression_device(seed=0, n=30000, m=30000, p=1000, k=16, steps=3):
+    """The gradient-descent workload of gd_regression at the paper's size
+    (Section 6: n = 30K, p = 1000, k = 16), built on the device: X (m x n) and
+    Y (m x p) ~ N(0, 1) from a seeded device generator, X^T X and X^T Y on the
+    library's own GEMM (split TF32), lambda_max by power iteration, A = I -
+    eta X^T X, B = eta X^T Y.  Incremental row replacements (rank-2 dA, rank-1
+    dB) in the linear, exponential and skip-4 models against re-evaluating the
+    k iterations (own GEMM, cuBLAS BF16x9 and TF32)."""
+    import torch
+    from paper_1403_6968_gb300 import Program, gemm
+
+    gen = torch.Generator(device="cuda").manual_seed(1000 + seed)
+    t_set = time.perf_counter()
+    x = torch.randn((m, n), generator=gen, device="cuda")
+    y = torch.randn((m, p), generator=gen, device="cuda")
+    g = torch.empty((n, n), device="cuda")
+    gemm(x, x, g, ta=True)                     # X^T X, own GEMM
+    xty = torch.empty((n, p), device="cuda")
+    gemm(x, y, xty, ta=True)                   # X^T Y
+    z = torch.randn((n, 1), generator=gen, device="cuda")
+    for _ in range(30):                        # lambda_max by power iteration
+        z = g @ z
+        z /= z.norm()
+    eta = 1.0 / (1.05 * float((z.T @ (g @ z)).item()))
+    a = -eta * g
+    a.diagonal().add_(1.0)
+    del g
+    b = eta * xty
+    del xty
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_set
+    newx = torch.randn((steps + 2, n), generator=gen, device="cuda")
+    rowsel = torch.randint(0, m, (steps + 2,), generator=gen, device="cuda").tolist()
+    deltas = []
+    for j in range(steps + 2):
+        i = int(rowsel[j])
+        xo, xn = x[i].clone(), newx[j]
+        x[i] = xn
+        u = torch.stack([xn, xo], dim=1).contiguous()
+        v = torch.stack([-eta * xn, eta * xo], dim=1).contiguous()
+        ub = (xn - xo).reshape(n, 1).contiguous()
+        vb = (eta * y[i]).reshape(p, 1).contiguous()
+        deltas.append((u, v, ub, vb))
+    del x
+    out = {"n": n, "m": m, "p": p, "k": k, "eta": eta, "setup_s": setup_s,
+           "inputs": "X, Y ~ N(0,1) from a seeded device generator; X^T X, X^T Y on the own GEMM"}
+    for key, kw in (("linear", {"model": "linear"}), ("exp_model", {"model": "exp"}),
+                    ("skip4_model", {"model": "skip", "skip": 4})):
+        prog = Program("iteration", [a, b, torch.zeros((n, p), device="cuda")], k=k, r_max=2,
+                       **kw)
+
+        def replace_row(j):
+            u, v, ub, vb = deltas[j]
+            prog.apply_delta(u, v)
+            prog.apply_delta(ub, vb, input_id=1)
+
+        replace_row(0)
+        replace_row(1)
+        out[f"{key}_ms_per_row_replacement"] = _event_ms(lambda j: replace_row(2 + j), steps)
+        if key == "linear":
+            for mode in ("tc3", "bf16x9", "tf32"):
+                prog.set_reeval_mode(mode)
+                prog.reeval()
+                out[f"reeval_{mode}_ms"] = _event_ms(lambda j: prog.reeval(), 1)
+        prog.sync()
+        prog.close()
+    best = min(out[f"{m_}_ms_per_row_replacement"] for m_ in ("linear", "exp_model", "skip4_model"))
+    out["speedup_best_model_vs_own_reeval"] = out["reeval_tc3_ms"] / best
+    out["speedup_best_model_vs_bf16x9_reeval"] = out["reeval_bf16x9_ms"] / best
+    out["note"] = ("per row replacement of X: the rank-2 dA and rank-1 dB; re-evaluation: "
+                   "T_i = A T_{i-1} + B for i = 1..k")
+    return out
 
 
 def gd_regression(seed=0, n=4096, m=4096, p=1024, k=16, steps=6):
@@ -1190,6 +1280,8 @@ def run_only(args):
            "serving": lambda: serving_sweep(args),
            "zipf_batches": lambda: zipf_batches(args),
            "gemm": lambda: gemm_section(args),
+           "iteration_p_sweep_n30000": lambda: iteration_p_sweep(args, steps=3, n=30000),
+           "gd_regression_n30000": lambda: gd_regression_device(),
            "drift": lambda: drift_report(drift_streams(args), _drift_a(args), args.k,
                                          not args.no_cpu_baseline)}
     print(json.dumps({"section": args.only, args.only: fns[args.only]()}), flush=True)

@@ -326,9 +326,9 @@ linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp
  *   (ld >= M); B is K x N (ld >= N), or N x K when tb (ld >= K).  beta = 0
  *   ignores C's old contents.  M = 0 or N = 0 is an empty product (OK, no
  *   pointer is read); K >= 1.
- *  precision LINVIEW_F32: the tcgen05 split-TF32 GEMM (FP32 accuracy, three
- *   TF32 products per operand pair, FP32 accumulation) when M >= 128,
- *   N >= 32 and K >= 128, else the CUDA-core GEMM in FP32; LINVIEW_F64: the
+ *  precision LINVIEW_F32: the tcgen05 split-TF32 GEMM (near-FP32 accuracy,
+ *   three TF32 products per operand pair, FP32 accumulation) when M >= 128,
+ *   N >= 8 and K >= 128, else the CUDA-core GEMM in FP32; LINVIEW_F64: the
  *   FP64 CUDA-core GEMM.
  * Temporary device memory (split operands, partial sums) is allocated
  * stream-ordered on ``stream`` and released before the call returns; the call

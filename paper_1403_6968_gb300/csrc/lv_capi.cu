@@ -639,7 +639,7 @@ static linview_status tc_scratch(linview_program* p, TcScratch* sc, int64_t a_ro
 // the rest run on the CUDA cores.
 static bool tc_eligible(const linview_program* p, const TcScratch* sc, int64_t M, int64_t N,
                         int64_t K) {
-  return p->elem == 4 && sc && sc->a && M >= 128 && N >= 32 && K >= 128 && M <= sc->a_rows &&
+  return p->elem == 4 && sc && sc->a && M >= 128 && N >= 8 && K >= 128 && M <= sc->a_rows &&
          N <= sc->b_rows && K <= sc->K;
 }
 
@@ -718,6 +718,57 @@ static linview_status gemm_cm_own(linview_program* p, bool ta, bool tb, int64_t 
                                      static_cast<double*>(p->gwork), p->gwork_elems, p->sms, s,
                                      batch, a_bs, b_bs, c_bs));
   p->all_launches += 2;
+  return LINVIEW_OK;
+}
+
+// Narrow products of a square view with a row-major panel, out (n x nc,
+// row-major) = op(view) X (+ add; add may be out) with op = identity or transpose, nc <=
+// kMaxFusedR: one products pass over the view (memory-bound, the view's own
+// arithmetic) instead of a GEMM whose tiles a few columns cannot fill.  X is
+// staged column-major in the GEMM work buffer, the pass's partial sums are
+// reduced there, and the result is transposed back into ``out``.  Returns
+// false (nothing enqueued) when the shapes do not fit this path.
+template <typename T>
+static bool view_panel_fits(const linview_program* p, const View& v, int nc) {
+  const int64_t fs = rup(v.rows, 64);
+  return v.square && nc >= 1 && nc <= kMaxFusedR && p->xp_s >= (int64_t)nc * p->part_cs &&
+         p->yp_q >= (int64_t)nc * p->part_cs && p->part_cs >= v.rows && p->gwork &&
+         3 * fs * nc <= p->gwork_elems;
+}
+
+template <typename T>
+static linview_status view_panel_product(linview_program* p, const View& v, bool transpose,
+                                         const T* X, int64_t ldx, int nc, const T* add,
+                                         int64_t ldadd, T* out, int64_t ldo, cudaStream_t s) {
+  const int n = (int)v.rows;
+  const int64_t fs = rup(n, 64);
+  T* xcm = static_cast<T*>(p->gwork);
+  T* ocm = xcm + fs * nc;
+  const PassGeom g = fused_geom(sizeof(T), n, p->sms);
+  const int64_t fs_prog = p->fs;
+  p->fs = fs;  // the staged factor's column stride
+  LV_CUDA(launch_rm_to_cm<T>(X, ldx, xcm, fs, n, nc, s));
+  const linview_status st =
+      run_fused<T>(p, v, transpose ? kModeXY : kModeX, nc, xcm, transpose ? xcm : nullptr,
+                   nullptr, nullptr, p->Xpart, p->Ypart, s);
+  p->fs = fs_prog;
+  LV_TRY(st);
+  if (transpose)
+    LV_CUDA(launch_sum_partials<T>(static_cast<const T*>(p->Ypart), g.gR, p->yp_q, p->part_cs, n,
+                                   nc, ocm, fs, s));
+  else
+    LV_CUDA(launch_sum_partials<T>(static_cast<const T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n,
+                                   nc, ocm, fs, s));
+  // column-major n x nc -> row-major: the transpose of an nc x n row-major block
+  if (add && add == out) {  // out += op(view) X: transpose into the scratch, then add
+    T* rm = ocm + fs * nc;  // row-major n x nc, ld nc
+    LV_CUDA(launch_rm_to_cm<T>(ocm, fs, rm, nc, nc, n, s));
+    LV_CUDA(launch_axpy_rows<T>(out, ldo, rm, nc, T(1), n, nc, s));
+  } else {
+    LV_CUDA(launch_rm_to_cm<T>(ocm, fs, out, ldo, nc, n, s));
+    if (add) LV_CUDA(launch_axpy_rows<T>(out, ldo, add, ldadd, T(1), n, nc, s));
+  }
+  p->all_launches += add ? 4 : 3;
   return LINVIEW_OK;
 }
 
@@ -1207,7 +1258,8 @@ static linview_status iter_reeval(linview_program* p, cudaStream_t s) {
   View& a = p->views[0];
   char* T = static_cast<char*>(p->Tpanel);
   TcScratch sc;
-  if (!library_mode(mode)) LV_TRY(tc_scratch(p, &sc, n, pp, n, s));
+  if (!library_mode(mode) && !(p->elem == 4 && view_panel_fits<float>(p, a, (int)pp)))
+    LV_TRY(tc_scratch(p, &sc, n, pp, n, s));
   for (int i = 1; i <= k; ++i) {
     void* ti = T + (size_t)i * pp * p->elem;
     void* tp = T + (size_t)(i - 1) * pp * p->elem;
@@ -1216,6 +1268,11 @@ static linview_status iter_reeval(linview_program* p, cudaStream_t s) {
                                 cudaMemcpyDeviceToDevice, s));
       LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, a.ptr, a.ld, tp, p->ldT, 1.0, ti, p->ldT, s,
                      mode));
+    } else if (p->elem == 4 && view_panel_fits<float>(p, a, (int)pp)) {
+      // a few columns: one products pass over A per step
+      LV_TRY(view_panel_product<float>(p, a, false, static_cast<const float*>(tp), p->ldT,
+                                       (int)pp, static_cast<const float*>(p->Bm), p->ldB,
+                                       static_cast<float*>(ti), p->ldT, s));
     } else {  // T_i = A T_{i-1} + B, A's rows split once
       LV_TRY(gemm_ab(p, n, pp, n, 1.0, rows_of(a.ptr, a.ld), cols_of(tp, p->ldT), 1.0, p->Bm,
                      p->ldB, ti, p->ldT, s, &sc, i > 1));
@@ -1269,7 +1326,7 @@ static linview_status iter_create(linview_program* p, const void* const* inputs,
   if (p->d.strategy == LINVIEW_STRATEGY_HYBRID) {
     p->ldD = rup(pp, 64);
     LV_TRY(dalloc(p, (size_t)2 * n * p->ldD * p->elem, &p->Dh, s));
-    if (p->elem == 4 && n >= 128 && pp >= 32) {  // products A D_{i-1} on the tensor cores
+    if (p->elem == 4 && n >= 128 && pp > kMaxFusedR) {  // products A D_{i-1} on the tensor cores
       void* t = nullptr;
       LV_TRY(dalloc(p, (size_t)n * tc_split_ld(n) * 4, &t, s));
       p->hyA = static_cast<float*>(t);
@@ -1425,9 +1482,13 @@ static linview_status iter_propagate_hybrid(linview_program* p, int r, bool b_up
       LV_TRY(gemm_cm_own(p, false, false, pp, r, n, 1.0, tprev, p->ldT, V1, fs, 0.0, W, pp, s));
     double beta = 0.0;
     if (i >= 2) {  // D_i = A D_{i-1}
-      LV_TRY(gemm_ab(p, n, pp, n, 1.0, rows_of(a.ptr, a.ld), cols_of(dp, p->ldD), 0.0, nullptr, 0,
-                     dc, p->ldD, s, p->hyA ? &hy : nullptr, a_split));
-      a_split = true;
+      if (sizeof(T) == 4 && view_panel_fits<T>(p, a, (int)pp)) {  // a few columns
+        LV_TRY(view_panel_product<T>(p, a, false, dp, p->ldD, (int)pp, nullptr, 0, dc, p->ldD, s));
+      } else {
+        LV_TRY(gemm_ab(p, n, pp, n, 1.0, rows_of(a.ptr, a.ld), cols_of(dp, p->ldD), 0.0, nullptr,
+                       0, dc, p->ldD, s, p->hyA ? &hy : nullptr, a_split));
+        a_split = true;
+      }
       beta = 1.0;
     }
     // D_i^T += W U^T  (the rank-r term)
@@ -1486,6 +1547,14 @@ static linview_status iter_sk_next(linview_program* p, const View& th, View& t2,
     return gemm_rm(p, false, false, n, pp, n, 1.0, sh.ptr, sh.ld, b.ptr, b.ld, 1.0, t2.ptr, t2.ld,
                    s, mode);
   }
+  if (e == 4 && view_panel_fits<float>(p, ph, (int)pp)) {  // a few columns: products passes
+    LV_TRY(view_panel_product<float>(p, ph, false, static_cast<const float*>(p->Dh), p->ldD,
+                                     (int)pp, static_cast<const float*>(b.ptr), b.ld,
+                                     static_cast<float*>(t2.ptr), t2.ld, s));
+    return view_panel_product<float>(p, sh, false, static_cast<const float*>(b.ptr), b.ld, (int)pp,
+                                     static_cast<const float*>(t2.ptr), t2.ld,
+                                     static_cast<float*>(t2.ptr), t2.ld, s);
+  }
   LV_TRY(gemm_ab(p, n, pp, n, 1.0, rows_of(ph.ptr, ph.ld), cols_of(p->Dh, p->ldD), 1.0, b.ptr,
                  b.ld, t2.ptr, t2.ld, s, sc));
   return gemm_ab(p, n, pp, n, 1.0, rows_of(sh.ptr, sh.ld), cols_of(b.ptr, b.ld), 1.0, t2.ptr,
@@ -1526,6 +1595,10 @@ static linview_status iter_sk_reeval(linview_program* p, cudaStream_t s) {
                               cudaMemcpyDeviceToDevice, s));
     LV_TRY(gemm_rm(p, false, false, n, pp, n, 1.0, a.ptr, a.ld, t0.ptr, t0.ld, 1.0, t1.ptr,
                    t1.ld, s, mode));
+  } else if (e == 4 && view_panel_fits<float>(p, a, (int)pp)) {
+    LV_TRY(view_panel_product<float>(p, a, false, static_cast<const float*>(t0.ptr), t0.ld,
+                                     (int)pp, static_cast<const float*>(b.ptr), b.ld,
+                                     static_cast<float*>(t1.ptr), t1.ld, s));
   } else {
     LV_TRY(gemm_ab(p, n, pp, n, 1.0, rows_of(a.ptr, a.ld), cols_of(t0.ptr, t0.ld), 1.0, b.ptr,
                    b.ld, t1.ptr, t1.ld, s, &sc));
@@ -2555,6 +2628,8 @@ static linview_status adjoint_iteration(linview_program* p, const void* Gk, int6
   // length up to max(n, k p)
   TcScratch sc;
   LV_TRY(tc_scratch(p, &sc, n, n, n > k * pp ? n : k * pp, s));
+  // a few columns (FP32): the products with A and A^T are products passes over A
+  const bool narrow = e == 4 && view_panel_fits<float>(p, a, (int)pp);
   if (iter_exp(p)) {
     // the exponential and skip models keep only some T_i: the reverse pass
     // needs T_0 .. T_k, recomputed here as T_i = A T_{i-1} + B (the same
@@ -2568,9 +2643,17 @@ static linview_status adjoint_iteration(linview_program* p, const void* Gk, int6
     const View& t0 = p->views[p->ie_NT + 2];
     LV_CUDA(cudaMemcpy2DAsync(T, ldT * e, t0.ptr, t0.ld * e, pp * e, n, cudaMemcpyDeviceToDevice,
                               s));
-    for (int i = 1; i <= k; ++i)
-      LV_TRY(gemm_ab(p, n, pp, n, 1.0, rows_of(a.ptr, a.ld), cols_of(T + (size_t)(i - 1) * pp * e, ldT),
-                     1.0, p->Bm, p->ldB, T + (size_t)i * pp * e, ldT, s, &sc, i > 1));
+    for (int i = 1; i <= k; ++i) {
+      char* tp = T + (size_t)(i - 1) * pp * e;
+      char* ti = T + (size_t)i * pp * e;
+      if (narrow)
+        LV_TRY(view_panel_product<float>(p, a, false, reinterpret_cast<const float*>(tp), ldT,
+                                         (int)pp, static_cast<const float*>(p->Bm), p->ldB,
+                                         reinterpret_cast<float*>(ti), ldT, s));
+      else
+        LV_TRY(gemm_ab(p, n, pp, n, 1.0, rows_of(a.ptr, a.ld), cols_of(tp, ldT), 1.0, p->Bm,
+                       p->ldB, ti, ldT, s, &sc, i > 1));
+    }
   }
   // G_k = seed; G_i = A^T G_{i+1}
   void* gk = G + (size_t)(k - 1) * pp * e;
@@ -2590,14 +2673,24 @@ static linview_status adjoint_iteration(linview_program* p, const void* Gk, int6
   for (int i = k - 1; i >= 1; --i) {
     void* gi = G + (size_t)(i - 1) * pp * e;
     void* gn = G + (size_t)i * pp * e;
-    LV_TRY(gemm_ab(p, n, pp, n, 1.0, cols_of(a.ptr, a.ld), cols_of(gn, p->ldG), 0.0, nullptr, 0,
-                   gi, p->ldG, s, &sc, at_split));
-    at_split = true;
+    if (narrow) {
+      LV_TRY(view_panel_product<float>(p, a, true, static_cast<const float*>(gn), p->ldG, (int)pp,
+                                       nullptr, 0, static_cast<float*>(gi), p->ldG, s));
+    } else {
+      LV_TRY(gemm_ab(p, n, pp, n, 1.0, cols_of(a.ptr, a.ld), cols_of(gn, p->ldG), 0.0, nullptr,
+                     0, gi, p->ldG, s, &sc, at_split));
+      at_split = true;
+    }
   }
   if (dT0) {
     // dL/dT_0 = A^T G_1
-    LV_TRY(gemm_ab(p, n, pp, n, 1.0, cols_of(a.ptr, a.ld), cols_of(G, p->ldG), 0.0, nullptr, 0,
-                   dT0, ld_dT0, s, &sc, at_split));
+    if (narrow)
+      LV_TRY(view_panel_product<float>(p, a, true, static_cast<const float*>(static_cast<void*>(G)),
+                                       p->ldG, (int)pp, nullptr, 0, static_cast<float*>(dT0),
+                                       ld_dT0, s));
+    else
+      LV_TRY(gemm_ab(p, n, pp, n, 1.0, cols_of(a.ptr, a.ld), cols_of(G, p->ldG), 0.0, nullptr, 0,
+                     dT0, ld_dT0, s, &sc, at_split));
   }
   if (dB) {
     LV_CUDA(cudaMemcpy2DAsync(dB, ld_dB * e, G, p->ldG * e, pp * e, n, cudaMemcpyDeviceToDevice, s));

@@ -45,7 +45,8 @@ def _run(M, N, K, ta, tb, alpha, beta, dtype, seed=0):
 
 
 @pytest.mark.parametrize("M,N,K", [(1000, 1000, 1000), (300, 200, 700), (8192, 64, 8192),
-                                   (2048, 256, 2048), (129, 33, 129), (640, 384, 1024)])
+                                   (2048, 256, 2048), (129, 33, 129), (640, 384, 1024),
+                                   (1000, 8, 1000), (2048, 16, 4096)])
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
 def test_fp32_tensor_core_products(M, N, K, ta, tb):
     if M * N * K > 2e10 and (ta, tb) != (False, False):

@@ -106,8 +106,11 @@ def test_iteration_adjoint_fp64_central_fd_n512():
         assert abs(fd - float(np.sum(db * e))) <= 1e-6 * float(np.linalg.norm(db))
 
 
-def test_iteration_adjoint_fp32_vs_oracle():
-    n, p, k = 2048, 64, 16
+@pytest.mark.parametrize("n,p", [(2048, 64), (1000, 3)])
+def test_iteration_adjoint_fp32_vs_oracle(n, p):
+    """p = 64: the products with A and A^T on the split-TF32 GEMM; p = 3: as
+    products passes over A (a few columns)."""
+    k = 16
     a, b, t0 = li.iteration_inputs(n, p, seed=31, dtype=np.float32)
     prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=k, r_max=2)
     (u, v), = li.lowrank_update_stream(n, 2, 1, seed=32, dtype=np.float32)
@@ -120,6 +123,16 @@ def test_iteration_adjoint_fp32_vs_oracle():
     ra, rb, _ = oi.adjoint(acur, b.astype(np.float64), t0.astype(np.float64), k)
     assert rel_frob(dA.cpu().numpy(), ra) <= 1e-4
     assert rel_frob(dB.cpu().numpy(), rb) <= 1e-4
+    # the seeded form at the seed 2 T_k is the same reverse pass, and adds
+    # dT_0 = A^T G_1 (the oracle's third gradient)
+    ra, rb, rt0 = oi.adjoint(acur, b.astype(np.float64), t0.astype(np.float64), k)
+    gk = 2.0 * prog.read_view(k)
+    dT0 = torch.empty((n, p), dtype=torch.float32, device="cuda")
+    prog.adjoint_iteration_seed(gk, dA, dB, dT0)
+    torch.cuda.synchronize()
+    assert rel_frob(dT0.cpu().numpy(), rt0) <= 1e-4
+    assert rel_frob(dB.cpu().numpy(), rb) <= 1e-4
+    assert rel_frob(dA.cpu().numpy(), ra) <= 1e-4
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
