@@ -2031,6 +2031,19 @@ static linview_status ols_replace_t(linview_program* p, int kr, const void* nrow
   LV_CUDA(launch_gather_rows<T>(static_cast<const T*>(p->Yd), p->ldY, p->rows_d, kr, pp,
                                 static_cast<T*>(p->Yr), pp, 1, s));
   p->all_launches += 2;
+  // X's rows and X^T Y read only U and Y_R: a side stream, next to the
+  // Woodbury passes and the core, joined before the beta refresh that reads
+  // the new X^T Y
+  {
+    cudaStream_t side = nullptr;
+    LV_TRY(side_fork(p, s, &side));
+    LV_CUDA(launch_scatter_rows<T>(static_cast<T*>(p->Xd), p->ldX, p->rows_d, kr, n, U, fs,
+                                   side));
+    View& xty0 = p->views[kOlsXtY];
+    LV_CUDA(launch_xty_update<T>(static_cast<T*>(xty0.ptr), xty0.ld, static_cast<T*>(p->XtYc),
+                                 fs, U, n, pp, kr, static_cast<const T*>(p->Yr), side));
+    p->all_launches += 2;
+  }
   // G = W U (one read of W per 16 columns in FP32, per 8 in FP64)
   LV_TRY(run_products_update<T>(p, w, kk, U, nullptr, nullptr, nullptr, s));
   {
@@ -2045,7 +2058,7 @@ static linview_status ols_replace_t(linview_program* p, int kr, const void* nrow
   }
   {
     ProfScope ps(p, s, 0.0);
-    LV_CUDA(launch_core_inverse(p->C, kk, kr, p->Minv, p->status, s));
+    LV_CUDA(launch_core_inverse(p->C, kk, kr, p->Minv, p->status, s, sizeof(T) == 4));
   }
   {
     ProfScope ps(p, s, 0.0);
@@ -2053,12 +2066,7 @@ static linview_status ols_replace_t(linview_program* p, int kr, const void* nrow
   }
   // W' = W + G Wu^T = W - G M^{-1} G^T
   LV_TRY(run_update<T>(p, w, G, Wu, kk, s));
-  // X rows, X^T Y, beta = W' X^T Y
-  LV_CUDA(launch_scatter_rows<T>(static_cast<T*>(p->Xd), p->ldX, p->rows_d, kr, n, U, fs, s));
-  View& xty = p->views[kOlsXtY];
-  LV_CUDA(launch_xty_update<T>(static_cast<T*>(xty.ptr), xty.ld, static_cast<T*>(p->XtYc), fs, U,
-                               n, pp, kr, static_cast<const T*>(p->Yr), s));
-  p->all_launches += 2;
+  LV_TRY(side_join(p, s));  // the new X rows and X^T Y
   // beta' = beta + (G_1 - G_2) Y_R + G (Wu^T C'): from the factors, no pass over W
   View& beta = p->views[kOlsBeta];
   {
@@ -2557,10 +2565,12 @@ linview_status linview_apply_row_block(linview_program* p, int64_t kr, const int
   LV_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   LV_CUDA(cudaMemcpyAsync(p->rows_d, rows, sizeof(int64_t) * kr, cudaMemcpyHostToDevice, s));
-  if (p->elem == 4)
-    LV_TRY(ols_replace_t<float>(p, (int)kr, new_rows, ld, on_device, s));
-  else
-    LV_TRY(ols_replace_t<double>(p, (int)kr, new_rows, ld, on_device, s));
+  const linview_status st = p->elem == 4
+                                ? ols_replace_t<float>(p, (int)kr, new_rows, ld, on_device, s)
+                                : ols_replace_t<double>(p, (int)kr, new_rows, ld, on_device, s);
+  const linview_status sj = side_join(p, s);  // also after an error, to close the fork
+  LV_TRY(st);
+  LV_TRY(sj);
   return after_update(p, s);
 }
 

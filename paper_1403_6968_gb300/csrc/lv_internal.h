@@ -202,8 +202,10 @@ cudaError_t launch_gather_rows(const T* X, int64_t ldx, const int64_t* rows, int
 template <typename T>
 cudaError_t launch_scatter_rows(T* X, int64_t ldx, const int64_t* rows, int k, int n,
                                 const T* src, int64_t ts, cudaStream_t s);
+// (double_float: the elimination in double-float arithmetic on the FP32 pipe,
+// for FP32 programs; else FP64)
 cudaError_t launch_core_inverse(const double* S, int kk, int kpos, double* Minv, unsigned* status,
-                                cudaStream_t s);
+                                cudaStream_t s, bool double_float = false);
 template <typename T>
 cudaError_t launch_wu(const T* G, int64_t fs, int n, int kk, const double* Minv, T* Wu,
                       cudaStream_t s);

@@ -138,6 +138,135 @@ __global__ void __launch_bounds__(kInvTx * kInvTy)
     for (int j = tx; j < kk; j += kInvTx) Minv[i * kk + j] = singular ? 0.0 : cur[i * w + kk + j];
 }
 
+// Double-float arithmetic (a value is hi + lo, two FP32 numbers, about 48
+// significant bits): the core inverse of FP32 programs runs on GB300's FP32
+// pipe, 64 times as wide as its FP64 pipe.  Products are exact by FMA
+// (p = a b, e = fma(a, b, -p)), sums by Knuth's TwoSum; the intrinsics keep
+// the compiler from contracting or reassociating any step.
+struct df2 {
+  float hi, lo;
+};
+__device__ __forceinline__ df2 df_make(double d) {
+  const float h = __double2float_rn(d);
+  return {h, __double2float_rn(d - (double)h)};
+}
+__device__ __forceinline__ double df_double(df2 x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ df2 df_sum(df2 a, df2 b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ df2 df_prod(df2 a, df2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  const float h = __fadd_rn(p, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+// a - f b
+__device__ __forceinline__ df2 df_fms(df2 a, df2 f, df2 b) {
+  const df2 q = df_prod(f, b);
+  return df_sum(a, {-q.hi, -q.lo});
+}
+// 1 / a: an FP32 reciprocal refined by two Newton steps x += x (1 - a x)
+__device__ __forceinline__ df2 df_recip(df2 a) {
+  df2 x = {__frcp_rn(a.hi), 0.f};
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const df2 ax = df_prod(a, x);
+    const df2 e = df_sum({1.f, 0.f}, {-ax.hi, -ax.lo});
+    x = df_sum(x, df_prod(x, e));
+  }
+  return x;
+}
+
+// The same Gauss-Jordan elimination as core_inverse_kernel in double-float
+// arithmetic (FP32 programs): M and the result are FP64 at the interface.
+__global__ void __launch_bounds__(kInvTx * kInvTy)
+    core_inverse_df_kernel(const double* S, int kk, int kpos, double* Minv, unsigned* status) {
+  extern __shared__ double inv_sm[];
+  const int w = 2 * kk;
+  df2* cur = reinterpret_cast<df2*>(inv_sm);  // kk x w
+  df2* nxt = cur + kk * w;                    // kk x w
+  df2* prow = nxt + kk * w;                   // w: the pivot row divided by the pivot
+  df2* fcol = prow + w;                       // kk: column col before the step
+  __shared__ float wmax[kInvTy];
+  __shared__ int s_piv, s_sing;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float m = 0.f;
+  for (int i = ty; i < kk; i += kInvTy)
+    for (int j = tx; j < w; j += kInvTx) {
+      df2 v;
+      if (j < kk) {
+        v = df_make(S[i * kk + j] + (i == j ? (i < kpos ? 1.0 : -1.0) : 0.0));
+        m = fmaxf(m, fabsf(v.hi));
+      } else {
+        v = {(j - kk == i) ? 1.f : 0.f, 0.f};
+      }
+      cur[i * w + j] = v;
+    }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (tx == 0) wmax[ty] = m;
+  if (tx == 0 && ty == 0) s_sing = 0;
+  __syncthreads();
+  float scale = 0.f;
+  for (int t = 0; t < kInvTy; ++t) scale = fmaxf(scale, wmax[t]);
+  const float tiny = 1e-13f * scale;
+  for (int col = 0; col < kk; ++col) {
+    if (ty == 0) {
+      float bv = -1.f;
+      int bi = kk;
+      for (int i = col + tx; i < kk; i += kInvTx) {
+        const float v = fabsf(cur[i * w + col].hi);
+        if (v > bv) { bv = v; bi = i; }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if (bi >= kk) bi = col;  // the column is all NaN
+      if (!(bv > tiny) && tx == 0) {
+        s_sing = 1;
+        atomicOr(status, kStatusSingular);
+      }
+      const df2 r = df_recip(cur[bi * w + col]);
+      for (int j = tx; j < w; j += kInvTx) prow[j] = df_prod(cur[bi * w + j], r);
+      for (int i = tx; i < kk; i += kInvTx) fcol[i] = cur[i * w + col];
+      if (tx == 0) s_piv = bi;
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    for (int i = ty; i < kk; i += kInvTy) {
+      const int src = (i == col) ? piv : (i == piv ? col : i);  // rows col and piv swap
+      const df2 f = fcol[src];
+      const df2* a = cur + src * w;
+      df2* o = nxt + i * w;
+      for (int j = tx; j < w; j += kInvTx) {
+        df2 v;
+        if (i == col) v = (j == col) ? df2{1.f, 0.f} : prow[j];
+        else if (j == col) v = {0.f, 0.f};
+        else if (j < col) v = a[j];  // finished columns: prow[j] is 0 there
+        else v = df_fms(a[j], f, prow[j]);
+        o[j] = v;
+      }
+    }
+    __syncthreads();
+    df2* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  const bool singular = s_sing != 0;
+  for (int i = ty; i < kk; i += kInvTy)
+    for (int j = tx; j < kk; j += kInvTx)
+      Minv[i * kk + j] = singular ? 0.0 : df_double(cur[i * w + kk + j]);
+}
+
 // Wu(:, c) = - sum_c' G(:, c') Minv(c', c) in FP64; a thread computes two
 // columns c = 2 blockIdx.y, 2 blockIdx.y + 1 of one row j (kk is even).
 template <typename T>
@@ -282,14 +411,22 @@ cudaError_t launch_scatter_rows(T* X, int64_t ldx, const int64_t* rows, int k, i
 }
 
 cudaError_t launch_core_inverse(const double* S, int kk, int kpos, double* Minv, unsigned* status,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool double_float) {
   if (kk < 1 || kk > 64) return cudaErrorInvalidValue;
   static const cudaError_t configured =
       cudaFuncSetAttribute(core_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)core_inverse_smem(64));
   if (configured != cudaSuccess) return configured;
-  core_inverse_kernel<<<1, dim3(kInvTx, kInvTy), core_inverse_smem(kk), s>>>(S, kk, kpos, Minv,
-                                                                           status);
+  static const cudaError_t configured_df =
+      cudaFuncSetAttribute(core_inverse_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)core_inverse_smem(64));
+  if (configured_df != cudaSuccess) return configured_df;
+  if (double_float)
+    core_inverse_df_kernel<<<1, dim3(kInvTx, kInvTy), core_inverse_smem(kk), s>>>(S, kk, kpos,
+                                                                                Minv, status);
+  else
+    core_inverse_kernel<<<1, dim3(kInvTx, kInvTy), core_inverse_smem(kk), s>>>(S, kk, kpos, Minv,
+                                                                             status);
   return cudaGetLastError();
 }
 
