@@ -599,10 +599,13 @@ static void tfree(linview_program* p, void* ptr, size_t bytes_in, cudaStream_t s
     cudaFreeAsync(ptr, s);
 }
 
-// Split-operand scratch of the tensor-core GEMM: rows of A_s then of B_s.
+// Split-operand scratch of the tensor-core GEMM: rows of A_s, then of B_s,
+// then room for the K parts of a split product.
+constexpr int64_t kTcWorkFloats = int64_t(4) << 20;  // 16 MB
 struct TcScratch {
   float* a = nullptr;
   float* b = nullptr;
+  float* work = nullptr;
   int64_t a_rows = 0, b_rows = 0, K = 0;
   void* block = nullptr;  // temporary block owned by this scratch (null: borrowed)
   size_t bytes = 0;
@@ -620,7 +623,8 @@ static linview_status tc_scratch(linview_program* p, TcScratch* sc, int64_t a_ro
   if (p->elem != 4 || a_rows < 128) return LINVIEW_OK;  // such products run on the CUDA cores
   const int64_t ld = tc_split_ld(K);
   const size_t abytes = (size_t)alloc_bytes(a_rows * ld * 4);
-  const size_t bytes = abytes + (size_t)b_rows * ld * 4;
+  const size_t bbytes = (size_t)alloc_bytes(b_rows * ld * 4);
+  const size_t bytes = abytes + bbytes + (size_t)kTcWorkFloats * 4;
   void* blk = nullptr;
   LV_TRY(talloc(p, bytes, &blk, s));
   sc->block = blk;
@@ -629,6 +633,7 @@ static linview_status tc_scratch(linview_program* p, TcScratch* sc, int64_t a_ro
   sc->s = s;
   sc->a = static_cast<float*>(blk);
   sc->b = reinterpret_cast<float*>(static_cast<char*>(blk) + abytes);
+  sc->work = reinterpret_cast<float*>(static_cast<char*>(blk) + abytes + bbytes);
   sc->a_rows = a_rows;
   sc->b_rows = b_rows;
   sc->K = K;
@@ -668,7 +673,7 @@ static linview_status gemm_ab(linview_program* p, int64_t M, int64_t N, int64_t 
     }
     LV_CUDA(launch_tc_gemm(sc->a, sc->b, (int)M, (int)N, (int)K, static_cast<float*>(D), ldd,
                            static_cast<const float*>(C), ldc, (float)alpha, (float)beta, p->sms,
-                           p->status, s));
+                           p->status, s, sc->work, sc->work ? kTcWorkFloats : 0));
     p->all_launches++;
     return LINVIEW_OK;
   }

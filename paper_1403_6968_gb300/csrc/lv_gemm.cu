@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(GShape<BN>::Threads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    int M, int N, int nk, int kp, float* __restrict__ D, int64_t ldd,
                    const float* __restrict__ C, int64_t ldc, float alpha, float beta, int vec_ok,
-                   unsigned* status) {
+                   int ksplit, float* __restrict__ work, unsigned* status) {
   using Sh = GShape<BN>;
   constexpr int S = Sh::S, CW = Sh::CW, NE = Sh::NE;
   extern __shared__ __align__(1024) unsigned char g_smem_raw[];
@@ -178,8 +178,10 @@ __global__ void __launch_bounds__(GShape<BN>::Threads, 1)
   const int lane = tid & 31;
   const int mt = (M + kGBM - 1) / kGBM;
   const int nt = (N + BN - 1) / BN;
-  const long long T = (long long)mt * nt;
-  const int nseg = (nk + kSegChunks - 1) / kSegChunks;
+  // work items: (tile, K part); a split K (ksplit > 1) sends each part's
+  // product to work[part] and a second kernel sums the parts in order
+  const long long tiles = (long long)mt * nt;
+  const long long T = tiles * ksplit;
 
   if (tid == 0) {
     prefetch_tmap(&tmA);
@@ -214,8 +216,10 @@ __global__ void __launch_bounds__(GShape<BN>::Threads, 1)
       long long g = 0;
       for (long long t = blockIdx.x; t < T && !*abort_flag; t += gridDim.x) {
         int mb, nb;
-        g_tile(t, mt, nt, mb, nb);
-        for (int kc = 0; kc < nk; ++kc, ++g) {
+        g_tile(t % tiles, mt, nt, mb, nb);
+        const int ks = (int)(t / tiles);
+        const int kb = (int)((long long)nk * ks / ksplit), ke = (int)((long long)nk * (ks + 1) / ksplit);
+        for (int kc = kb; kc < ke; ++kc, ++g) {
           const int st = (int)(g % S);
           const long long use = g / S;
           if (use >= 1 && !g_wait(&bars->empty[st], (uint32_t)((use - 1) & 1), abort_flag, status))
@@ -242,6 +246,9 @@ __global__ void __launch_bounds__(GShape<BN>::Threads, 1)
       long long g = 0, gs = 0;  // chunks and segments consumed
       bool ok = true;
       for (long long t = blockIdx.x; t < T && ok && !*abort_flag; t += gridDim.x) {
+        const int ks = (int)(t / tiles);
+        const int kb = (int)((long long)nk * ks / ksplit), ke = (int)((long long)nk * (ks + 1) / ksplit);
+        const int nseg = (ke - kb + kSegChunks - 1) / kSegChunks;
         for (int sg = 0; sg < nseg && ok; ++sg, ++gs) {
           const int buf = (int)(gs & 1);
           const long long ause = gs >> 1;
@@ -252,8 +259,9 @@ __global__ void __launch_bounds__(GShape<BN>::Threads, 1)
           }
           g_fence_after();
           const uint32_t d = tmem + buf * BN;
-          const int kc1 = (sg + 1) * kSegChunks < nk ? (sg + 1) * kSegChunks : nk;
-          for (int kc = sg * kSegChunks; kc < kc1; ++kc, ++g) {
+          const int kc0 = kb + sg * kSegChunks;
+          const int kc1 = kc0 + kSegChunks < ke ? kc0 + kSegChunks : ke;
+          for (int kc = kc0; kc < kc1; ++kc, ++g) {
             const int st = (int)(g % S);
             if (!g_wait(&bars->full[st], (uint32_t)((g / S) & 1), abort_flag, status)) {
               ok = false;
@@ -267,7 +275,7 @@ __global__ void __launch_bounds__(GShape<BN>::Threads, 1)
             // lo(A) hi(B), hi(A) lo(B), then hi(A) hi(B)
             const uint32_t pa[3] = {a_lo, a_hi, a_hi};
             const uint32_t pb[3] = {b_hi, b_lo, b_hi};
-            const bool first = kc == sg * kSegChunks;
+            const bool first = kc == kc0;
 #pragma unroll
             for (int pr = 0; pr < 3; ++pr) {
 #pragma unroll
@@ -295,7 +303,10 @@ __global__ void __launch_bounds__(GShape<BN>::Threads, 1)
     bool ok = true;
     for (long long t = blockIdx.x; t < T && ok; t += gridDim.x) {
       int mb, nb;
-      g_tile(t, mt, nt, mb, nb);
+      g_tile(t % tiles, mt, nt, mb, nb);
+      const int ks = (int)(t / tiles);
+      const int kb = (int)((long long)nk * ks / ksplit), ke = (int)((long long)nk * (ks + 1) / ksplit);
+      const int nseg = (ke - kb + kSegChunks - 1) / kSegChunks;
       float acc[CW];
 #pragma unroll
       for (int c = 0; c < CW; ++c) acc[c] = 0.f;
@@ -323,7 +334,14 @@ __global__ void __launch_bounds__(GShape<BN>::Threads, 1)
       if (!ok) break;
       const int grow = mb * kGBM + row;
       const int gc0 = nb * BN + cpart * CW;
-      if (grow < M && gc0 < N) {
+      if (ksplit > 1) {  // this K part's product, to be summed by gemm_parts_kernel
+        if (grow < M && gc0 < N) {
+          float* wrow = work + ((int64_t)ks * M + grow) * N + gc0;
+#pragma unroll
+          for (int j = 0; j < CW; ++j)
+            if (gc0 + j < N) wrow[j] = acc[j];
+        }
+      } else if (grow < M && gc0 < N) {
         float* drow = D + (int64_t)grow * ldd + gc0;
         const float* crow = (C && beta != 0.f) ? C + (int64_t)grow * ldc + gc0 : nullptr;
         if (vec_ok && gc0 + CW <= N) {
@@ -513,19 +531,47 @@ __global__ void gemm_reduce_kernel(int M, int N, int splits, int batch, T alpha,
   }
 }
 
+// D = alpha sum_q work[q] + beta C (the K parts of a split product, summed in order)
+__global__ void gemm_parts_kernel(int M, int N, int parts, const float* __restrict__ work,
+                                  float alpha, float beta, const float* C, int64_t ldc, float* D,
+                                  int64_t ldd) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float acc = work[e];
+    for (int q = 1; q < parts; ++q) acc += work[(int64_t)q * total + e];
+    const int m = (int)(e / N), n = (int)(e - (int64_t)m * N);
+    float o = alpha * acc;
+    if (C && beta != 0.f) o += beta * C[(int64_t)m * ldc + n];
+    D[(int64_t)m * ldd + n] = o;
+  }
+}
+
 template <int BN>
 cudaError_t launch_tc_gemm_t(const CUtensorMap& tmA, const CUtensorMap& tmB, int M, int N, int nk,
                              int kp, float* D, int64_t ldd, const float* C, int64_t ldc,
-                             float alpha, float beta, int vec_ok, int num_sms, unsigned* status,
-                             cudaStream_t s) {
+                             float alpha, float beta, int vec_ok, int num_sms, float* work,
+                             int64_t work_floats, unsigned* status, cudaStream_t s) {
   using Sh = GShape<BN>;
   static const cudaError_t configured = cudaFuncSetAttribute(
       tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SmemBytes);
   if (configured != cudaSuccess) return configured;
-  const long long T = (long long)((M + kGBM - 1) / kGBM) * ((N + BN - 1) / BN);
+  const long long tiles = (long long)((M + kGBM - 1) / kGBM) * ((N + BN - 1) / BN);
+  // too few tiles to fill the SMs: split K (each part at least 16 chunks of 32)
+  int ksplit = 1;
+  if (work) {
+    while (tiles * (ksplit + 1) <= num_sms && nk / (ksplit + 1) >= 16 &&
+           (int64_t)(ksplit + 1) * M * N <= work_floats)
+      ++ksplit;
+  }
+  const long long T = tiles * ksplit;
   const int grid = (int)(T < num_sms ? T : num_sms);
-  tc_gemm_kernel<BN><<<grid, Sh::Threads, Sh::SmemBytes, s>>>(tmA, tmB, M, N, nk, kp, D, ldd, C,
-                                                             ldc, alpha, beta, vec_ok, status);
+  tc_gemm_kernel<BN><<<grid, Sh::Threads, Sh::SmemBytes, s>>>(
+      tmA, tmB, M, N, nk, kp, D, ldd, C, ldc, alpha, beta, vec_ok, ksplit, work, status);
+  if (ksplit == 1) return cudaGetLastError();
+  const int64_t total = (int64_t)M * N;
+  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  gemm_parts_kernel<<<blocks, 256, 0, s>>>(M, N, ksplit, work, alpha, beta, C, ldc, D, ldd);
   return cudaGetLastError();
 }
 
@@ -545,7 +591,8 @@ cudaError_t launch_split_rows(const float* X, int64_t rs, int64_t cs, int rows, 
 
 cudaError_t launch_tc_gemm(const float* As, const float* Bs, int M, int N, int K, float* D,
                            int64_t ldd, const float* C, int64_t ldc, float alpha, float beta,
-                           int num_sms, unsigned* status, cudaStream_t s) {
+                           int num_sms, unsigned* status, cudaStream_t s, float* work,
+                           int64_t work_floats) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
   const int64_t ld = tc_split_ld(K);
   const int kp = (int)(ld / 2);
@@ -562,12 +609,12 @@ cudaError_t launch_tc_gemm(const float* As, const float* Bs, int M, int N, int K
                      (!c_used || (ldc % 4 == 0 && reinterpret_cast<uintptr_t>(C) % 16 == 0));
   if (BN == 256)
     return launch_tc_gemm_t<256>(tmA, tmB, M, N, nk, kp, D, ldd, C, ldc, alpha, beta, vec_ok,
-                                 num_sms, status, s);
+                                 num_sms, work, work_floats, status, s);
   if (BN == 128)
     return launch_tc_gemm_t<128>(tmA, tmB, M, N, nk, kp, D, ldd, C, ldc, alpha, beta, vec_ok,
-                                 num_sms, status, s);
+                                 num_sms, work, work_floats, status, s);
   return launch_tc_gemm_t<64>(tmA, tmB, M, N, nk, kp, D, ldd, C, ldc, alpha, beta, vec_ok,
-                              num_sms, status, s);
+                              num_sms, work, work_floats, status, s);
 }
 
 static int gemm_simt_splits(int M, int N, int K, int batch, int num_sms, int64_t work_elems) {

@@ -109,10 +109,13 @@ cudaError_t launch_split_rows(const float* X, int64_t rs, int64_t cs, int rows, 
                               int64_t ldd, cudaStream_t s);
 // D (M x N, row-major, ldd) = alpha A_s B_s^T + beta C on the tensor cores
 // (split TF32, FP32 accumulation), A_s / B_s split rows of inner length K
-// (16-byte aligned).  C may alias D (beta == 0 ignores it).
+// (16-byte aligned).  C may alias D (beta == 0 ignores it).  ``work``
+// (work_floats floats, may be null): room for the K parts of a product with
+// too few tiles to fill the SMs (split K, parts summed in a fixed order).
 cudaError_t launch_tc_gemm(const float* As, const float* Bs, int M, int N, int K, float* D,
                            int64_t ldd, const float* C, int64_t ldc, float alpha, float beta,
-                           int num_sms, unsigned* status, cudaStream_t s);
+                           int num_sms, unsigned* status, cudaStream_t s, float* work = nullptr,
+                           int64_t work_floats = 0);
 // C (M x N) = alpha A B + beta C on the CUDA cores, A(m, k) = A[m a_rs + k a_cs],
 // B(k, n) = B[k b_rs + n b_cs], C(m, n) = C[m c_rs + n c_cs]; long inner
 // dimensions are split over ``work`` (work_elems elements, may be null) and
