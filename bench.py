@@ -55,6 +55,8 @@ def _args():
     ap.add_argument("--serve-rates", default="1e2,1e3,3e3,1e4,3e4,1e5",
                     help="request rates (per s) of the serving sweep")
     ap.add_argument("--serve-views", type=int, default=32)
+    ap.add_argument("--serve-inflight", type=int, default=8,
+                    help="views refreshing at once in the serving sweep")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-rank4", action="store_true")
     ap.add_argument("--no-ksweep", action="store_true")
@@ -1166,7 +1168,7 @@ def serving_sweep(args, seed=0):
     from paper_1403_6968_gb300 import Server
 
     sizes = li.serving_views(args.serve_views, seed=seed)
-    srv = Server(max_inflight=8, r_cap=8)
+    srv = Server(max_inflight=args.serve_inflight, r_cap=8)
     t0 = time.perf_counter()
     for i, n in enumerate(sizes):
         srv.add_view(torch.from_numpy(li.power_matrix(n, seed=100 + i, dtype=np.float32)).cuda(),
@@ -1197,7 +1199,7 @@ def serving_sweep(args, seed=0):
     srv.close()
     return {"views": len(sizes), "n_counts": {str(n): sizes.count(n) for n in sorted(set(sizes))},
             "k": 16, "resident_bytes": st0["bytes_used"], "setup_s": setup_s,
-            "max_inflight": 8, "r_cap": 8, "sweep": sweep,
+            "max_inflight": args.serve_inflight, "r_cap": 8, "sweep": sweep,
             "note": "open-loop Poisson arrivals replayed by the library; queued requests to a "
                     "busy view coalesce up to rank 8; latency = completion seen by the "
                     "scheduler - arrival"}
