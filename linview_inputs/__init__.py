@@ -142,10 +142,12 @@ def ols_inputs(m: int, n: int, p: int, seed: int = 0, frac: float = 0.1,
 
 
 def ols_row_replacements(m: int, n: int, k: int, count: int, seed: int = 0,
-                         frac: float = 0.1, scale: float = 1e-2, dtype=np.float64):
+                         frac: float = 0.1, scale: float = 1e-2, dtype=np.float64,
+                         cols_seed: int | None = None):
     """List of ``count`` updates (rows, new_rows): k distinct rows in [0, m)
-    replaced by fresh rows with the same column scaling."""
-    cols = ols_scaled_columns(n, seed, frac)
+    replaced by fresh rows with the same column scaling as X: ``cols_seed`` is
+    the seed X was drawn with (its scaled columns); None uses ``seed``."""
+    cols = ols_scaled_columns(n, seed if cols_seed is None else cols_seed, frac)
     g = rng(seed, _STREAM_OLS_UPD)
     out = []
     for _ in range(count):

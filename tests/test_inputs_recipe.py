@@ -58,6 +58,14 @@ def test_ols_inputs_scaled_columns_and_replacements():
     allnew = np.concatenate([new for _, new in ups])
     assert abs(allnew[:, cols].std() / 1e-2 - 1) < 0.1   # the same column scaling
     assert abs(allnew[:, other].std() - 1) < 0.05
+    # an update stream drawn with its own seed keeps X's scaled columns
+    ups2 = li.ols_row_replacements(m, n, k, 20, seed=9, cols_seed=2)
+    new2 = np.concatenate([new for _, new in ups2])
+    assert abs(new2[:, cols].std() / 1e-2 - 1) < 0.1 and abs(new2[:, other].std() - 1) < 0.05
+    # so the leverage of a replacement row stays near n / m (not ~ n / m x 1e4)
+    w = np.linalg.inv(x.T @ x)
+    lev = np.einsum("ij,jk,ik->i", new2, w, new2)
+    assert lev.max() < 4 * n / m
 
 
 @pytest.mark.parametrize("z", [0.0, 1.0, 3.0])

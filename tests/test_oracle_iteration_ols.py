@@ -155,7 +155,7 @@ def test_woodbury_row_blocks_vs_sm_and_lstsq(k):
     x, y, _ = li.ols_inputs(m, n, p, seed=5)
     a = oo.IncrementalOLS(x, y)
     b = oo.IncrementalOLS(x, y)
-    for rows, new in li.ols_row_replacements(m, n, k, 3, seed=6):
+    for rows, new in li.ols_row_replacements(m, n, k, 3, seed=6, cols_seed=5):
         a.replace_rows(rows, new, "woodbury")
         b.replace_rows(rows, new, "sm")
     ref = oo.reeval(a.x, y)
@@ -181,7 +181,7 @@ def test_factored_beta_refresh_reaches_the_definition(k):
     x, y, _ = li.ols_inputs(m, n, p, seed=11)
     ref = oo.IncrementalOLS(x, y)
     w, beta, xty = ref.w.copy(), ref.beta.copy(), ref.xty.copy()
-    for rows, new in li.ols_row_replacements(m, n, k, 4, seed=12):
+    for rows, new in li.ols_row_replacements(m, n, k, 4, seed=12, cols_seed=11):
         u = np.concatenate([new.T, ref.x[rows].T], axis=1)
         g = w @ u
         core = np.diag([1.0] * k + [-1.0] * k) + u.T @ g
