@@ -1118,8 +1118,8 @@ def ols_sweep(seed=0, m=65536, n=4096, p=16, ks=(1, 4, 16), steps=6):
     fixed 10% of its columns scaled by 1e-2 (kappa(X^T X) ~ 3e4), Y ~ N(0, 1);
     an update replaces k rows of X by fresh rows with the same scaling.  Per
     k: the incremental refresh of W = (X^T X)^-1 and beta (block Woodbury,
-    FP32 views, FP64 2k x 2k core) against the re-evaluation (FP64 X^T X by
-    row chunks, Cholesky inverse)."""
+    FP32 views, double-float 2k x 2k core) against the re-evaluation (FP64
+    X^T X by row chunks, Cholesky inverse)."""
     import numpy as np
     import torch
     import linview_inputs as li
@@ -1130,7 +1130,8 @@ def ols_sweep(seed=0, m=65536, n=4096, p=16, ks=(1, 4, 16), steps=6):
     rows = []
     for k in ks:
         prog = Program("ols", [xd, yd], k=k)
-        ups = li.ols_row_replacements(m, n, k, steps + 2, seed=seed + k, dtype=np.float32)
+        ups = li.ols_row_replacements(m, n, k, steps + 2, seed=seed + k, dtype=np.float32,
+                                      cols_seed=seed)
         dev = [(r_, torch.from_numpy(nw).cuda()) for r_, nw in ups]
         for r_, nw in dev[:2]:
             prog.apply_row_block(r_, nw)
@@ -1151,8 +1152,10 @@ def ols_sweep(seed=0, m=65536, n=4096, p=16, ks=(1, 4, 16), steps=6):
                      "speedup": re / inc, "w_pass_gbs": gbs,
                      "rel_err_vs_reeval": errs})
     return {"m": m, "n": n, "p": p, "rows": rows,
-            "note": "incremental: block Woodbury on W (FP32, two passes) with an FP64 2k x 2k "
-                    "core and the factored beta refresh (no pass over W); re-evaluation: FP64 "
+            "note": "incremental: block Woodbury on W (FP32, two passes: G = W^T U by column "
+                    "sums, W += G Wu^T) with a double-float 2k x 2k core (Newton-Schulz, "
+                    "Gauss-Jordan fallback) and the factored beta refresh (no pass over W); "
+                    "re-evaluation: FP64 "
                     "X^T X, Cholesky inverse, beta = W X^T Y; rel_err_vs_reeval: the views after "
                     f"{steps + 2} updates against the re-evaluation that follows them"}
 

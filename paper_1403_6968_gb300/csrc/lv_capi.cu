@@ -173,6 +173,7 @@ struct linview_program {
   void* Yr = nullptr;     // Y rows of the block, k x p
   int64_t* rows_d = nullptr;
   double* Minv = nullptr;
+  void* Cdf = nullptr;  // OLS FP32: the Woodbury core as double-float pairs
   // OLS re-evaluation scratch (FP64)
   double* Z64 = nullptr;
   double* X64 = nullptr;
@@ -2002,15 +2003,30 @@ static linview_status ols_create(linview_program* p, const void* const* inputs,
   LV_TRY(dalloc(p, (size_t)kmax * pp * p->elem, &p->Yr, s));
   LV_TRY(dalloc(p, sizeof(int64_t) * kmax, &t, s));
   p->rows_d = static_cast<int64_t*>(t);
-  LV_TRY(dalloc(p, sizeof(double) * kk * kk, &t, s));
+  LV_TRY(dalloc(p, sizeof(double) * kk * kk, &t, s));  // (FP32: kk x kk float2 pairs)
   p->Minv = static_cast<double*>(t);
+  if (p->elem == 4) LV_TRY(dalloc(p, sizeof(float2) * kk * kk, &p->Cdf, s));
   const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
   p->part_cs = p->fs;
   const int64_t width = (kk > pp) ? kk : pp;
   p->xp_s = rup(width, kMaxFusedR) * p->part_cs;
-  p->yp_q = p->xp_s;
   LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart, s));
-  LV_TRY(dalloc(p, (size_t)g.gR * kMaxFusedR * p->part_cs * p->elem, &p->Ypart, s));
+  // FP32: G = W U by column sums, up to kMaxColSumR columns per pass, one
+  // partial per row block
+  const int64_t ycols = p->elem == 4 ? rup(kk < kMaxColSumR ? kk : kMaxColSumR, kMaxFusedR)
+                                     : kMaxFusedR;
+  p->yp_q = ycols * p->part_cs;
+  LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart, s));
+  if (p->elem == 4 && kk > kMaxProductR) {
+    // split factors of the tensor-core update pass W += G Wu^T
+    void* tc = nullptr;
+    LV_TRY(dalloc(p, (size_t)tc_split_floats(n) * sizeof(float), &tc, s));
+    p->tcA = static_cast<float*>(tc);
+    p->tcB = p->tcA + tc_split_floats(n) / 2;
+    if (!make_tmap_sw128(&p->tmA, p->tcA, 128, n, 128, 128) ||
+        !make_tmap_sw128(&p->tmB, p->tcB, 128, n, 128, 32))
+      return fail(LINVIEW_EDEVICE, "cuTensorMapEncodeTiled failed for the split factors");
+  }
   p->ols_chunk = m < 8192 ? m : 8192;
   return p->elem == 4 ? ols_reeval_t<float>(p, s) : ols_reeval_t<double>(p, s);
 }
@@ -2049,25 +2065,45 @@ static linview_status ols_replace_t(linview_program* p, int kr, const void* nrow
                                  fs, U, n, pp, kr, static_cast<const T*>(p->Yr), side));
     p->all_launches += 2;
   }
-  // G = W U (one read of W per 16 columns in FP32, per 8 in FP64)
-  LV_TRY(run_products_update<T>(p, w, kk, U, nullptr, nullptr, nullptr, s));
-  {
+  if constexpr (sizeof(T) == 4) {
+    // G = W U = W^T U (W is symmetric): column sums of a pass over W, which
+    // need no cross-lane reductions, up to 32 columns per read of W
+    for (int c0 = 0; c0 < kk; c0 += kMaxColSumR) {
+      const int wd = (kk - c0 < kMaxColSumR) ? kk - c0 : kMaxColSumR;
+      LV_TRY(run_fused<T>(p, w, kModeY, wd, nullptr, U + (int64_t)c0 * fs, nullptr, nullptr,
+                          p->Xpart, p->Ypart, s));
+      ProfScope ps(p, s, 0.0);
+      LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Ypart), g.gR, p->yp_q, p->part_cs, n, wd,
+                                     G + (int64_t)c0 * fs, fs, s));
+    }
+  } else {
+    // G = W U (row sums, one read of W per 8 columns)
+    LV_TRY(run_products_update<T>(p, w, kk, U, nullptr, nullptr, nullptr, s));
     ProfScope ps(p, s, 0.0);
     LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, kk, G,
                                    fs, s));
   }
   // M = C^{-1} + U^T G (FP64), its inverse, Wu = -G M^{-1}
+  // (FP32 programs: the core and its inverse as double-float pairs)
+  float2* Cdf = sizeof(T) == 4 ? reinterpret_cast<float2*>(p->Cdf) : nullptr;
   {
     ProfScope ps(p, s, 0.0);
-    LV_CUDA((launch_gram<T>(U, G, fs, n, kk, p->Cpart, p->ticket, p->C, p->status, s)));
+    LV_CUDA((launch_gram<T>(U, G, fs, n, kk, p->Cpart, p->ticket, p->C, p->status, s, Cdf)));
   }
   {
     ProfScope ps(p, s, 0.0);
-    LV_CUDA(launch_core_inverse(p->C, kk, kr, p->Minv, p->status, s, sizeof(T) == 4));
+    if constexpr (sizeof(T) == 4)
+      LV_CUDA(launch_core_inverse_df(Cdf, kk, kr, reinterpret_cast<float2*>(p->Minv), p->status,
+                                     s));
+    else
+      LV_CUDA(launch_core_inverse(p->C, kk, kr, p->Minv, p->status, s));
   }
   {
     ProfScope ps(p, s, 0.0);
-    LV_CUDA(launch_wu<T>(G, fs, n, kk, p->Minv, Wu, s));
+    if constexpr (sizeof(T) == 4)
+      LV_CUDA(launch_wu(G, fs, n, kk, reinterpret_cast<const float2*>(p->Minv), Wu, s));
+    else
+      LV_CUDA(launch_wu(G, fs, n, kk, p->Minv, Wu, s));
   }
   // W' = W + G Wu^T = W - G M^{-1} G^T
   LV_TRY(run_update<T>(p, w, G, Wu, kk, s));

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) gram_df_kernel(const float* __restri
 // One warp per core entry: lane l adds the partials of blocks l, l + 32, ...
 // in order, then a fixed butterfly combines the lanes (lane 0's sum is kept).
 __global__ void gram_reduce_kernel(const float2* __restrict__ Cpart, int G, int ne, double* C,
-                                   unsigned* status) {
+                                   unsigned* status, float2* Cdf) {
   const int e = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (e >= ne) return;  // warp-uniform
@@ -175,12 +175,17 @@ __global__ void gram_reduce_kernel(const float2* __restrict__ Cpart, int G, int 
     const double sum = (double)h + (double)l;
     if (!isfinite(sum)) atomicOr(status, kStatusNonFinite);
     C[e] = sum;
+    if (Cdf) {  // the same sum as a normalised FP32 pair
+      const float hh = __fadd_rn(h, l);
+      Cdf[e] = make_float2(hh, __fsub_rn(l, __fsub_rn(hh, h)));
+    }
   }
 }
 
 template <typename T>
 cudaError_t launch_gram(const T* V, const T* U, int64_t fs, int n, int r, double* Cpart,
-                        unsigned* ticket, double* C, unsigned* status, cudaStream_t s) {
+                        unsigned* ticket, double* C, unsigned* status, cudaStream_t s,
+                        float2* Cdf) {
   if (r < 1 || r > kGramMaxR) return cudaErrorInvalidValue;
   const int G = gram_grid(n);
   if constexpr (std::is_same<T, float>::value) {
@@ -189,7 +194,7 @@ cudaError_t launch_gram(const T* V, const T* U, int64_t fs, int n, int r, double
     const int ne = r * r;
     const int warps_per_block = kThreads / 32;
     gram_reduce_kernel<<<(ne + warps_per_block - 1) / warps_per_block, kThreads, 0, s>>>(
-        part, G, ne, C, status);
+        part, G, ne, C, status, Cdf);
   } else {
     gram_f64_kernel<<<G, kThreads, 0, s>>>(V, U, fs, n, r, Cpart, ticket, C, status);
   }
@@ -452,13 +457,48 @@ __global__ void sum_partials_kernel(const T* part, int blocks, int64_t bs, int64
   out[(int64_t)c * ocs + j] = (T)acc;
 }
 
+// FP32 partials: a cascaded sum in FP32 pairs (each addition's rounding
+// error, exact by TwoSum, is carried in a second accumulator), so the total
+// is FP32-rounded from a ~48-bit sum without GB300's narrow FP64 pipe (some
+// passes leave a few dozen partials per entry).
+__global__ void sum_partials_f32_kernel(const float* part, int blocks, int64_t bs, int64_t cs,
+                                        int n, int r, float* out, int64_t ocs) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * r) return;
+  int c, j;
+  split_index(idx, n, c, j);
+  float hi = 0.f, lo = 0.f;
+  auto add = [&](float x) {
+    const float t = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(t, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(x, bb)));
+    hi = t;
+  };
+  const float* src = part + (int64_t)c * cs + j;
+  int b = 0;
+  for (; b + 8 <= blocks; b += 8) {  // eight loads in flight, added in order
+    float x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = src[(int64_t)(b + i) * bs];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) add(x[i]);
+  }
+  for (; b < blocks; ++b) add(src[(int64_t)b * bs]);
+  out[(int64_t)c * ocs + j] = __fadd_rn(hi, lo);
+}
+
 template <typename T>
 cudaError_t launch_sum_partials(const T* part, int blocks, int64_t block_stride, int64_t cs, int n,
                                 int r, T* out, int64_t out_cs, cudaStream_t s) {
   const int64_t tot = (int64_t)n * r;
   if (tot == 0) return cudaSuccess;
-  sum_partials_kernel<T><<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-      part, blocks, block_stride, cs, n, r, out, out_cs);
+  const unsigned grid = (unsigned)((tot + kThreads - 1) / kThreads);
+  if constexpr (sizeof(T) == 4)
+    sum_partials_f32_kernel<<<grid, kThreads, 0, s>>>(part, blocks, block_stride, cs, n, r, out,
+                                                      out_cs);
+  else
+    sum_partials_kernel<T><<<grid, kThreads, 0, s>>>(part, blocks, block_stride, cs, n, r, out,
+                                                      out_cs);
   return cudaGetLastError();
 }
 
@@ -526,7 +566,7 @@ cudaError_t launch_bounded_wait_probe(uint64_t limit_ns, unsigned* status,
 
 #define LV_INST(T)                                                                              \
   template cudaError_t launch_gram<T>(const T*, const T*, int64_t, int, int, double*, unsigned*, \
-                                      double*, unsigned*, cudaStream_t);                        \
+                                      double*, unsigned*, cudaStream_t, float2*);               \
   template cudaError_t launch_assemble<T>(const AssembleParams&, cudaStream_t);                  \
   template cudaError_t launch_suffix_sums<T>(const T*, T*, int64_t, int, int, int, cudaStream_t); \
   template cudaError_t launch_rm_to_cm<T>(const T*, int64_t, T*, int64_t, int, int,               \

@@ -38,7 +38,8 @@ constexpr int kMaxUpdateR = 32;   // widest factor block of one update pass (sha
                                   // broadcasts of the factor rows bound wider blocks)
 
 // Pass modes: which of X = P Xf, Y = P^T Yf and P += Uu Wu^T a launch does.
-enum PassMode : int { kModeXYU = 7, kModeXY = 3, kModeXU = 5, kModeX = 1 };
+enum PassMode : int { kModeXYU = 7, kModeXY = 3, kModeXU = 5, kModeX = 1, kModeY = 2 };
+constexpr int kMaxColSumR = 32;  // widest factor block of an FP32 column-sums-only pass (Y)
 
 // Everything a view pass needs.  Factors are column-major with column
 // stride ``fs`` (elements); the partial-sum arrays are [block][column][row]
@@ -144,10 +145,12 @@ cudaError_t launch_update(const PassParams& p, const CUtensorMap& tm, int R, cud
 
 // Factor cores and assembly (lv_core.cu).
 // C (r x r, FP64, row-major) = V^T U over n rows; deterministic two-level
-// reduction using Cpart (grid x r*r doubles) and a ticket counter.
+// reduction using Cpart (grid x r*r doubles) and a ticket counter.  FP32
+// programs may also take C as double-float pairs (Cdf, r x r float2).
 template <typename T>
 cudaError_t launch_gram(const T* V, const T* U, int64_t fs, int n, int r, double* Cpart,
-                        unsigned* ticket, double* C, unsigned* status, cudaStream_t s);
+                        unsigned* ticket, double* C, unsigned* status, cudaStream_t s,
+                        float2* Cdf = nullptr);
 int gram_grid(int n);
 
 struct AssembleParams {
@@ -205,12 +208,17 @@ cudaError_t launch_gather_rows(const T* X, int64_t ldx, const int64_t* rows, int
 template <typename T>
 cudaError_t launch_scatter_rows(T* X, int64_t ldx, const int64_t* rows, int k, int n,
                                 const T* src, int64_t ts, cudaStream_t s);
-// (double_float: the elimination in double-float arithmetic on the FP32 pipe,
-// for FP32 programs; else FP64)
+// Minv = (diag(+1 x kpos, -1 x (kk - kpos)) + S)^{-1}, kk <= 64: FP64
+// programs in FP64 (S and Minv kk x kk doubles); FP32 programs in
+// double-float on the FP32 pipe (S and Minv kk x kk float2 pairs).
 cudaError_t launch_core_inverse(const double* S, int kk, int kpos, double* Minv, unsigned* status,
-                                cudaStream_t s, bool double_float = false);
-template <typename T>
-cudaError_t launch_wu(const T* G, int64_t fs, int n, int kk, const double* Minv, T* Wu,
+                                cudaStream_t s);
+cudaError_t launch_core_inverse_df(const float2* S, int kk, int kpos, float2* Minv,
+                                   unsigned* status, cudaStream_t s);
+// Wu = -G Minv (FP64 core for double views, double-float core for float views)
+cudaError_t launch_wu(const double* G, int64_t fs, int n, int kk, const double* Minv, double* Wu,
+                      cudaStream_t s);
+cudaError_t launch_wu(const float* G, int64_t fs, int n, int kk, const float2* Minv, float* Wu,
                       cudaStream_t s);
 template <typename T>
 cudaError_t launch_xty_update(T* xty, int64_t ld, T* xtyc, int64_t fs, const T* U, int n, int p,

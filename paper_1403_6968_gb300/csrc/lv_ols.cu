@@ -183,25 +183,100 @@ __device__ __forceinline__ df2 df_recip(df2 a) {
   return x;
 }
 
-// The same Gauss-Jordan elimination as core_inverse_kernel in double-float
-// arithmetic (FP32 programs): M and the result are FP64 at the interface.
-__global__ void __launch_bounds__(kInvTx * kInvTy)
-    core_inverse_df_kernel(const double* S, int kk, int kpos, double* Minv, unsigned* status) {
-  extern __shared__ double inv_sm[];
+// ---------------------------------------------------------------------------
+// FP32 programs: the core inverse in double-float on the FP32 pipe (one CTA
+// of kCoreThreads threads), M = C^{-1} + S with S = U^T W U given as FP32
+// pairs and C = diag(I, -I).
+//
+// Newton-Schulz first.  M stays close to C^{-1} = C (the replaced rows'
+// leverages x^T W x are about n / m), so X_{j+1} = X_j + X_j R_j with
+// R_j = I - M X_j and X_0 = C converges quadratically: R_{j+1} = R_j^2, hence
+// ||R_{j+1}||_F <= ||R_j||_F^2 (Frobenius norm, submultiplicative) and the
+// iteration converges iff ||R_0||_F < 1.  Every step is two kk x kk products
+// whose entries are independent dot products (each thread takes a 2 x 2 tile
+// of entries), not kk barrier-separated pivot steps.  The steps run in FP32
+// on M rounded to FP32 until their rounding floor (a step that no longer
+// squares the norm, or a norm below 1e-6).  One residual R = I - M X of that
+// FP32 iterate is then taken in double-float against the unrounded M and
+// rounded to FP32 (|R| ~ 1e-6, so FP32 keeps it to ~1e-13 absolute), and the
+// result is X + X R: the product X R in FP32 (its rounding error is ~1e-13
+// of X), the sum as a double-float pair.  Since the new residual is R^2 plus
+// that rounding, a double-float residual below kNsFinish gives an inverse
+// with a residual near 1e-11 or better.
+//
+// Otherwise -- ||R_0|| >= 1, an FP32 floor above 1e-3, a double-float
+// residual at or above kNsFinish, or non-finite values: a core far from C,
+// ill-conditioned or singular -- the same CTA runs Gauss-Jordan elimination
+// with partial pivoting in double-float (as core_inverse_kernel does in FP64),
+// which also latches kStatusSingular for a singular core.
+// ---------------------------------------------------------------------------
+constexpr int kCoreThreads = kInvTx * kInvTy;  // 512
+constexpr int kNsMaxIter = 12;
+constexpr float kNsFinish = 1e-5f;
+
+__host__ __device__ inline int ns_ld(int kk) { return kk + 2; }  // padded row stride (even)
+
+size_t core_df_smem(int kk) {
+  const size_t ld = (size_t)ns_ld(kk);
+  const size_t ns = (size_t)kk * ld * (sizeof(df2) + 4 * sizeof(float));  // Md, Mf, Xa, Xb, Rf
+  const size_t gj = sizeof(df2) * ((size_t)4 * kk * kk + 3 * kk);
+  return ns > gj ? ns : gj;
+}
+
+// acc += x y for df2 x and float y: the exact product of the high parts by
+// FMA, the low part's product in FP32; the high sum by TwoSum, the errors
+// collected in acc.lo (renormalised by the caller)
+__device__ __forceinline__ void df_acc(df2& acc, df2 x, float y) {
+  const float p = __fmul_rn(x.hi, y);
+  const float e = __fmaf_rn(x.lo, y, __fmaf_rn(x.hi, y, -p));
+  const float t = __fadd_rn(acc.hi, p);
+  const float z = __fsub_rn(t, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+  acc.hi = t;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ df2 df_norm(df2 a) {
+  const float h = __fadd_rn(a.hi, a.lo);
+  return {h, __fsub_rn(a.lo, __fsub_rn(h, a.hi))};
+}
+
+// sum over the CTA of the per-thread values v, in a fixed order; every
+// thread returns the same total
+__device__ __forceinline__ float cta_sum(float v, float* wsum) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();  // earlier readers of wsum are done
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+#pragma unroll
+  for (int w = 0; w < kCoreThreads / 32; ++w) t += wsum[w];
+  return t;
+}
+
+// Gauss-Jordan elimination with partial pivoting in double-float on the
+// augmented [M | I]: each column step reads one copy and writes the other;
+// warp 0 picks the pivot (largest magnitude, first row on ties) and scales the
+// pivot row.  A pivot at or below 1e-13 max|M| latches kStatusSingular and
+// the result is zero.  (tx, ty) in [0, kInvTx) x [0, kInvTy).
+__device__ void gauss_jordan_df(const float2* S, int kk, int kpos, float2* Minv, unsigned* status,
+                                df2* sm, int tx, int ty) {
   const int w = 2 * kk;
-  df2* cur = reinterpret_cast<df2*>(inv_sm);  // kk x w
-  df2* nxt = cur + kk * w;                    // kk x w
-  df2* prow = nxt + kk * w;                   // w: the pivot row divided by the pivot
-  df2* fcol = prow + w;                       // kk: column col before the step
+  df2* cur = sm;               // kk x w
+  df2* nxt = cur + kk * w;     // kk x w
+  df2* prow = nxt + kk * w;    // w: the pivot row divided by the pivot
+  df2* fcol = prow + w;        // kk: column col before the step
   __shared__ float wmax[kInvTy];
   __shared__ int s_piv, s_sing;
-  const int tx = threadIdx.x, ty = threadIdx.y;
   float m = 0.f;
   for (int i = ty; i < kk; i += kInvTy)
     for (int j = tx; j < w; j += kInvTx) {
       df2 v;
       if (j < kk) {
-        v = df_make(S[i * kk + j] + (i == j ? (i < kpos ? 1.0 : -1.0) : 0.0));
+        const float2 sv = S[i * kk + j];
+        v = {sv.x, sv.y};
+        if (i == j) v = df_sum(v, {i < kpos ? 1.f : -1.f, 0.f});
         m = fmaxf(m, fabsf(v.hi));
       } else {
         v = {(j - kk == i) ? 1.f : 0.f, 0.f};
@@ -263,14 +338,158 @@ __global__ void __launch_bounds__(kInvTx * kInvTy)
   }
   const bool singular = s_sing != 0;
   for (int i = ty; i < kk; i += kInvTy)
-    for (int j = tx; j < kk; j += kInvTx)
-      Minv[i * kk + j] = singular ? 0.0 : df_double(cur[i * w + kk + j]);
+    for (int j = tx; j < kk; j += kInvTx) {
+      const df2 v = cur[i * w + kk + j];
+      Minv[i * kk + j] = singular ? make_float2(0.f, 0.f) : make_float2(v.hi, v.lo);
+    }
 }
 
-// Wu(:, c) = - sum_c' G(:, c') Minv(c', c) in FP64; a thread computes two
-// columns c = 2 blockIdx.y, 2 blockIdx.y + 1 of one row j (kk is even).
-template <typename T>
-__global__ void wu_kernel(const T* G, int64_t fs, int n, int kk, const double* Minv, T* Wu) {
+// O = D + sgn A B over 2 x 2 tiles (FP32; A, B, O with row stride ld; D the
+// identity if ident, else A itself when addA).  Returns this thread's sum of
+// squares of the O entries it wrote.
+__device__ __forceinline__ float ns_product(const float* A, const float* B, float* O, int kk,
+                                            int ld, float sgn, bool ident, const float* Dsrc) {
+  const int h = kk / 2;
+  float m = 0.f;
+  for (int tile = threadIdx.x; tile < h * h; tile += kCoreThreads) {
+    const int i0 = 2 * (tile / h), j0 = 2 * (tile % h);
+    float a00, a01, a10, a11;
+    if (ident) {
+      a00 = (i0 == j0) ? 1.f : 0.f;
+      a01 = 0.f;
+      a10 = 0.f;
+      a11 = a00;
+    } else {
+      const float2 d0 = *reinterpret_cast<const float2*>(Dsrc + i0 * ld + j0);
+      const float2 d1 = *reinterpret_cast<const float2*>(Dsrc + (i0 + 1) * ld + j0);
+      a00 = d0.x; a01 = d0.y; a10 = d1.x; a11 = d1.y;
+    }
+    const float* a0 = A + i0 * ld;
+    const float* a1 = a0 + ld;
+#pragma unroll 4
+    for (int t = 0; t < kk; ++t) {
+      const float2 bv = *reinterpret_cast<const float2*>(B + t * ld + j0);
+      const float x0 = sgn * a0[t], x1 = sgn * a1[t];
+      a00 = fmaf(x0, bv.x, a00);
+      a01 = fmaf(x0, bv.y, a01);
+      a10 = fmaf(x1, bv.x, a10);
+      a11 = fmaf(x1, bv.y, a11);
+    }
+    *reinterpret_cast<float2*>(O + i0 * ld + j0) = make_float2(a00, a01);
+    *reinterpret_cast<float2*>(O + (i0 + 1) * ld + j0) = make_float2(a10, a11);
+    m = fmaf(a00, a00, fmaf(a01, a01, fmaf(a10, a10, fmaf(a11, a11, m))));
+  }
+  return m;
+}
+
+__global__ void __launch_bounds__(kCoreThreads)
+    core_inverse_df_kernel(const float2* S, int kk, int kpos, float2* Minv, unsigned* status) {
+  extern __shared__ __align__(16) unsigned char core_sm[];
+  __shared__ float wsum[kCoreThreads / 32];
+  const int tid = threadIdx.x;
+  const int ld = ns_ld(kk);
+  const int e2 = kk * kk;
+  df2* Md = reinterpret_cast<df2*>(core_sm);  // kk x ld
+  float* Mf = reinterpret_cast<float*>(Md + kk * ld);
+  float* Xa = Mf + kk * ld;
+  float* Xb = Xa + kk * ld;
+  float* Rf = Xb + kk * ld;
+  for (int e = tid; e < e2; e += kCoreThreads) {
+    const int i = e / kk, j = e % kk;
+    const float2 sv = S[e];
+    df2 v = {sv.x, sv.y};
+    float c = 0.f;
+    if (i == j) {
+      c = i < kpos ? 1.f : -1.f;
+      v = df_sum(v, {c, 0.f});
+    }
+    Md[i * ld + j] = v;
+    Mf[i * ld + j] = v.hi;
+    Xa[i * ld + j] = c;
+  }
+  __syncthreads();
+  float* Xc = Xa;
+  float* Xn = Xb;
+  bool to_df = false;
+  if ((kk & 1) == 0) {
+    float prev = -1.f;
+    for (int it = 0; it < kNsMaxIter; ++it) {
+      // R = I - M X (FP32); every thread reaches the same decision
+      const float r = sqrtf(cta_sum(ns_product(Mf, Xc, Rf, kk, ld, -1.f, true, nullptr), wsum));
+      if (!(r < 1.f)) break;  // diverges (or NaN): Gauss-Jordan
+      if (r < 1e-6f || (prev >= 0.f && r > 2.f * prev * prev)) {
+        to_df = r < 1e-3f;  // the FP32 floor: finish in double-float
+        break;
+      }
+      prev = r;
+      // X' = X + X R into the other buffer
+      ns_product(Xc, Rf, Xn, kk, ld, 1.f, false, Xc);
+      __syncthreads();
+      float* t = Xc;
+      Xc = Xn;
+      Xn = t;
+    }
+  }
+  if (to_df) {
+    // R = I - M X with M in double-float, rounded to FP32
+    const int h = kk / 2;
+    float m = 0.f;
+    __syncthreads();  // the FP32 residual's readers are done
+    for (int tile = tid; tile < h * h; tile += kCoreThreads) {
+      const int i0 = 2 * (tile / h), j0 = 2 * (tile % h);
+      df2 a00 = {(i0 == j0) ? 1.f : 0.f, 0.f}, a01 = {0.f, 0.f}, a10 = {0.f, 0.f}, a11 = a00;
+      const df2* m0 = Md + i0 * ld;
+      const df2* m1 = m0 + ld;
+      for (int t = 0; t < kk; ++t) {
+        const float2 bv = *reinterpret_cast<const float2*>(Xc + t * ld + j0);
+        const df2 x0 = {-m0[t].hi, -m0[t].lo}, x1 = {-m1[t].hi, -m1[t].lo};
+        df_acc(a00, x0, bv.x);
+        df_acc(a01, x0, bv.y);
+        df_acc(a10, x1, bv.x);
+        df_acc(a11, x1, bv.y);
+      }
+      const float r00 = __fadd_rn(a00.hi, a00.lo), r01 = __fadd_rn(a01.hi, a01.lo);
+      const float r10 = __fadd_rn(a10.hi, a10.lo), r11 = __fadd_rn(a11.hi, a11.lo);
+      *reinterpret_cast<float2*>(Rf + i0 * ld + j0) = make_float2(r00, r01);
+      *reinterpret_cast<float2*>(Rf + (i0 + 1) * ld + j0) = make_float2(r10, r11);
+      m = fmaf(r00, r00, fmaf(r01, r01, fmaf(r10, r10, fmaf(r11, r11, m))));
+    }
+    const float r = sqrtf(cta_sum(m, wsum));
+    if (r < kNsFinish) {
+      // Minv = X + X R: X R in FP32, the sum as a pair
+      for (int tile = tid; tile < h * h; tile += kCoreThreads) {
+        const int i0 = 2 * (tile / h), j0 = 2 * (tile % h);
+        float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
+        const float* x0 = Xc + i0 * ld;
+        const float* x1 = x0 + ld;
+#pragma unroll 4
+        for (int t = 0; t < kk; ++t) {
+          const float2 bv = *reinterpret_cast<const float2*>(Rf + t * ld + j0);
+          a00 = fmaf(x0[t], bv.x, a00);
+          a01 = fmaf(x0[t], bv.y, a01);
+          a10 = fmaf(x1[t], bv.x, a10);
+          a11 = fmaf(x1[t], bv.y, a11);
+        }
+        const df2 o00 = df_sum({x0[j0], 0.f}, {a00, 0.f}), o01 = df_sum({x0[j0 + 1], 0.f}, {a01, 0.f});
+        const df2 o10 = df_sum({x1[j0], 0.f}, {a10, 0.f}), o11 = df_sum({x1[j0 + 1], 0.f}, {a11, 0.f});
+        Minv[i0 * kk + j0] = make_float2(o00.hi, o00.lo);
+        Minv[i0 * kk + j0 + 1] = make_float2(o01.hi, o01.lo);
+        Minv[(i0 + 1) * kk + j0] = make_float2(o10.hi, o10.lo);
+        Minv[(i0 + 1) * kk + j0 + 1] = make_float2(o11.hi, o11.lo);
+      }
+      return;
+    }
+  }
+  __syncthreads();  // the Newton-Schulz buffers are done with: the same memory
+  gauss_jordan_df(S, kk, kpos, Minv, status, reinterpret_cast<df2*>(core_sm), tid % kInvTx,
+                  tid / kInvTx);
+}
+
+// Wu(:, c) = - sum_c' G(:, c') Minv(c', c), FP64 views and core; a thread
+// computes two columns c = 2 blockIdx.y, 2 blockIdx.y + 1 of one row j (kk
+// is even).
+__global__ void wu_f64_kernel(const double* G, int64_t fs, int n, int kk, const double* Minv,
+                              double* Wu) {
   __shared__ double ms[64][2];
   const int c = 2 * blockIdx.y;
   for (int e = threadIdx.x; e < kk; e += blockDim.x) {
@@ -282,17 +501,47 @@ __global__ void wu_kernel(const T* G, int64_t fs, int n, int kk, const double* M
   if (j >= n) return;
   double a0 = 0.0, a1 = 0.0;
   for (int c2 = 0; c2 < kk; ++c2) {
-    const double g = (double)G[(int64_t)c2 * fs + j];
+    const double g = G[(int64_t)c2 * fs + j];
     a0 = fma(g, ms[c2][0], a0);
     a1 = fma(g, ms[c2][1], a1);
   }
-  Wu[(int64_t)c * fs + j] = (T)(-a0);
-  Wu[(int64_t)(c + 1) * fs + j] = (T)(-a1);
+  Wu[(int64_t)c * fs + j] = -a0;
+  Wu[(int64_t)(c + 1) * fs + j] = -a1;
+}
+
+// The same for FP32 views with the double-float core: each product of an
+// FP32 G entry and a core pair is accumulated as a pair (df_acc) and the sum
+// is rounded once to FP32.  A thread computes four columns c = 4 blockIdx.y
+// .. + 3 of one row j (kk is even; a trailing pair is masked).
+constexpr int kWuCols = 4;
+__global__ void wu_df_kernel(const float* G, int64_t fs, int n, int kk, const float2* Minv,
+                             float* Wu) {
+  __shared__ df2 ms[64][kWuCols];
+  const int c0 = kWuCols * blockIdx.y;
+  for (int e = threadIdx.x; e < kk * kWuCols; e += blockDim.x) {
+    const int r = e / kWuCols, q = e % kWuCols;
+    const float2 v = (c0 + q < kk) ? Minv[r * kk + c0 + q] : make_float2(0.f, 0.f);
+    ms[r][q] = {-v.x, -v.y};
+  }
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  df2 acc[kWuCols];
+#pragma unroll
+  for (int q = 0; q < kWuCols; ++q) acc[q] = {0.f, 0.f};
+  for (int c2 = 0; c2 < kk; ++c2) {
+    const float g = G[(int64_t)c2 * fs + j];
+#pragma unroll
+    for (int q = 0; q < kWuCols; ++q) df_acc(acc[q], ms[c2][q], g);
+  }
+#pragma unroll
+  for (int q = 0; q < kWuCols; ++q)
+    if (c0 + q < kk) Wu[(int64_t)(c0 + q) * fs + j] = __fadd_rn(acc[q].hi, acc[q].lo);
 }
 
 // X^T Y += (X'_R - X_R)^T Y_R.  U holds X'_R^T in columns [0, k) and X_R^T in
 // [k, 2k); Yr is k x p row-major.  Updates the row-major view (ld) and the
-// column-major mirror (fs).
+// column-major mirror (fs).  FP64 views: FP64 sums.
 template <typename T>
 __global__ void xty_update_kernel(T* xty, int64_t ld, T* xtyc, int64_t fs, const T* U, int n,
                                   int p, int k, const T* Yr) {
@@ -307,6 +556,38 @@ __global__ void xty_update_kernel(T* xty, int64_t ld, T* xtyc, int64_t fs, const
   }
   xty[(int64_t)j * ld + c] = (T)acc;
   xtyc[(int64_t)c * fs + j] = (T)acc;
+}
+
+// FP32 views: the same sum in double-float (the old value, then the exact
+// products x'_t y_t and -x_t y_t accumulated as pairs), rounded once.  A
+// thread takes kRowCols columns c0 .. of one row j, so the factor entries are
+// loaded once per row and the loads of U are coalesced over j.
+constexpr int kRowCols = 4;
+__global__ void xty_update_df_kernel(float* xty, int64_t ld, float* xtyc, int64_t fs,
+                                     const float* U, int n, int p, int k, const float* Yr) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c0 = blockIdx.y * kRowCols;
+  if (j >= n) return;
+  df2 acc[kRowCols];
+#pragma unroll
+  for (int q = 0; q < kRowCols; ++q)
+    acc[q] = {c0 + q < p ? xty[(int64_t)j * ld + c0 + q] : 0.f, 0.f};
+  for (int t = 0; t < k; ++t) {
+    const float xn = U[(int64_t)t * fs + j], xo = U[(int64_t)(k + t) * fs + j];
+#pragma unroll
+    for (int q = 0; q < kRowCols; ++q) {
+      const float y = c0 + q < p ? Yr[(int64_t)t * p + c0 + q] : 0.f;
+      df_acc(acc[q], {xn, 0.f}, y);
+      df_acc(acc[q], {-xo, 0.f}, y);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kRowCols; ++q)
+    if (c0 + q < p) {
+      const float v = __fadd_rn(acc[q].hi, acc[q].lo);
+      xty[(int64_t)j * ld + c0 + q] = v;
+      xtyc[(int64_t)(c0 + q) * fs + j] = v;
+    }
 }
 
 // H(c2, c) = sum_j Wu(j, c2) C(j, c) for column-major Wu (n x kk) and C
@@ -336,19 +617,39 @@ __global__ void __launch_bounds__(256) wtc_kernel(const T* Wu, const T* Cc, int6
 
 // beta(j, c) += sum_t (G(j, t) - G(j, k + t)) Y_R(t, c) + sum_c2 G(j, c2) H(c2, c)
 // (the factored beta refresh above); G column-major (fs), Y_R k x p and H
-// 2k x p row-major, beta row-major (ld).
+// 2k x p row-major, beta row-major (ld).  A thread takes kRowCols columns c0
+// .. of one row j: the two G entries of each t are loaded once (coalesced
+// over j) and serve both sums; Y_R and H are read from shared memory.
 template <typename T>
 __global__ void beta_update_kernel(T* beta, int64_t ld, const T* G, int64_t fs, int n, int p,
                                    int k, const T* Yr, const T* H) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * p) return;
-  int j, c;
-  split_index(idx, p, j, c);
-  T acc = 0;
-  for (int t = 0; t < k; ++t)
-    acc += (G[(int64_t)t * fs + j] - G[(int64_t)(k + t) * fs + j]) * Yr[t * p + c];
-  for (int c2 = 0; c2 < 2 * k; ++c2) acc += G[(int64_t)c2 * fs + j] * H[c2 * p + c];
-  beta[(int64_t)j * ld + c] += acc;
+  extern __shared__ __align__(16) unsigned char beta_sm[];
+  T* Ys = reinterpret_cast<T*>(beta_sm);  // k x kRowCols
+  T* Hs = Ys + k * kRowCols;              // 2k x kRowCols
+  const int c0 = blockIdx.y * kRowCols;
+  for (int e = threadIdx.x; e < 3 * k * kRowCols; e += blockDim.x) {
+    const int r = e / kRowCols, q = e % kRowCols;
+    const bool ok = c0 + q < p;
+    if (r < k) Ys[e] = ok ? Yr[(int64_t)r * p + c0 + q] : T(0);
+    else Hs[e - k * kRowCols] = ok ? H[(int64_t)(r - k) * p + c0 + q] : T(0);
+  }
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  T acc[kRowCols] = {};
+  for (int t = 0; t < k; ++t) {
+    const T g1 = G[(int64_t)t * fs + j], g2 = G[(int64_t)(k + t) * fs + j];
+    const T d = g1 - g2;
+#pragma unroll
+    for (int q = 0; q < kRowCols; ++q) {
+      acc[q] += d * Ys[t * kRowCols + q];
+      acc[q] += g1 * Hs[t * kRowCols + q];
+      acc[q] += g2 * Hs[(k + t) * kRowCols + q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kRowCols; ++q)
+    if (c0 + q < p) beta[(int64_t)j * ld + c0 + q] += acc[q];
 }
 
 // dst (double, row-major rows x cols, ldd) = (double) src (T, lds)
@@ -411,30 +712,40 @@ cudaError_t launch_scatter_rows(T* X, int64_t ldx, const int64_t* rows, int k, i
 }
 
 cudaError_t launch_core_inverse(const double* S, int kk, int kpos, double* Minv, unsigned* status,
-                                cudaStream_t s, bool double_float) {
+                                cudaStream_t s) {
   if (kk < 1 || kk > 64) return cudaErrorInvalidValue;
   static const cudaError_t configured =
       cudaFuncSetAttribute(core_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)core_inverse_smem(64));
   if (configured != cudaSuccess) return configured;
-  static const cudaError_t configured_df =
-      cudaFuncSetAttribute(core_inverse_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)core_inverse_smem(64));
-  if (configured_df != cudaSuccess) return configured_df;
-  if (double_float)
-    core_inverse_df_kernel<<<1, dim3(kInvTx, kInvTy), core_inverse_smem(kk), s>>>(S, kk, kpos,
-                                                                                Minv, status);
-  else
-    core_inverse_kernel<<<1, dim3(kInvTx, kInvTy), core_inverse_smem(kk), s>>>(S, kk, kpos, Minv,
-                                                                             status);
+  core_inverse_kernel<<<1, dim3(kInvTx, kInvTy), core_inverse_smem(kk), s>>>(S, kk, kpos, Minv,
+                                                                           status);
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_wu(const T* G, int64_t fs, int n, int kk, const double* Minv, T* Wu,
+cudaError_t launch_core_inverse_df(const float2* S, int kk, int kpos, float2* Minv,
+                                   unsigned* status, cudaStream_t s) {
+  if (kk < 1 || kk > 64) return cudaErrorInvalidValue;
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(core_inverse_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)core_df_smem(64));
+  if (configured != cudaSuccess) return configured;
+  core_inverse_df_kernel<<<1, kCoreThreads, core_df_smem(kk), s>>>(S, kk, kpos, Minv, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wu(const double* G, int64_t fs, int n, int kk, const double* Minv, double* Wu,
                       cudaStream_t s) {
   if (kk < 2 || kk > 64 || (kk & 1)) return cudaErrorInvalidValue;
-  wu_kernel<T><<<dim3(blocks_for(n), kk / 2), kThreads, 0, s>>>(G, fs, n, kk, Minv, Wu);
+  wu_f64_kernel<<<dim3(blocks_for(n), kk / 2), kThreads, 0, s>>>(G, fs, n, kk, Minv, Wu);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wu(const float* G, int64_t fs, int n, int kk, const float2* Minv, float* Wu,
+                      cudaStream_t s) {
+  if (kk < 2 || kk > 64 || (kk & 1)) return cudaErrorInvalidValue;
+  wu_df_kernel<<<dim3(blocks_for(n), (kk + kWuCols - 1) / kWuCols), kThreads, 0, s>>>(G, fs, n,
+                                                                                      kk, Minv, Wu);
   return cudaGetLastError();
 }
 
@@ -443,16 +754,21 @@ cudaError_t launch_beta_update(T* beta, int64_t ld, const T* G, const T* Wu, con
                                int64_t fs, int n, int p, int k, const T* Yr, T* H,
                                cudaStream_t s) {
   wtc_kernel<T><<<(unsigned)(2 * k * p), 256, 0, s>>>(Wu, Cc, fs, n, 2 * k, p, H);
-  beta_update_kernel<T><<<blocks_for((int64_t)n * p), kThreads, 0, s>>>(beta, ld, G, fs, n, p, k,
-                                                                        Yr, H);
+  beta_update_kernel<T>
+      <<<dim3(blocks_for(n), (p + kRowCols - 1) / kRowCols), kThreads,
+         sizeof(T) * 3 * k * kRowCols, s>>>(beta, ld, G, fs, n, p, k, Yr, H);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_xty_update(T* xty, int64_t ld, T* xtyc, int64_t fs, const T* U, int n, int p,
                               int k, const T* Yr, cudaStream_t s) {
-  xty_update_kernel<T><<<blocks_for((int64_t)n * p), kThreads, 0, s>>>(xty, ld, xtyc, fs, U, n, p,
-                                                                       k, Yr);
+  if constexpr (sizeof(T) == 4)
+    xty_update_df_kernel<<<dim3(blocks_for(n), (p + kRowCols - 1) / kRowCols), kThreads, 0, s>>>(
+        xty, ld, xtyc, fs, U, n, p, k, Yr);
+  else
+    xty_update_kernel<T><<<blocks_for((int64_t)n * p), kThreads, 0, s>>>(xty, ld, xtyc, fs, U, n,
+                                                                         p, k, Yr);
   return cudaGetLastError();
 }
 
@@ -486,7 +802,6 @@ cudaError_t launch_from_double(const double* src, int64_t lds, T* dst, int64_t l
                                              int64_t, int64_t, cudaStream_t);                    \
   template cudaError_t launch_scatter_rows<T>(T*, int64_t, const int64_t*, int, int, const T*,    \
                                               int64_t, cudaStream_t);                            \
-  template cudaError_t launch_wu<T>(const T*, int64_t, int, int, const double*, T*, cudaStream_t); \
   template cudaError_t launch_beta_update<T>(T*, int64_t, const T*, const T*, const T*, int64_t,  \
                                              int, int, int, const T*, T*, cudaStream_t);         \
   template cudaError_t launch_xty_update<T>(T*, int64_t, T*, int64_t, const T*, int, int, int,    \

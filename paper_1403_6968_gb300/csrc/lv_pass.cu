@@ -531,7 +531,7 @@ static cudaError_t launch_fused_t(const PassParams& p, const CUtensorMap& tm, cu
       kWs ? sizeof(T) * kStagesWs * kBatch * STRIP + sizeof(uint64_t) * (2 * kStagesWs + 2) +
                 kStagesWs * kBatch * R *
                     (((MODE & 4) ? sizeof(float) : 0) + ((MODE & 2) ? sizeof(float) : 0) +
-                     4 * sizeof(float)) +
+                     ((MODE & 1) ? 4 * sizeof(float) : 0)) +
                 (((MODE & 6) == 6) ? sizeof(double) * kThreads : 0)
           : sizeof(T) * kStages * kBatch * STRIP + sizeof(uint64_t) * kStages +
                 sizeof(T) * (2 * kBatch * R + kBatch * R * (128 + 32 / R)) +
@@ -571,6 +571,8 @@ static cudaError_t fused_by_r(const PassParams& p, const CUtensorMap& tm, int R,
   if (R <= 8) return launch_fused_t<T, 8, MODE>(p, tm, s);
   if constexpr (std::is_same<T, float>::value && (MODE & 4) == 0)
     if (R <= kMaxProductR) return launch_fused_t<T, kMaxProductR, MODE>(p, tm, s);
+  if constexpr (std::is_same<T, float>::value && MODE == kModeY)
+    if (R <= kMaxColSumR) return launch_fused_t<T, kMaxColSumR, MODE>(p, tm, s);
   return cudaErrorInvalidValue;
 }
 
@@ -582,6 +584,9 @@ cudaError_t launch_fused(const PassParams& p, const CUtensorMap& tm, int R, int 
     case kModeXY: return fused_by_r<T, kModeXY>(p, tm, R, s);
     case kModeXU: return fused_by_r<T, kModeXU>(p, tm, R, s);
     case kModeX: return fused_by_r<T, kModeX>(p, tm, R, s);
+    case kModeY:
+      if constexpr (std::is_same<T, float>::value) return fused_by_r<T, kModeY>(p, tm, R, s);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

@@ -160,8 +160,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   // regions a mode does not use take no space
   T* Us = reinterpret_cast<T*>(empty + S + 2);   // [S][kBatch][R] (DO_U)
   T* Vs = Us + (DO_U ? S * kBatch * R : 0);      // [S][kBatch][R] (DO_Y)
-  T* Xw = Vs + (DO_Y ? S * kBatch * R : 0);      // [S][kBatch][4][R] warp sums
-  double* Csh = reinterpret_cast<double*>(Xw + S * kBatch * 4 * R);  // [kThreads] core sums (DO_U && DO_Y)
+  T* Xw = Vs + (DO_Y ? S * kBatch * R : 0);      // [S][kBatch][4][R] warp sums (DO_X)
+  double* Csh = reinterpret_cast<double*>(Xw + (DO_X ? S * kBatch * 4 * R : 0));  // [kThreads] core sums (DO_U && DO_Y)
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;

@@ -35,6 +35,7 @@ def _dev(x):
 @pytest.mark.parametrize("m,n,p,k", [(2000, 200, 4, 1), (3000, 257, 3, 4), (4096, 512, 16, 16),
                                      (100, 30, 1, 5), (1500, 100, 2, 32)])
 def test_row_block_updates(prec, m, n, p, k):
+    """Every update against the oracle's fresh solve."""
     dt = np.float64 if prec == "f64" else np.float32
     x, y, _ = li.ols_inputs(m, n, p, seed=m + n, dtype=dt)
     prog = _prog("ols", [_dev(x), _dev(y)], k=k, precision=prec)
@@ -43,7 +44,7 @@ def test_row_block_updates(prec, m, n, p, k):
     prog.sync()
     assert rel_frob(prog.read_view_host(0), ref.w) <= tol
     assert rel_frob(prog.read_view_host(1), ref.beta) <= tol
-    for rows, new in li.ols_row_replacements(m, n, k, 5, seed=m, dtype=dt):
+    for rows, new in li.ols_row_replacements(m, n, k, 5, seed=m, dtype=dt, cols_seed=m + n):
         prog.apply_row_block(rows, _dev(new))
         ref.replace_rows(rows, new.astype(np.float64))
         prog.sync()
@@ -60,7 +61,7 @@ def test_host_rows_and_errors():
     x, y, _ = li.ols_inputs(m, n, p, seed=1)
     prog = _prog("ols", [x, y], k=k, precision="f64")
     ref = oo.IncrementalOLS(x, y)
-    (rows, new), = li.ols_row_replacements(m, n, k, 1, seed=2)
+    (rows, new), = li.ols_row_replacements(m, n, k, 1, seed=2, cols_seed=1)
     prog.apply_row_block(rows, new)          # host new rows
     ref.replace_rows(rows, new)
     prog.sync()
@@ -75,17 +76,39 @@ def test_host_rows_and_errors():
     assert rel_frob(prog.read_view_host(0), ref.w) <= 1e-10
 
 
-def test_singular_core_is_reported():
+def test_high_leverage_core_f32():
+    """FP32 programs invert the Woodbury core by a Newton-Schulz iteration from
+    C = diag(I, -I), which converges when the replaced rows' leverages are
+    small (m >> n) and hands over to Gauss-Jordan otherwise.  m = 40, n = 32
+    without scaled columns: leverages near 0.8, kappa(X^T X) about 1e2, so
+    FP32 still meets 1e-4 after every update."""
+    m, n, p, k = 40, 32, 2, 3
+    x, y, _ = li.ols_inputs(m, n, p, seed=77, frac=0.0, dtype=np.float32)
+    prog = _prog("ols", [_dev(x), _dev(y)], k=k, precision="f32")
+    ref = oo.IncrementalOLS(x.astype(np.float64), y.astype(np.float64))
+    for rows, new in li.ols_row_replacements(m, n, k, 6, seed=78, frac=0.0, dtype=np.float32):
+        prog.apply_row_block(rows, _dev(new))
+        ref.replace_rows(rows, new.astype(np.float64))
+        prog.sync()
+        fresh = oo.reeval(ref.x, ref.y)
+        assert rel_frob(prog.read_view_host(0), fresh["W"]) <= 1e-4
+        assert rel_frob(prog.read_view_host(1), fresh["beta"]) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_singular_core_is_reported(prec):
     """X = I (16 x 16): replacing row 0 by zeros makes X'^T X' singular, so the
     Woodbury core M = diag(1, -1) + U^T W U = [[1, 0], [0, 0]] is exactly
-    singular; the device latches ESINGULAR and W is left as it was."""
+    singular; the device latches ESINGULAR and W is left as it was (FP32: the
+    Newton-Schulz residual starts at 1, so Gauss-Jordan decides)."""
     from paper_1403_6968_gb300 import LinviewError
     n = 16
-    x = np.eye(n)
-    y = np.arange(2 * n, dtype=np.float64).reshape(n, 2)
-    prog = _prog("ols", [x, y], k=1, precision="f64")
+    dt = np.float64 if prec == "f64" else np.float32
+    x = np.eye(n, dtype=dt)
+    y = np.arange(2 * n, dtype=dt).reshape(n, 2)
+    prog = _prog("ols", [x, y], k=1, precision=prec)
     prog.sync()
-    prog.apply_row_block([0], np.zeros((1, n)))
+    prog.apply_row_block([0], np.zeros((1, n), dtype=dt))
     with pytest.raises(LinviewError) as e:
         prog.sync()
     assert e.value.name == "ESINGULAR"
@@ -97,7 +120,7 @@ def test_reeval_resets_to_fresh_inverse():
     x, y, _ = li.ols_inputs(m, n, p, seed=3, dtype=np.float32)
     prog = _prog("ols", [_dev(x), _dev(y)], k=k)
     xs = x.astype(np.float64)
-    for rows, new in li.ols_row_replacements(m, n, k, 4, seed=4, dtype=np.float32):
+    for rows, new in li.ols_row_replacements(m, n, k, 4, seed=4, dtype=np.float32, cols_seed=3):
         prog.apply_row_block(rows, _dev(new))
         xs[rows] = new
     prog.reeval()
@@ -116,7 +139,8 @@ def test_full_size_precision_form(k):
     prog = _prog("ols", [_dev(x), _dev(y)], k=k)
     ref = oo.IncrementalOLS(x.astype(np.float64), y.astype(np.float64))
     rows_s = [0, 1000, 2047, n - 1]
-    for rows, new in li.ols_row_replacements(m, n, k, 3, seed=k, dtype=np.float32):
+    for rows, new in li.ols_row_replacements(m, n, k, 3, seed=k, dtype=np.float32,
+                                             cols_seed=0):
         prog.apply_row_block(rows, _dev(new))
         ref.replace_rows(rows, new.astype(np.float64))
         prog.sync()
