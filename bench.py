@@ -72,7 +72,7 @@ def _args():
                     choices=["rank4_stream", "k_sweep", "iteration_p_sweep", "gd_regression",
                              "small_fp64", "ols_row_blocks", "iteration_adjoint", "serving",
                              "zipf_batches", "drift", "gemm", "iteration_p_sweep_n30000",
-                             "gd_regression_n30000"],
+                             "gd_regression_n30000", "ols_drift"],
                     help="run one secondary section alone (no headline line): profiling")
     return ap.parse_args()
 
@@ -573,6 +573,9 @@ def run_ours(args):
     if not args.no_drift and ws == 1:
         section("drift", lambda: drift_report(drift_streams(args), _drift_a(args), k,
                                               not args.no_cpu_baseline))
+        if not args.no_ols:
+            section("ols_drift", lambda: ols_drift_report(ols_drift_streams(seed=rank),
+                                                          not args.no_cpu_baseline))
     if not args.no_ksweep:
         section("k_sweep", lambda: k_sweep(args, seed=rank))
     if not args.no_general:
@@ -728,6 +731,121 @@ def drift_report(d, a32, k, with_oracle):
     out["how"] = ("sampled rows (14 fixed, plus the updated row for row updates) of all 9 views "
                   "at the checked updates vs the FP64 oracle's rows computed from the plain "
                   "definition on the updated A; times are CUDA-event intervals per update")
+    return out
+
+
+def ols_drift_streams(seed=0, m=65536, n=4096, p=16, ks=(1, 4, 16), count=100, period=50,
+                      checks=(1, 49, 50, 99, 100), nrows=16):
+    """Residual correction of OLS, measured: per k, 100 row-block updates of
+    the OLS workload (m = 65536, n = 4096, p = 16, FP32) through a program
+    without correction and through one created with correction="newton" and
+    correction_period = ``period`` (a Newton-Schulz step W <- W + W (I - Z W)
+    from the maintained Z = X^T X after every ``period``-th update).  At the
+    checked updates ``nrows`` sampled rows of W and all of beta are read back;
+    the CPU-baseline leg compares them with the FP64 oracle
+    (ols_drift_oracle_errors).  Also times an update of each program and a
+    correction alone."""
+    import numpy as np
+    import torch
+    import linview_inputs as li
+    from paper_1403_6968_gb300 import Program
+
+    x, y, _ = li.ols_inputs(m, n, p, seed=seed, dtype=np.float32)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    g = np.random.default_rng(97)
+    rows_s = sorted(set(int(i) for i in g.choice(n, nrows - 2, replace=False)) | {0, n - 1})
+    out = {}
+    for k in ks:
+        ups = li.ols_row_replacements(m, n, k, count, seed=seed + 100 + k, dtype=np.float32,
+                                      cols_seed=seed)
+        dev = [(r_, torch.from_numpy(nw).cuda()) for r_, nw in ups]
+        runs = {}
+        for variant in ("no_correction", "newton"):
+            kw = {"correction": "newton", "correction_period": period} if variant == "newton" else {}
+            prog = Program("ols", [xd, yd], k=k, **kw)
+            prog.sync()
+            stream = torch.cuda.current_stream()
+            # an event pair around every update (the checks' host reads fall
+            # outside every interval)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(count + 1)]
+            at = {}
+            for t in range(1, count + 1):
+                ev[t][0].record(stream)
+                prog.apply_row_block(*dev[t - 1])
+                ev[t][1].record(stream)
+                if t in checks:
+                    prog.sync()
+                    at[t] = {"W_rows": np.stack([prog.read_view_rows(0, i, 1)[0] for i in rows_s]),
+                             "beta": prog.read_view_host(1)}
+            prog.sync()
+            corrects = variant == "newton"
+            plain = [ev[t][0].elapsed_time(ev[t][1]) for t in range(1, count + 1)
+                     if not (corrects and t % period == 0)]
+            r = {"at": at, "ms_update": float(np.median(plain))}
+            if corrects:
+                # the updates that end in a correction: the update, Z brought up to
+                # date with the history since the last correction, the step
+                r["ms_correcting_update"] = float(np.median(
+                    [ev[t][0].elapsed_time(ev[t][1]) for t in range(period, count + 1, period)]))
+                r["ms_correction_alone"] = _event_ms(lambda j: prog.correct(), 2)
+                # (the timed corrections changed W: nothing is read after them)
+            runs[variant] = r
+            prog.close()
+        out[k] = {"ups": ups, "runs": runs}
+    return {"m": m, "n": n, "p": p, "updates": count, "correction_period": period,
+            "checks": list(checks), "rows": rows_s, "x": x, "y": y, "ks": out}
+
+
+def ols_drift_oracle_errors(d):
+    """Part of the CPU-baseline leg: the FP64 oracle (IncrementalOLS: X, Z =
+    X^T X and X^T Y carried exactly under the same replacements) at every
+    checked update, W = inv(Z) and beta = W X^T Y from the definition; the
+    relative Frobenius error of the program's sampled W rows and beta."""
+    import copy
+    import numpy as np
+    from oracle import ols as oo
+    from oracle.metrics import rel_frob
+
+    base = oo.IncrementalOLS(d["x"], d["y"])
+    rows = d["rows"]
+    errs = {}
+    for k, kd in d["ks"].items():
+        ref = copy.deepcopy(base)
+        e = {v: {} for v in kd["runs"]}
+        for t, (r_, nw) in enumerate(kd["ups"], start=1):
+            ref.replace_rows(r_, nw.astype(np.float64))
+            if t in d["checks"]:
+                w = np.linalg.inv(ref.z)
+                beta = w @ ref.xty
+                for v, run in kd["runs"].items():
+                    got = run["at"][t]
+                    e[v][t] = {"W": rel_frob(got["W_rows"], w[rows]),
+                               "beta": rel_frob(got["beta"], beta)}
+        errs[k] = e
+    return errs
+
+
+def ols_drift_report(d, with_oracle):
+    out = {"m": d["m"], "n": d["n"], "p": d["p"], "updates": d["updates"],
+           "correction_period": d["correction_period"], "checks": d["checks"], "k": {}}
+    errs = ols_drift_oracle_errors(d) if with_oracle else None
+    for k, kd in d["ks"].items():
+        rep = {}
+        for v, run in kd["runs"].items():
+            r = {k2: v2 for k2, v2 in run.items() if k2.startswith("ms_")}
+            if errs is not None:
+                r["oracle_rel_err_at"] = {str(t): errs[k][v][t] for t in d["checks"]}
+            rep[v] = r
+        out["k"][str(k)] = rep
+    out["how"] = (f"{len(d['rows'])} sampled rows of W and all of beta after the checked "
+                  "updates vs the FP64 oracle (Z = X^T X carried exactly, W = inv(Z)); newton: "
+                  "correction=\"newton\" (Z = X^T X kept as double-float pairs, "
+                  "W <- W + W (I - Z W) and beta <- beta + W (X^T Y - Z beta) after every "
+                  "correction_period-th update); times: median CUDA-event interval of an "
+                  "update without a correction, of an update that ends in one (Z brought up "
+                  "to date with the period's replaced rows, then the step), and of a "
+                  "correction alone (no rows pending)")
     return out
 
 
@@ -1288,7 +1406,8 @@ def run_only(args):
            "iteration_p_sweep_n30000": lambda: iteration_p_sweep(args, steps=3, n=30000),
            "gd_regression_n30000": lambda: gd_regression_device(),
            "drift": lambda: drift_report(drift_streams(args), _drift_a(args), args.k,
-                                         not args.no_cpu_baseline)}
+                                         not args.no_cpu_baseline),
+           "ols_drift": lambda: ols_drift_report(ols_drift_streams(), not args.no_cpu_baseline)}
     print(json.dumps({"section": args.only, args.only: fns[args.only]()}), flush=True)
     return 0
 

@@ -95,8 +95,9 @@ typedef struct {
                                 exponential model, a multiple of s >= 2s in the skip
                                 model); OLS: largest row block */
   int32_t r_max;             /* largest rank accepted by linview_apply_delta (>= 1) */
-  int32_t correction_period; /* >0: re-evaluate every this many updates (residual
-                                correction of accumulated rounding); 0 = never */
+  int32_t correction_period; /* >0: correct every this many updates (residual
+                                correction of accumulated rounding, see
+                                desc.correction); 0 = never */
   int32_t reeval_mode;       /* linview_reeval_mode used by linview_reeval and by correction */
   int32_t model;             /* POWER/POWER_SUM: linview_model; ITERATION:
                                 LINVIEW_MODEL_LINEAR (views T_1..T_k), LINVIEW_MODEL_EXP
@@ -126,7 +127,24 @@ typedef struct {
   void* (*alloc)(size_t bytes, void* stream, void* alloc_ctx);
   void (*free)(void* ptr, size_t bytes, void* stream, void* alloc_ctx);
   void* alloc_ctx;
+  int32_t correction;        /* linview_correction: what a residual correction does (every
+                                correction_period updates, or on linview_correct) */
 } linview_program_desc;
+
+/* Residual correction (desc.correction).  LINVIEW_CORRECT_REEVAL: re-evaluate
+ * every view (linview_reeval), any program.  LINVIEW_CORRECT_NEWTON: OLS
+ * programs in FP32 only.  The program also keeps Z = X^T X as double-float
+ * pairs (two n x n FP32 arrays, initialised from the FP64 X^T X of every
+ * re-evaluation and refreshed by the rank-2k update Z += X'_R^T X'_R -
+ * X_R^T X_R of every row block, on the side stream next to the Woodbury
+ * passes); a correction is then one Newton-Schulz step for the inverse of Z,
+ * W <- W + W (I - Z W), with the residual I - Z W in double-float and W (I - Z W)
+ * on the split-TF32 GEMM, followed by beta = W X^T Y.  The step squares the
+ * error of W in the residual sense (W - Z^-1 -> -(W - Z^-1) Z (W - Z^-1)), so
+ * a W that has drifted by rounding returns to FP32 rounding of Z^-1 without
+ * the re-evaluation's FP64 X^T X over all m rows.  Other kinds or FP64 OLS
+ * programs with LINVIEW_CORRECT_NEWTON fail creation with LINVIEW_EUNSUPPORTED. */
+typedef enum { LINVIEW_CORRECT_REEVAL = 0, LINVIEW_CORRECT_NEWTON = 1 } linview_correction;
 
 /* Evaluation strategy of an iteration program's updates (Section 4.3). */
 typedef enum {
@@ -252,6 +270,13 @@ linview_status linview_view_device_ptr(const linview_program* prog, int view_id,
 /* Re-evaluate every view from the current inputs (Section 4.2.2,
  * "Re-evaluation"), with the program's reeval_mode arithmetic. */
 linview_status linview_reeval(linview_program* prog, void* stream);
+
+/* Run the program's residual correction now (desc.correction): linview_reeval,
+ * or for an OLS program with LINVIEW_CORRECT_NEWTON one Newton-Schulz step on
+ * W and beta = W X^T Y.  Enqueued on ``stream``; LINVIEW_ENOMEM if its
+ * temporaries (two n x n FP32 arrays and the GEMM's split operands) cannot be
+ * allocated. */
+linview_status linview_correct(linview_program* prog, void* stream);
 linview_status linview_set_reeval_mode(linview_program* prog, int reeval_mode);
 
 /* Synchronise ``stream`` and return (and clear) the latched device status. */

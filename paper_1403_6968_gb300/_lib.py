@@ -24,6 +24,8 @@ REEVAL_DEFAULT, REEVAL_FP32, REEVAL_TF32, REEVAL_BF16X9, REEVAL_FP64, REEVAL_TC3
 # linview_model
 MODEL_EXP, MODEL_LINEAR, MODEL_SKIP = 0, 1, 2
 STRATEGY_FACTORED, STRATEGY_HYBRID = 0, 1
+# linview_correction
+CORRECT_REEVAL, CORRECT_NEWTON = 0, 1
 
 
 class ProgramDesc(C.Structure):
@@ -43,6 +45,7 @@ class ProgramDesc(C.Structure):
         ("alloc", C.c_void_p),
         ("free", C.c_void_p),
         ("alloc_ctx", C.c_void_p),
+        ("correction", C.c_int32),
     ]
 
 
@@ -107,6 +110,7 @@ _SIGS = [
     ("linview_read_view_rows", _I, [_P, _I, _I64, _I64, _P, _I64, _I, _P]),
     ("linview_view_device_ptr", _I, [_P, _I, C.POINTER(_P), C.POINTER(_I64)]),
     ("linview_reeval", _I, [_P, _P]),
+    ("linview_correct", _I, [_P, _P]),
     ("linview_set_reeval_mode", _I, [_P, _I]),
     ("linview_sync", _I, [_P, _P]),
     ("linview_check_bounded_wait", _I, [_I64, _P, C.POINTER(_I64)]),

@@ -174,6 +174,13 @@ struct linview_program {
   int64_t* rows_d = nullptr;
   double* Minv = nullptr;
   void* Cdf = nullptr;  // OLS FP32: the Woodbury core as double-float pairs
+  float* Zh = nullptr;  // OLS with Newton-Schulz correction: Z = X^T X as pairs (Zh + Zl)
+  float* Zl = nullptr;
+  int64_t ldz = 0;
+  float* XtYl = nullptr;  // ... and the low halves of X^T Y (layout of the X^T Y view)
+  float* Hp = nullptr;    // ... the replaced rows since Z was last brought up to date:
+  float* Hm = nullptr;    //     new rows (Hp) and old rows (Hm), columns of stride fs
+  int hcap = 0, hcnt = 0;
   // OLS re-evaluation scratch (FP64)
   double* Z64 = nullptr;
   double* X64 = nullptr;
@@ -1898,6 +1905,9 @@ static linview_status iter_sk_propagate_b(linview_program* p, int rb, cudaStream
   } while (0)
 
 enum { kOlsW = 0, kOlsBeta = 1, kOlsXtY = 2, kOlsX = 3 };
+// replaced rows held per side before they are folded into Z (Newton-Schulz
+// correction); a row block has at most 32 rows
+constexpr int kOlsHistory = 512;
 
 // Re-evaluation: Z = X^T X and X^T Y accumulated in FP64 over row chunks
 // (DSYRK / DGEMM), W = Z^{-1} by Cholesky (potrf + potri), beta = W X^T Y in
@@ -1935,6 +1945,10 @@ static linview_status ols_reeval_t(linview_program* p, cudaStream_t s) {
                         p->Y64, (int)pp, p->X64, (int)n, r0 ? &one : &zero, p->XtY64, (int)pp));
     p->all_launches += 4;
   }
+  if (p->Zh) {  // Z = X^T X as pairs, before the factorisation overwrites it
+    LV_CUDA(launch_z_from_lower(p->Z64, n, (int)n, p->Zh, p->Zl, p->ldz, s));
+    p->hcnt = 0;  // the history is in this Z already
+  }
   if (!p->solver_work) {
     int l1 = 0, l2 = 0;
     LV_SOLVER(cusolverDnDpotrf_bufferSize(p->solver, CUBLAS_FILL_MODE_LOWER, (int)n, p->Z64,
@@ -1962,6 +1976,7 @@ static linview_status ols_reeval_t(linview_program* p, cudaStream_t s) {
                                 static_cast<T*>(p->XtYc), p->fs, s));
   LV_CUDA(launch_from_double<T>(p->B64, pp, static_cast<T*>(beta.ptr), beta.ld, (int)n, (int)pp,
                                 static_cast<T*>(nullptr), 0, s));
+  if (p->XtYl) LV_CUDA(launch_low_half(p->XtY64, pp, p->XtYl, xty.ld, (int)n, (int)pp, s));
   p->all_launches += 6;
   int info[2] = {0, 0};
   LV_CUDA(cudaMemcpyAsync(info, p->solver_info, sizeof(info), cudaMemcpyDeviceToHost, s));
@@ -2005,6 +2020,20 @@ static linview_status ols_create(linview_program* p, const void* const* inputs,
   p->rows_d = static_cast<int64_t*>(t);
   LV_TRY(dalloc(p, sizeof(double) * kk * kk, &t, s));  // (FP32: kk x kk float2 pairs)
   p->Minv = static_cast<double*>(t);
+  if (p->d.correction == LINVIEW_CORRECT_NEWTON) {  // Z = X^T X as pairs, zero padding
+    p->ldz = rup(n, 64);
+    LV_TRY(dalloc(p, sizeof(float) * p->ldz * p->ldz, &t, s));
+    p->Zh = static_cast<float*>(t);
+    LV_TRY(dalloc(p, sizeof(float) * p->ldz * p->ldz, &t, s));
+    p->Zl = static_cast<float*>(t);
+    LV_TRY(dalloc(p, sizeof(float) * n * ldp, &t, s));
+    p->XtYl = static_cast<float*>(t);
+    p->hcap = kOlsHistory;
+    LV_TRY(dalloc(p, sizeof(float) * p->fs * p->hcap, &t, s));
+    p->Hp = static_cast<float*>(t);
+    LV_TRY(dalloc(p, sizeof(float) * p->fs * p->hcap, &t, s));
+    p->Hm = static_cast<float*>(t);
+  }
   if (p->elem == 4) LV_TRY(dalloc(p, sizeof(float2) * kk * kk, &p->Cdf, s));
   const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
   p->part_cs = p->fs;
@@ -2061,9 +2090,27 @@ static linview_status ols_replace_t(linview_program* p, int kr, const void* nrow
     LV_CUDA(launch_scatter_rows<T>(static_cast<T*>(p->Xd), p->ldX, p->rows_d, kr, n, U, fs,
                                    side));
     View& xty0 = p->views[kOlsXtY];
+    T* xtyl = nullptr;
+    if constexpr (sizeof(T) == 4) xtyl = p->XtYl;
     LV_CUDA(launch_xty_update<T>(static_cast<T*>(xty0.ptr), xty0.ld, static_cast<T*>(p->XtYc),
-                                 fs, U, n, pp, kr, static_cast<const T*>(p->Yr), side));
+                                 fs, U, n, pp, kr, static_cast<const T*>(p->Yr), side, xtyl));
     p->all_launches += 2;
+    if constexpr (sizeof(T) == 4) {
+      if (p->Zh) {
+        // Z += X'_R^T X'_R - X_R^T X_R, deferred: the rows join the history,
+        // which is folded into Z when full and before a correction
+        if (p->hcnt + kr > p->hcap) {
+          LV_CUDA(launch_z_flush(p->Zh, p->Zl, p->ldz, p->Hp, p->Hm, fs, n, p->hcnt, side));
+          p->all_launches++;
+          p->hcnt = 0;
+        }
+        LV_CUDA(cudaMemcpyAsync(p->Hp + (int64_t)p->hcnt * fs, U, sizeof(float) * fs * kr,
+                                cudaMemcpyDeviceToDevice, side));
+        LV_CUDA(cudaMemcpyAsync(p->Hm + (int64_t)p->hcnt * fs, U + (int64_t)kr * fs,
+                                sizeof(float) * fs * kr, cudaMemcpyDeviceToDevice, side));
+        p->hcnt += kr;
+      }
+    }
   }
   if constexpr (sizeof(T) == 4) {
     // G = W U = W^T U (W is symmetric): column sums of a pass over W, which
@@ -2120,6 +2167,68 @@ static linview_status ols_replace_t(linview_program* p, int kr, const void* nrow
   return LINVIEW_OK;
 }
 
+// Newton-Schulz correction of an FP32 OLS program: R = I - Z W (double-float),
+// W <- W + W R (split-TF32 GEMM; W R is small, so its FP32-level error is far
+// below W's rounding); then one step of iterative refinement of beta against
+// the normal equations, r = X^T Y - Z beta (double-float, X^T Y as pairs),
+// beta <- beta + W r.  (beta = W X^T Y from the corrected W would lose about
+// kappa(Z) u to cancellation in the product.)
+static linview_status ols_newton_correct(linview_program* p, cudaStream_t s) {
+  const int64_t n = p->d.n, pp = p->d.p;
+  View& w = p->views[kOlsW];
+  View& beta = p->views[kOlsBeta];
+  View& xty = p->views[kOlsXtY];
+  const int64_t ldr = rup(n, 64);
+  const size_t rbytes = (size_t)alloc_bytes(n * ldr * (int64_t)sizeof(float));
+  void* blk = nullptr;
+  LV_TRY(talloc(p, 2 * rbytes, &blk, s));
+  float* R = static_cast<float*>(blk);
+  float* Tw = reinterpret_cast<float*>(static_cast<char*>(blk) + rbytes);
+  float* W = static_cast<float*>(w.ptr);
+  linview_status st = LINVIEW_OK;
+  auto dev = [&](cudaError_t e, const char* what) {
+    p->all_launches++;
+    if (e != cudaSuccess && st == LINVIEW_OK)
+      st = fail(LINVIEW_EDEVICE, "%s: %s", what, cudaGetErrorString(e));
+  };
+  {
+    TcScratch sc;
+    st = tc_scratch(p, &sc, n, n > pp ? n : pp, n, s);
+    if (st == LINVIEW_OK) {  // Z up to date
+      dev(launch_z_flush(p->Zh, p->Zl, p->ldz, p->Hp, p->Hm, p->fs, (int)n, p->hcnt, s),
+          "history flush");
+      if (st == LINVIEW_OK) p->hcnt = 0;
+    }
+    if (st == LINVIEW_OK)  // R = I - Z W
+      dev(launch_ns_residual(p->Zh, p->Zl, p->ldz, W, w.ld, (int)n, nullptr, nullptr, 0, R, ldr,
+                             (int)n, s),
+          "Newton-Schulz residual");
+    if (st == LINVIEW_OK)  // Tw = W + W R
+      st = gemm_ab(p, n, n, n, 1.0, rows_of(W, w.ld), cols_of(R, ldr), 1.0, W, w.ld, Tw, ldr, s,
+                   &sc);
+    if (st == LINVIEW_OK &&
+        cudaMemcpy2DAsync(W, w.ld * sizeof(float), Tw, ldr * sizeof(float), n * sizeof(float), n,
+                          cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      st = fail(LINVIEW_EDEVICE, "copy of the corrected W failed");
+    if (st == LINVIEW_OK)  // r = X^T Y - Z beta (n x p, in R)
+      dev(launch_ns_residual(p->Zh, p->Zl, p->ldz, static_cast<const float*>(beta.ptr), beta.ld,
+                             (int)pp, static_cast<const float*>(xty.ptr), p->XtYl, xty.ld, R,
+                             beta.ld, (int)n, s),
+          "normal-equation residual");
+    if (st == LINVIEW_OK)  // beta += W r
+      st = gemm_ab(p, n, pp, n, 1.0, rows_of(W, w.ld), cols_of(R, beta.ld), 1.0, beta.ptr, beta.ld,
+                   beta.ptr, beta.ld, s, &sc);
+  }
+  tfree(p, blk, 2 * rbytes, s);
+  return st;
+}
+
+static linview_status correct_now(linview_program* p, cudaStream_t s) {
+  if (p->d.kind == LINVIEW_OLS && p->d.correction == LINVIEW_CORRECT_NEWTON)
+    return ols_newton_correct(p, s);
+  return linview_reeval(p, s);
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -2139,6 +2248,11 @@ linview_status linview_create_program(const linview_program_desc* desc, const vo
   if (desc->correction_period < 0) return fail(LINVIEW_EINVAL, "correction_period < 0");
   if ((desc->alloc == nullptr) != (desc->free == nullptr))
     return fail(LINVIEW_EINVAL, "alloc and free must both be given or both be NULL");
+  if (desc->correction != LINVIEW_CORRECT_REEVAL && desc->correction != LINVIEW_CORRECT_NEWTON)
+    return fail(LINVIEW_EINVAL, "bad correction %d", desc->correction);
+  if (desc->correction == LINVIEW_CORRECT_NEWTON &&
+      !(desc->kind == LINVIEW_OLS && desc->precision == LINVIEW_F32))
+    return fail(LINVIEW_EUNSUPPORTED, "Newton-Schulz correction is built for FP32 OLS programs");
   if (desc->model != LINVIEW_MODEL_EXP &&
       !(desc->model == LINVIEW_MODEL_LINEAR &&
         (desc->kind == LINVIEW_POWER || desc->kind == LINVIEW_POWER_SUM ||
@@ -2340,6 +2454,12 @@ linview_status linview_reeval(linview_program* p, void* stream) {
   }
 }
 
+linview_status linview_correct(linview_program* p, void* stream) {
+  if (!p) return fail(LINVIEW_EINVAL, "null program");
+  LV_CUDA(cudaSetDevice(p->device));
+  return correct_now(p, static_cast<cudaStream_t>(stream));
+}
+
 linview_status linview_set_reeval_mode(linview_program* p, int mode) {
   if (!p) return fail(LINVIEW_EINVAL, "null program");
   if (mode < LINVIEW_REEVAL_DEFAULT || mode > LINVIEW_REEVAL_TC3)
@@ -2355,7 +2475,7 @@ linview_status linview_set_reeval_mode(linview_program* p, int mode) {
 static linview_status after_update(linview_program* p, cudaStream_t s) {
   p->updates++;
   if (p->d.correction_period > 0 && p->updates % p->d.correction_period == 0)
-    return linview_reeval(p, s);
+    return correct_now(p, s);
   return LINVIEW_OK;
 }
 

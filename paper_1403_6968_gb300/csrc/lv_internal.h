@@ -220,9 +220,25 @@ cudaError_t launch_wu(const double* G, int64_t fs, int n, int kk, const double* 
                       cudaStream_t s);
 cudaError_t launch_wu(const float* G, int64_t fs, int n, int kk, const float2* Minv, float* Wu,
                       cudaStream_t s);
+// Newton-Schulz correction of FP32 OLS programs: Z = X^T X as double-float
+// pairs (Zh, Zl; n x n, row-major ldz, a multiple of 64 with zero padding)
+cudaError_t launch_z_from_lower(const double* L, int64_t ldl, int n, float* Zh, float* Zl,
+                                int64_t ldz, cudaStream_t s);
+// Z += Hp Hp^T - Hm Hm^T (cnt history columns each, column stride fs >= ldz)
+cudaError_t launch_z_flush(float* Zh, float* Zl, int64_t ldz, const float* Hp, const float* Hm,
+                           int64_t fs, int n, int cnt, cudaStream_t s);
+// R = D - Z B (B n x nb; D the identity if Dh is null, else the pairs Dh + Dl;
+// double-float sums, rounded to FP32)
+cudaError_t launch_ns_residual(const float* Zh, const float* Zl, int64_t ldz, const float* B,
+                               int64_t ldb, int nb, const float* Dh, const float* Dl, int64_t ldd,
+                               float* R, int64_t ldr, int n, cudaStream_t s);
+// lo = src - (float)src, rounded to FP32 (src FP64 row-major)
+cudaError_t launch_low_half(const double* src, int64_t lds, float* lo, int64_t ldl, int rows,
+                            int cols, cudaStream_t s);
 template <typename T>
 cudaError_t launch_xty_update(T* xty, int64_t ld, T* xtyc, int64_t fs, const T* U, int n, int p,
-                              int k, const T* Yr, cudaStream_t s);
+                              int k, const T* Yr, cudaStream_t s,
+                              T* xtyl = nullptr);
 template <typename T>
 cudaError_t launch_to_double(const T* src, int64_t lds, double* dst, int64_t ldd, int rows,
                              int cols, cudaStream_t s);

@@ -563,15 +563,18 @@ __global__ void xty_update_kernel(T* xty, int64_t ld, T* xtyc, int64_t fs, const
 // thread takes kRowCols columns c0 .. of one row j, so the factor entries are
 // loaded once per row and the loads of U are coalesced over j.
 constexpr int kRowCols = 4;
-__global__ void xty_update_df_kernel(float* xty, int64_t ld, float* xtyc, int64_t fs,
+__global__ void xty_update_df_kernel(float* xty, float* xtyl, int64_t ld, float* xtyc, int64_t fs,
                                      const float* U, int n, int p, int k, const float* Yr) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int c0 = blockIdx.y * kRowCols;
   if (j >= n) return;
   df2 acc[kRowCols];
 #pragma unroll
-  for (int q = 0; q < kRowCols; ++q)
-    acc[q] = {c0 + q < p ? xty[(int64_t)j * ld + c0 + q] : 0.f, 0.f};
+  for (int q = 0; q < kRowCols; ++q) {
+    const bool ok = c0 + q < p;
+    acc[q] = {ok ? xty[(int64_t)j * ld + c0 + q] : 0.f,
+              ok && xtyl ? xtyl[(int64_t)j * ld + c0 + q] : 0.f};
+  }
   for (int t = 0; t < k; ++t) {
     const float xn = U[(int64_t)t * fs + j], xo = U[(int64_t)(k + t) * fs + j];
 #pragma unroll
@@ -584,9 +587,10 @@ __global__ void xty_update_df_kernel(float* xty, int64_t ld, float* xtyc, int64_
 #pragma unroll
   for (int q = 0; q < kRowCols; ++q)
     if (c0 + q < p) {
-      const float v = __fadd_rn(acc[q].hi, acc[q].lo);
-      xty[(int64_t)j * ld + c0 + q] = v;
-      xtyc[(int64_t)(c0 + q) * fs + j] = v;
+      const df2 v = df_norm(acc[q]);
+      xty[(int64_t)j * ld + c0 + q] = v.hi;
+      xtyc[(int64_t)(c0 + q) * fs + j] = v.hi;
+      if (xtyl) xtyl[(int64_t)j * ld + c0 + q] = v.lo;  // the pair's low half, if kept
     }
 }
 
@@ -650,6 +654,217 @@ __global__ void beta_update_kernel(T* beta, int64_t ld, const T* G, int64_t fs, 
 #pragma unroll
   for (int q = 0; q < kRowCols; ++q)
     if (c0 + q < p) beta[(int64_t)j * ld + c0 + q] += acc[q];
+}
+
+// ---------------------------------------------------------------------------
+// Newton-Schulz residual correction of FP32 OLS programs: Z = X^T X kept as
+// double-float pairs (Zh + Zl, row-major, rows and columns padded to ldz with
+// zeros).
+// ---------------------------------------------------------------------------
+
+// (Zh, Zl)(i, j) = the pair of L(max(i, j), min(i, j)), L the lower triangle of
+// the FP64 X^T X (column-major, ldl) that re-evaluation computes.
+__global__ void z_from_lower_kernel(const double* L, int64_t ldl, int n, float* Zh, float* Zl,
+                                    int64_t ldz) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  const int r = i > j ? i : j, c = i > j ? j : i;
+  const double v = L[r + (int64_t)c * ldl];
+  const float h = __double2float_rn(v);
+  Zh[(int64_t)i * ldz + j] = h;
+  Zl[(int64_t)i * ldz + j] = __double2float_rn(v - (double)h);
+}
+
+// Z += Hp Hp^T - Hm Hm^T for the history of replaced rows (Hp: the new rows
+// X'_R^T, Hm: the old rows X_R^T of every row block since the last flush, cnt
+// columns each, column stride fs, zero past row n): each product of two FP32
+// entries is exact as a pair and is accumulated onto the pair (Zh, Zl)
+// (df_acc), so Z stays the FP64-grade sum of exact products.  Z is symmetric
+// and kept whole: a CTA takes one 64 x 64 tile on or below the diagonal and
+// writes it and its mirror image (a diagonal tile is symmetric by itself:
+// entries (i, j) and (j, i) take the same products in the same order).  A
+// thread holds 4 x 4 entries; the history passes through shared memory 32
+// columns at a time.  ldz is a multiple of 64 (whole tiles lie inside).
+constexpr int kZTile = 64, kZK = 32;
+__global__ void __launch_bounds__(256, 1)
+    z_flush_kernel(float* Zh, float* Zl, int64_t ldz, const float* Hp, const float* Hm,
+                   int64_t fs, int cnt) {
+  __shared__ __align__(16) float Si[kZK][kZTile];
+  __shared__ __align__(16) float Sj[kZK][kZTile];
+  // blockIdx.x -> (bi, bj), bj <= bi, row-wise over the lower triangle
+  int bi = (int)((sqrtf(8.f * blockIdx.x + 1.f) - 1.f) * 0.5f);
+  while ((bi + 1) * (bi + 2) / 2 <= (int)blockIdx.x) ++bi;
+  while (bi * (bi + 1) / 2 > (int)blockIdx.x) --bi;
+  const int bj = (int)blockIdx.x - bi * (bi + 1) / 2;
+  const int i0 = bi * kZTile, j0 = bj * kZTile;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  df2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t o = (int64_t)(i0 + 4 * ty + a) * ldz + j0 + 4 * tx;
+    const float4 h = *reinterpret_cast<const float4*>(Zh + o);
+    const float4 l = *reinterpret_cast<const float4*>(Zl + o);
+    acc[a][0] = {h.x, l.x};
+    acc[a][1] = {h.y, l.y};
+    acc[a][2] = {h.z, l.z};
+    acc[a][3] = {h.w, l.w};
+  }
+  for (int side = 0; side < 2; ++side) {
+    const float* H = side ? Hm : Hp;
+    const float sg = side ? -1.f : 1.f;
+    for (int t0 = 0; t0 < cnt; t0 += kZK) {
+      const int nt = min(kZK, cnt - t0);
+      __syncthreads();  // the previous chunk's readers are done
+      for (int e = threadIdx.x; e < nt * kZTile; e += blockDim.x) {
+        const int t = e / kZTile, r = e % kZTile;
+        Si[t][r] = H[(int64_t)(t0 + t) * fs + i0 + r];
+        Sj[t][r] = H[(int64_t)(t0 + t) * fs + j0 + r];
+      }
+      __syncthreads();
+      for (int t = 0; t < nt; ++t) {
+        const float4 ui = *reinterpret_cast<const float4*>(&Si[t][4 * ty]);
+        const float4 uj = *reinterpret_cast<const float4*>(&Sj[t][4 * tx]);
+        const float av[4] = {sg * ui.x, sg * ui.y, sg * ui.z, sg * ui.w};
+        const float bv[4] = {uj.x, uj.y, uj.z, uj.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) df_acc(acc[a][b], {av[a], 0.f}, bv[b]);
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = df_norm(acc[a][b]);
+  const df2(&v)[4][4] = acc;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t o = (int64_t)(i0 + 4 * ty + a) * ldz + j0 + 4 * tx;
+    *reinterpret_cast<float4*>(Zh + o) = make_float4(v[a][0].hi, v[a][1].hi, v[a][2].hi, v[a][3].hi);
+    *reinterpret_cast<float4*>(Zl + o) = make_float4(v[a][0].lo, v[a][1].lo, v[a][2].lo, v[a][3].lo);
+  }
+  if (bi != bj) {  // the mirror tile (j0.., i0..)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int64_t o = (int64_t)(j0 + 4 * tx + b) * ldz + i0 + 4 * ty;
+      *reinterpret_cast<float4*>(Zh + o) =
+          make_float4(v[0][b].hi, v[1][b].hi, v[2][b].hi, v[3][b].hi);
+      *reinterpret_cast<float4*>(Zl + o) =
+          make_float4(v[0][b].lo, v[1][b].lo, v[2][b].lo, v[3][b].lo);
+    }
+  }
+}
+
+// R = D - Z B for n x n Z (pairs), B n x nb (FP32, row-major ldb) and D the
+// identity (Dh null) or the pairs (Dh + Dl, row-major ldd), rounded to FP32
+// (ldr): every product of a Z pair and a B entry accumulated as a pair
+// (df_acc), so the residual, a difference of nearly equal numbers, keeps ~44
+// bits of the sums.  64 x 64 output tiles, K steps of 16 through shared
+// memory (Z tile stored K-major), a thread 4 x 4 outputs.
+constexpr int kRsTile = 64, kRsK = 16;
+__global__ void __launch_bounds__(256)
+    ns_residual_kernel(const float* Zh, const float* Zl, int64_t ldz, const float* B, int64_t ldb,
+                       int nb, const float* Dh, const float* Dl, int64_t ldd, float* R,
+                       int64_t ldr, int n) {
+  __shared__ __align__(16) float Ah[kRsK][kRsTile + 4];
+  __shared__ __align__(16) float Al[kRsK][kRsTile + 4];
+  __shared__ __align__(16) float Bs[kRsK][kRsTile + 4];
+  const int i0 = blockIdx.y * kRsTile, j0 = blockIdx.x * kRsTile;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  df2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = {0.f, 0.f};
+  for (int k0 = 0; k0 < n; k0 += kRsK) {
+    for (int e = threadIdx.x; e < kRsTile * kRsK; e += blockDim.x) {
+      const int r = e / kRsK, c = e % kRsK;  // Z(i0 + r, k0 + c)
+      const bool ok = i0 + r < n && k0 + c < n;
+      const int64_t o = (int64_t)(i0 + r) * ldz + k0 + c;
+      Ah[c][r] = ok ? Zh[o] : 0.f;
+      Al[c][r] = ok ? Zl[o] : 0.f;
+      const int rb = e / kRsTile, cb = e % kRsTile;  // B(k0 + rb, j0 + cb)
+      Bs[rb][cb] = (k0 + rb < n && j0 + cb < nb) ? B[(int64_t)(k0 + rb) * ldb + j0 + cb] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int t = 0; t < kRsK; ++t) {
+      const float4 h = *reinterpret_cast<const float4*>(&Ah[t][4 * ty]);
+      const float4 l = *reinterpret_cast<const float4*>(&Al[t][4 * ty]);
+      const float4 w = *reinterpret_cast<const float4*>(&Bs[t][4 * tx]);
+      const df2 zv[4] = {{h.x, l.x}, {h.y, l.y}, {h.z, l.z}, {h.w, l.w}};
+      const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) df_acc(acc[a][b], zv[a], wv[b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + 4 * ty + a;
+    if (i >= n) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + 4 * tx + b;
+      if (j >= nb) continue;
+      const df2 d = Dh ? df2{Dh[(int64_t)i * ldd + j], Dl[(int64_t)i * ldd + j]}
+                       : df2{i == j ? 1.f : 0.f, 0.f};
+      const df2 v = df_sum(d, {-acc[a][b].hi, -acc[a][b].lo});
+      R[(int64_t)i * ldr + j] = __fadd_rn(v.hi, v.lo);
+    }
+  }
+}
+
+// lo(i, j) = src(i, j) - (double)(float)src(i, j), rounded to FP32 (src
+// row-major FP64, lds): the low halves of a matrix whose FP32 rounding is
+// stored elsewhere.
+__global__ void low_half_kernel(const double* src, int64_t lds, float* lo, int64_t ldl, int rows,
+                                int cols) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)rows * cols) return;
+  const int i = (int)(idx / cols), j = (int)(idx % cols);
+  const double v = src[(int64_t)i * lds + j];
+  lo[(int64_t)i * ldl + j] = __double2float_rn(v - (double)__double2float_rn(v));
+}
+
+cudaError_t launch_low_half(const double* src, int64_t lds, float* lo, int64_t ldl, int rows,
+                            int cols, cudaStream_t s) {
+  const int64_t tot = (int64_t)rows * cols;
+  if (tot == 0) return cudaSuccess;
+  low_half_kernel<<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(src, lds, lo,
+                                                                                 ldl, rows, cols);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_z_from_lower(const double* L, int64_t ldl, int n, float* Zh, float* Zl,
+                                int64_t ldz, cudaStream_t s) {
+  const int64_t tot = (int64_t)n * n;
+  z_from_lower_kernel<<<(unsigned)((tot + kThreads - 1) / kThreads), kThreads, 0, s>>>(L, ldl, n,
+                                                                                     Zh, Zl, ldz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_z_flush(float* Zh, float* Zl, int64_t ldz, const float* Hp, const float* Hm,
+                           int64_t fs, int n, int cnt, cudaStream_t s) {
+  if (cnt == 0) return cudaSuccess;
+  if (cnt < 0 || ldz % kZTile || fs < ldz) return cudaErrorInvalidValue;
+  const int64_t g = (n + kZTile - 1) / kZTile;
+  z_flush_kernel<<<(unsigned)(g * (g + 1) / 2), 256, 0, s>>>(Zh, Zl, ldz, Hp, Hm, fs, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ns_residual(const float* Zh, const float* Zl, int64_t ldz, const float* B,
+                               int64_t ldb, int nb, const float* Dh, const float* Dl, int64_t ldd,
+                               float* R, int64_t ldr, int n, cudaStream_t s) {
+  if (nb < 1 || (Dh == nullptr) != (Dl == nullptr)) return cudaErrorInvalidValue;
+  const unsigned gy = (unsigned)((n + kRsTile - 1) / kRsTile);
+  const unsigned gx = (unsigned)((nb + kRsTile - 1) / kRsTile);
+  ns_residual_kernel<<<dim3(gx, gy), 256, 0, s>>>(Zh, Zl, ldz, B, ldb, nb, Dh, Dl, ldd, R, ldr, n);
+  return cudaGetLastError();
 }
 
 // dst (double, row-major rows x cols, ldd) = (double) src (T, lds)
@@ -762,10 +977,10 @@ cudaError_t launch_beta_update(T* beta, int64_t ld, const T* G, const T* Wu, con
 
 template <typename T>
 cudaError_t launch_xty_update(T* xty, int64_t ld, T* xtyc, int64_t fs, const T* U, int n, int p,
-                              int k, const T* Yr, cudaStream_t s) {
+                              int k, const T* Yr, cudaStream_t s, T* xtyl) {
   if constexpr (sizeof(T) == 4)
     xty_update_df_kernel<<<dim3(blocks_for(n), (p + kRowCols - 1) / kRowCols), kThreads, 0, s>>>(
-        xty, ld, xtyc, fs, U, n, p, k, Yr);
+        xty, xtyl, ld, xtyc, fs, U, n, p, k, Yr);
   else
     xty_update_kernel<T><<<blocks_for((int64_t)n * p), kThreads, 0, s>>>(xty, ld, xtyc, fs, U, n,
                                                                          p, k, Yr);
@@ -805,7 +1020,7 @@ cudaError_t launch_from_double(const double* src, int64_t lds, T* dst, int64_t l
   template cudaError_t launch_beta_update<T>(T*, int64_t, const T*, const T*, const T*, int64_t,  \
                                              int, int, int, const T*, T*, cudaStream_t);         \
   template cudaError_t launch_xty_update<T>(T*, int64_t, T*, int64_t, const T*, int, int, int,    \
-                                            const T*, cudaStream_t);                             \
+                                            const T*, cudaStream_t, T*);                         \
   template cudaError_t launch_to_double<T>(const T*, int64_t, double*, int64_t, int, int,         \
                                            cudaStream_t);                                        \
   template cudaError_t launch_sym_lower_to_full<T>(const double*, int64_t, int, T*, int64_t,      \

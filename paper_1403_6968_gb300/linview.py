@@ -17,6 +17,7 @@ from ._lib import LinviewError  # noqa: F401
 KINDS = {"power": L.POWER, "power_sum": L.POWER_SUM, "iteration": L.ITERATION, "ols": L.OLS}
 MODELS = {"exp": L.MODEL_EXP, "linear": L.MODEL_LINEAR, "skip": L.MODEL_SKIP}
 STRATEGIES = {"factored": L.STRATEGY_FACTORED, "hybrid": L.STRATEGY_HYBRID}
+CORRECTIONS = {"reeval": L.CORRECT_REEVAL, "newton": L.CORRECT_NEWTON}
 REEVAL = {"default": L.REEVAL_DEFAULT, "fp32": L.REEVAL_FP32, "tf32": L.REEVAL_TF32,
           "bf16x9": L.REEVAL_BF16X9, "fp64": L.REEVAL_FP64, "tc3": L.REEVAL_TC3}
 
@@ -129,7 +130,7 @@ class Program:
 
     def __init__(self, kind, inputs, k, r_max=1, precision="f32", p=0, m=0,
                  correction_period=0, reeval_mode="default", model=None, skip=0,
-                 strategy="factored", stream=None, allocator="torch"):
+                 strategy="factored", stream=None, allocator="torch", correction="reeval"):
         self.lib = L.load()
         self.precision = L.F64 if precision in ("f64", "fp64", L.F64) else L.F32
         self.np_dtype = _dtype_of(self.precision)
@@ -149,6 +150,7 @@ class Program:
         d.model = MODELS[model] if isinstance(model, str) else int(model)
         d.skip = int(skip)
         d.strategy = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        d.correction = CORRECTIONS[correction] if isinstance(correction, str) else int(correction)
         if allocator == "torch":
             torch = _torch()
             fa, ff = _torch_allocator()
@@ -234,6 +236,12 @@ class Program:
     # -- strategies and status --------------------------------------------
     def reeval(self, stream=None):
         L.call("linview_reeval", self.h, _stream_ptr(stream))
+
+    def correct(self, stream=None):
+        """The program's residual correction now (``correction``): re-evaluation,
+        or for an FP32 OLS program created with correction="newton" one
+        Newton-Schulz step W <- W + W (I - Z W) from the maintained Z = X^T X."""
+        L.call("linview_correct", self.h, _stream_ptr(stream))
 
     def set_reeval_mode(self, mode):
         L.call("linview_set_reeval_mode", self.h, REEVAL[mode] if isinstance(mode, str) else mode)

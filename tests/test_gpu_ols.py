@@ -147,3 +147,73 @@ def test_full_size_precision_form(k):
         w = prog.read_view_rows(0, 0, n)[rows_s]
         assert rel_frob(w, ref.w[rows_s]) <= 1e-4
         assert rel_frob(prog.read_view_host(1), ref.beta) <= 1e-4
+
+
+@pytest.mark.parametrize("k,count", [(8, 12), (32, 20)])
+def test_newton_correction_step(k, count):
+    """correction="newton" (FP32 OLS): the program keeps Z = X^T X as
+    double-float pairs through the row-block updates, and correct() applies one
+    Newton-Schulz step W <- W + W (I - Z W), then refines beta by
+    beta + W (X^T Y - Z beta).  The corrected W equals that step taken in FP64
+    from the program's own W before the correction and the oracle's exact Z (to
+    FP32 rounding: 2e-7); W and beta are no farther from the exact solution
+    than before.  k = 32, 20 updates: the 640 replaced rows overflow the
+    program's 512-row history once, so Z is also brought up to date in the
+    middle of the stream."""
+    m, n, p = 3000, 256, 4
+    x, y, _ = li.ols_inputs(m, n, p, seed=21, dtype=np.float32)
+    prog = _prog("ols", [_dev(x), _dev(y)], k=k, correction="newton")
+    ref = oo.IncrementalOLS(x.astype(np.float64), y.astype(np.float64))
+    for rows, new in li.ols_row_replacements(m, n, k, count, seed=22, dtype=np.float32,
+                                             cols_seed=21):
+        prog.apply_row_block(rows, _dev(new))
+        ref.replace_rows(rows, new.astype(np.float64))
+    prog.sync()
+    w0 = prog.read_view_host(0).astype(np.float64)
+    b0 = prog.read_view_host(1).astype(np.float64)
+    z = ref.x.T @ ref.x
+    fresh = oo.reeval(ref.x, ref.y)
+    step = w0 + w0 @ (np.eye(n) - z @ w0)
+    prog.correct()
+    prog.sync()
+    w1 = prog.read_view_host(0).astype(np.float64)
+    b1 = prog.read_view_host(1).astype(np.float64)
+    assert rel_frob(w1, step) <= 2e-7
+    assert rel_frob(w1, fresh["W"]) <= 1.05 * rel_frob(w0, fresh["W"]) + 1e-7
+    assert rel_frob(b1, fresh["beta"]) <= 1.05 * rel_frob(b0, fresh["beta"]) + 1e-7
+
+
+def test_newton_correction_period_and_reeval():
+    """Every correction_period-th update runs the step; a re-evaluation resets Z
+    from the FP64 X^T X (a step right after it keeps W at its rounding)."""
+    m, n, p, k = 2000, 200, 3, 4
+    x, y, _ = li.ols_inputs(m, n, p, seed=31, dtype=np.float32)
+    prog = _prog("ols", [_dev(x), _dev(y)], k=k, correction="newton", correction_period=3)
+    ref = oo.IncrementalOLS(x.astype(np.float64), y.astype(np.float64))
+    for rows, new in li.ols_row_replacements(m, n, k, 7, seed=32, dtype=np.float32,
+                                             cols_seed=31):
+        prog.apply_row_block(rows, _dev(new))
+        ref.replace_rows(rows, new.astype(np.float64))
+        prog.sync()
+        fresh = oo.reeval(ref.x, ref.y)
+        assert rel_frob(prog.read_view_host(0), fresh["W"]) <= 1e-4
+        assert rel_frob(prog.read_view_host(1), fresh["beta"]) <= 1e-4
+    prog.reeval()
+    prog.sync()
+    w0 = prog.read_view_host(0)
+    e0 = rel_frob(w0, fresh["W"])
+    prog.correct()
+    prog.sync()
+    assert rel_frob(prog.read_view_host(0), fresh["W"]) <= 2 * e0 + 1e-7
+
+
+def test_newton_correction_is_fp32_ols_only():
+    from paper_1403_6968_gb300 import LinviewError
+    x, y, _ = li.ols_inputs(300, 20, 2, seed=41)
+    with pytest.raises(LinviewError) as e:
+        _prog("ols", [x, y], k=2, precision="f64", correction="newton")
+    assert e.value.name == "EUNSUPPORTED"
+    a = li.power_matrix(64, seed=1, dtype=np.float32)
+    with pytest.raises(LinviewError) as e:
+        _prog("power", [_dev(a)], k=4, correction="newton")
+    assert e.value.name == "EUNSUPPORTED"
