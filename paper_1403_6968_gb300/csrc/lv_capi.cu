@@ -113,6 +113,9 @@ struct linview_program {
   float* tcB = nullptr;
   CUtensorMap tmA, tmB;
   // a second set for the sums updates on the side stream (wide sums only)
+  float* tpF = nullptr;  // split factor of the tensor-core products pass (128 x fs floats)
+  int xslots = 0, yslots = 0;  // partial sets Xpart / Ypart hold
+  int pc_x = 0, pc_y = 0;      // partial sets the last products pass wrote
   float* tcA2 = nullptr;
   float* tcB2 = nullptr;
   CUtensorMap tmA2, tmB2;
@@ -461,12 +464,51 @@ static linview_status run_update(linview_program* p, const View& v, const T* Uu,
 template <typename T>
 static linview_status run_products_update(linview_program* p, const View& v, int r, const T* Xf,
                                           const T* Yf, const T* Uu, const T* Wu, cudaStream_t s,
-                                          double* Cpart = nullptr) {
+                                          double* Cpart = nullptr, bool allow_tc = false) {
   const bool want_y = (Yf != nullptr);
+  const PassGeom g = fused_geom(sizeof(T), (int)v.rows, p->sms);
+  p->pc_x = g.gC;
+  p->pc_y = g.gR;
   if (r <= kMaxFusedR) {
     const int mode = kModeX | (want_y ? 2 : 0) | (Uu ? 4 : 0);  // XYU, XY, XU or X
     return run_fused<T>(p, v, mode, r, Xf, Yf, Uu, Wu, p->Xpart, p->Ypart, s,
                         mode == kModeXYU ? Cpart : nullptr);
+  }
+  if constexpr (sizeof(T) == 4) {
+    // blocks wider than the CUDA-core products pass sustains: X = P U and
+    // Y = P^T V on the tensor cores, one read of P each, K split in ``parts``
+    const int n = (int)v.rows;
+    int parts = tp_parts(n, p->sms);
+    if (parts > p->xslots) parts = p->xslots;
+    if (want_y && parts > p->yslots) parts = p->yslots;
+    if (allow_tc && p->tpF && v.square && r > kMaxProductR && parts >= 1 &&
+        (v.ld * 4) % 16 == 0 && p->fs % 64 == 0) {
+      const double nn = (double)n * (double)n * sizeof(float);
+      for (int c0 = 0; c0 < r; c0 += kMaxTcR) {
+        const int w = (r - c0 < kMaxTcR) ? (r - c0) : kMaxTcR;
+        {
+          ProfScope ps(p, s, nn, 1);
+          LV_CUDA(launch_tc_products(false, static_cast<const float*>(v.ptr), v.ld,
+                                     reinterpret_cast<const float*>(Xf) + (int64_t)c0 * p->fs,
+                                     p->fs, p->tpF, n, w,
+                                     static_cast<float*>(p->Xpart) + (int64_t)c0 * p->part_cs,
+                                     p->xp_s, p->part_cs, parts, p->sms, p->status, s));
+          p->all_launches++;  // the split kernel
+        }
+        if (want_y) {
+          ProfScope ps(p, s, nn, 1);
+          LV_CUDA(launch_tc_products(true, static_cast<const float*>(v.ptr), v.ld,
+                                     reinterpret_cast<const float*>(Yf) + (int64_t)c0 * p->fs,
+                                     p->fs, p->tpF, n, w,
+                                     static_cast<float*>(p->Ypart) + (int64_t)c0 * p->part_cs,
+                                     p->yp_q, p->part_cs, parts, p->sms, p->status, s));
+          p->all_launches++;
+        }
+      }
+      p->pc_x = p->pc_y = parts;
+      if (Uu) LV_TRY(run_update<T>(p, v, Uu, Wu, r, s));
+      return LINVIEW_OK;
+    }
   }
   constexpr int MW = sizeof(T) == 4 ? kMaxProductR : kMaxFusedR;  // products-only width
   for (int c0 = 0; c0 < r; c0 += MW) {
@@ -981,6 +1023,12 @@ static int powers_num_views(const linview_program_desc& d) {
 static bool powers_uses_tc(const linview_program_desc& d) {
   return d.precision == LINVIEW_F32 && (int64_t)d.r_max * d.k > kMaxProductR;
 }
+// exponential-model products of width r_h = r h, h <= k / 2, wider than the
+// CUDA-core products pass: the tensor-core products pass
+static bool powers_uses_tp(const linview_program_desc& d) {
+  return d.precision == LINVIEW_F32 && d.model == LINVIEW_MODEL_EXP &&
+         (int64_t)d.r_max * (d.k / 2) > kMaxProductR;
+}
 
 // Device bytes powers_create allocates (with the buffers every program has),
 // in the same order; linview_estimate_device_bytes reports it.
@@ -996,9 +1044,13 @@ static int64_t powers_device_bytes(const linview_program_desc& d, int sms) {
   b += (powers_wide_sums(d) ? 3 : 2) * alloc_bytes(fs * Rcap * elem);
   const PassGeom g = fused_geom(elem, (int)n, sms);
   const int64_t half = Rcap / 2 > 0 ? Rcap / 2 : 1;
-  b += alloc_bytes((int64_t)g.gC * half * fs * elem) + alloc_bytes((int64_t)g.gR * half * fs * elem);
+  const bool tp = powers_uses_tp(d);
+  const int64_t xs = tp && g.gC < kTpMaxParts ? kTpMaxParts : g.gC;
+  const int64_t ys = tp && g.gR < kTpMaxParts ? kTpMaxParts : g.gR;
+  b += alloc_bytes(xs * half * fs * elem) + alloc_bytes(ys * half * fs * elem);
   b += alloc_bytes(2 * n * d.r_max * elem);
   if (powers_uses_tc(d)) b += alloc_bytes(tc_split_floats(n) * 4) * (powers_wide_sums(d) ? 2 : 1);
+  if (tp) b += alloc_bytes(128 * fs * 4);
   return b;
 }
 
@@ -1036,8 +1088,18 @@ static linview_status powers_create(linview_program* p, const void* const* input
   p->part_cs = p->fs;
   p->xp_s = (int64_t)half * p->part_cs;
   p->yp_q = (int64_t)half * p->part_cs;
-  LV_TRY(dalloc(p, (size_t)g.gC * p->xp_s * p->elem, &p->Xpart, s));
-  LV_TRY(dalloc(p, (size_t)g.gR * p->yp_q * p->elem, &p->Ypart, s));
+  // levels wider than the CUDA-core products pass go to the tensor cores,
+  // whose K parts need their own partial sets
+  const bool tp = powers_uses_tp(p->d);
+  p->xslots = tp && g.gC < kTpMaxParts ? kTpMaxParts : g.gC;
+  p->yslots = tp && g.gR < kTpMaxParts ? kTpMaxParts : g.gR;
+  LV_TRY(dalloc(p, (size_t)p->xslots * p->xp_s * p->elem, &p->Xpart, s));
+  LV_TRY(dalloc(p, (size_t)p->yslots * p->yp_q * p->elem, &p->Ypart, s));
+  if (tp) {
+    void* t = nullptr;
+    LV_TRY(dalloc(p, sizeof(float) * 128 * p->fs, &t, s));
+    p->tpF = static_cast<float*>(t);
+  }
   // host-side update factors are staged here (allocated now so that an
   // update never allocates)
   LV_TRY(ensure_stage(p, (size_t)2 * n * p->d.r_max * p->elem, s));
@@ -1138,16 +1200,16 @@ static linview_status exp_levels(linview_program* p, int r, int nlev, bool sums,
     // (side stream, concurrent with the level pass)
     if (sums && l >= 1) LV_TRY(sums_update<T>(p, sview(p, l), U, Vh, rh, r, s));
     LV_TRY(run_products_update<T>(p, pview(p, l), rh, U, Vh, U, Vh, s,
-                                  fused ? p->Cpart : nullptr));
+                                  fused ? p->Cpart : nullptr, /*allow_tc=*/true));
     AssembleParams a{};
     a.n = n;
     a.r_h = rh;
     a.fs = fs;
     a.Xpart = p->Xpart;
-    a.gC = g.gC;
+    a.gC = p->pc_x;
     a.xp_s = p->xp_s;
     a.Ypart = p->Ypart;
-    a.gR = g.gR;
+    a.gR = p->pc_y;
     a.yp_q = p->yp_q;
     a.part_cs = p->part_cs;
     a.C = fused ? p->Cpart : p->C;
@@ -3006,12 +3068,22 @@ linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp
   tmp.xp_s = r * tmp.part_cs;
   tmp.yp_q = r * tmp.part_cs;
   const bool products = (X != nullptr) || (Y != nullptr);
+  // FP32 blocks wider than 16 columns: the tensor-core products pass (its own
+  // K parts, up to kTpMaxParts partial sets)
+  const bool tp = e == 4 && products && r > kMaxProductR && ldf % 64 == 0;
+  tmp.xslots = tp && g.gC < kTpMaxParts ? kTpMaxParts : g.gC;
+  tmp.yslots = tp && g.gR < kTpMaxParts ? kTpMaxParts : g.gR;
   void* xp = nullptr;
   void* yp = nullptr;
   void* stw = nullptr;
+  void* tpf = nullptr;
   if (products) {
-    LV_CUDA(cudaMallocAsync(&xp, (size_t)g.gC * tmp.xp_s * e, s));
-    LV_CUDA(cudaMallocAsync(&yp, (size_t)g.gR * tmp.yp_q * e, s));
+    LV_CUDA(cudaMallocAsync(&xp, (size_t)tmp.xslots * tmp.xp_s * e, s));
+    LV_CUDA(cudaMallocAsync(&yp, (size_t)tmp.yslots * tmp.yp_q * e, s));
+  }
+  if (tp) {
+    LV_CUDA(cudaMallocAsync(&tpf, sizeof(float) * 128 * ldf, s));
+    tmp.tpF = static_cast<float*>(tpf);
   }
   LV_CUDA(cudaMallocAsync(&stw, sizeof(unsigned) * 4, s));
   LV_CUDA(cudaMemsetAsync(stw, 0, sizeof(unsigned) * 4, s));
@@ -3036,15 +3108,15 @@ linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp
     const float* vv = static_cast<const float*>(V);
     if (products)
       st = run_products_update<float>(&tmp, v, (int)r, u, vv, do_update ? u : nullptr,
-                                      do_update ? vv : nullptr, s);
+                                      do_update ? vv : nullptr, s, nullptr, /*allow_tc=*/tp);
     else if (do_update)
       st = run_update<float>(&tmp, v, u, vv, (int)r, s);
     if (st == LINVIEW_OK && X)
-      st = launch_sum_partials<float>(static_cast<float*>(xp), g.gC, tmp.xp_s, tmp.part_cs,
+      st = launch_sum_partials<float>(static_cast<float*>(xp), tmp.pc_x, tmp.xp_s, tmp.part_cs,
                                       (int)n, (int)r, static_cast<float*>(X), ldf, s) == cudaSuccess
                ? LINVIEW_OK : fail(LINVIEW_EDEVICE, "sum_partials launch failed");
     if (st == LINVIEW_OK && Y)
-      st = launch_sum_partials<float>(static_cast<float*>(yp), g.gR, tmp.yp_q, tmp.part_cs,
+      st = launch_sum_partials<float>(static_cast<float*>(yp), tmp.pc_y, tmp.yp_q, tmp.part_cs,
                                       (int)n, (int)r, static_cast<float*>(Y), ldf, s) == cudaSuccess
                ? LINVIEW_OK : fail(LINVIEW_EDEVICE, "sum_partials launch failed");
   } else {
@@ -3069,6 +3141,7 @@ linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp
   if (xp) cudaFreeAsync(xp, s);
   if (yp) cudaFreeAsync(yp, s);
   if (tcs) cudaFreeAsync(tcs, s);
+  if (tpf) cudaFreeAsync(tpf, s);
   cudaFreeAsync(stw, s);
   LV_CUDA(cudaStreamSynchronize(s));
   if (st == LINVIEW_OK && (hs & kStatusTimeout)) st = fail(LINVIEW_ETIMEOUT, "bounded wait expired");

@@ -426,6 +426,343 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const float* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core products passes: X = P U (rows of P, TR = false) and Y = P^T V
+// (columns of P, TR = true) for a factor block of up to RP (32 or 64)
+// columns -- App. A's P_h U_h and P_h^T V_h once the block is too wide for
+// the CUDA-core pass (a 16-column products pass is issue bound there).
+//
+// Arithmetic: split TF32 as in the update pass, with both operands split.
+// The factor is pre-split as [hi | lo] rows (hi rounded to nearest TF32).
+// P is split on the fly in shared memory: the tensor pipe reads a TF32
+// operand from the top 19 bits of each 32-bit word, so the loaded FP32 box
+// itself is hi(P) = P truncated to TF32 (X; the transposing split of Y
+// writes it out explicitly), and lo(P) = P - hi(P) is exact in FP32.  Per K
+// chunk of 32 the products hi*[hi | lo] (one MMA of width 2 RP) and lo*hi go
+// into one TMEM accumulator, and the epilogue warps add each chunk's
+// accumulator into FP32 registers (round to nearest): the tensor pipe
+// truncates its own accumulations, which over K = n would bias the sums.
+//
+// Operands, all K-major with 128-byte swizzle (the layout TMA writes):
+//   X: A = P rows (the loaded 128 x 32 box of P; lo beside it),
+//      B = U^T (RP factor columns x 32 of K);
+//   Y: A = P^T (the loaded 32 x 128 slab of P transposed by the split warps
+//      into 128 x 32 hi and lo tiles), B = V^T.
+// Work items: output tile (128 rows of X or of Y) x K part; a part's sums
+// land in partial ``part`` of the output (Xpart / Ypart layout: partial
+// stride ps, column stride cs), summed by the assembly.  One CTA per SM,
+// contiguous items per CTA.  Warps: 0 TMA producer, 1 TMEM allocation and
+// MMA issue, 2-5 split, 6-9 epilogue.  The pass is bound by shared-memory
+// traffic (the TMA writes, the split, and the tensor pipe reading each A
+// tile three times), not by HBM.  Every mbarrier wait is bounded: an expired
+// wait latches LINVIEW_ETIMEOUT, stops the CTA's loops, drains the copies and
+// MMAs in flight and frees the TMEM.
+constexpr int kTpThreads = 320;
+constexpr int kTpMaxStages = 5;
+
+template <bool TR, int RP>
+struct TpShape {
+  static constexpr uint32_t PBytes = kBM * 128;            // 128 x 32 FP32 (X) / 4 boxes 32 x 32 (Y)
+  static constexpr uint32_t HiBytes = TR ? kBM * 128 : 0;  // Y: transposed hi (X: the loaded box)
+  static constexpr uint32_t LoBytes = kBM * 128;
+  static constexpr uint32_t BBytes = 2 * RP * 128;         // factor chunk: hi rows, then lo rows
+  static constexpr uint32_t StageBytes = PBytes + HiBytes + LoBytes + BBytes;
+  static constexpr int S = (int)((221184u / StageBytes) < (uint32_t)kTpMaxStages
+                                     ? (221184u / StageBytes) : (uint32_t)kTpMaxStages);
+  static constexpr uint32_t OffBar = S * StageBytes;
+  static constexpr uint32_t SmemBytes = OffBar + 512 + 1024;
+  // a chunk accumulator holds hi(A) [hi(B) | lo(B)] in 2 RP columns (with
+  // lo(A) hi(B) added to the first RP); two of them
+  static constexpr uint32_t TmemCols = 4 * RP;
+  static constexpr uint32_t IdescW = (1u << 4) | (2u << 7) | (2u << 10) |
+                                     ((uint32_t)(2 * RP >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+  static constexpr uint32_t IdescN = (1u << 4) | (2u << 7) | (2u << 10) |
+                                     ((uint32_t)(RP >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+};
+static_assert(TpShape<false, 64>::SmemBytes <= 232448 && TpShape<true, 64>::SmemBytes <= 232448,
+              "shared memory per CTA");
+static_assert(TpShape<true, 64>::S >= 3 && TpShape<false, 64>::S >= 4, "pipeline depth");
+
+struct TpBars {
+  uint64_t full[kTpMaxStages], split[kTpMaxStages], empty[kTpMaxStages];
+  uint64_t acc_full[2], acc_empty[2];
+  uint32_t tmem_base;
+  int abort;
+};
+static_assert(sizeof(TpBars) <= 512, "barrier block");
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+__device__ __forceinline__ float tf32_trunc(float x) {
+  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
+// byte offset of 16-byte chunk ``chunk`` of row ``row`` in a tile of 128-byte
+// rows with 128-byte swizzle: the chunk sits at chunk ^ (row % 8)
+__device__ __forceinline__ uint32_t sw128_off(int row, int chunk) {
+  return (uint32_t)(row * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+template <bool TR, int RP>
+__global__ void __launch_bounds__(kTpThreads, 1)
+    tc_products_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmF,
+                       float* out, int64_t ps, int64_t cs, int n, int r_out, int parts,
+                       unsigned* status) {
+  using Sh = TpShape<TR, RP>;
+  constexpr int S = Sh::S;
+  extern __shared__ __align__(1024) unsigned char tp_smem_raw[];
+  const uint32_t raw = smem_u32(tp_smem_raw);
+  unsigned char* base = tp_smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  TpBars* bars = reinterpret_cast<TpBars*>(base + Sh::OffBar);
+  volatile int* abort_flag = &bars->abort;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+
+  const int ot_n = (n + kBM - 1) / kBM;  // output tiles
+  const int nkb = (n + 31) / 32;          // K chunks of 32
+  const long long T = (long long)ot_n * parts;
+  const long long t0 = T * blockIdx.x / gridDim.x;
+  const long long t1 = T * (blockIdx.x + 1) / gridDim.x;
+  auto item = [&](long long t, int& ot, int& part, int& kb0, int& kb1) {
+    ot = (int)(t / parts);
+    part = (int)(t % parts);
+    kb0 = (int)((long long)nkb * part / parts);
+    kb1 = (int)((long long)nkb * (part + 1) / parts);
+  };
+
+  if (tid == 0) {
+    prefetch_tmap(&tmP);
+    prefetch_tmap(&tmF);
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&bars->full[i], 1);
+      mbar_init(&bars->split[i], 4);  // one arrival per split warp
+      mbar_init(&bars->empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bars->acc_full[i], 1);
+      mbar_init(&bars->acc_empty[i], 4);  // one arrival per epilogue warp
+    }
+    bars->abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&bars->tmem_base)),
+                 "r"(Sh::TmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      long long g = 0, issued = 0;
+      for (long long t = t0; t < t1 && !*abort_flag; ++t) {
+        int ot, part, kb0, kb1;
+        item(t, ot, part, kb0, kb1);
+        for (int kb = kb0; kb < kb1 && !*abort_flag; ++kb, ++g) {
+          const int st = (int)(g % S);
+          const long long use = g / S;
+          if (use >= 1 && !tc_wait(&bars->empty[st], (uint32_t)((use - 1) & 1), abort_flag, status))
+            break;
+          unsigned char* sb = base + st * Sh::StageBytes;
+          fence_proxy_async();
+          mbar_arrive_expect_tx(&bars->full[st], Sh::PBytes + Sh::BBytes);
+          if constexpr (!TR) {
+            tma_load_2d(sb, &tmP, kb * 32, ot * kBM, &bars->full[st]);
+          } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              tma_load_2d(sb + b * 4096, &tmP, ot * kBM + 32 * b, kb * 32, &bars->full[st]);
+          }
+          unsigned char* bb = sb + Sh::PBytes + Sh::HiBytes + Sh::LoBytes;
+          tma_load_2d(bb, &tmF, kb * 32, 0, &bars->full[st]);
+          tma_load_2d(bb + RP * 128, &tmF, kb * 32, 64, &bars->full[st]);
+          issued = g + 1;
+        }
+      }
+      if (*abort_flag)  // the loads issued land before the CTA exits (bounded)
+        for (long long j = (issued > S ? issued - S : 0); j < issued; ++j)
+          mbar_wait_bounded(&bars->full[j % S], (uint32_t)((j / S) & 1), nullptr);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      long long g = 0, issued = 0;
+      for (long long t = t0; t < t1 && !*abort_flag; ++t) {
+        int ot, part, kb0, kb1;
+        item(t, ot, part, kb0, kb1);
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
+          const int st = (int)(g % S);
+          const long long use = g / S;
+          const int buf = (int)(g & 1);
+          const long long bu = g >> 1;
+          if (!tc_wait(&bars->split[st], (uint32_t)(use & 1), abort_flag, status)) break;
+          if (bu >= 1 && !tc_wait(&bars->acc_empty[buf], (uint32_t)((bu - 1) & 1), abort_flag, status))
+            break;
+          tc_fence_after();
+          const uint32_t d = tmem + buf * (2 * RP);
+          const uint32_t s0 = smem_u32(base + st * Sh::StageBytes);
+          const uint32_t a_hi = TR ? s0 + Sh::PBytes : s0;
+          const uint32_t a_lo = s0 + Sh::PBytes + Sh::HiBytes;
+          const uint32_t b_hi = a_lo + Sh::LoBytes;  // 2 RP rows: hi(B), then lo(B)
+          // per K step of 8 (32 bytes of each 128-byte row): hi(A) [hi(B) |
+          // lo(B)] over 2 RP columns, then lo(A) hi(B) into the first RP: the
+          // three products of the split in two MMAs, the wider one filling
+          // the tensor pipe better than three of width RP
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            tc_mma(d, sw128_desc(a_hi + kk * 32), sw128_desc(b_hi + kk * 32), Sh::IdescW,
+                   kk != 0 ? 1u : 0u);
+            tc_mma(d, sw128_desc(a_lo + kk * 32), sw128_desc(b_hi + kk * 32), Sh::IdescN, 1u);
+          }
+          tc_commit(&bars->empty[st]);
+          tc_commit(&bars->acc_full[buf]);
+          issued = g + 1;
+        }
+      }
+      if (*abort_flag && issued > 0) {
+        const long long j = issued - 1;  // the MMAs issued finish before the TMEM is freed
+        mbar_wait_bounded(&bars->acc_full[j & 1], (uint32_t)((j >> 1) & 1), nullptr);
+      }
+    }
+  } else if (warp < 6) {
+    // ---------------- split (warps 2..5, 128 threads) ----------------
+    const int st_tid = tid - 64;
+    long long g = 0;
+    bool ok = true;
+    for (long long t = t0; t < t1 && ok; ++t) {
+      int ot, part, kb0, kb1;
+      item(t, ot, part, kb0, kb1);
+      for (int kb = kb0; kb < kb1; ++kb, ++g) {
+        const int st = (int)(g % S);
+        const long long use = g / S;
+        ok = tc_wait(&bars->full[st], (uint32_t)(use & 1), abort_flag, status);
+        if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+        unsigned char* sb = base + st * Sh::StageBytes;
+        if constexpr (!TR) {
+          // the loaded box is hi(P) as the tensor pipe reads it; lo beside it
+          // (same swizzled offsets)
+          const float4* pv = reinterpret_cast<const float4*>(sb);
+          float4* lv = reinterpret_cast<float4*>(sb + Sh::PBytes);
+#pragma unroll
+          for (int q = 0; q < (int)(Sh::PBytes / 16) / 128; ++q) {
+            const int f = st_tid + q * 128;
+            const float4 x = pv[f];
+            lv[f] = make_float4(x.x - tf32_trunc(x.x), x.y - tf32_trunc(x.y),
+                                x.z - tf32_trunc(x.z), x.w - tf32_trunc(x.w));
+          }
+        } else {
+          // slab rows i (32) x columns j (128, 4 boxes of 32) -> hi/lo tiles of
+          // 128 rows j x 32 i; a thread moves 4 x 4 blocks (4 i, 4 j): the 8
+          // threads of a group take distinct (i-block, j-block mod 8) pairs,
+          // which fall in distinct 16-byte chunks on both sides
+          unsigned char* hi = sb + Sh::PBytes;
+          unsigned char* lo = hi + Sh::HiBytes;
+#pragma unroll
+          for (int it = 0; it < 2; ++it) {
+            const int grp = (st_tid >> 3) + 16 * it;  // 0..31
+            const int k8 = st_tid & 7;
+            const int ib = k8;                                       // rows 4 ib .. 4 ib + 3
+            const int jb = 8 * (grp & 3) + ((k8 + (grp >> 2)) & 7);  // columns 4 jb .. + 3
+            const int box = jb >> 3, jc = jb & 7;
+            float x[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              const float4 v = *reinterpret_cast<const float4*>(sb + box * 4096 +
+                                                                sw128_off(4 * ib + a, jc));
+              x[a][0] = v.x; x[a][1] = v.y; x[a][2] = v.z; x[a][3] = v.w;
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              const int j = 4 * jb + b;
+              float4 h, l2;
+              h.x = tf32_rn(x[0][b]); l2.x = x[0][b] - h.x;
+              h.y = tf32_rn(x[1][b]); l2.y = x[1][b] - h.y;
+              h.z = tf32_rn(x[2][b]); l2.z = x[2][b] - h.z;
+              h.w = tf32_rn(x[3][b]); l2.w = x[3][b] - h.w;
+              *reinterpret_cast<float4*>(hi + sw128_off(j, ib)) = h;
+              *reinterpret_cast<float4*>(lo + sw128_off(j, ib)) = l2;
+            }
+          }
+        }
+        fence_proxy_async();  // generic-proxy writes, read next by the tensor cores
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->split[st]);
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 6..9) ----------------
+    const int quarter = warp & 3;  // TMEM lanes 32 quarter .. + 31
+    const int row = quarter * 32 + lane;
+    long long g = 0;
+    bool ok = true;
+    for (long long t = t0; t < t1 && ok; ++t) {
+      int ot, part, kb0, kb1;
+      item(t, ot, part, kb0, kb1);
+      float acc[RP];
+#pragma unroll
+      for (int c = 0; c < RP; ++c) acc[c] = 0.f;
+      for (int kb = kb0; kb < kb1; ++kb, ++g) {
+        const int buf = (int)(g & 1);
+        const long long bu = g >> 1;
+        ok = tc_wait(&bars->acc_full[buf], (uint32_t)(bu & 1), abort_flag, status);
+        if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + buf * (2 * RP);
+#pragma unroll
+        for (int q = 0; q < RP / 16; ++q) {
+          float v[16], w[16];
+          tmem_ld16(ta + q * 16, v);       // hi hi + lo hi
+          tmem_ld16(ta + RP + q * 16, w);  // hi lo
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) acc[q * 16 + e] += w[e] + v[e];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars->acc_empty[buf]);
+      }
+      if (!ok) break;
+      const int orow = ot * kBM + row;
+      if (orow < n) {
+        float* o = out + (int64_t)part * ps + orow;
+#pragma unroll
+        for (int c = 0; c < RP; ++c)
+          if (c < r_out) o[(int64_t)c * cs] = acc[c];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(Sh::TmemCols)
+                 : "memory");
+  }
+}
+
+// Factor split for the products passes: F (128 rows x fs) row c = hi(Fin
+// column c) for c < r, 0 for r <= c < rp; row 64 + c = the low part.  Fin is
+// column-major (column stride fs), n rows.
+__global__ void tp_split_kernel(const float* __restrict__ Fin, int64_t fs, int n, int r, int rp,
+                                float* __restrict__ F) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)rp * n) return;
+  const int c = (int)(idx / n), i = (int)(idx % n);
+  const float x = c < r ? Fin[(int64_t)c * fs + i] : 0.f;
+  const float h = tf32_rn(x);
+  F[(int64_t)c * fs + i] = h;
+  F[(int64_t)(64 + c) * fs + i] = x - h;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
     cudaDriverEntryPointQueryResult q;
@@ -480,6 +817,51 @@ cudaError_t launch_tc_update(const CUtensorMap& tmP, const CUtensorMap& tmA,
   tc_split_kernel<<<(n + 31) / 32, 256, 0, s>>>(U, W, fs, n, r, half, Acat, Bcat);
   if (half == 32) return launch_tc_t<32>(tmP, tmA, tmB, P, ldp, n, num_sms, status, s);
   return launch_tc_t<64>(tmP, tmA, tmB, P, ldp, n, num_sms, status, s);
+}
+
+int tp_parts(int n, int num_sms) {
+  const int ot = (n + kBM - 1) / kBM;
+  int parts = num_sms / ot;
+  if (parts < 1) parts = 1;
+  if (parts > kTpMaxParts) parts = kTpMaxParts;
+  return parts;
+}
+
+template <bool TR, int RP>
+static cudaError_t launch_tp_t(const CUtensorMap& tmP, const CUtensorMap& tmF, float* out,
+                               int64_t ps, int64_t cs, int n, int r_out, int parts, int num_sms,
+                               unsigned* status, cudaStream_t s) {
+  using Sh = TpShape<TR, RP>;
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      tc_products_kernel<TR, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SmemBytes);
+  if (configured != cudaSuccess) return configured;
+  const long long T = (long long)((n + kBM - 1) / kBM) * parts;
+  const int grid = (int)(T < num_sms ? T : num_sms);
+  tc_products_kernel<TR, RP><<<grid, kTpThreads, Sh::SmemBytes, s>>>(tmP, tmF, out, ps, cs, n,
+                                                                     r_out, parts, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_products(bool transpose, const float* P, int64_t ldp, const float* F,
+                               int64_t fs, float* Fsplit, int n, int r, float* out, int64_t ps,
+                               int64_t cs, int parts, int num_sms, unsigned* status,
+                               cudaStream_t s) {
+  if (r < 1 || r > kMaxTcR || parts < 1 || parts > kTpMaxParts || fs % 64 || fs < n)
+    return cudaErrorInvalidValue;
+  const int rp = r <= 32 ? 32 : 64;
+  const int64_t tot = (int64_t)rp * n;
+  tp_split_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(F, fs, n, r, rp, Fsplit);
+  CUtensorMap tmP, tmF;
+  // P: boxes of 32 columns x 128 rows (X) or 32 x 32 (Y); F: 32 columns of
+  // K x rp factor rows (hi at row 0, lo at row 64)
+  if (!make_tmap_sw128(&tmP, P, n, n, ldp, transpose ? 32 : 128) ||
+      !make_tmap_sw128(&tmF, Fsplit, n, 128, fs, rp))
+    return cudaErrorInvalidValue;
+  if (transpose)
+    return rp == 32 ? launch_tp_t<true, 32>(tmP, tmF, out, ps, cs, n, r, parts, num_sms, status, s)
+                    : launch_tp_t<true, 64>(tmP, tmF, out, ps, cs, n, r, parts, num_sms, status, s);
+  return rp == 32 ? launch_tp_t<false, 32>(tmP, tmF, out, ps, cs, n, r, parts, num_sms, status, s)
+                  : launch_tp_t<false, 64>(tmP, tmF, out, ps, cs, n, r, parts, num_sms, status, s);
 }
 
 }  // namespace lv

@@ -141,6 +141,44 @@ def test_level_pass_kernel(prec, n, r, upd):
     assert bool((P[:, n:] == 3.0).all())  # padding untouched
 
 
+@pytest.mark.parametrize("n,r,upd", [(200, 17, True), (1000, 32, False), (1031, 33, True),
+                                     (2048, 48, True), (129, 64, True), (4100, 64, False)])
+def test_tensor_core_products_pass(n, r, upd):
+    """Level passes wider than 16 columns in FP32 with a factor stride that is
+    a multiple of 64: X = P U and Y = P^T V run on the tensor cores (split
+    TF32, K cut into parts whose partial sums are added afterwards), then
+    P += U V^T.  Against the oracle's FP64 products: ragged n (not a multiple
+    of 32 or of 128), one and two factor-column blocks (r <= 32, r > 32).
+    Bound 2e-6: each product carries ~2^-21 relative error (TF32 split with a
+    truncated low part), and the 32-deep tensor-pipe segments are summed in
+    FP32 registers, so the error does not grow with n."""
+    from paper_1403_6968_gb300 import level_pass
+    g = np.random.default_rng(n * 7 + r)
+    p = g.standard_normal((n, n)).astype(np.float32)
+    u = g.standard_normal((n, r)).astype(np.float32)
+    v = g.standard_normal((n, r)).astype(np.float32)
+    ld = ((n + 3) // 4) * 4
+    ldf = ((n + 63) // 64) * 64
+    P = torch.full((n, ld), 3.0, dtype=torch.float32, device="cuda")
+    P[:, :n] = _dev(p)
+    Pv = P[:, :n]
+
+    def fac(x):
+        buf = torch.zeros((r, ldf), dtype=torch.float32, device="cuda")
+        if x is not None:
+            buf[:, :n] = _dev(x.T.copy())
+        return buf[:, :n]
+
+    Ut, Vt, Xt, Yt = fac(u), fac(v), fac(None), fac(None)
+    level_pass(Pv, Ut, Vt, Xt, Yt, do_update=upd)
+    torch.cuda.synchronize()
+    x_ref, y_ref, p_ref = op.level_products(p, u, v)
+    assert rel_frob(Xt.cpu().numpy().T, x_ref) <= 2e-6
+    assert rel_frob(Yt.cpu().numpy().T, y_ref) <= 2e-6
+    assert rel_frob(Pv.cpu().numpy(), p_ref if upd else p) <= 1e-5
+    assert bool((P[:, n:] == 3.0).all())
+
+
 def test_reeval_modes_against_oracle():
     n, k = 1024, 16
     a = li.power_matrix(n, seed=5, dtype=np.float32)
