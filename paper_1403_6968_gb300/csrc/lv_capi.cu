@@ -478,11 +478,9 @@ static linview_status run_products_update(linview_program* p, const View& v, int
     // blocks wider than the CUDA-core products pass sustains: X = P U and
     // Y = P^T V on the tensor cores, one read of P each, K split in ``parts``
     const int n = (int)v.rows;
-    int parts = tp_parts(n, p->sms);
-    if (parts > p->xslots) parts = p->xslots;
-    if (want_y && parts > p->yslots) parts = p->yslots;
-    if (allow_tc && p->tpF && v.square && r > kMaxProductR && parts >= 1 &&
-        (v.ld * 4) % 16 == 0 && p->fs % 64 == 0) {
+    const int parts = tp_parts(n, p->sms);  // partial sets the pass writes
+    if (allow_tc && p->tpF && v.square && r > kMaxProductR && parts <= p->xslots &&
+        (!want_y || parts <= p->yslots) && (v.ld * 4) % 16 == 0 && p->fs % 64 == 0) {
       const double nn = (double)n * (double)n * sizeof(float);
       for (int c0 = 0; c0 < r; c0 += kMaxTcR) {
         const int w = (r - c0 < kMaxTcR) ? (r - c0) : kMaxTcR;

@@ -92,15 +92,16 @@ int64_t tc_split_floats(int64_t n);
 constexpr int kMaxTcR = 64;  // widest factor block of one tensor-core update pass
 constexpr int kTpMaxParts = 8;  // K parts (partial sums) of a tensor-core products pass
 // Tensor-core products pass (FP32, 1 <= r <= 64): transpose = false: the
-// partial sums of X = P F over ``parts`` column ranges of P; true: of
-// Y = P^T F over row ranges.  Partial q, factor column c, output row i lands
-// at out[q ps + c cs + i].  F column-major (column stride fs, a multiple of
-// 64, >= n); Fsplit is scratch of 128 x fs floats (the split factor).
+// partial sums of X = P F over column ranges of P; true: of Y = P^T F over
+// row ranges; ``parts`` = tp_parts(n, num_sms) partial sets, every one
+// written.  Partial q, factor column c, output row i lands at
+// out[q ps + c cs + i].  F column-major (column stride fs, a multiple of 64,
+// >= n); Fsplit is scratch of 128 x fs floats (the split factor).
 cudaError_t launch_tc_products(bool transpose, const float* P, int64_t ldp, const float* F,
                                int64_t fs, float* Fsplit, int n, int r, float* out, int64_t ps,
                                int64_t cs, int parts, int num_sms, unsigned* status,
                                cudaStream_t s);
-// K parts the products pass uses for an n x n view (<= kTpMaxParts)
+// partial sets the products pass writes for an n x n view (<= kTpMaxParts)
 int tp_parts(int n, int num_sms);
 // Tensor-core update pass P += U W^T (FP32 view, 17 <= r <= 64 factor
 // columns, split TF32): splits U, W into the scratch, then one persistent

@@ -448,10 +448,11 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const float* __restrict__
 //      B = U^T (RP factor columns x 32 of K);
 //   Y: A = P^T (the loaded 32 x 128 slab of P transposed by the split warps
 //      into 128 x 32 hi and lo tiles), B = V^T.
-// Work items: output tile (128 rows of X or of Y) x K part; a part's sums
-// land in partial ``part`` of the output (Xpart / Ypart layout: partial
-// stride ps, column stride cs), summed by the assembly.  One CTA per SM,
-// contiguous items per CTA.  Warps: 0 TMA producer, 1 TMEM allocation and
+// Work: the output tiles' K chunks in one tile-major sequence, cut into one
+// contiguous range per CTA (one CTA per SM); a tile's chunks are shared by a
+// few CTAs, whose sums land in consecutive partials of the output (Xpart /
+// Ypart layout: partial stride ps, column stride cs), summed by the
+// assembly.  Warps: 0 TMA producer, 1 TMEM allocation and
 // MMA issue, 2-5 split, 6-9 epilogue.  The pass is bound by shared-memory
 // traffic (the TMA writes, the split, and the tensor pipe reading each A
 // tile three times), not by HBM.  Every mbarrier wait is bounded: an expired
@@ -520,16 +521,26 @@ __global__ void __launch_bounds__(kTpThreads, 1)
   const int warp = tid >> 5;
   const int lane = tid & 31;
 
+  // Work: the C = ot_n x nkb chunks (output tile ot, K chunk kb of 32),
+  // tile-major, cut into gridDim.x contiguous ranges; a CTA's range splits
+  // into segments, one per output tile it touches.  The CTAs touching tile
+  // ot are b_lo(ot) .. : a segment's sums go to partial b - b_lo(ot) (< parts),
+  // and the CTA that ends a tile zero-fills the partials past its own.
   const int ot_n = (n + kBM - 1) / kBM;  // output tiles
   const int nkb = (n + 31) / 32;          // K chunks of 32
-  const long long T = (long long)ot_n * parts;
-  const long long t0 = T * blockIdx.x / gridDim.x;
-  const long long t1 = T * (blockIdx.x + 1) / gridDim.x;
-  auto item = [&](long long t, int& ot, int& part, int& kb0, int& kb1) {
-    ot = (int)(t / parts);
-    part = (int)(t % parts);
-    kb0 = (int)((long long)nkb * part / parts);
-    kb1 = (int)((long long)nkb * (part + 1) / parts);
+  const long long C = (long long)ot_n * nkb;
+  const long long G = gridDim.x;
+  const long long c0 = C * blockIdx.x / G;
+  const long long c1 = C * (blockIdx.x + 1) / G;
+  // first CTA whose range holds chunk x: the largest b with C b / G <= x
+  auto cta_of = [&](long long x) { return (int)(((x + 1) * G + C - 1) / C - 1); };
+  // segment of the chunk range starting at chunk c: tile, K range, slot
+  auto segment = [&](long long c, int& ot, int& kb0, int& kb1, int& part) {
+    ot = (int)(c / nkb);
+    kb0 = (int)(c % nkb);
+    const long long tile_end = (long long)(ot + 1) * nkb;
+    kb1 = (int)((c1 < tile_end ? c1 : tile_end) - (long long)ot * nkb);
+    part = (int)blockIdx.x - cta_of((long long)ot * nkb);
   };
 
   if (tid == 0) {
@@ -563,9 +574,10 @@ __global__ void __launch_bounds__(kTpThreads, 1)
     // ---------------- producer ----------------
     if (lane == 0) {
       long long g = 0, issued = 0;
-      for (long long t = t0; t < t1 && !*abort_flag; ++t) {
+      for (long long c = c0; c < c1 && !*abort_flag;) {
         int ot, part, kb0, kb1;
-        item(t, ot, part, kb0, kb1);
+        segment(c, ot, kb0, kb1, part);
+        c += kb1 - kb0;
         for (int kb = kb0; kb < kb1 && !*abort_flag; ++kb, ++g) {
           const int st = (int)(g % S);
           const long long use = g / S;
@@ -595,9 +607,10 @@ __global__ void __launch_bounds__(kTpThreads, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       long long g = 0, issued = 0;
-      for (long long t = t0; t < t1 && !*abort_flag; ++t) {
+      for (long long c = c0; c < c1 && !*abort_flag;) {
         int ot, part, kb0, kb1;
-        item(t, ot, part, kb0, kb1);
+        segment(c, ot, kb0, kb1, part);
+        c += kb1 - kb0;
         for (int kb = kb0; kb < kb1; ++kb, ++g) {
           const int st = (int)(g % S);
           const long long use = g / S;
@@ -637,9 +650,10 @@ __global__ void __launch_bounds__(kTpThreads, 1)
     const int st_tid = tid - 64;
     long long g = 0;
     bool ok = true;
-    for (long long t = t0; t < t1 && ok; ++t) {
+    for (long long c = c0; c < c1 && ok;) {
       int ot, part, kb0, kb1;
-      item(t, ot, part, kb0, kb1);
+      segment(c, ot, kb0, kb1, part);
+      c += kb1 - kb0;
       for (int kb = kb0; kb < kb1; ++kb, ++g) {
         const int st = (int)(g % S);
         const long long use = g / S;
@@ -703,9 +717,10 @@ __global__ void __launch_bounds__(kTpThreads, 1)
     const int row = quarter * 32 + lane;
     long long g = 0;
     bool ok = true;
-    for (long long t = t0; t < t1 && ok; ++t) {
+    for (long long c = c0; c < c1 && ok;) {
       int ot, part, kb0, kb1;
-      item(t, ot, part, kb0, kb1);
+      segment(c, ot, kb0, kb1, part);
+      c += kb1 - kb0;
       float acc[RP];
 #pragma unroll
       for (int c = 0; c < RP; ++c) acc[c] = 0.f;
@@ -734,8 +749,11 @@ __global__ void __launch_bounds__(kTpThreads, 1)
       if (orow < n) {
         float* o = out + (int64_t)part * ps + orow;
 #pragma unroll
-        for (int c = 0; c < RP; ++c)
-          if (c < r_out) o[(int64_t)c * cs] = acc[c];
+        for (int q = 0; q < RP; ++q)
+          if (q < r_out) o[(int64_t)q * cs] = acc[q];
+        if (kb1 == nkb)  // this CTA ends the tile: the partials past its own are zero
+          for (int pz = part + 1; pz < parts; ++pz)
+            for (int q = 0; q < r_out; ++q) out[(int64_t)pz * ps + (int64_t)q * cs + orow] = 0.f;
       }
     }
   }
@@ -819,12 +837,21 @@ cudaError_t launch_tc_update(const CUtensorMap& tmP, const CUtensorMap& tmA,
   return launch_tc_t<64>(tmP, tmA, tmB, P, ldp, n, num_sms, status, s);
 }
 
+// CTAs of a products pass over an n x n view: one per SM, but at most
+// kTpMaxParts - 1 per output tile and no more than the chunks
+static long long tp_grid(int n, int num_sms) {
+  const long long ot = (n + kBM - 1) / kBM, chunks = ot * ((n + 31) / 32);
+  long long g = num_sms;
+  if (g > ot * (kTpMaxParts - 1)) g = ot * (kTpMaxParts - 1);
+  if (g > chunks) g = chunks;
+  return g < 1 ? 1 : g;
+}
+
+// partial sets: a tile's chunks span at most ceil(G / ot) + 1 CTAs
 int tp_parts(int n, int num_sms) {
-  const int ot = (n + kBM - 1) / kBM;
-  int parts = num_sms / ot;
-  if (parts < 1) parts = 1;
-  if (parts > kTpMaxParts) parts = kTpMaxParts;
-  return parts;
+  const long long ot = (n + kBM - 1) / kBM;
+  const long long g = tp_grid(n, num_sms);
+  return (int)((g + ot - 1) / ot + 1);
 }
 
 template <bool TR, int RP>
@@ -835,8 +862,7 @@ static cudaError_t launch_tp_t(const CUtensorMap& tmP, const CUtensorMap& tmF, f
   static const cudaError_t configured = cudaFuncSetAttribute(
       tc_products_kernel<TR, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SmemBytes);
   if (configured != cudaSuccess) return configured;
-  const long long T = (long long)((n + kBM - 1) / kBM) * parts;
-  const int grid = (int)(T < num_sms ? T : num_sms);
+  const int grid = (int)tp_grid(n, num_sms);
   tc_products_kernel<TR, RP><<<grid, kTpThreads, Sh::SmemBytes, s>>>(tmP, tmF, out, ps, cs, n,
                                                                      r_out, parts, status);
   return cudaGetLastError();
@@ -846,7 +872,7 @@ cudaError_t launch_tc_products(bool transpose, const float* P, int64_t ldp, cons
                                int64_t fs, float* Fsplit, int n, int r, float* out, int64_t ps,
                                int64_t cs, int parts, int num_sms, unsigned* status,
                                cudaStream_t s) {
-  if (r < 1 || r > kMaxTcR || parts < 1 || parts > kTpMaxParts || fs % 64 || fs < n)
+  if (r < 1 || r > kMaxTcR || parts != tp_parts(n, num_sms) || fs % 64 || fs < n)
     return cudaErrorInvalidValue;
   const int rp = r <= 32 ? 32 : 64;
   const int64_t tot = (int64_t)rp * n;
