@@ -374,10 +374,11 @@ linview_status linview_gemm(int precision, int ta, int tb, int64_t M, int64_t N,
  * into the library (16 MiB of device memory, reserved on a device once the
  * library's kernels are first used there -- CUDA's lazy module loading -- and
  * held until the process exits) instead of stream-ordered allocations.  It
- * launches the allocating entry's products passes and reductions; FP32 updates
- * wider than 16 columns run on the CUDA-core update pass instead of the
- * tensor-core pass (which needs a factor scratch buffer), so for those the two
- * entries agree within FP32 rounding rather than bit for bit.  Sizes whose
+ * launches the allocating entry's CUDA-core products passes and reductions;
+ * FP32 blocks wider than 16 columns run on the CUDA-core passes here (products
+ * in blocks of 16, updates in blocks of 32), where the allocating entry uses
+ * the tensor-core passes (which need factor scratch buffers), so for those the
+ * two entries agree within FP32 rounding rather than bit for bit.  Sizes whose
  * partial sums do not fit (roughly n * r beyond 8192 * 8 for FP32 on a 152-SM
  * GPU) return LINVIEW_ESHAPE with the needed byte count, before the array is
  * touched.  The first call on a device looks up the array's device address

@@ -8,12 +8,13 @@
 // synchronisation a cudaMalloc/cudaFree may cause.  linview_level_pass gets
 // its cross-block partial sums from the stream-ordered allocator; this
 // variant takes them from one fixed array compiled into the library instead.
-// It launches the same products passes (FP32 in blocks of 16 columns, FP64
-// in blocks of 8) and the same partial-sum reductions.  One difference: FP32
-// updates wider than 16 columns run on the CUDA-core update pass here (in
-// blocks of 32), where the allocating entry splits the factors into a scratch
-// buffer for the tensor-core pass; both are FP32-accurate, so those results
-// agree within FP32 rounding, not bit for bit.
+// It launches the CUDA-core products passes (FP32 in blocks of 16 columns,
+// FP64 in blocks of 8) and partial-sum reductions of the allocating entry.
+// One difference: FP32 blocks wider than 16 columns run on the CUDA-core
+// passes here (products in blocks of 16, updates in blocks of 32), where the
+// allocating entry splits the factors into scratch buffers for the
+// tensor-core products and update passes; both are FP32-accurate, so those
+// results agree within FP32 rounding, not bit for bit.
 //
 // The array is a file-scope __device__ variable of kNoAllocScratchBytes
 // (16 MiB).  Under CUDA's lazy module loading it is reserved on a device once
