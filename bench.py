@@ -1316,14 +1316,57 @@ def serving_sweep(args, seed=0):
             "mean_coalesced_rank": (after["coalesced_rank_sum"] - before["coalesced_rank_sum"])
             / max(nref, 1),
             "mean_request_rank": float(ranks.mean()),
-            "max_inflight_seen": after["max_inflight_seen"]})
+            "max_inflight_seen": after["max_inflight_seen"],
+            "_recs": recs, "_span": span})
     srv.close()
+    # what a refresh of each view size costs alone, per coalesced rank, and
+    # hence how the GPU time of each sweep point splits over the view sizes
+    cost = serving_view_costs(sorted(set(sizes)), seed=seed)
+    for pt in sweep:
+        recs, span = pt.pop("_recs"), pt.pop("_span")
+        seen = {}
+        for rc in recs:  # one refresh per (view, issue time)
+            seen[(rc["view"], rc["start_s"])] = rc["batch_rank"]
+        busy = {}
+        for (v, _), r in seen.items():
+            nv = sizes[v]
+            busy[nv] = busy.get(nv, 0.0) + cost[str(nv)][str(min(max(int(r), 1), 8))]
+        pt["gpu_busy_share_by_n"] = {str(nv): busy[nv] / 1e3 / span for nv in sorted(busy)}
     return {"views": len(sizes), "n_counts": {str(n): sizes.count(n) for n in sorted(set(sizes))},
             "k": 16, "resident_bytes": st0["bytes_used"], "setup_s": setup_s,
             "max_inflight": args.serve_inflight, "r_cap": 8, "sweep": sweep,
+            "refresh_ms_alone": cost,
             "note": "open-loop Poisson arrivals replayed by the library; queued requests to a "
                     "busy view coalesce up to rank 8; latency = completion seen by the "
-                    "scheduler - arrival"}
+                    "scheduler - arrival; refresh_ms_alone: one refresh of an A^16 view of "
+                    "each size per coalesced rank, timed alone (CUDA events); "
+                    "gpu_busy_share_by_n: the sum of those costs over a sweep point's "
+                    "refreshes, per view size, divided by the point's wall time"}
+
+
+def serving_view_costs(ns, seed=0, reps=5):
+    """ms of one refresh of an A^16 view (the server's program: power, k = 16,
+    r_max = 8) per view size and delta rank 1..8, each timed alone."""
+    import numpy as np
+    import torch
+    import linview_inputs as li
+    from paper_1403_6968_gb300 import Program
+
+    out = {}
+    for n in ns:
+        prog = Program("power", [torch.from_numpy(li.power_matrix(n, seed=seed, dtype=np.float32))
+                                 .cuda()], k=16, r_max=8)
+        ups = li.lowrank_update_stream(n, 8, 1, seed=seed + 1, dtype=np.float32)[0]
+        u8, v8 = torch.from_numpy(ups[0]).cuda(), torch.from_numpy(ups[1]).cuda()
+        row = {}
+        for r in range(1, 9):
+            u, v = u8[:, :r].contiguous(), v8[:, :r].contiguous()
+            for _ in range(2):
+                prog.apply_delta(u, v)
+            row[str(r)] = _event_ms(lambda j: prog.apply_delta(u, v), reps)
+        out[str(n)] = row
+        prog.close()
+    return out
 
 
 def zipf_batches(args, seed=0, count=1000):
