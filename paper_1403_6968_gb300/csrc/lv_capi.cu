@@ -3071,32 +3071,43 @@ linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp
   const bool tp = e == 4 && products && r > kMaxProductR && ldf % 64 == 0;
   tmp.xslots = tp && g.gC < kTpMaxParts ? kTpMaxParts : g.gC;
   tmp.yslots = tp && g.gR < kTpMaxParts ? kTpMaxParts : g.gR;
+  // the call's temporaries, returned in stream order on every exit path
+  struct Temps {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    ~Temps() {
+      for (void* q : ptrs) cudaFreeAsync(q, s);
+    }
+  } temps{s, {}};
+  auto talloc_s = [&](void** out, size_t bytes) {
+    const cudaError_t ce = cudaMallocAsync(out, bytes, s);
+    if (ce == cudaSuccess) temps.ptrs.push_back(*out);
+    return ce;
+  };
   void* xp = nullptr;
   void* yp = nullptr;
   void* stw = nullptr;
   void* tpf = nullptr;
   if (products) {
-    LV_CUDA(cudaMallocAsync(&xp, (size_t)tmp.xslots * tmp.xp_s * e, s));
-    LV_CUDA(cudaMallocAsync(&yp, (size_t)tmp.yslots * tmp.yp_q * e, s));
+    LV_CUDA(talloc_s(&xp, (size_t)tmp.xslots * tmp.xp_s * e));
+    LV_CUDA(talloc_s(&yp, (size_t)tmp.yslots * tmp.yp_q * e));
   }
   if (tp) {
-    LV_CUDA(cudaMallocAsync(&tpf, sizeof(float) * 128 * ldf, s));
+    LV_CUDA(talloc_s(&tpf, sizeof(float) * 128 * ldf));
     tmp.tpF = static_cast<float*>(tpf);
   }
-  LV_CUDA(cudaMallocAsync(&stw, sizeof(unsigned) * 4, s));
+  LV_CUDA(talloc_s(&stw, sizeof(unsigned) * 4));
   LV_CUDA(cudaMemsetAsync(stw, 0, sizeof(unsigned) * 4, s));
   tmp.status = static_cast<unsigned*>(stw);
   void* tcs = nullptr;  // split factors of the tensor-core update pass (FP32, r > 16)
   if (e == 4 && do_update && r > kMaxProductR) {
-    LV_CUDA(cudaMallocAsync(&tcs, (size_t)tc_split_floats(n) * sizeof(float), s));
+    LV_CUDA(talloc_s(&tcs, (size_t)tc_split_floats(n) * sizeof(float)));
     tmp.tcA = static_cast<float*>(tcs);
     tmp.tcB = tmp.tcA + tc_split_floats(n) / 2;
     if (!make_tmap_sw128(&tmp.tmA, tmp.tcA, 128, n, 128, 128) ||
         !make_tmap_sw128(&tmp.tmB, tmp.tcB, 128, n, 128, 32) ||
-        !make_tmap_sw128(&v.tmap_tc, P, n, n, ldp, 128)) {
-      cudaFreeAsync(tcs, s);
+        !make_tmap_sw128(&v.tmap_tc, P, n, n, ldp, 128))
       return fail(LINVIEW_EDEVICE, "tensor map encode failed");
-    }
   }
   tmp.Xpart = xp;
   tmp.Ypart = yp;
@@ -3136,11 +3147,6 @@ linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp
   }
   unsigned hs = 0;
   cudaMemcpyAsync(&hs, stw, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-  if (xp) cudaFreeAsync(xp, s);
-  if (yp) cudaFreeAsync(yp, s);
-  if (tcs) cudaFreeAsync(tcs, s);
-  if (tpf) cudaFreeAsync(tpf, s);
-  cudaFreeAsync(stw, s);
   LV_CUDA(cudaStreamSynchronize(s));
   if (st == LINVIEW_OK && (hs & kStatusTimeout)) st = fail(LINVIEW_ETIMEOUT, "bounded wait expired");
   return st;
