@@ -2121,9 +2121,11 @@ static linview_status ols_create(linview_program* p, const void* const* inputs,
 }
 
 // Row-block replacement by block Woodbury (see lv_ols.cu for the algebra).
+// The launches of a row-block update once the new rows are in U's first kr
+// columns and the row indices in rows_d: they depend only on kr (all
+// pointers are the program's own), so they replay as a CUDA graph per kr.
 template <typename T>
-static linview_status ols_replace_t(linview_program* p, int kr, const void* nrows, int64_t ld,
-                                    int on_dev, cudaStream_t s) {
+static linview_status ols_propagate_t(linview_program* p, int kr, cudaStream_t s) {
   const int n = (int)p->d.n;
   const int pp = (int)p->d.p;
   const int64_t fs = p->fs;
@@ -2133,9 +2135,7 @@ static linview_status ols_replace_t(linview_program* p, int kr, const void* nrow
   T* Wu = static_cast<T*>(p->Wuf);
   View& w = p->views[kOlsW];
   const PassGeom g = fused_geom(sizeof(T), n, p->sms);
-  // U = [X'_R^T, X_R^T]: new rows become the first kr columns, old rows the next kr
-  LV_CUDA(cudaMemcpy2DAsync(U, fs * sizeof(T), nrows, ld * sizeof(T), (size_t)n * sizeof(T), kr,
-                            on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  // U = [X'_R^T, X_R^T]: the old rows become the kr columns after the new ones
   LV_CUDA(launch_gather_rows<T>(static_cast<const T*>(p->Xd), p->ldX, p->rows_d, kr, n,
                                 U + (int64_t)kr * fs, fs, 1, s));
   LV_CUDA(launch_gather_rows<T>(static_cast<const T*>(p->Yd), p->ldY, p->rows_d, kr, pp,
@@ -2155,22 +2155,6 @@ static linview_status ols_replace_t(linview_program* p, int kr, const void* nrow
     LV_CUDA(launch_xty_update<T>(static_cast<T*>(xty0.ptr), xty0.ld, static_cast<T*>(p->XtYc),
                                  fs, U, n, pp, kr, static_cast<const T*>(p->Yr), side, xtyl));
     p->all_launches += 2;
-    if constexpr (sizeof(T) == 4) {
-      if (p->Zh) {
-        // Z += X'_R^T X'_R - X_R^T X_R, deferred: the rows join the history,
-        // which is folded into Z when full and before a correction
-        if (p->hcnt + kr > p->hcap) {
-          LV_CUDA(launch_z_flush(p->Zh, p->Zl, p->ldz, p->Hp, p->Hm, fs, n, p->hcnt, side));
-          p->all_launches++;
-          p->hcnt = 0;
-        }
-        LV_CUDA(cudaMemcpyAsync(p->Hp + (int64_t)p->hcnt * fs, U, sizeof(float) * fs * kr,
-                                cudaMemcpyDeviceToDevice, side));
-        LV_CUDA(cudaMemcpyAsync(p->Hm + (int64_t)p->hcnt * fs, U + (int64_t)kr * fs,
-                                sizeof(float) * fs * kr, cudaMemcpyDeviceToDevice, side));
-        p->hcnt += kr;
-      }
-    }
   }
   if constexpr (sizeof(T) == 4) {
     // G = W U = W^T U (W is symmetric): column sums of a pass over W, which
@@ -2224,6 +2208,26 @@ static linview_status ols_replace_t(linview_program* p, int kr, const void* nrow
                                   static_cast<const T*>(p->Yr), static_cast<T*>(p->Hols), s));
   }
   p->all_launches += 2;
+  return LINVIEW_OK;
+}
+
+// Z += X'_R^T X'_R - X_R^T X_R for the Newton-Schulz correction, deferred:
+// the block's new and old rows (U's two halves) join the history, which is
+// folded into Z when full and before a correction.
+static linview_status ols_history_push(linview_program* p, int kr, cudaStream_t s) {
+  if (!p->Zh) return LINVIEW_OK;
+  const int64_t fs = p->fs;
+  const float* U = static_cast<const float*>(p->Uar);
+  if (p->hcnt + kr > p->hcap) {
+    LV_CUDA(launch_z_flush(p->Zh, p->Zl, p->ldz, p->Hp, p->Hm, fs, (int)p->d.n, p->hcnt, s));
+    p->all_launches++;
+    p->hcnt = 0;
+  }
+  LV_CUDA(cudaMemcpyAsync(p->Hp + (int64_t)p->hcnt * fs, U, sizeof(float) * fs * kr,
+                          cudaMemcpyDeviceToDevice, s));
+  LV_CUDA(cudaMemcpyAsync(p->Hm + (int64_t)p->hcnt * fs, U + (int64_t)kr * fs,
+                          sizeof(float) * fs * kr, cudaMemcpyDeviceToDevice, s));
+  p->hcnt += kr;
   return LINVIEW_OK;
 }
 
@@ -2553,6 +2557,13 @@ constexpr int kKeyB = 1024;
 
 // The launches of one update after its factors are in place, on stream s.
 static linview_status propagate_eager(linview_program* p, int key, cudaStream_t s) {
+  if (p->d.kind == LINVIEW_OLS) {
+    const linview_status st = p->elem == 4 ? ols_propagate_t<float>(p, key, s)
+                                           : ols_propagate_t<double>(p, key, s);
+    const linview_status sj = side_join(p, s);  // also after an error, to close the fork
+    LV_TRY(st);
+    return sj;
+  }
   if (p->d.kind == LINVIEW_ITERATION) {
     if (iter_exp(p)) {
       if (key >= kKeyB)
@@ -2652,6 +2663,7 @@ static linview_status propagate(linview_program* p, int key, cudaStream_t s) {
     case LINVIEW_POWER:
     case LINVIEW_POWER_SUM:
     case LINVIEW_ITERATION:
+    case LINVIEW_OLS:
       if (p->use_graphs) return graph_propagate(p, key, s);
       return propagate_eager(p, key, s);
     default: return fail(LINVIEW_EUNSUPPORTED, "updates for kind %d", p->d.kind);
@@ -2785,13 +2797,12 @@ linview_status linview_apply_row_block(linview_program* p, int64_t kr, const int
   }
   LV_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // stage: the row indices, and the new rows as U's first kr columns
   LV_CUDA(cudaMemcpyAsync(p->rows_d, rows, sizeof(int64_t) * kr, cudaMemcpyHostToDevice, s));
-  const linview_status st = p->elem == 4
-                                ? ols_replace_t<float>(p, (int)kr, new_rows, ld, on_device, s)
-                                : ols_replace_t<double>(p, (int)kr, new_rows, ld, on_device, s);
-  const linview_status sj = side_join(p, s);  // also after an error, to close the fork
-  LV_TRY(st);
-  LV_TRY(sj);
+  LV_CUDA(cudaMemcpy2DAsync(p->Uar, p->fs * p->elem, new_rows, ld * p->elem, (size_t)n * p->elem,
+                            kr, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  LV_TRY(propagate(p, (int)kr, s));
+  LV_TRY(ols_history_push(p, (int)kr, s));
   return after_update(p, s);
 }
 

@@ -40,9 +40,13 @@ def _requested():
 @pytest.mark.parametrize("kind,n,k,r_max", [("power", 1000, 16, 4), ("power_sum", 2048, 16, 1),
                                             ("power_sum", 513, 8, 8)])
 def test_power_program_memory_is_torchs(kind, n, k, r_max):
+    import gc
     P = _pkg()
     a = li.power_matrix(n, seed=3, dtype=np.float32)
     ad = torch.from_numpy(a).cuda()
+    # programs left unreferenced by earlier tests return their memory when
+    # collected: collect them now, not in the middle of the measurement
+    gc.collect()
     torch.cuda.synchronize()
     before, req0 = torch.cuda.memory_allocated(), _requested()
     prog = P.Program(kind, [ad], k=k, r_max=r_max)
@@ -75,9 +79,11 @@ def test_cudamalloc_default_is_invisible_to_torch():
 
 
 def test_lazy_work_space_and_ols_through_the_allocator():
+    import gc
     P = _pkg()
     n, p, k = 300, 8, 4
     a, b, t0 = li.iteration_inputs(n, p, seed=6)
+    gc.collect()  # earlier tests' unreferenced programs free their memory now
     torch.cuda.synchronize()
     req0 = _requested()
     prog = P.Program("iteration", [a, b, t0], k=k, r_max=2, p=p, precision="f64")
