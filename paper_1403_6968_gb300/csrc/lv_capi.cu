@@ -1465,12 +1465,11 @@ static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) 
   } else {
     LV_TRY(run_update<T>(p, a, K, V1, r, s));
   }
-  // T_i += [K_0 .. K_{i-1}] [M_{i-1} .. M_0]^T; column-major: T_i^T (p x n)
-  // += Mc (p x ir) Kc^T, Kc column-major n x ir (ld fs)
-  for (int i = 1; i <= k; ++i) {
-    void* ti = Tp + (size_t)i * pp * sizeof(T);
-    const T* mc = M + (int64_t)(k - i) * r * pp;
-    LV_TRY(gemm_cm_own(p, false, true, pp, n, (int64_t)i * r, 1.0, mc, pp, K, fs, 1.0, ti, p->ldT, s));
+  // T_i += [K_0 .. K_{i-1}] [M_{i-1} .. M_0]^T for every i, one launch
+  {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_panel_update<T>(reinterpret_cast<T*>(Tp), p->ldT, K, fs, M, pp, n, (int)pp, k,
+                                   r, s));
   }
   return LINVIEW_OK;
 }
@@ -1501,10 +1500,12 @@ static linview_status iter_propagate_b(linview_program* p, int rb, cudaStream_t 
     LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, rb,
                                    K + (int64_t)j * rb * fs, fs, s));
   }
-  // T_i += [K_0 .. K_{i-1}] [V_b .. V_b]^T; column-major T_i^T (p x n)
-  for (int i = 1; i <= k; ++i) {
-    void* ti = Tp + (size_t)i * pp * sizeof(T);
-    LV_TRY(gemm_cm_own(p, false, true, pp, n, (int64_t)i * rb, 1.0, M, pp, K, fs, 1.0, ti, p->ldT, s));
+  // T_i += [K_0 .. K_{i-1}] [V_b .. V_b]^T for every i, one launch (every M
+  // block is V_b)
+  {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_panel_update<T>(reinterpret_cast<T*>(Tp), p->ldT, K, fs, M, pp, n, (int)pp, k,
+                                   rb, s));
   }
   // B += U_b V_b^T (column-major B^T, p x n)
   LV_TRY(gemm_cm_own(p, false, true, pp, n, rb, 1.0, M, pp, K, fs, 1.0, p->Bm, p->ldB, s));

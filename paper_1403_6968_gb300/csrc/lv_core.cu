@@ -564,6 +564,84 @@ cudaError_t launch_bounded_wait_probe(uint64_t limit_ns, unsigned* status,
   return cudaGetLastError();
 }
 
+// T panel update of the linear iteration model, all views in one launch:
+// T_i += [K_0 .. K_{i-1}] [M blocks]^T for i = 1..k, i.e.
+//   T_i(j, q) = Tp[j ldT + i p + q] += sum_{t < i r} K[t fs + j] M[((k - i) r + t) ldm + q]
+// (App. B, linear model: view i takes the first i Krylov blocks and the i
+// newest M blocks).  A CTA takes 16 rows j and 64 columns q of every view;
+// the 16 x k r Krylov rows and the k r x 64 slice of M are staged in shared
+// memory once for all k views.  A thread owns 4 adjacent columns of one row
+// (one broadcast K load and one 128-bit M load per 4 FMAs) and loads the T
+// entries of 8 views at once before it updates them.  Sums over t in
+// increasing order, in T.
+constexpr int kPanelRows = 16, kPanelQ = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    panel_update_kernel(T* Tp, int64_t ldT, const T* K, int64_t fs, const T* M, int64_t ldm,
+                        int n, int p, int k, int r) {
+  extern __shared__ __align__(16) unsigned char panel_sm[];
+  const int KR = k * r;
+  T* Ks = reinterpret_cast<T*>(panel_sm);  // [kPanelRows][KR]
+  T* Ms = Ks + kPanelRows * KR;            // [KR][kPanelQ]
+  const int j0 = blockIdx.x * kPanelRows, q0 = blockIdx.y * kPanelQ;
+  for (int e = threadIdx.x; e < kPanelRows * KR; e += blockDim.x) {
+    const int jr = e % kPanelRows, t = e / kPanelRows;  // coalesced down a Krylov column
+    Ks[jr * KR + t] = (j0 + jr < n) ? K[(int64_t)t * fs + j0 + jr] : T(0);
+  }
+  for (int e = threadIdx.x; e < KR * kPanelQ; e += blockDim.x) {
+    const int q = e % kPanelQ, t = e / kPanelQ;
+    Ms[t * kPanelQ + q] = (q0 + q < p) ? M[(int64_t)t * ldm + q0 + q] : T(0);
+  }
+  __syncthreads();
+  const int jr = threadIdx.x / 16, qa = 4 * (threadIdx.x % 16);
+  const int j = j0 + jr;
+  if (j >= n || q0 + qa >= p) return;
+  const int nq = (p - q0 - qa) < 4 ? p - q0 - qa : 4;  // columns of this thread in the view
+  const T* kr = Ks + jr * KR;
+  T* trow = Tp + (int64_t)j * ldT + q0 + qa;
+  constexpr int VB = 8;  // views per group: their T loads are in flight together
+  for (int i0 = 1; i0 <= k; i0 += VB) {
+    T tv[VB][4];
+#pragma unroll
+    for (int v = 0; v < VB; ++v)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (i0 + v <= k && c < nq) tv[v][c] = trow[(int64_t)(i0 + v) * p + c];
+#pragma unroll
+    for (int v = 0; v < VB; ++v) {
+      const int i = i0 + v;
+      if (i > k) break;
+      const T* mi = Ms + (k - i) * r * kPanelQ + qa;
+      T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      for (int t = 0; t < i * r; ++t) {
+        const T kv = kr[t];
+        const T* mt = mi + t * kPanelQ;
+        a0 += kv * mt[0];
+        a1 += kv * mt[1];
+        a2 += kv * mt[2];
+        a3 += kv * mt[3];
+      }
+      const T av[4] = {a0, a1, a2, a3};
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < nq) trow[(int64_t)i * p + c] = tv[v][c] + av[c];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_panel_update(T* Tp, int64_t ldT, const T* K, int64_t fs, const T* M,
+                                int64_t ldm, int n, int p, int k, int r, cudaStream_t s) {
+  if (n <= 0 || p <= 0 || k < 1 || r < 1) return cudaSuccess;
+  const size_t smem = sizeof(T) * (size_t)(kPanelRows + kPanelQ) * k * r;
+  if (smem > 49152) return cudaErrorInvalidValue;  // k r <= 64 in FP64, 128 in FP32
+  const dim3 grid((unsigned)((n + kPanelRows - 1) / kPanelRows),
+                  (unsigned)((p + kPanelQ - 1) / kPanelQ));
+  panel_update_kernel<T><<<grid, 256, smem, s>>>(Tp, ldT, K, fs, M, ldm, n, p, k, r);
+  return cudaGetLastError();
+}
+
 #define LV_INST(T)                                                                              \
   template cudaError_t launch_gram<T>(const T*, const T*, int64_t, int, int, double*, unsigned*, \
                                       double*, unsigned*, cudaStream_t, float2*);               \
@@ -577,7 +655,9 @@ cudaError_t launch_bounded_wait_probe(uint64_t limit_ns, unsigned* status,
   template cudaError_t launch_axpy_rows<T>(T*, int64_t, const T*, int64_t, T, int, int,           \
                                            cudaStream_t);                                       \
   template cudaError_t launch_scale_copy<T>(T*, int64_t, const T*, int64_t, T, int, int,          \
-                                            cudaStream_t);
+                                            cudaStream_t);                                      \
+  template cudaError_t launch_panel_update<T>(T*, int64_t, const T*, int64_t, const T*, int64_t, \
+                                              int, int, int, int, cudaStream_t);
 LV_INST(float)
 LV_INST(double)
 

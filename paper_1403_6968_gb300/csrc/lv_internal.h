@@ -213,6 +213,11 @@ cudaError_t launch_axpy_rows(T* y, int64_t ldy, const T* x, int64_t ldx, T alpha
 template <typename T>
 cudaError_t launch_scale_copy(T* y, int64_t ldy, const T* x, int64_t ldx, T alpha, int rows,
                               int cols, cudaStream_t s);  // y = alpha x
+// Linear-model T panel update, all k views in one launch: T_i(j, q) =
+// Tp[j ldT + i p + q] += sum_{t < i r} K[t fs + j] M[((k - i) r + t) ldm + q]
+template <typename T>
+cudaError_t launch_panel_update(T* Tp, int64_t ldT, const T* K, int64_t fs, const T* M,
+                                int64_t ldm, int n, int p, int k, int r, cudaStream_t s);
 
 // OLS pieces (lv_ols.cu).
 template <typename T>
