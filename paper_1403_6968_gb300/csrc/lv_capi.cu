@@ -141,6 +141,8 @@ struct linview_program {
   void* Kar = nullptr;  // Krylov blocks K_0..K_{k-1}, column-major n x k r_max
   void* V1 = nullptr;   // input right factor, column-major n x r_max
   void* Mr = nullptr;   // T_i^T V blocks in reverse order, p x k r_max
+  void* TVpart = nullptr;  // row-block partial sums of those products
+  int64_t tv_cap = 0;      // columns x p the partial sets hold (k r p <= tv_cap)
   void* Gpanel = nullptr;
   void* Dh = nullptr;   // hybrid strategy: dense deltas D_{i-1}, D_i (2 x n x p, ld ldD)
   int64_t ldD = 0;
@@ -1362,6 +1364,8 @@ static bool iter_exp(const linview_program* p) {
 static linview_status iter_sk_create(linview_program* p, const void* const* inputs,
                                      const int64_t* lds, int on_dev, cudaStream_t s);
 
+constexpr int64_t kTvCap = 16384;  // k r p of the one-pass M_i products
+
 static linview_status iter_create(linview_program* p, const void* const* inputs,
                                   const int64_t* lds, int on_dev, cudaStream_t s) {
   if (iter_exp(p)) return iter_sk_create(p, inputs, lds, on_dev, s);
@@ -1390,6 +1394,12 @@ static linview_status iter_create(linview_program* p, const void* const* inputs,
   LV_TRY(dalloc(p, (size_t)p->fs * p->Rcap * p->elem, &p->Kar, s));
   LV_TRY(dalloc(p, (size_t)p->fs * p->d.r_max * p->elem, &p->V1, s));
   LV_TRY(dalloc(p, (size_t)pp * p->Rcap * p->elem, &p->Mr, s));
+  // partial sets of M_i = T_i^T V for all views (one pass over the T panel),
+  // when small: k r_max p <= 16384 per row block
+  if ((int64_t)p->Rcap * pp <= kTvCap) {
+    p->tv_cap = (int64_t)p->Rcap * pp;
+    LV_TRY(dalloc(p, (size_t)panel_tv_blocks((int)n) * p->tv_cap * p->elem, &p->TVpart, s));
+  }
   const PassGeom g = fused_geom(p->elem, (int)n, p->sms);
   p->part_cs = p->fs;
   p->xp_s = (int64_t)kMaxFusedR * p->part_cs;
@@ -1428,10 +1438,18 @@ static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) 
   View& a = p->views[0];
   const PassGeom g = fused_geom(sizeof(T), n, p->sms);
   // M_i = T_i^T V (old T_i), stored at block k-1-i so that [M_{i-1} .. M_0]
-  // is one contiguous p x (i r) slab; all k products in one batched launch
+  // is one contiguous p x (i r) slab: one pass over the T panel (partials
+  // per row block) when its partial sets fit, else one batched GEMM launch
   // (column-major view: T_i is p x n (ld ldT) at panel block i, V is n x r (ld fs))
-  LV_TRY(gemm_cm_own(p, false, false, pp, r, n, 1.0, Tp, p->ldT, V1, fs, 0.0,
-                     M + (int64_t)(k - 1) * r * pp, pp, s, k, pp, 0, -(int64_t)r * pp));
+  if (p->TVpart && (int64_t)k * r * pp <= p->tv_cap) {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_panel_tv<T>(reinterpret_cast<const T*>(Tp), p->ldT, V1, fs,
+                               static_cast<T*>(p->TVpart), M, pp, n, (int)pp, k, r, s));
+    p->all_launches++;  // the partial sums
+  } else {
+    LV_TRY(gemm_cm_own(p, false, false, pp, r, n, 1.0, Tp, p->ldT, V1, fs, 0.0,
+                       M + (int64_t)(k - 1) * r * pp, pp, s, k, pp, 0, -(int64_t)r * pp));
+  }
   if (k >= 2) {
     {
       ProfScope ps(p, s, 0.0);

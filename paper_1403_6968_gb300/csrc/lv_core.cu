@@ -630,6 +630,63 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// M_i = T_i^T V of the linear iteration model, all views in one pass over
+// the T panel (App. B: V_{i+1} = [T_i^T V_1, V_i]): for i < k, c < r, q < p,
+//   M[((k - 1 - i) r + c) ldm + q] = sum_j Tp[j ldT + i p + q] V[c fs + j],
+// as partial sums over blocks of ``rows`` rows (part[b][col][q], column
+// stride p) that launch_sum_partials adds in block order.  A thread owns
+// column q of one view (4 views per CTA, grid z over the views); V's rows of
+// the block are staged in shared memory (r <= 8).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    panel_tv_kernel(const T* Tp, int64_t ldT, const T* V, int64_t fs, T* part, int n, int p,
+                    int k, int r, int rows) {
+  extern __shared__ __align__(16) unsigned char tv_sm[];
+  T* Vs = reinterpret_cast<T*>(tv_sm);  // [rows][8]
+  const int j0 = blockIdx.x * rows, q0 = blockIdx.y * 64;
+  for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {
+    const int jr = e % rows, c = e / rows;
+    Vs[jr * 8 + c] = (j0 + jr < n) ? V[(int64_t)c * fs + j0 + jr] : T(0);
+  }
+  __syncthreads();
+  const int q = q0 + (int)(threadIdx.x % 64);
+  const int i = (int)blockIdx.z * 4 + (int)(threadIdx.x / 64);
+  if (q >= p || i >= k) return;
+  const int nr = (n - j0 < rows) ? n - j0 : rows;
+  T* pb = part + (int64_t)blockIdx.x * k * r * p;
+  {
+    T acc[8] = {};
+    const T* tcol = Tp + (int64_t)j0 * ldT + (int64_t)i * p + q;
+#pragma unroll 8
+    for (int jr = 0; jr < nr; ++jr) {
+      const T t = tcol[(int64_t)jr * ldT];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[c] += t * Vs[jr * 8 + c];
+    }
+    for (int c = 0; c < r; ++c) pb[((int64_t)(k - 1 - i) * r + c) * p + q] = acc[c];
+  }
+}
+
+int panel_tv_blocks(int n) {
+  int rows = (n + 127) / 128;
+  rows = rows < 64 ? 64 : (rows + 7) / 8 * 8;
+  return (n + rows - 1) / rows;
+}
+
+template <typename T>
+cudaError_t launch_panel_tv(const T* Tp, int64_t ldT, const T* V, int64_t fs, T* part, T* M,
+                            int64_t ldm, int n, int p, int k, int r, cudaStream_t s) {
+  if (r < 1 || r > 8 || k < 1 || p < 1) return cudaErrorInvalidValue;
+  const int nb = panel_tv_blocks(n);
+  const int rows = (n + nb - 1) / nb;
+  const dim3 grid((unsigned)nb, (unsigned)((p + 63) / 64), (unsigned)((k + 3) / 4));
+  panel_tv_kernel<T><<<grid, 256, sizeof(T) * (size_t)rows * 8, s>>>(Tp, ldT, V, fs, part, n, p,
+                                                                     k, r, rows);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_sum_partials<T>(part, nb, (int64_t)k * r * p, p, p, k * r, M, ldm, s);
+}
+
 template <typename T>
 cudaError_t launch_panel_update(T* Tp, int64_t ldT, const T* K, int64_t fs, const T* M,
                                 int64_t ldm, int n, int p, int k, int r, cudaStream_t s) {
@@ -657,7 +714,9 @@ cudaError_t launch_panel_update(T* Tp, int64_t ldT, const T* K, int64_t fs, cons
   template cudaError_t launch_scale_copy<T>(T*, int64_t, const T*, int64_t, T, int, int,          \
                                             cudaStream_t);                                      \
   template cudaError_t launch_panel_update<T>(T*, int64_t, const T*, int64_t, const T*, int64_t, \
-                                              int, int, int, int, cudaStream_t);
+                                              int, int, int, int, cudaStream_t);                \
+  template cudaError_t launch_panel_tv<T>(const T*, int64_t, const T*, int64_t, T*, T*, int64_t, \
+                                          int, int, int, int, cudaStream_t);
 LV_INST(float)
 LV_INST(double)
 

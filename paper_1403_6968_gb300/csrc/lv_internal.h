@@ -218,6 +218,13 @@ cudaError_t launch_scale_copy(T* y, int64_t ldy, const T* x, int64_t ldx, T alph
 template <typename T>
 cudaError_t launch_panel_update(T* Tp, int64_t ldT, const T* K, int64_t fs, const T* M,
                                 int64_t ldm, int n, int p, int k, int r, cudaStream_t s);
+// M[((k - 1 - i) r + c) ldm + q] = sum_j Tp[j ldT + i p + q] V[c fs + j] for
+// i < k, c < r <= 8, q < p, through panel_tv_blocks(n) partial sets in
+// ``part`` (panel_tv_blocks(n) x k r p elements)
+int panel_tv_blocks(int n);
+template <typename T>
+cudaError_t launch_panel_tv(const T* Tp, int64_t ldT, const T* V, int64_t fs, T* part, T* M,
+                            int64_t ldm, int n, int p, int k, int r, cudaStream_t s);
 
 // OLS pieces (lv_ols.cu).
 template <typename T>
