@@ -381,7 +381,8 @@ struct ProfScope {
 template <typename T>
 static linview_status run_fused(linview_program* p, const View& v, int mode, int r, const T* Xf,
                                 const T* Yf, const T* Uu, const T* Wu, void* Xpart, void* Ypart,
-                                cudaStream_t s, double* Cpart = nullptr) {
+                                cudaStream_t s, double* Cpart = nullptr,
+                                bool reverse = false) {
   const PassGeom g = fused_geom(sizeof(T), (int)v.rows, p->sms);
   PassParams pp{};
   pp.P = v.ptr;
@@ -404,15 +405,20 @@ static linview_status run_fused(linview_program* p, const View& v, int mode, int
   pp.status = p->status;
   pp.Cpart = Cpart;
   pp.tma_store = v.tma_store ? 1 : 0;
+  pp.reverse = reverse ? 1 : 0;
   const double nn = (double)v.rows * (double)v.rows * sizeof(T);
   ProfScope ps(p, s, (mode & 4) ? 2.0 * nn : nn, 1);
   LV_CUDA((launch_fused<T>(pp, v.tmap, r, mode, s)));
   return LINVIEW_OK;
 }
 
+// A view pass that follows another one over the same view (same row ranges
+// per CTA) runs in the opposite row order (reverse), so that it starts on the
+// rows that are still in L2; blocks of one update alternate in the same way.
 template <typename T>
 static linview_status run_update(linview_program* p, const View& v, const T* Uu, const T* Wu,
-                                 int r, cudaStream_t s, int suffix_rin = 0, int tcset = 0) {
+                                 int r, cudaStream_t s, int suffix_rin = 0, int tcset = 0,
+                                 bool reverse = false) {
   constexpr int MU = kMaxUpdateR;
   // split-factor scratch of the tensor-core pass (set 1: the side stream's)
   float* tA = tcset ? p->tcA2 : p->tcA;
@@ -433,6 +439,7 @@ static linview_status run_update(linview_program* p, const View& v, const T* Uu,
                                  (int)v.rows, w, p->sms, p->status, s));
         p->all_launches++;  // the split kernel
         c0 += w;
+        reverse = !reverse;
         continue;
       }
     }
@@ -451,10 +458,12 @@ static linview_status run_update(linview_program* p, const View& v, const T* Uu,
     pp.status = p->status;
     pp.suffix_rin = suffix_rin;  // host guarantees a single chunk when set
     pp.tma_store = v.tma_store ? 1 : 0;
+    pp.reverse = reverse ? 1 : 0;
     ProfScope ps(p, s, 2.0 * (double)v.rows * (double)v.rows * sizeof(T), 2);
     // a block after the first follows a pass that wrote this view
     LV_CUDA((launch_update<T>(pp, v.tmap, w, s, /*programmatic=*/c0 == 0)));
     c0 += w;
+    reverse = !reverse;
   }
   return LINVIEW_OK;
 }
@@ -463,16 +472,21 @@ static linview_status run_update(linview_program* p, const View& v, const T* Uu,
 // FP32, kMaxFusedR in FP64) into
 // the program's partial buffers (column block c0 at column offset c0), then
 // (if Uu) the in-place update.  Fused in one pass when r <= kMaxFusedR.
+// next_reverse (if given) receives the row order for a further pass over the
+// view (the opposite of the last CUDA-core products pass).
 template <typename T>
 static linview_status run_products_update(linview_program* p, const View& v, int r, const T* Xf,
                                           const T* Yf, const T* Uu, const T* Wu, cudaStream_t s,
-                                          double* Cpart = nullptr, bool allow_tc = false) {
+                                          double* Cpart = nullptr, bool allow_tc = false,
+                                          bool* next_reverse = nullptr) {
+  if (next_reverse) *next_reverse = false;
   const bool want_y = (Yf != nullptr);
   const PassGeom g = fused_geom(sizeof(T), (int)v.rows, p->sms);
   p->pc_x = g.gC;
   p->pc_y = g.gR;
   if (r <= kMaxFusedR) {
     const int mode = kModeX | (want_y ? 2 : 0) | (Uu ? 4 : 0);  // XYU, XY, XU or X
+    if (next_reverse) *next_reverse = true;
     return run_fused<T>(p, v, mode, r, Xf, Yf, Uu, Wu, p->Xpart, p->Ypart, s,
                         mode == kModeXYU ? Cpart : nullptr);
   }
@@ -511,14 +525,18 @@ static linview_status run_products_update(linview_program* p, const View& v, int
     }
   }
   constexpr int MW = sizeof(T) == 4 ? kMaxProductR : kMaxFusedR;  // products-only width
+  bool rev = false;  // consecutive passes over the view alternate their row order
   for (int c0 = 0; c0 < r; c0 += MW) {
     const int w = (r - c0 < MW) ? (r - c0) : MW;
     T* xp = static_cast<T*>(p->Xpart) + (int64_t)c0 * p->part_cs;
     T* yp = static_cast<T*>(p->Ypart) + (int64_t)c0 * p->part_cs;
     LV_TRY(run_fused<T>(p, v, want_y ? kModeXY : kModeX, w, Xf + (int64_t)c0 * p->fs,
-                        want_y ? Yf + (int64_t)c0 * p->fs : nullptr, nullptr, nullptr, xp, yp, s));
+                        want_y ? Yf + (int64_t)c0 * p->fs : nullptr, nullptr, nullptr, xp, yp, s,
+                        nullptr, rev));
+    rev = !rev;
   }
-  if (Uu) LV_TRY(run_update<T>(p, v, Uu, Wu, r, s));
+  if (next_reverse) *next_reverse = rev;
+  if (Uu) LV_TRY(run_update<T>(p, v, Uu, Wu, r, s, 0, 0, rev));
   return LINVIEW_OK;
 }
 
@@ -1251,8 +1269,9 @@ static linview_status krylov_levels(linview_program* p, int bw, int nsteps, int 
       ProfScope ps(p, s, 0.0);
       LV_CUDA((launch_gram<T>(Vj, U, fs, n, rh, p->Cpart, p->ticket, p->C, p->status, s)));
     }
-    LV_TRY(run_products_update<T>(p, Q, bw, U, Vb, nullptr, nullptr, s));
-    LV_TRY(run_update<T>(p, Q, U, Vj, rh, s));
+    bool rev = false;
+    LV_TRY(run_products_update<T>(p, Q, bw, U, Vb, nullptr, nullptr, s, nullptr, false, &rev));
+    LV_TRY(run_update<T>(p, Q, U, Vj, rh, s, 0, 0, rev));
     // skip model with sums: U_j, V_j are Krylov bases of width j bw, so
     // dS'_h = U_j (V_j K^T)^T as in the exponential model
     // (S'_1 is A itself: no sums view for power index 0)
@@ -1473,9 +1492,10 @@ static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) 
       ProfScope ps(p, s, 0.0);
       LV_CUDA(launch_assemble<T>(as, s));
     }
+    // the k - 1 passes over A alternate their row order (j = 1 was forward)
     for (int j = 2; j < k; ++j) {
       LV_TRY(run_fused<T>(p, a, kModeX, r, K + (int64_t)(j - 1) * r * fs, nullptr, nullptr,
-                          nullptr, p->Xpart, p->Ypart, s));
+                          nullptr, p->Xpart, p->Ypart, s, nullptr, j % 2 == 0));
       ProfScope ps(p, s, 0.0);
       LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, r,
                                      K + (int64_t)j * r * fs, fs, s));
@@ -1513,7 +1533,7 @@ static linview_status iter_propagate_b(linview_program* p, int rb, cudaStream_t 
                             cudaMemcpyDeviceToDevice, s));
   for (int j = 1; j < k; ++j) {
     LV_TRY(run_fused<T>(p, a, kModeX, rb, K + (int64_t)(j - 1) * rb * fs, nullptr, nullptr,
-                        nullptr, p->Xpart, p->Ypart, s));
+                        nullptr, p->Xpart, p->Ypart, s, nullptr, j % 2 == 0));
     ProfScope ps(p, s, 0.0);
     LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, rb,
                                    K + (int64_t)j * rb * fs, fs, s));

@@ -68,6 +68,10 @@ struct PassParams {
                       // row extent is a multiple of 16 bytes (a TMA store writes whole
                       // 16-byte units, so a row ending inside one would overwrite the
                       // elements past the view, e.g. a caller's padding)
+  int reverse;        // FP32 passes: each CTA visits its row batches last to first.
+                      // Alternating it over consecutive passes on one view makes a
+                      // pass start on the rows the previous one read last, which are
+                      // still in L2 (the FP64 pass ignores it)
 };
 
 // Host: grid geometry for a pass over an n x n view.

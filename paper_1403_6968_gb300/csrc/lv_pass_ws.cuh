@@ -180,6 +180,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int strip0 = s * STRIP;
   const int col0 = strip0 + tc * COLS;
   const int nbatch = (re - rb + kBatch - 1) / kBatch;
+  // first row of batch b: a reversed pass walks the CTA's row range from its
+  // last batch up to its first
+  const bool rev = p.reverse != 0;
+  auto batch_row = [&](int b) { return rb + (rev ? nbatch - 1 - b : b) * kBatch; };
   const T* Xf = static_cast<const T*>(p.Xf);
   const T* Yf = static_cast<const T*>(p.Yf);
   const T* Uu = static_cast<const T*>(p.Uu);
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   // warp 0: start batch b in stage b % S (factor rows by cp.async, tile by TMA)
   auto produce_rows = [&](int b) {
     const int st = b % S;
-    const int row0 = rb + b * kBatch;
+    const int row0 = batch_row(b);
     const int nb = min(kBatch, re - row0);
     if constexpr (STAGE_ROWS) {
       // consecutive lanes take consecutive factor columns of a row: the shared
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   };
   auto produce_tile = [&](int b) {
     const int st = b % S;
-    const int row0 = rb + b * kBatch;
+    const int row0 = batch_row(b);
     if (lane == 0) {
       fence_proxy_async();
       mbar_arrive_expect_tx(&full[st], stage_bytes);
@@ -325,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   for (int b = 0; b < nbatch; ++b) {
     const int st = b % S;
     const uint32_t parity = (uint32_t)((b / S) & 1);
-    const int row0 = rb + b * kBatch;
+    const int row0 = batch_row(b);
     const int nb = min(kBatch, re - row0);
     const bool full_batch = nb == kBatch;  // the same for the whole CTA
     if (wait_or_abort(&full[st], parity, abort_flag, p.status)) {
@@ -605,6 +609,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int strip0 = s * STRIP;
   const int col0 = strip0 + tc * COLS;
   const int nbatch = (re - rb + kBatch - 1) / kBatch;
+  const bool rev = p.reverse != 0;  // as in the fused pass
+  auto batch_row = [&](int b) { return rb + (rev ? nbatch - 1 - b : b) * kBatch; };
   const T* Uu = static_cast<const T*>(p.Uu);
   const T* Wu = static_cast<const T*>(p.Wu);
   T* P = static_cast<T*>(p.P);
@@ -625,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const uint32_t stage_bytes = (uint32_t)(nbox * kBatch * BOXC * sizeof(T));
   auto produce_rows = [&](int b) {
     const int st = b % S;
-    const int row0 = rb + b * kBatch;
+    const int row0 = batch_row(b);
     const int nb = min(kBatch, re - row0);
     for (int idx = lane; idx < kBatch * R; idx += 32) {  // lanes over columns (see above)
       const int j = idx / R;
@@ -638,7 +644,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   };
   auto produce_tile = [&](int b) {
     const int st = b % S;
-    const int row0 = rb + b * kBatch;
+    const int row0 = batch_row(b);
     if (lane == 0) {
       fence_proxy_async();
       mbar_arrive_expect_tx(&full[st], stage_bytes);
@@ -707,7 +713,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   for (int b = 0; b < nbatch; ++b) {
     const int st = b % S;
     const uint32_t parity = (uint32_t)((b / S) & 1);
-    const int row0 = rb + b * kBatch;
+    const int row0 = batch_row(b);
     const int nb = min(kBatch, re - row0);
     const bool ready = wait_or_abort(&full[st], parity, abort_flag, p.status);
     if (ready) waited = b + 1;
