@@ -1444,6 +1444,32 @@ static linview_status iter_create(linview_program* p, const void* const* inputs,
 // Krylov blocks K_a = A'^a U (A' = A + U V^T); each step adds only the
 // newest block, K_1 = A K_0 + K_0 (V^T K_0) from the old A in the pass that
 // also writes A', and K_a = A' K_{a-1} afterwards.
+// T_i += [K_0 .. K_{i-1}] [M_{i-1} .. M_0]^T for i = 1 .. k on the T panel
+// (App. B, linear model; M blocks stored newest first, p x r each, or all
+// equal to V_b when same_m): one launch of the panel kernel, else (its
+// staged blocks past the device's shared memory) one GEMM per view,
+// column-major T_i^T (p x n) += Mc (p x i r) Kc^T.
+template <typename T>
+static linview_status panel_update(linview_program* p, char* Tp, const T* K, const T* M, int k,
+                                   int r, bool same_m, cudaStream_t s) {
+  const int n = (int)p->d.n;
+  const int64_t pp = p->d.p;
+  const int64_t fs = p->fs;
+  if (panel_update_fits(k, r, sizeof(T))) {
+    ProfScope ps(p, s, 0.0);
+    LV_CUDA(launch_panel_update<T>(reinterpret_cast<T*>(Tp), p->ldT, K, fs, M, pp, n, (int)pp, k,
+                                   r, s));
+    return LINVIEW_OK;
+  }
+  for (int i = 1; i <= k; ++i) {
+    void* ti = Tp + (size_t)i * pp * sizeof(T);
+    const T* mc = same_m ? M : M + (int64_t)(k - i) * r * pp;
+    LV_TRY(gemm_cm_own(p, false, true, pp, n, (int64_t)i * r, 1.0, mc, pp, K, fs, 1.0, ti, p->ldT,
+                       s));
+  }
+  return LINVIEW_OK;
+}
+
 template <typename T>
 static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) {
   const int n = (int)p->d.n;
@@ -1503,12 +1529,9 @@ static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) 
   } else {
     LV_TRY(run_update<T>(p, a, K, V1, r, s));
   }
-  // T_i += [K_0 .. K_{i-1}] [M_{i-1} .. M_0]^T for every i, one launch
-  {
-    ProfScope ps(p, s, 0.0);
-    LV_CUDA(launch_panel_update<T>(reinterpret_cast<T*>(Tp), p->ldT, K, fs, M, pp, n, (int)pp, k,
-                                   r, s));
-  }
+  // T_i += [K_0 .. K_{i-1}] [M_{i-1} .. M_0]^T for every i: one launch, or
+  // one GEMM per view when the panel kernel's staged blocks do not fit
+  LV_TRY(panel_update<T>(p, Tp, K, M, k, r, false, s));
   return LINVIEW_OK;
 }
 
@@ -1538,13 +1561,8 @@ static linview_status iter_propagate_b(linview_program* p, int rb, cudaStream_t 
     LV_CUDA(launch_sum_partials<T>(static_cast<T*>(p->Xpart), g.gC, p->xp_s, p->part_cs, n, rb,
                                    K + (int64_t)j * rb * fs, fs, s));
   }
-  // T_i += [K_0 .. K_{i-1}] [V_b .. V_b]^T for every i, one launch (every M
-  // block is V_b)
-  {
-    ProfScope ps(p, s, 0.0);
-    LV_CUDA(launch_panel_update<T>(reinterpret_cast<T*>(Tp), p->ldT, K, fs, M, pp, n, (int)pp, k,
-                                   rb, s));
-  }
+  // T_i += [K_0 .. K_{i-1}] [V_b .. V_b]^T for every i (every M block is V_b)
+  LV_TRY(panel_update<T>(p, Tp, K, M, k, rb, true, s));
   // B += U_b V_b^T (column-major B^T, p x n)
   LV_TRY(gemm_cm_own(p, false, true, pp, n, rb, 1.0, M, pp, K, fs, 1.0, p->Bm, p->ldB, s));
   return LINVIEW_OK;

@@ -687,12 +687,36 @@ cudaError_t launch_panel_tv(const T* Tp, int64_t ldT, const T* V, int64_t fs, T*
   return launch_sum_partials<T>(part, nb, (int64_t)k * r * p, p, p, k * r, M, ldm, s);
 }
 
+// largest dynamic shared memory a block of this device may opt in to
+static int smem_optin_max() {
+  static const int v = [] {
+    int dev = 0, b = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return 49152;
+    }
+    return b;
+  }();
+  return v;
+}
+
+bool panel_update_fits(int k, int r, size_t elem_bytes) {
+  return elem_bytes * (size_t)(kPanelRows + kPanelQ) * (size_t)k * (size_t)r <=
+         (size_t)smem_optin_max();
+}
+
 template <typename T>
 cudaError_t launch_panel_update(T* Tp, int64_t ldT, const T* K, int64_t fs, const T* M,
                                 int64_t ldm, int n, int p, int k, int r, cudaStream_t s) {
   if (n <= 0 || p <= 0 || k < 1 || r < 1) return cudaSuccess;
+  if (!panel_update_fits(k, r, sizeof(T))) return cudaErrorInvalidValue;
   const size_t smem = sizeof(T) * (size_t)(kPanelRows + kPanelQ) * k * r;
-  if (smem > 49152) return cudaErrorInvalidValue;  // k r <= 64 in FP64, 128 in FP32
+  if (smem > 49152) {  // opt in once, to the device's limit
+    static const cudaError_t configured = cudaFuncSetAttribute(
+        panel_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin_max());
+    if (configured != cudaSuccess) return configured;
+  }
   const dim3 grid((unsigned)((n + kPanelRows - 1) / kPanelRows),
                   (unsigned)((p + kPanelQ - 1) / kPanelQ));
   panel_update_kernel<T><<<grid, 256, smem, s>>>(Tp, ldT, K, fs, M, ldm, n, p, k, r);

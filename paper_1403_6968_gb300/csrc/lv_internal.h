@@ -219,9 +219,12 @@ cudaError_t launch_scale_copy(T* y, int64_t ldy, const T* x, int64_t ldx, T alph
                               int cols, cudaStream_t s);  // y = alpha x
 // Linear-model T panel update, all k views in one launch: T_i(j, q) =
 // Tp[j ldT + i p + q] += sum_{t < i r} K[t fs + j] M[((k - i) r + t) ldm + q]
+// (one launch for all views; its shared memory, (16 + 64) k r elements, must fit
+// the device's opt-in limit: panel_update_fits)
 template <typename T>
 cudaError_t launch_panel_update(T* Tp, int64_t ldT, const T* K, int64_t fs, const T* M,
                                 int64_t ldm, int n, int p, int k, int r, cudaStream_t s);
+bool panel_update_fits(int k, int r, size_t elem_bytes);
 // M[((k - 1 - i) r + c) ldm + q] = sum_j Tp[j ldT + i p + q] V[c fs + j] for
 // i < k, c < r <= 8, q < p, through panel_tv_blocks(n) partial sets in
 // ``part`` (panel_tv_blocks(n) x k r p elements)

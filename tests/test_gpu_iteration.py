@@ -183,6 +183,39 @@ def test_iteration_b_updates(prec, n, p, k, rb):
     prog.close()
 
 
+@pytest.mark.parametrize("prec,k,r", [("f64", 16, 8), ("f32", 32, 8), ("f64", 48, 8),
+                                      ("f32", 96, 8)])
+def test_iteration_long_chains_wide_updates(prec, k, r):
+    """Many views times a wide rank: the T-panel update stages (16 + 64) k r
+    elements.  Past 48 KB (FP64 k r = 128, FP32 k r = 256) it opts in to more
+    shared memory; past the device's limit (FP64 k r = 384, FP32 k r = 768)
+    every view takes its own GEMM.  Updates to A and to B, against the
+    oracle's re-evaluation."""
+    n, p = 160, 3
+    dt = np.float64 if prec == "f64" else np.float32
+    a, b, t0 = li.iteration_inputs(n, p, seed=k + r, dtype=dt)
+    prog = _prog("iteration", [_dev(a), _dev(b), _dev(t0)], k=k, r_max=r, precision=prec)
+    acur, bcur = a.astype(np.float64), b.astype(np.float64)
+    g = np.random.default_rng(k)
+    for step in range(3):
+        if step != 1:
+            u = (g.standard_normal((n, r)) * 0.01).astype(dt)
+            v = (g.standard_normal((n, r)) * 0.01).astype(dt)
+            prog.apply_delta(_dev(u), _dev(v))
+            acur += u.astype(np.float64) @ v.astype(np.float64).T
+        else:
+            ub = g.standard_normal((n, r)).astype(dt)
+            vb = g.standard_normal((p, r)).astype(dt)
+            prog.apply_delta(_dev(ub), _dev(vb), input_id=1)
+            bcur += ub.astype(np.float64) @ vb.astype(np.float64).T
+    prog.sync()
+    ref = oi.reeval(acur, bcur, t0.astype(np.float64), k)
+    tol = 1e-10 if prec == "f64" else 1e-4
+    for i in range(1, k + 1):
+        assert rel_frob(prog.read_view_host(i), ref[i]) <= tol, i
+    prog.close()
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("n,p,k,r", [(300, 5, 16, 2), (1, 1, 1, 1), (777, 64, 16, 2),
                                      (1030, 3, 4, 4), (513, 1, 16, 1)])
