@@ -667,9 +667,12 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// blocks of about n / 128 rows (at least 64, at most 768, so that V's staged
+// rows stay within 48 KB of shared memory in FP64)
 int panel_tv_blocks(int n) {
   int rows = (n + 127) / 128;
   rows = rows < 64 ? 64 : (rows + 7) / 8 * 8;
+  if (rows > 768) rows = 768;
   return (n + rows - 1) / rows;
 }
 
