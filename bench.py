@@ -72,7 +72,7 @@ def _args():
                     choices=["rank4_stream", "k_sweep", "iteration_p_sweep", "gd_regression",
                              "small_fp64", "ols_row_blocks", "iteration_adjoint", "serving",
                              "zipf_batches", "drift", "gemm", "iteration_p_sweep_n30000",
-                             "gd_regression_n30000", "ols_drift"],
+                             "gd_regression_n30000", "ols_drift", "serving_inflight"],
                     help="run one secondary section alone (no headline line): profiling")
     return ap.parse_args()
 
@@ -593,6 +593,7 @@ def run_ours(args):
         section("iteration_adjoint", lambda: iteration_adjoint(seed=rank))
     if rank == 0 and not args.no_serving:
         section("serving", lambda: serving_sweep(args, seed=rank))
+        section("serving_inflight", lambda: serving_inflight(args, seed=rank))
         section("zipf_batches", lambda: zipf_batches(args, seed=rank))
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -1344,6 +1345,46 @@ def serving_sweep(args, seed=0):
                     "refreshes, per view size, divided by the point's wall time"}
 
 
+def serving_inflight(args, seed=0, rate=1e5, count=2000, levels=(4, 8, 16, 32)):
+    """The serving workload past saturation (one open-loop trace at ``rate``)
+    for several bounds on the number of views refreshing at once: a server of
+    the same views per bound, the same trace replayed through each."""
+    import numpy as np
+    import torch
+    import linview_inputs as li
+    from paper_1403_6968_gb300 import Server
+
+    sizes = li.serving_views(args.serve_views, seed=seed)
+    mats = [li.power_matrix(n, seed=100 + i, dtype=np.float32) for i, n in enumerate(sizes)]
+    t_s, views, ranks, factors, offsets = li.serving_trace(sizes, count, rate, seed=seed + 7)
+    rows = []
+    for m in levels:
+        srv = Server(max_inflight=m, r_cap=8)
+        for a in mats:
+            srv.add_view(torch.from_numpy(a).cuda(), 16)
+        before = srv.stats()
+        srv.replay(t_s, views, ranks, factors, offsets)
+        srv.drain(timeout_s=300)
+        recs = srv.poll()
+        after = srv.stats()
+        srv.close()
+        torch.cuda.empty_cache()
+        lat = np.array([r["done_s"] - r["arrival_s"] for r in recs]) * 1e3
+        span = max(r["done_s"] for r in recs) - min(r["arrival_s"] for r in recs)
+        nref = after["refreshes"] - before["refreshes"]
+        rows.append({"max_inflight": m, "requests_per_s": count / span,
+                     "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)), "refreshes": nref,
+                     "mean_coalesced_rank": (after["coalesced_rank_sum"]
+                                             - before["coalesced_rank_sum"]) / max(nref, 1),
+                     "max_inflight_seen": after["max_inflight_seen"],
+                     "failed": after["failed"] - before["failed"]})
+    return {"views": len(sizes), "rate_per_s": rate, "requests": count, "r_cap": 8,
+            "rows": rows,
+            "note": "the same open-loop trace past saturation replayed through a server per "
+                    "bound on the views refreshing at once (each view on its own stream)"}
+
+
 def serving_view_costs(ns, seed=0, reps=5):
     """ms of one refresh of an A^16 view (the server's program: power, k = 16,
     r_max = 8) per view size and delta rank 1..8, each timed alone."""
@@ -1444,6 +1485,7 @@ def run_only(args):
            "ols_row_blocks": lambda: ols_sweep(),
            "iteration_adjoint": lambda: iteration_adjoint(),
            "serving": lambda: serving_sweep(args),
+           "serving_inflight": lambda: serving_inflight(args),
            "zipf_batches": lambda: zipf_batches(args),
            "gemm": lambda: gemm_section(args),
            "iteration_p_sweep_n30000": lambda: iteration_p_sweep(args, steps=3, n=30000),
