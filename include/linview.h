@@ -207,8 +207,10 @@ linview_status linview_apply_row_delta(linview_program* prog, int input_id, int6
 /*
  * OLS only: replace ``kr`` distinct rows of X (indices ``rows``, host array)
  * by ``new_rows`` (kr x n, row-major, ld).  Y is unchanged.  W is maintained
- * by block Woodbury with an FP64 2kr x 2kr core (the rank-2kr generalisation
- * of the two Sherman-Morrison steps of Example 3.3); beta = W X^T Y is
+ * by block Woodbury with a 2kr x 2kr core (the rank-2kr generalisation of the
+ * two Sherman-Morrison steps of Example 3.3), inverted in FP64 for FP64
+ * programs and as double-float pairs (Newton-Schulz, Gauss-Jordan fallback)
+ * for FP32 programs; beta = W X^T Y is
  * refreshed from the same factors (the delta of a product, Section 3.2), with
  * no further pass over W.
  * Errors: EINVAL, ESHAPE (kr > desc.k), ESINGULAR (latched, see linview_sync):
