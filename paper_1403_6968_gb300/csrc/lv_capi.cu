@@ -1577,8 +1577,9 @@ static linview_status iter_propagate_b(linview_program* p, int rb, cudaStream_t 
 // two products by V^T taken once on the refreshed T'_{i-1} = T_{i-1} +
 // D_{i-1}; then A += U V^T.  For dB = U_b V_b^T (U_b in K_0, V_b in the first
 // block of M; A unchanged):  D_1 = U_b V_b^T,  D_i = A D_{i-1} + U_b V_b^T,
-// and B += U_b V_b^T.  Each step is one n x n x p product with A (cuBLAS,
-// IEEE arithmetic), the rank-r term and T_i += D_i.  Column-major views:
+// and B += U_b V_b^T.  Each step is one n x n x p product with A (the own
+// split-TF32 GEMM, or one products pass over A when p is a few columns), the
+// rank-r term and T_i += D_i.  Column-major views:
 // T_i^T, D_i^T are p x n (ld ldT, ldD), A's row-major storage is A^T.
 template <typename T>
 static linview_status iter_propagate_hybrid(linview_program* p, int r, bool b_update,
