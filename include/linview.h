@@ -246,17 +246,29 @@ int linview_num_views(const linview_program* prog);
 linview_status linview_view_shape(const linview_program* prog, int view_id, int64_t* rows,
                                   int64_t* cols);
 
+/* Destinations of linview_read_view / linview_read_view_rows (dst_on_device). */
+enum {
+  LINVIEW_DST_HOST = 0,       /* host memory; the call synchronises the stream */
+  LINVIEW_DST_DEVICE = 1,     /* device memory; asynchronous on the stream */
+  LINVIEW_DST_HOST_ASYNC = 2  /* host memory, asynchronous on the stream: the caller
+                                 synchronises the stream (or an event recorded after
+                                 the call) before reading dst and keeps dst alive until
+                                 then; page-locked dst makes the copy overlap later work */
+};
+
 /*
  * Copy view ``view_id`` into dst (row-major, ld >= cols).  dst_on_device
- * selects device or host destination.  For a host destination the call
- * synchronises the stream before returning.
+ * selects the destination (LINVIEW_DST_*).  For LINVIEW_DST_HOST the call
+ * synchronises the stream before returning.  Errors: EINVAL (null, bad id or
+ * destination), ESHAPE (ld < cols).
  */
 linview_status linview_read_view(const linview_program* prog, int view_id, void* dst, int64_t ld,
                                  int dst_on_device, void* stream);
 
 /*
  * Copy rows [row0, row0 + nrows) of view ``view_id`` into dst (nrows x cols,
- * row-major, ld >= cols).  Same device/host rules as linview_read_view.
+ * row-major, ld >= cols).  Same destinations and synchronisation as
+ * linview_read_view.
  */
 linview_status linview_read_view_rows(const linview_program* prog, int view_id, int64_t row0,
                                       int64_t nrows, void* dst, int64_t ld, int dst_on_device,

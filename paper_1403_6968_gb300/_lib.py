@@ -26,6 +26,7 @@ MODEL_EXP, MODEL_LINEAR, MODEL_SKIP = 0, 1, 2
 STRATEGY_FACTORED, STRATEGY_HYBRID = 0, 1
 # linview_correction
 CORRECT_REEVAL, CORRECT_NEWTON = 0, 1
+DST_HOST, DST_DEVICE, DST_HOST_ASYNC = 0, 1, 2  # read destinations
 
 
 class ProgramDesc(C.Structure):

@@ -2532,13 +2532,16 @@ linview_status linview_read_view(const linview_program* p, int id, void* dst, in
                                  int dst_on_device, void* stream) {
   if (!p || !dst) return fail(LINVIEW_EINVAL, "null argument");
   if (id < 0 || id >= (int)p->views.size()) return fail(LINVIEW_EINVAL, "bad view id %d", id);
+  if (dst_on_device < LINVIEW_DST_HOST || dst_on_device > LINVIEW_DST_HOST_ASYNC)
+    return fail(LINVIEW_EINVAL, "bad destination %d", dst_on_device);
   const View& v = p->views[id];
   if (ld < v.cols) return fail(LINVIEW_ESHAPE, "ld %lld < cols %lld", (long long)ld, (long long)v.cols);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   LV_CUDA(cudaSetDevice(p->device));
+  const bool dev = dst_on_device == LINVIEW_DST_DEVICE;
   LV_CUDA(cudaMemcpy2DAsync(dst, ld * p->elem, v.ptr, v.ld * p->elem, v.cols * p->elem, v.rows,
-                            dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-  if (!dst_on_device) LV_CUDA(cudaStreamSynchronize(s));
+                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (dst_on_device == LINVIEW_DST_HOST) LV_CUDA(cudaStreamSynchronize(s));
   return LINVIEW_OK;
 }
 
@@ -2547,6 +2550,8 @@ linview_status linview_read_view_rows(const linview_program* p, int id, int64_t 
                                       void* stream) {
   if (!p || !dst) return fail(LINVIEW_EINVAL, "null argument");
   if (id < 0 || id >= (int)p->views.size()) return fail(LINVIEW_EINVAL, "bad view id %d", id);
+  if (dst_on_device < LINVIEW_DST_HOST || dst_on_device > LINVIEW_DST_HOST_ASYNC)
+    return fail(LINVIEW_EINVAL, "bad destination %d", dst_on_device);
   const View& v = p->views[id];
   if (row0 < 0 || nrows < 0 || row0 + nrows > v.rows)
     return fail(LINVIEW_EINVAL, "rows [%lld, %lld) outside the view", (long long)row0,
@@ -2558,8 +2563,10 @@ linview_status linview_read_view_rows(const linview_program* p, int id, int64_t 
     LV_CUDA(cudaMemcpy2DAsync(dst, ld * p->elem,
                               static_cast<const char*>(v.ptr) + (size_t)row0 * v.ld * p->elem,
                               v.ld * p->elem, v.cols * p->elem, nrows,
-                              dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-  if (!dst_on_device) LV_CUDA(cudaStreamSynchronize(s));
+                              dst_on_device == LINVIEW_DST_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                  : cudaMemcpyDeviceToHost,
+                              s));
+  if (dst_on_device == LINVIEW_DST_HOST) LV_CUDA(cudaStreamSynchronize(s));
   return LINVIEW_OK;
 }
 

@@ -215,15 +215,23 @@ class Program:
                1 if out.is_cuda else 0, _stream_ptr(stream))
         return out
 
-    def read_view_rows(self, vid, row0, nrows, out=None, stream=None):
+    def read_view_rows(self, vid, row0, nrows, out=None, stream=None, sync=True):
         """Rows [row0, row0+nrows) of a view into ``out`` (numpy or torch; host
-        or device); returns ``out``."""
+        or device); returns ``out``.  A host ``out`` is ready on return unless
+        ``sync`` is False: then the copy is queued on the stream and the caller
+        synchronises the stream (or an event recorded after the call) before
+        reading ``out``, which must stay alive until then (a pinned tensor lets
+        the copy overlap later work)."""
         rows, cols = self.view_shape(vid)
         if out is None:
             out = np.empty((nrows, cols), dtype=self.np_dtype)
         o = _Operand(out, self.np_dtype)
+        if o.keep is not out and not (hasattr(out, "data_ptr") and
+                                      o.keep.data_ptr() == out.data_ptr()):
+            raise ValueError("out must be a contiguous row-major array")
+        dst = o.on_device if (o.on_device or sync) else L.DST_HOST_ASYNC
         L.call("linview_read_view_rows", self.h, int(vid), int(row0), int(nrows), o.ptr, o.ld,
-               o.on_device, _stream_ptr(stream))
+               dst, _stream_ptr(stream))
         return out
 
     def read_view_host(self, vid, stream=None):

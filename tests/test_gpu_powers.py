@@ -263,6 +263,45 @@ def test_host_side_factors_and_errors():
     _check_all(prog, acur, k, False, 1e-5)             # failed calls changed nothing
 
 
+def test_read_rows_async_host_destination():
+    """LINVIEW_DST_HOST_ASYNC: the rows reach a pinned host buffer once the
+    stream is synchronised, equal to a synchronous read; an unknown
+    destination is EINVAL.  Two steps in flight, as the bench's e2e loop."""
+    import ctypes as C
+    from paper_1403_6968_gb300 import _lib as L
+    n, k = 640, 8
+    a = li.power_matrix(n, seed=31, dtype=np.float32)
+    prog = _prog("power", [_dev(a)], k=k, r_max=1)
+    acur = a.astype(np.float64)
+    bufs = [torch.empty((3, n), dtype=torch.float32).pin_memory() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+    cur = torch.cuda.current_stream()
+    seen = []
+    for t, (i, v) in enumerate(li.row_update_stream(n, 5, seed=32, dtype=np.float32)):
+        b = t % 2
+        prog.apply_row_delta(i, torch.from_numpy(v).pin_memory())
+        acur[i] += v.astype(np.float64)
+        prog.read_view_rows(3, 100 + t, 3, out=bufs[b], sync=False)
+        done[b].record(cur)
+        if t >= 1:
+            done[1 - b].synchronize()
+            seen.append((t - 1, bufs[1 - b].numpy().copy()))
+    done[b].synchronize()
+    seen.append((t, bufs[b].numpy().copy()))
+    # the last read matches a synchronous read of the same rows, and the
+    # A^8 rows agree with the oracle on the final A
+    assert np.array_equal(seen[-1][1], prog.read_view_rows(3, 100 + t, 3))
+    ref = op.reeval_powers(acur, k)[k]
+    assert rel_frob(seen[-1][1], ref[100 + t:103 + t]) <= 1e-4
+    lib = L.load()
+    dst = np.zeros((1, n), np.float32)
+    st = lib.linview_read_view_rows(prog.h, 3, 0, 1, C.c_void_p(dst.ctypes.data), n, 3, None)
+    assert st == L.EINVAL
+    with pytest.raises(ValueError):  # a strided out would receive nothing
+        prog.read_view_rows(3, 0, 1, out=np.zeros((1, 2 * n), np.float32)[:, ::2])
+    prog.close()
+
+
 def test_full_size_sampled_rows():
     """configs: A^16 and S' = sum_{i<=16} A^i, n=8192, FP32, row and rank-4
     updates; sampled rows of every view vs the oracle computed row by row."""
