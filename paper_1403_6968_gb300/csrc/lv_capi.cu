@@ -1220,6 +1220,7 @@ static linview_status exp_levels(linview_program* p, int r, int nlev, bool sums,
     LV_TRY(run_products_update<T>(p, pview(p, l), rh, U, Vh, U, Vh, s,
                                   fused ? p->Cpart : nullptr, /*allow_tc=*/true));
     AssembleParams a{};
+    a.status = p->status;
     a.n = n;
     a.r_h = rh;
     a.fs = fs;
@@ -1278,6 +1279,7 @@ static linview_status krylov_levels(linview_program* p, int bw, int nsteps, int 
     if (sums_r > 0 && view0 + j - 1 >= 1)
       LV_TRY(sums_update<T>(p, sview(p, view0 + j - 1), U, Vj, rh, sums_r, s));
     AssembleParams a{};
+    a.status = p->status;
     a.n = n;
     a.r_h = rh;
     a.r_out = bw;
@@ -1503,6 +1505,7 @@ static linview_status iter_propagate(linview_program* p, int r, cudaStream_t s) 
     // X = A K_0 on the old A, A += K_0 V^T in the same pass
     LV_TRY(run_fused<T>(p, a, kModeXU, r, K, nullptr, K, V1, p->Xpart, p->Ypart, s));
     AssembleParams as{};
+    as.status = p->status;
     as.n = n;
     as.r_h = r;
     as.fs = fs;
@@ -1893,6 +1896,7 @@ static linview_status iter_sk_propagate(linview_program* p, int r, cudaStream_t 
     LV_TRY(run_products_update<T>(p, ph, rh, U, Vh, U, Vh, s, fused ? p->Cpart : nullptr));
     if (l >= 1) LV_TRY(run_update<T>(p, ie_S(p, l), U, Wh, rh, s));  // dS'_h = U_h W^_h^T
     AssembleParams a{};
+    a.status = p->status;
     a.n = n;
     a.r_h = rh;
     a.fs = fs;

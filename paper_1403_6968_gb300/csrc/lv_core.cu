@@ -276,7 +276,11 @@ __global__ void __launch_bounds__(kThreads) assemble_kernel(const AssembleParams
                            : 0.0;
 #pragma unroll
     for (int o = 1; o < 8; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if ((lane & 7) == 0 && c2 < rh) Cc[c2] = (T)sum;
+    if ((lane & 7) == 0 && c2 < rh) {
+      Cc[c2] = (T)sum;
+      // every CTA sums the same core: the first one reports a non-finite entry
+      if (a.status && blockIdx.x == 0 && !isfinite(sum)) atomicOr(a.status, kStatusNonFinite);
+    }
   }
   // this warp's share of the strips, row ranges and columns of U_h
   T x = strided_sum<T, T>(Xp + (int64_t)c * a.part_cs + jj, a.xp_s, a.gC, warp);
@@ -336,7 +340,11 @@ __global__ void __launch_bounds__(kThreads) assemble_wide_kernel(const AssembleP
                            : 0.0;
 #pragma unroll
     for (int o = 1; o < 8; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if ((lane & 7) == 0 && c2 < rh) Cc[c2] = (T)sum;
+    if ((lane & 7) == 0 && c2 < rh) {
+      Cc[c2] = (T)sum;
+      // every CTA sums the same core: the first one reports a non-finite entry
+      if (a.status && blockIdx.x == 0 && !isfinite(sum)) atomicOr(a.status, kStatusNonFinite);
+    }
   }
   T x = strided_sum_all<T>(Xp + (int64_t)c * a.part_cs + jj, a.xp_s, a.gC);
   T y = Yp ? strided_sum_all<T>(Yp + (int64_t)c * a.part_cs + jj, a.yp_q, a.gR) : T(0);

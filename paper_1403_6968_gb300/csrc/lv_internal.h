@@ -183,6 +183,8 @@ struct AssembleParams {
   const void* Uh;         // U_h (n x r_h)
   void* Unew;             // destination of X_h + U_h C_h (n x r_h), = U arena + r_h columns
   void* Ynew;             // destination of Y_h (n x r_h), = V arena left of V_h
+  unsigned* status;       // device status word: a non-finite C_h entry latches
+                          // kStatusNonFinite (or null)
 };
 template <typename T>
 cudaError_t launch_assemble(const AssembleParams& a, cudaStream_t s);

@@ -263,6 +263,42 @@ def test_host_side_factors_and_errors():
     _check_all(prog, acur, k, False, 1e-5)             # failed calls changed nothing
 
 
+@pytest.mark.parametrize("prec,r", [("f32", 1), ("f64", 1), ("f32", 4)])
+def test_nonfinite_delta_is_reported(prec, r):
+    """A NaN in an update makes a factor core non-finite (at the first level
+    whose core involves it: C_2 = V_2^T U_2 carries P^T v); linview_sync
+    reports ENONFINITE once, and a program created afterwards is unaffected.
+    Rank 1 reaches the cores summed by the assembly (levels of <= 8 columns),
+    rank 4 also the stand-alone core reductions (16 and 32 columns)."""
+    from paper_1403_6968_gb300 import LinviewError
+    n, k = 256, 16
+    dt = _np(prec)
+    a = li.power_matrix(n, seed=41, dtype=dt)
+    prog = _prog("power", [_dev(a)], k=k, r_max=r, precision=prec)
+    if r == 1:
+        v = np.zeros(n, dt)
+        v[7] = np.nan
+        prog.apply_row_delta(3, _dev(v))
+    else:
+        (u, v), = li.lowrank_update_stream(n, r, 1, seed=42, dtype=dt)
+        v = v.copy()
+        v[5, 2] = np.inf
+        prog.apply_delta(_dev(u), _dev(v))
+    with pytest.raises(LinviewError) as e:
+        prog.sync()
+    assert e.value.name == "ENONFINITE"
+    prog.sync()  # reported once
+    prog.close()
+    fresh = _prog("power", [_dev(a)], k=k, r_max=r, precision=prec)
+    (i, v), = li.row_update_stream(n, 1, seed=43, dtype=dt)
+    fresh.apply_row_delta(i, _dev(v))
+    fresh.sync()
+    acur = a.astype(np.float64)
+    acur[i] += v.astype(np.float64)
+    _check_all(fresh, acur, k, False, TOL[prec])
+    fresh.close()
+
+
 def test_read_rows_async_host_destination():
     """LINVIEW_DST_HOST_ASYNC: the rows reach a pinned host buffer once the
     stream is synchronised, equal to a synchronous read; an unknown
