@@ -471,9 +471,16 @@ linview_status linview_estimate_device_bytes(const linview_program_desc* desc, i
  *   LINVIEW_POWER program: 0 = A, j = A^(2^j).
  * linview_server_submit: one request dA = U V^T for ``view``; U, V are n x
  *   rank FP32 row-major host arrays (ldu, ldv >= rank), copied before the
- *   call returns; 1 <= rank <= r_cap, else LINVIEW_ERANK.  arrival_s < 0
- *   stamps the current server time.  *ticket receives the request id
- *   (tickets count from 1 in submission order).
+ *   call returns; 1 <= rank <= n, else LINVIEW_ERANK.  Requests of rank <=
+ *   r_cap coalesce as described above.  A request of rank > r_cap is served
+ *   by re-evaluation (Section 4.2.2, "Re-evaluation"): when it is the oldest
+ *   request of its view, it and every request queued behind it are added to
+ *   A (update-only level passes on the device) and every view of the program
+ *   is recomputed from the new A (linview_reeval; its temporary operands are
+ *   device memory the admission budget does not reserve, so ENOMEM is
+ *   possible on a full GPU).  arrival_s < 0 stamps the current server time.
+ *   *ticket receives the request id (tickets count from 1 in submission
+ *   order).
  * linview_server_submit_row: a row update dA = e_row v^T (v: n floats, host,
  *   copied).  Row updates queued for one view coalesce by row: requests to a
  *   row already in the delta add their v to that row's column and no rank,
@@ -529,7 +536,7 @@ typedef struct {
   int64_t coalesced_rank_sum; /* sum of their ranks */
   int32_t views_resident, views_waiting;
   int32_t max_inflight_seen;  /* most views refreshing at the same time */
-  int32_t reserved;
+  int32_t reevals;            /* refreshes served by re-evaluation (a rank past r_cap) */
   int64_t bytes_used, bytes_budget;
 } linview_server_stats;
 

@@ -80,7 +80,7 @@ class ServerStats(C.Structure):
         ("views_resident", C.c_int32),
         ("views_waiting", C.c_int32),
         ("max_inflight_seen", C.c_int32),
-        ("reserved", C.c_int32),
+        ("reevals", C.c_int32),
         ("bytes_used", C.c_int64),
         ("bytes_budget", C.c_int64),
     ]

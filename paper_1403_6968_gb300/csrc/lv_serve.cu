@@ -9,6 +9,10 @@
 // [U_1 .. U_m][V_1 .. V_m]^T (Section 3.2: deltas in factored form sum by
 // concatenating their factors).  Each refresh is linview_apply_delta on the
 // view's stream, i.e. the propagation of Appendix A through the squarings.
+// A request of rank above the coalescing cap takes the re-evaluation strategy
+// instead (Section 4.2.2: apply the delta, recompute): it and every request
+// queued behind it are added to A by update-only level passes, and every view
+// of the program is recomputed from the new A (linview_reeval).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -69,6 +73,7 @@ struct ServedView {
   std::vector<Request> batch;
   std::vector<int64_t> batch_rows;  // distinct rows of the batch's row updates
   int32_t batch_rank = 0;
+  bool batch_reeval = false;        // the batch is served by re-evaluation
   double start = 0.0;
 };
 
@@ -185,7 +190,65 @@ void cancel_queue(linview_server* s, ServedView* v, double t) {
 
 // Pack the batch's factors into the view's pinned buffer ([U | V], each
 // n x R row-major) and issue the refresh; returns the status of the issue.
+// The re-evaluation batch: A += sum_j U_j V_j^T by update-only level passes
+// of at most 64 columns (the factors of all requests concatenated, column-major
+// in a stream-ordered device buffer), then every view recomputed from A.
+linview_status issue_reeval_batch(linview_server* s, ServedView* v) {
+  const int64_t n = v->n;
+  const int64_t ldf = (n + 63) / 64 * 64;
+  int64_t R = 0;
+  for (const Request& r : v->batch) R += r.rank;
+  std::vector<float> host((size_t)2 * ldf * R, 0.f);  // U columns, then V columns
+  float* hu = host.data();
+  float* hv = host.data() + (size_t)ldf * R;
+  int64_t c0 = 0;
+  for (const Request& r : v->batch) {
+    if (r.row >= 0) {
+      hu[c0 * ldf + r.row] = 1.f;
+      std::memcpy(hv + c0 * ldf, r.V, sizeof(float) * n);
+    } else {
+      for (int64_t i = 0; i < n; ++i)
+        for (int32_t c = 0; c < r.rank; ++c) {
+          hu[(c0 + c) * ldf + i] = r.U[i * r.rank + c];
+          hv[(c0 + c) * ldf + i] = r.V[i * r.rank + c];
+        }
+    }
+    c0 += r.rank;
+  }
+  void* A = nullptr;
+  int64_t lda = 0;
+  LV_TRY(linview_view_device_ptr(v->prog, 0, &A, &lda));
+  float* d = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&d), host.size() * sizeof(float), v->stream) !=
+      cudaSuccess) {
+    (void)cudaGetLastError();
+    return set_err(LINVIEW_ENOMEM, "no device memory for the re-evaluation batch's factors");
+  }
+  linview_status st = LINVIEW_OK;
+  if (cudaMemcpyAsync(d, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice,
+                      v->stream) != cudaSuccess) {
+    (void)cudaGetLastError();
+    st = set_err(LINVIEW_EDEVICE, "factor copy failed");
+  }
+  for (int64_t b = 0; b < R && st == LINVIEW_OK; b += 64) {
+    const int64_t w = R - b < 64 ? R - b : 64;
+    st = linview_level_pass(LINVIEW_F32, n, A, lda, d + b * ldf, d + (R + b) * ldf, ldf, w,
+                            nullptr, nullptr, 1, v->stream);
+  }
+  // (a copy from pageable memory has been staged when cudaMemcpyAsync
+  // returns, so ``host`` may go now)
+  if (cudaFreeAsync(d, v->stream) != cudaSuccess) (void)cudaGetLastError();
+  if (st != LINVIEW_OK) return st;
+  LV_TRY(linview_reeval(v->prog, v->stream));
+  if (cudaEventRecord(v->done, v->stream) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return set_err(LINVIEW_EDEVICE, "cudaEventRecord failed");
+  }
+  return LINVIEW_OK;
+}
+
 linview_status issue_batch(linview_server* s, ServedView* v) {
+  if (v->batch_reeval) return issue_reeval_batch(s, v);
   const int64_t n = v->n;
   const int R = v->batch_rank;
   float* U = v->pin;
@@ -319,6 +382,16 @@ void scheduler(linview_server* s) {
       std::vector<int64_t>& rows = pick->batch_rows;
       rows.clear();
       std::deque<Request> rest;
+      // a request past the rank cap: re-evaluation, which serves every
+      // request queued for the view at once
+      pick->batch_reeval = pick->queue.front().rank > s->r_cap;
+      if (pick->batch_reeval) {
+        for (Request& f : pick->queue) {
+          R += f.rank;
+          pick->batch.push_back(std::move(f));
+        }
+        pick->queue.clear();
+      }
       while (!pick->queue.empty()) {
         Request f = std::move(pick->queue.front());
         pick->queue.pop_front();
@@ -340,6 +413,7 @@ void scheduler(linview_server* s) {
       s->st.max_inflight_seen = std::max(s->st.max_inflight_seen, s->inflight);
       s->st.refreshes++;
       s->st.coalesced_rank_sum += R;
+      if (pick->batch_reeval) s->st.reevals++;
       lk.unlock();
       const linview_status st = issue_batch(s, pick);
       lk.lock();
@@ -469,7 +543,7 @@ linview_status linview_server_submit(linview_server* s, int32_t view, int32_t ra
                                      int64_t ldu, const void* V, int64_t ldv, double arrival_s,
                                      uint64_t* ticket) {
   if (!s || !U || !V) return set_err(LINVIEW_EINVAL, "null argument");
-  if (rank < 1 || rank > s->r_cap) return set_err(LINVIEW_ERANK, "rank must be in 1..r_cap");
+  if (rank < 1) return set_err(LINVIEW_ERANK, "rank must be >= 1");
   if (ldu < rank || ldv < rank) return set_err(LINVIEW_ESHAPE, "ldu/ldv < rank");
   int64_t n = 0;
   {
@@ -478,6 +552,7 @@ linview_status linview_server_submit(linview_server* s, int32_t view, int32_t ra
       return set_err(LINVIEW_EINVAL, "bad view id");
     n = s->views[view]->n;
   }
+  if (rank > n) return set_err(LINVIEW_ERANK, "rank must be <= n");
   Request r;
   r.rank = rank;
   r.own.resize((size_t)2 * n * rank);
@@ -535,8 +610,8 @@ linview_status linview_server_replay(linview_server* s, int64_t count, const dou
         return set_err(LINVIEW_EINVAL, "bad view id in the trace");
       if (rows && rows[i] >= s->views[view[i]]->n)
         return set_err(LINVIEW_EINVAL, "row out of range in the trace");
-      if (!(rows && rows[i] >= 0) && (rank[i] < 1 || rank[i] > s->r_cap))
-        return set_err(LINVIEW_ERANK, "rank outside 1..r_cap");
+      if (!(rows && rows[i] >= 0) && (rank[i] < 1 || rank[i] > s->views[view[i]]->n))
+        return set_err(LINVIEW_ERANK, "rank outside 1..n");
       if (i > 0 && t_s[i] < t_s[i - 1]) return set_err(LINVIEW_EINVAL, "t_s must be non-decreasing");
     }
   }

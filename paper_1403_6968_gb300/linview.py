@@ -475,10 +475,16 @@ class Server:
         return v.value
 
     def submit(self, view, U, V, arrival_s=-1.0):
+        """Request dA = U V^T (U, V: n x rank).  Up to r_cap columns it
+        coalesces with the view's queued requests; a wider request is served
+        by re-evaluation together with everything queued for the view."""
         u = np.ascontiguousarray(np.asarray(U, dtype=np.float32))
         w = np.ascontiguousarray(np.asarray(V, dtype=np.float32))
         if u.ndim == 1:
             u, w = u.reshape(-1, 1), w.reshape(-1, 1)
+        n = self._n.get(int(view), (None,))[0]
+        if u.ndim != 2 or u.shape != w.shape or (n is not None and u.shape[0] != n):
+            raise ValueError(f"U and V must both be n x rank (n = {n}), got {u.shape}, {w.shape}")
         t = C.c_uint64()
         L.call("linview_server_submit", self.h, int(view), u.shape[1], C.c_void_p(u.ctypes.data),
                u.shape[1], C.c_void_p(w.ctypes.data), w.shape[1], float(arrival_s), C.byref(t))
@@ -487,6 +493,9 @@ class Server:
     def submit_row(self, view, row, v, arrival_s=-1.0):
         """Row update dA = e_row v^T (coalesced by row with other queued ones)."""
         w = np.ascontiguousarray(np.asarray(v, dtype=np.float32).reshape(-1))
+        n = self._n.get(int(view), (None,))[0]
+        if n is not None and w.shape[0] != n:
+            raise ValueError(f"v must have n = {n} entries, got {w.shape[0]}")
         t = C.c_uint64()
         L.call("linview_server_submit_row", self.h, int(view), int(row),
                C.c_void_p(w.ctypes.data), float(arrival_s), C.byref(t))

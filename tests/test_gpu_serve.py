@@ -191,8 +191,9 @@ def _body_serve_remove_cancels_queue_and_errors():
     try:
         v = srv.add_view(li.power_matrix(n, seed=5, dtype=np.float32), 8)
         u, w = li.lowrank_update_stream(n, 5, 1, seed=6, dtype=np.float32)[0]
+        wide = np.zeros((n, n + 1), np.float32)
         with pytest.raises(P.LinviewError) as e:
-            srv.submit(v, u, w)  # rank 5 > r_cap 4
+            srv.submit(v, wide, wide)  # rank n + 1 > n (a rank past r_cap is re-evaluation)
         assert e.value.name == "ERANK"
         with pytest.raises(P.LinviewError) as e:
             srv.submit(7, u[:, :1], w[:, :1])
@@ -249,6 +250,59 @@ def _body_serve_row_coalescing():
     assert rel_frob(got, op.reeval_powers(af, K)[K]) <= TOL
 
 
+def _body_serve_over_cap_reeval():
+    """A request of rank above r_cap is served by re-evaluation (Sec. 4.2.2):
+    it and everything queued behind it go into A, every view is recomputed.
+    Mixed with in-cap requests and row updates on one view; the view equals
+    the oracle on A + all deltas, later in-cap requests refresh it
+    incrementally again, and factors of the wrong shape are refused."""
+    P = _pkg()
+    n = 384
+    a0 = li.power_matrix(n, seed=60, dtype=np.float32)
+    g = np.random.default_rng(61)
+    srv = P.Server(max_inflight=1, r_cap=2)
+    reqs = []
+    try:
+        v = srv.add_view(a0, K)
+        for rank in (1, 5, 2, 70, 1):   # 5 and 70 exceed r_cap; 70 spans two 64-column passes
+            u = (g.standard_normal((n, rank)) * 0.01).astype(np.float32)
+            w = (g.standard_normal((n, rank)) * 0.01).astype(np.float32)
+            srv.submit(v, u, w)
+            reqs.append((u, w))
+        i = 17
+        row = (g.standard_normal(n) * 0.01).astype(np.float32)
+        srv.submit_row(v, i, row)
+        e = np.zeros((n, 1), np.float32)
+        e[i] = 1
+        reqs.append((e, row.reshape(-1, 1)))
+        srv.drain(timeout_s=120)
+        recs = srv.poll()
+        st = srv.stats()
+        assert len(recs) == len(reqs) and all(r["status"] == 0 for r in recs), recs
+        assert st["reevals"] >= 1 and st["failed"] == 0
+        got = srv.program(v).read_view(L).cpu().numpy().astype(np.float64)
+        assert rel_frob(got, op.reeval_powers(_final_a(a0, reqs), K)[K]) <= TOL
+        # incremental refreshes resume after the re-evaluation
+        u = (g.standard_normal((n, 2)) * 0.01).astype(np.float32)
+        w = (g.standard_normal((n, 2)) * 0.01).astype(np.float32)
+        srv.submit(v, u, w)
+        reqs.append((u, w))
+        srv.drain(timeout_s=120)
+        assert srv.stats()["reevals"] == st["reevals"]
+        got = srv.program(v).read_view(L).cpu().numpy().astype(np.float64)
+        assert rel_frob(got, op.reeval_powers(_final_a(a0, reqs), K)[K]) <= TOL
+        for bad in ((np.zeros((n - 1, 2), np.float32),) * 2,
+                    (np.zeros((n, 2), np.float32), np.zeros((n, 3), np.float32))):
+            try:
+                srv.submit(v, *bad)
+            except ValueError:
+                pass
+            else:
+                raise AssertionError("wrong factor shapes accepted")
+    finally:
+        srv.close()
+
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -277,6 +331,10 @@ def test_serve_remove_cancels_queue_and_errors():
 
 def test_serve_row_coalescing():
     _run_child("serve_row_coalescing")
+
+
+def test_serve_over_cap_reeval():
+    _run_child("serve_over_cap_reeval")
 
 
 @pytest.mark.parametrize("kind,n,k,r_max,model", [
