@@ -169,28 +169,52 @@ class Program:
                C.byref(h))
         self.h = h
         self.desc = d
+        self.device_index = _torch().cuda.current_device() if _torch().cuda.is_available() else 0
         if allocator == "torch":
             _track(self)
         self.n = d.n
         self.k = d.k
 
     # -- updates -----------------------------------------------------------
+    def _check_side(self, *ops):
+        """Operands the library reads on the device: CUDA tensors on this
+        program's device (a wrong shape or device would become an
+        out-of-bounds access there instead of an error here)."""
+        for o in ops:
+            if o.on_device and o.keep.device.index != self.device_index:
+                raise ValueError(f"operand on {o.keep.device}, program on cuda:{self.device_index}")
+
     def apply_delta(self, U, V, input_id=0, stream=None):
+        """dX = U V^T for input ``input_id``: U is n x rank; V is n x rank for
+        A (input 0) and p x rank for B (input 1 of an iteration program)."""
         u = _Operand(U, self.np_dtype)
         v = _Operand(V, self.np_dtype)
         if u.on_device != v.on_device:
             raise ValueError("U and V must be on the same side")
+        if len(u.shape) != 2 or len(v.shape) != 2 or u.shape[1] != v.shape[1]:
+            raise ValueError(f"U and V must be 2-D with the same rank, got {u.shape}, {v.shape}")
+        v_rows = self.desc.p if (int(input_id) == 1 and self.desc.kind == L.ITERATION) else self.n
+        if u.shape[0] != self.n or v.shape[0] != v_rows:
+            raise ValueError(f"U must be {self.n} x rank and V {v_rows} x rank, "
+                             f"got {u.shape}, {v.shape}")
+        self._check_side(u, v)
         L.call("linview_apply_delta", self.h, input_id, u.shape[1], u.ptr, u.ld, v.ptr, v.ld,
                u.on_device, _stream_ptr(stream))
 
     def apply_row_delta(self, row, v, input_id=0, stream=None):
         o = _Operand(v, self.np_dtype)
+        if o.shape[0] * o.shape[1] != self.n:
+            raise ValueError(f"v must have n = {self.n} entries, got shape {o.shape}")
+        self._check_side(o)
         L.call("linview_apply_row_delta", self.h, input_id, int(row), o.ptr, o.on_device,
                _stream_ptr(stream))
 
     def apply_row_block(self, rows, new_rows, stream=None):
         rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
         o = _Operand(new_rows, self.np_dtype)
+        if o.shape != (len(rows), self.n):
+            raise ValueError(f"new_rows must be {len(rows)} x {self.n}, got {o.shape}")
+        self._check_side(o)
         L.call("linview_apply_row_block", self.h, len(rows),
                rows.ctypes.data_as(C.POINTER(C.c_int64)), o.ptr, o.ld, o.on_device,
                _stream_ptr(stream))
@@ -442,6 +466,13 @@ class _ServedProgram(Program):
         self.precision = L.F32
         self.np_dtype = np.float32
         self.n, self.k = n, k
+        self.device_index = _torch().cuda.current_device()
+
+    def _refuse(self, *a, **kw):
+        raise RuntimeError("a served view is updated through Server.submit / submit_row "
+                           "(the server's scheduler thread issues its work)")
+
+    apply_delta = apply_row_delta = apply_row_block = _refuse
 
     def close(self):
         self.h = None
