@@ -176,6 +176,26 @@ class Program:
         self.k = d.k
 
     # -- updates -----------------------------------------------------------
+    def _check_tensor(self, t, shape, name, device_only=True):
+        """A tensor the library reads or writes through a raw pointer: the
+        program's dtype, unit inner stride, exactly ``shape``, and a CUDA
+        tensor on the program's device (or host memory where allowed)."""
+        torch = _torch()
+        want = torch.float64 if self.precision == L.F64 else torch.float32
+        if not isinstance(t, torch.Tensor) or t.dim() != 2:
+            raise ValueError(f"{name} must be a 2-D tensor")
+        if t.dtype != want:
+            raise ValueError(f"{name} has dtype {t.dtype}, the program computes in {want}")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} must be {tuple(shape)}, got {tuple(t.shape)}")
+        if t.shape[0] > 0 and t.shape[1] > 0 and t.stride(1) != 1:
+            raise ValueError(f"{name} must have unit inner stride")
+        if t.is_cuda:
+            if t.device.index != self.device_index:
+                raise ValueError(f"{name} is on {t.device}, the program on cuda:{self.device_index}")
+        elif device_only:
+            raise ValueError(f"{name} must be a CUDA tensor")
+
     def _check_side(self, *ops):
         """Operands the library reads on the device: CUDA tensors on this
         program's device (a wrong shape or device would become an
@@ -235,6 +255,7 @@ class Program:
         if out is None:
             dt = torch.float64 if self.precision == L.F64 else torch.float32
             out = torch.empty((rows, cols), dtype=dt, device="cuda")
+        self._check_tensor(out, (rows, cols), "out", device_only=False)
         L.call("linview_read_view", self.h, int(vid), C.c_void_p(out.data_ptr()), out.stride(0),
                1 if out.is_cuda else 0, _stream_ptr(stream))
         return out
@@ -253,6 +274,9 @@ class Program:
         if o.keep is not out and not (hasattr(out, "data_ptr") and
                                       o.keep.data_ptr() == out.data_ptr()):
             raise ValueError("out must be a contiguous row-major array")
+        if tuple(o.shape) != (int(nrows), cols):
+            raise ValueError(f"out must be {(int(nrows), cols)}, got {tuple(o.shape)}")
+        self._check_side(o)
         dst = o.on_device if (o.on_device or sync) else L.DST_HOST_ASYNC
         L.call("linview_read_view_rows", self.h, int(vid), int(row0), int(nrows), o.ptr, o.ld,
                dst, _stream_ptr(stream))
@@ -283,6 +307,11 @@ class Program:
 
     # -- adjoints ----------------------------------------------------------
     def adjoint_iteration(self, dA=None, dB=None, stream=None):
+        n, p = self.n, self.desc.p
+        if dA is not None:
+            self._check_tensor(dA, (n, n), "dA")
+        if dB is not None:
+            self._check_tensor(dB, (n, p), "dB")
         pa = C.c_void_p(dA.data_ptr()) if dA is not None else None
         pb = C.c_void_p(dB.data_ptr()) if dB is not None else None
         L.call("linview_adjoint_iteration", self.h, pa, dA.stride(0) if dA is not None else 0,
@@ -290,6 +319,12 @@ class Program:
 
     def adjoint_iteration_seed(self, Gk, dA=None, dB=None, dT0=None, stream=None):
         """Vector-Jacobian product of (A, B, T_0) -> T_k at dL/dT_k = Gk (CUDA tensors)."""
+        n, p = self.n, self.desc.p
+        self._check_tensor(Gk, (n, p), "Gk")
+        for t, shape, name in ((dA, (n, n), "dA"), (dB, (n, p), "dB"), (dT0, (n, p), "dT0")):
+            if t is not None:
+                self._check_tensor(t, shape, name)
+
         def ptr(t):
             return (C.c_void_p(t.data_ptr()), t.stride(0)) if t is not None else (None, 0)
         (pa, la), (pb, lb), (pt, lt) = ptr(dA), ptr(dB), ptr(dT0)
@@ -297,6 +332,8 @@ class Program:
                pa, la, pb, lb, pt, lt, _stream_ptr(stream))
 
     def adjoint_power(self, G, dA, stream=None):
+        self._check_tensor(G, (self.n, self.n), "G")
+        self._check_tensor(dA, (self.n, self.n), "dA")
         L.call("linview_adjoint_power", self.h, C.c_void_p(G.data_ptr()), G.stride(0),
                C.c_void_p(dA.data_ptr()), dA.stride(0), _stream_ptr(stream))
 

@@ -78,3 +78,26 @@ def test_wrong_dtype_is_refused():
     prog = shell(n=8)
     with pytest.raises(TypeError):
         prog.apply_delta(np.zeros((8, 1)), np.zeros((8, 1)))   # FP64 factors, FP32 program
+
+
+def test_read_and_adjoint_operands():
+    """read_view / read_view_rows destinations and the adjoints' tensors:
+    exact shape, the program's dtype, unit inner stride; the adjoints take
+    CUDA tensors only (a host tensor here is refused before any call)."""
+    import torch
+    prog = shell(kind=L.ITERATION, n=8, p=3)
+    prog.view_shape = lambda vid: (8, 3)   # the shell has no device program to ask
+    for bad in (torch.zeros((8, 2)), torch.zeros((8, 3), dtype=torch.float64),
+                torch.zeros((3, 8)).t()):
+        with pytest.raises(ValueError):
+            prog.read_view(1, out=bad, stream=NullStream())
+    with pytest.raises(ValueError):
+        prog.read_view_rows(1, 0, 2, out=np.zeros((3, 3), np.float32), stream=NullStream())
+    assert reaches_library(prog.read_view_rows, 1, 0, 2, out=np.zeros((2, 3), np.float32))
+    g = torch.zeros((8, 3))
+    with pytest.raises(ValueError):        # host tensors: the adjoints write device memory
+        prog.adjoint_iteration_seed(g, dA=torch.zeros((8, 8)), stream=NullStream())
+    with pytest.raises(ValueError):
+        prog.adjoint_power(torch.zeros((8, 8)), torch.zeros((8, 8)), stream=NullStream())
+    with pytest.raises(ValueError):
+        prog.adjoint_iteration(dA=torch.zeros((8, 7)), stream=NullStream())
