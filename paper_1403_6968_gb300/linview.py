@@ -151,6 +151,14 @@ class Program:
         d.skip = int(skip)
         d.strategy = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
         d.correction = CORRECTIONS[correction] if isinstance(correction, str) else int(correction)
+        # the library reads each input in place with these shapes
+        want = {L.POWER: [(d.n, d.n)], L.POWER_SUM: [(d.n, d.n)],
+                L.ITERATION: [(d.n, d.n), (d.n, d.p), (d.n, d.p)],
+                L.OLS: [(d.m, d.n), (d.m, d.p)]}.get(d.kind)
+        if want is not None and (len(ops) != len(want) or
+                                 any(tuple(o.shape) != w for o, w in zip(ops, want))):
+            raise ValueError(f"{kind} inputs must have shapes {want}, got "
+                             f"{[tuple(o.shape) for o in ops]}")
         if allocator == "torch":
             torch = _torch()
             fa, ff = _torch_allocator()
@@ -534,6 +542,8 @@ class Server:
 
     def add_view(self, A, k):
         a = _Operand(A, np.float32)
+        if len(a.shape) != 2 or a.shape[0] != a.shape[1]:
+            raise ValueError(f"A must be square, got {a.shape}")
         if a.on_device:  # the server reads A on its own stream
             _torch().cuda.current_stream().synchronize()
         v = C.c_int32()
@@ -582,6 +592,17 @@ class Server:
         rows_a = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
         if factors.dtype != np.float32 or not factors.flags.c_contiguous:
             raise TypeError("factors must be a contiguous float32 array")
+        m = len(t_s)
+        if not (len(views) == len(ranks) == len(offsets) == m) or \
+                (rows_a is not None and len(rows_a) != m):
+            raise ValueError("t_s, views, ranks, offsets (and rows) must have one entry per request")
+        # every request's factors lie inside ``factors`` (the library reads
+        # them in place): n floats for a row update, 2 n rank otherwise
+        nv = np.array([self._n.get(int(v), (0,))[0] for v in views], dtype=np.int64)
+        is_row = np.zeros(m, bool) if rows_a is None else rows_a >= 0
+        need = np.where(is_row, nv, 2 * nv * ranks.astype(np.int64))
+        if m and (np.any(offsets < 0) or np.any(offsets + need > factors.size)):
+            raise ValueError("a request's factors reach past the end of ``factors``")
         self._keep.append(factors)
         L.call("linview_server_replay", self.h, len(t_s), C.c_void_p(t_s.ctypes.data),
                C.c_void_p(views.ctypes.data), C.c_void_p(ranks.ctypes.data),

@@ -101,3 +101,22 @@ def test_read_and_adjoint_operands():
         prog.adjoint_power(torch.zeros((8, 8)), torch.zeros((8, 8)), stream=NullStream())
     with pytest.raises(ValueError):
         prog.adjoint_iteration(dA=torch.zeros((8, 7)), stream=NullStream())
+
+
+def test_program_inputs_and_replay_factors_are_checked():
+    """Program inputs must have the kind's shapes (the library reads them in
+    place); a replay trace whose factors reach past its array is refused."""
+    from paper_1403_6968_gb300.linview import Server
+    with pytest.raises(ValueError):
+        Program("power", [z(8, 9)], k=4)
+    with pytest.raises(ValueError):
+        Program("iteration", [z(8, 8), z(8, 3), z(7, 3)], k=4)
+    with pytest.raises(ValueError):
+        Program("ols", [z(20, 8), z(19, 2)], k=2)
+    srv = object.__new__(Server)
+    srv.h, srv._n, srv._keep = None, {0: (16, 16)}, []
+    f = np.zeros(2 * 16 * 3, np.float32)
+    with pytest.raises(ValueError):   # rank 3 at offset 1 needs 96 floats from there
+        srv.replay([0.0], [0], [3], f, [1])
+    with pytest.raises(ValueError):
+        srv.replay([0.0, 0.1], [0], [3], f, [0])
