@@ -29,6 +29,12 @@
  *    them in linview_destroy; it never frees caller memory.
  *  - Errors are reported by status code only (no exceptions cross the ABI).
  *    linview_last_error() returns a thread-local message for the last failure.
+ *  - Every pointer an entry point takes as device memory (on_device = 1, a
+ *    device destination, the stand-alone passes' and GEMM's operands) must be
+ *    device or managed memory of the current (or the program's) device; other
+ *    memory is EINVAL before any work is queued.  Sizes cannot be checked
+ *    from a pointer: the caller keeps every buffer at least as large as the
+ *    shapes and leading dimensions it passes.
  *    Problems detected on the device (a non-finite factor core, a singular
  *    Woodbury core, an expired bounded wait) are latched in a device status
  *    word and returned by the next linview_sync() on that program.

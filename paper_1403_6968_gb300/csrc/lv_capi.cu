@@ -51,6 +51,23 @@ linview_status lv_set_error(linview_status st, const char* fmt, ...) {
   g_err = buf;
   return st;
 }
+
+// A pointer that kernels will read or write must be device (or managed)
+// memory of ``device``: a host pointer handed over as device memory, or
+// memory of another GPU, would be an invalid device access, so it is EINVAL
+// here instead (a host-side query; null pointers are the caller's check).
+linview_status check_dev_ptr(const void* ptr, int device, const char* name) {
+  if (!ptr) return LINVIEW_OK;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return lv_set_error(LINVIEW_EINVAL, "%s is not device memory", name);
+  }
+  if (a.type == cudaMemoryTypeManaged) return LINVIEW_OK;
+  if (a.type != cudaMemoryTypeDevice || a.device != device)
+    return lv_set_error(LINVIEW_EINVAL, "%s is not device memory of device %d", name, device);
+  return LINVIEW_OK;
+}
 }  // namespace lv
 
 #define LV_CUDA(expr)                                                                     \
@@ -2406,6 +2423,11 @@ linview_status linview_create_program(const linview_program_desc* desc, const vo
     (void)cudaGetLastError();
     return fail(LINVIEW_EDEVICE, "no CUDA device");
   }
+  if (inputs_on_device) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (int i = 0; i < ninputs; ++i) LV_TRY(check_dev_ptr(inputs[i], cur, "an input"));
+  }
   linview_program* p = new linview_program();
   p->d = *desc;
   p->elem = desc->precision == LINVIEW_F64 ? 8 : 4;
@@ -2543,6 +2565,7 @@ linview_status linview_read_view(const linview_program* p, int id, void* dst, in
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   LV_CUDA(cudaSetDevice(p->device));
   const bool dev = dst_on_device == LINVIEW_DST_DEVICE;
+  if (dev) LV_TRY(check_dev_ptr(dst, p->device, "dst"));
   LV_CUDA(cudaMemcpy2DAsync(dst, ld * p->elem, v.ptr, v.ld * p->elem, v.cols * p->elem, v.rows,
                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   if (dst_on_device == LINVIEW_DST_HOST) LV_CUDA(cudaStreamSynchronize(s));
@@ -2561,6 +2584,7 @@ linview_status linview_read_view_rows(const linview_program* p, int id, int64_t 
     return fail(LINVIEW_EINVAL, "rows [%lld, %lld) outside the view", (long long)row0,
                 (long long)(row0 + nrows));
   if (ld < v.cols) return fail(LINVIEW_ESHAPE, "ld < cols");
+  if (dst_on_device == LINVIEW_DST_DEVICE) LV_TRY(check_dev_ptr(dst, p->device, "dst"));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   LV_CUDA(cudaSetDevice(p->device));
   if (nrows > 0)
@@ -2795,6 +2819,10 @@ linview_status linview_apply_delta(linview_program* p, int input_id, int64_t ran
   if (rank < 1) return fail(LINVIEW_EINVAL, "rank must be >= 1");
   if (rank > p->d.r_max) return fail(LINVIEW_ERANK, "rank %lld > r_max %d", (long long)rank, p->d.r_max);
   if (ldu < rank || ldv < rank) return fail(LINVIEW_ESHAPE, "ldu/ldv < rank");
+  if (on_device) {
+    LV_TRY(check_dev_ptr(U, p->device, "U"));
+    LV_TRY(check_dev_ptr(V, p->device, "V"));
+  }
   LV_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (b_update) return apply_b_delta(p, (int)rank, U, ldu, V, ldv, on_device, s);
@@ -2835,6 +2863,7 @@ linview_status linview_apply_row_delta(linview_program* p, int input_id, int64_t
   if (input_id != 0) return fail(LINVIEW_EUNSUPPORTED, "only input 0 (A) has a trigger");
   const int64_t n = p->d.n;
   if (row < 0 || row >= n) return fail(LINVIEW_EINVAL, "row %lld out of range", (long long)row);
+  if (on_device) LV_TRY(check_dev_ptr(v, p->device, "v"));
   LV_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   LV_CUDA(cudaMemcpyAsync(v_dst(p, 1), v, n * p->elem,
@@ -2864,6 +2893,7 @@ linview_status linview_apply_row_block(linview_program* p, int64_t kr, const int
     for (int64_t j = 0; j < i; ++j)
       if (rows[j] == rows[i]) return fail(LINVIEW_EINVAL, "row indices must be distinct");
   }
+  if (on_device) LV_TRY(check_dev_ptr(new_rows, p->device, "new_rows"));
   LV_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // stage: the row indices, and the new rows as U's first kr columns
@@ -2924,6 +2954,10 @@ static linview_status adjoint_iteration(linview_program* p, const void* Gk, int6
   const int k = p->d.k;
   if ((dA && ld_dA < n) || (dB && ld_dB < pp) || (Gk && ldg < pp) || (dT0 && ld_dT0 < pp))
     return fail(LINVIEW_ESHAPE, "bad leading dims");
+  LV_TRY(check_dev_ptr(Gk, p->device, "Gk"));
+  LV_TRY(check_dev_ptr(dA, p->device, "dA"));
+  LV_TRY(check_dev_ptr(dB, p->device, "dB"));
+  LV_TRY(check_dev_ptr(dT0, p->device, "dT0"));
   LV_CUDA(cudaSetDevice(p->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!p->Gpanel) {
@@ -3041,6 +3075,8 @@ linview_status linview_adjoint_power(linview_program* p, const void* G, int64_t 
   if (!p || !G || !dA) return fail(LINVIEW_EINVAL, "null argument");
   if (p->d.kind != LINVIEW_POWER && p->d.kind != LINVIEW_POWER_SUM)
     return fail(LINVIEW_EINVAL, "not a power program");
+  LV_TRY(check_dev_ptr(G, p->device, "G"));
+  LV_TRY(check_dev_ptr(dA, p->device, "dA"));
   if (p->d.model != LINVIEW_MODEL_EXP)
     return fail(LINVIEW_EUNSUPPORTED, "the power adjoint runs on the squaring chain (exponential model)");
   const int64_t n = p->d.n;
@@ -3089,6 +3125,9 @@ linview_status linview_gemm(int precision, int ta, int tb, int64_t M, int64_t N,
   linview_program tmp;  // borrowed machinery, no views owned
   tmp.elem = precision == LINVIEW_F64 ? 8 : 4;
   cudaGetDevice(&tmp.device);
+  LV_TRY(check_dev_ptr(A, tmp.device, "A"));
+  LV_TRY(check_dev_ptr(B, tmp.device, "B"));
+  LV_TRY(check_dev_ptr(C, tmp.device, "C"));
   cudaDeviceGetAttribute(&tmp.sms, cudaDevAttrMultiProcessorCount, tmp.device);
   void* work = nullptr;
   LV_TRY(talloc(&tmp, kGemmWorkBytes + 256, &work, s));
@@ -3131,6 +3170,11 @@ linview_status linview_level_pass(int precision, int64_t n, void* P, int64_t ldp
   linview_program tmp;  // borrowed machinery, no views owned
   tmp.elem = e;
   cudaGetDevice(&tmp.device);
+  {
+    const void* ptrs[5] = {P, U, V, X, Y};
+    const char* names[5] = {"P", "U", "V", "X", "Y"};
+    for (int i = 0; i < 5; ++i) LV_TRY(check_dev_ptr(ptrs[i], tmp.device, names[i]));
+  }
   cudaDeviceGetAttribute(&tmp.sms, cudaDevAttrMultiProcessorCount, tmp.device);
   View v;
   v.ptr = P;

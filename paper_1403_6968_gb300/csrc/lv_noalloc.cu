@@ -37,6 +37,9 @@
 namespace lv {
 // sets the thread-local message returned by linview_last_error (lv_capi.cu)
 linview_status lv_set_error(linview_status st, const char* fmt, ...);
+// EINVAL unless a non-null ``ptr`` is device or managed memory of ``device``
+// (lv_capi.cu)
+linview_status check_dev_ptr(const void* ptr, int device, const char* name);
 }  // namespace lv
 
 namespace {
@@ -162,6 +165,14 @@ extern "C" linview_status linview_level_pass_noalloc(int precision, int64_t n, v
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     (void)cudaGetLastError();
     return lv_set_error(LINVIEW_EDEVICE, "no CUDA device");
+  }
+  {
+    const void* ptrs[5] = {P, U, V, X, Y};
+    const char* names[5] = {"P", "U", "V", "X", "Y"};
+    for (int i = 0; i < 5; ++i) {
+      const linview_status st = check_dev_ptr(ptrs[i], dev, names[i]);
+      if (st != LINVIEW_OK) return st;
+    }
   }
   // scratch layout: [status word | row-sum partials | column-sum partials]
   const PassGeom g = fused_geom(e, (int)n, sms);

@@ -299,6 +299,34 @@ def test_nonfinite_delta_is_reported(prec, r):
     fresh.close()
 
 
+def test_device_pointer_flags_are_checked():
+    """Entry points that take device pointers refuse host memory flagged as
+    device memory with EINVAL before any launch.  The host memory here is
+    page-locked, which kernels could read through unified addressing, so the
+    test cannot fault the GPU even if a check were missing; the views are
+    unchanged afterwards."""
+    import ctypes as C
+    from paper_1403_6968_gb300 import _lib as L
+    lib = L.load()
+    n, k = 64, 4
+    a = li.power_matrix(n, seed=71, dtype=np.float32)
+    prog = _prog("power", [_dev(a)], k=k, r_max=2)
+    before = prog.read_view_host(2)
+    host = torch.zeros((n, n), dtype=torch.float32).pin_memory()
+    hp = C.c_void_p(host.data_ptr())
+    dev = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    dp = C.c_void_p(dev.data_ptr())
+    assert lib.linview_apply_delta(prog.h, 0, 2, hp, n, hp, n, 1, None) == L.EINVAL
+    assert lib.linview_apply_row_delta(prog.h, 0, 3, hp, 1, None) == L.EINVAL
+    assert lib.linview_read_view(prog.h, 0, hp, n, L.DST_DEVICE, None) == L.EINVAL
+    assert lib.linview_level_pass(L.F32, n, hp, n, dp, dp, n, 2, None, None, 1, None) == L.EINVAL
+    assert lib.linview_level_pass(L.F32, n, dp, n, hp, dp, n, 2, None, None, 1, None) == L.EINVAL
+    assert lib.linview_gemm(L.F32, 0, 0, n, n, n, 1.0, dp, n, hp, n, 0.0, dp, n, None) == L.EINVAL
+    prog.sync()
+    assert np.array_equal(prog.read_view_host(2), before)
+    prog.close()
+
+
 def test_read_rows_async_host_destination():
     """LINVIEW_DST_HOST_ASYNC: the rows reach a pinned host buffer once the
     stream is synchronised, equal to a synchronous read; an unknown
