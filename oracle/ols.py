@@ -16,6 +16,13 @@ Z = X^T X and W = Z^{-1}.
   Replacing rows R of X by X'_R gives U = [X'_R^T, X_R^T], c = (+1..., -1...),
   since dZ = X'_R^T X'_R - X_R^T X_R.  The 2k x 2k core is solved by LU with
   partial pivoting (numpy.linalg.solve); it is indefinite, so not Cholesky.
+* residual correction of the maintained W (the paper maintains W = Z^{-1},
+  Section 4.1, and leaves its rounding drift open; the correction is the
+  Newton-Schulz iteration for a matrix inverse, Schulz 1933): one step
+      W <- W + W (I - Z W),
+  whose residual is the square of the old one, I - Z W' = (I - Z W)^2; and
+  the matching refinement of beta = W X^T Y:
+      beta <- beta + W (X^T Y - Z beta).
 """
 from __future__ import annotations
 
@@ -62,6 +69,21 @@ def woodbury(w, u, c):
     g = w @ u
     m = np.diag(1.0 / c) + u.T @ g
     return w - g @ np.linalg.solve(m, g.T)
+
+
+def newton_schulz_step(w, z):
+    """One Newton-Schulz step toward Z^{-1}: W + W (I - Z W)."""
+    w = np.asarray(w, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    return w + w @ (np.eye(w.shape[0]) - z @ w)
+
+
+def refine_beta(w, beta, xty, z):
+    """One refinement step of beta for Z beta = X^T Y with the approximate
+    inverse W: beta + W (X^T Y - Z beta)."""
+    w = np.asarray(w, dtype=np.float64)
+    beta = np.asarray(beta, dtype=np.float64)
+    return beta + w @ (np.asarray(xty, dtype=np.float64) - np.asarray(z, dtype=np.float64) @ beta)
 
 
 class IncrementalOLS:

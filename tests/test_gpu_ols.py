@@ -173,12 +173,14 @@ def test_newton_correction_step(k, count):
     b0 = prog.read_view_host(1).astype(np.float64)
     z = ref.x.T @ ref.x
     fresh = oo.reeval(ref.x, ref.y)
-    step = w0 + w0 @ (np.eye(n) - z @ w0)
+    step = oo.newton_schulz_step(w0, z)
     prog.correct()
     prog.sync()
     w1 = prog.read_view_host(0).astype(np.float64)
     b1 = prog.read_view_host(1).astype(np.float64)
     assert rel_frob(w1, step) <= 2e-7
+    # beta: one refinement step with the corrected W (the program's own)
+    assert rel_frob(b1, oo.refine_beta(w1, b0, ref.xty, z)) <= 2e-7
     assert rel_frob(w1, fresh["W"]) <= 1.05 * rel_frob(w0, fresh["W"]) + 1e-7
     assert rel_frob(b1, fresh["beta"]) <= 1.05 * rel_frob(b0, fresh["beta"]) + 1e-7
 

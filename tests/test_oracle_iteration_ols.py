@@ -203,6 +203,38 @@ def test_ols_inputs_are_ill_conditioned():
     assert 5e3 < kappa < 1e5
 
 
+def test_newton_schulz_step_pins():
+    """The residual-correction step, pinned by what it must satisfy rather
+    than by its formula: the exact inverse is a fixed point; from a perturbed
+    inverse the new residual I - Z W' equals the square of the old one
+    (quadratic convergence), so a few steps reach the library inverse; the
+    beta refinement with the exact W lands on the solution of Z beta = X^T Y
+    from any start.  A dropped factor W, a sign error or Z W for W Z breaks
+    one of these (Z and W do not commute once W is perturbed)."""
+    x, y, _ = li.ols_inputs(400, 30, 3, seed=5)
+    z = x.T @ x
+    w = np.linalg.inv(z)
+    assert rel_frob(oo.newton_schulz_step(w, z), w) <= 1e-9
+    g = np.random.default_rng(6)
+    # W0 = W (I + d R): residual I - Z W0 = -d R (norm ~ 1e-2, inside the
+    # iteration's region of convergence); not symmetric, so Z W0 != W0 Z
+    w0 = w @ (np.eye(30) + 1e-3 * g.standard_normal((30, 30)))
+    r0 = np.eye(30) - z @ w0
+    w1 = oo.newton_schulz_step(w0, z)
+    assert rel_frob(np.eye(30) - z @ w1, r0 @ r0) <= 1e-8
+    wk = w0
+    for _ in range(4):
+        wk = oo.newton_schulz_step(wk, z)
+    assert rel_frob(wk, w) <= 1e-9 < rel_frob(w0, w)
+    xty = x.T @ y
+    beta = np.linalg.lstsq(x, y, rcond=None)[0]
+    start = beta + g.standard_normal(beta.shape)
+    assert rel_frob(oo.refine_beta(w, start, xty, z), beta) <= 1e-8
+    # with an approximate W the refinement contracts the error by I - W Z
+    b1 = oo.refine_beta(w0, start, xty, z)
+    assert rel_frob(b1 - beta, (np.eye(30) - w0 @ z) @ (start - beta)) <= 1e-8
+
+
 # ------------------------------------------------- iteration, exponential model
 @pytest.mark.parametrize("n,p,k", [(9, 3, 16), (6, 1, 2), (7, 4, 8)])
 def test_exp_reeval_matches_linear_at_powers_of_two(n, p, k):
