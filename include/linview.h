@@ -315,6 +315,15 @@ linview_status linview_check_bounded_wait(int64_t limit_ns, void* stream, int64_
 
 linview_status linview_sync(linview_program* prog, void* stream);
 
+/*
+ * Capture the per-update propagation graphs of ranks 1..max_rank now, ahead
+ * of the first update of each rank (which would otherwise capture it): a
+ * warm-up for latency-sensitive callers.  Queues no work.  Power, power-sum
+ * and iteration programs (updates to A); a no-op for OLS.  Errors: EINVAL,
+ * ERANK (max_rank outside 1..r_max), EDEVICE.
+ */
+linview_status linview_prepare_updates(linview_program* prog, int32_t max_rank, void* stream);
+
 void linview_destroy(linview_program* prog);
 const char* linview_last_error(void);
 

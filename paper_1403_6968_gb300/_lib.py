@@ -114,6 +114,7 @@ _SIGS = [
     ("linview_correct", _I, [_P, _P]),
     ("linview_set_reeval_mode", _I, [_P, _I]),
     ("linview_sync", _I, [_P, _P]),
+    ("linview_prepare_updates", _I, [_P, _I, _P]),
     ("linview_check_bounded_wait", _I, [_I64, _P, C.POINTER(_I64)]),
     ("linview_destroy", None, [_P]),
     ("linview_last_error", C.c_char_p, []),

@@ -2714,25 +2714,32 @@ static linview_status capture_graph(linview_program* p, int r, bool inst,
   return LINVIEW_OK;
 }
 
-static linview_status graph_propagate(linview_program* p, int r, cudaStream_t s) {
+// The graphs of key r (captured on first use), indices into p->graphs.
+static linview_status graphs_for(linview_program* p, int r, bool inst, std::vector<size_t>* idx) {
   if (!p->gstream) {
     LV_CUDA(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
     LV_CUDA(cudaEventCreateWithFlags(&p->gev_in, cudaEventDisableTiming));
     LV_CUDA(cudaEventCreateWithFlags(&p->gev_out, cudaEventDisableTiming));
   }
-  const bool inst = p->prof;
-  std::vector<size_t> idx;
+  idx->clear();
   for (size_t i = 0; i < p->graphs.size(); ++i)
-    if (p->graphs[i].r == r && p->graphs[i].instrumented == inst) idx.push_back(i);
-  if (idx.empty()) {
+    if (p->graphs[i].r == r && p->graphs[i].instrumented == inst) idx->push_back(i);
+  if (idx->empty()) {
     const int copies = inst ? kProfCopies : 1;
     for (int c = 0; c < copies; ++c) {
       linview_program::GraphEntry ge;
       LV_TRY(capture_graph(p, r, inst, &ge));
       p->graphs.push_back(std::move(ge));
-      idx.push_back(p->graphs.size() - 1);
+      idx->push_back(p->graphs.size() - 1);
     }
   }
+  return LINVIEW_OK;
+}
+
+static linview_status graph_propagate(linview_program* p, int r, cudaStream_t s) {
+  const bool inst = p->prof;
+  std::vector<size_t> idx;
+  LV_TRY(graphs_for(p, r, inst, &idx));
   size_t pick = idx[0];
   if (inst) {
     if ((int)p->prof_rr.size() <= r) p->prof_rr.resize(r + 1, 0);
@@ -2903,6 +2910,18 @@ linview_status linview_apply_row_block(linview_program* p, int64_t kr, const int
   LV_TRY(propagate(p, (int)kr, s));
   LV_TRY(ols_history_push(p, (int)kr, s));
   return after_update(p, s);
+}
+
+linview_status linview_prepare_updates(linview_program* p, int32_t max_rank, void* stream) {
+  if (!p) return fail(LINVIEW_EINVAL, "null program");
+  if (max_rank < 1 || max_rank > p->d.r_max)
+    return fail(LINVIEW_ERANK, "max_rank must be in 1..r_max (%d)", p->d.r_max);
+  (void)stream;  // capture only: nothing is queued
+  if (!p->use_graphs || p->d.kind == LINVIEW_OLS) return LINVIEW_OK;
+  LV_CUDA(cudaSetDevice(p->device));
+  std::vector<size_t> idx;
+  for (int r = 1; r <= max_rank; ++r) LV_TRY(graphs_for(p, r, p->prof, &idx));
+  return LINVIEW_OK;
 }
 
 linview_status linview_sync(linview_program* p, void* stream) {

@@ -12,7 +12,8 @@
 // A request of rank above the coalescing cap takes the re-evaluation strategy
 // instead (Section 4.2.2: apply the delta, recompute): it and every request
 // queued behind it are added to A by update-only level passes, and every view
-// of the program is recomputed from the new A (linview_reeval).
+// of the program is recomputed from the new A (linview_reeval).  A view's
+// propagation graphs for ranks 1..r_cap are captured when it is admitted.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -145,6 +146,13 @@ linview_status create_view_program(linview_server* s, ServedView* v, const void*
     (void)cudaGetLastError();
     linview_destroy(prog);
     return set_err(LINVIEW_EDEVICE, "view creation failed on the device");
+  }
+  // every coalesced rank the view can see, captured now rather than by the
+  // first request of each rank
+  st = linview_prepare_updates(prog, s->r_cap, v->stream);
+  if (st != LINVIEW_OK) {
+    linview_destroy(prog);
+    return st;
   }
   v->prog = prog;
   return LINVIEW_OK;

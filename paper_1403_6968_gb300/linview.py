@@ -310,6 +310,12 @@ class Program:
     def set_reeval_mode(self, mode):
         L.call("linview_set_reeval_mode", self.h, REEVAL[mode] if isinstance(mode, str) else mode)
 
+    def prepare_updates(self, max_rank=None, stream=None):
+        """Capture the propagation graphs of update ranks 1..max_rank (default
+        r_max) now, so that no first update of a rank pays for the capture."""
+        r = self.desc.r_max if max_rank is None else int(max_rank)
+        L.call("linview_prepare_updates", self.h, r, _stream_ptr(stream))
+
     def sync(self, stream=None):
         L.call("linview_sync", self.h, _stream_ptr(stream))
 

@@ -299,6 +299,37 @@ def test_nonfinite_delta_is_reported(prec, r):
     fresh.close()
 
 
+@pytest.mark.parametrize("kind,model", [("power_sum", "exp"), ("power", "linear")])
+def test_prepare_updates_then_every_rank(kind, model):
+    """linview_prepare_updates captures the propagation graphs of ranks
+    1..r_max without running anything (the views are unchanged); updates of
+    every rank afterwards replay them and match the oracle.  max_rank past
+    r_max is ERANK."""
+    from paper_1403_6968_gb300 import LinviewError
+    n, k, r_max = 300, 8, 4
+    a = li.power_matrix(n, seed=81, dtype=np.float32)
+    prog = _prog(kind, [_dev(a)], k=k, r_max=r_max, model=model)
+    before = prog.read_view_host(1)
+    prog.prepare_updates()
+    prog.sync()
+    assert np.array_equal(prog.read_view_host(1), before)
+    with pytest.raises(LinviewError) as e:
+        prog.prepare_updates(r_max + 1)
+    assert e.value.name == "ERANK"
+    acur = a.astype(np.float64)
+    for r in range(1, r_max + 1):
+        (u, v), = li.lowrank_update_stream(n, r, 1, seed=82 + r, dtype=np.float32)
+        prog.apply_delta(_dev(u), _dev(v))
+        acur += u.astype(np.float64) @ v.astype(np.float64).T
+    prog.sync()
+    if model == "exp":
+        _check_all(prog, acur, k, kind == "power_sum", TOL["f32"])
+    else:
+        pw = op.reeval_powers(acur, k)
+        assert rel_frob(prog.read_view_host(k - 1), pw[k]) <= TOL["f32"]
+    prog.close()
+
+
 def test_device_pointer_flags_are_checked():
     """Entry points that take device pointers refuse host memory flagged as
     device memory with EINVAL before any launch.  The host memory here is
