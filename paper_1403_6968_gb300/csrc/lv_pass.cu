@@ -540,7 +540,7 @@ static cudaError_t launch_fused_t(const PassParams& p, const CUtensorMap& tm, cu
   Kfn kfn;
   if constexpr (kWs) {
     // the TMA write-back variant exists for the non-split update modes only
-    constexpr bool kTs = (MODE & 4) != 0 && R <= 2;
+    constexpr bool kTs = (MODE & 4) != 0 && R <= 4;
     static const cudaError_t configured_ts =
         cudaFuncSetAttribute(fused_ws_kernel<R, MODE, kTs>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -116,12 +116,14 @@ __device__ __forceinline__ void rank_update_row(const float* u, const float (&pv
 // Fused products (+ update) pass, FP32, R in {1, 2, 4, 8}; products only
 // (no update) also R = 16.
 // Thread (rg = warp / 4, tc = tid % 128) owns columns strip0 + 4 tc .. +3.
-//  R <= 2: row group rg takes rows rg, rg+2, rg+4, rg+6 of every batch (all
-//          R factor columns);
-//  R >= 4 (SPLIT): row group rg takes the products P U and P^T V of factor
+//  R <= 4: row group rg takes rows rg, rg+2, rg+4, rg+6 of every batch (all
+//          R factor columns); every element is read and updated by one
+//          thread, so updated tiles can leave by TMA store;
+//  R >= 8 (SPLIT): row group rg takes the products P U and P^T V of factor
 //          columns rg R/2 .. rg R/2 + R/2 - 1 on all 8 rows of the batch, and
 //          the in-place update of rows 4 rg .. 4 rg + 3; this halves the
-//          column factors each thread keeps in registers.
+//          column factors each thread keeps in registers (R = 4 fits without:
+//          89 us instead of 93 at n = 8192, with the TMA store).
 // ---------------------------------------------------------------------------
 template <int R, int MODE, bool TS>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   constexpr bool DO_U = (MODE & 4) != 0;
   constexpr bool PACK = R >= 2;
   constexpr int R2 = PACK ? R / 2 : 1;
-  constexpr bool SPLIT = R >= 4;
+  constexpr bool SPLIT = R >= 8;
   constexpr int RH = SPLIT ? R / 2 : R;          // factor columns of the products per group
   constexpr int RH2 = PACK ? RH / 2 : 1;         // ... as packed pairs
   constexpr int ROWS = SPLIT ? kBatch : kBatch / 2;  // batch rows a thread visits
