@@ -142,7 +142,8 @@ def test_level_pass_kernel(prec, n, r, upd):
 
 
 @pytest.mark.parametrize("n,r,upd", [(200, 17, True), (1000, 32, False), (1031, 33, True),
-                                     (2048, 48, True), (129, 64, True), (4100, 64, False)])
+                                     (2048, 48, True), (129, 64, True), (4100, 64, False),
+                                     (20, 24, True), (33, 40, False)])
 def test_tensor_core_products_pass(n, r, upd):
     """Level passes wider than 16 columns in FP32 with a factor stride that is
     a multiple of 64: X = P U and Y = P^T V run on the tensor cores (split
