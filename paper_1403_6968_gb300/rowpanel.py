@@ -1,4 +1,6 @@
-"""Row-panel sharding of one maintained power program over W GPUs: the plan.
+"""Row-panel sharding of one maintained program over W GPUs: the plan
+(power programs below; the general iteration and OLS in iteration_exchanges
+and ols_exchanges).
 
 Host logic only (no arithmetic of the method).  Each rank owns the rows
 [r0, r1) of every view P_h and S'_h of the exponential model; the factor
@@ -64,3 +66,45 @@ def update_exchange_bytes(n: int, k: int, r: int, world: int, elem_bytes: int = 
     """Total payload of the collectives of one update (all levels)."""
     return sum(e["allgather"]["bytes"] + e["allreduce"]["bytes"]
                for e in level_exchanges(n, k, r, world, elem_bytes))
+
+
+def iteration_exchanges(n: int, p: int, k: int, r: int, world: int, elem_bytes: int = 4):
+    """The exchanges of one rank-r update of A in the general iteration
+    T_i = A T_{i-1} + B (linear model, Appendix B) with the rows of A and of
+    every T_i sharded like the views above and the factors replicated.
+
+    The Krylov blocks K_j = A' K_{j-1} (A' = A + U V^T; K_0 = U) are the only
+    products with A: each rank computes its row block from its rows of A,
+    the replicated K_{j-1} and (V^T K_{j-1}), then an all-gather gives every
+    rank K_j (j = 1 .. k-1).  The right factors T_i^T V (i = 0 .. k-1, p x r
+    each) are partial sums over the owned rows: one all-reduce of all k of
+    them.  T_i += [K_0 .. K_{i-1}] [M_{i-1} .. M_0]^T and A += U V^T touch
+    only the owned rows."""
+    if n < 1 or p < 1 or k < 1 or r < 1:
+        raise ValueError("need n, p, k, r >= 1")
+    rows = [b - a for a, b in panels(n, world)]
+    out = [{"op": "all_gather", "what": f"K_{j} row blocks", "rows_per_rank": rows, "cols": r,
+            "bytes": n * r * elem_bytes} for j in range(1, k)]
+    out.append({"op": "all_reduce_sum", "what": "partial T_i^T V, i = 0 .. k-1",
+                "rows": k * r, "cols": p, "bytes": k * r * p * elem_bytes})
+    return out
+
+
+def ols_exchanges(n: int, p: int, kr: int, world: int, elem_bytes: int = 4):
+    """The exchanges of one replacement of kr rows of X (Section 4.1, block
+    Woodbury) with the rows of W, beta and X^T Y sharded and the update's
+    data (the old and new rows of X, their rows of Y) replicated.
+
+    G = W U (U = [X'_R^T, X_R^T], n x 2kr): row blocks from the owned rows of
+    W, then an all-gather; the core C^-1 + U^T G, its inverse and
+    Wu = -G M^-1 follow redundantly on every rank.  W += G Wu^T and
+    X^T Y += (X'_R - X_R)^T Y_R touch only the owned rows.  The refresh of
+    beta needs H = Wu^T (X^T Y)' (2kr x p), partial sums over the owned rows:
+    one all-reduce; then beta += (G_1 - G_2) Y_R + G H on the owned rows."""
+    if n < 1 or p < 1 or kr < 1:
+        raise ValueError("need n, p, kr >= 1")
+    rows = [b - a for a, b in panels(n, world)]
+    return [{"op": "all_gather", "what": "G = W U row blocks", "rows_per_rank": rows,
+             "cols": 2 * kr, "bytes": n * 2 * kr * elem_bytes},
+            {"op": "all_reduce_sum", "what": "partial H = Wu^T (X^T Y)'", "rows": 2 * kr,
+             "cols": p, "bytes": 2 * kr * p * elem_bytes}]

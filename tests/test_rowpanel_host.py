@@ -129,3 +129,149 @@ def test_panels_and_plan():
     assert rowpanel.update_exchange_bytes(8192, 16, 1, 8) == 2 * 8192 * 15 * 4
     with pytest.raises(ValueError):
         rowpanel.level_exchanges(100, 12, 1, 2)
+
+
+def _gloo(rank, ws, port):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    return dist
+
+
+def _collectives(dist, pan, ws, sent):
+    import torch
+    maxrows = max(b - a for a, b in pan)
+
+    def all_gather_rows(x_loc):
+        buf = np.zeros((maxrows, x_loc.shape[1]))
+        buf[:x_loc.shape[0]] = x_loc
+        parts = [torch.zeros(maxrows, x_loc.shape[1], dtype=torch.float64) for _ in range(ws)]
+        dist.all_gather(parts, torch.from_numpy(buf))
+        out = np.concatenate([parts[w].numpy()[:b - e] for w, (e, b) in enumerate(pan)])
+        sent.append(("all_gather", out.nbytes))
+        return out
+
+    def all_reduce_sum(y_part):
+        t = torch.from_numpy(np.ascontiguousarray(y_part))
+        dist.all_reduce(t)
+        sent.append(("all_reduce_sum", t.numpy().nbytes))
+        return t.numpy()
+
+    return all_gather_rows, all_reduce_sum
+
+
+def _rank_iteration(rank, ws, port, outdir, n, p, k, r, nupd):
+    """Linear model of the general iteration with the rows of A and every T_i
+    owned: K_j from the owned rows of A and an all-gather, the right factors
+    T_i^T V from one all-reduce, the refreshes on the owned rows."""
+    dist = _gloo(rank, ws, port)
+    import linview_inputs as li
+    from oracle import iteration as oi
+    from paper_1403_6968_gb300 import rowpanel
+    pan = rowpanel.panels(n, ws)
+    r0, r1 = pan[rank]
+    sent = []
+    gather, reduce = _collectives(dist, pan, ws, sent)
+    a, b, t0 = li.iteration_inputs(n, p, seed=11)
+    full = oi.reeval(a, b, t0, k)
+    T = {i: full[i][r0:r1].copy() for i in range(k + 1)}
+    A = a[r0:r1].copy()
+    acur = a.copy()
+    for u, v in li.lowrank_update_stream(n, r, nupd, seed=12, sigma=0.2):
+        acur += u @ v.T
+        # M_i = T_i^T v (old T_i), i = 0 .. k-1: one all-reduce of all of them
+        M = reduce(np.stack([T[i].T @ v[r0:r1] for i in range(k)]))
+        K = [u]
+        for j in range(1, k):                      # K_j = (A + u v^T) K_{j-1}
+            K.append(gather(A @ K[j - 1] + u[r0:r1] @ (v.T @ K[j - 1])))
+        A += u[r0:r1] @ v.T
+        for i in range(1, k + 1):                  # T_i += sum_a K_a M_{i-1-a}^T
+            T[i] += sum(K[q][r0:r1] @ M[i - 1 - q].T for q in range(i))
+    ref = oi.reeval(acur, b, t0, k)
+    err = max(float(np.linalg.norm(T[i] - ref[i][r0:r1]) / np.linalg.norm(ref[i][r0:r1]))
+              for i in range(1, k + 1))
+    err = max(err, float(np.linalg.norm(A - acur[r0:r1]) / np.linalg.norm(acur[r0:r1])))
+    with open(os.path.join(outdir, f"it{rank}.json"), "w") as f:
+        json.dump({"err": err, "sent": sent}, f)
+    dist.destroy_process_group()
+
+
+def _rank_ols(rank, ws, port, outdir, m, n, p, kr, nupd):
+    """Block Woodbury with the rows of W, beta and X^T Y owned: G from the
+    owned rows of W and an all-gather, H = Wu^T (X^T Y)' from one all-reduce,
+    every refresh on the owned rows (X and the replaced rows replicated)."""
+    dist = _gloo(rank, ws, port)
+    import linview_inputs as li
+    from oracle import ols as oo
+    from paper_1403_6968_gb300 import rowpanel
+    pan = rowpanel.panels(n, ws)
+    r0, r1 = pan[rank]
+    sent = []
+    gather, reduce = _collectives(dist, pan, ws, sent)
+    x, y, _ = li.ols_inputs(m, n, p, seed=13)
+    ref = oo.reeval(x, y)
+    W, beta, xty = ref["W"][r0:r1].copy(), ref["beta"][r0:r1].copy(), ref["XtY"][r0:r1].copy()
+    for rows, new in li.ols_row_replacements(m, n, kr, nupd, seed=14, cols_seed=13):
+        old = x[rows].copy()
+        U = np.hstack([new.T, old.T])                          # n x 2kr
+        c = np.concatenate([np.ones(kr), -np.ones(kr)])
+        G = gather(W @ U)
+        wu = -G @ np.linalg.inv(np.diag(1.0 / c) + U.T @ G)
+        W += G[r0:r1] @ wu.T
+        yr = y[rows]
+        xty += (new - old).T[r0:r1] @ yr
+        H = reduce(wu[r0:r1].T @ xty)                          # 2kr x p
+        beta += (G[r0:r1, :kr] - G[r0:r1, kr:]) @ yr + G[r0:r1] @ H
+        x[rows] = new
+    fresh = oo.reeval(x, y)
+    err = max(float(np.linalg.norm(W - fresh["W"][r0:r1]) / np.linalg.norm(fresh["W"][r0:r1])),
+              float(np.linalg.norm(beta - fresh["beta"][r0:r1]) /
+                    np.linalg.norm(fresh["beta"][r0:r1])))
+    with open(os.path.join(outdir, f"ols{rank}.json"), "w") as f:
+        json.dump({"err": err, "sent": sent}, f)
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("ws,n", [(2, 29), (3, 48)])
+def test_sharded_iteration_equals_the_oracle(tmp_path, ws, n):
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    from paper_1403_6968_gb300 import rowpanel
+    p, k, r, nupd = 3, 8, 2, 3
+    mp.spawn(_rank_iteration, args=(ws, _free_port(), str(tmp_path), n, p, k, r, nupd),
+             nprocs=ws, join=True)
+    plan = rowpanel.iteration_exchanges(n, p, k, r, ws, elem_bytes=8)
+    # the all-reduce of the right factors comes first in an update, then the gathers
+    want = [(plan[-1]["op"], plan[-1]["bytes"])] + [(e["op"], e["bytes"]) for e in plan[:-1]]
+    for w in range(ws):
+        got = json.load(open(tmp_path / f"it{w}.json"))
+        assert got["err"] <= 1e-11, got["err"]
+        assert [tuple(s) for s in got["sent"]] == want * nupd
+
+
+@pytest.mark.parametrize("ws,kr", [(2, 1), (3, 4)])
+def test_sharded_ols_equals_the_oracle(tmp_path, ws, kr):
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    from paper_1403_6968_gb300 import rowpanel
+    m, n, p, nupd = 200, 20, 3, 3
+    mp.spawn(_rank_ols, args=(ws, _free_port(), str(tmp_path), m, n, p, kr, nupd),
+             nprocs=ws, join=True)
+    plan = rowpanel.ols_exchanges(n, p, kr, ws, elem_bytes=8)
+    for w in range(ws):
+        got = json.load(open(tmp_path / f"ols{w}.json"))
+        assert got["err"] <= 1e-9, got["err"]
+        assert [tuple(s) for s in got["sent"]] == [(e["op"], e["bytes"]) for e in plan] * nupd
+
+
+def test_iteration_and_ols_plans():
+    from paper_1403_6968_gb300 import rowpanel
+    it = rowpanel.iteration_exchanges(8192, 64, 16, 2, 8)
+    assert [e["op"] for e in it] == ["all_gather"] * 15 + ["all_reduce_sum"]
+    # n = 8192, p = 64, k = 16, rank 2: 15 x 64 KB gathers + one 8 KB reduction
+    assert sum(e["bytes"] for e in it) == 15 * 8192 * 2 * 4 + 16 * 2 * 64 * 4
+    ols = rowpanel.ols_exchanges(4096, 16, 16, 8)
+    assert [e["bytes"] for e in ols] == [4096 * 32 * 4, 32 * 16 * 4]
+    with pytest.raises(ValueError):
+        rowpanel.ols_exchanges(0, 1, 1, 2)
